@@ -1,0 +1,237 @@
+/*
+ * hybrid1d.h -- C ABI of the GB300 kinetic-electron PIC/MCC library.
+ *
+ * The library advances the electron part of the 1D hybrid scheme of Eremin,
+ * Hemke and Mussenbrock (arXiv 1508.02892) on one GPU: electron
+ * macroparticles (Sec. II.A, Eqs. 1.1-1.2) pushed by leapfrog in the
+ * CIC-interpolated field, removed at the walls, CIC-deposited, and collided
+ * with the background gas by the modified null-collision method; impact
+ * ionization births and gamma secondary emission (Sec. II.D); coupled every
+ * step to the ion fluid (drift-diffusion, Eqs. 2.5-2.8, or the full model,
+ * Eqs. 2.3-2.4) and to the Poisson equation (Sec. II.D).
+ *
+ * Units are SI unless a name says otherwise (_ev, _amu, _td).  The geometry is
+ * planar: quantities are per unit electrode area (S = 1 m^2 in Eq. 1.2), so
+ * the macroparticle weight is in m^-2 and fluxes in m^-2 s^-1.
+ *
+ * Conventions for every call:
+ *   - returns HYB_OK (0), a positive warning, or a negative HYB_ERR_*; on an
+ *     error hyb_last_error() gives a thread-local message;
+ *   - pointers marked "host" are read or written by the call before it
+ *     returns and stay owned by the caller; the library owns all device
+ *     memory it allocates and frees it in the matching destroy call;
+ *   - a handle is not thread-safe; distinct handles are independent;
+ *   - device work is enqueued on the stream given at creation (NULL: the
+ *     library creates its own); advance calls return before the GPU is done,
+ *     read/sync calls wait for it.
+ */
+#ifndef HYBRID1D_H
+#define HYBRID1D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define HYB_OK 0
+#define HYB_WARN_DT_NULLCOLL 1  /* nu_max*dt > 0.1: coarser than the time-step rule of Sec. II.A */
+#define HYB_ERR_ARG (-1)        /* invalid argument or parameter */
+#define HYB_ERR_OOM (-2)        /* device memory, or the batch's HBM cap, exhausted */
+#define HYB_ERR_CAPACITY (-3)   /* particle store full: births were dropped */
+#define HYB_ERR_NONFINITE (-4)  /* NaN/Inf in an input table or in the fields */
+#define HYB_ERR_TIMEOUT (-5)    /* a bounded device wait gave up */
+#define HYB_ERR_CUDA (-6)       /* a CUDA runtime call failed */
+#define HYB_ERR_UNSTABLE (-7)   /* the ion-fluid update left its stability range */
+#define HYB_ERR_STATE (-8)      /* call not valid in the handle's current state */
+
+/* ---------------------------------------------------------------- choices */
+#define HYB_GAS_HE 0            /* background gas mass 4.002602 u */
+#define HYB_GAS_AR 1            /* background gas mass 39.948 u */
+
+#define HYB_ION_DD_CONST 0      /* drift-diffusion, constant mobility, T_i = T_gas (Eqs. 2.5-2.7) */
+#define HYB_ION_DD_TABLE 1      /* drift-diffusion, mu(E) table, T_i from Eq. 2.8 */
+#define HYB_ION_FULL 2          /* momentum equation with inertia, Eq. 2.3, nu(u) table */
+
+#define HYB_FP64 0              /* particles and grids in FP64 */
+#define HYB_FP32_SPLIT 1        /* particles as (cell, FP32 offset) + FP32 velocity; FP64 grids */
+
+#define HYB_MAX_CELLS 4000      /* largest grid a discharge may have */
+#define HYB_MAX_INSTANCES 256   /* largest batch */
+
+/* Problem statement of one discharge (Secs. II and III).  Copied at creation;
+ * the table pointers are host pointers read during the call. */
+typedef struct hyb_params {
+    double gap_m;               /* electrode distance L; powered electrode at z = 0 */
+    int32_t n_cells;            /* uniform grid, n_cells + 1 nodes, 2..HYB_MAX_CELLS */
+    int32_t gas;                /* HYB_GAS_* */
+    double pressure_pa;         /* background gas, uniform and frozen (Sec. II.A) */
+    double gas_temp_k;
+    double v_rf_amp_v;          /* phi(0, t) = v_dc_v + v_rf_amp_v sin(2 pi f_rf_hz t), phi(L) = 0 */
+    double f_rf_hz;
+    double v_dc_v;
+    double dt_s;                /* time step shared by electrons and ions */
+    int64_t n_particles;        /* initial electron macroparticles */
+    double n0_m3;               /* initial uniform electron and ion density */
+    double te0_ev;              /* initial Maxwellian temperature of the electrons */
+    double weight;              /* real electrons per m^2 per macroparticle; 0: n0 L / n_particles (Eq. 1.2, S = 1) */
+    double gamma_see;           /* ion-induced secondary emission coefficient (Sec. II.D) */
+    double see_energy_ev;       /* energy of an emitted secondary; 0: 1 eV */
+    int32_t ion_model;          /* HYB_ION_* */
+    double ion_mass_amu;        /* 0: the gas mass */
+    double gas_mass_amu;        /* 0: set by `gas` */
+    double mu_const;            /* mobility for HYB_ION_DD_CONST, m^2/(V s) */
+    const double *tab_eon_td;   /* host, n_tab increasing E/N values (Td) */
+    const double *tab_mu;       /* host, n_tab mobilities at tab_eon_td */
+    const double *tab_nu;       /* host, n_tab exchange frequencies at u = mu E (Sec. II.C) */
+    int32_t n_tab;              /* 0 allowed for HYB_ION_DD_CONST */
+    const double *xs_ev;        /* host, n_xs log-spaced energies (eV) */
+    const double *xs_el;        /* host, elastic cross section (m^2) at xs_ev */
+    const double *xs_exc;       /* host, excitation cross section */
+    const double *xs_ion;       /* host, ionization cross section */
+    int32_t n_xs;               /* >= 2 */
+    double e_exc_ev;            /* excitation threshold / energy loss */
+    double e_iz_ev;             /* ionization threshold / energy loss */
+    uint64_t seed;              /* Philox counter words 1-2 */
+    int32_t eedf_bins;          /* 0: 256 */
+    double eedf_max_ev;         /* 0: 64 eV */
+    int32_t precision;          /* HYB_FP64 or HYB_FP32_SPLIT */
+    double capacity_factor;     /* particle store = factor * n_particles (min 4096); 0: 2 */
+    int32_t sort_interval;      /* steps between cell sorts; 0: library default */
+} hyb_params;
+
+/* Time averages since creation or the last hyb_reset_moments (Sec. III
+ * diagnostics).  Caller-owned host buffers: n_nodes = n_cells + 1 entries for
+ * the profiles, eedf_bins + 1 for the EEDF (last entry = fraction above
+ * eedf_max_ev; the others are normalised so that sum f dE + last = 1).  Any
+ * pointer may be NULL to skip that quantity. */
+typedef struct hyb_moments {
+    double *ne;                 /* electron density, m^-3 */
+    double *ni;                 /* ion density, m^-3 */
+    double *gamma_i;            /* ion flux, m^-2 s^-1 */
+    double *mean_energy_ev;     /* CIC-weighted mean electron energy per node */
+    double *eedf;               /* eV^-1 */
+    int64_t n_samples;          /* out: steps averaged */
+} hyb_moments;
+
+/* Instantaneous grids after the last completed step; host buffers of n_nodes
+ * doubles, any may be NULL. */
+typedef struct hyb_fields {
+    double *ne, *ni, *gamma_i, *phi, *efield, *ion_source;
+} hyb_fields;
+
+/* Integer bookkeeping since creation. */
+typedef struct hyb_counters {
+    int64_t step;
+    int64_t particles;          /* live macroparticles */
+    int64_t births_ionization;
+    int64_t births_see[2];      /* gamma secondaries at z = 0 and z = L */
+    int64_t losses[2];          /* absorbed at z = 0 and z = L */
+    int64_t collisions[4];      /* elastic, excitation, ionization, null (candidates without a real collision) */
+    int64_t clamps;             /* ion densities clamped at zero */
+    uint32_t status;            /* bit set of HYB_STATUS_* below */
+} hyb_counters;
+
+#define HYB_STATUS_CAPACITY 1u
+#define HYB_STATUS_NONFINITE 2u
+#define HYB_STATUS_UNSTABLE 4u
+#define HYB_STATUS_EMIT_CAP 8u
+
+/* Derived constants of a discharge. */
+typedef struct hyb_info {
+    int32_t n_nodes, eedf_bins;
+    double weight, gas_density, nu_max, p_max, dz;
+    int64_t capacity;
+    int64_t device_bytes;
+} hyb_info;
+
+typedef struct hyb_discharge hyb_discharge;
+typedef struct hyb_batch hyb_batch;
+
+/* ----------------------------------------------------- single discharge */
+
+/* Create a discharge: validate, derive the constants of Secs. II.A-II.D
+ * (gas density p/(k_B T), weight of Eq. 1.2, nu_max over the table nodes,
+ * P_max = 1 - exp(-nu_max dt)), load n_particles electrons (uniform positions,
+ * Maxwellian at te0_ev, drawn from Philox at step 0xFFFFFFFF), deposit them
+ * and solve the initial field.  `stream` is a cudaStream_t or NULL.  Returns
+ * HYB_WARN_DT_NULLCOLL (handle valid) when nu_max dt > 0.1. */
+int hyb_create_discharge(const hyb_params *p, void *stream, hyb_discharge **out);
+
+/* Enqueue n_steps full steps (push, wall removal, deposit, MCC and births;
+ * ion fluid; Poisson; moments; secondaries for the next step). */
+int hyb_advance(hyb_discharge *h, int64_t n_steps);
+
+/* Wait for the enqueued work; returns the first error the device flagged. */
+int hyb_sync(hyb_discharge *h);
+
+int hyb_read_moments(hyb_discharge *h, hyb_moments *out);
+int hyb_read_fields(hyb_discharge *h, hyb_fields *out);
+int hyb_read_counters(hyb_discharge *h, hyb_counters *out);
+int hyb_get_info(hyb_discharge *h, hyb_info *out);
+int hyb_reset_moments(hyb_discharge *h);
+
+/* Copy the live particles, sorted by id, into host arrays of `cap` entries
+ * (position z in m, velocity in m/s, FP64 whatever the precision); *n gets
+ * the live count (HYB_ERR_ARG if it exceeds cap). */
+int hyb_read_particles(hyb_discharge *h, double *z, double *vx, double *vy, double *vz, uint64_t *id,
+                       int64_t cap, int64_t *n);
+
+/* Replace the whole particle set (including secondaries already born for the
+ * next step) with n host particles and re-solve the field for the current
+ * time.  Positions must lie in [0, L). */
+int hyb_write_particles(hyb_discharge *h, int64_t n, const double *z, const double *vx, const double *vy,
+                        const double *vz, const uint64_t *id);
+
+/* Overwrite the ion density (host, n_nodes values) and re-solve the field. */
+int hyb_write_ion_density(hyb_discharge *h, const double *ni);
+
+int hyb_destroy(hyb_discharge *h);
+
+/* ------------------------------------------------ batches and serving */
+
+/* A batch advances up to max_instances independent discharges of one
+ * precision in lockstep launches (one electron kernel over all instances'
+ * particles, one field block per instance).  hbm_cap_bytes bounds the device
+ * memory of admitted instances (0: no cap). */
+int hyb_batch_create(int32_t max_instances, int32_t precision, int64_t hbm_cap_bytes, void *stream,
+                     hyb_batch **out);
+
+/* Device bytes an instance with these parameters would hold. */
+int hyb_footprint(const hyb_params *p, int64_t *bytes);
+
+/* Admit a discharge into a free slot; it runs for n_steps steps of later
+ * hyb_batch_advance calls (n_steps <= 0: until evicted) and then stops by
+ * itself.  HYB_ERR_OOM when the cap or the slots are exhausted. */
+int hyb_batch_admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int32_t *slot);
+
+/* Enqueue n_steps steps of every running instance. */
+int hyb_batch_advance(hyb_batch *b, int64_t n_steps);
+
+/* Wait, then report in done[0..*n_done) the slots that reached their step
+ * count since the last poll (cap entries at most). */
+int hyb_batch_poll(hyb_batch *b, int32_t *done, int32_t cap, int32_t *n_done);
+
+/* Per-slot reads (wait for the GPU first). */
+int hyb_batch_read_moments(hyb_batch *b, int32_t slot, hyb_moments *out);
+int hyb_batch_read_counters(hyb_batch *b, int32_t slot, hyb_counters *out);
+int hyb_batch_read_particles(hyb_batch *b, int32_t slot, double *z, double *vx, double *vy, double *vz,
+                             uint64_t *id, int64_t cap, int64_t *n);
+
+/* Free a slot and its memory (waits for the GPU). */
+int hyb_batch_evict(hyb_batch *b, int32_t slot);
+
+/* Running slots, live particles over them, device bytes held. */
+int hyb_batch_stats(hyb_batch *b, int32_t *running, int64_t *particles, int64_t *bytes);
+
+int hyb_batch_destroy(hyb_batch *b);
+
+/* Thread-local message of the last error. */
+const char *hyb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYBRID1D_H */

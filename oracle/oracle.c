@@ -13,7 +13,9 @@
  * (fluid ions, Poisson).  Where the paper is silent the readings are:
  *   - work per unit electrode area, S = 1 m^2 (Eq. 1.2);
  *   - 1D3V velocities, leapfrog start v^{-1/2} = v^0;
- *   - gamma secondaries for step n are born from the ion wall flux of step n-1;
+ *   - gamma secondaries for step n are born from the ion wall flux of step n-1,
+ *     at the end of step n-1 (so they are part of the particle set between
+ *     steps);
  *   - deposit before MCC, so ionization children enter n_e one step later;
  *   - boundary rows of Eqs. 2.3/2.4 by half-cell integration with a Dirichlet
  *     wall flux alpha*mu*n*E (Sec. II.C wall condition) at the wall nodes;
@@ -678,12 +680,12 @@ void orc_init_field(orc_sim *s)
     memset(s->dep_n, 0, sizeof(double) * s->G);
 }
 
-/* One full step n -> n+1 (Secs. II.A and II.D). */
+/* One full step n -> n+1 (Secs. II.A and II.D), ending with the gamma
+ * secondaries that will take part in step n+1. */
 static void step_once(orc_sim *s)
 {
     int G = s->G;
     uint32_t n = (uint32_t)s->step;
-    emit_secondaries(s, n);
     memset(s->dep_n, 0, sizeof(double) * G);
     memset(s->dep_e, 0, sizeof(double) * G);
     memset(s->s_iz, 0, sizeof(double) * G);
@@ -738,6 +740,8 @@ static void step_once(orc_sim *s)
     }
     s->n_samples++;
     s->step++;
+    /* secondaries of the next step, from the ion wall flux just computed */
+    emit_secondaries(s, (uint32_t)s->step);
 }
 
 int orc_step(orc_sim *s, int64_t nsteps)

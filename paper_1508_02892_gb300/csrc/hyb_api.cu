@@ -1,0 +1,1036 @@
+// hyb_api.cu -- host runtime behind the C ABI of include/hybrid1d.h: parameter
+// validation and derived constants (arXiv 1508.02892, Secs. II.A-II.D),
+// instance slots with one device allocation each, the HBM cap of a batch, the
+// initial load, CUDA-graph chunks of steps, reads and writes of the state.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "hyb_internal.cuh"
+
+using namespace hyb;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(expr)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (expr);                                                                  \
+        if (e_ != cudaSuccess) return fail(HYB_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kDefaultSort = 16;
+constexpr int kElectronBlock = 256;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t part_bytes, grid_off, total;
+    size_t off[64];
+    int n;
+};
+
+struct Slot {
+    bool used = false;
+    bool reported = false;
+    hyb_params p{};
+    InstDev h{};
+    void *mem = nullptr;
+    int64_t bytes = 0;
+    int64_t target = 0;
+};
+
+double mass_gas_amu(const hyb_params &p)
+{
+    if (p.gas_mass_amu > 0) return p.gas_mass_amu;
+    return p.gas == HYB_GAS_AR ? 39.948 : 4.002602;
+}
+
+int bins_of(const hyb_params &p) { return p.eedf_bins > 0 ? p.eedf_bins : 256; }
+
+int64_t capacity_of(const hyb_params &p)
+{
+    const double f = p.capacity_factor > 0 ? p.capacity_factor : 2.0;
+    int64_t c = (int64_t)ceil(f * (double)p.n_particles);
+    return c < 4096 ? 4096 : c;
+}
+
+bool finite_all(const double *x, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(x[i])) return false;
+    return true;
+}
+
+int validate(const hyb_params *p)
+{
+    if (!p) return fail(HYB_ERR_ARG, "params is NULL");
+    if (!(p->gap_m > 0) || !(p->dt_s > 0) || !(p->pressure_pa > 0) || !(p->gas_temp_k > 0))
+        return fail(HYB_ERR_ARG, "gap, dt, pressure and gas temperature must be positive");
+    if (p->n_cells < 2 || p->n_cells > HYB_MAX_CELLS)
+        return fail(HYB_ERR_ARG, "n_cells must be in [2, %d]", HYB_MAX_CELLS);
+    if (p->gas != HYB_GAS_HE && p->gas != HYB_GAS_AR) return fail(HYB_ERR_ARG, "unknown gas");
+    if (p->n_particles < 0 || p->n0_m3 < 0 || p->te0_ev < 0 || p->weight < 0 || p->gamma_see < 0)
+        return fail(HYB_ERR_ARG, "negative particle count, density, temperature, weight or gamma");
+    if (p->precision != HYB_FP64 && p->precision != HYB_FP32_SPLIT) return fail(HYB_ERR_ARG, "unknown precision");
+    if (p->ion_model < HYB_ION_DD_CONST || p->ion_model > HYB_ION_FULL) return fail(HYB_ERR_ARG, "unknown ion model");
+    if (p->eedf_bins < 0 || p->eedf_bins > 4096) return fail(HYB_ERR_ARG, "eedf_bins must be in [0, 4096]");
+    if (!p->xs_ev || !p->xs_el || !p->xs_exc || !p->xs_ion || p->n_xs < 2)
+        return fail(HYB_ERR_ARG, "cross-section tables missing");
+    if (!finite_all(p->xs_ev, p->n_xs) || !finite_all(p->xs_el, p->n_xs) || !finite_all(p->xs_exc, p->n_xs) ||
+        !finite_all(p->xs_ion, p->n_xs))
+        return fail(HYB_ERR_NONFINITE, "non-finite cross-section table entry");
+    if (!(p->xs_ev[0] > 0)) return fail(HYB_ERR_ARG, "cross-section energies must be positive");
+    for (int i = 1; i < p->n_xs; ++i)
+        if (!(p->xs_ev[i] > p->xs_ev[i - 1])) return fail(HYB_ERR_ARG, "cross-section energies must increase");
+    for (int i = 0; i < p->n_xs; ++i)
+        if (p->xs_el[i] < 0 || p->xs_exc[i] < 0 || p->xs_ion[i] < 0)
+            return fail(HYB_ERR_ARG, "negative cross section");
+    if (p->e_exc_ev < 0 || p->e_iz_ev < 0) return fail(HYB_ERR_ARG, "negative threshold");
+    if (p->ion_model != HYB_ION_DD_CONST) {
+        if (!p->tab_eon_td || !p->tab_mu || !p->tab_nu || p->n_tab < 2)
+            return fail(HYB_ERR_ARG, "ion transport tables missing");
+        if (!finite_all(p->tab_eon_td, p->n_tab) || !finite_all(p->tab_mu, p->n_tab) ||
+            !finite_all(p->tab_nu, p->n_tab))
+            return fail(HYB_ERR_NONFINITE, "non-finite ion transport table entry");
+        for (int k = 1; k < p->n_tab; ++k)
+            if (!(p->tab_eon_td[k] > p->tab_eon_td[k - 1])) return fail(HYB_ERR_ARG, "E/N table must increase");
+        if (p->ion_model == HYB_ION_FULL)
+            for (int k = 1; k < p->n_tab; ++k)
+                if (!(p->tab_mu[k] * p->tab_eon_td[k] > p->tab_mu[k - 1] * p->tab_eon_td[k - 1]))
+                    return fail(HYB_ERR_ARG, "drift speed mu E must increase along the table");
+    } else if (!(p->mu_const >= 0)) {
+        return fail(HYB_ERR_ARG, "mu_const must be non-negative");
+    }
+    if (!isfinite(p->v_rf_amp_v) || !isfinite(p->f_rf_hz) || !isfinite(p->v_dc_v))
+        return fail(HYB_ERR_NONFINITE, "non-finite drive");
+    return HYB_OK;
+}
+
+Layout layout_of(const hyb_params &p)
+{
+    Layout L{};
+    const int64_t cap = capacity_of(p);
+    const int G = p.n_cells + 1;
+    const int nb = bins_of(p);
+    size_t o = 0;
+    auto add = [&](size_t bytes) {
+        L.off[L.n++] = o;
+        o += align256(bytes);
+    };
+    // particle buffers x2
+    for (int b = 0; b < 2; ++b) {
+        if (p.precision == HYB_FP32_SPLIT) {
+            add(4 * cap);  // c
+            add(4 * cap);  // o
+            add(4 * cap);  // vx
+            add(4 * cap);  // vy
+            add(4 * cap);  // vz
+        } else {
+            add(8 * cap);  // z
+            add(8 * cap);
+            add(8 * cap);
+            add(8 * cap);
+        }
+        add(8 * cap);  // id
+    }
+    L.part_bytes = o;
+    L.grid_off = o;
+    for (int k = 0; k < 14; ++k) add(8 * (size_t)G);  // ni gam phi E ne gsrc dep_n dep_e s_iz acc x5
+    add(4 * (size_t)G);                                 // Ef
+    add(4 * (size_t)G);                                 // cell_cnt (n_cells + 1)
+    add(8 * (size_t)(nb + 1));                          // eedf
+    add(32 * (size_t)p.n_xs);                           // xs
+    add(16 * (size_t)p.n_xs);                           // xsf
+    add(32 * (size_t)(p.n_tab > 0 ? p.n_tab : 1));      // tab
+    L.total = o;
+    return L;
+}
+
+// sigma_k(E) with the log-index, linear-in-energy lookup and the thresholds.
+void xs_eval_host(const hyb_params &p, double e_lo, double e_hi, double inv_dlog, double en, double sig[3])
+{
+    const int n = p.n_xs;
+    int i;
+    double f;
+    if (en <= e_lo) {
+        i = 0;
+        f = 0.0;
+    } else if (en >= e_hi) {
+        i = n - 2;
+        f = 1.0;
+    } else {
+        const double x = log(en / e_lo) * inv_dlog;
+        i = (int)floor(x);
+        if (i < 0) i = 0;
+        if (i > n - 2) i = n - 2;
+        f = (en - p.xs_ev[i]) / (p.xs_ev[i + 1] - p.xs_ev[i]);
+    }
+    sig[0] = p.xs_el[i] + f * (p.xs_el[i + 1] - p.xs_el[i]);
+    sig[1] = p.xs_exc[i] + f * (p.xs_exc[i + 1] - p.xs_exc[i]);
+    sig[2] = p.xs_ion[i] + f * (p.xs_ion[i + 1] - p.xs_ion[i]);
+    if (en < p.e_exc_ev) sig[1] = 0.0;
+    if (en < p.e_iz_ev) sig[2] = 0.0;
+}
+
+// Derived constants of Secs. II.A-II.D; fills K (pointers excluded) and the
+// host copies of the tables.
+void derive(const hyb_params &p, InstDev &K, std::vector<double> &xs, std::vector<float4> &xsf,
+            std::vector<double> &tab)
+{
+    memset(&K, 0, sizeof K);
+    K.precision = p.precision;
+    K.n_cells = p.n_cells;
+    K.G = p.n_cells + 1;
+    K.ion_model = p.ion_model;
+    K.n_xs = p.n_xs;
+    K.n_tab = p.ion_model == HYB_ION_DD_CONST ? 0 : p.n_tab;
+    K.eedf_bins = bins_of(p);
+    K.capacity = capacity_of(p);
+    K.L = p.gap_m;
+    K.dz = p.gap_m / p.n_cells;
+    K.dt = p.dt_s;
+    K.ngas = p.pressure_pa / (kKb * p.gas_temp_k);
+    K.w = p.weight > 0 ? p.weight : (p.n_particles > 0 ? p.n0_m3 * p.gap_m / (double)p.n_particles : 0.0);
+    const double mg = mass_gas_amu(p);
+    K.m_gas = mg * kAmu;
+    K.m_ion = (p.ion_mass_amu > 0 ? p.ion_mass_amu : mg) * kAmu;
+    K.qm = kQe / kMe;
+    K.n_floor = 1e-6 * p.n0_m3;
+    K.bin_w = (p.eedf_max_ev > 0 ? p.eedf_max_ev : 64.0) / K.eedf_bins;
+    K.e_lo = p.xs_ev[0];
+    K.e_hi = p.xs_ev[p.n_xs - 1];
+    K.inv_dlog = (p.n_xs - 1) / log(K.e_hi / K.e_lo);
+    K.e_exc = p.e_exc_ev;
+    K.e_iz = p.e_iz_ev;
+    K.two_mM = 2.0 * (kMe / K.m_gas);
+    K.gamma_see = p.gamma_see;
+    K.see_speed = sqrt(2.0 * kQe * (p.see_energy_ev > 0 ? p.see_energy_ev : 1.0) / kMe);
+    K.v_rf = p.v_rf_amp_v;
+    K.f_rf = p.f_rf_hz;
+    K.v_dc = p.v_dc_v;
+    K.mu_const = p.mu_const;
+    K.kT_gas = kKb * p.gas_temp_k;
+    K.seed_lo = (uint32_t)p.seed;
+    K.seed_hi = (uint32_t)(p.seed >> 32);
+    // nu_max over the table nodes and P_max (Sec. II.A)
+    double nu_max = 0.0;
+    for (int i = 0; i < p.n_xs; ++i) {
+        double sig[3];
+        xs_eval_host(p, K.e_lo, K.e_hi, K.inv_dlog, p.xs_ev[i], sig);
+        const double v = sqrt(2.0 * kQe * p.xs_ev[i] / kMe);
+        const double nu = K.ngas * (sig[0] + sig[1] + sig[2]) * v;
+        if (nu > nu_max) nu_max = nu;
+    }
+    K.nu_max = nu_max;
+    K.p_max = 1.0 - exp(-nu_max * K.dt);
+    // FP32 copies
+    K.f_dt_dz = (float)(K.dt / K.dz);
+    K.f_qm_dt = (float)(K.qm * K.dt);
+    K.f_half_m_q = (float)(0.5 * kMe / kQe);
+    K.f_two_q_m = (float)(2.0 * kQe / kMe);
+    K.f_pmax = (float)K.p_max;
+    K.f_e_lo = (float)K.e_lo;
+    K.f_e_hi = (float)K.e_hi;
+    K.f_inv_e_lo = (float)(1.0 / K.e_lo);
+    K.f_inv_dlog = (float)K.inv_dlog;
+    K.f_e_exc = (float)K.e_exc;
+    K.f_e_iz = (float)K.e_iz;
+    K.f_two_mM = (float)K.two_mM;
+    K.f_bin_inv = (float)(1.0 / K.bin_w);
+    xs.resize(4 * (size_t)p.n_xs);
+    xsf.resize(p.n_xs);
+    const double scale = nu_max > 0 ? K.ngas / nu_max : 0.0;
+    for (int i = 0; i < p.n_xs; ++i) {
+        xs[4 * i + 0] = p.xs_ev[i];
+        xs[4 * i + 1] = p.xs_el[i];
+        xs[4 * i + 2] = p.xs_exc[i];
+        xs[4 * i + 3] = p.xs_ion[i];
+        xsf[i] = make_float4((float)p.xs_ev[i], (float)(scale * p.xs_el[i]), (float)(scale * p.xs_exc[i]),
+                             (float)(scale * p.xs_ion[i]));
+    }
+    const int nt = K.n_tab > 0 ? K.n_tab : 1;
+    tab.assign(4 * (size_t)nt, 0.0);
+    for (int k = 0; k < K.n_tab; ++k) {
+        tab[4 * k + 0] = p.tab_eon_td[k];
+        tab[4 * k + 1] = p.tab_mu[k];
+        tab[4 * k + 2] = p.tab_nu[k];
+        tab[4 * k + 3] = p.tab_mu[k] * p.tab_eon_td[k] * 1e-21 * K.ngas;
+    }
+}
+
+void bind_pointers(const hyb_params &p, const Layout &L, char *base, InstDev &K)
+{
+    int k = 0;
+    for (int b = 0; b < 2; ++b) {
+        PartBuf &B = K.buf[b];
+        memset(&B, 0, sizeof B);
+        if (p.precision == HYB_FP32_SPLIT) {
+            B.c = (int32_t *)(base + L.off[k++]);
+            B.o = (float *)(base + L.off[k++]);
+            B.vxf = (float *)(base + L.off[k++]);
+            B.vyf = (float *)(base + L.off[k++]);
+            B.vzf = (float *)(base + L.off[k++]);
+        } else {
+            B.z = (double *)(base + L.off[k++]);
+            B.vxd = (double *)(base + L.off[k++]);
+            B.vyd = (double *)(base + L.off[k++]);
+            B.vzd = (double *)(base + L.off[k++]);
+        }
+        B.id = (uint64_t *)(base + L.off[k++]);
+    }
+    double **grids[14] = {&K.ni, &K.gam, &K.phi, &K.E, &K.ne, &K.gsrc, &K.dep_n, &K.dep_e,
+                          &K.s_iz, &K.acc_ne, &K.acc_ni, &K.acc_gi, &K.acc_wn, &K.acc_we};
+    for (int g = 0; g < 14; ++g) *grids[g] = (double *)(base + L.off[k++]);
+    K.Ef = (float *)(base + L.off[k++]);
+    K.cell_cnt = (int32_t *)(base + L.off[k++]);
+    K.eedf = (unsigned long long *)(base + L.off[k++]);
+    K.xs = (const double *)(base + L.off[k++]);
+    K.xsf = (const float4 *)(base + L.off[k++]);
+    K.tab = (const double *)(base + L.off[k++]);
+}
+
+}  // namespace
+
+struct hyb_batch {
+    int max_inst = 0;
+    int precision = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    InstDev *d_inst = nullptr;
+    int64_t *d_prefix = nullptr;
+    int64_t *d_prefix1 = nullptr;
+    unsigned *d_ticket = nullptr;
+    unsigned *d_ticket1 = nullptr;
+    std::vector<Slot> slots;
+    int64_t hbm_cap = 0, hbm_used = 0;
+    int max_nodes = 0, max_bins = 0;
+    LaunchCfg cfg{};
+    int sort_interval = kDefaultSort;
+    int since_sort = 0;
+    cudaGraphExec_t graph = nullptr;
+    int num_sms = 0;
+    InstDev *h_stage = nullptr;  // pinned, max_inst entries
+};
+
+struct hyb_discharge {
+    hyb_batch *b;
+    int slot;
+};
+
+namespace {
+
+int fetch_inst(hyb_batch *b, int slot)
+{
+    CK(cudaMemcpyAsync(&b->h_stage[slot], &b->d_inst[slot], sizeof(InstDev), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return HYB_OK;
+}
+
+int status_code(unsigned st)
+{
+    if (st & HYB_STATUS_NONFINITE) return fail(HYB_ERR_NONFINITE, "non-finite field or ion density");
+    if (st & HYB_STATUS_CAPACITY) return fail(HYB_ERR_CAPACITY, "particle store full: births dropped");
+    if (st & HYB_STATUS_UNSTABLE) return fail(HYB_ERR_UNSTABLE, "ion-fluid update outside its stability range");
+    return HYB_OK;
+}
+
+int drop_graph(hyb_batch *b)
+{
+    if (b->graph) {
+        CK(cudaGraphExecDestroy(b->graph));
+        b->graph = nullptr;
+    }
+    return HYB_OK;
+}
+
+int configure(hyb_batch *b, int nodes, int bins)
+{
+    if (nodes <= b->max_nodes && bins <= b->max_bins) return HYB_OK;
+    b->max_nodes = std::max(b->max_nodes, nodes);
+    b->max_bins = std::max(b->max_bins, bins);
+    b->cfg.block = kElectronBlock;
+    b->cfg.smem = electron_smem_bytes(b->precision, b->max_nodes, b->max_bins);
+    int per_sm = electron_blocks_per_sm(b->precision, b->cfg.smem);
+    if (per_sm < 1) return fail(HYB_ERR_ARG, "grid too large for the electron kernel's shared memory");
+    b->cfg.grid = b->num_sms * per_sm;
+    return drop_graph(b);
+}
+
+int launch_step(hyb_batch *b)
+{
+    CK(launch_electron_step(b->d_inst, b->max_inst, b->d_prefix, b->precision, b->cfg, b->stream));
+    CK(launch_field(b->d_inst, b->max_inst, b->d_prefix, b->d_ticket, b->stream));
+    return HYB_OK;
+}
+
+int launch_sort_all(hyb_batch *b)
+{
+    CK(launch_sort(b->d_inst, b->max_inst, b->d_prefix, b->precision, b->cfg, b->stream));
+    return HYB_OK;
+}
+
+// Graph of one sort interval: K steps then the cell sort.
+int build_graph(hyb_batch *b)
+{
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = HYB_OK;
+    for (int k = 0; k < b->sort_interval && rc == HYB_OK; ++k) rc = launch_step(b);
+    if (rc == HYB_OK) rc = launch_sort_all(b);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (rc != HYB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    CK(e);
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return HYB_OK;
+}
+
+// (Re)initialise one slot's field from its particles: deposit, Poisson at the
+// current time, then a cell sort of that instance alone.
+int reinit_slot(hyb_batch *b, int slot, bool sort)
+{
+    InstDev *K = &b->d_inst[slot];
+    CK(launch_prefix_one(K, b->d_prefix1, b->stream));
+    CK(launch_deposit_init(K, 1, b->d_prefix1, b->precision, b->cfg, b->stream));
+    CK(launch_field(K, 1, b->d_prefix1, b->d_ticket1, b->stream));
+    if (sort) {
+        CK(launch_prefix_one(K, b->d_prefix1, b->stream));
+        CK(launch_sort(K, 1, b->d_prefix1, b->precision, b->cfg, b->stream));
+    }
+    return HYB_OK;
+}
+
+int set_mutable(hyb_batch *b, int slot, int64_t n_slots, int init_pending)
+{
+    // write n_slots / n_slots_step / init_pending of the device struct
+    Slot &S = b->slots[slot];
+    CK(cudaStreamSynchronize(b->stream));
+    int rc = fetch_inst(b, slot);
+    if (rc) return rc;
+    InstDev h = b->h_stage[slot];
+    h.n_slots = (unsigned long long)n_slots;
+    h.n_slots_step = n_slots;
+    h.init_pending = init_pending;
+    CK(cudaMemcpyAsync(&b->d_inst[slot], &h, sizeof h, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    (void)S;
+    return HYB_OK;
+}
+
+int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
+{
+    int rc = validate(p);
+    if (rc) return rc;
+    if (p->precision != b->precision) return fail(HYB_ERR_ARG, "precision differs from the batch's");
+    int slot = -1;
+    for (int i = 0; i < b->max_inst; ++i)
+        if (!b->slots[i].used) {
+            slot = i;
+            break;
+        }
+    if (slot < 0) return fail(HYB_ERR_OOM, "no free slot in the batch");
+    const Layout L = layout_of(*p);
+    if (b->hbm_cap > 0 && b->hbm_used + (int64_t)L.total > b->hbm_cap)
+        return fail(HYB_ERR_OOM, "HBM cap: %lld + %lld > %lld bytes", (long long)b->hbm_used, (long long)L.total,
+                    (long long)b->hbm_cap);
+    rc = configure(b, p->n_cells + 1, bins_of(*p) + 1);
+    if (rc) return rc;
+
+    Slot &S = b->slots[slot];
+    std::vector<double> xs, tab;
+    std::vector<float4> xsf;
+    derive(*p, S.h, xs, xsf, tab);
+    void *mem = nullptr;
+    cudaError_t e = cudaMallocAsync(&mem, L.total, b->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HYB_ERR_OOM, "cudaMallocAsync(%zu): %s", L.total, cudaGetErrorString(e));
+    }
+    char *base = (char *)mem;
+    bind_pointers(*p, L, base, S.h);
+    CK(cudaMemsetAsync(base + L.grid_off, 0, L.total - L.grid_off, b->stream));
+    const int G = S.h.G;
+    std::vector<double> ni(G, p->n0_m3);
+    CK(cudaMemcpyAsync(S.h.ni, ni.data(), 8 * (size_t)G, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync((void *)S.h.xs, xs.data(), 8 * xs.size(), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync((void *)S.h.xsf, xsf.data(), 16 * xsf.size(), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync((void *)S.h.tab, tab.data(), 8 * tab.size(), cudaMemcpyHostToDevice, b->stream));
+    S.h.active = 0;
+    S.h.cur = 0;
+    S.h.step = 0;
+    S.h.target_step = n_steps > 0 ? n_steps : 0;
+    S.h.n_slots = (unsigned long long)p->n_particles;
+    S.h.n_slots_step = p->n_particles;
+    S.h.init_pending = 1;
+    if (p->n_particles > S.h.capacity) return fail(HYB_ERR_CAPACITY, "n_particles exceeds capacity");
+    CK(cudaMemcpyAsync(&b->d_inst[slot], &S.h, sizeof(InstDev), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));  // host staging vectors go out of scope
+    const double vth = sqrt(kQe * p->te0_ev / kMe);
+    CK(launch_load(&b->d_inst[slot], p->n_particles, vth, p->precision, b->stream));
+    rc = reinit_slot(b, slot, true);
+    if (rc) return rc;
+    CK(launch_set_active(&b->d_inst[slot], 1, S.h.target_step, b->stream));
+    CK(launch_prefix(b->d_inst, b->max_inst, b->d_prefix, b->stream));
+    S.used = true;
+    S.reported = false;
+    S.p = *p;
+    S.p.tab_eon_td = S.p.tab_mu = S.p.tab_nu = nullptr;
+    S.p.xs_ev = S.p.xs_el = S.p.xs_exc = S.p.xs_ion = nullptr;
+    S.mem = mem;
+    S.bytes = (int64_t)L.total;
+    S.target = S.h.target_step;
+    b->hbm_used += S.bytes;
+    *slot_out = slot;
+    if (S.h.nu_max * S.h.dt > 0.1) {
+        fail(HYB_WARN_DT_NULLCOLL, "nu_max*dt = %.3g exceeds 0.1", S.h.nu_max * S.h.dt);
+        return HYB_WARN_DT_NULLCOLL;
+    }
+    return HYB_OK;
+}
+
+int advance(hyb_batch *b, int64_t n)
+{
+    if (n < 0) return fail(HYB_ERR_ARG, "negative step count");
+    int rc;
+    while (n > 0) {
+        if (b->since_sort == 0 && n >= b->sort_interval) {
+            if (!b->graph) {
+                rc = build_graph(b);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(b->graph, b->stream));
+            n -= b->sort_interval;
+            continue;
+        }
+        rc = launch_step(b);
+        if (rc) return rc;
+        --n;
+        if (++b->since_sort == b->sort_interval) {
+            rc = launch_sort_all(b);
+            if (rc) return rc;
+            b->since_sort = 0;
+        }
+    }
+    return HYB_OK;
+}
+
+int sync_status(hyb_batch *b, int slot)
+{
+    CK(cudaStreamSynchronize(b->stream));
+    int rc = fetch_inst(b, slot);
+    if (rc) return rc;
+    return status_code(b->h_stage[slot].status);
+}
+
+int check_slot(hyb_batch *b, int slot)
+{
+    if (!b) return fail(HYB_ERR_ARG, "NULL batch");
+    if (slot < 0 || slot >= b->max_inst || !b->slots[slot].used) return fail(HYB_ERR_ARG, "no discharge in slot %d", slot);
+    return HYB_OK;
+}
+
+int read_moments(hyb_batch *b, int slot, hyb_moments *out)
+{
+    int rc = check_slot(b, slot);
+    if (rc) return rc;
+    if (!out) return fail(HYB_ERR_ARG, "NULL output");
+    rc = sync_status(b, slot);
+    const InstDev &K = b->h_stage[slot];
+    const int G = K.G, nb = K.eedf_bins;
+    std::vector<double> acc(5 * (size_t)G);
+    std::vector<unsigned long long> eedf(nb + 1);
+    double *src[5] = {K.acc_ne, K.acc_ni, K.acc_gi, K.acc_wn, K.acc_we};
+    for (int k = 0; k < 5; ++k)
+        CK(cudaMemcpyAsync(acc.data() + (size_t)k * G, src[k], 8 * (size_t)G, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(eedf.data(), K.eedf, 8 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    const int64_t ns = K.n_samples;
+    out->n_samples = ns;
+    for (int j = 0; j < G; ++j) {
+        if (out->ne) out->ne[j] = ns ? acc[j] / ns : 0.0;
+        if (out->ni) out->ni[j] = ns ? acc[G + j] / ns : 0.0;
+        if (out->gamma_i) out->gamma_i[j] = ns ? acc[2 * G + j] / ns : 0.0;
+        if (out->mean_energy_ev) out->mean_energy_ev[j] = acc[3 * G + j] > 0 ? acc[4 * G + j] / acc[3 * G + j] : 0.0;
+    }
+    if (out->eedf) {
+        double tot = 0.0;
+        for (int k = 0; k <= nb; ++k) tot += (double)eedf[k];
+        for (int k = 0; k < nb; ++k) out->eedf[k] = tot > 0 ? (double)eedf[k] / (tot * K.bin_w) : 0.0;
+        out->eedf[nb] = tot > 0 ? (double)eedf[nb] / tot : 0.0;
+    }
+    return rc;
+}
+
+int read_counters(hyb_batch *b, int slot, hyb_counters *c)
+{
+    int rc = check_slot(b, slot);
+    if (rc) return rc;
+    if (!c) return fail(HYB_ERR_ARG, "NULL output");
+    rc = sync_status(b, slot);
+    const InstDev &K = b->h_stage[slot];
+    c->step = K.step;
+    c->births_ionization = (int64_t)K.ctr[C_BIRTH_IZ];
+    c->births_see[0] = (int64_t)K.ctr[C_SEE0];
+    c->births_see[1] = (int64_t)K.ctr[C_SEE1];
+    c->losses[0] = (int64_t)K.ctr[C_LOSS0];
+    c->losses[1] = (int64_t)K.ctr[C_LOSS1];
+    c->collisions[0] = (int64_t)K.ctr[C_EL];
+    c->collisions[1] = (int64_t)K.ctr[C_EXC];
+    c->collisions[2] = (int64_t)K.ctr[C_IZ];
+    c->collisions[3] = (int64_t)K.ctr[C_NULL];
+    c->clamps = (int64_t)K.ctr[C_CLAMP];
+    c->status = K.status;
+    // live particles: slots minus removed ones
+    const int64_t ns = (int64_t)K.n_slots;
+    const PartBuf P = K.buf[K.cur];
+    int64_t live = 0;
+    if (ns > 0) {
+        if (K.precision == HYB_FP32_SPLIT) {
+            std::vector<int32_t> cc(ns);
+            CK(cudaMemcpy(cc.data(), P.c, 4 * (size_t)ns, cudaMemcpyDeviceToHost));
+            for (int32_t x : cc) live += x >= 0;
+        } else {
+            std::vector<double> zz(ns);
+            CK(cudaMemcpy(zz.data(), P.z, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+            for (double x : zz) live += x >= 0.0;
+        }
+    }
+    c->particles = live;
+    return rc;
+}
+
+int read_particles(hyb_batch *b, int slot, double *z, double *vx, double *vy, double *vz, uint64_t *id, int64_t cap,
+                   int64_t *n)
+{
+    int rc = check_slot(b, slot);
+    if (rc) return rc;
+    rc = sync_status(b, slot);
+    const InstDev &K = b->h_stage[slot];
+    const int64_t ns = (int64_t)K.n_slots;
+    const PartBuf P = K.buf[K.cur];
+    std::vector<double> hz(ns), hx(ns), hy(ns), hv(ns);
+    std::vector<uint64_t> hid(ns);
+    std::vector<char> alive(ns, 0);
+    if (ns > 0) {
+        CK(cudaMemcpy(hid.data(), P.id, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+        if (K.precision == HYB_FP32_SPLIT) {
+            std::vector<int32_t> c(ns);
+            std::vector<float> o(ns), fx(ns), fy(ns), fz(ns);
+            CK(cudaMemcpy(c.data(), P.c, 4 * (size_t)ns, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(o.data(), P.o, 4 * (size_t)ns, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(fx.data(), P.vxf, 4 * (size_t)ns, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(fy.data(), P.vyf, 4 * (size_t)ns, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(fz.data(), P.vzf, 4 * (size_t)ns, cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < ns; ++i) {
+                alive[i] = c[i] >= 0;
+                hz[i] = ((double)c[i] + (double)o[i]) * K.dz;
+                hx[i] = fx[i];
+                hy[i] = fy[i];
+                hv[i] = fz[i];
+            }
+        } else {
+            CK(cudaMemcpy(hz.data(), P.z, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(hx.data(), P.vxd, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(hy.data(), P.vyd, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(hv.data(), P.vzd, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < ns; ++i) alive[i] = hz[i] >= 0.0;
+        }
+    }
+    std::vector<int64_t> idx;
+    idx.reserve(ns);
+    for (int64_t i = 0; i < ns; ++i)
+        if (alive[i]) idx.push_back(i);
+    std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t c) { return hid[a] < hid[c]; });
+    *n = (int64_t)idx.size();
+    if (*n > cap) return fail(HYB_ERR_ARG, "%lld live particles exceed the buffers (%lld)", (long long)*n, (long long)cap);
+    for (size_t k = 0; k < idx.size(); ++k) {
+        const int64_t i = idx[k];
+        if (z) z[k] = hz[i];
+        if (vx) vx[k] = hx[i];
+        if (vy) vy[k] = hy[i];
+        if (vz) vz[k] = hv[i];
+        if (id) id[k] = hid[i];
+    }
+    return rc;
+}
+
+int free_slot(hyb_batch *b, int slot)
+{
+    Slot &S = b->slots[slot];
+    if (!S.used) return HYB_OK;
+    CK(launch_set_active(&b->d_inst[slot], 0, 0, b->stream));
+    CK(launch_prefix(b->d_inst, b->max_inst, b->d_prefix, b->stream));
+    CK(cudaFreeAsync(S.mem, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    b->hbm_used -= S.bytes;
+    S = Slot{};
+    return HYB_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+const char *hyb_last_error(void) { return g_err.c_str(); }
+
+int hyb_footprint(const hyb_params *p, int64_t *bytes)
+{
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!bytes) return fail(HYB_ERR_ARG, "NULL output");
+    *bytes = (int64_t)layout_of(*p).total;
+    return HYB_OK;
+}
+
+int hyb_batch_create(int32_t max_instances, int32_t precision, int64_t hbm_cap_bytes, void *stream, hyb_batch **out)
+{
+    if (!out) return fail(HYB_ERR_ARG, "NULL output");
+    *out = nullptr;
+    if (max_instances < 1 || max_instances > HYB_MAX_INSTANCES)
+        return fail(HYB_ERR_ARG, "max_instances must be in [1, %d]", HYB_MAX_INSTANCES);
+    if (precision != HYB_FP64 && precision != HYB_FP32_SPLIT) return fail(HYB_ERR_ARG, "unknown precision");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    hyb::configure_kernels();
+    hyb_batch *b = new hyb_batch();
+    b->max_inst = max_instances;
+    b->precision = precision;
+    b->hbm_cap = hbm_cap_bytes > 0 ? hbm_cap_bytes : 0;
+    b->slots.resize(max_instances);
+    CK(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
+    }
+    CK(cudaMalloc(&b->d_inst, sizeof(InstDev) * (size_t)max_instances));
+    CK(cudaMemset(b->d_inst, 0, sizeof(InstDev) * (size_t)max_instances));
+    CK(cudaMalloc(&b->d_prefix, sizeof(int64_t) * (size_t)(max_instances + 1)));
+    CK(cudaMemset(b->d_prefix, 0, sizeof(int64_t) * (size_t)(max_instances + 1)));
+    CK(cudaMalloc(&b->d_prefix1, sizeof(int64_t) * 2));
+    CK(cudaMalloc(&b->d_ticket, sizeof(unsigned) * 2));
+    CK(cudaMemset(b->d_ticket, 0, sizeof(unsigned) * 2));
+    b->d_ticket1 = b->d_ticket + 1;
+    CK(cudaMallocHost(&b->h_stage, sizeof(InstDev) * (size_t)max_instances));
+    int rc = configure(b, 3, 2);
+    if (rc) return rc;
+    *out = b;
+    return HYB_OK;
+}
+
+int hyb_batch_admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int32_t *slot)
+{
+    if (!b || !slot) return fail(HYB_ERR_ARG, "NULL argument");
+    int s = -1;
+    int rc = admit(b, p, n_steps, &s);
+    *slot = s;
+    return rc;
+}
+
+int hyb_batch_advance(hyb_batch *b, int64_t n_steps)
+{
+    if (!b) return fail(HYB_ERR_ARG, "NULL batch");
+    return advance(b, n_steps);
+}
+
+int hyb_batch_poll(hyb_batch *b, int32_t *done, int32_t cap, int32_t *n_done)
+{
+    if (!b || !n_done) return fail(HYB_ERR_ARG, "NULL argument");
+    CK(cudaMemcpyAsync(b->h_stage, b->d_inst, sizeof(InstDev) * (size_t)b->max_inst, cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    int k = 0;
+    int rc = HYB_OK;
+    for (int i = 0; i < b->max_inst; ++i) {
+        Slot &S = b->slots[i];
+        if (!S.used || S.reported) continue;
+        const InstDev &K = b->h_stage[i];
+        const bool finished = S.target > 0 && K.step >= S.target && !K.active;
+        const bool failed = (K.status & (HYB_STATUS_NONFINITE | HYB_STATUS_CAPACITY | HYB_STATUS_UNSTABLE)) != 0;
+        if (finished || failed) {
+            if (k < cap && done) done[k] = i;
+            ++k;
+            S.reported = true;
+            if (failed && rc == HYB_OK) rc = status_code(K.status);
+        }
+    }
+    *n_done = k < cap ? k : cap;
+    return rc;
+}
+
+int hyb_batch_read_moments(hyb_batch *b, int32_t slot, hyb_moments *out) { return read_moments(b, slot, out); }
+
+int hyb_batch_read_counters(hyb_batch *b, int32_t slot, hyb_counters *out) { return read_counters(b, slot, out); }
+
+int hyb_batch_read_particles(hyb_batch *b, int32_t slot, double *z, double *vx, double *vy, double *vz, uint64_t *id,
+                             int64_t cap, int64_t *n)
+{
+    return read_particles(b, slot, z, vx, vy, vz, id, cap, n);
+}
+
+int hyb_batch_evict(hyb_batch *b, int32_t slot)
+{
+    int rc = check_slot(b, slot);
+    if (rc) return rc;
+    return free_slot(b, slot);
+}
+
+int hyb_batch_stats(hyb_batch *b, int32_t *running, int64_t *particles, int64_t *bytes)
+{
+    if (!b) return fail(HYB_ERR_ARG, "NULL batch");
+    CK(cudaMemcpyAsync(b->h_stage, b->d_inst, sizeof(InstDev) * (size_t)b->max_inst, cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    int r = 0;
+    int64_t np = 0;
+    for (int i = 0; i < b->max_inst; ++i) {
+        if (!b->slots[i].used) continue;
+        if (b->h_stage[i].active) {
+            ++r;
+            np += b->h_stage[i].n_slots_step;
+        }
+    }
+    if (running) *running = r;
+    if (particles) *particles = np;
+    if (bytes) *bytes = b->hbm_used;
+    return HYB_OK;
+}
+
+int hyb_batch_destroy(hyb_batch *b)
+{
+    if (!b) return HYB_OK;
+    cudaStreamSynchronize(b->stream);
+    for (int i = 0; i < b->max_inst; ++i)
+        if (b->slots[i].used) cudaFreeAsync(b->slots[i].mem, b->stream);
+    cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_prefix);
+    cudaFree(b->d_prefix1);
+    cudaFree(b->d_ticket);
+    cudaFreeHost(b->h_stage);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return HYB_OK;
+}
+
+// ------------------------------------------------------------- single run
+
+int hyb_create_discharge(const hyb_params *p, void *stream, hyb_discharge **out)
+{
+    if (!out) return fail(HYB_ERR_ARG, "NULL output");
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    hyb_batch *b = nullptr;
+    rc = hyb_batch_create(1, p->precision, 0, stream, &b);
+    if (rc) return rc;
+    if (p->sort_interval > 0) b->sort_interval = p->sort_interval;
+    int slot = -1;
+    rc = admit(b, p, 0, &slot);
+    if (rc < 0) {
+        std::string msg = g_err;
+        hyb_batch_destroy(b);
+        g_err = msg;
+        return rc;
+    }
+    hyb_discharge *h = new hyb_discharge{b, slot};
+    *out = h;
+    return rc;
+}
+
+int hyb_advance(hyb_discharge *h, int64_t n_steps)
+{
+    if (!h) return fail(HYB_ERR_ARG, "NULL handle");
+    return advance(h->b, n_steps);
+}
+
+int hyb_sync(hyb_discharge *h)
+{
+    if (!h) return fail(HYB_ERR_ARG, "NULL handle");
+    return sync_status(h->b, h->slot);
+}
+
+int hyb_read_moments(hyb_discharge *h, hyb_moments *out)
+{
+    if (!h) return fail(HYB_ERR_ARG, "NULL handle");
+    return read_moments(h->b, h->slot, out);
+}
+
+int hyb_read_counters(hyb_discharge *h, hyb_counters *out)
+{
+    if (!h) return fail(HYB_ERR_ARG, "NULL handle");
+    return read_counters(h->b, h->slot, out);
+}
+
+int hyb_read_fields(hyb_discharge *h, hyb_fields *out)
+{
+    if (!h || !out) return fail(HYB_ERR_ARG, "NULL argument");
+    hyb_batch *b = h->b;
+    int rc = sync_status(b, h->slot);
+    const InstDev &K = b->h_stage[h->slot];
+    const size_t bytes = 8 * (size_t)K.G;
+    double *dst[6] = {out->ne, out->ni, out->gamma_i, out->phi, out->efield, out->ion_source};
+    const double *src[6] = {K.ne, K.ni, K.gam, K.phi, K.E, K.gsrc};
+    for (int k = 0; k < 6; ++k)
+        if (dst[k]) CK(cudaMemcpyAsync(dst[k], src[k], bytes, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return rc;
+}
+
+int hyb_get_info(hyb_discharge *h, hyb_info *out)
+{
+    if (!h || !out) return fail(HYB_ERR_ARG, "NULL argument");
+    const Slot &S = h->b->slots[h->slot];
+    out->n_nodes = S.h.G;
+    out->eedf_bins = S.h.eedf_bins;
+    out->weight = S.h.w;
+    out->gas_density = S.h.ngas;
+    out->nu_max = S.h.nu_max;
+    out->p_max = S.h.p_max;
+    out->dz = S.h.dz;
+    out->capacity = S.h.capacity;
+    out->device_bytes = S.bytes;
+    return HYB_OK;
+}
+
+int hyb_reset_moments(hyb_discharge *h)
+{
+    if (!h) return fail(HYB_ERR_ARG, "NULL handle");
+    hyb_batch *b = h->b;
+    int rc = fetch_inst(b, h->slot);
+    if (rc) return rc;
+    InstDev K = b->h_stage[h->slot];
+    const size_t bytes = 8 * (size_t)K.G;
+    double *acc[5] = {K.acc_ne, K.acc_ni, K.acc_gi, K.acc_wn, K.acc_we};
+    for (int k = 0; k < 5; ++k) CK(cudaMemsetAsync(acc[k], 0, bytes, b->stream));
+    CK(cudaMemsetAsync(K.eedf, 0, 8 * (size_t)(K.eedf_bins + 1), b->stream));
+    K.n_samples = 0;
+    CK(cudaMemcpyAsync(&b->d_inst[h->slot], &K, sizeof K, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return HYB_OK;
+}
+
+int hyb_read_particles(hyb_discharge *h, double *z, double *vx, double *vy, double *vz, uint64_t *id, int64_t cap,
+                       int64_t *n)
+{
+    if (!h || !n) return fail(HYB_ERR_ARG, "NULL argument");
+    return read_particles(h->b, h->slot, z, vx, vy, vz, id, cap, n);
+}
+
+int hyb_write_particles(hyb_discharge *h, int64_t n, const double *z, const double *vx, const double *vy,
+                        const double *vz, const uint64_t *id)
+{
+    if (!h) return fail(HYB_ERR_ARG, "NULL handle");
+    if (n < 0 || (n > 0 && (!z || !vx || !vy || !vz || !id))) return fail(HYB_ERR_ARG, "bad particle arrays");
+    hyb_batch *b = h->b;
+    const Slot &S = b->slots[h->slot];
+    if (n > S.h.capacity) return fail(HYB_ERR_CAPACITY, "%lld particles exceed capacity %lld", (long long)n,
+                                      (long long)S.h.capacity);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(z[i] >= 0.0 && z[i] < S.h.L)) return fail(HYB_ERR_ARG, "particle %lld outside [0, L)", (long long)i);
+        if (!isfinite(vx[i]) || !isfinite(vy[i]) || !isfinite(vz[i]))
+            return fail(HYB_ERR_NONFINITE, "non-finite velocity of particle %lld", (long long)i);
+    }
+    int rc = fetch_inst(b, h->slot);
+    if (rc) return rc;
+    const InstDev K = b->h_stage[h->slot];
+    const PartBuf P = K.buf[K.cur];
+    if (n > 0) {
+        CK(cudaMemcpy(P.id, id, 8 * (size_t)n, cudaMemcpyHostToDevice));
+        if (K.precision == HYB_FP32_SPLIT) {
+            std::vector<int32_t> c(n);
+            std::vector<float> o(n), fx(n), fy(n), fz(n);
+            for (int64_t i = 0; i < n; ++i) {
+                const double x = z[i] / K.dz;
+                const double f = floor(x);
+                int ci = (int)f;
+                double oi = x - f;
+                if (ci >= K.n_cells) {
+                    ci = K.n_cells - 1;
+                    oi = 1.0;
+                }
+                c[i] = ci;
+                o[i] = (float)oi;
+                fx[i] = (float)vx[i];
+                fy[i] = (float)vy[i];
+                fz[i] = (float)vz[i];
+            }
+            CK(cudaMemcpy(P.c, c.data(), 4 * (size_t)n, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(P.o, o.data(), 4 * (size_t)n, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(P.vxf, fx.data(), 4 * (size_t)n, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(P.vyf, fy.data(), 4 * (size_t)n, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(P.vzf, fz.data(), 4 * (size_t)n, cudaMemcpyHostToDevice));
+        } else {
+            CK(cudaMemcpy(P.z, z, 8 * (size_t)n, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(P.vxd, vx, 8 * (size_t)n, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(P.vyd, vy, 8 * (size_t)n, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(P.vzd, vz, 8 * (size_t)n, cudaMemcpyHostToDevice));
+        }
+    }
+    rc = set_mutable(b, h->slot, n, 1);
+    if (rc) return rc;
+    rc = reinit_slot(b, h->slot, true);
+    if (rc) return rc;
+    CK(launch_prefix(b->d_inst, b->max_inst, b->d_prefix, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return HYB_OK;
+}
+
+int hyb_write_ion_density(hyb_discharge *h, const double *ni)
+{
+    if (!h || !ni) return fail(HYB_ERR_ARG, "NULL argument");
+    hyb_batch *b = h->b;
+    const Slot &S = b->slots[h->slot];
+    if (!finite_all(ni, S.h.G)) return fail(HYB_ERR_NONFINITE, "non-finite ion density");
+    CK(cudaStreamSynchronize(b->stream));
+    CK(cudaMemcpy(S.h.ni, ni, 8 * (size_t)S.h.G, cudaMemcpyHostToDevice));
+    int rc = fetch_inst(b, h->slot);
+    if (rc) return rc;
+    rc = set_mutable(b, h->slot, (int64_t)b->h_stage[h->slot].n_slots, 1);
+    if (rc) return rc;
+    rc = reinit_slot(b, h->slot, false);
+    if (rc) return rc;
+    CK(launch_prefix(b->d_inst, b->max_inst, b->d_prefix, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return HYB_OK;
+}
+
+int hyb_destroy(hyb_discharge *h)
+{
+    if (!h) return HYB_OK;
+    hyb_batch_destroy(h->b);
+    delete h;
+    return HYB_OK;
+}
+
+}  // extern "C"

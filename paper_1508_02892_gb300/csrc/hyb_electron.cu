@@ -1,0 +1,880 @@
+// hyb_electron.cu -- the per-particle kernels of the electron PIC/MCC step
+// (arXiv 1508.02892, Sec. II.A): leapfrog push in the CIC-interpolated field,
+// wall removal, CIC charge assignment with the energy moment and EEDF sample,
+// modified null-collision MCC with ionization births (Sec. II.D), plus the
+// initial load and the periodic counting sort by cell.
+//
+// Work decomposition: the running instances' slot ranges are concatenated and
+// each block takes one contiguous chunk (particles are kept sorted by cell, so
+// a chunk covers a narrow range of cells).  Deposits go to block-private
+// shared-memory arrays (FP32 in split mode, FP64 in FP64 mode), aggregated per
+// warp when all lanes share a cell, and are flushed over the touched node range
+// into the FP64 global sums.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hyb_internal.cuh"
+
+namespace hyb {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename T>
+struct WarpSum;
+
+template <>
+struct WarpSum<float> {
+    __device__ static float run(float v)
+    {
+#pragma unroll
+        for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+        return v;
+    }
+};
+template <>
+struct WarpSum<double> {
+    __device__ static double run(double v)
+    {
+#pragma unroll
+        for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+        return v;
+    }
+};
+
+// Add (w0 at node c, w1 at node c+1) for every lane that has `on`; when every
+// participating lane has the same c, sum over the warp first.
+template <typename T>
+__device__ __forceinline__ void deposit_pair(T *arr, bool on, int c, T w0, T w1)
+{
+    const int kmin = __reduce_min_sync(kFull, on ? c : INT32_MAX);
+    const int kmax = __reduce_max_sync(kFull, on ? c : -1);
+    if (kmin == kmax) {
+        T a = WarpSum<T>::run(on ? w0 : T(0));
+        T b = WarpSum<T>::run(on ? w1 : T(0));
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&arr[kmin], a);
+            atomicAdd(&arr[kmin + 1], b);
+        }
+    } else if (on) {
+        atomicAdd(&arr[c], w0);
+        atomicAdd(&arr[c + 1], w1);
+    }
+}
+
+struct SegCounters {
+    unsigned el = 0, exc = 0, iz = 0, nul = 0, loss0 = 0, loss1 = 0, overflow = 0;
+    int cmin = INT32_MAX, cmax = -1;
+};
+
+// Append children with one atomic per warp; all 32 lanes must call this.
+template <typename T>
+__device__ __forceinline__ void append_children(InstDev *K, const PartBuf &P, int64_t capacity, bool has, int cc, T co,
+                                                double cz, T cvx, T cvy, T cvz, uint64_t cid, unsigned &overflow);
+
+template <>
+__device__ __forceinline__ void append_children<float>(InstDev *K, const PartBuf &P, int64_t capacity, bool has,
+                                                       int cc, float co, double, float cvx, float cvy, float cvz,
+                                                       uint64_t cid, unsigned &overflow)
+{
+    const unsigned m = __ballot_sync(kFull, has);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&K->n_slots, (unsigned long long)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (has) {
+        const unsigned long long slot = base + __popc(m & lanemask_lt());
+        if (slot < (unsigned long long)capacity) {
+            P.c[slot] = cc;
+            P.o[slot] = co;
+            P.vxf[slot] = cvx;
+            P.vyf[slot] = cvy;
+            P.vzf[slot] = cvz;
+            P.id[slot] = cid;
+        } else {
+            overflow = 1;
+        }
+    }
+}
+
+template <>
+__device__ __forceinline__ void append_children<double>(InstDev *K, const PartBuf &P, int64_t capacity, bool has, int,
+                                                        double, double cz, double cvx, double cvy, double cvz,
+                                                        uint64_t cid, unsigned &overflow)
+{
+    const unsigned m = __ballot_sync(kFull, has);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&K->n_slots, (unsigned long long)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (has) {
+        const unsigned long long slot = base + __popc(m & lanemask_lt());
+        if (slot < (unsigned long long)capacity) {
+            P.z[slot] = cz;
+            P.vxd[slot] = cvx;
+            P.vyd[slot] = cvy;
+            P.vzd[slot] = cvz;
+            P.id[slot] = cid;
+        } else {
+            overflow = 1;
+        }
+    }
+}
+
+// ------------------------------------------------------------ FP32 split
+//
+// Position = (cell c, offset o in [0,1)).  Constants are the f_* copies.
+
+template <int MODE>
+__device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *smem, SegCounters &cnt)
+{
+    const int nc = K->n_cells;
+    const int G = K->G;
+    const int nb = K->eedf_bins;
+    const uint32_t step = (uint32_t)K->step;
+    const uint32_t sl = K->seed_lo, sh = K->seed_hi;
+    const PartBuf P = K->buf[K->cur];
+    const int64_t capacity = K->capacity;
+    const float *__restrict__ Ef = K->Ef;
+    const float4 *__restrict__ xs = K->xsf;
+    const int nxs = K->n_xs;
+    const float dt_dz = K->f_dt_dz, qm_dt = K->f_qm_dt, half_m_q = K->f_half_m_q, two_q_m = K->f_two_q_m;
+    const float pmax = K->f_pmax, e_lo = K->f_e_lo, e_hi = K->f_e_hi, inv_e_lo = K->f_inv_e_lo;
+    const float inv_dlog = K->f_inv_dlog, e_exc = K->f_e_exc, e_iz = K->f_e_iz, two_mM = K->f_two_mM;
+    const float bin_inv = K->f_bin_inv;
+
+    float *sd_n = reinterpret_cast<float *>(smem);
+    float *sd_e = sd_n + G;
+    float *sd_iz = sd_e + G;
+    unsigned *s_eedf = reinterpret_cast<unsigned *>(sd_iz + G);
+    for (int j = threadIdx.x; j < 3 * G; j += blockDim.x) sd_n[j] = 0.f;
+    for (int j = threadIdx.x; j <= nb; j += blockDim.x) s_eedf[j] = 0u;
+    __syncthreads();
+
+    for (int64_t base = a; base < b; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int c = i < b ? P.c[i] : kDeadCell;
+        bool alive = c >= 0 && c < nc;
+        float o = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+        uint64_t id = 0;
+        if (alive) {
+            o = P.o[i];
+            vx = P.vxf[i];
+            vy = P.vyf[i];
+            vz = P.vzf[i];
+            if (MODE == 0) id = P.id[i];
+        }
+        if (MODE == 0 && alive) {
+            // leapfrog with the CIC-gathered field (Sec. II.A)
+            const float ep = (1.f - o) * __ldg(&Ef[c]) + o * __ldg(&Ef[c + 1]);
+            vz = vz - qm_dt * ep;
+            o = o + vz * dt_dz;
+            const float fl = floorf(o);
+            c += (int)fl;
+            o -= fl;
+            if (o >= 1.f) {
+                o -= 1.f;
+                c += 1;
+            }
+            if (c < 0 || c >= nc) {  // absorbed by an electrode and removed
+                if (c < 0)
+                    ++cnt.loss0;
+                else
+                    ++cnt.loss1;
+                alive = false;
+                P.c[i] = kDeadCell;
+            }
+        }
+        // CIC charge assignment, energy moment and EEDF sample
+        const float en = half_m_q * (vx * vx + vy * vy + vz * vz);
+        deposit_pair<float>(sd_n, alive, c, 1.f - o, o);
+        if (MODE == 0) {
+            deposit_pair<float>(sd_e, alive, c, (1.f - o) * en, o * en);
+            if (alive) {
+                int bin = (int)(en * bin_inv);
+                bin = bin > nb ? nb : bin;
+                atomicAdd(&s_eedf[bin], 1u);
+                cnt.cmin = min(cnt.cmin, c);
+                cnt.cmax = max(cnt.cmax, c);
+            }
+        } else if (alive) {
+            cnt.cmin = min(cnt.cmin, c);
+            cnt.cmax = max(cnt.cmax, c);
+        }
+
+        bool has_child = false;
+        float cvx = 0.f, cvy = 0.f, cvz = 0.f;
+        uint64_t cid = 0;
+        if (MODE == 0 && alive) {
+            // modified null-collision method: every particle draws R1 < P_max
+            const uint4 r = draw(id, step, sl, sh, 0);
+            if (u01f(r.x) < pmax) {
+                const float speed = sqrtf(vx * vx + vy * vy + vz * vz);
+                float4 lo, hi;
+                float f;
+                if (en <= e_lo) {
+                    lo = hi = __ldg(&xs[0]);
+                    f = 0.f;
+                } else if (en >= e_hi) {
+                    lo = hi = __ldg(&xs[nxs - 1]);
+                    f = 0.f;
+                } else {
+                    int k = (int)(__logf(en * inv_e_lo) * inv_dlog);
+                    k = k < 0 ? 0 : (k > nxs - 2 ? nxs - 2 : k);
+                    lo = __ldg(&xs[k]);
+                    hi = __ldg(&xs[k + 1]);
+                    f = __fdividef(en - lo.x, hi.x - lo.x);
+                }
+                const float s_el = lo.y + f * (hi.y - lo.y);
+                const float s_ex = en < e_exc ? 0.f : lo.z + f * (hi.z - lo.z);
+                const float s_iz = en < e_iz ? 0.f : lo.w + f * (hi.w - lo.w);
+                const float t0 = s_el * speed, t1 = t0 + s_ex * speed, t2 = t1 + s_iz * speed;
+                const float r2 = u01f(r.y);
+                if (r2 < t2) {
+                    const float ct = 1.f - 2.f * u01f(r.z);
+                    const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
+                    float sn, cs;
+                    __sincosf(6.283185307179586f * u01f(r.w), &sn, &cs);
+                    const float dx = st * cs, dy = st * sn, dz = ct;
+                    float sp;
+                    if (r2 < t0) {  // elastic, lab-frame isotropic
+                        const float cchi = (vx * dx + vy * dy + vz * dz) / speed;
+                        sp = speed * sqrtf(1.f - two_mM * (1.f - cchi));
+                        ++cnt.el;
+                    } else if (r2 < t1) {  // excitation
+                        sp = sqrtf(two_q_m * (en - e_exc));
+                        ++cnt.exc;
+                    } else {  // ionization: split E - E_iz, eject a new electron
+                        const uint4 r1 = draw(id, step, sl, sh, 1);
+                        const float de = en - e_iz;
+                        const float e_ej = u01f(r1.x) * de;
+                        sp = sqrtf(two_q_m * (de - e_ej));
+                        const float cj = 1.f - 2.f * u01f(r1.y);
+                        const float sj = sqrtf(fmaxf(0.f, 1.f - cj * cj));
+                        float snj, csj;
+                        __sincosf(6.283185307179586f * u01f(r1.z), &snj, &csj);
+                        const float spj = sqrtf(two_q_m * e_ej);
+                        cvx = spj * sj * csj;
+                        cvy = spj * sj * snj;
+                        cvz = spj * cj;
+                        cid = child_id(id, step);
+                        has_child = true;
+                        ++cnt.iz;
+                        atomicAdd(&sd_iz[c], 1.f - o);
+                        atomicAdd(&sd_iz[c + 1], o);
+                    }
+                    vx = sp * dx;
+                    vy = sp * dy;
+                    vz = sp * dz;
+                } else {
+                    ++cnt.nul;
+                }
+            }
+        }
+        if (MODE == 0) {
+            append_children<float>(K, P, capacity, has_child, c, o, 0.0, cvx, cvy, cvz, cid, cnt.overflow);
+            if (alive) {
+                P.c[i] = c;
+                P.o[i] = o;
+                P.vxf[i] = vx;
+                P.vyf[i] = vy;
+                P.vzf[i] = vz;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ FP64
+//
+// Same step in FP64 with the position z, written in the same order of
+// operations as a plain FP64 program would use, so the two agree to rounding.
+
+__device__ __forceinline__ void locate_d(double z, double dz, int nc, int &c, double &o)
+{
+    const double x = z / dz;
+    const double f = floor(x);
+    c = (int)f;
+    o = x - f;
+    if (c >= nc) {
+        c = nc - 1;
+        o = 1.0;
+    }
+}
+
+__device__ __forceinline__ void xs_eval_d(const double *__restrict__ xs, int n, double e_lo, double e_hi,
+                                          double inv_dlog, double e_exc, double e_iz, double en, double sig[3])
+{
+    int i;
+    double f;
+    if (en <= e_lo) {
+        i = 0;
+        f = 0.0;
+    } else if (en >= e_hi) {
+        i = n - 2;
+        f = 1.0;
+    } else {
+        const double x = log(en / e_lo) * inv_dlog;
+        i = (int)floor(x);
+        if (i < 0) i = 0;
+        if (i > n - 2) i = n - 2;
+        f = (en - xs[4 * i]) / (xs[4 * (i + 1)] - xs[4 * i]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sig[k] = xs[4 * i + 1 + k] + f * (xs[4 * (i + 1) + 1 + k] - xs[4 * i + 1 + k]);
+    if (en < e_exc) sig[1] = 0.0;
+    if (en < e_iz) sig[2] = 0.0;
+}
+
+__device__ __forceinline__ void iso_dir_d(double u_cos, double u_phi, double d[3])
+{
+    const double ct = 1.0 - 2.0 * u_cos;
+    const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    const double ph = kTwoPi * u_phi;
+    d[0] = st * cos(ph);
+    d[1] = st * sin(ph);
+    d[2] = ct;
+}
+
+template <int MODE>
+__device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *smem, SegCounters &cnt)
+{
+    const int nc = K->n_cells;
+    const int G = K->G;
+    const int nb = K->eedf_bins;
+    const uint32_t step = (uint32_t)K->step;
+    const uint32_t sl = K->seed_lo, sh = K->seed_hi;
+    const PartBuf P = K->buf[K->cur];
+    const int64_t capacity = K->capacity;
+    const double *__restrict__ E = K->E;
+    const double *__restrict__ xs = K->xs;
+    const int nxs = K->n_xs;
+    const double dz = K->dz, dt = K->dt, L = K->L, qm = K->qm, ngas = K->ngas, nu_max = K->nu_max;
+    const double pmax = K->p_max, e_lo = K->e_lo, e_hi = K->e_hi, inv_dlog = K->inv_dlog;
+    const double e_exc = K->e_exc, e_iz = K->e_iz, two_mM = K->two_mM, bin_w = K->bin_w;
+
+    double *sd_n = reinterpret_cast<double *>(smem);
+    double *sd_e = sd_n + G;
+    double *sd_iz = sd_e + G;
+    unsigned *s_eedf = reinterpret_cast<unsigned *>(sd_iz + G);
+    for (int j = threadIdx.x; j < 3 * G; j += blockDim.x) sd_n[j] = 0.0;
+    for (int j = threadIdx.x; j <= nb; j += blockDim.x) s_eedf[j] = 0u;
+    __syncthreads();
+
+    for (int64_t base = a; base < b; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        double z = i < b ? P.z[i] : -1.0;
+        bool alive = z >= 0.0 && z < L;  // also false for NaN
+        double vx = 0.0, vy = 0.0, vz = 0.0;
+        uint64_t id = 0;
+        if (alive) {
+            vx = P.vxd[i];
+            vy = P.vyd[i];
+            vz = P.vzd[i];
+            if (MODE == 0) id = P.id[i];
+        }
+        int c = 0;
+        double o = 0.0;
+        if (MODE == 0 && alive) {
+            locate_d(z, dz, nc, c, o);
+            const double ep = (1.0 - o) * E[c] + o * E[c + 1];
+            vz = vz - qm * ep * dt;
+            z = z + vz * dt;
+            if (!(z >= 0.0 && z < L)) {
+                if (z < 0.0)
+                    ++cnt.loss0;
+                else
+                    ++cnt.loss1;
+                alive = false;
+                P.z[i] = -1.0;
+            }
+        }
+        if (alive) locate_d(z, dz, nc, c, o);
+        const double en = 0.5 * kMe * (vx * vx + vy * vy + vz * vz) / kQe;
+        deposit_pair<double>(sd_n, alive, c, 1.0 - o, o);
+        if (MODE == 0) {
+            deposit_pair<double>(sd_e, alive, c, (1.0 - o) * en, o * en);
+            if (alive) {
+                int bin = (int)(en / bin_w);
+                if (bin > nb || bin < 0) bin = nb;
+                atomicAdd(&s_eedf[bin], 1u);
+            }
+        }
+        if (alive) {
+            cnt.cmin = min(cnt.cmin, c);
+            cnt.cmax = max(cnt.cmax, c);
+        }
+
+        bool has_child = false;
+        double cvx = 0.0, cvy = 0.0, cvz = 0.0;
+        uint64_t cid = 0;
+        if (MODE == 0 && alive) {
+            const uint4 r = draw(id, step, sl, sh, 0);
+            if (u01d(r.x) < pmax) {
+                const double speed = sqrt(vx * vx + vy * vy + vz * vz);
+                double sig[3];
+                xs_eval_d(xs, nxs, e_lo, e_hi, inv_dlog, e_exc, e_iz, en, sig);
+                const double nu_el = ngas * sig[0] * speed;
+                const double nu_ex = ngas * sig[1] * speed;
+                const double nu_iz = ngas * sig[2] * speed;
+                const double rr = u01d(r.y) * nu_max;
+                double d[3];
+                iso_dir_d(u01d(r.z), u01d(r.w), d);
+                if (rr < nu_el) {
+                    const double cchi = (vx * d[0] + vy * d[1] + vz * d[2]) / speed;
+                    const double sp = speed * sqrt(1.0 - two_mM * (1.0 - cchi));
+                    vx = sp * d[0];
+                    vy = sp * d[1];
+                    vz = sp * d[2];
+                    ++cnt.el;
+                } else if (rr < nu_el + nu_ex) {
+                    const double sp = sqrt(2.0 * kQe * (en - e_exc) / kMe);
+                    vx = sp * d[0];
+                    vy = sp * d[1];
+                    vz = sp * d[2];
+                    ++cnt.exc;
+                } else if (rr < nu_el + nu_ex + nu_iz) {
+                    const uint4 r1 = draw(id, step, sl, sh, 1);
+                    const double de = en - e_iz;
+                    const double e_ej = u01d(r1.x) * de;
+                    const double e_sc = de - e_ej;
+                    const double sp = sqrt(2.0 * kQe * e_sc / kMe);
+                    double dj[3];
+                    iso_dir_d(u01d(r1.y), u01d(r1.z), dj);
+                    const double sj = sqrt(2.0 * kQe * e_ej / kMe);
+                    cvx = sj * dj[0];
+                    cvy = sj * dj[1];
+                    cvz = sj * dj[2];
+                    cid = child_id(id, step);
+                    has_child = true;
+                    vx = sp * d[0];
+                    vy = sp * d[1];
+                    vz = sp * d[2];
+                    ++cnt.iz;
+                    atomicAdd(&sd_iz[c], 1.0 - o);
+                    atomicAdd(&sd_iz[c + 1], o);
+                } else {
+                    ++cnt.nul;
+                }
+            }
+        }
+        if (MODE == 0) {
+            append_children<double>(K, P, capacity, has_child, 0, 0.0, z, cvx, cvy, cvz, cid, cnt.overflow);
+            if (alive) {
+                P.z[i] = z;
+                P.vxd[i] = vx;
+                P.vyd[i] = vy;
+                P.vzd[i] = vz;
+            }
+        }
+    }
+}
+
+// Reduce the per-thread counters, then flush the block-private sums over the
+// touched node range into the global FP64 sums.
+template <typename T, int MODE>
+__device__ void flush_segment(InstDev *K, unsigned char *smem, SegCounters &cnt)
+{
+    __shared__ unsigned s_ctr[8];
+    __shared__ int s_cmin, s_cmax;
+    if (threadIdx.x < 8) s_ctr[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) {
+        s_cmin = INT32_MAX;
+        s_cmax = -1;
+    }
+    __syncthreads();
+    const unsigned v[7] = {cnt.el, cnt.exc, cnt.iz, cnt.nul, cnt.loss0, cnt.loss1, cnt.overflow};
+    const int mn = __reduce_min_sync(kFull, cnt.cmin);
+    const int mx = __reduce_max_sync(kFull, cnt.cmax);
+    unsigned tot[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) tot[k] = __reduce_add_sync(kFull, v[k]);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+            if (tot[k]) atomicAdd(&s_ctr[k], tot[k]);
+        atomicMin(&s_cmin, mn);
+        atomicMax(&s_cmax, mx);
+    }
+    __syncthreads();
+    const int G = K->G;
+    const int nb = K->eedf_bins;
+    T *sd_n = reinterpret_cast<T *>(smem);
+    T *sd_e = sd_n + G;
+    T *sd_iz = sd_e + G;
+    unsigned *s_eedf = reinterpret_cast<unsigned *>(sd_iz + G);
+    const int jlo = s_cmin, jhi = s_cmax < 0 ? -1 : min(s_cmax + 1, G - 1);
+    for (int j = (jhi < 0 ? 0 : jlo) + (int)threadIdx.x; j <= jhi; j += blockDim.x) {
+        const T a = sd_n[j];
+        if (a != T(0)) atomicAdd(&K->dep_n[j], (double)a);
+        if (MODE == 0) {
+            const T e = sd_e[j];
+            if (e != T(0)) atomicAdd(&K->dep_e[j], (double)e);
+            const T s = sd_iz[j];
+            if (s != T(0)) atomicAdd(&K->s_iz[j], (double)s);
+        }
+    }
+    if (MODE == 0) {
+        for (int j = threadIdx.x; j <= nb; j += blockDim.x)
+            if (s_eedf[j]) atomicAdd(&K->eedf[j], (unsigned long long)s_eedf[j]);
+        if (threadIdx.x == 0) {
+            const int map[6] = {C_EL, C_EXC, C_IZ, C_NULL, C_LOSS0, C_LOSS1};
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                if (s_ctr[k]) atomicAdd(&K->ctr[map[k]], (unsigned long long)s_ctr[k]);
+            if (s_ctr[2]) atomicAdd(&K->ctr[C_BIRTH_IZ], (unsigned long long)s_ctr[2]);
+            if (s_ctr[6]) atomicOr(&K->status, (unsigned)HYB_STATUS_CAPACITY);
+        }
+    }
+    __syncthreads();
+}
+
+// Block chunk of the concatenated slot ranges -> per-instance segments.
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 4 : 2) k_electron(InstDev *__restrict__ insts, int n_max,
+                                                     const int64_t *__restrict__ prefix)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t total = prefix[n_max];
+    if (total <= 0) return;
+    int64_t chunk = (total + gridDim.x - 1) / gridDim.x;
+    chunk = (chunk + 127) & ~(int64_t)127;
+    const int64_t glo = (int64_t)blockIdx.x * chunk;
+    if (glo >= total) return;
+    const int64_t ghi = glo + chunk < total ? glo + chunk : total;
+    int lo = 0, hi = n_max;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= glo)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    for (int i = lo; i < n_max; ++i) {
+        const int64_t p0 = prefix[i], p1 = prefix[i + 1];
+        if (p0 >= ghi) break;
+        if (p1 <= glo || p1 == p0) continue;
+        const int64_t a = (glo > p0 ? glo : p0) - p0;
+        const int64_t b = (ghi < p1 ? ghi : p1) - p0;
+        SegCounters cnt;
+        if (PREC == HYB_FP32_SPLIT) {
+            segment_split<MODE>(&insts[i], a, b, smem, cnt);
+            flush_segment<float, MODE>(&insts[i], smem, cnt);
+        } else {
+            segment_fp64<MODE>(&insts[i], a, b, smem, cnt);
+            flush_segment<double, MODE>(&insts[i], smem, cnt);
+        }
+    }
+}
+
+// ------------------------------------------------------------- initial load
+// Uniform positions and a Maxwellian (Box-Muller), ids 0..n-1, drawn at the
+// reserved step 0xFFFFFFFF.
+__global__ void k_load(InstDev *K, int64_t n, double vth, int prec)
+{
+    const PartBuf P = K->buf[K->cur];
+    const double L = K->L, dz = K->dz;
+    const int nc = K->n_cells;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t id = (uint64_t)j;
+        const uint4 a = draw(id, 0xFFFFFFFFu, K->seed_lo, K->seed_hi, 0);
+        const uint4 b = draw(id, 0xFFFFFFFFu, K->seed_lo, K->seed_hi, 1);
+        const double z = u01d(a.x) * L;
+        const double r1 = sqrt(-2.0 * log(u01d(a.y)));
+        const double p1 = kTwoPi * u01d(a.z);
+        const double r2 = sqrt(-2.0 * log(u01d(a.w)));
+        const double p2 = kTwoPi * u01d(b.x);
+        const double vx = vth * (r1 * cos(p1)), vy = vth * (r1 * sin(p1)), vz = vth * (r2 * cos(p2));
+        P.id[j] = id;
+        if (prec == HYB_FP32_SPLIT) {
+            int c;
+            double o;
+            locate_d(z, dz, nc, c, o);
+            P.c[j] = c;
+            P.o[j] = (float)o;
+            P.vxf[j] = (float)vx;
+            P.vyf[j] = (float)vy;
+            P.vzf[j] = (float)vz;
+        } else {
+            P.z[j] = z;
+            P.vxd[j] = vx;
+            P.vyd[j] = vy;
+            P.vzd[j] = vz;
+        }
+    }
+}
+
+// --------------------------------------------------------------- cell sort
+// Counting sort by cell every few steps: removes dead slots, folds the
+// appended births in, and restores cell locality for the deposit.
+
+template <int PREC>
+__device__ __forceinline__ bool cell_of(const PartBuf &P, int64_t i, double dz, int nc, int &c)
+{
+    if (PREC == HYB_FP32_SPLIT) {
+        c = P.c[i];
+        return c >= 0;
+    }
+    const double z = P.z[i];
+    if (z < 0.0) return false;
+    double o;
+    locate_d(z, dz, nc, c, o);
+    return true;
+}
+
+template <int PREC, int PHASE>  // PHASE 0: count, 1: scatter
+__global__ void __launch_bounds__(kBlock) k_sort_pass(InstDev *__restrict__ insts, int n_max,
+                                                      const int64_t *__restrict__ prefix)
+{
+    const int64_t total = prefix[n_max];
+    if (total <= 0) return;
+    int64_t chunk = (total + gridDim.x - 1) / gridDim.x;
+    chunk = (chunk + 127) & ~(int64_t)127;
+    const int64_t glo = (int64_t)blockIdx.x * chunk;
+    if (glo >= total) return;
+    const int64_t ghi = glo + chunk < total ? glo + chunk : total;
+    int lo = 0, hi = n_max;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= glo)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const int lane = threadIdx.x & 31;
+    for (int inst = lo; inst < n_max; ++inst) {
+        const int64_t p0 = prefix[inst], p1 = prefix[inst + 1];
+        if (p0 >= ghi) break;
+        if (p1 <= glo || p1 == p0) continue;
+        const int64_t a = (glo > p0 ? glo : p0) - p0;
+        const int64_t b = (ghi < p1 ? ghi : p1) - p0;
+        InstDev *K = &insts[inst];
+        const PartBuf S = K->buf[K->cur];
+        const PartBuf D = K->buf[K->cur ^ 1];
+        int32_t *cnt = K->cell_cnt;
+        const double dz = K->dz;
+        const int nc = K->n_cells;
+        for (int64_t base = a; base < b; base += blockDim.x) {
+            const int64_t i = base + threadIdx.x;
+            int c = -1;
+            const bool alive = i < b && cell_of<PREC>(S, i, dz, nc, c);
+            const unsigned act = __ballot_sync(kFull, alive);
+            if (!alive) continue;
+            const unsigned peers = __match_any_sync(act, c);
+            const int leader = __ffs(peers) - 1;
+            int pos = 0;
+            if (lane == leader) pos = atomicAdd(&cnt[c], __popc(peers));
+            if (PHASE == 1) {
+                pos = __shfl_sync(peers, pos, leader) + __popc(peers & lanemask_lt());
+                D.id[pos] = S.id[i];
+                if (PREC == HYB_FP32_SPLIT) {
+                    D.c[pos] = c;
+                    D.o[pos] = S.o[i];
+                    D.vxf[pos] = S.vxf[i];
+                    D.vyf[pos] = S.vyf[i];
+                    D.vzf[pos] = S.vzf[i];
+                } else {
+                    D.z[pos] = S.z[i];
+                    D.vxd[pos] = S.vxd[i];
+                    D.vyd[pos] = S.vyd[i];
+                    D.vzd[pos] = S.vzd[i];
+                }
+            }
+        }
+    }
+}
+
+// Exclusive scan of the cell counts, one CTA per sorted instance; the total
+// goes to cell_cnt[n_cells].
+__global__ void __launch_bounds__(1024) k_sort_scan(InstDev *insts, const int64_t *prefix)
+{
+    InstDev *K = &insts[blockIdx.x];
+    if (prefix[blockIdx.x + 1] == prefix[blockIdx.x]) return;
+    int32_t *cnt = K->cell_cnt;
+    const int nc = K->n_cells;
+    __shared__ int32_t s_warp[32];
+    __shared__ int32_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nc; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        const int32_t v = j < nc ? cnt[j] : 0;
+        int32_t x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(kFull, x, d);
+            if ((threadIdx.x & 31) >= d) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int32_t w = threadIdx.x < (blockDim.x >> 5) ? s_warp[threadIdx.x] : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, w, d);
+                if ((int)threadIdx.x >= d) w += y;
+            }
+            s_warp[threadIdx.x] = w;
+        }
+        __syncthreads();
+        const int32_t warp_off = (threadIdx.x >> 5) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
+        const int32_t carry = s_carry;
+        if (j < nc) cnt[j] = carry + warp_off + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = carry + warp_off + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cnt[nc] = s_carry;
+}
+
+// After the scatter: flip the buffers, set the slot counts, clear the counts.
+__global__ void k_sort_finish(InstDev *insts, const int64_t *prefix)
+{
+    InstDev *K = &insts[blockIdx.x];
+    if (prefix[blockIdx.x + 1] == prefix[blockIdx.x]) return;
+    __shared__ int32_t total;
+    if (threadIdx.x == 0) total = K->cell_cnt[K->n_cells];
+    __syncthreads();
+    for (int j = threadIdx.x; j <= K->n_cells; j += blockDim.x) K->cell_cnt[j] = 0;
+    if (threadIdx.x == 0) {
+        K->cur ^= 1;
+        K->n_slots = (unsigned long long)total;
+        K->n_slots_step = total;
+    }
+}
+
+__global__ void k_prefix(InstDev *insts, int n_max, int64_t *prefix)
+{
+    if (threadIdx.x != 0) return;
+    int64_t acc = 0;
+    prefix[0] = 0;
+    for (int i = 0; i < n_max; ++i) {
+        if (insts[i].active) acc += insts[i].n_slots_step;
+        prefix[i + 1] = acc;
+    }
+}
+
+// prefix over one instance that is being (re)initialised
+__global__ void k_prefix_one(InstDev *K, int64_t *prefix)
+{
+    if (threadIdx.x != 0) return;
+    prefix[0] = 0;
+    prefix[1] = (int64_t)K->n_slots;
+    K->n_slots_step = (int64_t)K->n_slots;
+}
+
+__global__ void k_set_active(InstDev *K, int active, int64_t target_step)
+{
+    if (threadIdx.x != 0) return;
+    K->active = active;
+    K->target_step = target_step;
+}
+
+template <int PREC, int MODE>
+cudaError_t launch_k(InstDev *inst, int n_max, const int64_t *prefix, LaunchCfg cfg, cudaStream_t s)
+{
+    k_electron<PREC, MODE><<<cfg.grid, cfg.block, cfg.smem, s>>>(inst, n_max, prefix);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+void configure_kernels()
+{
+    // opt in to the full 227 KB of shared memory per block
+    const int most = 227 * 1024;
+    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_electron<HYB_FP64, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_electron<HYB_FP64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    configure_field_kernel();
+}
+
+int electron_blocks_per_sm(int precision, size_t smem)
+{
+    int n = 0;
+    if (precision == HYB_FP32_SPLIT)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_electron<HYB_FP32_SPLIT, 0>, kBlock, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_electron<HYB_FP64, 0>, kBlock, smem);
+    return n;
+}
+
+size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins)
+{
+    const size_t el = precision == HYB_FP32_SPLIT ? 4 : 8;
+    return 3 * el * (size_t)max_nodes + 4 * (size_t)(eedf_bins + 1) + 16;
+}
+
+cudaError_t launch_electron_step(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
+                                 cudaStream_t s)
+{
+    return precision == HYB_FP32_SPLIT ? launch_k<HYB_FP32_SPLIT, 0>(inst, n_max, prefix, cfg, s)
+                                       : launch_k<HYB_FP64, 0>(inst, n_max, prefix, cfg, s);
+}
+
+cudaError_t launch_deposit_init(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
+                                cudaStream_t s)
+{
+    return precision == HYB_FP32_SPLIT ? launch_k<HYB_FP32_SPLIT, 1>(inst, n_max, prefix, cfg, s)
+                                       : launch_k<HYB_FP64, 1>(inst, n_max, prefix, cfg, s);
+}
+
+cudaError_t launch_load(InstDev *inst, int64_t n, double vth, int precision, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int grid = (int)((n + 255) / 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_load<<<grid, 256, 0, s>>>(inst, n, vth, precision);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(InstDev *inst, int n_max, int64_t *prefix, int precision, LaunchCfg cfg, cudaStream_t s)
+{
+    if (precision == HYB_FP32_SPLIT) {
+        k_sort_pass<HYB_FP32_SPLIT, 0><<<cfg.grid, kBlock, 0, s>>>(inst, n_max, prefix);
+    } else {
+        k_sort_pass<HYB_FP64, 0><<<cfg.grid, kBlock, 0, s>>>(inst, n_max, prefix);
+    }
+    k_sort_scan<<<n_max, 1024, 0, s>>>(inst, prefix);
+    if (precision == HYB_FP32_SPLIT) {
+        k_sort_pass<HYB_FP32_SPLIT, 1><<<cfg.grid, kBlock, 0, s>>>(inst, n_max, prefix);
+    } else {
+        k_sort_pass<HYB_FP64, 1><<<cfg.grid, kBlock, 0, s>>>(inst, n_max, prefix);
+    }
+    k_sort_finish<<<n_max, 256, 0, s>>>(inst, prefix);
+    k_prefix<<<1, 32, 0, s>>>(inst, n_max, prefix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prefix(InstDev *inst, int n_max, int64_t *prefix, cudaStream_t s)
+{
+    k_prefix<<<1, 32, 0, s>>>(inst, n_max, prefix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prefix_one(InstDev *inst, int64_t *prefix, cudaStream_t s)
+{
+    k_prefix_one<<<1, 32, 0, s>>>(inst, prefix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_active(InstDev *inst, int active, int64_t target_step, cudaStream_t s)
+{
+    k_set_active<<<1, 32, 0, s>>>(inst, active, target_step);
+    return cudaGetLastError();
+}
+
+}  // namespace hyb

@@ -1,0 +1,457 @@
+// hyb_field.cu -- the per-instance FP64 grid kernel of each step (arXiv
+// 1508.02892, Secs. II.B-II.D): electron density from the CIC sums, the ion
+// fluid update (drift-diffusion, Eqs. 2.5-2.8, or the full model, Eq. 2.3,
+// then continuity, Eq. 2.4), the Poisson solve and field, the time sums, and
+// the gamma secondaries that will take part in the next step.
+//
+// One CTA of 1024 threads per instance, all node arrays in shared memory
+// (7 x n_nodes doubles), thread t owning a contiguous run of nodes.
+//   * Poisson: the constant-coefficient tridiagonal system is solved in closed
+//     form by two block prefix scans (phi = linear part + discrete double
+//     integral of the charge) instead of the serial Thomas recursion.
+//   * Full-model flux: the tridiagonal system of Eq. 2.3 is diagonally
+//     dominant with ratio r = max (|a|+|c|)/b (a Courant number); it is solved
+//     by Jacobi sweeps, ceil(ln 2^-60 / ln r) of them, which bounds the error
+//     by 2^-60 of the initial one.  r >= 1/2 is reported as unstable.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "hyb_internal.cuh"
+
+namespace hyb {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kArrays = 7;
+
+struct Red {
+    double w[32];
+    double total;
+    int flag;
+    unsigned long long count;
+};
+
+// Exclusive block scan of one double per thread; *total gets the sum.
+__device__ double block_exscan(double v, Red &r, double *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const double y = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) r.w[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        double t = lane < nw ? r.w[lane] : 0.0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const double y = __shfl_up_sync(kFull, t, d);
+            if (lane >= d) t += y;
+        }
+        r.w[lane] = t;
+    }
+    __syncthreads();
+    const double off = wid ? r.w[wid - 1] : 0.0;
+    if (total) *total = r.w[nw - 1];
+    __syncthreads();
+    return off + x - v;
+}
+
+__device__ double block_max(double v, Red &r)
+{
+#pragma unroll
+    for (int d = 16; d; d >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, d));
+    if ((threadIdx.x & 31) == 0) r.w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double m = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, r.w[k]);
+    __syncthreads();
+    return m;
+}
+
+// linear interpolation in a 4-column table, clamped at the ends
+__device__ double interp_lin(const double *tab, int n, int cx, int cy, double v)
+{
+    if (v <= tab[cx]) return tab[cy];
+    if (v >= tab[4 * (n - 1) + cx]) return tab[4 * (n - 1) + cy];
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (tab[4 * mid + cx] <= v)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const double f = (v - tab[4 * lo + cx]) / (tab[4 * (lo + 1) + cx] - tab[4 * lo + cx]);
+    return tab[4 * lo + cy] + f * (tab[4 * (lo + 1) + cy] - tab[4 * lo + cy]);
+}
+
+struct Fluid {
+    int model, n_tab;
+    const double *tab;
+    double mu_const, ngas, kT, mi, mn;
+
+    // ion mobility at |E| (Sec. II.C, tabulated Tables 2/4)
+    __device__ double mobility(double e_abs) const
+    {
+        if (model == HYB_ION_DD_CONST) return mu_const;
+        const double eon_td = e_abs / ngas * 1e21;
+        return interp_lin(tab, n_tab, 0, 1, eon_td);
+    }
+    // ion temperature (J): gas temperature, or Eq. 2.8
+    __device__ double temp(double mu, double e_abs) const
+    {
+        if (model == HYB_ION_DD_CONST) return kT;
+        const double ud = mu * e_abs;
+        return kT + (mi + mn) / (5.0 * mi + 3.0 * mn) * mn * ud * ud;
+    }
+    // momentum-exchange frequency at |u| (Sec. II.B, tabulated Tables 3/5)
+    __device__ double exch(double u_abs) const { return interp_lin(tab, n_tab, 3, 2, u_abs); }
+    // field-driven wall flux with the alpha switch of Sec. II.C
+    __device__ double wall(int w, double n, double E) const
+    {
+        const bool into = w == 0 ? (E < 0.0) : (E > 0.0);
+        if (!into) return 0.0;
+        return mobility(fabs(E)) * n * E;
+    }
+};
+
+__device__ __forceinline__ double node_volume(int j, int G, double dz) { return (j == 0 || j == G - 1) ? 0.5 * dz : dz; }
+
+__device__ void field_body(InstDev *K, double *sm, Red &red)
+{
+    const int G = K->G;
+    const int T = blockDim.x;
+    const int t = threadIdx.x;
+    const int per = (G + T - 1) / T;
+    const int j0 = min(t * per, G), j1 = min(j0 + per, G);
+    const double dz = K->dz, dt = K->dt, w = K->w;
+    const bool init = K->init_pending != 0;
+
+    double *s_ni = sm;
+    double *s_E = sm + G;
+    double *s_g = sm + 2 * G;
+    double *s_A = sm + 3 * G;
+    double *s_ib = sm + 4 * G;
+    double *s_d = sm + 5 * G;
+    double *s_x = sm + 6 * G;
+
+    for (int j = j0; j < j1; ++j) {
+        s_ni[j] = K->ni[j];
+        s_E[j] = K->E[j];
+        s_g[j] = K->gam[j];
+    }
+    if (t == 0) {
+        red.flag = 0;
+        red.count = 0ull;
+    }
+    __syncthreads();
+
+    const Fluid F{K->ion_model, K->n_tab, K->tab, K->mu_const, K->ngas, K->kT_gas, K->m_ion, K->m_gas};
+    double *gfin = s_g;
+    if (!init) {
+        // ---------------------------------------------------------- ion fluid
+        if (K->ion_model == HYB_ION_FULL) {
+            // Eq. 2.3: nu at u^n = Gamma^{n-1/2}/n^n, advection semi-implicit
+            for (int j = j0; j < j1; ++j) {
+                const double nj = s_ni[j];
+                s_A[j] = nj >= K->n_floor ? s_g[j] / nj : 0.0;
+                const double ea = fabs(s_E[j]);
+                s_x[j] = nj * F.temp(F.mobility(ea), ea);
+            }
+            __syncthreads();
+            const double h = dt / (2.0 * dz);
+            double rmax = 0.0;
+            for (int j = j0; j < j1; ++j) {
+                if (j == 0 || j == G - 1) continue;
+                const double nu = F.exch(fabs(s_A[j]));
+                const double b = 1.0 + nu * dt / 2.0;
+                s_d[j] = s_g[j] * (1.0 - nu * dt / 2.0) + kQe * s_ni[j] * s_E[j] * dt / K->m_ion -
+                         h / K->m_ion * (s_x[j + 1] - s_x[j - 1]);
+                s_ib[j] = 1.0 / b;
+                rmax = fmax(rmax, (fabs(h * s_A[j - 1]) + fabs(h * s_A[j + 1])) / b);
+            }
+            const double r = block_max(rmax, red);
+            // Dirichlet wall rows (field-driven wall flux), both Jacobi buffers
+            if (t == 0) {
+                const double g0 = F.wall(0, s_ni[0], s_E[0]);
+                const double gN = F.wall(1, s_ni[G - 1], s_E[G - 1]);
+                s_g[0] = g0;
+                s_x[0] = g0;
+                s_g[G - 1] = gN;
+                s_x[G - 1] = gN;
+                if (r >= 0.5) atomicOr(&K->status, (unsigned)HYB_STATUS_UNSTABLE);
+            }
+            int iters = 1;
+            if (r > 1e-300) iters = (int)ceil(-41.58883083359672 / log(r));
+            iters = iters < 1 ? 1 : (iters > 64 ? 64 : iters);
+            __syncthreads();
+            double *X = s_g, *Y = s_x;
+            for (int it = 0; it < iters; ++it) {
+                for (int j = j0; j < j1; ++j) {
+                    if (j == 0 || j == G - 1) continue;
+                    Y[j] = (s_d[j] + h * s_A[j - 1] * X[j - 1] - h * s_A[j + 1] * X[j + 1]) * s_ib[j];
+                }
+                __syncthreads();
+                double *tmp = X;
+                X = Y;
+                Y = tmp;
+            }
+            gfin = X;
+        } else {
+            // Eq. 2.5 at level n (explicit drift-diffusion)
+            for (int j = j0; j < j1; ++j) {
+                if (j == 0) {
+                    s_x[j] = F.wall(0, s_ni[0], s_E[0]);
+                } else if (j == G - 1) {
+                    s_x[j] = F.wall(1, s_ni[G - 1], s_E[G - 1]);
+                } else {
+                    const double ea = fabs(s_E[j]);
+                    const double mu = F.mobility(ea);
+                    const double D = mu * F.temp(mu, ea) / kQe;
+                    s_x[j] = mu * s_ni[j] * s_E[j] - D * (s_ni[j + 1] - s_ni[j - 1]) / (2.0 * dz);
+                }
+            }
+            __syncthreads();
+            gfin = s_x;
+        }
+        // ------------------------------------- continuity, Eq. 2.4 (G^n source)
+        unsigned long long clamps = 0;
+        for (int j = j0; j < j1; ++j) {
+            const double gs = w * K->s_iz[j] / (node_volume(j, G, dz) * dt);
+            double nn;
+            if (j == 0)
+                nn = s_ni[0] - dt / dz * (gfin[1] - gfin[0]) + dt * gs;
+            else if (j == G - 1)
+                nn = s_ni[G - 1] - dt / dz * (gfin[G - 1] - gfin[G - 2]) + dt * gs;
+            else
+                nn = s_ni[j] - dt / (2.0 * dz) * (gfin[j + 1] - gfin[j - 1]) + dt * gs;
+            if (nn < 0.0) {
+                nn = 0.0;
+                ++clamps;
+            }
+            s_ni[j] = nn;
+            K->ni[j] = nn;
+            K->gam[j] = gfin[j];
+            K->gsrc[j] = gs;
+            K->acc_ni[j] += nn;
+            K->acc_gi[j] += gfin[j];
+        }
+        if (clamps) atomicAdd(&red.count, clamps);
+        __syncthreads();
+    }
+
+    // ------------------------------------------------------------- Poisson
+    const double phi0 = K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)(K->step + (init ? 0 : 1)) * dt));
+    double *s_rho = s_A;
+    double *s_S = s_ib;
+    double *s_phi = s_d;
+    double part = 0.0;
+    for (int j = j0; j < j1; ++j) {
+        const double ne = w * K->dep_n[j] / node_volume(j, G, dz);
+        K->ne[j] = ne;
+        const double rho = kQe * (s_ni[j] - ne);
+        s_rho[j] = rho;
+        const double sj = (j >= 1 && j <= G - 2) ? dz * dz * rho / kEps0 : 0.0;
+        part += sj;
+        s_S[j] = part;  // local inclusive
+        if (!init) {
+            K->acc_ne[j] += ne;
+            K->acc_wn[j] += K->dep_n[j];
+            K->acc_we[j] += K->dep_e[j];
+        }
+        K->dep_n[j] = 0.0;
+        K->dep_e[j] = 0.0;
+        K->s_iz[j] = 0.0;
+    }
+    // S_j = sum_{k=1..j} s_k
+    const double off = block_exscan(part, red, nullptr);
+    double ssum = 0.0;
+    for (int j = j0; j < j1; ++j) {
+        s_S[j] += off;
+        if (j <= G - 2) ssum += s_S[j];
+    }
+    double stot;
+    block_exscan(ssum, red, &stot);
+    // d_0 = (phi_N - phi_0 + sum_{j=0}^{G-2} S_j)/(G-1); d_j = d_0 - S_j
+    const double d0 = (0.0 - phi0 + stot) / (double)(G - 1);
+    double dpart = 0.0;
+    for (int j = j0; j < j1; ++j) {
+        const double dj = j <= G - 2 ? d0 - s_S[j] : 0.0;
+        s_phi[j] = dpart;  // local exclusive
+        dpart += dj;
+    }
+    const double doff = block_exscan(dpart, red, nullptr);
+    for (int j = j0; j < j1; ++j) s_phi[j] = phi0 + doff + s_phi[j];
+    __syncthreads();
+    if (t == 0) s_phi[G - 1] = 0.0;
+    __syncthreads();
+    int bad = 0;
+    for (int j = j0; j < j1; ++j) {
+        double e;
+        if (j == 0) {
+            e = -d0 / dz - s_rho[0] * dz / (2.0 * kEps0);
+        } else if (j == G - 1) {
+            e = -(d0 - s_S[G - 2]) / dz + s_rho[G - 1] * dz / (2.0 * kEps0);
+        } else {
+            e = -((d0 - s_S[j]) + (d0 - s_S[j - 1])) / (2.0 * dz);
+        }
+        K->E[j] = e;
+        K->Ef[j] = (float)e;
+        K->phi[j] = s_phi[j];
+        if (!isfinite(e) || !isfinite(s_ni[j])) bad = 1;
+    }
+    if (bad) red.flag = 1;
+    __syncthreads();
+    if (red.flag && t == 0) atomicOr(&K->status, (unsigned)HYB_STATUS_NONFINITE);
+
+    if (init) {
+        if (t == 0) {
+            K->n_slots_step = (int64_t)K->n_slots;
+            K->init_pending = 0;
+        }
+        return;
+    }
+
+    // ------------------------------------------- bookkeeping, gamma emission
+    __shared__ int s_cnt[2];
+    __shared__ unsigned long long s_base;
+    if (t == 0) {
+        if (red.count) K->ctr[C_CLAMP] += red.count;
+        K->n_samples += 1;
+        const double g0 = gfin[0], gN = gfin[G - 1];
+        K->flux_in[0] = g0 < 0.0 ? -g0 : 0.0;
+        K->flux_in[1] = gN > 0.0 ? gN : 0.0;
+        K->step += 1;
+        const uint32_t n = (uint32_t)K->step;
+        s_cnt[0] = s_cnt[1] = 0;
+        if (K->gamma_see > 0.0 && w > 0.0) {
+            for (int wall = 0; wall < 2; ++wall) {
+                const double ns = K->gamma_see * K->flux_in[wall] * dt / w;
+                if (!(ns > 0.0)) continue;
+                const double k = floor(ns);
+                const double frac = ns - k;
+                const uint4 r = draw(0xFFFFFFFFFFFFFF00ull | (uint64_t)wall, n, K->seed_lo, K->seed_hi, 3);
+                int64_t c = (int64_t)k + (u01d(r.x) < frac ? 1 : 0);
+                if (c > (1 << 20) - 1) {
+                    c = (1 << 20) - 1;
+                    K->status |= HYB_STATUS_EMIT_CAP;
+                }
+                s_cnt[wall] = (int)c;
+            }
+        }
+        s_base = K->n_slots;
+        const unsigned long long tot = (unsigned long long)(s_cnt[0] + s_cnt[1]);
+        K->n_slots = s_base + tot;
+        K->ctr[C_SEE0] += s_cnt[0];
+        K->ctr[C_SEE1] += s_cnt[1];
+    }
+    __syncthreads();
+    const int ntot = s_cnt[0] + s_cnt[1];
+    if (ntot) {
+        const PartBuf P = K->buf[K->cur];
+        const uint32_t n = (uint32_t)K->step;
+        const double sp = K->see_speed, L = K->L;
+        for (int k = t; k < ntot; k += T) {
+            const int wall = k < s_cnt[0] ? 0 : 1;
+            const uint32_t j = (uint32_t)(wall == 0 ? k : k - s_cnt[0]);
+            const uint64_t id = see_id(wall, n, j);
+            const uint4 r = draw(id, n, K->seed_lo, K->seed_hi, 2);
+            const double ct = sqrt(u01d(r.x));
+            const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+            const double ph = kTwoPi * u01d(r.y);
+            const double vn = sp * ct;
+            const double vx = sp * st * cos(ph), vy = sp * st * sin(ph);
+            double vz, z;
+            if (wall == 0) {
+                vz = vn;
+                z = u01d(r.z) * vn * dt;
+            } else {
+                vz = -vn;
+                z = L - u01d(r.z) * vn * dt;
+            }
+            const unsigned long long slot = s_base + (unsigned long long)k;
+            if (slot >= (unsigned long long)K->capacity) {
+                atomicOr(&K->status, (unsigned)HYB_STATUS_CAPACITY);
+                continue;
+            }
+            P.id[slot] = id;
+            if (K->precision == HYB_FP32_SPLIT) {
+                const double x = z / dz;
+                const double f = floor(x);
+                int c = (int)f;
+                double o = x - f;
+                if (c >= K->n_cells) {
+                    c = K->n_cells - 1;
+                    o = 1.0;
+                }
+                P.c[slot] = c;
+                P.o[slot] = (float)o;
+                P.vxf[slot] = (float)vx;
+                P.vyf[slot] = (float)vy;
+                P.vzf[slot] = (float)vz;
+            } else {
+                P.z[slot] = z;
+                P.vxd[slot] = vx;
+                P.vyd[slot] = vy;
+                P.vzd[slot] = vz;
+            }
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        unsigned long long ns = K->n_slots;
+        if (ns > (unsigned long long)K->capacity) {
+            K->status |= HYB_STATUS_CAPACITY;
+            ns = (unsigned long long)K->capacity;
+            K->n_slots = ns;
+        }
+        K->n_slots_step = (int64_t)ns;
+        if (K->target_step > 0 && K->step >= K->target_step) K->active = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kFieldThreads) k_field(InstDev *insts, int n_max, int64_t *prefix, unsigned *ticket)
+{
+    extern __shared__ __align__(16) double sm[];
+    __shared__ Red red;
+    InstDev *K = &insts[blockIdx.x];
+    if (K->active || K->init_pending) field_body(K, sm, red);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned tk = atomicAdd(ticket, 1u);
+        if (tk == gridDim.x - 1) {
+            __threadfence();
+            int64_t acc = 0;
+            prefix[0] = 0;
+            for (int i = 0; i < n_max; ++i) {
+                const volatile InstDev *Ki = &insts[i];
+                if (Ki->active) acc += Ki->n_slots_step;
+                prefix[i + 1] = acc;
+            }
+            *ticket = 0u;
+        }
+    }
+}
+
+}  // namespace
+
+size_t field_smem_bytes(int max_nodes) { return (size_t)kArrays * 8 * (size_t)max_nodes; }
+
+void configure_field_kernel()
+{
+    cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)field_smem_bytes(kMaxNodes));
+}
+
+cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, cudaStream_t s)
+{
+    k_field<<<n_max, kFieldThreads, field_smem_bytes(kMaxNodes), s>>>(inst, n_max, prefix, ticket);
+    return cudaGetLastError();
+}
+
+}  // namespace hyb

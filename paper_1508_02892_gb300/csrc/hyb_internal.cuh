@@ -1,0 +1,149 @@
+// hyb_internal.cuh -- device-side state and helpers shared by the kernels and
+// the host runtime of the GB300 electron PIC/MCC library (arXiv 1508.02892).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hybrid1d.h"
+
+namespace hyb {
+
+// CODATA 2018 (e and k_B exact)
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kKb = 1.380649e-23;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kAmu = 1.66053906660e-27;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+constexpr int32_t kDeadCell = INT32_MIN;  // cell index of a removed split-mode particle
+constexpr int kFieldThreads = 1024;         // one field CTA per instance
+constexpr int kMaxNodes = HYB_MAX_CELLS + 1;
+
+// Particle store, structure of arrays.  Split mode uses c/o/vxf..; FP64 mode
+// uses z/vxd..; id is shared.
+struct PartBuf {
+    int32_t *c;
+    float *o, *vxf, *vyf, *vzf;
+    double *z, *vxd, *vyd, *vzd;
+    uint64_t *id;
+};
+
+// Everything a kernel needs about one discharge.  Lives in device memory; the
+// host writes it at admission and the kernels update the mutable tail.
+struct InstDev {
+    // ---- constant after admission
+    int32_t precision, n_cells, G, ion_model, n_xs, n_tab, eedf_bins, pad0;
+    int64_t capacity;
+    double L, dz, dt, ngas, w, m_gas, m_ion, qm, nu_max, p_max, n_floor, bin_w;
+    double e_lo, e_hi, inv_dlog, e_exc, e_iz, two_mM, gamma_see, see_speed;
+    double v_rf, f_rf, v_dc, mu_const, kT_gas;
+    uint32_t seed_lo, seed_hi;
+    // FP32 copies for the split-mode electron kernel
+    float f_dt_dz, f_qm_dt, f_half_m_q, f_two_q_m, f_pmax, f_e_lo, f_e_hi, f_inv_e_lo, f_inv_dlog;
+    float f_e_exc, f_e_iz, f_two_mM, f_bin_inv;
+    // tables (device)
+    const double *xs;    // [n_xs][4] {E, sigma_el, sigma_exc, sigma_ion}
+    const float4 *xsf;   // [n_xs] {E, N sigma_el/nu_max, N sigma_exc/nu_max, N sigma_ion/nu_max}
+    const double *tab;   // [n_tab][4] {E/N (Td), mu, nu, u = mu E}
+    // particles (double-buffered for the cell sort)
+    PartBuf buf[2];
+    // grids, n_nodes entries
+    double *ni, *gam, *phi, *E, *ne, *gsrc;
+    float *Ef;
+    double *dep_n, *dep_e, *s_iz;                     // per-step sums, cleared by the field kernel
+    double *acc_ne, *acc_ni, *acc_gi, *acc_wn, *acc_we; // time sums
+    unsigned long long *eedf;                         // eedf_bins + 1 counts
+    int32_t *cell_cnt;                                // n_cells + 1, sort scratch
+    // ---- mutable
+    int32_t active, cur;
+    int64_t step, target_step;
+    unsigned long long n_slots;       // slots in use (atomic append)
+    int64_t n_slots_step;             // slots processed by the current step
+    int64_t n_samples;
+    double flux_in[2];
+    unsigned long long ctr[10];       // births_iz, see0, see1, loss0, loss1, el, exc, iz, null, clamps
+    unsigned int status;
+    int32_t init_pending;             // field kernel runs in initial-solve mode
+};
+
+enum { C_BIRTH_IZ = 0, C_SEE0, C_SEE1, C_LOSS0, C_LOSS1, C_EL, C_EXC, C_IZ, C_NULL, C_CLAMP };
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter (step, seed_lo,
+// seed_hi, call), key = particle id.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint64_t id, uint32_t step, uint32_t seed_lo, uint32_t seed_hi, uint32_t call)
+{
+    return philox4x32_10(make_uint4(step, seed_lo, seed_hi, call), make_uint2((uint32_t)id, (uint32_t)(id >> 32)));
+}
+
+// (k + 1/2) 2^-23 from the top 23 bits: the same value in float and double.
+__device__ __forceinline__ float u01f(uint32_t x) { return ((float)(x >> 9) + 0.5f) * 1.1920928955078125e-07f; }
+__device__ __forceinline__ double u01d(uint32_t x) { return ((double)(x >> 9) + 0.5) * 1.1920928955078125e-07; }
+
+// SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t child_id(uint64_t parent, uint32_t step)
+{
+    return mix64(parent ^ ((uint64_t)step * 0x9E3779B97F4A7C15ull)) | (1ull << 63);
+}
+
+__host__ __device__ __forceinline__ uint64_t see_id(int wall, uint32_t step, uint32_t k)
+{
+    return (1ull << 62) | ((uint64_t)wall << 60) | ((uint64_t)step << 20) | (uint64_t)k;
+}
+
+// ------------------------------------------------------- launch helpers
+// Work decomposition shared by the particle kernels: the running instances'
+// slot ranges are concatenated (prefix[i]..prefix[i+1]) and each block takes
+// one contiguous chunk.
+
+struct LaunchCfg {
+    int grid, block;
+    size_t smem;
+};
+
+// electron kernels (hyb_electron.cu)
+cudaError_t launch_electron_step(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
+                                 cudaStream_t s);
+cudaError_t launch_deposit_init(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
+                                cudaStream_t s);
+cudaError_t launch_load(InstDev *inst, int64_t n, double vth, int precision, cudaStream_t s);
+cudaError_t launch_sort(InstDev *inst, int n_max, int64_t *prefix, int precision, LaunchCfg cfg, cudaStream_t s);
+cudaError_t launch_prefix(InstDev *inst, int n_max, int64_t *prefix, cudaStream_t s);
+cudaError_t launch_prefix_one(InstDev *inst, int64_t *prefix, cudaStream_t s);
+cudaError_t launch_set_active(InstDev *inst, int active, int64_t target_step, cudaStream_t s);
+size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins);
+
+// field kernel (hyb_field.cu)
+cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned int *ticket, cudaStream_t s);
+size_t field_smem_bytes(int max_nodes);
+void configure_field_kernel();
+
+// one-time kernel attributes and occupancy (hyb_electron.cu)
+void configure_kernels();
+int electron_blocks_per_sm(int precision, size_t smem);
+
+}  // namespace hyb

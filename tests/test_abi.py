@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/hybrid1d.h declares (no GPU needed: nothing is computed)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "hybrid1d.h")) as f:
+        src = f.read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(hyb_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for need in ("hyb_create_discharge", "hyb_advance", "hyb_read_moments", "hyb_destroy",
+                 "hyb_batch_create", "hyb_batch_admit", "hyb_batch_advance", "hyb_batch_poll"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1508_02892_gb300 import build, hybrid
+    build.build()
+    L = hybrid.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+    assert set(_declared()) <= set(hybrid.EXPORTS)
+
+
+def test_binding_structs_match_header_field_order():
+    from paper_1508_02892_gb300 import hybrid
+    with open(os.path.join(ROOT, "include", "hybrid1d.h")) as f:
+        src = f.read()
+    body = re.search(r"typedef struct hyb_params \{(.*?)\} hyb_params;", src, re.S).group(1)
+    fields = []
+    for line in body.split("\n"):
+        line = re.sub(r"/\*.*?\*/", "", line).strip()
+        if not line:
+            continue
+        for decl in line.rstrip(";").split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            names = re.findall(r"\*?\s*(\w+)\s*(?:,|$)", decl.split(None, 1)[1] if " " in decl else decl)
+            fields += [n for n in names if n not in ("const", "double", "int32_t", "int64_t", "uint64_t")]
+    assert fields == [f for f, _ in hybrid.Params._fields_]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_1508_02892_gb300 import hybrid
+    monkeypatch.setattr(hybrid, "_lib", None)
+    monkeypatch.setattr(hybrid, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        hybrid.lib()
+
+
+def test_host_validation_rejects_bad_params():
+    """Argument checks run on the host before any device work."""
+    import numpy as np
+
+    from paper_1508_02892_gb300 import hybrid, workloads
+    hybrid.build_ok = True
+    p = workloads.config1(n_particles=100)
+    p["n_cells"] = 1
+    with pytest.raises(hybrid.HybError) as e:
+        hybrid.footprint(p)
+    assert e.value.code == -1
+    p = workloads.config1(n_particles=100)
+    p["xs_el"] = p["xs_el"].copy()
+    p["xs_el"][5] = np.nan
+    with pytest.raises(hybrid.HybError) as e:
+        hybrid.footprint(p)
+    assert e.value.code == -4
+    p = workloads.config1(n_particles=100)
+    assert hybrid.footprint(p) > 0

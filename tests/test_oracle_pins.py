@@ -517,8 +517,9 @@ def test_initial_load_maxwellian_uniform():
 def test_step_bookkeeping_exact():
     """Particle count, CIC charge and ion inventory close exactly every step:
     N_{n+1} = N_n + births + secondaries - losses; sum n_e dV = w (N_{n+1} -
-    births_n) (children are deposited one step later); ion inventory changes by
-    births w - dt (Gamma_N - Gamma_0)."""
+    births_n - secondaries_n) (children are deposited one step later and the
+    secondaries born at the end of step n enter at step n+1); ion inventory
+    changes by births w - dt (Gamma_N - Gamma_0)."""
     p = W.config1(n_particles=4000, te0_ev=25.0, v_rf_amp_v=400.0, gamma_see=0.3, n_cells=100, weight=2e5)
     o = oracle.Oracle(p)
     G = o.G
@@ -539,7 +540,7 @@ def test_step_bookkeeping_exact():
         seen_see += see
         assert c["particles"] == prev["particles"] + births + see - d["losses0"] - d["losses1"]
         ne = o.grid(oracle.GRID_NE)
-        assert (ne * dv).sum() == pytest.approx(w * (c["particles"] - births), rel=1e-12)
+        assert (ne * dv).sum() == pytest.approx(w * (c["particles"] - births - see), rel=1e-12)
         ni = o.grid(oracle.GRID_NI)
         g = o.grid(oracle.GRID_GAMMA)
         src = o.grid(oracle.GRID_GSRC)
