@@ -1,0 +1,386 @@
+"""Benchmark: electron particle-steps/s of the batched FP32-split PIC/MCC step.
+
+Workload (default): 64 independent helium discharges advanced together, gaps
+U(0.3, 2) mm at 150..2000 cells, 1e4..2e6 electrons each (log-uniform),
+100..400 V, drift-diffusion or full-fluid ions, FP32 particles with FP64 field
+solves; one bench step = one 100-step chunk (one CUDA graph).  Inputs are
+seeded and synthetic.
+
+One JSON line on rank 0.  --impl reference runs the FP64 CPU oracle on the
+same workload instead (one PIC step over all discharges per bench step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_SPLIT = 48   # per particle-step: read c,o,v,id (28 B) + write c,o,v (20 B)
+BYTES_FP64 = 72    # read z,v,id (40 B) + write z,v (32 B)
+CHUNK = 100
+METRIC = "electron particle-steps/s, FP32-batched vs FP64 plain, 1 GB300; p50/p99 latency"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1508_02892_gb300", "csrc", "hyb_electron.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_push():
+    """DRAM bytes per particle push of the electron kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "electron_split_config3_ncu.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_push"])
+    except Exception:
+        return None
+
+
+def workload(rank=0, n_inst=64, scale=1.0):
+    from paper_1508_02892_gb300 import workloads as W
+    inst = W.config3_instances(n=n_inst, seed=2026 + 7919 * rank, scale=scale)
+    return inst
+
+
+def cpu_baseline(params_list, budget_s=12.0, window=3):
+    """The FP64 oracle as it stands, single thread, on the first discharges of
+    the workload, `window` steps each, until `budget_s` of stepping."""
+    import oracle
+    pushes = 0
+    t_used = 0.0
+    used = []
+    for i, p in enumerate(params_list):
+        o = oracle.Oracle(p)
+        for _ in range(window):
+            n = o.n_particles
+            t0 = time.perf_counter()
+            o.step(1)
+            t_used += time.perf_counter() - t0
+            pushes += n
+        used.append(i)
+        o.close()
+        if t_used >= budget_s:
+            break
+    return {"value": pushes / t_used, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"discharges {used[0]}..{used[-1]} of the workload, {window} steps each, "
+                      f"{pushes} particle-steps in {t_used:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the same workload."""
+    import oracle  # noqa: F401  (built by build())
+    from oracle import Oracle
+    params = workload(0, args.instances, args.scale)
+    sims = [Oracle(p) for p in params]
+    def step():
+        n = sum(s.n_particles for s in sims)
+        t0 = time.perf_counter()
+        for s in sims:
+            s.step(1)
+        return n, time.perf_counter() - t0
+    for _ in range(args.warmup):
+        step()
+    tot_n, tot_t, lat = 0, 0.0, []
+    for _ in range(args.steps):
+        n, t = step()
+        tot_n += n
+        tot_t += t
+        lat.append(t * 1e3)
+    v = tot_n / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.instances} batched He discharges (config 3 ranges), one PIC step "
+                                   f"over all of them per bench step", "instances": args.instances,
+                       "particles": sum(s.n_particles for s in sims)},
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"all {args.instances} discharges, {args.steps} timed PIC steps"},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_fp64_plain(params, chunks=2, steps=20):
+    """The plain FP64 path: one discharge at a time (the largest of the mix)."""
+    import torch
+
+    from paper_1508_02892_gb300 import hybrid, workloads as W
+    p = dict(max(params, key=lambda q: q["n_particles"]))
+    p["precision"] = W.FP64
+    stream = torch.cuda.current_stream()
+    d = hybrid.Discharge(p, stream=stream.cuda_stream)
+    d.advance(steps)
+    d.sync()
+    c0 = d.counters()["pushes"]
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(chunks):
+        s.record(stream)
+        d.advance(steps)
+        e.record(stream)
+        e.synchronize()
+        ms += s.elapsed_time(e)
+    n = d.counters()["pushes"] - c0
+    d.close()
+    return {"value": n / (ms / 1e3), "unit": "particle-steps/s", "particles": int(p["n_particles"]),
+            "steps": chunks * steps, "dtype": "f64"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as G
+    G.build()
+    if os.environ.get("HYB_CHECKED") == "1":
+        from paper_1508_02892_gb300 import build as B
+        B.build(checked=True)
+    from paper_1508_02892_gb300 import hybrid, workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    params = workload(rank, args.instances, args.scale)
+    # one non-default stream for the library, the L2 flush and the timing events
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    b = hybrid.Batch(args.instances, hybrid.HYB_FP32_SPLIT, stream=stream.cuda_stream)
+    slots = [b.admit(p) for p in params]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def pushes():
+        return sum(b.counters(s)["pushes"] for s in slots)
+
+    for _ in range(args.warmup):
+        b.advance(CHUNK)
+    torch.cuda.synchronize()
+    b.set_profiling(True)
+    b.profile(reset=True)
+    prof0 = b.profile()
+    p0 = pushes()
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()                         # L2 flush outside the timed interval
+        ev_s[k].record(stream)
+        b.advance(CHUNK)
+        ev_e[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    lat = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
+    ms_local = sum(lat)
+    prof = b.profile()
+    n_local = pushes() - p0
+    b.set_profiling(False)
+    if world > 1:
+        t = torch.tensor([ms_local, float(n_local)], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_tot, n_tot = mx[0].item(), sm[1].item()
+    else:
+        ms_tot, n_tot = ms_local, float(n_local)
+    value = n_tot / (ms_tot / 1e3)
+
+    # roofline of the dominant kernel (electron step)
+    n_launch = prof["n_electron"] - prof0["n_electron"]
+    ms_e = prof["ms_electron"] - prof0["ms_electron"]
+    per_launch = n_local / max(n_launch, 1)
+    avg_ms = ms_e / max(n_launch, 1)
+    peak, peak_kind = peaks()
+    achieved = BYTES_SPLIT * per_launch / (avg_ms / 1e3) / 1e9
+    tpp = traffic_per_push()
+    shares = {"electron": ms_e, "field": prof["ms_field"] - prof0["ms_field"],
+              "sort": prof["ms_sort"] - prof0["ms_sort"]}
+
+    # end to end through the public API: admit from host parameters, chunks
+    # with a host read of every discharge's moments, evict
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b2 = hybrid.Batch(args.instances, hybrid.HYB_FP32_SPLIT, stream=stream.cuda_stream)
+        s2 = [b2.admit(p) for p in params]
+        h2d = 0
+        for p in params:
+            h2d += sum(p[k].nbytes for k in ("xs_ev", "xs_el", "xs_exc", "xs_ion", "tab_eon_td", "tab_mu", "tab_nu"))
+            h2d += 8 * (p["n_cells"] + 1)
+        d2h = 0
+        for _ in range(args.steps):
+            b2.advance(CHUNK)
+            for s in s2:
+                m = b2.moments(s)
+                d2h += sum(m[k].nbytes for k in ("ne", "ni", "gamma", "ebar", "eedf"))
+        n2 = sum(b2.counters(s)["pushes"] for s in s2)
+        for s in s2:
+            b2.evict(s)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter() - t0
+        b2.close()
+        e2e = {"value": n2 / t2, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d // args.steps,
+               "d2h_bytes_per_step": d2h // args.steps,
+               "note": "admission from host parameters and tables (pageable), per-chunk host read of all "
+                       "moments, eviction, all inside the wall-clock region"}
+
+    fp64 = None
+    if rank == 0 and not args.no_fp64:
+        fp64 = run_fp64_plain(params)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(params, budget_s=args.cpu_budget)
+
+    total_particles = sum(p["n_particles"] for p in params)
+    lat_sorted = sorted(lat)
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 particles / f64 grids", "data": "synthetic",
+        "config": {"workload": f"{args.instances} batched He discharges (gap 0.3-2 mm, 150-2000 cells, "
+                               f"1e4-2e6 electrons log-uniform, 100-400 V, DD/full ions), FP32 split, "
+                               f"{CHUNK}-step CUDA-graph chunks", "instances": args.instances,
+                   "initial_particles_per_gpu": total_particles, "chunk_steps": CHUNK,
+                   "l2": "256 MB buffer written between timed chunks; particle store > L2"},
+        "p50_ms_per_chunk": lat_sorted[len(lat) // 2], "p99_ms_per_chunk": lat_sorted[min(len(lat) - 1,
+                                                                                           int(0.99 * len(lat)))],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind,
+                     "traffic": (tpp * per_launch if tpp is not None else None),
+                     "kernel": "k_electron<FP32_SPLIT>", "bytes_per_unit": BYTES_SPLIT,
+                     "units_per_launch": per_launch, "avg_launch_ms": avg_ms},
+        "kernel_ms": shares,
+        "gpu_launches": prof["kernel_launches"] - prof0["kernel_launches"],
+        "clocks": clk,
+    }
+    if fp64:
+        line["fp64_plain"] = fp64
+        line["speedup_vs_fp64_plain"] = value / world / fp64["value"]
+    if e2e:
+        line["e2e"] = e2e
+    if cpu:
+        line["cpu_baseline"] = cpu
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        import oracle
+        oracle.build()
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -130,6 +130,7 @@ typedef struct hyb_counters {
     int64_t losses[2];          /* absorbed at z = 0 and z = L */
     int64_t collisions[4];      /* elastic, excitation, ionization, null (candidates without a real collision) */
     int64_t clamps;             /* ion densities clamped at zero */
+    int64_t pushes;             /* particle pushes done (particle-steps) */
     uint32_t status;            /* bit set of HYB_STATUS_* below */
 } hyb_counters;
 
@@ -226,6 +227,30 @@ int hyb_batch_evict(hyb_batch *b, int32_t slot);
 int hyb_batch_stats(hyb_batch *b, int32_t *running, int64_t *particles, int64_t *bytes);
 
 int hyb_batch_destroy(hyb_batch *b);
+
+/* Launch accounting and per-kernel device time.  With profiling on, every
+ * kernel of a step (also inside the captured graphs) is bracketed by CUDA
+ * events on the batch's stream and hyb_batch_advance waits for each chunk to
+ * read them; times are summed until read. */
+typedef struct hyb_profile {
+    int64_t kernel_launches;    /* kernels enqueued since creation */
+    int64_t steps;              /* lockstep steps enqueued */
+    double ms_electron, ms_field, ms_sort; /* summed device time of the timed launches */
+    int64_t n_electron, n_field, n_sort;   /* timed launches */
+} hyb_profile;
+
+int hyb_batch_set_profiling(hyb_batch *b, int32_t on);
+int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset);
+
+/* The batch behind a single discharge (for profiling and statistics). */
+hyb_batch *hyb_discharge_batch(hyb_discharge *h);
+
+/* First failed device self-check since load: out[0] = site (0: none),
+ * out[1] = index, out[2] = bound.  Only the checked build (compiled with
+ * HYB_CHECKS) tests indices; the normal build reports zeros.  Covers the
+ * electron, sort and load kernels (out[0..2]) and the field kernel
+ * (out[3..5]). */
+int hyb_debug_checks(uint64_t out[6]);
 
 /* Thread-local message of the last error. */
 const char *hyb_last_error(void);

@@ -40,7 +40,7 @@ int fail(int code, const char *fmt, ...)
         if (e_ != cudaSuccess) return fail(HYB_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
     } while (0)
 
-constexpr int kDefaultSort = 16;
+constexpr int kDefaultSort = 20;
 constexpr int kElectronBlock = 256;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -332,6 +332,13 @@ struct hyb_batch {
     cudaGraphExec_t graph = nullptr;
     int num_sms = 0;
     InstDev *h_stage = nullptr;  // pinned, max_inst entries
+    // launch accounting and optional per-kernel timing
+    int64_t launches = 0, steps = 0;
+    bool profiling = false;
+    bool pending = false;         // events of the last graph launch not read yet
+    std::vector<cudaEvent_t> ev;  // 3 per step + 2 per sort of a chunk
+    double ms[3] = {0, 0, 0};
+    int64_t nt[3] = {0, 0, 0};
 };
 
 struct hyb_discharge {
@@ -340,6 +347,12 @@ struct hyb_discharge {
 };
 
 namespace {
+
+int64_t live_count(const InstDev &K)
+{
+    return K.n_base + (int64_t)(K.ctr[C_BIRTH_IZ] + K.ctr[C_SEE0] + K.ctr[C_SEE1]) -
+           (int64_t)(K.ctr[C_LOSS0] + K.ctr[C_LOSS1]);
+}
 
 int fetch_inst(hyb_batch *b, int slot)
 {
@@ -378,27 +391,111 @@ int configure(hyb_batch *b, int nodes, int bins)
     return drop_graph(b);
 }
 
-int launch_step(hyb_batch *b)
+constexpr int kSortKernels = 5;
+constexpr int kChunkTarget = 100;  // steps per captured graph (a multiple of the sort interval)
+
+int chunk_len(const hyb_batch *b)
 {
+    const int k = b->sort_interval;
+    const int m = kChunkTarget / k > 0 ? kChunkTarget / k : 1;
+    return k * m;
+}
+
+int ensure_events(hyb_batch *b)
+{
+    const int GL = chunk_len(b);
+    const size_t need = 3 * (size_t)GL + 2 * (size_t)(GL / b->sort_interval);
+    while (b->ev.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        b->ev.push_back(e);
+    }
+    return HYB_OK;
+}
+
+// Timing event on the batch stream; inside a stream capture it must become an
+// event-record node of the graph (cudaEventRecordExternal).
+int record(hyb_batch *b, cudaEvent_t e)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(b->stream, &st));
+    if (st == cudaStreamCaptureStatusActive)
+        CK(cudaEventRecordWithFlags(e, b->stream, cudaEventRecordExternal));
+    else
+        CK(cudaEventRecord(e, b->stream));
+    return HYB_OK;
+}
+
+// One step; with profiling, events 3k..3k+2 bracket the two kernels.
+int launch_step(hyb_batch *b, int k)
+{
+    int rc;
+    if (b->profiling && (rc = record(b, b->ev[3 * k]))) return rc;
     CK(launch_electron_step(b->d_inst, b->max_inst, b->d_prefix, b->precision, b->cfg, b->stream));
+    if (b->profiling && (rc = record(b, b->ev[3 * k + 1]))) return rc;
     CK(launch_field(b->d_inst, b->max_inst, b->d_prefix, b->d_ticket, b->stream));
+    if (b->profiling && (rc = record(b, b->ev[3 * k + 2]))) return rc;
     return HYB_OK;
 }
 
-int launch_sort_all(hyb_batch *b)
+// The cell sort; with profiling, sort j of a chunk is bracketed by two events.
+int launch_sort_all(hyb_batch *b, int j)
 {
+    int rc;
+    const size_t s0 = 3 * (size_t)chunk_len(b) + 2 * (size_t)j;
+    if (b->profiling && (rc = record(b, b->ev[s0]))) return rc;
     CK(launch_sort(b->d_inst, b->max_inst, b->d_prefix, b->precision, b->cfg, b->stream));
+    if (b->profiling && (rc = record(b, b->ev[s0 + 1]))) return rc;
     return HYB_OK;
 }
 
-// Graph of one sort interval: K steps then the cell sort.
+// Sum the device times of `steps` profiled steps and `sorts` sorts.
+int collect_times(hyb_batch *b, int steps, int sorts)
+{
+    CK(cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < steps; ++k) {
+        float t0 = 0.f, t1 = 0.f;
+        CK(cudaEventElapsedTime(&t0, b->ev[3 * k], b->ev[3 * k + 1]));
+        CK(cudaEventElapsedTime(&t1, b->ev[3 * k + 1], b->ev[3 * k + 2]));
+        b->ms[0] += t0;
+        b->ms[1] += t1;
+        b->nt[0] += 1;
+        b->nt[1] += 1;
+    }
+    const size_t s0 = 3 * (size_t)chunk_len(b);
+    for (int j = 0; j < sorts; ++j) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, b->ev[s0 + 2 * j], b->ev[s0 + 2 * j + 1]));
+        b->ms[2] += t;
+        b->nt[2] += 1;
+    }
+    return HYB_OK;
+}
+
+int flush_pending(hyb_batch *b)
+{
+    if (!b->pending) return HYB_OK;
+    b->pending = false;
+    const int GL = chunk_len(b);
+    return collect_times(b, GL, GL / b->sort_interval);
+}
+
+// Graph of one chunk: sort_interval-long runs of steps, each followed by the
+// cell sort.
 int build_graph(hyb_batch *b)
 {
+    if (b->profiling) {
+        int rc0 = ensure_events(b);
+        if (rc0) return rc0;
+    }
+    const int GL = chunk_len(b);
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     int rc = HYB_OK;
-    for (int k = 0; k < b->sort_interval && rc == HYB_OK; ++k) rc = launch_step(b);
-    if (rc == HYB_OK) rc = launch_sort_all(b);
+    for (int k = 0; k < GL && rc == HYB_OK; ++k) {
+        rc = launch_step(b, k);
+        if (rc == HYB_OK && (k + 1) % b->sort_interval == 0) rc = launch_sort_all(b, (k + 1) / b->sort_interval - 1);
+    }
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     if (rc != HYB_OK) {
         if (g) cudaGraphDestroy(g);
@@ -434,6 +531,10 @@ int set_mutable(hyb_batch *b, int slot, int64_t n_slots, int init_pending)
     int rc = fetch_inst(b, slot);
     if (rc) return rc;
     InstDev h = b->h_stage[slot];
+    if (init_pending == 1 && (int64_t)h.n_slots != n_slots) {
+        // a new particle set: keep live = n_base + births - losses equal to it
+        h.n_base = n_slots - (live_count(h) - h.n_base);
+    }
     h.n_slots = (unsigned long long)n_slots;
     h.n_slots_step = n_slots;
     h.init_pending = init_pending;
@@ -487,6 +588,7 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     S.h.target_step = n_steps > 0 ? n_steps : 0;
     S.h.n_slots = (unsigned long long)p->n_particles;
     S.h.n_slots_step = p->n_particles;
+    S.h.n_base = p->n_particles;
     S.h.init_pending = 1;
     if (p->n_particles > S.h.capacity) return fail(HYB_ERR_CAPACITY, "n_particles exceeds capacity");
     CK(cudaMemcpyAsync(&b->d_inst[slot], &S.h, sizeof(InstDev), cudaMemcpyHostToDevice, b->stream));
@@ -518,23 +620,41 @@ int advance(hyb_batch *b, int64_t n)
 {
     if (n < 0) return fail(HYB_ERR_ARG, "negative step count");
     int rc;
+    if (b->profiling) {
+        rc = ensure_events(b);
+        if (rc) return rc;
+    }
+    const int GL = chunk_len(b);
     while (n > 0) {
-        if (b->since_sort == 0 && n >= b->sort_interval) {
+        rc = flush_pending(b);
+        if (rc) return rc;
+        if (b->since_sort == 0 && n >= GL) {
             if (!b->graph) {
                 rc = build_graph(b);
                 if (rc) return rc;
             }
             CK(cudaGraphLaunch(b->graph, b->stream));
-            n -= b->sort_interval;
+            b->launches += 2 * (int64_t)GL + kSortKernels * (int64_t)(GL / b->sort_interval);
+            b->steps += GL;
+            n -= GL;
+            b->pending = b->profiling;
             continue;
         }
-        rc = launch_step(b);
+        rc = launch_step(b, 0);
         if (rc) return rc;
+        b->launches += 2;
+        b->steps += 1;
         --n;
-        if (++b->since_sort == b->sort_interval) {
-            rc = launch_sort_all(b);
+        const bool sort_now = ++b->since_sort == b->sort_interval;
+        if (sort_now) {
+            rc = launch_sort_all(b, 0);
             if (rc) return rc;
+            b->launches += kSortKernels;
             b->since_sort = 0;
+        }
+        if (b->profiling) {
+            rc = collect_times(b, 1, sort_now ? 1 : 0);
+            if (rc) return rc;
         }
     }
     return HYB_OK;
@@ -605,23 +725,9 @@ int read_counters(hyb_batch *b, int slot, hyb_counters *c)
     c->collisions[2] = (int64_t)K.ctr[C_IZ];
     c->collisions[3] = (int64_t)K.ctr[C_NULL];
     c->clamps = (int64_t)K.ctr[C_CLAMP];
+    c->pushes = (int64_t)K.ctr[C_PUSH];
     c->status = K.status;
-    // live particles: slots minus removed ones
-    const int64_t ns = (int64_t)K.n_slots;
-    const PartBuf P = K.buf[K.cur];
-    int64_t live = 0;
-    if (ns > 0) {
-        if (K.precision == HYB_FP32_SPLIT) {
-            std::vector<int32_t> cc(ns);
-            CK(cudaMemcpy(cc.data(), P.c, 4 * (size_t)ns, cudaMemcpyDeviceToHost));
-            for (int32_t x : cc) live += x >= 0;
-        } else {
-            std::vector<double> zz(ns);
-            CK(cudaMemcpy(zz.data(), P.z, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
-            for (double x : zz) live += x >= 0.0;
-        }
-    }
-    c->particles = live;
+    c->particles = live_count(K);
     return rc;
 }
 
@@ -833,6 +939,7 @@ int hyb_batch_destroy(hyb_batch *b)
         if (b->slots[i].used) cudaFreeAsync(b->slots[i].mem, b->stream);
     cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     cudaFree(b->d_inst);
     cudaFree(b->d_prefix);
     cudaFree(b->d_prefix1);
@@ -840,6 +947,56 @@ int hyb_batch_destroy(hyb_batch *b)
     cudaFreeHost(b->h_stage);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
+    return HYB_OK;
+}
+
+int hyb_batch_set_profiling(hyb_batch *b, int32_t on)
+{
+    if (!b) return fail(HYB_ERR_ARG, "NULL batch");
+    if ((on != 0) != b->profiling) {
+        int rc = flush_pending(b);
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(b->stream));
+        rc = drop_graph(b);
+        if (rc) return rc;
+        b->profiling = on != 0;
+    }
+    return HYB_OK;
+}
+
+int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset)
+{
+    if (!b || !out) return fail(HYB_ERR_ARG, "NULL argument");
+    int rc = flush_pending(b);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(b->stream));
+    out->kernel_launches = b->launches;
+    out->steps = b->steps;
+    out->ms_electron = b->ms[0];
+    out->ms_field = b->ms[1];
+    out->ms_sort = b->ms[2];
+    out->n_electron = b->nt[0];
+    out->n_field = b->nt[1];
+    out->n_sort = b->nt[2];
+    if (reset) {
+        b->ms[0] = b->ms[1] = b->ms[2] = 0.0;
+        b->nt[0] = b->nt[1] = b->nt[2] = 0;
+    }
+    return HYB_OK;
+}
+
+hyb_batch *hyb_discharge_batch(hyb_discharge *h) { return h ? h->b : nullptr; }
+
+int hyb_debug_checks(uint64_t out[6])
+{
+    if (!out) return fail(HYB_ERR_ARG, "NULL output");
+    unsigned long long e[3], f[3];
+    read_checks_electron(e);
+    read_checks_field(f);
+    for (int k = 0; k < 3; ++k) {
+        out[k] = e[k];
+        out[3 + k] = f[k];
+    }
     return HYB_OK;
 }
 
@@ -854,7 +1011,7 @@ int hyb_create_discharge(const hyb_params *p, void *stream, hyb_discharge **out)
     hyb_batch *b = nullptr;
     rc = hyb_batch_create(1, p->precision, 0, stream, &b);
     if (rc) return rc;
-    if (p->sort_interval > 0) b->sort_interval = p->sort_interval;
+    if (p->sort_interval > 0) b->sort_interval = p->sort_interval > 1000 ? 1000 : p->sort_interval;
     int slot = -1;
     rc = admit(b, p, 0, &slot);
     if (rc < 0) {

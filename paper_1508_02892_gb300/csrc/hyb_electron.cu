@@ -54,8 +54,9 @@ struct WarpSum<double> {
 // Add (w0 at node c, w1 at node c+1) for every lane that has `on`; when every
 // participating lane has the same c, sum over the warp first.
 template <typename T>
-__device__ __forceinline__ void deposit_pair(T *arr, bool on, int c, T w0, T w1)
+__device__ __forceinline__ void deposit_pair(T *arr, bool on, int c, T w0, T w1, int G)
 {
+    if (on && !HYB_CHECK(c >= 0 && c + 1 < G, 4, c, G)) on = false;
     const int kmin = __reduce_min_sync(kFull, on ? c : INT32_MAX);
     const int kmax = __reduce_max_sync(kFull, on ? c : -1);
     if (kmin == kmax) {
@@ -72,7 +73,7 @@ __device__ __forceinline__ void deposit_pair(T *arr, bool on, int c, T w0, T w1)
 }
 
 struct SegCounters {
-    unsigned el = 0, exc = 0, iz = 0, nul = 0, loss0 = 0, loss1 = 0, overflow = 0;
+    unsigned el = 0, exc = 0, iz = 0, nul = 0, loss0 = 0, loss1 = 0, overflow = 0, push = 0;
     int cmin = INT32_MAX, cmax = -1;
 };
 
@@ -160,6 +161,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     float *sd_e = sd_n + G;
     float *sd_iz = sd_e + G;
     unsigned *s_eedf = reinterpret_cast<unsigned *>(sd_iz + G);
+    if (!HYB_CHECK(b <= capacity && a >= 0, 10, b, capacity)) b = a;
     for (int j = threadIdx.x; j < 3 * G; j += blockDim.x) sd_n[j] = 0.f;
     for (int j = threadIdx.x; j <= nb; j += blockDim.x) s_eedf[j] = 0u;
     __syncthreads();
@@ -178,6 +180,8 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             if (MODE == 0) id = P.id[i];
         }
         if (MODE == 0 && alive) {
+            ++cnt.push;
+            if (!HYB_CHECK(c + 1 < G, 2, c, G)) c = 0;
             // leapfrog with the CIC-gathered field (Sec. II.A)
             const float ep = (1.f - o) * __ldg(&Ef[c]) + o * __ldg(&Ef[c + 1]);
             vz = vz - qm_dt * ep;
@@ -200,13 +204,13 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
         }
         // CIC charge assignment, energy moment and EEDF sample
         const float en = half_m_q * (vx * vx + vy * vy + vz * vz);
-        deposit_pair<float>(sd_n, alive, c, 1.f - o, o);
+        deposit_pair<float>(sd_n, alive, c, 1.f - o, o, G);
         if (MODE == 0) {
-            deposit_pair<float>(sd_e, alive, c, (1.f - o) * en, o * en);
+            deposit_pair<float>(sd_e, alive, c, (1.f - o) * en, o * en, G);
             if (alive) {
                 int bin = (int)(en * bin_inv);
-                bin = bin > nb ? nb : bin;
-                atomicAdd(&s_eedf[bin], 1u);
+                if (bin > nb || bin < 0 || !(en >= 0.f)) bin = nb;  // overflow bin (also NaN)
+                if (HYB_CHECK(bin >= 0 && bin <= nb, 5, bin, nb)) atomicAdd(&s_eedf[bin], 1u);
                 cnt.cmin = min(cnt.cmin, c);
                 cnt.cmax = max(cnt.cmax, c);
             }
@@ -234,6 +238,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 } else {
                     int k = (int)(__logf(en * inv_e_lo) * inv_dlog);
                     k = k < 0 ? 0 : (k > nxs - 2 ? nxs - 2 : k);
+                    if (!HYB_CHECK(k >= 0 && k + 1 < nxs, 3, k, nxs)) k = 0;
                     lo = __ldg(&xs[k]);
                     hi = __ldg(&xs[k + 1]);
                     f = __fdividef(en - lo.x, hi.x - lo.x);
@@ -369,6 +374,7 @@ __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *sm
     double *sd_e = sd_n + G;
     double *sd_iz = sd_e + G;
     unsigned *s_eedf = reinterpret_cast<unsigned *>(sd_iz + G);
+    if (!HYB_CHECK(b <= capacity && a >= 0, 10, b, capacity)) b = a;
     for (int j = threadIdx.x; j < 3 * G; j += blockDim.x) sd_n[j] = 0.0;
     for (int j = threadIdx.x; j <= nb; j += blockDim.x) s_eedf[j] = 0u;
     __syncthreads();
@@ -388,6 +394,7 @@ __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *sm
         int c = 0;
         double o = 0.0;
         if (MODE == 0 && alive) {
+            ++cnt.push;
             locate_d(z, dz, nc, c, o);
             const double ep = (1.0 - o) * E[c] + o * E[c + 1];
             vz = vz - qm * ep * dt;
@@ -403,12 +410,12 @@ __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *sm
         }
         if (alive) locate_d(z, dz, nc, c, o);
         const double en = 0.5 * kMe * (vx * vx + vy * vy + vz * vz) / kQe;
-        deposit_pair<double>(sd_n, alive, c, 1.0 - o, o);
+        deposit_pair<double>(sd_n, alive, c, 1.0 - o, o, G);
         if (MODE == 0) {
-            deposit_pair<double>(sd_e, alive, c, (1.0 - o) * en, o * en);
+            deposit_pair<double>(sd_e, alive, c, (1.0 - o) * en, o * en, G);
             if (alive) {
                 int bin = (int)(en / bin_w);
-                if (bin > nb || bin < 0) bin = nb;
+                if (bin > nb || bin < 0 || !(en >= 0.0)) bin = nb;  // overflow bin (also NaN)
                 atomicAdd(&s_eedf[bin], 1u);
             }
         }
@@ -495,15 +502,15 @@ __device__ void flush_segment(InstDev *K, unsigned char *smem, SegCounters &cnt)
         s_cmax = -1;
     }
     __syncthreads();
-    const unsigned v[7] = {cnt.el, cnt.exc, cnt.iz, cnt.nul, cnt.loss0, cnt.loss1, cnt.overflow};
+    const unsigned v[8] = {cnt.el, cnt.exc, cnt.iz, cnt.nul, cnt.loss0, cnt.loss1, cnt.overflow, cnt.push};
     const int mn = __reduce_min_sync(kFull, cnt.cmin);
     const int mx = __reduce_max_sync(kFull, cnt.cmax);
-    unsigned tot[7];
+    unsigned tot[8];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) tot[k] = __reduce_add_sync(kFull, v[k]);
+    for (int k = 0; k < 8; ++k) tot[k] = __reduce_add_sync(kFull, v[k]);
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-        for (int k = 0; k < 7; ++k)
+        for (int k = 0; k < 8; ++k)
             if (tot[k]) atomicAdd(&s_ctr[k], tot[k]);
         atomicMin(&s_cmin, mn);
         atomicMax(&s_cmax, mx);
@@ -515,7 +522,8 @@ __device__ void flush_segment(InstDev *K, unsigned char *smem, SegCounters &cnt)
     T *sd_e = sd_n + G;
     T *sd_iz = sd_e + G;
     unsigned *s_eedf = reinterpret_cast<unsigned *>(sd_iz + G);
-    const int jlo = s_cmin, jhi = s_cmax < 0 ? -1 : min(s_cmax + 1, G - 1);
+    int jlo = s_cmin, jhi = s_cmax < 0 ? -1 : min(s_cmax + 1, G - 1);
+    if (jhi >= 0 && !HYB_CHECK(jlo >= 0 && jlo <= jhi, 6, jlo, jhi)) jhi = -1;
     for (int j = (jhi < 0 ? 0 : jlo) + (int)threadIdx.x; j <= jhi; j += blockDim.x) {
         const T a = sd_n[j];
         if (a != T(0)) atomicAdd(&K->dep_n[j], (double)a);
@@ -536,6 +544,7 @@ __device__ void flush_segment(InstDev *K, unsigned char *smem, SegCounters &cnt)
                 if (s_ctr[k]) atomicAdd(&K->ctr[map[k]], (unsigned long long)s_ctr[k]);
             if (s_ctr[2]) atomicAdd(&K->ctr[C_BIRTH_IZ], (unsigned long long)s_ctr[2]);
             if (s_ctr[6]) atomicOr(&K->status, (unsigned)HYB_STATUS_CAPACITY);
+            if (s_ctr[7]) atomicAdd(&K->ctr[C_PUSH], (unsigned long long)s_ctr[7]);
         }
     }
     __syncthreads();
@@ -587,6 +596,7 @@ __global__ void k_load(InstDev *K, int64_t n, double vth, int prec)
     const PartBuf P = K->buf[K->cur];
     const double L = K->L, dz = K->dz;
     const int nc = K->n_cells;
+    if (!HYB_CHECK(n <= K->capacity, 9, n, K->capacity)) return;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t id = (uint64_t)j;
         const uint4 a = draw(id, 0xFFFFFFFFu, K->seed_lo, K->seed_hi, 0);
@@ -662,6 +672,7 @@ __global__ void __launch_bounds__(kBlock) k_sort_pass(InstDev *__restrict__ inst
         const int64_t b = (ghi < p1 ? ghi : p1) - p0;
         InstDev *K = &insts[inst];
         const PartBuf S = K->buf[K->cur];
+        if (!HYB_CHECK(b <= K->capacity, 11, b, K->capacity)) continue;
         const PartBuf D = K->buf[K->cur ^ 1];
         int32_t *cnt = K->cell_cnt;
         const double dz = K->dz;
@@ -669,7 +680,8 @@ __global__ void __launch_bounds__(kBlock) k_sort_pass(InstDev *__restrict__ inst
         for (int64_t base = a; base < b; base += blockDim.x) {
             const int64_t i = base + threadIdx.x;
             int c = -1;
-            const bool alive = i < b && cell_of<PREC>(S, i, dz, nc, c);
+            bool alive = i < b && cell_of<PREC>(S, i, dz, nc, c);
+            if (alive && !HYB_CHECK(c < nc, 7, c, nc)) alive = false;
             const unsigned act = __ballot_sync(kFull, alive);
             if (!alive) continue;
             const unsigned peers = __match_any_sync(act, c);
@@ -678,6 +690,7 @@ __global__ void __launch_bounds__(kBlock) k_sort_pass(InstDev *__restrict__ inst
             if (lane == leader) pos = atomicAdd(&cnt[c], __popc(peers));
             if (PHASE == 1) {
                 pos = __shfl_sync(peers, pos, leader) + __popc(peers & lanemask_lt());
+                if (!HYB_CHECK(pos >= 0 && pos < K->capacity, 8, pos, K->capacity)) continue;
                 D.id[pos] = S.id[i];
                 if (PREC == HYB_FP32_SPLIT) {
                     D.c[pos] = c;
@@ -790,6 +803,15 @@ cudaError_t launch_k(InstDev *inst, int n_max, const int64_t *prefix, LaunchCfg 
 }
 
 }  // namespace
+
+void read_checks_electron(unsigned long long out[3])
+{
+#ifdef HYB_CHECKS
+    cudaMemcpyFromSymbol(out, g_hyb_check, sizeof(unsigned long long) * 3);
+#else
+    out[0] = out[1] = out[2] = 0ull;
+#endif
+}
 
 void configure_kernels()
 {

@@ -420,7 +420,8 @@ __global__ void __launch_bounds__(kFieldThreads) k_field(InstDev *insts, int n_m
     extern __shared__ __align__(16) double sm[];
     __shared__ Red red;
     InstDev *K = &insts[blockIdx.x];
-    if (K->active || K->init_pending) field_body(K, sm, red);
+    const bool fits = HYB_CHECK(K->G >= 3 && K->G <= kMaxNodes, 20, K->G, kMaxNodes);
+    if ((K->active || K->init_pending) && fits) field_body(K, sm, red);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -442,6 +443,15 @@ __global__ void __launch_bounds__(kFieldThreads) k_field(InstDev *insts, int n_m
 }  // namespace
 
 size_t field_smem_bytes(int max_nodes) { return (size_t)kArrays * 8 * (size_t)max_nodes; }
+
+void read_checks_field(unsigned long long out[3])
+{
+#ifdef HYB_CHECKS
+    cudaMemcpyFromSymbol(out, g_hyb_check, sizeof(unsigned long long) * 3);
+#else
+    out[0] = out[1] = out[2] = 0ull;
+#endif
+}
 
 void configure_field_kernel()
 {

@@ -63,12 +63,32 @@ struct InstDev {
     int64_t n_slots_step;             // slots processed by the current step
     int64_t n_samples;
     double flux_in[2];
-    unsigned long long ctr[10];       // births_iz, see0, see1, loss0, loss1, el, exc, iz, null, clamps
+    unsigned long long ctr[11];       // births_iz, see0, see1, loss0, loss1, el, exc, iz, null, clamps, pushes
+    int64_t n_base;                   // live count = n_base + births - losses
     unsigned int status;
     int32_t init_pending;             // field kernel runs in initial-solve mode
 };
 
-enum { C_BIRTH_IZ = 0, C_SEE0, C_SEE1, C_LOSS0, C_LOSS1, C_EL, C_EXC, C_IZ, C_NULL, C_CLAMP };
+enum { C_BIRTH_IZ = 0, C_SEE0, C_SEE1, C_LOSS0, C_LOSS1, C_EL, C_EXC, C_IZ, C_NULL, C_CLAMP, C_PUSH };
+
+// ------------------------------------------------------------ self-checks
+// In the checked build (-DHYB_CHECKS) every guarded index is tested; the first
+// failure in each translation unit is recorded (site, index, bound) and the
+// access is skipped.  In the normal build the guards compile away.
+#ifdef HYB_CHECKS
+static __device__ unsigned long long g_hyb_check[3];
+__device__ __noinline__ static bool hyb_check_fail(int site, long long a, long long b)
+{
+    if (atomicCAS(&g_hyb_check[0], 0ull, (unsigned long long)site) == 0ull) {
+        g_hyb_check[1] = (unsigned long long)a;
+        g_hyb_check[2] = (unsigned long long)b;
+    }
+    return false;
+}
+#define HYB_CHECK(cond, site, a, b) ((cond) ? true : hyb_check_fail((site), (long long)(a), (long long)(b)))
+#else
+#define HYB_CHECK(cond, site, a, b) true
+#endif
 
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter (step, seed_lo,
@@ -141,6 +161,10 @@ size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins);
 cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned int *ticket, cudaStream_t s);
 size_t field_smem_bytes(int max_nodes);
 void configure_field_kernel();
+
+// first failed self-check of each translation unit (zeros in the normal build)
+void read_checks_electron(unsigned long long out[3]);
+void read_checks_field(unsigned long long out[3]);
 
 // one-time kernel attributes and occupancy (hyb_electron.cu)
 void configure_kernels();

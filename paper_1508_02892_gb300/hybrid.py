@@ -12,7 +12,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libhybrid1d.so")
+# HYB_CHECKED=1 selects the self-checking build (device index guards)
+LIB_PATH = os.path.join(HERE, "_build", "checked" if os.environ.get("HYB_CHECKED") == "1" else "",
+                        "libhybrid1d.so")
 
 HYB_OK, HYB_WARN_DT_NULLCOLL = 0, 1
 ERRORS = {-1: "HYB_ERR_ARG", -2: "HYB_ERR_OOM", -3: "HYB_ERR_CAPACITY", -4: "HYB_ERR_NONFINITE",
@@ -58,13 +60,19 @@ class Fields(C.Structure):
 class Counters(C.Structure):
     _fields_ = [("step", C.c_int64), ("particles", C.c_int64), ("births_ionization", C.c_int64),
                 ("births_see", C.c_int64 * 2), ("losses", C.c_int64 * 2), ("collisions", C.c_int64 * 4),
-                ("clamps", C.c_int64), ("status", C.c_uint32)]
+                ("clamps", C.c_int64), ("pushes", C.c_int64), ("status", C.c_uint32)]
 
 
 class Info(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("eedf_bins", C.c_int32), ("weight", C.c_double),
                 ("gas_density", C.c_double), ("nu_max", C.c_double), ("p_max", C.c_double), ("dz", C.c_double),
                 ("capacity", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("steps", C.c_int64), ("ms_electron", C.c_double),
+                ("ms_field", C.c_double), ("ms_sort", C.c_double), ("n_electron", C.c_int64),
+                ("n_field", C.c_int64), ("n_sort", C.c_int64)]
 
 
 _lib = None
@@ -95,8 +103,26 @@ EXPORTS = {
     "hyb_batch_evict": (C.c_int, [C.c_void_p, C.c_int32]),
     "hyb_batch_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "hyb_batch_destroy": (C.c_int, [C.c_void_p]),
+    "hyb_batch_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
+    "hyb_batch_profile": (C.c_int, [C.c_void_p, C.POINTER(Profile), C.c_int32]),
+    "hyb_discharge_batch": (C.c_void_p, [C.c_void_p]),
+    "hyb_debug_checks": (C.c_int, [C.POINTER(C.c_uint64)]),
     "hyb_last_error": (C.c_char_p, []),
 }
+
+
+def debug_checks():
+    """First failed device self-check (checked build): (site, index, bound) for
+    the particle kernels and for the field kernel; zeros when none failed."""
+    out = (C.c_uint64 * 6)()
+    _check(lib().hyb_debug_checks(out))
+    return tuple(out[:3]), tuple(out[3:])
+
+
+def _profile(bh, reset):
+    p = Profile()
+    _check(lib().hyb_batch_profile(bh, C.byref(p), int(reset)))
+    return {f: getattr(p, f) for f, _ in Profile._fields_}
 
 
 def lib():
@@ -171,7 +197,8 @@ def _counters(call):
     return {"step": c.step, "particles": c.particles, "births_iz": c.births_ionization,
             "births_see0": c.births_see[0], "births_see1": c.births_see[1], "losses0": c.losses[0],
             "losses1": c.losses[1], "elastic": c.collisions[0], "excitation": c.collisions[1],
-            "ionization": c.collisions[2], "null": c.collisions[3], "clamps": c.clamps, "status": c.status}
+            "ionization": c.collisions[2], "null": c.collisions[3], "clamps": c.clamps, "pushes": c.pushes,
+            "status": c.status}
 
 
 def _particles(call, cap):
@@ -247,6 +274,12 @@ class Discharge:
                                          vy.ctypes.data_as(_pd), vz.ctypes.data_as(_pd),
                                          ids.ctypes.data_as(C.POINTER(C.c_uint64))))
 
+    def set_profiling(self, on=True):
+        _check(lib().hyb_batch_set_profiling(lib().hyb_discharge_batch(self.h), int(bool(on))))
+
+    def profile(self, reset=False):
+        return _profile(lib().hyb_discharge_batch(self.h), reset)
+
     def set_ion_density(self, ni):
         ni = _arr(ni)
         _check(lib().hyb_write_ion_density(self.h, ni.ctypes.data_as(_pd)))
@@ -288,7 +321,8 @@ class Batch:
         rc = lib().hyb_batch_admit(self.h, C.byref(p), int(n_steps), C.byref(slot))
         _check(rc)
         bins = int(params.get("eedf_bins", 0) or 256)
-        self._shape[slot.value] = (int(params["n_cells"]) + 1, bins, int(2 * params["n_particles"]) + 4096)
+        cap = max(4096, int(np.ceil((params.get("capacity_factor") or 2.0) * params["n_particles"])))
+        self._shape[slot.value] = (int(params["n_cells"]) + 1, bins, cap)
         return slot.value
 
     def advance(self, n):
@@ -314,6 +348,12 @@ class Batch:
     def evict(self, slot):
         _check(lib().hyb_batch_evict(self.h, int(slot)))
         self._shape.pop(slot, None)
+
+    def set_profiling(self, on=True):
+        _check(lib().hyb_batch_set_profiling(self.h, int(bool(on))))
+
+    def profile(self, reset=False):
+        return _profile(self.h, reset)
 
     def stats(self):
         r, n, b = C.c_int32(0), C.c_int64(0), C.c_int64(0)

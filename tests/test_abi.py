@@ -62,7 +62,6 @@ def test_host_validation_rejects_bad_params():
     import numpy as np
 
     from paper_1508_02892_gb300 import hybrid, workloads
-    hybrid.build_ok = True
     p = workloads.config1(n_particles=100)
     p["n_cells"] = 1
     with pytest.raises(hybrid.HybError) as e:
