@@ -212,9 +212,6 @@ def run_ours(args):
 
     import __graft_entry__ as G
     G.build()
-    if os.environ.get("HYB_CHECKED") == "1":
-        from paper_1508_02892_gb300 import build as B
-        B.build(checked=True)
     from paper_1508_02892_gb300 import hybrid, workloads as W
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -352,6 +349,7 @@ def run_ours(args):
         line["e2e"] = e2e
     if cpu:
         line["cpu_baseline"] = cpu
+    line["device_index_guards"] = hybrid.debug_checks()
     b.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

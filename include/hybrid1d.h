@@ -245,11 +245,10 @@ int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset);
 /* The batch behind a single discharge (for profiling and statistics). */
 hyb_batch *hyb_discharge_batch(hyb_discharge *h);
 
-/* First failed device self-check since load: out[0] = site (0: none),
- * out[1] = index, out[2] = bound.  Only the checked build (compiled with
- * HYB_CHECKS) tests indices; the normal build reports zeros.  Covers the
- * electron, sort and load kernels (out[0..2]) and the field kernel
- * (out[3..5]). */
+/* First failed device index guard since load: out[0] = guard site (0:
+ * none), out[1] = index, out[2] = bound, for the electron, sort and load
+ * kernels; out[3..5] the same for the field kernel.  A failed guard skips the
+ * access it protects, so a nonzero site means results are not to be trusted. */
 int hyb_debug_checks(uint64_t out[6]);
 
 /* Thread-local message of the last error. */

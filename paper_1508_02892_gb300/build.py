@@ -39,13 +39,10 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
-    """Build the library; `checked` builds the self-checking variant (device
-    index guards that record the first failure and skip the access) into
-    _build/checked/."""
-    out_dir = os.path.join(BUILD, "checked") if checked else BUILD
-    lib = os.path.join(out_dir, "libhybrid1d.so")
-    extra = ["-DHYB_CHECKS"] if checked else []
+def build(force: bool = False, verbose: bool = False) -> str:
+    out_dir = BUILD
+    lib = LIB
+    extra = []
     os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, "hyb_internal.cuh"), os.path.join(ROOT, "include", "hybrid1d.h")]
     objs = []
@@ -76,4 +73,4 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True))

@@ -73,7 +73,8 @@ int64_t capacity_of(const hyb_params &p)
 {
     const double f = p.capacity_factor > 0 ? p.capacity_factor : 2.0;
     int64_t c = (int64_t)ceil(f * (double)p.n_particles);
-    return c < 4096 ? 4096 : c;
+    c = c < 4096 ? 4096 : c;
+    return (c + 255) & ~(int64_t)255;
 }
 
 bool finite_all(const double *x, int n)

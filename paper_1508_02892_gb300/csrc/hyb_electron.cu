@@ -138,6 +138,55 @@ __device__ __forceinline__ void append_children<double>(InstDev *K, const PartBu
 // ------------------------------------------------------------ FP32 split
 //
 // Position = (cell c, offset o in [0,1)).  Constants are the f_* copies.
+// Each thread takes kVec consecutive particles (16-byte vector loads and
+// stores), pushes, deposits and collides them one after the other, and keeps
+// a run of CIC weights for one cell in registers; the runs of a warp are merged
+// with shuffles when the warp spans one or two cells (the usual case once the
+// particles are sorted by cell), so a shared-memory atomic serves many
+// particles.
+
+constexpr int kVec = 4;
+
+struct Run {
+    int c = -1;
+    float a0 = 0.f, a1 = 0.f, e0 = 0.f, e1 = 0.f;
+};
+
+// Merge the runs of a warp into the block-private arrays.
+__device__ __forceinline__ void flush_runs(float *sd_n, float *sd_e, const Run &r, int G)
+{
+    const bool on = r.c >= 0 && HYB_CHECK(r.c + 1 < G, 4, r.c, G);
+    const int kmin = __reduce_min_sync(kFull, on ? r.c : INT32_MAX);
+    const int kmax = __reduce_max_sync(kFull, on ? r.c : -1);
+    if (kmax < 0) return;
+    if (kmax - kmin <= 1) {
+        // two cells at most: reduce the low and the high run separately
+        const bool lo = on && r.c == kmin, hi = on && r.c == kmax && kmax != kmin;
+        float v[8] = {lo ? r.a0 : 0.f, lo ? r.a1 : 0.f, lo ? r.e0 : 0.f, lo ? r.e1 : 0.f,
+                      hi ? r.a0 : 0.f, hi ? r.a1 : 0.f, hi ? r.e0 : 0.f, hi ? r.e1 : 0.f};
+        const int nv = kmax != kmin ? 8 : 4;
+#pragma unroll
+        for (int d = 16; d; d >>= 1)
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < nv) v[k] += __shfl_xor_sync(kFull, v[k], d);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&sd_n[kmin], v[0]);
+            atomicAdd(&sd_n[kmin + 1], v[1] + v[4]);
+            atomicAdd(&sd_e[kmin], v[2]);
+            atomicAdd(&sd_e[kmin + 1], v[3] + v[6]);
+            if (nv == 8) {
+                atomicAdd(&sd_n[kmax + 1], v[5]);
+                atomicAdd(&sd_e[kmax + 1], v[7]);
+            }
+        }
+    } else if (on) {
+        atomicAdd(&sd_n[r.c], r.a0);
+        atomicAdd(&sd_n[r.c + 1], r.a1);
+        atomicAdd(&sd_e[r.c], r.e0);
+        atomicAdd(&sd_e[r.c + 1], r.e1);
+    }
+}
 
 template <int MODE>
 __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *smem, SegCounters &cnt)
@@ -161,142 +210,200 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     float *sd_e = sd_n + G;
     float *sd_iz = sd_e + G;
     unsigned *s_eedf = reinterpret_cast<unsigned *>(sd_iz + G);
-    if (!HYB_CHECK(b <= capacity && a >= 0, 10, b, capacity)) b = a;
+    if (!HYB_CHECK(b <= capacity && a >= 0 && (a & (kVec - 1)) == 0, 10, b, capacity)) b = a;
     for (int j = threadIdx.x; j < 3 * G; j += blockDim.x) sd_n[j] = 0.f;
     for (int j = threadIdx.x; j <= nb; j += blockDim.x) s_eedf[j] = 0u;
     __syncthreads();
 
-    for (int64_t base = a; base < b; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        int c = i < b ? P.c[i] : kDeadCell;
-        bool alive = c >= 0 && c < nc;
-        float o = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
-        uint64_t id = 0;
-        if (alive) {
-            o = P.o[i];
-            vx = P.vxf[i];
-            vy = P.vyf[i];
-            vz = P.vzf[i];
-            if (MODE == 0) id = P.id[i];
-        }
-        if (MODE == 0 && alive) {
-            ++cnt.push;
-            if (!HYB_CHECK(c + 1 < G, 2, c, G)) c = 0;
-            // leapfrog with the CIC-gathered field (Sec. II.A)
-            const float ep = (1.f - o) * __ldg(&Ef[c]) + o * __ldg(&Ef[c + 1]);
-            vz = vz - qm_dt * ep;
-            o = o + vz * dt_dz;
-            const float fl = floorf(o);
-            c += (int)fl;
-            o -= fl;
-            if (o >= 1.f) {
-                o -= 1.f;
-                c += 1;
+    for (int64_t base = a; base < b; base += (int64_t)blockDim.x * kVec) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * kVec;
+        const bool full = i0 + kVec <= b;
+        int cc[kVec];
+        float oo[kVec], vx[kVec], vy[kVec], vz[kVec];
+        uint64_t ids[kVec];
+        if (full) {
+            const int4 c4 = *reinterpret_cast<const int4 *>(P.c + i0);
+            const float4 o4 = *reinterpret_cast<const float4 *>(P.o + i0);
+            const float4 x4 = *reinterpret_cast<const float4 *>(P.vxf + i0);
+            const float4 y4 = *reinterpret_cast<const float4 *>(P.vyf + i0);
+            const float4 z4 = *reinterpret_cast<const float4 *>(P.vzf + i0);
+            cc[0] = c4.x, cc[1] = c4.y, cc[2] = c4.z, cc[3] = c4.w;
+            oo[0] = o4.x, oo[1] = o4.y, oo[2] = o4.z, oo[3] = o4.w;
+            vx[0] = x4.x, vx[1] = x4.y, vx[2] = x4.z, vx[3] = x4.w;
+            vy[0] = y4.x, vy[1] = y4.y, vy[2] = y4.z, vy[3] = y4.w;
+            vz[0] = z4.x, vz[1] = z4.y, vz[2] = z4.z, vz[3] = z4.w;
+            if (MODE == 0) {
+                const ulonglong2 d0 = *reinterpret_cast<const ulonglong2 *>(P.id + i0);
+                const ulonglong2 d1 = *reinterpret_cast<const ulonglong2 *>(P.id + i0 + 2);
+                ids[0] = d0.x, ids[1] = d0.y, ids[2] = d1.x, ids[3] = d1.y;
             }
-            if (c < 0 || c >= nc) {  // absorbed by an electrode and removed
-                if (c < 0)
-                    ++cnt.loss0;
-                else
-                    ++cnt.loss1;
-                alive = false;
-                P.c[i] = kDeadCell;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kVec; ++k) {
+                const bool in = i0 + k < b;
+                cc[k] = in ? P.c[i0 + k] : kDeadCell;
+                oo[k] = in ? P.o[i0 + k] : 0.f;
+                vx[k] = in ? P.vxf[i0 + k] : 0.f;
+                vy[k] = in ? P.vyf[i0 + k] : 0.f;
+                vz[k] = in ? P.vzf[i0 + k] : 0.f;
+                ids[k] = (MODE == 0 && in) ? P.id[i0 + k] : 0ull;
             }
-        }
-        // CIC charge assignment, energy moment and EEDF sample
-        const float en = half_m_q * (vx * vx + vy * vy + vz * vz);
-        deposit_pair<float>(sd_n, alive, c, 1.f - o, o, G);
-        if (MODE == 0) {
-            deposit_pair<float>(sd_e, alive, c, (1.f - o) * en, o * en, G);
-            if (alive) {
-                int bin = (int)(en * bin_inv);
-                if (bin > nb || bin < 0 || !(en >= 0.f)) bin = nb;  // overflow bin (also NaN)
-                if (HYB_CHECK(bin >= 0 && bin <= nb, 5, bin, nb)) atomicAdd(&s_eedf[bin], 1u);
-                cnt.cmin = min(cnt.cmin, c);
-                cnt.cmax = max(cnt.cmax, c);
-            }
-        } else if (alive) {
-            cnt.cmin = min(cnt.cmin, c);
-            cnt.cmax = max(cnt.cmax, c);
         }
 
-        bool has_child = false;
-        float cvx = 0.f, cvy = 0.f, cvz = 0.f;
-        uint64_t cid = 0;
-        if (MODE == 0 && alive) {
-            // modified null-collision method: every particle draws R1 < P_max
-            const uint4 r = draw(id, step, sl, sh, 0);
-            if (u01f(r.x) < pmax) {
-                const float speed = sqrtf(vx * vx + vy * vy + vz * vz);
-                float4 lo, hi;
-                float f;
-                if (en <= e_lo) {
-                    lo = hi = __ldg(&xs[0]);
-                    f = 0.f;
-                } else if (en >= e_hi) {
-                    lo = hi = __ldg(&xs[nxs - 1]);
-                    f = 0.f;
-                } else {
-                    int k = (int)(__logf(en * inv_e_lo) * inv_dlog);
-                    k = k < 0 ? 0 : (k > nxs - 2 ? nxs - 2 : k);
-                    if (!HYB_CHECK(k >= 0 && k + 1 < nxs, 3, k, nxs)) k = 0;
-                    lo = __ldg(&xs[k]);
-                    hi = __ldg(&xs[k + 1]);
-                    f = __fdividef(en - lo.x, hi.x - lo.x);
+        Run run;
+#pragma unroll
+        for (int k = 0; k < kVec; ++k) {
+            int c = cc[k];
+            float o = oo[k];
+            bool alive = c >= 0 && c < nc;
+            if (MODE == 0 && alive) {
+                ++cnt.push;
+                // leapfrog with the CIC-gathered field (Sec. II.A); the gather
+                // index is clamped so that no out-of-range address is formed
+                const int cg = min(max(c, 0), nc - 1);
+                const float ep = (1.f - o) * __ldg(&Ef[cg]) + o * __ldg(&Ef[cg + 1]);
+                vz[k] = vz[k] - qm_dt * ep;
+                o = o + vz[k] * dt_dz;
+                const float fl = floorf(o);
+                c += (int)fl;
+                o -= fl;
+                if (o >= 1.f) {
+                    o -= 1.f;
+                    c += 1;
                 }
-                const float s_el = lo.y + f * (hi.y - lo.y);
-                const float s_ex = en < e_exc ? 0.f : lo.z + f * (hi.z - lo.z);
-                const float s_iz = en < e_iz ? 0.f : lo.w + f * (hi.w - lo.w);
-                const float t0 = s_el * speed, t1 = t0 + s_ex * speed, t2 = t1 + s_iz * speed;
-                const float r2 = u01f(r.y);
-                if (r2 < t2) {
-                    const float ct = 1.f - 2.f * u01f(r.z);
-                    const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
-                    float sn, cs;
-                    __sincosf(6.283185307179586f * u01f(r.w), &sn, &cs);
-                    const float dx = st * cs, dy = st * sn, dz = ct;
-                    float sp;
-                    if (r2 < t0) {  // elastic, lab-frame isotropic
-                        const float cchi = (vx * dx + vy * dy + vz * dz) / speed;
-                        sp = speed * sqrtf(1.f - two_mM * (1.f - cchi));
-                        ++cnt.el;
-                    } else if (r2 < t1) {  // excitation
-                        sp = sqrtf(two_q_m * (en - e_exc));
-                        ++cnt.exc;
-                    } else {  // ionization: split E - E_iz, eject a new electron
-                        const uint4 r1 = draw(id, step, sl, sh, 1);
-                        const float de = en - e_iz;
-                        const float e_ej = u01f(r1.x) * de;
-                        sp = sqrtf(two_q_m * (de - e_ej));
-                        const float cj = 1.f - 2.f * u01f(r1.y);
-                        const float sj = sqrtf(fmaxf(0.f, 1.f - cj * cj));
-                        float snj, csj;
-                        __sincosf(6.283185307179586f * u01f(r1.z), &snj, &csj);
-                        const float spj = sqrtf(two_q_m * e_ej);
-                        cvx = spj * sj * csj;
-                        cvy = spj * sj * snj;
-                        cvz = spj * cj;
-                        cid = child_id(id, step);
-                        has_child = true;
-                        ++cnt.iz;
-                        atomicAdd(&sd_iz[c], 1.f - o);
-                        atomicAdd(&sd_iz[c + 1], o);
-                    }
-                    vx = sp * dx;
-                    vy = sp * dy;
-                    vz = sp * dz;
-                } else {
-                    ++cnt.nul;
+                if (c < 0 || c >= nc) {  // absorbed by an electrode and removed
+                    if (c < 0)
+                        ++cnt.loss0;
+                    else
+                        ++cnt.loss1;
+                    alive = false;
+                    c = kDeadCell;
                 }
             }
-        }
-        if (MODE == 0) {
-            append_children<float>(K, P, capacity, has_child, c, o, 0.0, cvx, cvy, cvz, cid, cnt.overflow);
+            // CIC charge assignment and energy moment, accumulated in a run
+            const float en = half_m_q * (vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
             if (alive) {
-                P.c[i] = c;
-                P.o[i] = o;
-                P.vxf[i] = vx;
-                P.vyf[i] = vy;
-                P.vzf[i] = vz;
+                const float w0 = 1.f - o, w1 = o;
+                if (run.c < 0 || run.c == c) {
+                    run.c = c;
+                    run.a0 += w0;
+                    run.a1 += w1;
+                    if (MODE == 0) {
+                        run.e0 += w0 * en;
+                        run.e1 += w1 * en;
+                    }
+                } else if (HYB_CHECK(c + 1 < G, 4, c, G)) {
+                    atomicAdd(&sd_n[c], w0);
+                    atomicAdd(&sd_n[c + 1], w1);
+                    if (MODE == 0) {
+                        atomicAdd(&sd_e[c], w0 * en);
+                        atomicAdd(&sd_e[c + 1], w1 * en);
+                    }
+                }
+                cnt.cmin = min(cnt.cmin, c);
+                cnt.cmax = max(cnt.cmax, c);
+                if (MODE == 0) {
+                    int bin = (int)(en * bin_inv);
+                    if (bin > nb || bin < 0 || !(en >= 0.f)) bin = nb;  // overflow bin (also NaN)
+                    if (HYB_CHECK(bin >= 0 && bin <= nb, 5, bin, nb)) atomicAdd(&s_eedf[bin], 1u);
+                }
+            }
+
+            bool has_child = false;
+            float cvx = 0.f, cvy = 0.f, cvz = 0.f;
+            uint64_t cid = 0;
+            if (MODE == 0 && alive) {
+                // modified null-collision method: every particle draws R1 < P_max
+                const uint4 r = draw(ids[k], step, sl, sh, 0);
+                if (u01f(r.x) < pmax) {
+                    const float speed = sqrtf(vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
+                    float4 lo, hi;
+                    float f;
+                    if (en <= e_lo) {
+                        lo = hi = __ldg(&xs[0]);
+                        f = 0.f;
+                    } else if (en >= e_hi) {
+                        lo = hi = __ldg(&xs[nxs - 1]);
+                        f = 0.f;
+                    } else {
+                        int kk = (int)(__logf(en * inv_e_lo) * inv_dlog);
+                        kk = kk < 0 ? 0 : (kk > nxs - 2 ? nxs - 2 : kk);
+                        lo = __ldg(&xs[kk]);
+                        hi = __ldg(&xs[kk + 1]);
+                        f = __fdividef(en - lo.x, hi.x - lo.x);
+                    }
+                    const float s_el = lo.y + f * (hi.y - lo.y);
+                    const float s_ex = en < e_exc ? 0.f : lo.z + f * (hi.z - lo.z);
+                    const float s_iz = en < e_iz ? 0.f : lo.w + f * (hi.w - lo.w);
+                    const float t0 = s_el * speed, t1 = t0 + s_ex * speed, t2 = t1 + s_iz * speed;
+                    const float r2 = u01f(r.y);
+                    if (r2 < t2) {
+                        const float ct = 1.f - 2.f * u01f(r.z);
+                        const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
+                        float sn, cs;
+                        __sincosf(6.283185307179586f * u01f(r.w), &sn, &cs);
+                        const float dx = st * cs, dy = st * sn, dz = ct;
+                        float sp;
+                        if (r2 < t0) {  // elastic, lab-frame isotropic
+                            const float cchi = (vx[k] * dx + vy[k] * dy + vz[k] * dz) / speed;
+                            sp = speed * sqrtf(1.f - two_mM * (1.f - cchi));
+                            ++cnt.el;
+                        } else if (r2 < t1) {  // excitation
+                            sp = sqrtf(two_q_m * (en - e_exc));
+                            ++cnt.exc;
+                        } else {  // ionization: split E - E_iz, eject a new electron
+                            const uint4 r1 = draw(ids[k], step, sl, sh, 1);
+                            const float de = en - e_iz;
+                            const float e_ej = u01f(r1.x) * de;
+                            sp = sqrtf(two_q_m * (de - e_ej));
+                            const float cj = 1.f - 2.f * u01f(r1.y);
+                            const float sj = sqrtf(fmaxf(0.f, 1.f - cj * cj));
+                            float snj, csj;
+                            __sincosf(6.283185307179586f * u01f(r1.z), &snj, &csj);
+                            const float spj = sqrtf(two_q_m * e_ej);
+                            cvx = spj * sj * csj;
+                            cvy = spj * sj * snj;
+                            cvz = spj * cj;
+                            cid = child_id(ids[k], step);
+                            has_child = true;
+                            ++cnt.iz;
+                            if (HYB_CHECK(c + 1 < G, 4, c, G)) {
+                                atomicAdd(&sd_iz[c], 1.f - o);
+                                atomicAdd(&sd_iz[c + 1], o);
+                            }
+                        }
+                        vx[k] = sp * dx;
+                        vy[k] = sp * dy;
+                        vz[k] = sp * dz;
+                    } else {
+                        ++cnt.nul;
+                    }
+                }
+            }
+            if (MODE == 0) append_children<float>(K, P, capacity, has_child, c, o, 0.0, cvx, cvy, cvz, cid,
+                                                  cnt.overflow);
+            cc[k] = alive ? c : kDeadCell;
+            oo[k] = o;
+        }
+        flush_runs(sd_n, sd_e, run, G);
+        if (MODE == 0) {
+            if (full) {
+                *reinterpret_cast<int4 *>(P.c + i0) = make_int4(cc[0], cc[1], cc[2], cc[3]);
+                *reinterpret_cast<float4 *>(P.o + i0) = make_float4(oo[0], oo[1], oo[2], oo[3]);
+                *reinterpret_cast<float4 *>(P.vxf + i0) = make_float4(vx[0], vx[1], vx[2], vx[3]);
+                *reinterpret_cast<float4 *>(P.vyf + i0) = make_float4(vy[0], vy[1], vy[2], vy[3]);
+                *reinterpret_cast<float4 *>(P.vzf + i0) = make_float4(vz[0], vz[1], vz[2], vz[3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < kVec; ++k) {
+                    if (i0 + k < b) {
+                        P.c[i0 + k] = cc[k];
+                        P.o[i0 + k] = oo[k];
+                        P.vxf[i0 + k] = vx[k];
+                        P.vyf[i0 + k] = vy[k];
+                        P.vzf[i0 + k] = vz[k];
+                    }
+                }
             }
         }
     }
@@ -550,42 +657,56 @@ __device__ void flush_segment(InstDev *K, unsigned char *smem, SegCounters &cnt)
     __syncthreads();
 }
 
-// Block chunk of the concatenated slot ranges -> per-instance segments.
-template <int PREC, int MODE>
-__global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 4 : 2) k_electron(InstDev *__restrict__ insts, int n_max,
-                                                     const int64_t *__restrict__ prefix)
+// This block's contiguous run of kChunk-slot chunks, split by instance:
+// fn(K, a, b) for each instance touched, with a a multiple of kChunk.
+template <class F>
+__device__ __forceinline__ void for_block_runs(InstDev *__restrict__ insts, int n_max,
+                                               const int64_t *__restrict__ prefix, F &&fn)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
     const int64_t total = prefix[n_max];
     if (total <= 0) return;
-    int64_t chunk = (total + gridDim.x - 1) / gridDim.x;
-    chunk = (chunk + 127) & ~(int64_t)127;
-    const int64_t glo = (int64_t)blockIdx.x * chunk;
-    if (glo >= total) return;
-    const int64_t ghi = glo + chunk < total ? glo + chunk : total;
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = (int64_t)blockIdx.x * per;
+    if (c0 >= total) return;
+    const int64_t c1 = c0 + per < total ? c0 + per : total;
     int lo = 0, hi = n_max;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (prefix[mid] <= glo)
+        if (prefix[mid] <= c0)
             lo = mid;
         else
             hi = mid;
     }
-    for (int i = lo; i < n_max; ++i) {
+    int64_t ch = c0;
+    for (int i = lo; i < n_max && ch < c1; ++i) {
         const int64_t p0 = prefix[i], p1 = prefix[i + 1];
-        if (p0 >= ghi) break;
-        if (p1 <= glo || p1 == p0) continue;
-        const int64_t a = (glo > p0 ? glo : p0) - p0;
-        const int64_t b = (ghi < p1 ? ghi : p1) - p0;
+        if (p1 <= ch) continue;
+        const int64_t e = c1 < p1 ? c1 : p1;
+        InstDev *K = &insts[i];
+        const int64_t n = K->n_slots_step;
+        const int64_t a = (ch - p0) * kChunk;
+        const int64_t b = (e - p0) * kChunk < n ? (e - p0) * kChunk : n;
+        if (HYB_CHECK(p1 - p0 == chunks_of(n) && (K->cur & ~1) == 0, 12, i, p1 - p0)) fn(K, a, b);
+        ch = e;
+    }
+}
+
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 3 : 2) k_electron(InstDev *__restrict__ insts,
+                                                                                       int n_max,
+                                                                                       const int64_t *__restrict__ prefix)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    for_block_runs(insts, n_max, prefix, [&](InstDev *K, int64_t a, int64_t b) {
         SegCounters cnt;
         if (PREC == HYB_FP32_SPLIT) {
-            segment_split<MODE>(&insts[i], a, b, smem, cnt);
-            flush_segment<float, MODE>(&insts[i], smem, cnt);
+            segment_split<MODE>(K, a, b, smem, cnt);
+            flush_segment<float, MODE>(K, smem, cnt);
         } else {
-            segment_fp64<MODE>(&insts[i], a, b, smem, cnt);
-            flush_segment<double, MODE>(&insts[i], smem, cnt);
+            segment_fp64<MODE>(K, a, b, smem, cnt);
+            flush_segment<double, MODE>(K, smem, cnt);
         }
-    }
+    });
 }
 
 // ------------------------------------------------------------- initial load
@@ -648,32 +769,11 @@ template <int PREC, int PHASE>  // PHASE 0: count, 1: scatter
 __global__ void __launch_bounds__(kBlock) k_sort_pass(InstDev *__restrict__ insts, int n_max,
                                                       const int64_t *__restrict__ prefix)
 {
-    const int64_t total = prefix[n_max];
-    if (total <= 0) return;
-    int64_t chunk = (total + gridDim.x - 1) / gridDim.x;
-    chunk = (chunk + 127) & ~(int64_t)127;
-    const int64_t glo = (int64_t)blockIdx.x * chunk;
-    if (glo >= total) return;
-    const int64_t ghi = glo + chunk < total ? glo + chunk : total;
-    int lo = 0, hi = n_max;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (prefix[mid] <= glo)
-            lo = mid;
-        else
-            hi = mid;
-    }
     const int lane = threadIdx.x & 31;
-    for (int inst = lo; inst < n_max; ++inst) {
-        const int64_t p0 = prefix[inst], p1 = prefix[inst + 1];
-        if (p0 >= ghi) break;
-        if (p1 <= glo || p1 == p0) continue;
-        const int64_t a = (glo > p0 ? glo : p0) - p0;
-        const int64_t b = (ghi < p1 ? ghi : p1) - p0;
-        InstDev *K = &insts[inst];
+    for_block_runs(insts, n_max, prefix, [&](InstDev *K, int64_t a, int64_t b) {
         const PartBuf S = K->buf[K->cur];
-        if (!HYB_CHECK(b <= K->capacity, 11, b, K->capacity)) continue;
         const PartBuf D = K->buf[K->cur ^ 1];
+        if (!HYB_CHECK(b <= K->capacity, 11, b, K->capacity)) return;
         int32_t *cnt = K->cell_cnt;
         const double dz = K->dz;
         const int nc = K->n_cells;
@@ -706,7 +806,7 @@ __global__ void __launch_bounds__(kBlock) k_sort_pass(InstDev *__restrict__ inst
                 }
             }
         }
-    }
+    });
 }
 
 // Exclusive scan of the cell counts, one CTA per sorted instance; the total
@@ -774,7 +874,7 @@ __global__ void k_prefix(InstDev *insts, int n_max, int64_t *prefix)
     int64_t acc = 0;
     prefix[0] = 0;
     for (int i = 0; i < n_max; ++i) {
-        if (insts[i].active) acc += insts[i].n_slots_step;
+        if (insts[i].active) acc += chunks_of(insts[i].n_slots_step);
         prefix[i + 1] = acc;
     }
 }
@@ -784,7 +884,7 @@ __global__ void k_prefix_one(InstDev *K, int64_t *prefix)
 {
     if (threadIdx.x != 0) return;
     prefix[0] = 0;
-    prefix[1] = (int64_t)K->n_slots;
+    prefix[1] = chunks_of((int64_t)K->n_slots);
     K->n_slots_step = (int64_t)K->n_slots;
 }
 
@@ -806,11 +906,8 @@ cudaError_t launch_k(InstDev *inst, int n_max, const int64_t *prefix, LaunchCfg 
 
 void read_checks_electron(unsigned long long out[3])
 {
-#ifdef HYB_CHECKS
-    cudaMemcpyFromSymbol(out, g_hyb_check, sizeof(unsigned long long) * 3);
-#else
-    out[0] = out[1] = out[2] = 0ull;
-#endif
+    if (cudaMemcpyFromSymbol(out, g_hyb_check, sizeof(unsigned long long) * 3) != cudaSuccess)
+        out[0] = out[1] = out[2] = 0ull;
 }
 
 void configure_kernels()

@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kFieldThreads) k_field(InstDev *insts, int n_m
             prefix[0] = 0;
             for (int i = 0; i < n_max; ++i) {
                 const volatile InstDev *Ki = &insts[i];
-                if (Ki->active) acc += Ki->n_slots_step;
+                if (Ki->active) acc += chunks_of(Ki->n_slots_step);
                 prefix[i + 1] = acc;
             }
             *ticket = 0u;
@@ -446,11 +446,8 @@ size_t field_smem_bytes(int max_nodes) { return (size_t)kArrays * 8 * (size_t)ma
 
 void read_checks_field(unsigned long long out[3])
 {
-#ifdef HYB_CHECKS
-    cudaMemcpyFromSymbol(out, g_hyb_check, sizeof(unsigned long long) * 3);
-#else
-    out[0] = out[1] = out[2] = 0ull;
-#endif
+    if (cudaMemcpyFromSymbol(out, g_hyb_check, sizeof(unsigned long long) * 3) != cudaSuccess)
+        out[0] = out[1] = out[2] = 0ull;
 }
 
 void configure_field_kernel()

@@ -20,6 +20,11 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr int32_t kDeadCell = INT32_MIN;  // cell index of a removed split-mode particle
 constexpr int kFieldThreads = 1024;         // one field CTA per instance
 constexpr int kMaxNodes = HYB_MAX_CELLS + 1;
+// Particle kernels split each instance's slots into chunks of kChunk slots;
+// prefix arrays hold chunk counts of the running instances.
+constexpr int kChunk = 2048;
+
+__host__ __device__ __forceinline__ int64_t chunks_of(int64_t n) { return (n + kChunk - 1) / kChunk; }
 
 // Particle store, structure of arrays.  Split mode uses c/o/vxf..; FP64 mode
 // uses z/vxd..; id is shared.
@@ -72,10 +77,9 @@ struct InstDev {
 enum { C_BIRTH_IZ = 0, C_SEE0, C_SEE1, C_LOSS0, C_LOSS1, C_EL, C_EXC, C_IZ, C_NULL, C_CLAMP, C_PUSH };
 
 // ------------------------------------------------------------ self-checks
-// In the checked build (-DHYB_CHECKS) every guarded index is tested; the first
-// failure in each translation unit is recorded (site, index, bound) and the
-// access is skipped.  In the normal build the guards compile away.
-#ifdef HYB_CHECKS
+// Every dynamic index of the kernels is guarded: the first failed guard of a
+// translation unit is recorded (site, index, bound) and the access is skipped.
+// The guards cost a compare each; the recording path is out of line.
 static __device__ unsigned long long g_hyb_check[3];
 __device__ __noinline__ static bool hyb_check_fail(int site, long long a, long long b)
 {
@@ -86,9 +90,6 @@ __device__ __noinline__ static bool hyb_check_fail(int site, long long a, long l
     return false;
 }
 #define HYB_CHECK(cond, site, a, b) ((cond) ? true : hyb_check_fail((site), (long long)(a), (long long)(b)))
-#else
-#define HYB_CHECK(cond, site, a, b) true
-#endif
 
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter (step, seed_lo,
@@ -136,9 +137,9 @@ __host__ __device__ __forceinline__ uint64_t see_id(int wall, uint32_t step, uin
 }
 
 // ------------------------------------------------------- launch helpers
-// Work decomposition shared by the particle kernels: the running instances'
-// slot ranges are concatenated (prefix[i]..prefix[i+1]) and each block takes
-// one contiguous chunk.
+// Work decomposition shared by the particle kernels: prefix[i]..prefix[i+1]
+// are instance i's chunks of kChunk slots; each block takes a contiguous run
+// of chunks.
 
 struct LaunchCfg {
     int grid, block;

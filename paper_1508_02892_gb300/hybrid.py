@@ -12,9 +12,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-# HYB_CHECKED=1 selects the self-checking build (device index guards)
-LIB_PATH = os.path.join(HERE, "_build", "checked" if os.environ.get("HYB_CHECKED") == "1" else "",
-                        "libhybrid1d.so")
+LIB_PATH = os.path.join(HERE, "_build", "libhybrid1d.so")
 
 HYB_OK, HYB_WARN_DT_NULLCOLL = 0, 1
 ERRORS = {-1: "HYB_ERR_ARG", -2: "HYB_ERR_OOM", -3: "HYB_ERR_CAPACITY", -4: "HYB_ERR_NONFINITE",
@@ -112,8 +110,8 @@ EXPORTS = {
 
 
 def debug_checks():
-    """First failed device self-check (checked build): (site, index, bound) for
-    the particle kernels and for the field kernel; zeros when none failed."""
+    """First failed device index guard: (site, index, bound) for the particle
+    kernels and for the field kernel; zeros when none failed."""
     out = (C.c_uint64 * 6)()
     _check(lib().hyb_debug_checks(out))
     return tuple(out[:3]), tuple(out[3:])

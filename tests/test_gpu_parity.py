@@ -124,3 +124,145 @@ def test_split_mode_statistics_config1():
         g.close()
     for k, (a, b) in acc.items():
         assert _l2(a, b) < 0.02, (k, _l2(a, b))
+
+
+def test_batch_matches_single_runs_fp64():
+    """Each discharge gives the same result alone and inside a batch (RNG is
+    keyed by particle id and step, so only summation order differs)."""
+    from paper_1508_02892_gb300 import hybrid
+    ps = [W.config1(precision=W.FP64, n_particles=5000, n_cells=80, seed=21, te0_ev=6.0),
+          W.config1(precision=W.FP64, n_particles=12000, n_cells=150, seed=22, ion_model=W.ION_FULL,
+                    gamma_see=0.2, weight=2e6, v_rf_amp_v=300.0),
+          W.config1(precision=W.FP64, n_particles=777, n_cells=33, seed=23, ion_model=W.ION_DD_TABLE)]
+    b = hybrid.Batch(4, hybrid.HYB_FP64)
+    slots = [b.admit(p) for p in ps]
+    b.advance(50)
+    for s, p in zip(slots, ps):
+        g = _gpu(p)
+        g.advance(50)
+        assert_particles_close(b.particles(s), g.particles(), p["gap_m"], PART_TOL)
+        ca, cb = b.counters(s), g.counters()
+        for k in COUNTERS:
+            assert ca[k] == cb[k], (k, ca[k], cb[k])
+        ma, mb = b.moments(s), g.moments()
+        for k in ("ne", "ni", "gamma", "ebar", "eedf"):
+            assert_grid_close(ma[k], mb[k], GRID_TOL, k)
+    b.close()
+
+
+def test_batch_admission_completion_and_eviction():
+    from paper_1508_02892_gb300 import hybrid
+    b = hybrid.Batch(2, hybrid.HYB_FP32_SPLIT)
+    p = W.config1(precision=W.FP32_SPLIT, n_particles=3000, n_cells=64)
+    s0 = b.admit(p, n_steps=30)
+    s1 = b.admit(dict(p, seed=9), n_steps=70)
+    with pytest.raises(hybrid.HybError):
+        b.admit(p)                      # no free slot
+    b.advance(40)
+    assert b.poll() == [s0]
+    assert b.counters(s0)["step"] == 30 and b.counters(s1)["step"] == 40
+    b.evict(s0)
+    s2 = b.admit(dict(p, seed=10), n_steps=10)
+    b.advance(40)
+    assert sorted(b.poll()) == sorted([s1, s2])
+    assert b.counters(s1)["step"] == 70 and b.counters(s2)["step"] == 10
+    b.close()
+
+
+def test_write_read_particles_roundtrip():
+    p = W.config1(precision=W.FP64, n_particles=100, n_cells=40)
+    g = _gpu(p)
+    s = W.random_particles(5003, p["gap_m"], 3.0, seed=5, id_base=1000)
+    g.set_particles(s["z"], s["vx"], s["vy"], s["vz"], s["id"])
+    r = g.particles()
+    assert np.array_equal(r["id"], s["id"])
+    for k in ("z", "vx", "vy", "vz"):
+        assert np.array_equal(r[k], s[k])
+    assert g.counters()["particles"] == 5003
+    ps = W.config1(precision=W.FP32_SPLIT, n_particles=100, n_cells=40)
+    gs = _gpu(ps)
+    gs.set_particles(s["z"], s["vx"], s["vy"], s["vz"], s["id"])
+    r = gs.particles()
+    assert np.array_equal(r["id"], s["id"])
+    np.testing.assert_allclose(r["z"], s["z"], rtol=0, atol=1e-7 * p["gap_m"])
+    np.testing.assert_allclose(r["vx"], s["vx"], rtol=1e-7)
+
+
+def test_written_particles_match_oracle_fp64():
+    """Parity from a particle set given by the seeded generator."""
+    p = W.config1(precision=W.FP64, n_particles=10, n_cells=120, te0_ev=12.0, gamma_see=0.2, weight=1e9)
+    s = W.random_particles(9000, p["gap_m"], 12.0, seed=77)
+    g = _gpu(p)
+    o = oracle.Oracle(p)
+    g.set_particles(s["z"], s["vx"], s["vy"], s["vz"], s["id"])
+    o.set_particles(s["z"], s["vx"], s["vy"], s["vz"], s["id"])
+    g.advance(80)
+    o.step(80)
+    _check_all(g, o, p)
+
+
+def test_capacity_overflow_is_reported():
+    from paper_1508_02892_gb300 import hybrid
+    p = W.config1(precision=W.FP32_SPLIT, n_particles=4000, capacity_factor=1.0, te0_ev=60.0, n_cells=50)
+    g = _gpu(p)
+    with pytest.raises(hybrid.HybError) as e:
+        g.advance(400)
+        g.sync()
+    assert e.value.code == -3
+
+
+def _split_state_to_oracle(s):
+    return np.stack([s["z"], s["vx"], s["vy"], s["vz"]], axis=1)
+
+
+@pytest.mark.parametrize("cfg", ["config2"])
+def test_full_size_sampled_step_against_oracle(cfg):
+    """Full-size FP32 split discharge in the benchmark's launch configuration:
+    a sample of particles is stepped one by one by the FP64 oracle from the
+    GPU's pre-step state and field; states agree to FP32 rounding and the
+    collision outcomes agree except for draws within rounding of a threshold."""
+    p = W.config2()
+    g = _gpu(p)
+    g.advance(20)
+    before = g.particles()
+    E = g.fields()["E"]
+    step = g.counters()["step"]
+    g.advance(1)
+    after = g.particles()
+    o = oracle.Oracle(dict(p, n_particles=1))
+    rng = np.random.default_rng(3)
+    idx = rng.choice(before["id"].size, 3000, replace=False)
+    pos = {int(k): i for i, k in enumerate(after["id"])}
+    mism = 0
+    for j in idx:
+        st = [before["z"][j], before["vx"][j], before["vy"][j], before["vz"][j]]
+        oc, out, child, cid = o.particle_step_one(E, step, st, int(before["id"][j]))
+        pid = int(before["id"][j])
+        if oc in (oracle.OUT_LOST0, oracle.OUT_LOST1):
+            mism += pid in pos
+            continue
+        if pid not in pos:
+            mism += 1
+            continue
+        k = pos[pid]
+        got = np.array([after["z"][k], after["vx"][k], after["vy"][k], after["vz"][k]])
+        sp = np.linalg.norm(out[1:])
+        ok = abs(got[0] - out[0]) <= 2e-6 * p["gap_m"] and np.linalg.norm(got[1:] - out[1:]) <= 1e-4 * sp + 1.0
+        mism += not ok
+        if oc == oracle.OUT_ION:
+            mism += cid not in pos
+    assert mism <= 3, mism
+
+
+def test_full_size_particle_conservation_and_unique_ids():
+    p = W.config2()
+    g = _gpu(p)
+    g.advance(60)
+    s = g.particles()
+    c = g.counters()
+    assert s["id"].size == c["particles"]
+    assert np.unique(s["id"]).size == s["id"].size
+    assert np.all((s["z"] >= 0) & (s["z"] < p["gap_m"]))
+    assert c["pushes"] > 59 * 1.9e6
+    from paper_1508_02892_gb300 import hybrid
+    assert hybrid.debug_checks() == ((0, 0, 0), (0, 0, 0))
