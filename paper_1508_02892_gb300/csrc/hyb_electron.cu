@@ -33,15 +33,6 @@ template <typename T>
 struct WarpSum;
 
 template <>
-struct WarpSum<float> {
-    __device__ static float run(float v)
-    {
-#pragma unroll
-        for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
-        return v;
-    }
-};
-template <>
 struct WarpSum<double> {
     __device__ static double run(double v)
     {
@@ -72,9 +63,29 @@ __device__ __forceinline__ void deposit_pair(T *arr, bool on, int c, T w0, T w1,
     }
 }
 
+// Per-thread event counts; the split kernel packs two 16-bit counts per word
+// (a thread handles far fewer than 65536 particles of one segment).
 struct SegCounters {
     unsigned el = 0, exc = 0, iz = 0, nul = 0, loss0 = 0, loss1 = 0, overflow = 0, push = 0;
     int cmin = INT32_MAX, cmax = -1;
+};
+
+struct PackedCounters {
+    unsigned el_exc = 0, iz_nul = 0, loss = 0, push_ovf = 0;
+    int cmin = INT32_MAX, cmax = -1;
+    __device__ void unpack(SegCounters &s) const
+    {
+        s.el = el_exc & 0xFFFFu;
+        s.exc = el_exc >> 16;
+        s.iz = iz_nul & 0xFFFFu;
+        s.nul = iz_nul >> 16;
+        s.loss0 = loss & 0xFFFFu;
+        s.loss1 = loss >> 16;
+        s.push = push_ovf & 0xFFFFu;
+        s.overflow = push_ovf >> 16;
+        s.cmin = cmin;
+        s.cmax = cmax;
+    }
 };
 
 // Append children with one atomic per warp; all 32 lanes must call this.
@@ -146,14 +157,27 @@ __device__ __forceinline__ void append_children<double>(InstDev *K, const PartBu
 // particles.
 
 constexpr int kVec = 4;
+// Block-private split-mode sums are 64-bit fixed point with 32 fraction bits:
+// integer shared-memory atomics are native and order-independent.
+constexpr float kFix = 4294967296.0f;
+constexpr double kUnfix = 1.0 / 4294967296.0;
+
+__device__ __forceinline__ unsigned long long fix(float x) { return __float2ull_rn(x * kFix); }
 
 struct Run {
     int c = -1;
     float a0 = 0.f, a1 = 0.f, e0 = 0.f, e1 = 0.f;
 };
 
-// Merge the runs of a warp into the block-private arrays.
-__device__ __forceinline__ void flush_runs(float *sd_n, float *sd_e, const Run &r, int G)
+__device__ __forceinline__ void track(PackedCounters &cnt, int c)
+{
+    cnt.cmin = min(cnt.cmin, c);
+    cnt.cmax = max(cnt.cmax, c);
+}
+
+// Merge the runs of a warp into the block-private sums.
+__device__ __forceinline__ void flush_runs(unsigned long long *sd_n, unsigned long long *sd_e, const Run &r, int G,
+                                           PackedCounters &cnt)
 {
     const bool on = r.c >= 0 && HYB_CHECK(r.c + 1 < G, 4, r.c, G);
     const int kmin = __reduce_min_sync(kFull, on ? r.c : INT32_MAX);
@@ -171,25 +195,28 @@ __device__ __forceinline__ void flush_runs(float *sd_n, float *sd_e, const Run &
             for (int k = 0; k < 8; ++k)
                 if (k < nv) v[k] += __shfl_xor_sync(kFull, v[k], d);
         if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&sd_n[kmin], v[0]);
-            atomicAdd(&sd_n[kmin + 1], v[1] + v[4]);
-            atomicAdd(&sd_e[kmin], v[2]);
-            atomicAdd(&sd_e[kmin + 1], v[3] + v[6]);
+            atomicAdd(&sd_n[kmin], fix(v[0]));
+            atomicAdd(&sd_n[kmin + 1], fix(v[1] + v[4]));
+            atomicAdd(&sd_e[kmin], fix(v[2]));
+            atomicAdd(&sd_e[kmin + 1], fix(v[3] + v[6]));
             if (nv == 8) {
-                atomicAdd(&sd_n[kmax + 1], v[5]);
-                atomicAdd(&sd_e[kmax + 1], v[7]);
+                atomicAdd(&sd_n[kmax + 1], fix(v[5]));
+                atomicAdd(&sd_e[kmax + 1], fix(v[7]));
             }
         }
+        track(cnt, kmin);
+        track(cnt, kmax);
     } else if (on) {
-        atomicAdd(&sd_n[r.c], r.a0);
-        atomicAdd(&sd_n[r.c + 1], r.a1);
-        atomicAdd(&sd_e[r.c], r.e0);
-        atomicAdd(&sd_e[r.c + 1], r.e1);
+        atomicAdd(&sd_n[r.c], fix(r.a0));
+        atomicAdd(&sd_n[r.c + 1], fix(r.a1));
+        atomicAdd(&sd_e[r.c], fix(r.e0));
+        atomicAdd(&sd_e[r.c + 1], fix(r.e1));
+        track(cnt, r.c);
     }
 }
 
 template <int MODE>
-__device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *smem, SegCounters &cnt)
+__device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *smem, PackedCounters &cnt)
 {
     const int nc = K->n_cells;
     const int G = K->G;
@@ -206,12 +233,12 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const float inv_dlog = K->f_inv_dlog, e_exc = K->f_e_exc, e_iz = K->f_e_iz, two_mM = K->f_two_mM;
     const float bin_inv = K->f_bin_inv;
 
-    float *sd_n = reinterpret_cast<float *>(smem);
-    float *sd_e = sd_n + G;
-    float *sd_iz = sd_e + G;
+    unsigned long long *sd_n = reinterpret_cast<unsigned long long *>(smem);
+    unsigned long long *sd_e = sd_n + G;
+    unsigned long long *sd_iz = sd_e + G;
     unsigned *s_eedf = reinterpret_cast<unsigned *>(sd_iz + G);
     if (!HYB_CHECK(b <= capacity && a >= 0 && (a & (kVec - 1)) == 0, 10, b, capacity)) b = a;
-    for (int j = threadIdx.x; j < 3 * G; j += blockDim.x) sd_n[j] = 0.f;
+    for (int j = threadIdx.x; j < 3 * G; j += blockDim.x) sd_n[j] = 0ull;
     for (int j = threadIdx.x; j <= nb; j += blockDim.x) s_eedf[j] = 0u;
     __syncthreads();
 
@@ -257,7 +284,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             float o = oo[k];
             bool alive = c >= 0 && c < nc;
             if (MODE == 0 && alive) {
-                ++cnt.push;
+                cnt.push_ovf += 1u;
                 // leapfrog with the CIC-gathered field (Sec. II.A); the gather
                 // index is clamped so that no out-of-range address is formed
                 const int cg = min(max(c, 0), nc - 1);
@@ -272,10 +299,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                     c += 1;
                 }
                 if (c < 0 || c >= nc) {  // absorbed by an electrode and removed
-                    if (c < 0)
-                        ++cnt.loss0;
-                    else
-                        ++cnt.loss1;
+                    cnt.loss += c < 0 ? 1u : (1u << 16);
                     alive = false;
                     c = kDeadCell;
                 }
@@ -293,15 +317,14 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                         run.e1 += w1 * en;
                     }
                 } else if (HYB_CHECK(c + 1 < G, 4, c, G)) {
-                    atomicAdd(&sd_n[c], w0);
-                    atomicAdd(&sd_n[c + 1], w1);
+                    atomicAdd(&sd_n[c], fix(w0));
+                    atomicAdd(&sd_n[c + 1], fix(w1));
                     if (MODE == 0) {
-                        atomicAdd(&sd_e[c], w0 * en);
-                        atomicAdd(&sd_e[c + 1], w1 * en);
+                        atomicAdd(&sd_e[c], fix(w0 * en));
+                        atomicAdd(&sd_e[c + 1], fix(w1 * en));
                     }
+                    track(cnt, c);
                 }
-                cnt.cmin = min(cnt.cmin, c);
-                cnt.cmax = max(cnt.cmax, c);
                 if (MODE == 0) {
                     int bin = (int)(en * bin_inv);
                     if (bin > nb || bin < 0 || !(en >= 0.f)) bin = nb;  // overflow bin (also NaN)
@@ -347,10 +370,10 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                         if (r2 < t0) {  // elastic, lab-frame isotropic
                             const float cchi = (vx[k] * dx + vy[k] * dy + vz[k] * dz) / speed;
                             sp = speed * sqrtf(1.f - two_mM * (1.f - cchi));
-                            ++cnt.el;
+                            cnt.el_exc += 1u;
                         } else if (r2 < t1) {  // excitation
                             sp = sqrtf(two_q_m * (en - e_exc));
-                            ++cnt.exc;
+                            cnt.el_exc += 1u << 16;
                         } else {  // ionization: split E - E_iz, eject a new electron
                             const uint4 r1 = draw(ids[k], step, sl, sh, 1);
                             const float de = en - e_iz;
@@ -366,26 +389,30 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                             cvz = spj * cj;
                             cid = child_id(ids[k], step);
                             has_child = true;
-                            ++cnt.iz;
+                            cnt.iz_nul += 1u;
                             if (HYB_CHECK(c + 1 < G, 4, c, G)) {
-                                atomicAdd(&sd_iz[c], 1.f - o);
-                                atomicAdd(&sd_iz[c + 1], o);
+                                atomicAdd(&sd_iz[c], fix(1.f - o));
+                                atomicAdd(&sd_iz[c + 1], fix(o));
+                                track(cnt, c);
                             }
                         }
                         vx[k] = sp * dx;
                         vy[k] = sp * dy;
                         vz[k] = sp * dz;
                     } else {
-                        ++cnt.nul;
+                        cnt.iz_nul += 1u << 16;
                     }
                 }
             }
-            if (MODE == 0) append_children<float>(K, P, capacity, has_child, c, o, 0.0, cvx, cvy, cvz, cid,
-                                                  cnt.overflow);
+            if (MODE == 0) {
+                unsigned ovf = 0;
+                append_children<float>(K, P, capacity, has_child, c, o, 0.0, cvx, cvy, cvz, cid, ovf);
+                cnt.push_ovf |= ovf << 16;
+            }
             cc[k] = alive ? c : kDeadCell;
             oo[k] = o;
         }
-        flush_runs(sd_n, sd_e, run, G);
+        flush_runs(sd_n, sd_e, run, G, cnt);
         if (MODE == 0) {
             if (full) {
                 *reinterpret_cast<int4 *>(P.c + i0) = make_int4(cc[0], cc[1], cc[2], cc[3]);
@@ -597,9 +624,13 @@ __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *sm
 }
 
 // Reduce the per-thread counters, then flush the block-private sums over the
-// touched node range into the global FP64 sums.
-template <typename T, int MODE>
-__device__ void flush_segment(InstDev *K, unsigned char *smem, SegCounters &cnt)
+// touched node range into the global FP64 sums.  S is the shared sum type:
+// 64-bit fixed point (split mode) or double (FP64 mode).
+__device__ __forceinline__ double sum_value(unsigned long long q) { return (double)q * kUnfix; }
+__device__ __forceinline__ double sum_value(double q) { return q; }
+
+template <typename S, int MODE>
+__device__ void flush_segment(InstDev *K, unsigned char *smem, const SegCounters &cnt)
 {
     __shared__ unsigned s_ctr[8];
     __shared__ int s_cmin, s_cmax;
@@ -625,20 +656,20 @@ __device__ void flush_segment(InstDev *K, unsigned char *smem, SegCounters &cnt)
     __syncthreads();
     const int G = K->G;
     const int nb = K->eedf_bins;
-    T *sd_n = reinterpret_cast<T *>(smem);
-    T *sd_e = sd_n + G;
-    T *sd_iz = sd_e + G;
+    S *sd_n = reinterpret_cast<S *>(smem);
+    S *sd_e = sd_n + G;
+    S *sd_iz = sd_e + G;
     unsigned *s_eedf = reinterpret_cast<unsigned *>(sd_iz + G);
     int jlo = s_cmin, jhi = s_cmax < 0 ? -1 : min(s_cmax + 1, G - 1);
     if (jhi >= 0 && !HYB_CHECK(jlo >= 0 && jlo <= jhi, 6, jlo, jhi)) jhi = -1;
     for (int j = (jhi < 0 ? 0 : jlo) + (int)threadIdx.x; j <= jhi; j += blockDim.x) {
-        const T a = sd_n[j];
-        if (a != T(0)) atomicAdd(&K->dep_n[j], (double)a);
+        const S a = sd_n[j];
+        if (a != S(0)) atomicAdd(&K->dep_n[j], sum_value(a));
         if (MODE == 0) {
-            const T e = sd_e[j];
-            if (e != T(0)) atomicAdd(&K->dep_e[j], (double)e);
-            const T s = sd_iz[j];
-            if (s != T(0)) atomicAdd(&K->s_iz[j], (double)s);
+            const S e = sd_e[j];
+            if (e != S(0)) atomicAdd(&K->dep_e[j], sum_value(e));
+            const S s = sd_iz[j];
+            if (s != S(0)) atomicAdd(&K->s_iz[j], sum_value(s));
         }
     }
     if (MODE == 0) {
@@ -700,8 +731,10 @@ __global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 3 : 2) k_elec
     for_block_runs(insts, n_max, prefix, [&](InstDev *K, int64_t a, int64_t b) {
         SegCounters cnt;
         if (PREC == HYB_FP32_SPLIT) {
-            segment_split<MODE>(K, a, b, smem, cnt);
-            flush_segment<float, MODE>(K, smem, cnt);
+            PackedCounters pc;
+            segment_split<MODE>(K, a, b, smem, pc);
+            pc.unpack(cnt);
+            flush_segment<unsigned long long, MODE>(K, smem, cnt);
         } else {
             segment_fp64<MODE>(K, a, b, smem, cnt);
             flush_segment<double, MODE>(K, smem, cnt);
@@ -933,7 +966,8 @@ int electron_blocks_per_sm(int precision, size_t smem)
 
 size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins)
 {
-    const size_t el = precision == HYB_FP32_SPLIT ? 4 : 8;
+    const size_t el = 8;  // 64-bit fixed point (split) or double (FP64)
+    (void)precision;
     return 3 * el * (size_t)max_nodes + 4 * (size_t)(eedf_bins + 1) + 16;
 }
 

@@ -170,7 +170,7 @@ def test_batch_admission_completion_and_eviction():
 
 
 def test_write_read_particles_roundtrip():
-    p = W.config1(precision=W.FP64, n_particles=100, n_cells=40)
+    p = W.config1(precision=W.FP64, n_particles=3000, n_cells=40)
     g = _gpu(p)
     s = W.random_particles(5003, p["gap_m"], 3.0, seed=5, id_base=1000)
     g.set_particles(s["z"], s["vx"], s["vy"], s["vz"], s["id"])
@@ -179,7 +179,7 @@ def test_write_read_particles_roundtrip():
     for k in ("z", "vx", "vy", "vz"):
         assert np.array_equal(r[k], s[k])
     assert g.counters()["particles"] == 5003
-    ps = W.config1(precision=W.FP32_SPLIT, n_particles=100, n_cells=40)
+    ps = W.config1(precision=W.FP32_SPLIT, n_particles=3000, n_cells=40)
     gs = _gpu(ps)
     gs.set_particles(s["z"], s["vx"], s["vy"], s["vz"], s["id"])
     r = gs.particles()
