@@ -157,12 +157,6 @@ __device__ __forceinline__ void append_children<double>(InstDev *K, const PartBu
 // particles.
 
 constexpr int kVec = 4;
-// Block-private split-mode sums are 64-bit fixed point with 32 fraction bits:
-// integer shared-memory atomics are native and order-independent.
-constexpr float kFix = 4294967296.0f;
-constexpr double kUnfix = 1.0 / 4294967296.0;
-
-__device__ __forceinline__ unsigned long long fix(float x) { return __float2ull_rn(x * kFix); }
 
 struct Run {
     int c = -1;
@@ -175,43 +169,55 @@ __device__ __forceinline__ void track(PackedCounters &cnt, int c)
     cnt.cmax = max(cnt.cmax, c);
 }
 
-// Merge the runs of a warp into the block-private sums.
-__device__ __forceinline__ void flush_runs(unsigned long long *sd_n, unsigned long long *sd_e, const Run &r, int G,
-                                           PackedCounters &cnt)
+// Warp-collective merge of one run per lane into the block-private sums: one
+// pass per distinct cell among the lanes, each a butterfly sum, after which a
+// single lane adds to shared memory, so no two lanes of a warp ever update the
+// same address.
+__device__ __forceinline__ void merge_runs(float *sd_n, float *sd_e, Run &r, int G, PackedCounters &cnt)
 {
     const bool on = r.c >= 0 && HYB_CHECK(r.c + 1 < G, 4, r.c, G);
-    const int kmin = __reduce_min_sync(kFull, on ? r.c : INT32_MAX);
-    const int kmax = __reduce_max_sync(kFull, on ? r.c : -1);
-    if (kmax < 0) return;
-    if (kmax - kmin <= 1) {
-        // two cells at most: reduce the low and the high run separately
-        const bool lo = on && r.c == kmin, hi = on && r.c == kmax && kmax != kmin;
-        float v[8] = {lo ? r.a0 : 0.f, lo ? r.a1 : 0.f, lo ? r.e0 : 0.f, lo ? r.e1 : 0.f,
-                      hi ? r.a0 : 0.f, hi ? r.a1 : 0.f, hi ? r.e0 : 0.f, hi ? r.e1 : 0.f};
-        const int nv = kmax != kmin ? 8 : 4;
+    unsigned todo = __ballot_sync(kFull, on);
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int key = __shfl_sync(kFull, r.c, leader);
+        const bool mine = on && r.c == key;
+        float v0 = mine ? r.a0 : 0.f, v1 = mine ? r.a1 : 0.f, v2 = mine ? r.e0 : 0.f, v3 = mine ? r.e1 : 0.f;
 #pragma unroll
-        for (int d = 16; d; d >>= 1)
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (k < nv) v[k] += __shfl_xor_sync(kFull, v[k], d);
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&sd_n[kmin], fix(v[0]));
-            atomicAdd(&sd_n[kmin + 1], fix(v[1] + v[4]));
-            atomicAdd(&sd_e[kmin], fix(v[2]));
-            atomicAdd(&sd_e[kmin + 1], fix(v[3] + v[6]));
-            if (nv == 8) {
-                atomicAdd(&sd_n[kmax + 1], fix(v[5]));
-                atomicAdd(&sd_e[kmax + 1], fix(v[7]));
-            }
+        for (int d = 16; d; d >>= 1) {
+            v0 += __shfl_xor_sync(kFull, v0, d);
+            v1 += __shfl_xor_sync(kFull, v1, d);
+            v2 += __shfl_xor_sync(kFull, v2, d);
+            v3 += __shfl_xor_sync(kFull, v3, d);
         }
-        track(cnt, kmin);
-        track(cnt, kmax);
-    } else if (on) {
-        atomicAdd(&sd_n[r.c], fix(r.a0));
-        atomicAdd(&sd_n[r.c + 1], fix(r.a1));
-        atomicAdd(&sd_e[r.c], fix(r.e0));
-        atomicAdd(&sd_e[r.c + 1], fix(r.e1));
-        track(cnt, r.c);
+        if ((int)(threadIdx.x & 31) == leader) {
+            atomicAdd(&sd_n[key], v0);
+            atomicAdd(&sd_n[key + 1], v1);
+            atomicAdd(&sd_e[key], v2);
+            atomicAdd(&sd_e[key + 1], v3);
+        }
+        track(cnt, key);
+        todo &= ~__ballot_sync(kFull, mine);
+    }
+    r = Run();
+}
+
+// Add one particle's CIC weights to one of the thread's two runs, or directly
+// to shared memory when both runs hold other cells.
+__device__ __forceinline__ void add_to_runs(Run &A, Run &B, int c, float w0, float w1, float e0, float e1,
+                                            float *sd_n, float *sd_e, int G, PackedCounters &cnt)
+{
+    if (A.c < 0 || A.c == c) {
+        A.c = c;
+        A.a0 += w0, A.a1 += w1, A.e0 += e0, A.e1 += e1;
+    } else if (B.c < 0 || B.c == c) {
+        B.c = c;
+        B.a0 += w0, B.a1 += w1, B.e0 += e0, B.e1 += e1;
+    } else if (HYB_CHECK(c + 1 < G, 4, c, G)) {
+        atomicAdd(&sd_n[c], w0);
+        atomicAdd(&sd_n[c + 1], w1);
+        atomicAdd(&sd_e[c], e0);
+        atomicAdd(&sd_e[c + 1], e1);
+        track(cnt, c);
     }
 }
 
@@ -233,12 +239,12 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const float inv_dlog = K->f_inv_dlog, e_exc = K->f_e_exc, e_iz = K->f_e_iz, two_mM = K->f_two_mM;
     const float bin_inv = K->f_bin_inv;
 
-    unsigned long long *sd_n = reinterpret_cast<unsigned long long *>(smem);
-    unsigned long long *sd_e = sd_n + G;
-    unsigned long long *sd_iz = sd_e + G;
+    float *sd_n = reinterpret_cast<float *>(smem);
+    float *sd_e = sd_n + G;
+    float *sd_iz = sd_e + G;
     unsigned *s_eedf = reinterpret_cast<unsigned *>(sd_iz + G);
     if (!HYB_CHECK(b <= capacity && a >= 0 && (a & (kVec - 1)) == 0, 10, b, capacity)) b = a;
-    for (int j = threadIdx.x; j < 3 * G; j += blockDim.x) sd_n[j] = 0ull;
+    for (int j = threadIdx.x; j < 3 * G; j += blockDim.x) sd_n[j] = 0.f;
     for (int j = threadIdx.x; j <= nb; j += blockDim.x) s_eedf[j] = 0u;
     __syncthreads();
 
@@ -277,7 +283,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
 
-        Run run;
+        Run runA, runB;
 #pragma unroll
         for (int k = 0; k < kVec; ++k) {
             int c = cc[k];
@@ -308,23 +314,8 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             const float en = half_m_q * (vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
             if (alive) {
                 const float w0 = 1.f - o, w1 = o;
-                if (run.c < 0 || run.c == c) {
-                    run.c = c;
-                    run.a0 += w0;
-                    run.a1 += w1;
-                    if (MODE == 0) {
-                        run.e0 += w0 * en;
-                        run.e1 += w1 * en;
-                    }
-                } else if (HYB_CHECK(c + 1 < G, 4, c, G)) {
-                    atomicAdd(&sd_n[c], fix(w0));
-                    atomicAdd(&sd_n[c + 1], fix(w1));
-                    if (MODE == 0) {
-                        atomicAdd(&sd_e[c], fix(w0 * en));
-                        atomicAdd(&sd_e[c + 1], fix(w1 * en));
-                    }
-                    track(cnt, c);
-                }
+                add_to_runs(runA, runB, c, w0, w1, MODE == 0 ? w0 * en : 0.f, MODE == 0 ? w1 * en : 0.f, sd_n, sd_e,
+                            G, cnt);
                 if (MODE == 0) {
                     int bin = (int)(en * bin_inv);
                     if (bin > nb || bin < 0 || !(en >= 0.f)) bin = nb;  // overflow bin (also NaN)
@@ -391,8 +382,8 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                             has_child = true;
                             cnt.iz_nul += 1u;
                             if (HYB_CHECK(c + 1 < G, 4, c, G)) {
-                                atomicAdd(&sd_iz[c], fix(1.f - o));
-                                atomicAdd(&sd_iz[c + 1], fix(o));
+                                atomicAdd(&sd_iz[c], 1.f - o);
+                                atomicAdd(&sd_iz[c + 1], o);
                                 track(cnt, c);
                             }
                         }
@@ -412,7 +403,8 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             cc[k] = alive ? c : kDeadCell;
             oo[k] = o;
         }
-        flush_runs(sd_n, sd_e, run, G, cnt);
+        merge_runs(sd_n, sd_e, runA, G, cnt);
+        merge_runs(sd_n, sd_e, runB, G, cnt);
         if (MODE == 0) {
             if (full) {
                 *reinterpret_cast<int4 *>(P.c + i0) = make_int4(cc[0], cc[1], cc[2], cc[3]);
@@ -625,8 +617,8 @@ __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *sm
 
 // Reduce the per-thread counters, then flush the block-private sums over the
 // touched node range into the global FP64 sums.  S is the shared sum type:
-// 64-bit fixed point (split mode) or double (FP64 mode).
-__device__ __forceinline__ double sum_value(unsigned long long q) { return (double)q * kUnfix; }
+// float (split mode) or double (FP64 mode).
+__device__ __forceinline__ double sum_value(float q) { return (double)q; }
 __device__ __forceinline__ double sum_value(double q) { return q; }
 
 template <typename S, int MODE>
@@ -734,7 +726,7 @@ __global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 3 : 2) k_elec
             PackedCounters pc;
             segment_split<MODE>(K, a, b, smem, pc);
             pc.unpack(cnt);
-            flush_segment<unsigned long long, MODE>(K, smem, cnt);
+            flush_segment<float, MODE>(K, smem, cnt);
         } else {
             segment_fp64<MODE>(K, a, b, smem, cnt);
             flush_segment<double, MODE>(K, smem, cnt);
@@ -966,8 +958,7 @@ int electron_blocks_per_sm(int precision, size_t smem)
 
 size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins)
 {
-    const size_t el = 8;  // 64-bit fixed point (split) or double (FP64)
-    (void)precision;
+    const size_t el = precision == HYB_FP32_SPLIT ? 4 : 8;
     return 3 * el * (size_t)max_nodes + 4 * (size_t)(eedf_bins + 1) + 16;
 }
 

@@ -190,7 +190,8 @@ def test_write_read_particles_roundtrip():
 
 def test_written_particles_match_oracle_fp64():
     """Parity from a particle set given by the seeded generator."""
-    p = W.config1(precision=W.FP64, n_particles=10, n_cells=120, te0_ev=12.0, gamma_see=0.2, weight=1e9)
+    p = W.config1(precision=W.FP64, n_particles=10, n_cells=120, te0_ev=12.0, gamma_see=0.2, weight=1e9,
+                  capacity_factor=2000.0)
     s = W.random_particles(9000, p["gap_m"], 12.0, seed=77)
     g = _gpu(p)
     o = oracle.Oracle(p)
