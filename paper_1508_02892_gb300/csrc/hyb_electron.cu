@@ -156,7 +156,7 @@ __device__ __forceinline__ void append_children<double>(InstDev *K, const PartBu
 // particles are sorted by cell), so a shared-memory atomic serves many
 // particles.
 
-constexpr int kVec = 4;
+constexpr int kVec = 2;
 
 struct Run {
     int c = -1;
@@ -169,14 +169,37 @@ __device__ __forceinline__ void track(PackedCounters &cnt, int c)
     cnt.cmax = max(cnt.cmax, c);
 }
 
-// Warp-collective merge of one run per lane into the block-private sums: one
-// pass per distinct cell among the lanes, each a butterfly sum, after which a
-// single lane adds to shared memory, so no two lanes of a warp ever update the
-// same address.
-__device__ __forceinline__ void merge_runs(float *sd_n, float *sd_e, Run &r, int G, PackedCounters &cnt)
+// Per-warp deposit window: lane l holds the CIC sums of the particles in cell
+// base + l (weights to its two nodes and the energy moment).  Cells outside the
+// window go to shared memory directly.
+struct Window {
+    int base = INT32_MIN;
+    float a0 = 0.f, a1 = 0.f, e0 = 0.f, e1 = 0.f;
+};
+
+__device__ __forceinline__ void window_flush(Window &w, float *sd_n, float *sd_e, int G, PackedCounters &cnt)
+{
+    const int c = w.base + (int)(threadIdx.x & 31);
+    const bool on = w.base != INT32_MIN && (w.a0 != 0.f || w.a1 != 0.f || w.e0 != 0.f || w.e1 != 0.f);
+    if (on && HYB_CHECK(c >= 0 && c + 1 < G, 4, c, G)) {
+        atomicAdd(&sd_n[c], w.a0);
+        atomicAdd(&sd_n[c + 1], w.a1);
+        atomicAdd(&sd_e[c], w.e0);
+        atomicAdd(&sd_e[c + 1], w.e1);
+        track(cnt, c);
+    }
+    w.a0 = w.a1 = w.e0 = w.e1 = 0.f;
+}
+
+// Warp-collective merge of one run per lane: one pass per distinct cell among
+// the lanes, each a butterfly sum; the total lands in the register of the
+// window lane that owns the cell (the window is re-based on the first cell of
+// the warp when it has none yet, and flushed when a cell falls outside it).
+__device__ __forceinline__ void merge_runs(Window &w, Run &r, float *sd_n, float *sd_e, int G, PackedCounters &cnt)
 {
     const bool on = r.c >= 0 && HYB_CHECK(r.c + 1 < G, 4, r.c, G);
     unsigned todo = __ballot_sync(kFull, on);
+    const int lane = threadIdx.x & 31;
     while (todo) {
         const int leader = __ffs(todo) - 1;
         const int key = __shfl_sync(kFull, r.c, leader);
@@ -189,29 +212,29 @@ __device__ __forceinline__ void merge_runs(float *sd_n, float *sd_e, Run &r, int
             v2 += __shfl_xor_sync(kFull, v2, d);
             v3 += __shfl_xor_sync(kFull, v3, d);
         }
-        if ((int)(threadIdx.x & 31) == leader) {
-            atomicAdd(&sd_n[key], v0);
-            atomicAdd(&sd_n[key + 1], v1);
-            atomicAdd(&sd_e[key], v2);
-            atomicAdd(&sd_e[key + 1], v3);
+        if (w.base == INT32_MIN || key < w.base || key >= w.base + 32) {
+            window_flush(w, sd_n, sd_e, G, cnt);
+            w.base = key - 8;  // particles drift both ways; keep room below
         }
-        track(cnt, key);
+        if (lane == key - w.base) {
+            w.a0 += v0;
+            w.a1 += v1;
+            w.e0 += v2;
+            w.e1 += v3;
+        }
         todo &= ~__ballot_sync(kFull, mine);
     }
     r = Run();
 }
 
-// Add one particle's CIC weights to one of the thread's two runs, or directly
-// to shared memory when both runs hold other cells.
-__device__ __forceinline__ void add_to_runs(Run &A, Run &B, int c, float w0, float w1, float e0, float e1,
-                                            float *sd_n, float *sd_e, int G, PackedCounters &cnt)
+// Add one particle's CIC weights to the thread's run, or directly to shared
+// memory when the run holds another cell.
+__device__ __forceinline__ void add_to_run(Run &A, int c, float w0, float w1, float e0, float e1, float *sd_n,
+                                           float *sd_e, int G, PackedCounters &cnt)
 {
     if (A.c < 0 || A.c == c) {
         A.c = c;
         A.a0 += w0, A.a1 += w1, A.e0 += e0, A.e1 += e1;
-    } else if (B.c < 0 || B.c == c) {
-        B.c = c;
-        B.a0 += w0, B.a1 += w1, B.e0 += e0, B.e1 += e1;
     } else if (HYB_CHECK(c + 1 < G, 4, c, G)) {
         atomicAdd(&sd_n[c], w0);
         atomicAdd(&sd_n[c + 1], w1);
@@ -248,32 +271,37 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     for (int j = threadIdx.x; j <= nb; j += blockDim.x) s_eedf[j] = 0u;
     __syncthreads();
 
-    for (int64_t base = a; base < b; base += (int64_t)blockDim.x * kVec) {
-        const int64_t i0 = base + (int64_t)threadIdx.x * kVec;
-        const bool full = i0 + kVec <= b;
+    // each warp sweeps a contiguous part of [a, b) in groups of 32 * kVec
+    const int nwarps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t per = (((b - a) + nwarps - 1) / nwarps + 32 * kVec - 1) / (32 * kVec) * (32 * kVec);
+    const int64_t wa = a + per * wid;
+    const int64_t wb = wa + per < b ? wa + per : b;
+    Window win;
+    for (int64_t base = wa; base < wb; base += 32 * kVec) {
+        const int64_t i0 = base + (int64_t)lane * kVec;
+        const bool full = i0 + kVec <= wb;
         int cc[kVec];
         float oo[kVec], vx[kVec], vy[kVec], vz[kVec];
         uint64_t ids[kVec];
         if (full) {
-            const int4 c4 = *reinterpret_cast<const int4 *>(P.c + i0);
-            const float4 o4 = *reinterpret_cast<const float4 *>(P.o + i0);
-            const float4 x4 = *reinterpret_cast<const float4 *>(P.vxf + i0);
-            const float4 y4 = *reinterpret_cast<const float4 *>(P.vyf + i0);
-            const float4 z4 = *reinterpret_cast<const float4 *>(P.vzf + i0);
-            cc[0] = c4.x, cc[1] = c4.y, cc[2] = c4.z, cc[3] = c4.w;
-            oo[0] = o4.x, oo[1] = o4.y, oo[2] = o4.z, oo[3] = o4.w;
-            vx[0] = x4.x, vx[1] = x4.y, vx[2] = x4.z, vx[3] = x4.w;
-            vy[0] = y4.x, vy[1] = y4.y, vy[2] = y4.z, vy[3] = y4.w;
-            vz[0] = z4.x, vz[1] = z4.y, vz[2] = z4.z, vz[3] = z4.w;
+            const int2 c2 = *reinterpret_cast<const int2 *>(P.c + i0);
+            const float2 o2 = *reinterpret_cast<const float2 *>(P.o + i0);
+            const float2 x2 = *reinterpret_cast<const float2 *>(P.vxf + i0);
+            const float2 y2 = *reinterpret_cast<const float2 *>(P.vyf + i0);
+            const float2 z2 = *reinterpret_cast<const float2 *>(P.vzf + i0);
+            cc[0] = c2.x, cc[1] = c2.y;
+            oo[0] = o2.x, oo[1] = o2.y;
+            vx[0] = x2.x, vx[1] = x2.y;
+            vy[0] = y2.x, vy[1] = y2.y;
+            vz[0] = z2.x, vz[1] = z2.y;
             if (MODE == 0) {
                 const ulonglong2 d0 = *reinterpret_cast<const ulonglong2 *>(P.id + i0);
-                const ulonglong2 d1 = *reinterpret_cast<const ulonglong2 *>(P.id + i0 + 2);
-                ids[0] = d0.x, ids[1] = d0.y, ids[2] = d1.x, ids[3] = d1.y;
+                ids[0] = d0.x, ids[1] = d0.y;
             }
         } else {
 #pragma unroll
             for (int k = 0; k < kVec; ++k) {
-                const bool in = i0 + k < b;
+                const bool in = i0 + k < wb;
                 cc[k] = in ? P.c[i0 + k] : kDeadCell;
                 oo[k] = in ? P.o[i0 + k] : 0.f;
                 vx[k] = in ? P.vxf[i0 + k] : 0.f;
@@ -283,7 +311,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
 
-        Run runA, runB;
+        Run runA;
 #pragma unroll
         for (int k = 0; k < kVec; ++k) {
             int c = cc[k];
@@ -314,8 +342,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             const float en = half_m_q * (vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
             if (alive) {
                 const float w0 = 1.f - o, w1 = o;
-                add_to_runs(runA, runB, c, w0, w1, MODE == 0 ? w0 * en : 0.f, MODE == 0 ? w1 * en : 0.f, sd_n, sd_e,
-                            G, cnt);
+                add_to_run(runA, c, w0, w1, MODE == 0 ? w0 * en : 0.f, MODE == 0 ? w1 * en : 0.f, sd_n, sd_e, G, cnt);
                 if (MODE == 0) {
                     int bin = (int)(en * bin_inv);
                     if (bin > nb || bin < 0 || !(en >= 0.f)) bin = nb;  // overflow bin (also NaN)
@@ -403,19 +430,18 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             cc[k] = alive ? c : kDeadCell;
             oo[k] = o;
         }
-        merge_runs(sd_n, sd_e, runA, G, cnt);
-        merge_runs(sd_n, sd_e, runB, G, cnt);
+        merge_runs(win, runA, sd_n, sd_e, G, cnt);
         if (MODE == 0) {
             if (full) {
-                *reinterpret_cast<int4 *>(P.c + i0) = make_int4(cc[0], cc[1], cc[2], cc[3]);
-                *reinterpret_cast<float4 *>(P.o + i0) = make_float4(oo[0], oo[1], oo[2], oo[3]);
-                *reinterpret_cast<float4 *>(P.vxf + i0) = make_float4(vx[0], vx[1], vx[2], vx[3]);
-                *reinterpret_cast<float4 *>(P.vyf + i0) = make_float4(vy[0], vy[1], vy[2], vy[3]);
-                *reinterpret_cast<float4 *>(P.vzf + i0) = make_float4(vz[0], vz[1], vz[2], vz[3]);
+                *reinterpret_cast<int2 *>(P.c + i0) = make_int2(cc[0], cc[1]);
+                *reinterpret_cast<float2 *>(P.o + i0) = make_float2(oo[0], oo[1]);
+                *reinterpret_cast<float2 *>(P.vxf + i0) = make_float2(vx[0], vx[1]);
+                *reinterpret_cast<float2 *>(P.vyf + i0) = make_float2(vy[0], vy[1]);
+                *reinterpret_cast<float2 *>(P.vzf + i0) = make_float2(vz[0], vz[1]);
             } else {
 #pragma unroll
                 for (int k = 0; k < kVec; ++k) {
-                    if (i0 + k < b) {
+                    if (i0 + k < wb) {
                         P.c[i0 + k] = cc[k];
                         P.o[i0 + k] = oo[k];
                         P.vxf[i0 + k] = vx[k];
@@ -426,6 +452,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
     }
+    window_flush(win, sd_n, sd_e, G, cnt);
 }
 
 // ------------------------------------------------------------------ FP64

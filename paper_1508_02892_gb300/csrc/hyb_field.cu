@@ -420,8 +420,8 @@ __global__ void __launch_bounds__(kFieldThreads) k_field(InstDev *insts, int n_m
     extern __shared__ __align__(16) double sm[];
     __shared__ Red red;
     InstDev *K = &insts[blockIdx.x];
-    const bool fits = HYB_CHECK(K->G >= 3 && K->G <= kMaxNodes, 20, K->G, kMaxNodes);
-    if ((K->active || K->init_pending) && fits) field_body(K, sm, red);
+    const bool run = K->active || K->init_pending;
+    if (run && HYB_CHECK(K->G >= 3 && K->G <= kMaxNodes, 20, K->G, kMaxNodes)) field_body(K, sm, red);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
