@@ -28,7 +28,10 @@ def _nvcc():
 
 
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+    # fast single-precision division and square root (the split-mode particle
+    # kernel); double precision is unaffected
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "--prec-div=false", "--prec-sqrt=false",
+                   "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 

@@ -158,89 +158,82 @@ __device__ __forceinline__ void append_children<double>(InstDev *K, const PartBu
 
 constexpr int kVec = 2;
 
-struct Run {
-    int c = -1;
-    float a0 = 0.f, a1 = 0.f, e0 = 0.f, e1 = 0.f;
-};
-
 __device__ __forceinline__ void track(PackedCounters &cnt, int c)
 {
     cnt.cmin = min(cnt.cmin, c);
     cnt.cmax = max(cnt.cmax, c);
 }
 
-// Per-warp deposit window: lane l holds the CIC sums of the particles in cell
-// base + l (weights to its two nodes and the energy moment).  Cells outside the
-// window go to shared memory directly.
-struct Window {
-    int base = INT32_MIN;
-    float a0 = 0.f, a1 = 0.f, e0 = 0.f, e1 = 0.f;
+// Per-warp deposit window: a private shared-memory row of kWin cells (CIC
+// weights to the two nodes of the cell and the energy moment) starting at
+// cell `base`.  Within a warp, lanes in the same cell are grouped with
+// __match_any_sync and summed with integer __reduce_add_sync on fixed-point
+// values; the group leader adds the sum to the row, so no two lanes write the
+// same word and no atomics are needed.  The row is flushed to the block sums
+// when the warp moves past it and at the end of the segment.
+constexpr int kWin = 64;
+constexpr float kFixW = 16777216.0f;   // 2^24: weights (<= 64 per group)
+constexpr float kFixE = 4096.0f;       // 2^12: weight x energy in eV
+struct WinRow {
+    float a0[kWin], a1[kWin], e0[kWin], e1[kWin];
 };
 
-__device__ __forceinline__ void window_flush(Window &w, float *sd_n, float *sd_e, int G, PackedCounters &cnt)
+__device__ __forceinline__ void window_flush(WinRow &row, int base, float *sd_n, float *sd_e, int G,
+                                             PackedCounters &cnt)
 {
-    const int c = w.base + (int)(threadIdx.x & 31);
-    const bool on = w.base != INT32_MIN && (w.a0 != 0.f || w.a1 != 0.f || w.e0 != 0.f || w.e1 != 0.f);
-    if (on && HYB_CHECK(c >= 0 && c + 1 < G, 4, c, G)) {
-        atomicAdd(&sd_n[c], w.a0);
-        atomicAdd(&sd_n[c + 1], w.a1);
-        atomicAdd(&sd_e[c], w.e0);
-        atomicAdd(&sd_e[c + 1], w.e1);
-        track(cnt, c);
-    }
-    w.a0 = w.a1 = w.e0 = w.e1 = 0.f;
-}
-
-// Warp-collective merge of one run per lane: one pass per distinct cell among
-// the lanes, each a butterfly sum; the total lands in the register of the
-// window lane that owns the cell (the window is re-based on the first cell of
-// the warp when it has none yet, and flushed when a cell falls outside it).
-__device__ __forceinline__ void merge_runs(Window &w, Run &r, float *sd_n, float *sd_e, int G, PackedCounters &cnt)
-{
-    const bool on = r.c >= 0 && HYB_CHECK(r.c + 1 < G, 4, r.c, G);
-    unsigned todo = __ballot_sync(kFull, on);
+    __syncwarp();
     const int lane = threadIdx.x & 31;
-    while (todo) {
-        const int leader = __ffs(todo) - 1;
-        const int key = __shfl_sync(kFull, r.c, leader);
-        const bool mine = on && r.c == key;
-        float v0 = mine ? r.a0 : 0.f, v1 = mine ? r.a1 : 0.f, v2 = mine ? r.e0 : 0.f, v3 = mine ? r.e1 : 0.f;
-#pragma unroll
-        for (int d = 16; d; d >>= 1) {
-            v0 += __shfl_xor_sync(kFull, v0, d);
-            v1 += __shfl_xor_sync(kFull, v1, d);
-            v2 += __shfl_xor_sync(kFull, v2, d);
-            v3 += __shfl_xor_sync(kFull, v3, d);
+    for (int j = lane; j < kWin; j += 32) {
+        const float a0 = row.a0[j], a1 = row.a1[j], e0 = row.e0[j], e1 = row.e1[j];
+        const int c = base + j;
+        if ((a0 != 0.f || a1 != 0.f || e0 != 0.f || e1 != 0.f) && HYB_CHECK(c >= 0 && c + 1 < G, 4, c, G)) {
+            atomicAdd(&sd_n[c], a0);
+            atomicAdd(&sd_n[c + 1], a1);
+            atomicAdd(&sd_e[c], e0);
+            atomicAdd(&sd_e[c + 1], e1);
+            track(cnt, c);
         }
-        if (w.base == INT32_MIN || key < w.base || key >= w.base + 32) {
-            window_flush(w, sd_n, sd_e, G, cnt);
-            w.base = key - 8;  // particles drift both ways; keep room below
-        }
-        if (lane == key - w.base) {
-            w.a0 += v0;
-            w.a1 += v1;
-            w.e0 += v2;
-            w.e1 += v3;
-        }
-        todo &= ~__ballot_sync(kFull, mine);
+        row.a0[j] = row.a1[j] = row.e0[j] = row.e1[j] = 0.f;
     }
-    r = Run();
+    __syncwarp();
 }
 
-// Add one particle's CIC weights to the thread's run, or directly to shared
-// memory when the run holds another cell.
-__device__ __forceinline__ void add_to_run(Run &A, int c, float w0, float w1, float e0, float e1, float *sd_n,
-                                           float *sd_e, int G, PackedCounters &cnt)
+// Deposit one particle per lane (key < 0: none) into the warp's window.
+__device__ __forceinline__ void window_deposit(WinRow &row, int &base, int key, float w0, float w1, float en,
+                                               float *sd_n, float *sd_e, int G, PackedCounters &cnt)
 {
-    if (A.c < 0 || A.c == c) {
-        A.c = c;
-        A.a0 += w0, A.a1 += w1, A.e0 += e0, A.e1 += e1;
-    } else if (HYB_CHECK(c + 1 < G, 4, c, G)) {
-        atomicAdd(&sd_n[c], w0);
-        atomicAdd(&sd_n[c + 1], w1);
-        atomicAdd(&sd_e[c], e0);
-        atomicAdd(&sd_e[c + 1], e1);
-        track(cnt, c);
+    if (__any_sync(kFull, key >= 0 && (key < base || key >= base + kWin))) {
+        window_flush(row, base, sd_n, sd_e, G, cnt);
+        base = __reduce_min_sync(kFull, key >= 0 ? key : INT32_MAX) - kWin / 4;
+    }
+    // a cell still outside the window (a warp spread over many cells) goes
+    // to the block sums directly
+    if (key >= 0 && (key < base || key >= base + kWin)) {
+        if (HYB_CHECK(key + 1 < G, 4, key, G)) {
+            atomicAdd(&sd_n[key], w0);
+            atomicAdd(&sd_n[key + 1], w1);
+            atomicAdd(&sd_e[key], w0 * en);
+            atomicAdd(&sd_e[key + 1], w1 * en);
+            track(cnt, key);
+        }
+        key = -1;
+    }
+    const bool on = key >= 0;
+    const unsigned peers = __match_any_sync(kFull, key);
+    const unsigned q0 = on ? __float2uint_rn(w0 * kFixW) : 0u;
+    const unsigned q1 = on ? __float2uint_rn(w1 * kFixW) : 0u;
+    const unsigned q2 = on ? __float2uint_rn(w0 * en * kFixE) : 0u;
+    const unsigned q3 = on ? __float2uint_rn(w1 * en * kFixE) : 0u;
+    const unsigned s0 = __reduce_add_sync(peers, q0);
+    const unsigned s1 = __reduce_add_sync(peers, q1);
+    const unsigned s2 = __reduce_add_sync(peers, q2);
+    const unsigned s3 = __reduce_add_sync(peers, q3);
+    if (on && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+        const int j = key - base;
+        row.a0[j] += (float)s0 * (1.f / kFixW);
+        row.a1[j] += (float)s1 * (1.f / kFixW);
+        row.e0[j] += (float)s2 * (1.f / kFixE);
+        row.e1[j] += (float)s3 * (1.f / kFixE);
     }
 }
 
@@ -276,7 +269,10 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const int64_t per = (((b - a) + nwarps - 1) / nwarps + 32 * kVec - 1) / (32 * kVec) * (32 * kVec);
     const int64_t wa = a + per * wid;
     const int64_t wb = wa + per < b ? wa + per : b;
-    Window win;
+    WinRow &row = reinterpret_cast<WinRow *>(s_eedf + ((nb + 1 + 3) & ~3))[wid];
+    int wbase = INT32_MIN / 2;
+    for (int j = lane; j < kWin; j += 32) row.a0[j] = row.a1[j] = row.e0[j] = row.e1[j] = 0.f;
+    __syncwarp();
     for (int64_t base = wa; base < wb; base += 32 * kVec) {
         const int64_t i0 = base + (int64_t)lane * kVec;
         const bool full = i0 + kVec <= wb;
@@ -311,7 +307,6 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
 
-        Run runA;
 #pragma unroll
         for (int k = 0; k < kVec; ++k) {
             int c = cc[k];
@@ -340,9 +335,8 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
             // CIC charge assignment and energy moment, accumulated in a run
             const float en = half_m_q * (vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
+            window_deposit(row, wbase, alive ? c : -1, 1.f - o, o, MODE == 0 ? en : 0.f, sd_n, sd_e, G, cnt);
             if (alive) {
-                const float w0 = 1.f - o, w1 = o;
-                add_to_run(runA, c, w0, w1, MODE == 0 ? w0 * en : 0.f, MODE == 0 ? w1 * en : 0.f, sd_n, sd_e, G, cnt);
                 if (MODE == 0) {
                     int bin = (int)(en * bin_inv);
                     if (bin > nb || bin < 0 || !(en >= 0.f)) bin = nb;  // overflow bin (also NaN)
@@ -430,7 +424,6 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             cc[k] = alive ? c : kDeadCell;
             oo[k] = o;
         }
-        merge_runs(win, runA, sd_n, sd_e, G, cnt);
         if (MODE == 0) {
             if (full) {
                 *reinterpret_cast<int2 *>(P.c + i0) = make_int2(cc[0], cc[1]);
@@ -452,7 +445,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
     }
-    window_flush(win, sd_n, sd_e, G, cnt);
+    window_flush(row, wbase, sd_n, sd_e, G, cnt);
 }
 
 // ------------------------------------------------------------------ FP64
@@ -986,6 +979,8 @@ int electron_blocks_per_sm(int precision, size_t smem)
 size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins)
 {
     const size_t el = precision == HYB_FP32_SPLIT ? 4 : 8;
+    if (precision == HYB_FP32_SPLIT)  // plus one deposit window row per warp
+        return 3 * el * (size_t)max_nodes + 4 * (size_t)((eedf_bins + 1 + 3) & ~3) + sizeof(WinRow) * (kBlock / 32) + 16;
     return 3 * el * (size_t)max_nodes + 4 * (size_t)(eedf_bins + 1) + 16;
 }
 
