@@ -164,76 +164,79 @@ __device__ __forceinline__ void track(PackedCounters &cnt, int c)
     cnt.cmax = max(cnt.cmax, c);
 }
 
-// Per-warp deposit window: a private shared-memory row of kWin cells (CIC
-// weights to the two nodes of the cell and the energy moment) starting at
-// cell `base`.  Within a warp, lanes in the same cell are grouped with
-// __match_any_sync and summed with integer __reduce_add_sync on fixed-point
-// values; the group leader adds the sum to the row, so no two lanes write the
-// same word and no atomics are needed.  The row is flushed to the block sums
-// when the warp moves past it and at the end of the segment.
-constexpr int kWin = 64;
-constexpr float kFixW = 16777216.0f;   // 2^24: weights (<= 64 per group)
-constexpr float kFixE = 4096.0f;       // 2^12: weight x energy in eV
-struct WinRow {
-    float a0[kWin], a1[kWin], e0[kWin], e1[kWin];
+// Per-warp deposit window held in registers: lane j accumulates the CIC sums
+// (weights to the two nodes of the cell, and the energy moment) of cell
+// base + j.  For each particle slot the warp finds the range [kmin, kmax] of
+// its lanes' cells (small once particles are sorted by cell) and, per cell of
+// that range, sums the lanes' fixed-point contributions with a full-warp
+// integer __reduce_add_sync; the owning lane adds the total.  Shared memory is
+// touched only when the window slides (and for warps spread over many cells).
+constexpr float kFixW = 16777216.0f;   // 2^24: CIC weights, 32 lanes sum < 2^29
+constexpr float kFixE = 65536.0f;      // 2^16: weight x energy (eV) up to 2048 per lane
+constexpr float kMaxFixE = 2048.0f;
+constexpr int kSpread = 8;             // widest cell range merged by reductions
+
+struct Win {
+    int base = INT32_MIN / 2;
+    float a0 = 0.f, a1 = 0.f, e0 = 0.f, e1 = 0.f;
 };
 
-__device__ __forceinline__ void window_flush(WinRow &row, int base, float *sd_n, float *sd_e, int G,
-                                             PackedCounters &cnt)
+__device__ __forceinline__ void add_direct(float *sd_n, float *sd_e, int c, float w0, float w1, float e0, float e1,
+                                           int G, PackedCounters &cnt)
 {
-    __syncwarp();
-    const int lane = threadIdx.x & 31;
-    for (int j = lane; j < kWin; j += 32) {
-        const float a0 = row.a0[j], a1 = row.a1[j], e0 = row.e0[j], e1 = row.e1[j];
-        const int c = base + j;
-        if ((a0 != 0.f || a1 != 0.f || e0 != 0.f || e1 != 0.f) && HYB_CHECK(c >= 0 && c + 1 < G, 4, c, G)) {
-            atomicAdd(&sd_n[c], a0);
-            atomicAdd(&sd_n[c + 1], a1);
-            atomicAdd(&sd_e[c], e0);
-            atomicAdd(&sd_e[c + 1], e1);
-            track(cnt, c);
-        }
-        row.a0[j] = row.a1[j] = row.e0[j] = row.e1[j] = 0.f;
+    if (HYB_CHECK(c >= 0 && c + 1 < G, 4, c, G)) {
+        atomicAdd(&sd_n[c], w0);
+        atomicAdd(&sd_n[c + 1], w1);
+        atomicAdd(&sd_e[c], e0);
+        atomicAdd(&sd_e[c + 1], e1);
+        track(cnt, c);
     }
-    __syncwarp();
 }
 
-// Deposit one particle per lane (key < 0: none) into the warp's window.
-__device__ __forceinline__ void window_deposit(WinRow &row, int &base, int key, float w0, float w1, float en,
-                                               float *sd_n, float *sd_e, int G, PackedCounters &cnt)
+__device__ __forceinline__ void window_flush(Win &w, float *sd_n, float *sd_e, int G, PackedCounters &cnt)
 {
-    if (__any_sync(kFull, key >= 0 && (key < base || key >= base + kWin))) {
-        window_flush(row, base, sd_n, sd_e, G, cnt);
-        base = __reduce_min_sync(kFull, key >= 0 ? key : INT32_MAX) - kWin / 4;
-    }
-    // a cell still outside the window (a warp spread over many cells) goes
-    // to the block sums directly
-    if (key >= 0 && (key < base || key >= base + kWin)) {
-        if (HYB_CHECK(key + 1 < G, 4, key, G)) {
-            atomicAdd(&sd_n[key], w0);
-            atomicAdd(&sd_n[key + 1], w1);
-            atomicAdd(&sd_e[key], w0 * en);
-            atomicAdd(&sd_e[key + 1], w1 * en);
-            track(cnt, key);
-        }
+    if (w.a0 != 0.f || w.a1 != 0.f || w.e0 != 0.f || w.e1 != 0.f)
+        add_direct(sd_n, sd_e, w.base + (int)(threadIdx.x & 31), w.a0, w.a1, w.e0, w.e1, G, cnt);
+    w.a0 = w.a1 = w.e0 = w.e1 = 0.f;
+}
+
+// Deposit one particle per lane (key < 0: none) through the warp's window.
+__device__ __forceinline__ void window_deposit(Win &w, int key, float w0, float w1, float en, float *sd_n,
+                                               float *sd_e, int G, PackedCounters &cnt)
+{
+    if (key >= 0 && !(en < kMaxFixE)) {  // outside the fixed-point range
+        add_direct(sd_n, sd_e, key, w0, w1, w0 * en, w1 * en, G, cnt);
         key = -1;
     }
     const bool on = key >= 0;
-    const unsigned peers = __match_any_sync(kFull, key);
+    const int kmin = __reduce_min_sync(kFull, on ? key : INT32_MAX);
+    if (kmin == INT32_MAX) return;
+    const int kmax = __reduce_max_sync(kFull, on ? key : -1);
+    if (kmax - kmin >= kSpread) {
+        if (on) add_direct(sd_n, sd_e, key, w0, w1, w0 * en, w1 * en, G, cnt);
+        return;
+    }
+    if (kmin < w.base || kmax >= w.base + 32) {
+        window_flush(w, sd_n, sd_e, G, cnt);
+        w.base = kmin - (32 - kSpread) / 2;
+    }
     const unsigned q0 = on ? __float2uint_rn(w0 * kFixW) : 0u;
     const unsigned q1 = on ? __float2uint_rn(w1 * kFixW) : 0u;
     const unsigned q2 = on ? __float2uint_rn(w0 * en * kFixE) : 0u;
     const unsigned q3 = on ? __float2uint_rn(w1 * en * kFixE) : 0u;
-    const unsigned s0 = __reduce_add_sync(peers, q0);
-    const unsigned s1 = __reduce_add_sync(peers, q1);
-    const unsigned s2 = __reduce_add_sync(peers, q2);
-    const unsigned s3 = __reduce_add_sync(peers, q3);
-    if (on && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
-        const int j = key - base;
-        row.a0[j] += (float)s0 * (1.f / kFixW);
-        row.a1[j] += (float)s1 * (1.f / kFixW);
-        row.e0[j] += (float)s2 * (1.f / kFixE);
-        row.e1[j] += (float)s3 * (1.f / kFixE);
+    const int lane = threadIdx.x & 31;
+    for (int k = kmin; k <= kmax; ++k) {
+        const bool sel = key == k;
+        const unsigned s0 = __reduce_add_sync(kFull, sel ? q0 : 0u);
+        const unsigned s1 = __reduce_add_sync(kFull, sel ? q1 : 0u);
+        const unsigned s2 = __reduce_add_sync(kFull, sel ? q2 : 0u);
+        const unsigned s3 = __reduce_add_sync(kFull, sel ? q3 : 0u);
+        if (lane == k - w.base) {
+            w.a0 += (float)s0 * (1.f / kFixW);
+            w.a1 += (float)s1 * (1.f / kFixW);
+            w.e0 += (float)s2 * (1.f / kFixE);
+            w.e1 += (float)s3 * (1.f / kFixE);
+        }
     }
 }
 
@@ -269,10 +272,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const int64_t per = (((b - a) + nwarps - 1) / nwarps + 32 * kVec - 1) / (32 * kVec) * (32 * kVec);
     const int64_t wa = a + per * wid;
     const int64_t wb = wa + per < b ? wa + per : b;
-    WinRow &row = reinterpret_cast<WinRow *>(s_eedf + ((nb + 1 + 3) & ~3))[wid];
-    int wbase = INT32_MIN / 2;
-    for (int j = lane; j < kWin; j += 32) row.a0[j] = row.a1[j] = row.e0[j] = row.e1[j] = 0.f;
-    __syncwarp();
+    Win win;
     for (int64_t base = wa; base < wb; base += 32 * kVec) {
         const int64_t i0 = base + (int64_t)lane * kVec;
         const bool full = i0 + kVec <= wb;
@@ -335,7 +335,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
             // CIC charge assignment and energy moment, accumulated in a run
             const float en = half_m_q * (vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
-            window_deposit(row, wbase, alive ? c : -1, 1.f - o, o, MODE == 0 ? en : 0.f, sd_n, sd_e, G, cnt);
+            window_deposit(win, alive ? c : -1, 1.f - o, o, MODE == 0 ? en : 0.f, sd_n, sd_e, G, cnt);
             if (alive) {
                 if (MODE == 0) {
                     int bin = (int)(en * bin_inv);
@@ -445,7 +445,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
     }
-    window_flush(row, wbase, sd_n, sd_e, G, cnt);
+    window_flush(win, sd_n, sd_e, G, cnt);
 }
 
 // ------------------------------------------------------------------ FP64
@@ -979,8 +979,6 @@ int electron_blocks_per_sm(int precision, size_t smem)
 size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins)
 {
     const size_t el = precision == HYB_FP32_SPLIT ? 4 : 8;
-    if (precision == HYB_FP32_SPLIT)  // plus one deposit window row per warp
-        return 3 * el * (size_t)max_nodes + 4 * (size_t)((eedf_bins + 1 + 3) & ~3) + sizeof(WinRow) * (kBlock / 32) + 16;
     return 3 * el * (size_t)max_nodes + 4 * (size_t)(eedf_bins + 1) + 16;
 }
 
