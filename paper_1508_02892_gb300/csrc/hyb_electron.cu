@@ -156,7 +156,7 @@ __device__ __forceinline__ void append_children<double>(InstDev *K, const PartBu
 // particles are sorted by cell), so a shared-memory atomic serves many
 // particles.
 
-constexpr int kVec = 2;
+constexpr int kVec = 2;  // the collision pass below picks between two slots
 
 __device__ __forceinline__ void track(PackedCounters &cnt, int c)
 {
@@ -200,40 +200,65 @@ __device__ __forceinline__ void window_flush(Win &w, float *sd_n, float *sd_e, i
     w.a0 = w.a1 = w.e0 = w.e1 = 0.f;
 }
 
-// Deposit one particle per lane (key < 0: none) through the warp's window.
-__device__ __forceinline__ void window_deposit(Win &w, int key, float w0, float w1, float en, float *sd_n,
-                                               float *sd_e, int G, PackedCounters &cnt)
+// Deposit kVec particles per lane (key < 0: none) through the warp's window.
+// Per cell k of the warp's range: n = number of particles in k (ballot
+// popcounts), a1 and the two energy moments by integer reductions; a0 = n - a1.
+__device__ __forceinline__ void window_deposit(Win &w, int (&key)[kVec], const float (&o)[kVec],
+                                               const float (&en)[kVec], float *sd_n, float *sd_e, int G,
+                                               PackedCounters &cnt)
 {
-    if (key >= 0 && !(en < kMaxFixE)) {  // outside the fixed-point range
-        add_direct(sd_n, sd_e, key, w0, w1, w0 * en, w1 * en, G, cnt);
-        key = -1;
+    int lo = INT32_MAX, hi = -1;
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) {
+        if (key[k] >= 0 && !(en[k] < kMaxFixE)) {  // outside the fixed-point range
+            add_direct(sd_n, sd_e, key[k], 1.f - o[k], o[k], (1.f - o[k]) * en[k], o[k] * en[k], G, cnt);
+            key[k] = -1;
+        }
+        if (key[k] >= 0) {
+            lo = min(lo, key[k]);
+            hi = max(hi, key[k]);
+        }
     }
-    const bool on = key >= 0;
-    const int kmin = __reduce_min_sync(kFull, on ? key : INT32_MAX);
+    const int kmin = __reduce_min_sync(kFull, lo);
     if (kmin == INT32_MAX) return;
-    const int kmax = __reduce_max_sync(kFull, on ? key : -1);
+    const int kmax = __reduce_max_sync(kFull, hi);
     if (kmax - kmin >= kSpread) {
-        if (on) add_direct(sd_n, sd_e, key, w0, w1, w0 * en, w1 * en, G, cnt);
+#pragma unroll
+        for (int k = 0; k < kVec; ++k)
+            if (key[k] >= 0)
+                add_direct(sd_n, sd_e, key[k], 1.f - o[k], o[k], (1.f - o[k]) * en[k], o[k] * en[k], G, cnt);
         return;
     }
     if (kmin < w.base || kmax >= w.base + 32) {
         window_flush(w, sd_n, sd_e, G, cnt);
         w.base = kmin - (32 - kSpread) / 2;
     }
-    const unsigned q0 = on ? __float2uint_rn(w0 * kFixW) : 0u;
-    const unsigned q1 = on ? __float2uint_rn(w1 * kFixW) : 0u;
-    const unsigned q2 = on ? __float2uint_rn(w0 * en * kFixE) : 0u;
-    const unsigned q3 = on ? __float2uint_rn(w1 * en * kFixE) : 0u;
+    unsigned q1[kVec], q2[kVec], q3[kVec];
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) {
+        const bool on = key[k] >= 0;
+        q1[k] = on ? __float2uint_rn(o[k] * kFixW) : 0u;
+        q2[k] = on ? __float2uint_rn((1.f - o[k]) * en[k] * kFixE) : 0u;
+        q3[k] = on ? __float2uint_rn(o[k] * en[k] * kFixE) : 0u;
+    }
     const int lane = threadIdx.x & 31;
-    for (int k = kmin; k <= kmax; ++k) {
-        const bool sel = key == k;
-        const unsigned s0 = __reduce_add_sync(kFull, sel ? q0 : 0u);
-        const unsigned s1 = __reduce_add_sync(kFull, sel ? q1 : 0u);
-        const unsigned s2 = __reduce_add_sync(kFull, sel ? q2 : 0u);
-        const unsigned s3 = __reduce_add_sync(kFull, sel ? q3 : 0u);
-        if (lane == k - w.base) {
-            w.a0 += (float)s0 * (1.f / kFixW);
-            w.a1 += (float)s1 * (1.f / kFixW);
+    for (int c = kmin; c <= kmax; ++c) {
+        unsigned n = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+        for (int k = 0; k < kVec; ++k) {
+            const bool sel = key[k] == c;
+            n += __popc(__ballot_sync(kFull, sel));
+            s1 += sel ? q1[k] : 0u;
+            s2 += sel ? q2[k] : 0u;
+            s3 += sel ? q3[k] : 0u;
+        }
+        s1 = __reduce_add_sync(kFull, s1);
+        s2 = __reduce_add_sync(kFull, s2);
+        s3 = __reduce_add_sync(kFull, s3);
+        if (lane == c - w.base) {
+            const float a1 = (float)s1 * (1.f / kFixW);
+            w.a0 += (float)n - a1;
+            w.a1 += a1;
             w.e0 += (float)s2 * (1.f / kFixE);
             w.e1 += (float)s3 * (1.f / kFixE);
         }
@@ -307,6 +332,10 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
 
+        int dkey[kVec];
+        float dfo[kVec], den[kVec];
+        unsigned coll = 0u;      // 2 bits per particle: 1 elastic, 2 excitation, 3 ionization
+        uint2 ru[kVec];          // direction draws of the colliding particles
 #pragma unroll
         for (int k = 0; k < kVec; ++k) {
             int c = cc[k];
@@ -335,7 +364,9 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
             // CIC charge assignment and energy moment, accumulated in a run
             const float en = half_m_q * (vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
-            window_deposit(win, alive ? c : -1, 1.f - o, o, MODE == 0 ? en : 0.f, sd_n, sd_e, G, cnt);
+            dkey[k] = alive ? c : -1;
+            dfo[k] = o;
+            den[k] = MODE == 0 ? en : 0.f;
             if (alive) {
                 if (MODE == 0) {
                     int bin = (int)(en * bin_inv);
@@ -344,11 +375,9 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 }
             }
 
-            bool has_child = false;
-            float cvx = 0.f, cvy = 0.f, cvz = 0.f;
-            uint64_t cid = 0;
             if (MODE == 0 && alive) {
-                // modified null-collision method: every particle draws R1 < P_max
+                // modified null-collision method: every particle draws R1 < P_max;
+                // the process is the first k with R2 nu_max < sum_{i<=k} nu_i
                 const uint4 r = draw(ids[k], step, sl, sh, 0);
                 if (u01f(r.x) < pmax) {
                     const float speed = sqrtf(vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
@@ -373,56 +402,85 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                     const float t0 = s_el * speed, t1 = t0 + s_ex * speed, t2 = t1 + s_iz * speed;
                     const float r2 = u01f(r.y);
                     if (r2 < t2) {
-                        const float ct = 1.f - 2.f * u01f(r.z);
-                        const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
-                        float sn, cs;
-                        __sincosf(6.283185307179586f * u01f(r.w), &sn, &cs);
-                        const float dx = st * cs, dy = st * sn, dz = ct;
-                        float sp;
-                        if (r2 < t0) {  // elastic, lab-frame isotropic
-                            const float cchi = (vx[k] * dx + vy[k] * dy + vz[k] * dz) / speed;
-                            sp = speed * sqrtf(1.f - two_mM * (1.f - cchi));
-                            cnt.el_exc += 1u;
-                        } else if (r2 < t1) {  // excitation
-                            sp = sqrtf(two_q_m * (en - e_exc));
-                            cnt.el_exc += 1u << 16;
-                        } else {  // ionization: split E - E_iz, eject a new electron
-                            const uint4 r1 = draw(ids[k], step, sl, sh, 1);
-                            const float de = en - e_iz;
-                            const float e_ej = u01f(r1.x) * de;
-                            sp = sqrtf(two_q_m * (de - e_ej));
-                            const float cj = 1.f - 2.f * u01f(r1.y);
-                            const float sj = sqrtf(fmaxf(0.f, 1.f - cj * cj));
-                            float snj, csj;
-                            __sincosf(6.283185307179586f * u01f(r1.z), &snj, &csj);
-                            const float spj = sqrtf(two_q_m * e_ej);
-                            cvx = spj * sj * csj;
-                            cvy = spj * sj * snj;
-                            cvz = spj * cj;
-                            cid = child_id(ids[k], step);
-                            has_child = true;
-                            cnt.iz_nul += 1u;
-                            if (HYB_CHECK(c + 1 < G, 4, c, G)) {
-                                atomicAdd(&sd_iz[c], 1.f - o);
-                                atomicAdd(&sd_iz[c + 1], o);
-                                track(cnt, c);
-                            }
-                        }
-                        vx[k] = sp * dx;
-                        vy[k] = sp * dy;
-                        vz[k] = sp * dz;
+                        const unsigned kind = r2 < t0 ? 1u : (r2 < t1 ? 2u : 3u);
+                        coll |= kind << (2 * k);
+                        ru[k] = make_uint2(r.z, r.w);
                     } else {
                         cnt.iz_nul += 1u << 16;
                     }
                 }
             }
-            if (MODE == 0) {
-                unsigned ovf = 0;
-                append_children<float>(K, P, capacity, has_child, c, o, 0.0, cvx, cvy, cvz, cid, ovf);
-                cnt.push_ovf |= ovf << 16;
-            }
             cc[k] = alive ? c : kDeadCell;
             oo[k] = o;
+        }
+        window_deposit(win, dkey, dfo, den, sd_n, sd_e, G, cnt);
+        if (MODE == 0) {
+            // real collisions of the warp, one particle per lane per pass:
+            // isotropic new direction; elastic energy loss (2m/M)(1 - cos chi),
+            // excitation loss, or ionization with a child electron (Sec. II.D)
+            while (__any_sync(kFull, coll != 0u)) {
+                const int k = (coll & 3u) ? 0 : 1;
+                const unsigned kind = (coll >> (2 * k)) & 3u;
+                bool has_child = false;
+                float cvx = 0.f, cvy = 0.f, cvz = 0.f;
+                uint64_t cid = 0;
+                int ck = 0;
+                float ok = 0.f;
+                if (kind) {
+                    const float px = k ? vx[1] : vx[0], py = k ? vy[1] : vy[0], pz = k ? vz[1] : vz[0];
+                    const uint2 rr = k ? ru[1] : ru[0];
+                    const uint64_t pid = k ? ids[1] : ids[0];
+                    ck = k ? cc[1] : cc[0];
+                    ok = k ? oo[1] : oo[0];
+                    const float v2 = px * px + py * py + pz * pz;
+                    const float en = half_m_q * v2;
+                    const float ct = 1.f - 2.f * u01f(rr.x);
+                    const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
+                    float sn, cs;
+                    __sincosf(6.283185307179586f * u01f(rr.y), &sn, &cs);
+                    const float dx = st * cs, dy = st * sn, dz = ct;
+                    float sp;
+                    if (kind == 1u) {  // elastic, lab-frame isotropic
+                        const float rs = rsqrtf(v2);
+                        const float cchi = (px * dx + py * dy + pz * dz) * rs;
+                        sp = v2 * rs * sqrtf(1.f - two_mM * (1.f - cchi));
+                        cnt.el_exc += 1u;
+                    } else if (kind == 2u) {  // excitation
+                        sp = sqrtf(two_q_m * (en - e_exc));
+                        cnt.el_exc += 1u << 16;
+                    } else {  // ionization: split E - E_iz, eject a new electron
+                        const uint4 r1 = draw(pid, step, sl, sh, 1);
+                        const float de = en - e_iz;
+                        const float e_ej = u01f(r1.x) * de;
+                        sp = sqrtf(two_q_m * (de - e_ej));
+                        const float cj = 1.f - 2.f * u01f(r1.y);
+                        const float sj = sqrtf(fmaxf(0.f, 1.f - cj * cj));
+                        float snj, csj;
+                        __sincosf(6.283185307179586f * u01f(r1.z), &snj, &csj);
+                        const float spj = sqrtf(two_q_m * e_ej);
+                        cvx = spj * sj * csj;
+                        cvy = spj * sj * snj;
+                        cvz = spj * cj;
+                        cid = child_id(pid, step);
+                        has_child = true;
+                        cnt.iz_nul += 1u;
+                        if (HYB_CHECK(ck >= 0 && ck + 1 < G, 4, ck, G)) {
+                            atomicAdd(&sd_iz[ck], 1.f - ok);
+                            atomicAdd(&sd_iz[ck + 1], ok);
+                            track(cnt, ck);
+                        }
+                    }
+                    if (k) {
+                        vx[1] = sp * dx, vy[1] = sp * dy, vz[1] = sp * dz;
+                    } else {
+                        vx[0] = sp * dx, vy[0] = sp * dy, vz[0] = sp * dz;
+                    }
+                }
+                unsigned ovf = 0;
+                append_children<float>(K, P, capacity, has_child, ck, ok, 0.0, cvx, cvy, cvz, cid, ovf);
+                cnt.push_ovf |= ovf << 16;
+                coll &= ~(3u << (2 * k));
+            }
         }
         if (MODE == 0) {
             if (full) {
