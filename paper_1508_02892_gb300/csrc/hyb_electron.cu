@@ -158,111 +158,69 @@ __device__ __forceinline__ void append_children<double>(InstDev *K, const PartBu
 
 constexpr int kVec = 2;  // the collision pass below picks between two slots
 
-__device__ __forceinline__ void track(PackedCounters &cnt, int c)
-{
-    cnt.cmin = min(cnt.cmin, c);
-    cnt.cmax = max(cnt.cmax, c);
-}
+// Per-warp deposit rows in shared memory: for kWin cells starting at `base`,
+// 32-bit fixed-point sums of the particle count, the CIC weight to the upper
+// node, and the energy moments to both nodes (weight to the lower node = count
+// minus upper weight).  Every particle adds with native integer shared
+// atomics; the warp flushes its row into the FP64 global sums every
+// kFlushIters iterations (which bounds the fixed-point range), when the warp
+// moves past the row, and at the end of the segment.
+constexpr int kWin = 64;
+constexpr int kFlushIters = 16;        // <= 16 * 32 * kVec = 1024 particles per cell between flushes
+constexpr float kFixW = 1048576.0f;    // 2^20: CIC weight, 1024 x 2^20 = 2^30
+constexpr float kFixE = 1024.0f;       // 2^10: weight x energy (eV), 1024 x 2047 x 2^10 < 2^31
+constexpr float kMaxFixE = 2047.0f;
 
-// Per-warp deposit window held in registers: lane j accumulates the CIC sums
-// (weights to the two nodes of the cell, and the energy moment) of cell
-// base + j.  For each particle slot the warp finds the range [kmin, kmax] of
-// its lanes' cells (small once particles are sorted by cell) and, per cell of
-// that range, sums the lanes' fixed-point contributions with a full-warp
-// integer __reduce_add_sync; the owning lane adds the total.  Shared memory is
-// touched only when the window slides (and for warps spread over many cells).
-constexpr float kFixW = 16777216.0f;   // 2^24: CIC weights, 32 lanes sum < 2^29
-constexpr float kFixE = 65536.0f;      // 2^16: weight x energy (eV) up to 2048 per lane
-constexpr float kMaxFixE = 2048.0f;
-constexpr int kSpread = 8;             // widest cell range merged by reductions
-
-struct Win {
-    int base = INT32_MIN / 2;
-    float a0 = 0.f, a1 = 0.f, e0 = 0.f, e1 = 0.f;
+struct WarpRow {
+    unsigned n[kWin], a1[kWin], e0[kWin], e1[kWin];
 };
 
-__device__ __forceinline__ void add_direct(float *sd_n, float *sd_e, int c, float w0, float w1, float e0, float e1,
-                                           int G, PackedCounters &cnt)
+__device__ __forceinline__ void add_global(InstDev *K, int c, double w0, double w1, double e0, double e1, int G)
 {
     if (HYB_CHECK(c >= 0 && c + 1 < G, 4, c, G)) {
-        atomicAdd(&sd_n[c], w0);
-        atomicAdd(&sd_n[c + 1], w1);
-        atomicAdd(&sd_e[c], e0);
-        atomicAdd(&sd_e[c + 1], e1);
-        track(cnt, c);
+        atomicAdd(&K->dep_n[c], w0);
+        atomicAdd(&K->dep_n[c + 1], w1);
+        atomicAdd(&K->dep_e[c], e0);
+        atomicAdd(&K->dep_e[c + 1], e1);
     }
 }
 
-__device__ __forceinline__ void window_flush(Win &w, float *sd_n, float *sd_e, int G, PackedCounters &cnt)
+__device__ __forceinline__ void row_flush(WarpRow &row, int base, InstDev *K, int G)
 {
-    if (w.a0 != 0.f || w.a1 != 0.f || w.e0 != 0.f || w.e1 != 0.f)
-        add_direct(sd_n, sd_e, w.base + (int)(threadIdx.x & 31), w.a0, w.a1, w.e0, w.e1, G, cnt);
-    w.a0 = w.a1 = w.e0 = w.e1 = 0.f;
-}
-
-// Deposit kVec particles per lane (key < 0: none) through the warp's window.
-// Per cell k of the warp's range: n = number of particles in k (ballot
-// popcounts), a1 and the two energy moments by integer reductions; a0 = n - a1.
-__device__ __forceinline__ void window_deposit(Win &w, int (&key)[kVec], const float (&o)[kVec],
-                                               const float (&en)[kVec], float *sd_n, float *sd_e, int G,
-                                               PackedCounters &cnt)
-{
-    int lo = INT32_MAX, hi = -1;
-#pragma unroll
-    for (int k = 0; k < kVec; ++k) {
-        if (key[k] >= 0 && !(en[k] < kMaxFixE)) {  // outside the fixed-point range
-            add_direct(sd_n, sd_e, key[k], 1.f - o[k], o[k], (1.f - o[k]) * en[k], o[k] * en[k], G, cnt);
-            key[k] = -1;
-        }
-        if (key[k] >= 0) {
-            lo = min(lo, key[k]);
-            hi = max(hi, key[k]);
+    __syncwarp();
+    for (int j = threadIdx.x & 31; j < kWin; j += 32) {
+        const unsigned n = row.n[j];
+        if (n) {
+            const double a1 = (double)row.a1[j] * (1.0 / kFixW);
+            add_global(K, base + j, (double)n - a1, a1, (double)row.e0[j] * (1.0 / kFixE),
+                       (double)row.e1[j] * (1.0 / kFixE), G);
+            row.n[j] = row.a1[j] = row.e0[j] = row.e1[j] = 0u;
         }
     }
-    const int kmin = __reduce_min_sync(kFull, lo);
-    if (kmin == INT32_MAX) return;
-    const int kmax = __reduce_max_sync(kFull, hi);
-    if (kmax - kmin >= kSpread) {
-#pragma unroll
-        for (int k = 0; k < kVec; ++k)
-            if (key[k] >= 0)
-                add_direct(sd_n, sd_e, key[k], 1.f - o[k], o[k], (1.f - o[k]) * en[k], o[k] * en[k], G, cnt);
+    __syncwarp();
+}
+
+// Deposit one particle per lane (key < 0: none); warp-collective.
+__device__ __forceinline__ void row_deposit(WarpRow &row, int &base, InstDev *K, int key, float o, float en, int G)
+{
+    if (key >= 0 && !(en < kMaxFixE)) {  // outside the fixed-point range
+        add_global(K, key, 1.0 - o, o, (1.0 - o) * en, (double)o * en, G);
+        key = -1;
+    }
+    if (__any_sync(kFull, key >= 0 && (key < base || key >= base + kWin))) {
+        row_flush(row, base, K, G);
+        base = __reduce_min_sync(kFull, key >= 0 ? key : INT32_MAX) - kWin / 4;
+    }
+    if (key < 0) return;
+    const int j = key - base;
+    if (j < 0 || j >= kWin) {  // a warp spread over more than the row
+        add_global(K, key, 1.0 - o, o, (1.0 - o) * en, (double)o * en, G);
         return;
     }
-    if (kmin < w.base || kmax >= w.base + 32) {
-        window_flush(w, sd_n, sd_e, G, cnt);
-        w.base = kmin - (32 - kSpread) / 2;
-    }
-    unsigned q1[kVec], q2[kVec], q3[kVec];
-#pragma unroll
-    for (int k = 0; k < kVec; ++k) {
-        const bool on = key[k] >= 0;
-        q1[k] = on ? __float2uint_rn(o[k] * kFixW) : 0u;
-        q2[k] = on ? __float2uint_rn((1.f - o[k]) * en[k] * kFixE) : 0u;
-        q3[k] = on ? __float2uint_rn(o[k] * en[k] * kFixE) : 0u;
-    }
-    const int lane = threadIdx.x & 31;
-    for (int c = kmin; c <= kmax; ++c) {
-        unsigned n = 0, s1 = 0, s2 = 0, s3 = 0;
-#pragma unroll
-        for (int k = 0; k < kVec; ++k) {
-            const bool sel = key[k] == c;
-            n += __popc(__ballot_sync(kFull, sel));
-            s1 += sel ? q1[k] : 0u;
-            s2 += sel ? q2[k] : 0u;
-            s3 += sel ? q3[k] : 0u;
-        }
-        s1 = __reduce_add_sync(kFull, s1);
-        s2 = __reduce_add_sync(kFull, s2);
-        s3 = __reduce_add_sync(kFull, s3);
-        if (lane == c - w.base) {
-            const float a1 = (float)s1 * (1.f / kFixW);
-            w.a0 += (float)n - a1;
-            w.a1 += a1;
-            w.e0 += (float)s2 * (1.f / kFixE);
-            w.e1 += (float)s3 * (1.f / kFixE);
-        }
-    }
+    atomicAdd(&row.n[j], 1u);
+    atomicAdd(&row.a1[j], __float2uint_rn(o * kFixW));
+    atomicAdd(&row.e0[j], __float2uint_rn((1.f - o) * en * kFixE));
+    atomicAdd(&row.e1[j], __float2uint_rn(o * en * kFixE));
 }
 
 template <int MODE>
@@ -283,13 +241,15 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const float inv_dlog = K->f_inv_dlog, e_exc = K->f_e_exc, e_iz = K->f_e_iz, two_mM = K->f_two_mM;
     const float bin_inv = K->f_bin_inv;
 
-    float *sd_n = reinterpret_cast<float *>(smem);
-    float *sd_e = sd_n + G;
-    float *sd_iz = sd_e + G;
-    unsigned *s_eedf = reinterpret_cast<unsigned *>(sd_iz + G);
+    // shared memory: EEDF histogram, then one deposit row per warp
+    unsigned *s_eedf = reinterpret_cast<unsigned *>(smem);
+    WarpRow *rows = reinterpret_cast<WarpRow *>(smem + 4 * (((nb + 1) + 3) & ~3));
     if (!HYB_CHECK(b <= capacity && a >= 0 && (a & (kVec - 1)) == 0, 10, b, capacity)) b = a;
-    for (int j = threadIdx.x; j < 3 * G; j += blockDim.x) sd_n[j] = 0.f;
     for (int j = threadIdx.x; j <= nb; j += blockDim.x) s_eedf[j] = 0u;
+    {
+        unsigned *r = reinterpret_cast<unsigned *>(rows);
+        for (int j = threadIdx.x; j < 4 * kWin * (int)(blockDim.x >> 5); j += blockDim.x) r[j] = 0u;
+    }
     __syncthreads();
 
     // each warp sweeps a contiguous part of [a, b) in groups of 32 * kVec
@@ -297,7 +257,9 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const int64_t per = (((b - a) + nwarps - 1) / nwarps + 32 * kVec - 1) / (32 * kVec) * (32 * kVec);
     const int64_t wa = a + per * wid;
     const int64_t wb = wa + per < b ? wa + per : b;
-    Win win;
+    WarpRow &row = rows[wid];
+    int rbase = INT32_MIN / 2;
+    int iter = 0;
     for (int64_t base = wa; base < wb; base += 32 * kVec) {
         const int64_t i0 = base + (int64_t)lane * kVec;
         const bool full = i0 + kVec <= wb;
@@ -332,8 +294,6 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
 
-        int dkey[kVec];
-        float dfo[kVec], den[kVec];
         unsigned coll = 0u;      // 2 bits per particle: 1 elastic, 2 excitation, 3 ionization
         uint2 ru[kVec];          // direction draws of the colliding particles
 #pragma unroll
@@ -364,9 +324,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
             // CIC charge assignment and energy moment, accumulated in a run
             const float en = half_m_q * (vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
-            dkey[k] = alive ? c : -1;
-            dfo[k] = o;
-            den[k] = MODE == 0 ? en : 0.f;
+            row_deposit(row, rbase, K, alive ? c : -1, o, MODE == 0 ? en : 0.f, G);
             if (alive) {
                 if (MODE == 0) {
                     int bin = (int)(en * bin_inv);
@@ -413,7 +371,10 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             cc[k] = alive ? c : kDeadCell;
             oo[k] = o;
         }
-        window_deposit(win, dkey, dfo, den, sd_n, sd_e, G, cnt);
+        if (++iter == kFlushIters) {
+            row_flush(row, rbase, K, G);
+            iter = 0;
+        }
         if (MODE == 0) {
             // real collisions of the warp, one particle per lane per pass:
             // isotropic new direction; elastic energy loss (2m/M)(1 - cos chi),
@@ -465,9 +426,8 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                         has_child = true;
                         cnt.iz_nul += 1u;
                         if (HYB_CHECK(ck >= 0 && ck + 1 < G, 4, ck, G)) {
-                            atomicAdd(&sd_iz[ck], 1.f - ok);
-                            atomicAdd(&sd_iz[ck + 1], ok);
-                            track(cnt, ck);
+                            atomicAdd(&K->s_iz[ck], 1.0 - ok);
+                            atomicAdd(&K->s_iz[ck + 1], (double)ok);
                         }
                     }
                     if (k) {
@@ -503,7 +463,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
     }
-    window_flush(win, sd_n, sd_e, G, cnt);
+    row_flush(row, rbase, K, G);
 }
 
 // ------------------------------------------------------------------ FP64
@@ -694,10 +654,44 @@ __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *sm
 }
 
 // Reduce the per-thread counters, then flush the block-private sums over the
-// touched node range into the global FP64 sums.  S is the shared sum type:
-// float (split mode) or double (FP64 mode).
-__device__ __forceinline__ double sum_value(float q) { return (double)q; }
+// touched node range into the global FP64 sums (FP64 mode).
 __device__ __forceinline__ double sum_value(double q) { return q; }
+
+// Split mode: the node sums went to global memory already; flush the EEDF
+// histogram and the counters.
+template <int MODE>
+__device__ void flush_segment_split(InstDev *K, unsigned char *smem, const SegCounters &cnt)
+{
+    __shared__ unsigned s_ctr2[8];
+    if (threadIdx.x < 8) s_ctr2[threadIdx.x] = 0u;
+    __syncthreads();
+    const unsigned v[8] = {cnt.el, cnt.exc, cnt.iz, cnt.nul, cnt.loss0, cnt.loss1, cnt.overflow, cnt.push};
+    unsigned tot[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tot[k] = __reduce_add_sync(kFull, v[k]);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (tot[k]) atomicAdd(&s_ctr2[k], tot[k]);
+    }
+    __syncthreads();
+    if (MODE == 0) {
+        const int nb = K->eedf_bins;
+        const unsigned *s_eedf = reinterpret_cast<const unsigned *>(smem);
+        for (int j = threadIdx.x; j <= nb; j += blockDim.x)
+            if (s_eedf[j]) atomicAdd(&K->eedf[j], (unsigned long long)s_eedf[j]);
+        if (threadIdx.x == 0) {
+            const int map[6] = {C_EL, C_EXC, C_IZ, C_NULL, C_LOSS0, C_LOSS1};
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                if (s_ctr2[k]) atomicAdd(&K->ctr[map[k]], (unsigned long long)s_ctr2[k]);
+            if (s_ctr2[2]) atomicAdd(&K->ctr[C_BIRTH_IZ], (unsigned long long)s_ctr2[2]);
+            if (s_ctr2[6]) atomicOr(&K->status, (unsigned)HYB_STATUS_CAPACITY);
+            if (s_ctr2[7]) atomicAdd(&K->ctr[C_PUSH], (unsigned long long)s_ctr2[7]);
+        }
+    }
+    __syncthreads();
+}
 
 template <typename S, int MODE>
 __device__ void flush_segment(InstDev *K, unsigned char *smem, const SegCounters &cnt)
@@ -804,7 +798,7 @@ __global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 3 : 2) k_elec
             PackedCounters pc;
             segment_split<MODE>(K, a, b, smem, pc);
             pc.unpack(cnt);
-            flush_segment<float, MODE>(K, smem, cnt);
+            flush_segment_split<MODE>(K, smem, cnt);
         } else {
             segment_fp64<MODE>(K, a, b, smem, cnt);
             flush_segment<double, MODE>(K, smem, cnt);
@@ -1036,7 +1030,9 @@ int electron_blocks_per_sm(int precision, size_t smem)
 
 size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins)
 {
-    const size_t el = precision == HYB_FP32_SPLIT ? 4 : 8;
+    if (precision == HYB_FP32_SPLIT)  // EEDF histogram and one deposit row per warp
+        return 4 * (size_t)(((eedf_bins + 1) + 3) & ~3) + sizeof(WarpRow) * (kBlock / 32) + 16;
+    const size_t el = 8;
     return 3 * el * (size_t)max_nodes + 4 * (size_t)(eedf_bins + 1) + 16;
 }
 
