@@ -110,8 +110,8 @@ int validate(const hyb_params *p)
             return fail(HYB_ERR_ARG, "negative cross section");
     if (p->e_exc_ev < 0 || p->e_iz_ev < 0) return fail(HYB_ERR_ARG, "negative threshold");
     if (p->ion_model != HYB_ION_DD_CONST) {
-        if (!p->tab_eon_td || !p->tab_mu || !p->tab_nu || p->n_tab < 2)
-            return fail(HYB_ERR_ARG, "ion transport tables missing");
+        if (!p->tab_eon_td || !p->tab_mu || !p->tab_nu || p->n_tab < 2 || p->n_tab > 256)
+            return fail(HYB_ERR_ARG, "ion transport tables missing or longer than 256");
         if (!finite_all(p->tab_eon_td, p->n_tab) || !finite_all(p->tab_mu, p->n_tab) ||
             !finite_all(p->tab_nu, p->n_tab))
             return fail(HYB_ERR_NONFINITE, "non-finite ion transport table entry");
@@ -434,7 +434,7 @@ int launch_step(hyb_batch *b, int k)
     if (b->profiling && (rc = record(b, b->ev[3 * k]))) return rc;
     CK(launch_electron_step(b->d_inst, b->max_inst, b->d_prefix, b->precision, b->cfg, b->stream));
     if (b->profiling && (rc = record(b, b->ev[3 * k + 1]))) return rc;
-    CK(launch_field(b->d_inst, b->max_inst, b->d_prefix, b->d_ticket, b->stream));
+    CK(launch_field(b->d_inst, b->max_inst, b->d_prefix, b->d_ticket, b->precision == HYB_FP32_SPLIT, b->stream));
     if (b->profiling && (rc = record(b, b->ev[3 * k + 2]))) return rc;
     return HYB_OK;
 }
@@ -516,7 +516,7 @@ int reinit_slot(hyb_batch *b, int slot, bool sort)
     InstDev *K = &b->d_inst[slot];
     CK(launch_prefix_one(K, b->d_prefix1, b->stream));
     CK(launch_deposit_init(K, 1, b->d_prefix1, b->precision, b->cfg, b->stream));
-    CK(launch_field(K, 1, b->d_prefix1, b->d_ticket1, b->stream));
+    CK(launch_field(K, 1, b->d_prefix1, b->d_ticket1, b->precision == HYB_FP32_SPLIT, b->stream));
     if (sort) {
         CK(launch_prefix_one(K, b->d_prefix1, b->stream));
         CK(launch_sort(K, 1, b->d_prefix1, b->precision, b->cfg, b->stream));

@@ -122,7 +122,54 @@ struct Fluid {
 
 __device__ __forceinline__ double node_volume(int j, int G, double dz) { return (j == 0 || j == G - 1) ? 0.5 * dz : dz; }
 
-__device__ void field_body(InstDev *K, double *sm, Red &red)
+// FP32 copy of the transport coefficients for the split mode: the table is
+// staged in shared memory and mu(E), T_i, nu(u) are evaluated in FP32; the
+// state (n, Gamma) and every difference of neighbouring values stay FP64.
+constexpr int kMaxTab = 256;
+
+__device__ __forceinline__ float interp_linf(const float *tab, int n, int cx, int cy, float v)
+{
+    if (v <= tab[cx]) return tab[cy];
+    if (v >= tab[4 * (n - 1) + cx]) return tab[4 * (n - 1) + cy];
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tab[4 * mid + cx] <= v)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const float f = __fdividef(v - tab[4 * lo + cx], tab[4 * (lo + 1) + cx] - tab[4 * lo + cx]);
+    return tab[4 * lo + cy] + f * (tab[4 * (lo + 1) + cy] - tab[4 * lo + cy]);
+}
+
+struct FluidF {
+    int model, n_tab;
+    const float *tab;  // shared memory
+    float mu_const, inv_ngas_td, kT, tfac;
+
+    __device__ float mobility(float e_abs) const
+    {
+        if (model == HYB_ION_DD_CONST) return mu_const;
+        return interp_linf(tab, n_tab, 0, 1, e_abs * inv_ngas_td);
+    }
+    __device__ float temp(float mu, float e_abs) const
+    {
+        if (model == HYB_ION_DD_CONST) return kT;
+        const float ud = mu * e_abs;
+        return kT + tfac * ud * ud;
+    }
+    __device__ float exch(float u_abs) const { return interp_linf(tab, n_tab, 3, 2, u_abs); }
+    __device__ double wall(int w, double n, double E) const
+    {
+        const bool into = w == 0 ? (E < 0.0) : (E > 0.0);
+        if (!into) return 0.0;
+        return (double)mobility(fabsf((float)E)) * n * E;
+    }
+};
+
+template <bool FAST>
+__device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
 {
     const int G = K->G;
     const int T = blockDim.x;
@@ -153,7 +200,105 @@ __device__ void field_body(InstDev *K, double *sm, Red &red)
 
     const Fluid F{K->ion_model, K->n_tab, K->tab, K->mu_const, K->ngas, K->kT_gas, K->m_ion, K->m_gas};
     double *gfin = s_g;
-    if (!init) {
+    if (FAST && !init) {
+        // ------------------------------------ ion fluid, FP32 coefficients
+        for (int j = t; j < 4 * K->n_tab; j += T) s_tabf[j] = (float)K->tab[j];
+        __syncthreads();
+        const double mi = K->m_ion, mn = K->m_gas;
+        const FluidF FF{K->ion_model, K->n_tab, s_tabf, (float)K->mu_const, (float)(1e21 / K->ngas),
+                        (float)K->kT_gas, (float)((mi + mn) / (5.0 * mi + 3.0 * mn) * mn)};
+        const double h = dt / (2.0 * dz);
+        const double inv2dz = 1.0 / (2.0 * dz);
+        if (K->ion_model == HYB_ION_FULL) {
+            const double qdt_m = kQe * dt / mi, h_m = h / mi;
+            const float hdt = (float)(0.5 * dt);
+            for (int j = j0; j < j1; ++j) {
+                const double nj = s_ni[j];
+                const float A = nj >= K->n_floor ? (float)s_g[j] / (float)nj : 0.f;
+                s_A[j] = h * (double)A;  // h Gamma/n, the advection coefficient
+                const float ea = fabsf((float)s_E[j]);
+                s_x[j] = nj * (double)FF.temp(FF.mobility(ea), ea);
+            }
+            __syncthreads();
+            float rmax = 0.f;
+            for (int j = j0; j < j1; ++j) {
+                if (j == 0 || j == G - 1) continue;
+                const float nu = FF.exch(fabsf((float)(s_A[j] / h)));
+                const float ib = 1.f / (1.f + nu * hdt);
+                s_d[j] = s_g[j] * (double)(1.f - nu * hdt) + qdt_m * s_ni[j] * s_E[j] - h_m * (s_x[j + 1] - s_x[j - 1]);
+                s_ib[j] = (double)ib;
+                rmax = fmaxf(rmax, (fabsf((float)s_A[j - 1]) + fabsf((float)s_A[j + 1])) * ib);
+            }
+            const double r = block_max((double)rmax, red);
+            if (t == 0) {
+                const double g0 = FF.wall(0, s_ni[0], s_E[0]);
+                const double gN = FF.wall(1, s_ni[G - 1], s_E[G - 1]);
+                s_g[0] = g0;
+                s_x[0] = g0;
+                s_g[G - 1] = gN;
+                s_x[G - 1] = gN;
+                if (r >= 0.5) atomicOr(&K->status, (unsigned)HYB_STATUS_UNSTABLE);
+            }
+            int iters = 1;
+            if (r > 1e-300) iters = (int)ceil(-41.58883083359672 / log(r));
+            iters = iters < 1 ? 1 : (iters > 64 ? 64 : iters);
+            __syncthreads();
+            double *X = s_g, *Y = s_x;
+            for (int it = 0; it < iters; ++it) {
+                for (int j = j0; j < j1; ++j) {
+                    if (j == 0 || j == G - 1) continue;
+                    Y[j] = (s_d[j] + s_A[j - 1] * X[j - 1] - s_A[j + 1] * X[j + 1]) * s_ib[j];
+                }
+                __syncthreads();
+                double *tmp = X;
+                X = Y;
+                Y = tmp;
+            }
+            gfin = X;
+        } else {
+            for (int j = j0; j < j1; ++j) {
+                if (j == 0) {
+                    s_x[j] = FF.wall(0, s_ni[0], s_E[0]);
+                } else if (j == G - 1) {
+                    s_x[j] = FF.wall(1, s_ni[G - 1], s_E[G - 1]);
+                } else {
+                    const float ea = fabsf((float)s_E[j]);
+                    const float mu = FF.mobility(ea);
+                    const float D = mu * FF.temp(mu, ea) * (float)(1.0 / kQe);
+                    s_x[j] = (double)mu * s_ni[j] * s_E[j] - (double)D * ((s_ni[j + 1] - s_ni[j - 1]) * inv2dz);
+                }
+            }
+            __syncthreads();
+            gfin = s_x;
+        }
+        unsigned long long clamps = 0;
+        const double c_in = dt * inv2dz, c_wall = dt / dz;
+        const double gs_in = w / (dz * dt), gs_wall = w / (0.5 * dz * dt);
+        for (int j = j0; j < j1; ++j) {
+            const bool wall = j == 0 || j == G - 1;
+            const double gs = K->s_iz[j] * (wall ? gs_wall : gs_in);
+            double nn;
+            if (j == 0)
+                nn = s_ni[0] - c_wall * (gfin[1] - gfin[0]) + dt * gs;
+            else if (j == G - 1)
+                nn = s_ni[G - 1] - c_wall * (gfin[G - 1] - gfin[G - 2]) + dt * gs;
+            else
+                nn = s_ni[j] - c_in * (gfin[j + 1] - gfin[j - 1]) + dt * gs;
+            if (nn < 0.0) {
+                nn = 0.0;
+                ++clamps;
+            }
+            s_ni[j] = nn;
+            K->ni[j] = nn;
+            K->gam[j] = gfin[j];
+            K->gsrc[j] = gs;
+            K->acc_ni[j] += nn;
+            K->acc_gi[j] += gfin[j];
+        }
+        if (clamps) atomicAdd(&red.count, clamps);
+        __syncthreads();
+    }
+    if (!FAST && !init) {
         // ---------------------------------------------------------- ion fluid
         if (K->ion_model == HYB_ION_FULL) {
             // Eq. 2.3: nu at u^n = Gamma^{n-1/2}/n^n, advection semi-implicit
@@ -415,13 +560,16 @@ __device__ void field_body(InstDev *K, double *sm, Red &red)
     }
 }
 
+template <bool FAST>
 __global__ void __launch_bounds__(kFieldThreads) k_field(InstDev *insts, int n_max, int64_t *prefix, unsigned *ticket)
 {
     extern __shared__ __align__(16) double sm[];
     __shared__ Red red;
+    __shared__ float s_tabf[FAST ? 4 * kMaxTab : 1];
     InstDev *K = &insts[blockIdx.x];
     const bool run = K->active || K->init_pending;
-    if (run && HYB_CHECK(K->G >= 3 && K->G <= kMaxNodes, 20, K->G, kMaxNodes)) field_body(K, sm, red);
+    if (run && HYB_CHECK(K->G >= 3 && K->G <= kMaxNodes && K->n_tab <= kMaxTab, 20, K->G, kMaxNodes))
+        field_body<FAST>(K, sm, red, s_tabf);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -452,12 +600,17 @@ void read_checks_field(unsigned long long out[3])
 
 void configure_field_kernel()
 {
-    cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)field_smem_bytes(kMaxNodes));
+    cudaFuncSetAttribute(k_field<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)field_smem_bytes(kMaxNodes));
+    cudaFuncSetAttribute(k_field<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)field_smem_bytes(kMaxNodes));
 }
 
-cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, cudaStream_t s)
+// `fast`: FP32 transport coefficients (split mode); FP64 throughout otherwise.
+cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, bool fast, cudaStream_t s)
 {
-    k_field<<<n_max, kFieldThreads, field_smem_bytes(kMaxNodes), s>>>(inst, n_max, prefix, ticket);
+    if (fast)
+        k_field<true><<<n_max, kFieldThreads, field_smem_bytes(kMaxNodes), s>>>(inst, n_max, prefix, ticket);
+    else
+        k_field<false><<<n_max, kFieldThreads, field_smem_bytes(kMaxNodes), s>>>(inst, n_max, prefix, ticket);
     return cudaGetLastError();
 }
 

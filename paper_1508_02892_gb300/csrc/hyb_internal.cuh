@@ -159,7 +159,7 @@ cudaError_t launch_set_active(InstDev *inst, int active, int64_t target_step, cu
 size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins);
 
 // field kernel (hyb_field.cu)
-cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned int *ticket, cudaStream_t s);
+cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned int *ticket, bool fast, cudaStream_t s);
 size_t field_smem_bytes(int max_nodes);
 void configure_field_kernel();
 
