@@ -20,8 +20,12 @@
 using namespace hyb;
 
 namespace {
-
 thread_local std::string g_err;
+}
+
+void hyb::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
+namespace {
 
 int fail(int code, const char *fmt, ...)
 {

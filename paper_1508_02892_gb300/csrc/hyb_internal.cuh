@@ -167,6 +167,9 @@ void configure_field_kernel();
 void read_checks_electron(unsigned long long out[3]);
 void read_checks_field(unsigned long long out[3]);
 
+// sets the message hyb_last_error() returns (hyb_api.cu)
+void set_last_error(const char *msg);
+
 // one-time kernel attributes and occupancy (hyb_electron.cu)
 void configure_kernels();
 int electron_blocks_per_sm(int precision, size_t smem);

@@ -105,6 +105,8 @@ EXPORTS = {
     "hyb_batch_profile": (C.c_int, [C.c_void_p, C.POINTER(Profile), C.c_int32]),
     "hyb_discharge_batch": (C.c_void_p, [C.c_void_p]),
     "hyb_debug_checks": (C.c_int, [C.POINTER(C.c_uint64)]),
+    "hyb_field_from_particles_noalloc": (C.c_int, [C.POINTER(Params), C.c_int64, C.c_void_p, C.c_void_p,
+                                                   C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hyb_last_error": (C.c_char_p, []),
 }
 
