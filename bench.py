@@ -109,7 +109,7 @@ def traffic_per_push():
             for line in f:
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
-                    kv[k.strip()] = v.strip()
+                    kv[k.strip()] = (v.split() or [""])[0]
         if kv.get("kernel_source_sha256_16") != kernel_hash():
             return None
         return float(kv["dram_bytes_per_push"])

@@ -965,15 +965,10 @@ __global__ void k_sort_finish(InstDev *insts, const int64_t *prefix)
     }
 }
 
-__global__ void k_prefix(InstDev *insts, int n_max, int64_t *prefix)
+__global__ void __launch_bounds__(HYB_MAX_INSTANCES) k_prefix(InstDev *insts, int n_max, int64_t *prefix)
 {
-    if (threadIdx.x != 0) return;
-    int64_t acc = 0;
-    prefix[0] = 0;
-    for (int i = 0; i < n_max; ++i) {
-        if (insts[i].active) acc += chunks_of(insts[i].n_slots_step);
-        prefix[i + 1] = acc;
-    }
+    __shared__ int64_t s_buf[HYB_MAX_INSTANCES];
+    block_chunk_prefix(insts, n_max, prefix, s_buf);
 }
 
 // prefix over one instance that is being (re)initialised
@@ -1073,13 +1068,13 @@ cudaError_t launch_sort(InstDev *inst, int n_max, int64_t *prefix, int precision
         k_sort_pass<HYB_FP64, 1><<<cfg.grid, kBlock, 0, s>>>(inst, n_max, prefix);
     }
     k_sort_finish<<<n_max, 256, 0, s>>>(inst, prefix);
-    k_prefix<<<1, 32, 0, s>>>(inst, n_max, prefix);
+    k_prefix<<<1, HYB_MAX_INSTANCES, 0, s>>>(inst, n_max, prefix);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prefix(InstDev *inst, int n_max, int64_t *prefix, cudaStream_t s)
 {
-    k_prefix<<<1, 32, 0, s>>>(inst, n_max, prefix);
+    k_prefix<<<1, HYB_MAX_INSTANCES, 0, s>>>(inst, n_max, prefix);
     return cudaGetLastError();
 }
 

@@ -570,21 +570,19 @@ __global__ void __launch_bounds__(kFieldThreads) k_field(InstDev *insts, int n_m
     const bool run = K->active || K->init_pending;
     if (run && HYB_CHECK(K->G >= 3 && K->G <= kMaxNodes && K->n_tab <= kMaxTab, 20, K->G, kMaxNodes))
         field_body<FAST>(K, sm, red, s_tabf);
+    // the last block to finish computes the chunk prefix of the next step
+    __shared__ bool s_last;
+    __shared__ int64_t s_buf[HYB_MAX_INSTANCES];
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned tk = atomicAdd(ticket, 1u);
-        if (tk == gridDim.x - 1) {
-            __threadfence();
-            int64_t acc = 0;
-            prefix[0] = 0;
-            for (int i = 0; i < n_max; ++i) {
-                const volatile InstDev *Ki = &insts[i];
-                if (Ki->active) acc += chunks_of(Ki->n_slots_step);
-                prefix[i + 1] = acc;
-            }
-            *ticket = 0u;
-        }
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last) {
+        block_chunk_prefix(insts, n_max, prefix, s_buf);
+        if (threadIdx.x == 0) *ticket = 0u;
     }
 }
 

@@ -141,6 +141,29 @@ __host__ __device__ __forceinline__ uint64_t see_id(int wall, uint32_t step, uin
 // are instance i's chunks of kChunk slots; each block takes a contiguous run
 // of chunks.
 
+// Chunk prefix over the running instances, computed by all threads of one
+// block (blockDim >= n_max <= HYB_MAX_INSTANCES); s_buf holds n_max int64.
+// Reads other blocks' writes, so the caller must order them (kernel boundary
+// or fence + ticket).
+__device__ __forceinline__ void block_chunk_prefix(InstDev *insts, int n_max, int64_t *prefix, int64_t *s_buf)
+{
+    const int t = threadIdx.x;
+    if (t < n_max) {
+        const volatile InstDev *K = &insts[t];
+        s_buf[t] = K->active ? chunks_of(K->n_slots_step) : 0;
+    }
+    __syncthreads();
+    for (int d = 1; d < n_max; d <<= 1) {
+        int64_t v = 0;
+        if (t < n_max && t >= d) v = s_buf[t - d];
+        __syncthreads();
+        if (t < n_max) s_buf[t] += v;
+        __syncthreads();
+    }
+    if (t == 0) prefix[0] = 0;
+    if (t < n_max) prefix[t + 1] = s_buf[t];
+}
+
 struct LaunchCfg {
     int grid, block;
     size_t smem;
