@@ -123,7 +123,7 @@ def workload(rank=0, n_inst=64, scale=1.0):
     return inst
 
 
-def cpu_baseline(params_list, budget_s=12.0, window=3):
+def cpu_baseline(params_list, budget_s=12.0, window=6):
     """The FP64 oracle as it stands, single thread, on the first discharges of
     the workload, `window` steps each, until `budget_s` of stepping."""
     import oracle
@@ -236,11 +236,17 @@ def run_ours(args):
     def pushes():
         return sum(b.counters(s)["pushes"] for s in slots)
 
+    # launch configuration picked by the library's autotuner on this workload
+    # (its trial chunks are real steps of the runs and count as warm-up)
+    if args.lanes > 0:
+        tuning = b.set_tuning(lanes=args.lanes)
+    elif args.tune_steps > 0:
+        tuning = b.autotune(args.tune_steps)
+    else:
+        tuning = b.tuning()
     for _ in range(args.warmup):
         b.advance(CHUNK)
     torch.cuda.synchronize()
-    b.set_profiling(True)
-    b.profile(reset=True)
     prof0 = b.profile()
     p0 = pushes()
     clocks = Clocks(local)
@@ -259,9 +265,8 @@ def run_ours(args):
     clk = clocks.stop()
     lat = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
     ms_local = sum(lat)
-    prof = b.profile()
+    prof1 = b.profile()
     n_local = pushes() - p0
-    b.set_profiling(False)
     if world > 1:
         t = torch.tensor([ms_local, float(n_local)], dtype=torch.float64, device="cuda")
         mx = t.clone()
@@ -273,16 +278,32 @@ def run_ours(args):
         ms_tot, n_tot = ms_local, float(n_local)
     value = n_tot / (ms_tot / 1e3)
 
-    # roofline of the dominant kernel (electron step)
-    n_launch = prof["n_electron"] - prof0["n_electron"]
-    ms_e = prof["ms_electron"] - prof0["ms_electron"]
-    per_launch = n_local / max(n_launch, 1)
+    # roofline of the dominant kernel (electron step), timed alone: one lane,
+    # CUDA events around every kernel of a few more chunks
+    b.set_tuning(lanes=1)
+    b.set_profiling(True)
+    b.advance(CHUNK)
+    torch.cuda.synchronize()
+    b.profile(reset=True)
+    q0 = pushes()
+    rchunks = max(1, min(args.steps, 5))
+    for _ in range(rchunks):
+        flush.zero_()
+        b.advance(CHUNK)
+    torch.cuda.synchronize()
+    prof = b.profile()
+    n_roof = pushes() - q0
+    b.set_profiling(False)
+    b.set_tuning(lanes=tuning["lanes"])
+    n_launch = prof["n_electron"]
+    ms_e = prof["ms_electron"]
+    per_launch = n_roof / max(n_launch, 1)
     avg_ms = ms_e / max(n_launch, 1)
     peak, peak_kind = peaks()
     achieved = BYTES_SPLIT * per_launch / (avg_ms / 1e3) / 1e9
     tpp = traffic_per_push()
-    shares = {"electron": ms_e, "field": prof["ms_field"] - prof0["ms_field"],
-              "sort": prof["ms_sort"] - prof0["ms_sort"]}
+    shares = {"electron": ms_e, "field": prof["ms_field"], "sort": prof["ms_sort"],
+              "chunks": rchunks, "lanes": 1}
 
     # end to end through the public API: admit from host parameters, chunks
     # with a host read of every discharge's moments, evict
@@ -291,6 +312,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b2 = hybrid.Batch(args.instances, hybrid.HYB_FP32_SPLIT, stream=stream.cuda_stream)
+        b2.set_tuning(lanes=tuning["lanes"], sort_interval=tuning["sort_interval"],
+                      blocks_per_sm=tuning["blocks_per_sm"])
         s2 = [b2.admit(p) for p in params]
         h2d = 0
         for p in params:
@@ -330,6 +353,7 @@ def run_ours(args):
                                f"1e4-2e6 electrons log-uniform, 100-400 V, DD/full ions), FP32 split, "
                                f"{CHUNK}-step CUDA-graph chunks", "instances": args.instances,
                    "initial_particles_per_gpu": total_particles, "chunk_steps": CHUNK,
+                   "tuning": {k: tuning[k] for k in ("lanes", "sort_interval", "blocks_per_sm")},
                    "l2": "256 MB buffer written between timed chunks; particle store > L2"},
         "p50_ms_per_chunk": lat_sorted[len(lat) // 2], "p99_ms_per_chunk": lat_sorted[min(len(lat) - 1,
                                                                                            int(0.99 * len(lat)))],
@@ -337,9 +361,11 @@ def run_ours(args):
                      "peak_kind": peak_kind,
                      "traffic": (tpp * per_launch if tpp is not None else None),
                      "kernel": "k_electron<FP32_SPLIT>", "bytes_per_unit": BYTES_SPLIT,
-                     "units_per_launch": per_launch, "avg_launch_ms": avg_ms},
+                     "units_per_launch": per_launch, "avg_launch_ms": avg_ms,
+                     "timed": f"electron kernel alone (1 lane), CUDA events around each launch of "
+                              f"{rchunks} chunks after the headline region"},
         "kernel_ms": shares,
-        "gpu_launches": prof["kernel_launches"] - prof0["kernel_launches"],
+        "gpu_launches": prof1["kernel_launches"] - prof0["kernel_launches"],
         "clocks": clk,
     }
     if fp64:
@@ -366,6 +392,8 @@ def main():
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--tune-steps", type=int, default=200)
+    ap.add_argument("--lanes", type=int, default=0, help="fixed lane count instead of the autotuner's")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -242,6 +242,37 @@ typedef struct hyb_profile {
 int hyb_batch_set_profiling(hyb_batch *b, int32_t on);
 int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset);
 
+/* Launch configuration of a batch.  It decides how the work is laid out on
+ * the GPU, not what is computed (beyond the order of floating-point sums):
+ *   lanes          the slots are split into this many contiguous groups, each
+ *                  advanced by its own chain of launches; inside a captured
+ *                  chunk the chains run as parallel graph branches, so the
+ *                  field kernels of one group overlap the electron kernels of
+ *                  the others (1..8 and at most max_instances; a batch starts
+ *                  with min(4, max_instances));
+ *   sort_interval  steps between cell sorts (1..1000, default 20);
+ *   blocks_per_sm  electron-kernel blocks per SM (0: the occupancy limit).
+ * rate is filled by hyb_batch_autotune with the particle-steps/s it measured
+ * for the returned choice, and is ignored by hyb_batch_set_tuning. */
+typedef struct hyb_tuning {
+    int32_t lanes;
+    int32_t sort_interval;
+    int32_t blocks_per_sm;
+    double rate;
+} hyb_tuning;
+
+int hyb_batch_get_tuning(hyb_batch *b, hyb_tuning *out);
+/* Waits for the GPU; the next chunk re-captures its graph. */
+int hyb_batch_set_tuning(hyb_batch *b, const hyb_tuning *t);
+
+/* Time candidate configurations on the batch's own running discharges and
+ * keep the fastest: lanes in {1, 2, 4, 8}, then the sort interval in
+ * {10, 20, 50}, then the electron grid at the occupancy limit or twice it.
+ * Each trial advances every running discharge by one untimed chunk and then
+ * by trial_steps rounded up to whole chunks (100 steps): those are real steps
+ * of the runs.  Profiling must be off.  *chosen may be NULL. */
+int hyb_batch_autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *chosen);
+
 /* The batch behind a single discharge (for profiling and statistics). */
 hyb_batch *hyb_discharge_batch(hyb_discharge *h);
 

@@ -46,6 +46,8 @@ int fail(int code, const char *fmt, ...)
 
 constexpr int kDefaultSort = 20;
 constexpr int kElectronBlock = 256;
+constexpr int kMaxLanes = 8;
+constexpr int kDefaultLanes = 4;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -215,6 +217,7 @@ void derive(const hyb_params &p, InstDev &K, std::vector<double> &xs, std::vecto
     K.capacity = capacity_of(p);
     K.L = p.gap_m;
     K.dz = p.gap_m / p.n_cells;
+    K.inv_gm1 = 1.0 / (double)p.n_cells;
     K.dt = p.dt_s;
     K.ngas = p.pressure_pa / (kKb * p.gas_temp_k);
     K.w = p.weight > 0 ? p.weight : (p.n_particles > 0 ? p.n0_m3 * p.gap_m / (double)p.n_particles : 0.0);
@@ -318,16 +321,27 @@ void bind_pointers(const hyb_params &p, const Layout &L, char *base, InstDev &K)
 
 }  // namespace
 
+// Lanes: the slots are split into `lanes` contiguous groups, each advanced by
+// its own chain of launches (electron step, field, periodic sort) with its own
+// chunk prefix and field ticket.  Inside a captured chunk the chains are
+// parallel branches, so that the field kernels of one lane (one CTA per
+// instance, bound by that SM's FP64 rate) run beside the electron kernels of
+// the others instead of leaving most SMs idle.
 struct hyb_batch {
     int max_inst = 0;
     int precision = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     InstDev *d_inst = nullptr;
-    int64_t *d_prefix = nullptr;
+    int64_t *d_prefix = nullptr;   // kMaxLanes x (max_inst + 1)
     int64_t *d_prefix1 = nullptr;
-    unsigned *d_ticket = nullptr;
+    unsigned *d_ticket = nullptr;  // kMaxLanes field tickets, then the single-instance one
     unsigned *d_ticket1 = nullptr;
+    int lanes = 1, per_lane = 1;
+    cudaStream_t lstream[kMaxLanes] = {};  // lane k > 0 (lane 0 uses `stream`)
+    cudaEvent_t ev_fork = nullptr, ev_join[kMaxLanes] = {};
+    int blocks_per_sm = 0;                 // electron grid = SMs x this (0: occupancy limit)
+    int occ_per_sm = 0;
     std::vector<Slot> slots;
     int64_t hbm_cap = 0, hbm_used = 0;
     int max_nodes = 0, max_bins = 0;
@@ -341,7 +355,7 @@ struct hyb_batch {
     int64_t launches = 0, steps = 0;
     bool profiling = false;
     bool pending = false;         // events of the last graph launch not read yet
-    std::vector<cudaEvent_t> ev;  // 3 per step + 2 per sort of a chunk
+    std::vector<cudaEvent_t> ev;  // per lane: 3 per step + 2 per sort of a chunk
     double ms[3] = {0, 0, 0};
     int64_t nt[3] = {0, 0, 0};
 };
@@ -392,8 +406,24 @@ int configure(hyb_batch *b, int nodes, int bins)
     b->cfg.smem = electron_smem_bytes(b->precision, b->max_nodes, b->max_bins);
     int per_sm = electron_blocks_per_sm(b->precision, b->cfg.smem);
     if (per_sm < 1) return fail(HYB_ERR_ARG, "grid too large for the electron kernel's shared memory");
-    b->cfg.grid = b->num_sms * per_sm;
+    b->occ_per_sm = per_sm;
+    b->cfg.grid = b->num_sms * (b->blocks_per_sm > 0 ? b->blocks_per_sm : per_sm);
     return drop_graph(b);
+}
+
+int lane_first(const hyb_batch *b, int k) { return k * b->per_lane; }
+int lane_count(const hyb_batch *b, int k) { return std::max(0, std::min(b->per_lane, b->max_inst - k * b->per_lane)); }
+int64_t *lane_prefix(const hyb_batch *b, int k) { return b->d_prefix + (size_t)k * (b->max_inst + 1); }
+unsigned *lane_ticket(const hyb_batch *b, int k) { return b->d_ticket + k; }
+cudaStream_t lane_stream(const hyb_batch *b, int k) { return k == 0 ? b->stream : b->lstream[k]; }
+InstDev *lane_inst(const hyb_batch *b, int k) { return b->d_inst + lane_first(b, k); }
+
+// Chunk prefixes of every lane (after an admission, eviction or relayout).
+int prefix_all(hyb_batch *b)
+{
+    for (int k = 0; k < b->lanes; ++k)
+        if (lane_count(b, k) > 0) CK(launch_prefix(lane_inst(b, k), lane_count(b, k), lane_prefix(b, k), b->stream));
+    return HYB_OK;
 }
 
 constexpr int kSortKernels = 5;
@@ -406,10 +436,15 @@ int chunk_len(const hyb_batch *b)
     return k * m;
 }
 
-int ensure_events(hyb_batch *b)
+size_t events_per_lane(const hyb_batch *b)
 {
     const int GL = chunk_len(b);
-    const size_t need = 3 * (size_t)GL + 2 * (size_t)(GL / b->sort_interval);
+    return 3 * (size_t)GL + 2 * (size_t)(GL / b->sort_interval);
+}
+
+int ensure_events(hyb_batch *b)
+{
+    const size_t need = events_per_lane(b) * (size_t)b->lanes;
     while (b->ev.size() < need) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
@@ -418,61 +453,72 @@ int ensure_events(hyb_batch *b)
     return HYB_OK;
 }
 
-// Timing event on the batch stream; inside a stream capture it must become an
+// Timing event on a lane's stream; inside a stream capture it must become an
 // event-record node of the graph (cudaEventRecordExternal).
-int record(hyb_batch *b, cudaEvent_t e)
+int record(cudaStream_t s, cudaEvent_t e)
 {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
-    CK(cudaStreamIsCapturing(b->stream, &st));
+    CK(cudaStreamIsCapturing(s, &st));
     if (st == cudaStreamCaptureStatusActive)
-        CK(cudaEventRecordWithFlags(e, b->stream, cudaEventRecordExternal));
+        CK(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
     else
-        CK(cudaEventRecord(e, b->stream));
+        CK(cudaEventRecord(e, s));
     return HYB_OK;
 }
 
-// One step; with profiling, events 3k..3k+2 bracket the two kernels.
-int launch_step(hyb_batch *b, int k)
+cudaEvent_t lane_event(const hyb_batch *b, int lane, size_t i) { return b->ev[(size_t)lane * events_per_lane(b) + i]; }
+
+// One step of one lane on stream s; with profiling, the lane's events
+// 3k..3k+2 bracket the two kernels.
+int launch_step(hyb_batch *b, int k, int lane, cudaStream_t s)
 {
     int rc;
-    if (b->profiling && (rc = record(b, b->ev[3 * k]))) return rc;
-    CK(launch_electron_step(b->d_inst, b->max_inst, b->d_prefix, b->precision, b->cfg, b->stream));
-    if (b->profiling && (rc = record(b, b->ev[3 * k + 1]))) return rc;
-    CK(launch_field(b->d_inst, b->max_inst, b->d_prefix, b->d_ticket, b->precision == HYB_FP32_SPLIT, b->stream));
-    if (b->profiling && (rc = record(b, b->ev[3 * k + 2]))) return rc;
+    const int n = lane_count(b, lane);
+    if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k)))) return rc;
+    CK(launch_electron_step(lane_inst(b, lane), n, lane_prefix(b, lane), b->precision, b->cfg, s));
+    if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k + 1)))) return rc;
+    CK(launch_field(lane_inst(b, lane), n, lane_prefix(b, lane), lane_ticket(b, lane), b->precision == HYB_FP32_SPLIT,
+                    s));
+    if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k + 2)))) return rc;
     return HYB_OK;
 }
 
-// The cell sort; with profiling, sort j of a chunk is bracketed by two events.
-int launch_sort_all(hyb_batch *b, int j)
+// The cell sort of one lane; with profiling, sort j of a chunk is bracketed
+// by two of the lane's events.
+int launch_sort_all(hyb_batch *b, int j, int lane, cudaStream_t s)
 {
     int rc;
     const size_t s0 = 3 * (size_t)chunk_len(b) + 2 * (size_t)j;
-    if (b->profiling && (rc = record(b, b->ev[s0]))) return rc;
-    CK(launch_sort(b->d_inst, b->max_inst, b->d_prefix, b->precision, b->cfg, b->stream));
-    if (b->profiling && (rc = record(b, b->ev[s0 + 1]))) return rc;
+    if (b->profiling && (rc = record(s, lane_event(b, lane, s0)))) return rc;
+    CK(launch_sort(lane_inst(b, lane), lane_count(b, lane), lane_prefix(b, lane), b->precision, b->cfg, s));
+    if (b->profiling && (rc = record(s, lane_event(b, lane, s0 + 1)))) return rc;
     return HYB_OK;
 }
 
-// Sum the device times of `steps` profiled steps and `sorts` sorts.
+// Sum the device times of `steps` profiled steps and `sorts` sorts of every
+// lane (lanes that overlap each count their own launch's duration).
 int collect_times(hyb_batch *b, int steps, int sorts)
 {
     CK(cudaStreamSynchronize(b->stream));
-    for (int k = 0; k < steps; ++k) {
-        float t0 = 0.f, t1 = 0.f;
-        CK(cudaEventElapsedTime(&t0, b->ev[3 * k], b->ev[3 * k + 1]));
-        CK(cudaEventElapsedTime(&t1, b->ev[3 * k + 1], b->ev[3 * k + 2]));
-        b->ms[0] += t0;
-        b->ms[1] += t1;
-        b->nt[0] += 1;
-        b->nt[1] += 1;
-    }
     const size_t s0 = 3 * (size_t)chunk_len(b);
-    for (int j = 0; j < sorts; ++j) {
-        float t = 0.f;
-        CK(cudaEventElapsedTime(&t, b->ev[s0 + 2 * j], b->ev[s0 + 2 * j + 1]));
-        b->ms[2] += t;
-        b->nt[2] += 1;
+    for (int lane = 0; lane < b->lanes; ++lane) {
+        for (int k = 0; k < steps; ++k) {
+            float t0 = 0.f, t1 = 0.f;
+            CK(cudaEventElapsedTime(&t0, lane_event(b, lane, 3 * (size_t)k), lane_event(b, lane, 3 * (size_t)k + 1)));
+            CK(cudaEventElapsedTime(&t1, lane_event(b, lane, 3 * (size_t)k + 1),
+                                    lane_event(b, lane, 3 * (size_t)k + 2)));
+            b->ms[0] += t0;
+            b->ms[1] += t1;
+            b->nt[0] += 1;
+            b->nt[1] += 1;
+        }
+        for (int j = 0; j < sorts; ++j) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, lane_event(b, lane, s0 + 2 * (size_t)j),
+                                    lane_event(b, lane, s0 + 2 * (size_t)j + 1)));
+            b->ms[2] += t;
+            b->nt[2] += 1;
+        }
     }
     return HYB_OK;
 }
@@ -485,8 +531,32 @@ int flush_pending(hyb_batch *b)
     return collect_times(b, GL, GL / b->sort_interval);
 }
 
-// Graph of one chunk: sort_interval-long runs of steps, each followed by the
-// cell sort.
+// Split the slots into n lanes; streams and fork/join events are created on
+// first use.  Waits for the batch's stream.
+int set_lanes(hyb_batch *b, int n)
+{
+    if (n < 1 || n > kMaxLanes || n > b->max_inst) return fail(HYB_ERR_ARG, "lanes must be in [1, %d]",
+                                                               std::min(kMaxLanes, b->max_inst));
+    int rc = flush_pending(b);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(b->stream));
+    for (int k = 1; k < n; ++k)
+        if (!b->lstream[k]) CK(cudaStreamCreateWithFlags(&b->lstream[k], cudaStreamNonBlocking));
+    for (int k = 0; k < n; ++k)
+        if (!b->ev_join[k]) CK(cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming));
+    if (!b->ev_fork) CK(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    rc = drop_graph(b);
+    if (rc) return rc;
+    b->lanes = n;
+    b->per_lane = (b->max_inst + n - 1) / n;
+    b->lanes = (b->max_inst + b->per_lane - 1) / b->per_lane;  // no empty trailing lane
+    return prefix_all(b);
+}
+
+
+// Graph of one chunk: per lane, sort_interval-long runs of steps, each
+// followed by the cell sort; lanes are parallel branches forked from and
+// joined back into the batch's stream.
 int build_graph(hyb_batch *b)
 {
     if (b->profiling) {
@@ -497,11 +567,27 @@ int build_graph(hyb_batch *b)
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     int rc = HYB_OK;
-    for (int k = 0; k < GL && rc == HYB_OK; ++k) {
-        rc = launch_step(b, k);
-        if (rc == HYB_OK && (k + 1) % b->sort_interval == 0) rc = launch_sort_all(b, (k + 1) / b->sort_interval - 1);
+    cudaError_t e = cudaSuccess;
+    if (b->lanes > 1) {
+        e = cudaEventRecord(b->ev_fork, b->stream);
+        for (int lane = 1; lane < b->lanes && e == cudaSuccess; ++lane)
+            e = cudaStreamWaitEvent(b->lstream[lane], b->ev_fork, 0);
+        if (e != cudaSuccess) rc = fail(HYB_ERR_CUDA, "fork: %s", cudaGetErrorString(e));
     }
-    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    for (int lane = 0; lane < b->lanes && rc == HYB_OK; ++lane) {
+        const cudaStream_t s = lane_stream(b, lane);
+        for (int k = 0; k < GL && rc == HYB_OK; ++k) {
+            rc = launch_step(b, k, lane, s);
+            if (rc == HYB_OK && (k + 1) % b->sort_interval == 0)
+                rc = launch_sort_all(b, (k + 1) / b->sort_interval - 1, lane, s);
+        }
+    }
+    for (int lane = 1; lane < b->lanes && rc == HYB_OK; ++lane) {
+        e = cudaEventRecord(b->ev_join[lane], b->lstream[lane]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[lane], 0);
+        if (e != cudaSuccess) rc = fail(HYB_ERR_CUDA, "join: %s", cudaGetErrorString(e));
+    }
+    e = cudaStreamEndCapture(b->stream, &g);
     if (rc != HYB_OK) {
         if (g) cudaGraphDestroy(g);
         return rc;
@@ -603,7 +689,8 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     rc = reinit_slot(b, slot, true);
     if (rc) return rc;
     CK(launch_set_active(&b->d_inst[slot], 1, S.h.target_step, b->stream));
-    CK(launch_prefix(b->d_inst, b->max_inst, b->d_prefix, b->stream));
+    rc = prefix_all(b);
+    if (rc) return rc;
     S.used = true;
     S.reported = false;
     S.p = *p;
@@ -639,29 +726,149 @@ int advance(hyb_batch *b, int64_t n)
                 if (rc) return rc;
             }
             CK(cudaGraphLaunch(b->graph, b->stream));
-            b->launches += 2 * (int64_t)GL + kSortKernels * (int64_t)(GL / b->sort_interval);
+            b->launches += b->lanes * (2 * (int64_t)GL + kSortKernels * (int64_t)(GL / b->sort_interval));
             b->steps += GL;
             n -= GL;
             b->pending = b->profiling;
             continue;
         }
-        rc = launch_step(b, 0);
-        if (rc) return rc;
-        b->launches += 2;
+        // a single step: the lanes one after the other on the batch's stream
+        const bool sort_now = b->since_sort + 1 == b->sort_interval;
+        for (int lane = 0; lane < b->lanes; ++lane) {
+            rc = launch_step(b, 0, lane, b->stream);
+            if (rc) return rc;
+            if (sort_now && (rc = launch_sort_all(b, 0, lane, b->stream))) return rc;
+        }
+        b->launches += b->lanes * (2 + (sort_now ? kSortKernels : 0));
         b->steps += 1;
         --n;
-        const bool sort_now = ++b->since_sort == b->sort_interval;
-        if (sort_now) {
-            rc = launch_sort_all(b, 0);
-            if (rc) return rc;
-            b->launches += kSortKernels;
-            b->since_sort = 0;
-        }
+        b->since_sort = sort_now ? 0 : b->since_sort + 1;
         if (b->profiling) {
             rc = collect_times(b, 1, sort_now ? 1 : 0);
             if (rc) return rc;
         }
     }
+    return HYB_OK;
+}
+
+int64_t total_pushes(hyb_batch *b)
+{
+    int64_t n = 0;
+    for (int i = 0; i < b->max_inst; ++i)
+        if (b->slots[i].used) n += (int64_t)b->h_stage[i].ctr[C_PUSH];
+    return n;
+}
+
+int fetch_all(hyb_batch *b)
+{
+    CK(cudaMemcpyAsync(b->h_stage, b->d_inst, sizeof(InstDev) * (size_t)b->max_inst, cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return HYB_OK;
+}
+
+int set_tuning(hyb_batch *b, const hyb_tuning &t)
+{
+    if (t.sort_interval < 1 || t.sort_interval > 1000) return fail(HYB_ERR_ARG, "sort_interval must be in [1, 1000]");
+    if (t.blocks_per_sm < 0 || t.blocks_per_sm > 64) return fail(HYB_ERR_ARG, "blocks_per_sm must be in [0, 64]");
+    int rc = flush_pending(b);
+    if (rc) return rc;
+    if (t.lanes != b->lanes && (rc = set_lanes(b, t.lanes))) return rc;
+    if (t.sort_interval != b->sort_interval) {
+        if ((rc = drop_graph(b))) return rc;
+        b->sort_interval = t.sort_interval;
+        b->since_sort = 0;
+    }
+    if (t.blocks_per_sm != b->blocks_per_sm) {
+        b->blocks_per_sm = t.blocks_per_sm;
+        b->cfg.grid = b->num_sms * (t.blocks_per_sm > 0 ? t.blocks_per_sm : b->occ_per_sm);
+        if ((rc = drop_graph(b))) return rc;
+    }
+    return HYB_OK;
+}
+
+hyb_tuning get_tuning(const hyb_batch *b)
+{
+    hyb_tuning t{};
+    t.lanes = b->lanes;
+    t.sort_interval = b->sort_interval;
+    t.blocks_per_sm = b->blocks_per_sm;
+    t.rate = 0.0;
+    return t;
+}
+
+// Particle-steps/s of `steps` steps (whole chunks) under tuning t, after one
+// untimed chunk that builds the graph.  The steps are real steps of every
+// running discharge.
+int measure(hyb_batch *b, const hyb_tuning &t, int64_t steps, cudaEvent_t e0, cudaEvent_t e1, double *rate)
+{
+    int rc = set_tuning(b, t);
+    if (rc) return rc;
+    if ((rc = advance(b, chunk_len(b)))) return rc;
+    if ((rc = fetch_all(b))) return rc;
+    const int64_t p0 = total_pushes(b);
+    CK(cudaEventRecord(e0, b->stream));
+    if ((rc = advance(b, steps))) return rc;
+    CK(cudaEventRecord(e1, b->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if ((rc = fetch_all(b))) return rc;
+    *rate = ms > 0.f ? (double)(total_pushes(b) - p0) / (ms * 1e-3) : 0.0;
+    return HYB_OK;
+}
+
+// Coordinate search over lanes, then the sort interval, then the electron
+// grid, each trial timed on the batch's own running discharges.
+int autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *out)
+{
+    if (trial_steps < 1) return fail(HYB_ERR_ARG, "trial_steps must be positive");
+    if (b->profiling) return fail(HYB_ERR_ARG, "switch profiling off before tuning");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    hyb_tuning best = get_tuning(b);
+    best.rate = -1.0;
+    int rc = HYB_OK;
+    auto trial = [&](hyb_tuning t) {
+        if (rc) return;
+        const int64_t GL = chunk_len(b);
+        const int64_t steps = ((trial_steps + GL - 1) / GL) * GL;
+        double r = 0.0;
+        rc = measure(b, t, steps, e0, e1, &r);
+        if (rc == HYB_OK && r > best.rate) {
+            best = t;
+            best.rate = r;
+        }
+    };
+    const int lane_opts[4] = {1, 2, 4, 8};
+    for (int l : lane_opts) {
+        if (l > std::min(kMaxLanes, b->max_inst)) break;
+        hyb_tuning t = best;
+        t.lanes = l;
+        if (l == best.lanes && best.rate >= 0) continue;
+        trial(t);
+    }
+    const int sort_opts[3] = {10, 20, 50};
+    const hyb_tuning after_lanes = best;
+    for (int k : sort_opts) {
+        if (k == after_lanes.sort_interval) continue;
+        hyb_tuning t = after_lanes;
+        t.sort_interval = k;
+        trial(t);
+    }
+    const hyb_tuning after_sort = best;
+    {
+        hyb_tuning t = after_sort;
+        t.blocks_per_sm = after_sort.blocks_per_sm == 0 ? 2 * b->occ_per_sm : 0;
+        trial(t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    rc = set_tuning(b, best);
+    if (rc) return rc;
+    if (out) *out = best;
     return HYB_OK;
 }
 
@@ -796,7 +1003,8 @@ int free_slot(hyb_batch *b, int slot)
     Slot &S = b->slots[slot];
     if (!S.used) return HYB_OK;
     CK(launch_set_active(&b->d_inst[slot], 0, 0, b->stream));
-    CK(launch_prefix(b->d_inst, b->max_inst, b->d_prefix, b->stream));
+    int rc = prefix_all(b);
+    if (rc) return rc;
     CK(cudaFreeAsync(S.mem, b->stream));
     CK(cudaStreamSynchronize(b->stream));
     b->hbm_used -= S.bytes;
@@ -845,14 +1053,17 @@ int hyb_batch_create(int32_t max_instances, int32_t precision, int64_t hbm_cap_b
     }
     CK(cudaMalloc(&b->d_inst, sizeof(InstDev) * (size_t)max_instances));
     CK(cudaMemset(b->d_inst, 0, sizeof(InstDev) * (size_t)max_instances));
-    CK(cudaMalloc(&b->d_prefix, sizeof(int64_t) * (size_t)(max_instances + 1)));
-    CK(cudaMemset(b->d_prefix, 0, sizeof(int64_t) * (size_t)(max_instances + 1)));
+    const size_t np = (size_t)kMaxLanes * (size_t)(max_instances + 1);
+    CK(cudaMalloc(&b->d_prefix, sizeof(int64_t) * np));
+    CK(cudaMemset(b->d_prefix, 0, sizeof(int64_t) * np));
     CK(cudaMalloc(&b->d_prefix1, sizeof(int64_t) * 2));
-    CK(cudaMalloc(&b->d_ticket, sizeof(unsigned) * 2));
-    CK(cudaMemset(b->d_ticket, 0, sizeof(unsigned) * 2));
-    b->d_ticket1 = b->d_ticket + 1;
+    CK(cudaMalloc(&b->d_ticket, sizeof(unsigned) * (kMaxLanes + 1)));
+    CK(cudaMemset(b->d_ticket, 0, sizeof(unsigned) * (kMaxLanes + 1)));
+    b->d_ticket1 = b->d_ticket + kMaxLanes;
     CK(cudaMallocHost(&b->h_stage, sizeof(InstDev) * (size_t)max_instances));
     int rc = configure(b, 3, 2);
+    if (rc) return rc;
+    rc = set_lanes(b, std::min(kDefaultLanes, max_instances));
     if (rc) return rc;
     *out = b;
     return HYB_OK;
@@ -945,6 +1156,11 @@ int hyb_batch_destroy(hyb_batch *b)
     cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    for (int k = 0; k < kMaxLanes; ++k) {
+        if (b->lstream[k]) cudaStreamDestroy(b->lstream[k]);
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     cudaFree(b->d_inst);
     cudaFree(b->d_prefix);
     cudaFree(b->d_prefix1);
@@ -953,6 +1169,25 @@ int hyb_batch_destroy(hyb_batch *b)
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return HYB_OK;
+}
+
+int hyb_batch_get_tuning(hyb_batch *b, hyb_tuning *out)
+{
+    if (!b || !out) return fail(HYB_ERR_ARG, "NULL argument");
+    *out = get_tuning(b);
+    return HYB_OK;
+}
+
+int hyb_batch_set_tuning(hyb_batch *b, const hyb_tuning *t)
+{
+    if (!b || !t) return fail(HYB_ERR_ARG, "NULL argument");
+    return set_tuning(b, *t);
+}
+
+int hyb_batch_autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *chosen)
+{
+    if (!b) return fail(HYB_ERR_ARG, "NULL batch");
+    return autotune(b, trial_steps, chosen);
 }
 
 int hyb_batch_set_profiling(hyb_batch *b, int32_t on)
@@ -1163,7 +1398,8 @@ int hyb_write_particles(hyb_discharge *h, int64_t n, const double *z, const doub
     if (rc) return rc;
     rc = reinit_slot(b, h->slot, true);
     if (rc) return rc;
-    CK(launch_prefix(b->d_inst, b->max_inst, b->d_prefix, b->stream));
+    rc = prefix_all(b);
+    if (rc) return rc;
     CK(cudaStreamSynchronize(b->stream));
     return HYB_OK;
 }
@@ -1182,7 +1418,8 @@ int hyb_write_ion_density(hyb_discharge *h, const double *ni)
     if (rc) return rc;
     rc = reinit_slot(b, h->slot, false);
     if (rc) return rc;
-    CK(launch_prefix(b->d_inst, b->max_inst, b->d_prefix, b->stream));
+    rc = prefix_all(b);
+    if (rc) return rc;
     CK(cudaStreamSynchronize(b->stream));
     return HYB_OK;
 }

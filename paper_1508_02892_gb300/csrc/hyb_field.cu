@@ -396,12 +396,16 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
     double *s_S = s_ib;
     double *s_phi = s_d;
     double part = 0.0;
+    // the split mode multiplies by reciprocals where the FP64 mode divides (as
+    // the oracle does); FP64 division is a long instruction sequence here
+    const double w_in = w / dz, w_wall = 2.0 * w / dz, c_src = dz * dz / kEps0;
     for (int j = j0; j < j1; ++j) {
-        const double ne = w * K->dep_n[j] / node_volume(j, G, dz);
+        const double ne = FAST ? K->dep_n[j] * ((j == 0 || j == G - 1) ? w_wall : w_in)
+                               : w * K->dep_n[j] / node_volume(j, G, dz);
         K->ne[j] = ne;
         const double rho = kQe * (s_ni[j] - ne);
         s_rho[j] = rho;
-        const double sj = (j >= 1 && j <= G - 2) ? dz * dz * rho / kEps0 : 0.0;
+        const double sj = (j >= 1 && j <= G - 2) ? (FAST ? rho * c_src : dz * dz * rho / kEps0) : 0.0;
         part += sj;
         s_S[j] = part;  // local inclusive
         if (!init) {
@@ -423,7 +427,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
     double stot;
     block_exscan(ssum, red, &stot);
     // d_0 = (phi_N - phi_0 + sum_{j=0}^{G-2} S_j)/(G-1); d_j = d_0 - S_j
-    const double d0 = (0.0 - phi0 + stot) / (double)(G - 1);
+    const double d0 = FAST ? (0.0 - phi0 + stot) * K->inv_gm1 : (0.0 - phi0 + stot) / (double)(G - 1);
     double dpart = 0.0;
     for (int j = j0; j < j1; ++j) {
         const double dj = j <= G - 2 ? d0 - s_S[j] : 0.0;
@@ -436,9 +440,17 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
     if (t == 0) s_phi[G - 1] = 0.0;
     __syncthreads();
     int bad = 0;
+    const double inv_dz = 1.0 / dz, half_inv_dz = 0.5 / dz, c_gauss = dz / (2.0 * kEps0);
     for (int j = j0; j < j1; ++j) {
         double e;
-        if (j == 0) {
+        if (FAST) {
+            if (j == 0)
+                e = -d0 * inv_dz - s_rho[0] * c_gauss;
+            else if (j == G - 1)
+                e = -(d0 - s_S[G - 2]) * inv_dz + s_rho[G - 1] * c_gauss;
+            else
+                e = -((d0 - s_S[j]) + (d0 - s_S[j - 1])) * half_inv_dz;
+        } else if (j == 0) {
             e = -d0 / dz - s_rho[0] * dz / (2.0 * kEps0);
         } else if (j == G - 1) {
             e = -(d0 - s_S[G - 2]) / dz + s_rho[G - 1] * dz / (2.0 * kEps0);

@@ -44,6 +44,7 @@ struct InstDev {
     double L, dz, dt, ngas, w, m_gas, m_ion, qm, nu_max, p_max, n_floor, bin_w;
     double e_lo, e_hi, inv_dlog, e_exc, e_iz, two_mM, gamma_see, see_speed;
     double v_rf, f_rf, v_dc, mu_const, kT_gas;
+    double inv_gm1;  // 1 / (G - 1)
     uint32_t seed_lo, seed_hi;
     // FP32 copies for the split-mode electron kernel
     float f_dt_dz, f_qm_dt, f_half_m_q, f_two_q_m, f_pmax, f_e_lo, f_e_hi, f_inv_e_lo, f_inv_dlog;

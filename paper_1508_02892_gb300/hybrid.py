@@ -75,6 +75,11 @@ class Profile(C.Structure):
 
 _lib = None
 
+class Tuning(C.Structure):
+    _fields_ = [("lanes", C.c_int32), ("sort_interval", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("rate", C.c_double)]
+
+
 EXPORTS = {
     "hyb_create_discharge": (C.c_int, [C.POINTER(Params), C.c_void_p, C.POINTER(C.c_void_p)]),
     "hyb_advance": (C.c_int, [C.c_void_p, C.c_int64]),
@@ -103,6 +108,9 @@ EXPORTS = {
     "hyb_batch_destroy": (C.c_int, [C.c_void_p]),
     "hyb_batch_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "hyb_batch_profile": (C.c_int, [C.c_void_p, C.POINTER(Profile), C.c_int32]),
+    "hyb_batch_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(Tuning)]),
+    "hyb_batch_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(Tuning)]),
+    "hyb_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Tuning)]),
     "hyb_discharge_batch": (C.c_void_p, [C.c_void_p]),
     "hyb_debug_checks": (C.c_int, [C.POINTER(C.c_uint64)]),
     "hyb_field_from_particles_noalloc": (C.c_int, [C.POINTER(Params), C.c_int64, C.c_void_p, C.c_void_p,
@@ -354,6 +362,24 @@ class Batch:
 
     def profile(self, reset=False):
         return _profile(self.h, reset)
+
+    def tuning(self):
+        t = Tuning()
+        _check(lib().hyb_batch_get_tuning(self.h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+    def set_tuning(self, lanes=None, sort_interval=None, blocks_per_sm=None):
+        cur = self.tuning()
+        t = Tuning(int(lanes if lanes is not None else cur["lanes"]),
+                   int(sort_interval if sort_interval is not None else cur["sort_interval"]),
+                   int(blocks_per_sm if blocks_per_sm is not None else cur["blocks_per_sm"]), 0.0)
+        _check(lib().hyb_batch_set_tuning(self.h, C.byref(t)))
+        return self.tuning()
+
+    def autotune(self, trial_steps=200):
+        t = Tuning()
+        _check(lib().hyb_batch_autotune(self.h, int(trial_steps), C.byref(t)))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
     def stats(self):
         r, n, b = C.c_int32(0), C.c_int64(0), C.c_int64(0)

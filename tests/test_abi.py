@@ -30,11 +30,8 @@ def test_library_exports_every_declared_symbol():
     assert set(_declared()) <= set(hybrid.EXPORTS)
 
 
-def test_binding_structs_match_header_field_order():
-    from paper_1508_02892_gb300 import hybrid
-    with open(os.path.join(ROOT, "include", "hybrid1d.h")) as f:
-        src = f.read()
-    body = re.search(r"typedef struct hyb_params \{(.*?)\} hyb_params;", src, re.S).group(1)
+def _struct_fields(src, name):
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), src, re.S).group(1)
     fields = []
     for line in body.split("\n"):
         line = re.sub(r"/\*.*?\*/", "", line).strip()
@@ -46,7 +43,15 @@ def test_binding_structs_match_header_field_order():
                 continue
             names = re.findall(r"\*?\s*(\w+)\s*(?:,|$)", decl.split(None, 1)[1] if " " in decl else decl)
             fields += [n for n in names if n not in ("const", "double", "int32_t", "int64_t", "uint64_t")]
-    assert fields == [f for f, _ in hybrid.Params._fields_]
+    return fields
+
+
+def test_binding_structs_match_header_field_order():
+    from paper_1508_02892_gb300 import hybrid
+    with open(os.path.join(ROOT, "include", "hybrid1d.h")) as f:
+        src = f.read()
+    for cname, py in (("hyb_params", hybrid.Params), ("hyb_tuning", hybrid.Tuning), ("hyb_profile", hybrid.Profile)):
+        assert _struct_fields(src, cname) == [f for f, _ in py._fields_], cname
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -126,20 +126,24 @@ def test_split_mode_statistics_config1():
         assert _l2(a, b) < 0.02, (k, _l2(a, b))
 
 
-def test_batch_matches_single_runs_fp64():
-    """Each discharge gives the same result alone and inside a batch (RNG is
-    keyed by particle id and step, so only summation order differs)."""
+@pytest.mark.parametrize("lanes,sort_interval", [(1, 20), (2, 7), (4, 20)])
+def test_batch_matches_single_runs_fp64(lanes, sort_interval):
+    """Each discharge gives the same result alone and inside a batch, whatever
+    the launch layout (RNG is keyed by particle id and step, so only summation
+    order differs).  250 steps cover two captured chunks plus single steps."""
     from paper_1508_02892_gb300 import hybrid
     ps = [W.config1(precision=W.FP64, n_particles=5000, n_cells=80, seed=21, te0_ev=6.0),
           W.config1(precision=W.FP64, n_particles=12000, n_cells=150, seed=22, ion_model=W.ION_FULL,
                     gamma_see=0.2, weight=2e6, v_rf_amp_v=300.0),
           W.config1(precision=W.FP64, n_particles=777, n_cells=33, seed=23, ion_model=W.ION_DD_TABLE)]
     b = hybrid.Batch(4, hybrid.HYB_FP64)
+    t = b.set_tuning(lanes=lanes, sort_interval=sort_interval)
+    assert t["sort_interval"] == sort_interval and 1 <= t["lanes"] <= lanes
     slots = [b.admit(p) for p in ps]
-    b.advance(50)
+    b.advance(250 if lanes != 4 else 50)
     for s, p in zip(slots, ps):
         g = _gpu(p)
-        g.advance(50)
+        g.advance(250 if lanes != 4 else 50)
         assert_particles_close(b.particles(s), g.particles(), p["gap_m"], PART_TOL)
         ca, cb = b.counters(s), g.counters()
         for k in COUNTERS:
@@ -147,6 +151,28 @@ def test_batch_matches_single_runs_fp64():
         ma, mb = b.moments(s), g.moments()
         for k in ("ne", "ni", "gamma", "ebar", "eedf"):
             assert_grid_close(ma[k], mb[k], GRID_TOL, k)
+    b.close()
+
+
+def test_autotune_keeps_a_valid_configuration():
+    """The autotuner's trials are real steps: afterwards every discharge has
+    advanced, particle bookkeeping still holds and the choice is in range."""
+    from paper_1508_02892_gb300 import hybrid
+    b = hybrid.Batch(3, hybrid.HYB_FP32_SPLIT)
+    ps = [W.config1(precision=W.FP32_SPLIT, n_particles=n, n_cells=c, seed=s)
+          for n, c, s in ((20000, 200, 31), (8000, 120, 32), (30000, 300, 33))]
+    slots = [b.admit(p) for p in ps]
+    t = b.autotune(100)
+    assert 1 <= t["lanes"] <= 3 and t["sort_interval"] in (10, 20, 50) and t["rate"] > 0
+    assert b.tuning()["lanes"] == t["lanes"]
+    steps = [b.counters(s)["step"] for s in slots]
+    assert min(steps) == max(steps) >= 200
+    b.advance(100)
+    for s in slots:
+        c = b.counters(s)
+        assert c["status"] == 0 and c["particles"] == b.particles(s)["id"].size
+    from paper_1508_02892_gb300 import hybrid as H
+    assert H.debug_checks() == ((0, 0, 0), (0, 0, 0))
     b.close()
 
 
