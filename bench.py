@@ -206,6 +206,27 @@ def run_fp64_plain(params, chunks=2, steps=20):
             "steps": chunks * steps, "dtype": "f64"}
 
 
+def serve_load(args, stream, rank=0, world=1, tuning=None):
+    """Config-4 serving: Poisson arrivals (20/s) of discharges from the batched
+    ranges, 1e4..4e6 electrons, each advanced by `serve_steps` steps, admitted
+    under a 120 GB HBM cap into one resident batch (continuous batching);
+    requests are dealt to ranks round-robin."""
+    from paper_1508_02892_gb300 import hybrid, workloads as W
+    from paper_1508_02892_gb300.serve import Server, summarize
+    reqs = W.config4_requests(n_requests=args.serve_requests, steps=args.serve_steps)
+    reqs = [r for k, r in enumerate(reqs) if k % world == rank]
+    srv = Server(max_slots=64, hbm_cap_bytes=120e9, precision=hybrid.HYB_FP32_SPLIT, stream=stream.cuda_stream,
+                 tuning=tuning)
+    t0 = time.perf_counter()
+    out = srv.run(reqs, keep=("counters",))
+    wall = time.perf_counter() - t0
+    srv.close()
+    s = summarize(out, wall)
+    s.update({"rate_hz": 20.0, "steps_per_request": args.serve_steps, "hbm_cap_gb": 120,
+              "peak_admitted_gb": srv.max_bytes / 1e9, "failed": sum(1 for r in out if r["status"] != 0)})
+    return s
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -336,6 +357,10 @@ def run_ours(args):
                "note": "admission from host parameters and tables (pageable), per-chunk host read of all "
                        "moments, eviction, all inside the wall-clock region"}
 
+    serving = None
+    if rank == 0 and args.serve_requests > 0:
+        serving = serve_load(args, stream, tuning={k: tuning[k] for k in ("lanes", "sort_interval", "blocks_per_sm")})
+
     fp64 = None
     if rank == 0 and not args.no_fp64:
         fp64 = run_fp64_plain(params)
@@ -373,6 +398,8 @@ def run_ours(args):
         line["speedup_vs_fp64_plain"] = value / world / fp64["value"]
     if e2e:
         line["e2e"] = e2e
+    if serving:
+        line["serving"] = serving
     if cpu:
         line["cpu_baseline"] = cpu
     line["device_index_guards"] = hybrid.debug_checks()
@@ -394,6 +421,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--tune-steps", type=int, default=200)
     ap.add_argument("--lanes", type=int, default=0, help="fixed lane count instead of the autotuner's")
+    ap.add_argument("--serve-requests", type=int, default=100, help="config-4 serving requests (0: none)")
+    ap.add_argument("--serve-steps", type=int, default=5000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -640,12 +640,24 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     int rc = validate(p);
     if (rc) return rc;
     if (p->precision != b->precision) return fail(HYB_ERR_ARG, "precision differs from the batch's");
+    // a free slot in the lane holding the fewest initial particles, so that
+    // the lanes' chains stay about equally long
     int slot = -1;
-    for (int i = 0; i < b->max_inst; ++i)
-        if (!b->slots[i].used) {
-            slot = i;
-            break;
+    double best_load = 0.0;
+    for (int k = 0; k < b->lanes; ++k) {
+        double load = 0.0;
+        int free_i = -1;
+        for (int i = lane_first(b, k); i < lane_first(b, k) + lane_count(b, k); ++i) {
+            if (b->slots[i].used)
+                load += (double)b->slots[i].p.n_particles;
+            else if (free_i < 0)
+                free_i = i;
         }
+        if (free_i >= 0 && (slot < 0 || load < best_load)) {
+            slot = free_i;
+            best_load = load;
+        }
+    }
     if (slot < 0) return fail(HYB_ERR_OOM, "no free slot in the batch");
     const Layout L = layout_of(*p);
     if (b->hbm_cap > 0 && b->hbm_used + (int64_t)L.total > b->hbm_cap)

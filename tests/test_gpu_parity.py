@@ -108,21 +108,28 @@ def _l2(a, b):
 
 
 def test_split_mode_statistics_config1():
-    """FP32 split vs FP64 oracle: time-averaged n_e, <E>, Gamma_i and EEDF
-    within 2 % (L2) over seeds; both draw the same random numbers."""
-    acc = {k: [0.0, 0.0] for k in ("ne", "ebar", "gamma", "eedf")}
-    for seed in range(4):
+    """FP32 split vs FP64 oracle: the 16-seed ensemble means of the time-
+    averaged n_e, <E>, Gamma_i and EEDF agree within 2 % (L2); both sides draw
+    the same random numbers.  The seed-to-seed noise floor (oracle ensemble of
+    the even seeds against that of the odd ones) is printed beside it."""
+    keys = ("ne", "ebar", "gamma", "eedf")
+    gpu = {k: [] for k in keys}
+    orc = {k: [] for k in keys}
+    for seed in range(16):
         p = W.config1(precision=W.FP32_SPLIT, seed=100 + seed)
         g = _gpu(p)
         o = oracle.Oracle(p)
         g.advance(300)
         o.step(300)
         ma, mb = g.moments(), o.moments()
-        for k in acc:
-            acc[k][0] = acc[k][0] + ma[k]
-            acc[k][1] = acc[k][1] + mb[k]
+        for k in keys:
+            gpu[k].append(ma[k])
+            orc[k].append(mb[k])
         g.close()
-    for k, (a, b) in acc.items():
+    for k in keys:
+        a, b = np.mean(gpu[k], axis=0), np.mean(orc[k], axis=0)
+        noise = _l2(np.mean(orc[k][0::2], axis=0), np.mean(orc[k][1::2], axis=0))
+        print(f"split vs oracle, 16 seeds, {k}: L2 {_l2(a, b):.3e} (seed noise floor {noise:.3e})")
         assert _l2(a, b) < 0.02, (k, _l2(a, b))
 
 
@@ -242,13 +249,13 @@ def _split_state_to_oracle(s):
     return np.stack([s["z"], s["vx"], s["vy"], s["vz"]], axis=1)
 
 
-@pytest.mark.parametrize("cfg", ["config2"])
+@pytest.mark.parametrize("cfg", ["config2", "config5"])
 def test_full_size_sampled_step_against_oracle(cfg):
     """Full-size FP32 split discharge in the benchmark's launch configuration:
     a sample of particles is stepped one by one by the FP64 oracle from the
     GPU's pre-step state and field; states agree to FP32 rounding and the
     collision outcomes agree except for draws within rounding of a threshold."""
-    p = W.config2()
+    p = getattr(W, cfg)()
     g = _gpu(p)
     g.advance(20)
     before = g.particles()
@@ -281,8 +288,9 @@ def test_full_size_sampled_step_against_oracle(cfg):
     assert mism <= 3, mism
 
 
-def test_full_size_particle_conservation_and_unique_ids():
-    p = W.config2()
+@pytest.mark.parametrize("cfg", ["config2", "config5"])
+def test_full_size_particle_conservation_and_unique_ids(cfg):
+    p = getattr(W, cfg)()
     g = _gpu(p)
     g.advance(60)
     s = g.particles()
@@ -290,6 +298,8 @@ def test_full_size_particle_conservation_and_unique_ids():
     assert s["id"].size == c["particles"]
     assert np.unique(s["id"]).size == s["id"].size
     assert np.all((s["z"] >= 0) & (s["z"] < p["gap_m"]))
-    assert c["pushes"] > 59 * 1.9e6
+    assert c["pushes"] > 59 * 0.95 * p["n_particles"]
+    assert c["particles"] == p["n_particles"] + c["births_iz"] + c["births_see0"] + c["births_see1"] - \
+        c["losses0"] - c["losses1"]
     from paper_1508_02892_gb300 import hybrid
     assert hybrid.debug_checks() == ((0, 0, 0), (0, 0, 0))
