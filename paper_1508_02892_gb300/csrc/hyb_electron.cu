@@ -240,6 +240,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const float pmax = K->f_pmax, e_lo = K->f_e_lo, e_hi = K->f_e_hi, inv_e_lo = K->f_inv_e_lo;
     const float inv_dlog = K->f_inv_dlog, e_exc = K->f_e_exc, e_iz = K->f_e_iz, two_mM = K->f_two_mM;
     const float bin_inv = K->f_bin_inv;
+    const PhiloxPre pre = philox_pre(step, sh);
 
     // shared memory: EEDF histogram, then one deposit row per warp
     unsigned *s_eedf = reinterpret_cast<unsigned *>(smem);
@@ -296,6 +297,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
 
         unsigned coll = 0u;      // 2 bits per particle: 1 elastic, 2 excitation, 3 ionization
         uint2 ru[kVec];          // direction draws of the colliding particles
+        float ens[kVec];         // kinetic energies (eV) after the push
 #pragma unroll
         for (int k = 0; k < kVec; ++k) {
             int c = cc[k];
@@ -333,43 +335,42 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 }
             }
 
-            if (MODE == 0 && alive) {
-                // modified null-collision method: every particle draws R1 < P_max;
-                // the process is the first k with R2 nu_max < sum_{i<=k} nu_i
-                const uint4 r = draw(ids[k], step, sl, sh, 0);
-                if (u01f(r.x) < pmax) {
-                    const float speed = sqrtf(vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
-                    float4 lo, hi;
-                    float f;
-                    if (en <= e_lo) {
-                        lo = hi = __ldg(&xs[0]);
-                        f = 0.f;
-                    } else if (en >= e_hi) {
-                        lo = hi = __ldg(&xs[nxs - 1]);
-                        f = 0.f;
-                    } else {
-                        int kk = (int)(__logf(en * inv_e_lo) * inv_dlog);
-                        kk = kk < 0 ? 0 : (kk > nxs - 2 ? nxs - 2 : kk);
-                        lo = __ldg(&xs[kk]);
-                        hi = __ldg(&xs[kk + 1]);
-                        f = __fdividef(en - lo.x, hi.x - lo.x);
-                    }
-                    const float s_el = lo.y + f * (hi.y - lo.y);
-                    const float s_ex = en < e_exc ? 0.f : lo.z + f * (hi.z - lo.z);
-                    const float s_iz = en < e_iz ? 0.f : lo.w + f * (hi.w - lo.w);
-                    const float t0 = s_el * speed, t1 = t0 + s_ex * speed, t2 = t1 + s_iz * speed;
-                    const float r2 = u01f(r.y);
-                    if (r2 < t2) {
-                        const unsigned kind = r2 < t0 ? 1u : (r2 < t1 ? 2u : 3u);
-                        coll |= kind << (2 * k);
-                        ru[k] = make_uint2(r.z, r.w);
-                    } else {
-                        cnt.iz_nul += 1u << 16;
-                    }
-                }
-            }
+            ens[k] = en;
             cc[k] = alive ? c : kDeadCell;
             oo[k] = o;
+        }
+        if (MODE == 0) {
+            // modified null-collision method: every particle draws R1 < P_max;
+            // the process is the first k with R2 nu_max < sum_{i<=k} nu_i.  The
+            // kVec particles' draws are formed together (independent chains).
+            uint4 rk[kVec];
+            draw_n<kVec>(pre, ids, sl, 0u, rk);
+#pragma unroll
+            for (int k = 0; k < kVec; ++k) {
+                const float en = ens[k];
+                if (!(cc[k] >= 0 && cc[k] < nc) || !(u01f(rk[k].x) < pmax)) continue;
+                const float speed = sqrtf(vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
+                // table segment without branches: below the table the first
+                // node's values, above it the last node's
+                int kk = (int)(__logf(fmaxf(en, e_lo) * inv_e_lo) * inv_dlog);
+                kk = kk < 0 ? 0 : (kk > nxs - 2 ? nxs - 2 : kk);
+                const float4 lo = __ldg(&xs[kk]);
+                const float4 hi = __ldg(&xs[kk + 1]);
+                const bool below = en <= e_lo, above = en >= e_hi;
+                const float f = below ? 0.f : __fdividef(en - lo.x, hi.x - lo.x);
+                const float s_el = above ? hi.y : lo.y + f * (hi.y - lo.y);
+                const float s_ex = en < e_exc ? 0.f : (above ? hi.z : lo.z + f * (hi.z - lo.z));
+                const float s_iz = en < e_iz ? 0.f : (above ? hi.w : lo.w + f * (hi.w - lo.w));
+                const float t0 = s_el * speed, t1 = t0 + s_ex * speed, t2 = t1 + s_iz * speed;
+                const float r2 = u01f(rk[k].y);
+                if (r2 < t2) {
+                    const unsigned kind = r2 < t0 ? 1u : (r2 < t1 ? 2u : 3u);
+                    coll |= kind << (2 * k);
+                    ru[k] = make_uint2(rk[k].z, rk[k].w);
+                } else {
+                    cnt.iz_nul += 1u << 16;
+                }
+            }
         }
         if (++iter == kFlushIters) {
             row_flush(row, rbase, K, G);
@@ -410,7 +411,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                         sp = sqrtf(two_q_m * (en - e_exc));
                         cnt.el_exc += 1u << 16;
                     } else {  // ionization: split E - E_iz, eject a new electron
-                        const uint4 r1 = draw(pid, step, sl, sh, 1);
+                        const uint4 r1 = draw_pre(pre, pid, sl, 1u);
                         const float de = en - e_iz;
                         const float e_ej = u01f(r1.x) * de;
                         sp = sqrtf(two_q_m * (de - e_ej));

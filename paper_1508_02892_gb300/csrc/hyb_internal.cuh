@@ -95,24 +95,68 @@ __device__ __noinline__ static bool hyb_check_fail(int site, long long a, long l
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter (step, seed_lo,
 // seed_hi, call), key = particle id.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+// The draws of a step use the counter (step, seed_lo, seed_hi, call) and the
+// particle id as key, so the products of the first round's multiplied words
+// (step and seed_hi) are the same for every particle: PhiloxPre holds them.
+struct PhiloxPre {
+    uint32_t hi0, lo0, hi1, lo1;
+};
+
+__device__ __forceinline__ PhiloxPre philox_pre(uint32_t step, uint32_t seed_hi)
 {
+    return PhiloxPre{__umulhi(0xD2511F53u, step), 0xD2511F53u * step, __umulhi(0xCD9E8D57u, seed_hi),
+                     0xCD9E8D57u * seed_hi};
+}
+
+// state after the first round for key k
+__device__ __forceinline__ uint4 philox_first(const PhiloxPre &pre, uint32_t seed_lo, uint32_t call, uint2 k)
+{
+    return make_uint4(pre.hi1 ^ seed_lo ^ k.x, pre.lo1, pre.hi0 ^ call ^ k.y, pre.lo0);
+}
+
+// one later round: bump the key by the Weyl constants, then the S-box
+__device__ __forceinline__ void philox_round(uint4 &c, uint2 &k)
+{
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+}
+
+__device__ __forceinline__ uint2 philox_key(uint64_t id) { return make_uint2((uint32_t)id, (uint32_t)(id >> 32)); }
+
+// Philox4x32-10 of counter (step, seed_lo, seed_hi, call) under key id
+__device__ __forceinline__ uint4 draw_pre(const PhiloxPre &pre, uint64_t id, uint32_t seed_lo, uint32_t call)
+{
+    uint2 k = philox_key(id);
+    uint4 c = philox_first(pre, seed_lo, call, k);
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k.x += 0x9E3779B9u;
-            k.y += 0xBB67AE85u;
-        }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    }
+    for (int r = 1; r < 10; ++r) philox_round(c, k);
     return c;
 }
 
 __device__ __forceinline__ uint4 draw(uint64_t id, uint32_t step, uint32_t seed_lo, uint32_t seed_hi, uint32_t call)
 {
-    return philox4x32_10(make_uint4(step, seed_lo, seed_hi, call), make_uint2((uint32_t)id, (uint32_t)(id >> 32)));
+    return draw_pre(philox_pre(step, seed_hi), id, seed_lo, call);
+}
+
+// the same draw for N keys at once, the rounds interleaved across the keys
+template <int N>
+__device__ __forceinline__ void draw_n(const PhiloxPre &pre, const uint64_t *ids, uint32_t seed_lo, uint32_t call,
+                                       uint4 *out)
+{
+    uint2 k[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        k[j] = philox_key(ids[j]);
+        out[j] = philox_first(pre, seed_lo, call, k[j]);
+    }
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) philox_round(out[j], k[j]);
+    }
 }
 
 // (k + 1/2) 2^-23 from the top 23 bits: the same value in float and double.
