@@ -334,7 +334,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         b2 = hybrid.Batch(args.instances, hybrid.HYB_FP32_SPLIT, stream=stream.cuda_stream)
         b2.set_tuning(lanes=tuning["lanes"], sort_interval=tuning["sort_interval"],
-                      blocks_per_sm=tuning["blocks_per_sm"])
+                      blocks_per_sm=tuning["blocks_per_sm"], field_threads=tuning["field_threads"])
         s2 = [b2.admit(p) for p in params]
         h2d = 0
         for p in params:
@@ -359,7 +359,7 @@ def run_ours(args):
 
     serving = None
     if rank == 0 and args.serve_requests > 0:
-        serving = serve_load(args, stream, tuning={k: tuning[k] for k in ("lanes", "sort_interval", "blocks_per_sm")})
+        serving = serve_load(args, stream, tuning={k: tuning[k] for k in ("lanes", "sort_interval", "blocks_per_sm", "field_threads")})
 
     fp64 = None
     if rank == 0 and not args.no_fp64:
@@ -378,7 +378,7 @@ def run_ours(args):
                                f"1e4-2e6 electrons log-uniform, 100-400 V, DD/full ions), FP32 split, "
                                f"{CHUNK}-step CUDA-graph chunks", "instances": args.instances,
                    "initial_particles_per_gpu": total_particles, "chunk_steps": CHUNK,
-                   "tuning": {k: tuning[k] for k in ("lanes", "sort_interval", "blocks_per_sm")},
+                   "tuning": {k: tuning[k] for k in ("lanes", "sort_interval", "blocks_per_sm", "field_threads")},
                    "l2": "256 MB buffer written between timed chunks; particle store > L2"},
         "p50_ms_per_chunk": lat_sorted[len(lat) // 2], "p99_ms_per_chunk": lat_sorted[min(len(lat) - 1,
                                                                                            int(0.99 * len(lat)))],

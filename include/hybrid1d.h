@@ -251,13 +251,17 @@ int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset);
  *                  the others (1..8 and at most max_instances; a batch starts
  *                  with min(4, max_instances));
  *   sort_interval  steps between cell sorts (1..1000, default 20);
- *   blocks_per_sm  electron-kernel blocks per SM (0: the occupancy limit).
+ *   blocks_per_sm  electron-kernel blocks per SM (0: the occupancy limit);
+ *   field_threads  threads of each instance's field block: 256, 512 or 1024
+ *                  (default 256: a small block shares an SM with electron
+ *                  blocks of other lanes; a large one finishes sooner alone).
  * rate is filled by hyb_batch_autotune with the particle-steps/s it measured
  * for the returned choice, and is ignored by hyb_batch_set_tuning. */
 typedef struct hyb_tuning {
     int32_t lanes;
     int32_t sort_interval;
     int32_t blocks_per_sm;
+    int32_t field_threads;
     double rate;
 } hyb_tuning;
 
@@ -267,7 +271,8 @@ int hyb_batch_set_tuning(hyb_batch *b, const hyb_tuning *t);
 
 /* Time candidate configurations on the batch's own running discharges and
  * keep the fastest: lanes in {1, 2, 4, 8}, then the sort interval in
- * {10, 20, 50}, then the electron grid at the occupancy limit or twice it.
+ * {10, 20, 50}, then the electron grid at the occupancy limit or twice it,
+ * then the field block size in {256, 512, 1024}.
  * Each trial advances every running discharge by one untimed chunk and then
  * by trial_steps rounded up to whole chunks (100 steps): those are real steps
  * of the runs.  Profiling must be off.  *chosen may be NULL. */

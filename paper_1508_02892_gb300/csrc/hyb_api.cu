@@ -341,6 +341,7 @@ struct hyb_batch {
     cudaStream_t lstream[kMaxLanes] = {};  // lane k > 0 (lane 0 uses `stream`)
     cudaEvent_t ev_fork = nullptr, ev_join[kMaxLanes] = {};
     int blocks_per_sm = 0;                 // electron grid = SMs x this (0: occupancy limit)
+    int field_threads = 256;               // threads of an instance's field block
     int occ_per_sm = 0;
     std::vector<Slot> slots;
     int64_t hbm_cap = 0, hbm_used = 0;
@@ -478,7 +479,7 @@ int launch_step(hyb_batch *b, int k, int lane, cudaStream_t s)
     CK(launch_electron_step(lane_inst(b, lane), n, lane_prefix(b, lane), b->precision, b->cfg, s));
     if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k + 1)))) return rc;
     CK(launch_field(lane_inst(b, lane), n, lane_prefix(b, lane), lane_ticket(b, lane), b->precision == HYB_FP32_SPLIT,
-                    s));
+                    b->max_nodes, b->field_threads, s));
     if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k + 2)))) return rc;
     return HYB_OK;
 }
@@ -606,7 +607,8 @@ int reinit_slot(hyb_batch *b, int slot, bool sort)
     InstDev *K = &b->d_inst[slot];
     CK(launch_prefix_one(K, b->d_prefix1, b->stream));
     CK(launch_deposit_init(K, 1, b->d_prefix1, b->precision, b->cfg, b->stream));
-    CK(launch_field(K, 1, b->d_prefix1, b->d_ticket1, b->precision == HYB_FP32_SPLIT, b->stream));
+    CK(launch_field(K, 1, b->d_prefix1, b->d_ticket1, b->precision == HYB_FP32_SPLIT, b->max_nodes, b->field_threads,
+                    b->stream));
     if (sort) {
         CK(launch_prefix_one(K, b->d_prefix1, b->stream));
         CK(launch_sort(K, 1, b->d_prefix1, b->precision, b->cfg, b->stream));
@@ -783,6 +785,8 @@ int set_tuning(hyb_batch *b, const hyb_tuning &t)
 {
     if (t.sort_interval < 1 || t.sort_interval > 1000) return fail(HYB_ERR_ARG, "sort_interval must be in [1, 1000]");
     if (t.blocks_per_sm < 0 || t.blocks_per_sm > 64) return fail(HYB_ERR_ARG, "blocks_per_sm must be in [0, 64]");
+    if (t.field_threads != 256 && t.field_threads != 512 && t.field_threads != 1024)
+        return fail(HYB_ERR_ARG, "field_threads must be 256, 512 or 1024");
     int rc = flush_pending(b);
     if (rc) return rc;
     if (t.lanes != b->lanes && (rc = set_lanes(b, t.lanes))) return rc;
@@ -790,6 +794,10 @@ int set_tuning(hyb_batch *b, const hyb_tuning &t)
         if ((rc = drop_graph(b))) return rc;
         b->sort_interval = t.sort_interval;
         b->since_sort = 0;
+    }
+    if (t.field_threads != b->field_threads) {
+        if ((rc = drop_graph(b))) return rc;
+        b->field_threads = t.field_threads;
     }
     if (t.blocks_per_sm != b->blocks_per_sm) {
         b->blocks_per_sm = t.blocks_per_sm;
@@ -805,6 +813,7 @@ hyb_tuning get_tuning(const hyb_batch *b)
     t.lanes = b->lanes;
     t.sort_interval = b->sort_interval;
     t.blocks_per_sm = b->blocks_per_sm;
+    t.field_threads = b->field_threads;
     t.rate = 0.0;
     return t;
 }
@@ -873,6 +882,14 @@ int autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *out)
     {
         hyb_tuning t = after_sort;
         t.blocks_per_sm = after_sort.blocks_per_sm == 0 ? 2 * b->occ_per_sm : 0;
+        trial(t);
+    }
+    const hyb_tuning after_grid = best;
+    const int field_opts[3] = {256, 512, 1024};
+    for (int f : field_opts) {
+        if (f == after_grid.field_threads) continue;
+        hyb_tuning t = after_grid;
+        t.field_threads = f;
         trial(t);
     }
     cudaEventDestroy(e0);

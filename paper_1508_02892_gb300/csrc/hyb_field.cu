@@ -30,7 +30,20 @@ struct Red {
     double w[32];
     double total;
     int flag;
+    int iters;
     unsigned long long count;
+};
+
+// Instance constants of the field step, formed once per block by thread 0
+// (each the same expression the per-node code would evaluate, so results do
+// not change; FP64 division, sin and log are long instruction sequences on
+// this part's FP64 rate).
+struct FieldConsts {
+    double h, inv2dz, qdt_m, h_m, c_in, c_wall, gs_in, gs_wall;  // split-mode fluid
+    double dt_dz, dt_2dz, h_mion;                                // FP64-mode fluid
+    double w_in, w_wall, c_src, inv_dz, half_inv_dz, c_gauss;    // split-mode Poisson
+    double phi0;
+    float inv_ngas_td, tfac;
 };
 
 // Exclusive block scan of one double per thread; *total gets the sum.
@@ -67,10 +80,29 @@ __device__ double block_max(double v, Red &r)
     for (int d = 16; d; d >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, d));
     if ((threadIdx.x & 31) == 0) r.w[threadIdx.x >> 5] = v;
     __syncthreads();
-    double m = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, r.w[k]);
+    if (threadIdx.x < 32) {
+        double m = threadIdx.x < (blockDim.x >> 5) ? r.w[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int d = 16; d; d >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, d));
+        if (threadIdx.x == 0) r.total = fmax(m, 0.0);
+    }
+    __syncthreads();
+    const double m = r.total;
     __syncthreads();
     return m;
+}
+
+// Jacobi sweeps for a contraction ratio r: ceil(ln 2^-60 / ln r), 1..64,
+// formed by thread 0 and shared
+__device__ int jacobi_iters(double r, Red &red)
+{
+    if (threadIdx.x == 0) {
+        int iters = 1;
+        if (r > 1e-300) iters = (int)ceil(-41.58883083359672 / log(r));
+        red.iters = iters < 1 ? 1 : (iters > 64 ? 64 : iters);
+    }
+    __syncthreads();
+    return red.iters;
 }
 
 // linear interpolation in a 4-column table, clamped at the ends
@@ -169,7 +201,7 @@ struct FluidF {
 };
 
 template <bool FAST>
-__device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
+__device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, FieldConsts &fc)
 {
     const int G = K->G;
     const int T = blockDim.x;
@@ -195,6 +227,27 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
     if (t == 0) {
         red.flag = 0;
         red.count = 0ull;
+        const double mi = K->m_ion, mn = K->m_gas;
+        fc.h = dt / (2.0 * dz);
+        fc.inv2dz = 1.0 / (2.0 * dz);
+        fc.qdt_m = kQe * dt / mi;
+        fc.h_m = fc.h / mi;
+        fc.c_in = dt * fc.inv2dz;
+        fc.c_wall = dt / dz;
+        fc.gs_in = w / (dz * dt);
+        fc.gs_wall = w / (0.5 * dz * dt);
+        fc.dt_dz = dt / dz;
+        fc.dt_2dz = dt / (2.0 * dz);
+        fc.h_mion = fc.h / K->m_ion;
+        fc.w_in = w / dz;
+        fc.w_wall = 2.0 * w / dz;
+        fc.c_src = dz * dz / kEps0;
+        fc.inv_dz = 1.0 / dz;
+        fc.half_inv_dz = 0.5 / dz;
+        fc.c_gauss = dz / (2.0 * kEps0);
+        fc.phi0 = K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)(K->step + (init ? 0 : 1)) * dt));
+        fc.inv_ngas_td = (float)(1e21 / K->ngas);
+        fc.tfac = (float)((mi + mn) / (5.0 * mi + 3.0 * mn) * mn);
     }
     __syncthreads();
 
@@ -204,13 +257,12 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
         // ------------------------------------ ion fluid, FP32 coefficients
         for (int j = t; j < 4 * K->n_tab; j += T) s_tabf[j] = (float)K->tab[j];
         __syncthreads();
-        const double mi = K->m_ion, mn = K->m_gas;
-        const FluidF FF{K->ion_model, K->n_tab, s_tabf, (float)K->mu_const, (float)(1e21 / K->ngas),
-                        (float)K->kT_gas, (float)((mi + mn) / (5.0 * mi + 3.0 * mn) * mn)};
-        const double h = dt / (2.0 * dz);
-        const double inv2dz = 1.0 / (2.0 * dz);
+        const FluidF FF{K->ion_model, K->n_tab, s_tabf, (float)K->mu_const, fc.inv_ngas_td, (float)K->kT_gas,
+                        fc.tfac};
+        const double h = fc.h;
+        const double inv2dz = fc.inv2dz;
         if (K->ion_model == HYB_ION_FULL) {
-            const double qdt_m = kQe * dt / mi, h_m = h / mi;
+            const double qdt_m = fc.qdt_m, h_m = fc.h_m;
             const float hdt = (float)(0.5 * dt);
             for (int j = j0; j < j1; ++j) {
                 const double nj = s_ni[j];
@@ -239,10 +291,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
                 s_x[G - 1] = gN;
                 if (r >= 0.5) atomicOr(&K->status, (unsigned)HYB_STATUS_UNSTABLE);
             }
-            int iters = 1;
-            if (r > 1e-300) iters = (int)ceil(-41.58883083359672 / log(r));
-            iters = iters < 1 ? 1 : (iters > 64 ? 64 : iters);
-            __syncthreads();
+            const int iters = jacobi_iters(r, red);
             double *X = s_g, *Y = s_x;
             for (int it = 0; it < iters; ++it) {
                 for (int j = j0; j < j1; ++j) {
@@ -272,8 +321,8 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
             gfin = s_x;
         }
         unsigned long long clamps = 0;
-        const double c_in = dt * inv2dz, c_wall = dt / dz;
-        const double gs_in = w / (dz * dt), gs_wall = w / (0.5 * dz * dt);
+        const double c_in = fc.c_in, c_wall = fc.c_wall;
+        const double gs_in = fc.gs_in, gs_wall = fc.gs_wall;
         for (int j = j0; j < j1; ++j) {
             const bool wall = j == 0 || j == G - 1;
             const double gs = K->s_iz[j] * (wall ? gs_wall : gs_in);
@@ -309,14 +358,14 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
                 s_x[j] = nj * F.temp(F.mobility(ea), ea);
             }
             __syncthreads();
-            const double h = dt / (2.0 * dz);
+            const double h = fc.h;
             double rmax = 0.0;
             for (int j = j0; j < j1; ++j) {
                 if (j == 0 || j == G - 1) continue;
                 const double nu = F.exch(fabs(s_A[j]));
                 const double b = 1.0 + nu * dt / 2.0;
                 s_d[j] = s_g[j] * (1.0 - nu * dt / 2.0) + kQe * s_ni[j] * s_E[j] * dt / K->m_ion -
-                         h / K->m_ion * (s_x[j + 1] - s_x[j - 1]);
+                         fc.h_mion * (s_x[j + 1] - s_x[j - 1]);
                 s_ib[j] = 1.0 / b;
                 rmax = fmax(rmax, (fabs(h * s_A[j - 1]) + fabs(h * s_A[j + 1])) / b);
             }
@@ -331,10 +380,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
                 s_x[G - 1] = gN;
                 if (r >= 0.5) atomicOr(&K->status, (unsigned)HYB_STATUS_UNSTABLE);
             }
-            int iters = 1;
-            if (r > 1e-300) iters = (int)ceil(-41.58883083359672 / log(r));
-            iters = iters < 1 ? 1 : (iters > 64 ? 64 : iters);
-            __syncthreads();
+            const int iters = jacobi_iters(r, red);
             double *X = s_g, *Y = s_x;
             for (int it = 0; it < iters; ++it) {
                 for (int j = j0; j < j1; ++j) {
@@ -370,11 +416,11 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
             const double gs = w * K->s_iz[j] / (node_volume(j, G, dz) * dt);
             double nn;
             if (j == 0)
-                nn = s_ni[0] - dt / dz * (gfin[1] - gfin[0]) + dt * gs;
+                nn = s_ni[0] - fc.dt_dz * (gfin[1] - gfin[0]) + dt * gs;
             else if (j == G - 1)
-                nn = s_ni[G - 1] - dt / dz * (gfin[G - 1] - gfin[G - 2]) + dt * gs;
+                nn = s_ni[G - 1] - fc.dt_dz * (gfin[G - 1] - gfin[G - 2]) + dt * gs;
             else
-                nn = s_ni[j] - dt / (2.0 * dz) * (gfin[j + 1] - gfin[j - 1]) + dt * gs;
+                nn = s_ni[j] - fc.dt_2dz * (gfin[j + 1] - gfin[j - 1]) + dt * gs;
             if (nn < 0.0) {
                 nn = 0.0;
                 ++clamps;
@@ -391,14 +437,14 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
     }
 
     // ------------------------------------------------------------- Poisson
-    const double phi0 = K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)(K->step + (init ? 0 : 1)) * dt));
+    const double phi0 = fc.phi0;
     double *s_rho = s_A;
     double *s_S = s_ib;
     double *s_phi = s_d;
     double part = 0.0;
     // the split mode multiplies by reciprocals where the FP64 mode divides (as
     // the oracle does); FP64 division is a long instruction sequence here
-    const double w_in = w / dz, w_wall = 2.0 * w / dz, c_src = dz * dz / kEps0;
+    const double w_in = fc.w_in, w_wall = fc.w_wall, c_src = fc.c_src;
     for (int j = j0; j < j1; ++j) {
         const double ne = FAST ? K->dep_n[j] * ((j == 0 || j == G - 1) ? w_wall : w_in)
                                : w * K->dep_n[j] / node_volume(j, G, dz);
@@ -440,7 +486,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
     if (t == 0) s_phi[G - 1] = 0.0;
     __syncthreads();
     int bad = 0;
-    const double inv_dz = 1.0 / dz, half_inv_dz = 0.5 / dz, c_gauss = dz / (2.0 * kEps0);
+    const double inv_dz = fc.inv_dz, half_inv_dz = fc.half_inv_dz, c_gauss = fc.c_gauss;
     for (int j = j0; j < j1; ++j) {
         double e;
         if (FAST) {
@@ -572,16 +618,18 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf)
     }
 }
 
-template <bool FAST>
-__global__ void __launch_bounds__(kFieldThreads) k_field(InstDev *insts, int n_max, int64_t *prefix, unsigned *ticket)
+template <bool FAST, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_field(InstDev *insts, int n_max, int64_t *prefix, unsigned *ticket,
+                                                   int max_nodes)
 {
     extern __shared__ __align__(16) double sm[];
     __shared__ Red red;
     __shared__ float s_tabf[FAST ? 4 * kMaxTab : 1];
+    __shared__ FieldConsts fc;
     InstDev *K = &insts[blockIdx.x];
     const bool run = K->active || K->init_pending;
-    if (run && HYB_CHECK(K->G >= 3 && K->G <= kMaxNodes && K->n_tab <= kMaxTab, 20, K->G, kMaxNodes))
-        field_body<FAST>(K, sm, red, s_tabf);
+    if (run && HYB_CHECK(K->G >= 3 && K->G <= max_nodes && K->n_tab <= kMaxTab, 20, K->G, max_nodes))
+        field_body<FAST>(K, sm, red, s_tabf, fc);
     // the last block to finish computes the chunk prefix of the next step
     __shared__ bool s_last;
     __shared__ int64_t s_buf[HYB_MAX_INSTANCES];
@@ -610,18 +658,42 @@ void read_checks_field(unsigned long long out[3])
 
 void configure_field_kernel()
 {
-    cudaFuncSetAttribute(k_field<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)field_smem_bytes(kMaxNodes));
-    cudaFuncSetAttribute(k_field<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)field_smem_bytes(kMaxNodes));
+    const int sm = (int)field_smem_bytes(kMaxNodes);
+    cudaFuncSetAttribute(k_field<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_field<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_field<false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_field<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_field<false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_field<true, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+template <bool FAST>
+cudaError_t launch_field_t(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, int max_nodes, int threads,
+                           cudaStream_t s)
+{
+    const size_t smem = field_smem_bytes(max_nodes);
+    if (threads == 256)
+        k_field<FAST, 256><<<n_max, 256, smem, s>>>(inst, n_max, prefix, ticket, max_nodes);
+    else if (threads == 512)
+        k_field<FAST, 512><<<n_max, 512, smem, s>>>(inst, n_max, prefix, ticket, max_nodes);
+    else if (threads == 1024)
+        k_field<FAST, 1024><<<n_max, 1024, smem, s>>>(inst, n_max, prefix, ticket, max_nodes);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 // `fast`: FP32 transport coefficients (split mode); FP64 throughout otherwise.
-cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, bool fast, cudaStream_t s)
+// max_nodes bounds the node count of every instance launched (shared memory
+// is sized for it; a larger instance is skipped by the device guard);
+// threads: 256, 512 or 1024 per instance's block.
+cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, bool fast, int max_nodes,
+                         int threads, cudaStream_t s)
 {
-    if (fast)
-        k_field<true><<<n_max, kFieldThreads, field_smem_bytes(kMaxNodes), s>>>(inst, n_max, prefix, ticket);
-    else
-        k_field<false><<<n_max, kFieldThreads, field_smem_bytes(kMaxNodes), s>>>(inst, n_max, prefix, ticket);
-    return cudaGetLastError();
+    if (max_nodes < 3 || max_nodes > kMaxNodes || n_max > HYB_MAX_INSTANCES || n_max > threads)
+        return cudaErrorInvalidValue;
+    return fast ? launch_field_t<true>(inst, n_max, prefix, ticket, max_nodes, threads, s)
+                : launch_field_t<false>(inst, n_max, prefix, ticket, max_nodes, threads, s);
 }
 
 }  // namespace hyb

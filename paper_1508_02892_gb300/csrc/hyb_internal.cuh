@@ -18,7 +18,6 @@ constexpr double kAmu = 1.66053906660e-27;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 constexpr int32_t kDeadCell = INT32_MIN;  // cell index of a removed split-mode particle
-constexpr int kFieldThreads = 1024;         // one field CTA per instance
 constexpr int kMaxNodes = HYB_MAX_CELLS + 1;
 // Particle kernels split each instance's slots into chunks of kChunk slots;
 // prefix arrays hold chunk counts of the running instances.
@@ -227,7 +226,8 @@ cudaError_t launch_set_active(InstDev *inst, int active, int64_t target_step, cu
 size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins);
 
 // field kernel (hyb_field.cu)
-cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned int *ticket, bool fast, cudaStream_t s);
+cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned int *ticket, bool fast, int max_nodes,
+                         int threads, cudaStream_t s);
 size_t field_smem_bytes(int max_nodes);
 void configure_field_kernel();
 

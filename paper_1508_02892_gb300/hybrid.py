@@ -77,7 +77,7 @@ _lib = None
 
 class Tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("sort_interval", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("rate", C.c_double)]
+                ("field_threads", C.c_int32), ("rate", C.c_double)]
 
 
 EXPORTS = {
@@ -368,11 +368,12 @@ class Batch:
         _check(lib().hyb_batch_get_tuning(self.h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
-    def set_tuning(self, lanes=None, sort_interval=None, blocks_per_sm=None):
+    def set_tuning(self, lanes=None, sort_interval=None, blocks_per_sm=None, field_threads=None):
         cur = self.tuning()
         t = Tuning(int(lanes if lanes is not None else cur["lanes"]),
                    int(sort_interval if sort_interval is not None else cur["sort_interval"]),
-                   int(blocks_per_sm if blocks_per_sm is not None else cur["blocks_per_sm"]), 0.0)
+                   int(blocks_per_sm if blocks_per_sm is not None else cur["blocks_per_sm"]),
+                   int(field_threads if field_threads is not None else cur["field_threads"]), 0.0)
         _check(lib().hyb_batch_set_tuning(self.h, C.byref(t)))
         return self.tuning()
 

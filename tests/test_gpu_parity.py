@@ -133,8 +133,8 @@ def test_split_mode_statistics_config1():
         assert _l2(a, b) < 0.02, (k, _l2(a, b))
 
 
-@pytest.mark.parametrize("lanes,sort_interval", [(1, 20), (2, 7), (4, 20)])
-def test_batch_matches_single_runs_fp64(lanes, sort_interval):
+@pytest.mark.parametrize("lanes,sort_interval,field_threads", [(1, 20, 1024), (2, 7, 256), (4, 20, 512)])
+def test_batch_matches_single_runs_fp64(lanes, sort_interval, field_threads):
     """Each discharge gives the same result alone and inside a batch, whatever
     the launch layout (RNG is keyed by particle id and step, so only summation
     order differs).  250 steps cover two captured chunks plus single steps."""
@@ -144,8 +144,8 @@ def test_batch_matches_single_runs_fp64(lanes, sort_interval):
                     gamma_see=0.2, weight=2e6, v_rf_amp_v=300.0),
           W.config1(precision=W.FP64, n_particles=777, n_cells=33, seed=23, ion_model=W.ION_DD_TABLE)]
     b = hybrid.Batch(4, hybrid.HYB_FP64)
-    t = b.set_tuning(lanes=lanes, sort_interval=sort_interval)
-    assert t["sort_interval"] == sort_interval and 1 <= t["lanes"] <= lanes
+    t = b.set_tuning(lanes=lanes, sort_interval=sort_interval, field_threads=field_threads)
+    assert t["sort_interval"] == sort_interval and 1 <= t["lanes"] <= lanes and t["field_threads"] == field_threads
     slots = [b.admit(p) for p in ps]
     b.advance(250 if lanes != 4 else 50)
     for s, p in zip(slots, ps):
@@ -171,6 +171,7 @@ def test_autotune_keeps_a_valid_configuration():
     slots = [b.admit(p) for p in ps]
     t = b.autotune(100)
     assert 1 <= t["lanes"] <= 3 and t["sort_interval"] in (10, 20, 50) and t["rate"] > 0
+    assert t["field_threads"] in (256, 512, 1024)
     assert b.tuning()["lanes"] == t["lanes"]
     steps = [b.counters(s)["step"] for s in slots]
     assert min(steps) == max(steps) >= 200
