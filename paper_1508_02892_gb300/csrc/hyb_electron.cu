@@ -298,46 +298,53 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
         unsigned coll = 0u;      // 2 bits per particle: 1 elastic, 2 excitation, 3 ionization
         uint2 ru[kVec];          // direction draws of the colliding particles
         float ens[kVec];         // kinetic energies (eV) after the push
+        bool live[kVec];
 #pragma unroll
         for (int k = 0; k < kVec; ++k) {
+            // leapfrog with the CIC-gathered field (Sec. II.A), formed for every
+            // lane and kept for the live ones; the gather index is clamped so
+            // that no out-of-range address is formed
             int c = cc[k];
             float o = oo[k];
             bool alive = c >= 0 && c < nc;
-            if (MODE == 0 && alive) {
-                cnt.push_ovf += 1u;
-                // leapfrog with the CIC-gathered field (Sec. II.A); the gather
-                // index is clamped so that no out-of-range address is formed
+            if (MODE == 0) {
                 const int cg = min(max(c, 0), nc - 1);
-                const float ep = (1.f - o) * __ldg(&Ef[cg]) + o * __ldg(&Ef[cg + 1]);
-                vz[k] = vz[k] - qm_dt * ep;
-                o = o + vz[k] * dt_dz;
-                const float fl = floorf(o);
-                c += (int)fl;
-                o -= fl;
-                if (o >= 1.f) {
-                    o -= 1.f;
-                    c += 1;
-                }
-                if (c < 0 || c >= nc) {  // absorbed by an electrode and removed
-                    cnt.loss += c < 0 ? 1u : (1u << 16);
-                    alive = false;
-                    c = kDeadCell;
-                }
+                const float oi = alive ? o : 0.f;
+                const float ep = (1.f - oi) * __ldg(&Ef[cg]) + oi * __ldg(&Ef[cg + 1]);
+                const float vzn = vz[k] - qm_dt * ep;
+                float on = oi + vzn * dt_dz;
+                const float fl = floorf(on);
+                int cn = cg + (int)fl;
+                on -= fl;
+                const bool wrap = on >= 1.f;
+                on = wrap ? on - 1.f : on;
+                cn = wrap ? cn + 1 : cn;
+                const bool gone = cn < 0 || cn >= nc;  // absorbed by an electrode and removed
+                cnt.push_ovf += alive ? 1u : 0u;
+                cnt.loss += (alive && gone) ? (cn < 0 ? 1u : (1u << 16)) : 0u;
+                vz[k] = alive ? vzn : vz[k];
+                o = alive ? on : o;
+                c = cn;
+                alive = alive && !gone;
             }
-            // CIC charge assignment and energy moment, accumulated in a run
-            const float en = half_m_q * (vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
-            row_deposit(row, rbase, K, alive ? c : -1, o, MODE == 0 ? en : 0.f, G);
-            if (alive) {
-                if (MODE == 0) {
-                    int bin = (int)(en * bin_inv);
-                    if (bin > nb || bin < 0 || !(en >= 0.f)) bin = nb;  // overflow bin (also NaN)
-                    if (HYB_CHECK(bin >= 0 && bin <= nb, 5, bin, nb)) atomicAdd(&s_eedf[bin], 1u);
-                }
-            }
-
-            ens[k] = en;
+            ens[k] = half_m_q * (vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
+            live[k] = alive;
             cc[k] = alive ? c : kDeadCell;
             oo[k] = o;
+        }
+        // CIC charge assignment and energy moment, then the EEDF sample
+#pragma unroll
+        for (int k = 0; k < kVec; ++k)
+            row_deposit(row, rbase, K, live[k] ? cc[k] : -1, oo[k], MODE == 0 ? ens[k] : 0.f, G);
+        if (MODE == 0) {
+#pragma unroll
+            for (int k = 0; k < kVec; ++k) {
+                if (!live[k]) continue;
+                const float en = ens[k];
+                int bin = (int)(en * bin_inv);
+                if (bin > nb || bin < 0 || !(en >= 0.f)) bin = nb;  // overflow bin (also NaN)
+                if (HYB_CHECK(bin >= 0 && bin <= nb, 5, bin, nb)) atomicAdd(&s_eedf[bin], 1u);
+            }
         }
         if (MODE == 0) {
             // modified null-collision method: every particle draws R1 < P_max;
@@ -347,11 +354,13 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             draw_n<kVec>(pre, ids, sl, 0u, rk);
 #pragma unroll
             for (int k = 0; k < kVec; ++k) {
+                // computed for every lane without branches, so that the kVec
+                // chains interleave; only candidates keep their outcome
                 const float en = ens[k];
-                if (!(cc[k] >= 0 && cc[k] < nc) || !(u01f(rk[k].x) < pmax)) continue;
+                const bool cand = cc[k] >= 0 && cc[k] < nc && u01f(rk[k].x) < pmax;
                 const float speed = sqrtf(vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
-                // table segment without branches: below the table the first
-                // node's values, above it the last node's
+                // table segment: below the table the first node's values,
+                // above it the last node's
                 int kk = (int)(__logf(fmaxf(en, e_lo) * inv_e_lo) * inv_dlog);
                 kk = kk < 0 ? 0 : (kk > nxs - 2 ? nxs - 2 : kk);
                 const float4 lo = __ldg(&xs[kk]);
@@ -363,13 +372,31 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 const float s_iz = en < e_iz ? 0.f : (above ? hi.w : lo.w + f * (hi.w - lo.w));
                 const float t0 = s_el * speed, t1 = t0 + s_ex * speed, t2 = t1 + s_iz * speed;
                 const float r2 = u01f(rk[k].y);
-                if (r2 < t2) {
-                    const unsigned kind = r2 < t0 ? 1u : (r2 < t1 ? 2u : 3u);
-                    coll |= kind << (2 * k);
-                    ru[k] = make_uint2(rk[k].z, rk[k].w);
-                } else {
-                    cnt.iz_nul += 1u << 16;
-                }
+                const bool hit = cand && r2 < t2;
+                const unsigned kind = r2 < t0 ? 1u : (r2 < t1 ? 2u : 3u);
+                // elastic (lab-frame isotropic, energy loss (2m/M)(1 - cos chi))
+                // and excitation (E - E_exc) scatter in place, formed for every
+                // lane and kept where they happened; ionizations, which eject
+                // an electron, go to the warp pass below
+                const float v2 = vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k];
+                const float ct = 1.f - 2.f * u01f(rk[k].z);
+                const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
+                float sn, cs;
+                __sincosf(6.283185307179586f * u01f(rk[k].w), &sn, &cs);
+                const float dx = st * cs, dy = st * sn, dzz = ct;
+                const float rs = rsqrtf(v2);
+                const float cchi = (vx[k] * dx + vy[k] * dy + vz[k] * dzz) * rs;
+                const float sp_el = v2 * rs * sqrtf(1.f - two_mM * (1.f - cchi));
+                const float sp_ex = sqrtf(two_q_m * (en - e_exc));
+                const bool scat = hit && kind != 3u;
+                const float sp = kind == 1u ? sp_el : sp_ex;
+                vx[k] = scat ? sp * dx : vx[k];
+                vy[k] = scat ? sp * dy : vy[k];
+                vz[k] = scat ? sp * dzz : vz[k];
+                cnt.el_exc += scat ? (kind == 1u ? 1u : (1u << 16)) : 0u;
+                coll |= (hit && kind == 3u) ? (3u << (2 * k)) : 0u;
+                ru[k] = make_uint2(rk[k].z, rk[k].w);
+                cnt.iz_nul += (cand && !hit) ? (1u << 16) : 0u;
             }
         }
         if (++iter == kFlushIters) {
