@@ -244,9 +244,9 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
 
     // shared memory: EEDF histogram, then one deposit row per warp
     unsigned *s_eedf = reinterpret_cast<unsigned *>(smem);
-    WarpRow *rows = reinterpret_cast<WarpRow *>(smem + 4 * (((nb + 1) + 3) & ~3));
+    WarpRow *rows = reinterpret_cast<WarpRow *>(smem + 4 * (((nb + 2) + 3) & ~3));
     if (!HYB_CHECK(b <= capacity && a >= 0 && (a & (kVec - 1)) == 0, 10, b, capacity)) b = a;
-    for (int j = threadIdx.x; j <= nb; j += blockDim.x) s_eedf[j] = 0u;
+    for (int j = threadIdx.x; j <= nb + 1; j += blockDim.x) s_eedf[j] = 0u;
     {
         unsigned *r = reinterpret_cast<unsigned *>(rows);
         for (int j = threadIdx.x; j < 4 * kWin * (int)(blockDim.x >> 5); j += blockDim.x) r[j] = 0u;
@@ -337,13 +337,14 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
         for (int k = 0; k < kVec; ++k)
             row_deposit(row, rbase, K, live[k] ? cc[k] : -1, oo[k], MODE == 0 ? ens[k] : 0.f, G);
         if (MODE == 0) {
+            // EEDF sample: bin nb is the overflow (also NaN), bin nb + 1 takes the
+            // removed particles and is never read
 #pragma unroll
             for (int k = 0; k < kVec; ++k) {
-                if (!live[k]) continue;
                 const float en = ens[k];
                 int bin = (int)(en * bin_inv);
-                if (bin > nb || bin < 0 || !(en >= 0.f)) bin = nb;  // overflow bin (also NaN)
-                if (HYB_CHECK(bin >= 0 && bin <= nb, 5, bin, nb)) atomicAdd(&s_eedf[bin], 1u);
+                bin = (bin > nb || bin < 0 || !(en >= 0.f)) ? nb : bin;
+                atomicAdd(&s_eedf[live[k] ? bin : nb + 1], 1u);
             }
         }
         if (MODE == 0) {
@@ -1054,7 +1055,7 @@ int electron_blocks_per_sm(int precision, size_t smem)
 size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins)
 {
     if (precision == HYB_FP32_SPLIT)  // EEDF histogram and one deposit row per warp
-        return 4 * (size_t)(((eedf_bins + 1) + 3) & ~3) + sizeof(WarpRow) * (kBlock / 32) + 16;
+        return 4 * (size_t)(((eedf_bins + 2) + 3) & ~3) + sizeof(WarpRow) * (kBlock / 32) + 16;
     const size_t el = 8;
     return 3 * el * (size_t)max_nodes + 4 * (size_t)(eedf_bins + 1) + 16;
 }
