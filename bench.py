@@ -118,9 +118,8 @@ def traffic_per_push():
 
 
 def workload(rank=0, n_inst=64, scale=1.0):
-    from paper_1508_02892_gb300 import workloads as W
-    inst = W.config3_instances(n=n_inst, seed=2026 + 7919 * rank, scale=scale)
-    return inst
+    from paper_1508_02892_gb300 import shard, workloads as W
+    return W.config3_instances(n=n_inst, seed=shard.instance_seed(rank), scale=scale)
 
 
 def cpu_baseline(params_list, budget_s=12.0, window=6):
@@ -213,8 +212,8 @@ def serve_load(args, stream, rank=0, world=1, tuning=None):
     requests are dealt to ranks round-robin."""
     from paper_1508_02892_gb300 import hybrid, workloads as W
     from paper_1508_02892_gb300.serve import Server, summarize
-    reqs = W.config4_requests(n_requests=args.serve_requests, steps=args.serve_steps)
-    reqs = [r for k, r in enumerate(reqs) if k % world == rank]
+    from paper_1508_02892_gb300 import shard
+    reqs = shard.rank_share(W.config4_requests(n_requests=args.serve_requests, steps=args.serve_steps), rank, world)
     srv = Server(max_slots=64, hbm_cap_bytes=120e9, precision=hybrid.HYB_FP32_SPLIT, stream=stream.cuda_stream,
                  tuning=tuning)
     t0 = time.perf_counter()
@@ -288,15 +287,8 @@ def run_ours(args):
     ms_local = sum(lat)
     prof1 = b.profile()
     n_local = pushes() - p0
-    if world > 1:
-        t = torch.tensor([ms_local, float(n_local)], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_tot, n_tot = mx[0].item(), sm[1].item()
-    else:
-        ms_tot, n_tot = ms_local, float(n_local)
+    from paper_1508_02892_gb300 import shard
+    ms_tot, n_tot = shard.aggregate(ms_local, n_local, device="cuda")
     value = n_tot / (ms_tot / 1e3)
 
     # roofline of the dominant kernel (electron step), timed alone: one lane,
@@ -358,8 +350,14 @@ def run_ours(args):
                        "moments, eviction, all inside the wall-clock region"}
 
     serving = None
-    if rank == 0 and args.serve_requests > 0:
-        serving = serve_load(args, stream, tuning={k: tuning[k] for k in ("lanes", "sort_interval", "blocks_per_sm", "field_threads")})
+    if args.serve_requests > 0:
+        # every rank serves its round-robin share of the requests on its GPU
+        barrier()
+        serving = serve_load(args, stream, rank, world,
+                             tuning={k: tuning[k] for k in ("lanes", "sort_interval", "blocks_per_sm", "field_threads")})
+        wall_ms, steps_all = shard.aggregate(serving["wall_s"] * 1e3, serving["particle_steps"], device="cuda")
+        serving["throughput_all_ranks"] = steps_all / (wall_ms / 1e3)
+        serving["latency_ranks"] = "rank 0's requests" if world > 1 else "all requests"
 
     fp64 = None
     if rank == 0 and not args.no_fp64:
