@@ -68,6 +68,20 @@ class OrcParams(C.Structure):
     ]
 
 
+class OrcSwarmParams(C.Structure):
+    _fields_ = [("gas_mass_amu", C.c_double), ("ion_mass_amu", C.c_double), ("pressure_pa", C.c_double),
+                ("gas_temp_k", C.c_double), ("ion_temp0_k", C.c_double), ("dt_s", C.c_double),
+                ("e_field", C.c_double), ("nu_max", C.c_double), ("eps_max_ev", C.c_double),
+                ("n_ions", C.c_int64), ("n_steps", C.c_int64), ("n_relax", C.c_int64), ("id_base", C.c_int64),
+                ("xs_model", C.c_int32), ("seed", C.c_uint64)]
+
+
+class OrcSwarmResult(C.Structure):
+    _fields_ = [("drift", C.c_double), ("mean_energy_ev", C.c_double), ("mobility", C.c_double),
+                ("nu_exchange", C.c_double), ("nu_max", C.c_double), ("p_max", C.c_double),
+                ("candidates", C.c_int64), ("collisions", C.c_int64), ("overruns", C.c_int64)]
+
+
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -112,6 +126,11 @@ def lib():
                 "orc_poisson": (None, [C.c_int, dbl, pd, dbl, dbl, pd, pd]),
                 "orc_fluid_update": (i64, [vp, pd, pd, pd, pd, pd]),
                 "orc_particle_step_one": (C.c_int, [vp, pd, u32, pd, u64, pd, pd, pu64]),
+                "orc_swarm_run": (None, [C.POINTER(OrcSwarmParams), C.POINTER(OrcSwarmResult), pd]),
+                "orc_swarm_nu": (dbl, [dbl, dbl, C.c_int, dbl]),
+                "orc_swarm_nu_bound": (dbl, [dbl, dbl, C.c_int, dbl]),
+                "orc_swarm_qi": (dbl, [dbl]),
+                "orc_swarm_qb": (dbl, [dbl]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -122,6 +141,23 @@ def lib():
 
 
 # ----------------------------------------------------------------- helpers ---
+
+def swarm_run(params: dict, e_field: float, id_base: int = 0, velocities: bool = False):
+    """The ion-swarm Monte Carlo of Sec. II.C at one field value (ions
+    id_base .. id_base + n_ions - 1); returns the result dict and, if asked,
+    the final velocities (n_ions x 3)."""
+    p = OrcSwarmParams()
+    for name, _ in OrcSwarmParams._fields_:
+        if name in params:
+            setattr(p, name, params[name])
+    p.e_field = float(e_field)
+    p.id_base = int(id_base)
+    r = OrcSwarmResult()
+    v = np.zeros(3 * int(p.n_ions)) if velocities else None
+    lib().orc_swarm_run(C.byref(p), C.byref(r), _dp(v) if v is not None else None)
+    out = {f: getattr(r, f) for f, _ in OrcSwarmResult._fields_}
+    return (out, v.reshape(-1, 3)) if velocities else out
+
 
 def philox4x32_10(ctr, key):
     c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])

@@ -974,3 +974,150 @@ int64_t orc_emit_only(orc_sim *s, uint32_t n)
     emit_secondaries(s, n);
     return s->np - before;
 }
+
+/* ------------------------------------------------------------------------
+ * Auxiliary ion-swarm Monte Carlo (Sec. II.C).  One ion species is followed
+ * in a prescribed constant field E0 (along z) in a homogeneous, periodic
+ * domain, so positions play no part; collisions with the neutral gas at T_N
+ * are sampled by the null-collision method and scatter isotropically in the
+ * centre-of-mass frame on Q_m = Q_i + 2 Q_b (the Phelps prescription the
+ * paper adopts).  The He+/He cross sections are the ones quoted with
+ * Tables 2/3: Q_i = 7.63e-20 / sqrt(eps), Q_b = 1e-19 / [(eps/1000)^0.15
+ * (1 + eps/1000)^0.25 (1 + 5/eps)^0.15] m^2, eps = M_r g^2 / 2 in eV with g the
+ * relative speed.  The ensemble's mean velocity after the relaxation window is
+ * the drift u; the mobility is u/E0 and Eq. 2.6 gives the momentum-exchange
+ * frequency nu = e/(M mu).  xs_model 1 keeps Q_i only: then N Q g does not
+ * depend on g (a Maxwell-molecule gas), which gives a closed form to test
+ * against.
+ */
+typedef struct orc_swarm_params {
+    double gas_mass_amu, ion_mass_amu, pressure_pa, gas_temp_k, ion_temp0_k;
+    double dt_s, e_field, nu_max, eps_max_ev;
+    int64_t n_ions, n_steps, n_relax, id_base;
+    int32_t xs_model;
+    uint64_t seed;
+} orc_swarm_params;
+
+typedef struct orc_swarm_result {
+    double drift, mean_energy_ev, mobility, nu_exchange, nu_max, p_max;
+    int64_t candidates, collisions, overruns;
+} orc_swarm_result;
+
+/* Q_i and Q_b of the He+/He fits, eps > 0 in eV */
+double orc_swarm_qi(double eps) { return 7.63e-20 / sqrt(eps); }
+double orc_swarm_qb(double eps)
+{
+    return 1e-19 / (pow(eps / 1000.0, 0.15) * pow(1.0 + eps / 1000.0, 0.25) * pow(1.0 + 5.0 / eps, 0.15));
+}
+
+/* collision frequency N Q_m(eps(g)) g at relative speed g */
+double orc_swarm_nu(double ngas, double m_red, int xs_model, double g)
+{
+    if (!(g > 0.0)) {  /* the g -> 0 limits: Q_i g finite, Q_b g -> 0 */
+        return ngas * 7.63e-20 * sqrt(2.0 * Q_E / m_red);
+    }
+    double eps = 0.5 * m_red * g * g / Q_E;
+    double q = orc_swarm_qi(eps);
+    if (xs_model == 0) q += 2.0 * orc_swarm_qb(eps);
+    return ngas * q * g;
+}
+
+/* the bound nu_max: the largest N Q_m g over relative energies up to eps_max
+ * (a dense logarithmic grid, then a relative margin of 1e-6) */
+double orc_swarm_nu_bound(double ngas, double m_red, int xs_model, double eps_max)
+{
+    double best = 0.0;
+    const int n = 200000;
+    for (int i = 0; i <= n; ++i) {
+        double eps = 1e-8 * pow(eps_max / 1e-8, (double)i / n);
+        double g = sqrt(2.0 * Q_E * eps / m_red);
+        double v = orc_swarm_nu(ngas, m_red, xs_model, g);
+        if (v > best) best = v;
+    }
+    return best * (1.0 + 1e-6);
+}
+
+static void swarm_draws(const orc_swarm_params *p, uint64_t id, uint32_t step, uint32_t call, double u[4])
+{
+    uint32_t ctr[4] = {step, (uint32_t)p->seed, (uint32_t)(p->seed >> 32), call};
+    uint32_t key[2] = {(uint32_t)id, (uint32_t)(id >> 32)};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    for (int i = 0; i < 4; ++i) u[i] = orc_u01(r[i]);
+}
+
+/* One run at one field value.  Ion i (id id_base + i) starts from a
+ * Maxwellian at T_i0 drawn at step 0xFFFFFFFF; each step n: v_z += (e E0/M) dt,
+ * then R1 < P_max makes it a candidate, a neutral velocity is drawn from the
+ * Maxwellian at T_N, and R2 nu_max < N Q_m(eps) g makes the collision real.
+ * The velocities of every ion after the last step go to v_out (3 per ion, may
+ * be NULL). */
+void orc_swarm_run(const orc_swarm_params *p, orc_swarm_result *res, double *v_out)
+{
+    const double mg = p->gas_mass_amu > 0 ? p->gas_mass_amu : 4.002602;
+    const double M = (p->ion_mass_amu > 0 ? p->ion_mass_amu : mg) * AMU;
+    const double mn = mg * AMU;
+    const double m_red = M * mn / (M + mn);
+    const double ngas = p->pressure_pa / (K_B * p->gas_temp_k);
+    const double nu_max = p->nu_max > 0 ? p->nu_max
+                                        : orc_swarm_nu_bound(ngas, m_red, p->xs_model,
+                                                             p->eps_max_ev > 0 ? p->eps_max_ev : 100.0);
+    const double p_max = -expm1(-nu_max * p->dt_s);
+    const double acc = Q_E * p->e_field / M * p->dt_s;
+    const double vt0 = sqrt(K_B * p->ion_temp0_k / M);
+    const double vtn = sqrt(K_B * p->gas_temp_k / mn);
+    double sum_vz = 0.0, sum_en = 0.0;
+    int64_t cand = 0, coll = 0, over = 0;
+    for (int64_t i = 0; i < p->n_ions; ++i) {
+        const uint64_t id = (uint64_t)(p->id_base + i);
+        double u[4], w[4], g1, g2, g3, g4;
+        swarm_draws(p, id, 0xFFFFFFFFu, 0, u);
+        gauss2(u[0], u[1], &g1, &g2);
+        gauss2(u[2], u[3], &g3, &g4);
+        double v[3] = {vt0 * g1, vt0 * g2, vt0 * g3};
+        for (int64_t n = 0; n < p->n_steps; ++n) {
+            v[2] += acc;
+            swarm_draws(p, id, (uint32_t)n, 0, u);
+            if (u[0] < p_max) {
+                ++cand;
+                swarm_draws(p, id, (uint32_t)n, 1, w);
+                double a1, a2, a3, a4;
+                gauss2(u[2], u[3], &a1, &a2);
+                gauss2(w[0], w[1], &a3, &a4);
+                const double V[3] = {vtn * a1, vtn * a2, vtn * a3};
+                const double gv[3] = {v[0] - V[0], v[1] - V[1], v[2] - V[2]};
+                const double g = sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
+                const double nu = orc_swarm_nu(ngas, m_red, p->xs_model, g);
+                if (nu > nu_max) ++over;
+                if (u[1] * nu_max < nu) {
+                    ++coll;
+                    double d[3];
+                    iso_dir(w[2], w[3], d);
+                    for (int k = 0; k < 3; ++k) {
+                        const double vc = (M * v[k] + mn * V[k]) / (M + mn);
+                        v[k] = vc + mn / (M + mn) * g * d[k];
+                    }
+                }
+            }
+            if (n >= p->n_relax) {
+                sum_vz += v[2];
+                sum_en += 0.5 * M * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / Q_E;
+            }
+        }
+        if (v_out) {
+            v_out[3 * i] = v[0];
+            v_out[3 * i + 1] = v[1];
+            v_out[3 * i + 2] = v[2];
+        }
+    }
+    const double ns = (double)p->n_ions * (double)(p->n_steps - p->n_relax);
+    res->drift = ns > 0 ? sum_vz / ns : 0.0;
+    res->mean_energy_ev = ns > 0 ? sum_en / ns : 0.0;
+    res->mobility = p->e_field != 0.0 ? res->drift / p->e_field : 0.0;
+    res->nu_exchange = res->mobility != 0.0 ? Q_E / (M * res->mobility) : 0.0;
+    res->nu_max = nu_max;
+    res->p_max = p_max;
+    res->candidates = cand;
+    res->collisions = coll;
+    res->overruns = over;
+}

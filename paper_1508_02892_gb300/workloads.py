@@ -178,3 +178,24 @@ def random_particles(n: int, gap_m: float, te_ev: float, seed: int, id_base: int
     v = rng.normal(0.0, vth, (3, n))
     return {"z": z, "vx": v[0].copy(), "vy": v[1].copy(), "vz": v[2].copy(),
             "id": np.arange(id_base, id_base + n, dtype=np.uint64)}
+
+
+SWARM_QM, SWARM_QI_ONLY = 0, 1
+
+
+def swarm_params(**kw) -> dict:
+    """Auxiliary ion swarm (Sec. II.C): He+ in He at 1 atm and 300 K, ions
+    starting from a 300 K Maxwellian, dt 1e-13 s, 20000 steps of which the
+    first 4000 relax, Q_m = Q_i + 2 Q_b, FP64, collision bound over relative
+    energies up to 10 eV."""
+    p = dict(gas_mass_amu=0.0, ion_mass_amu=0.0, pressure_pa=101325.0, gas_temp_k=300.0, ion_temp0_k=300.0,
+             dt_s=1e-13, nu_max=0.0, eps_max_ev=10.0, n_ions=4096, n_steps=20000, n_relax=4000,
+             xs_model=SWARM_QM, precision=FP64, seed=11)
+    p.update(kw)
+    return p
+
+
+def swarm_fields(n: int = 64, e_max: float = 5e6) -> np.ndarray:
+    """Field values for a mobility table: n points evenly spaced in (0, e_max]."""
+    return np.linspace(e_max / n, e_max, n)
+
