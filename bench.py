@@ -226,6 +226,39 @@ def serve_load(args, stream, rank=0, world=1, tuning=None):
     return s
 
 
+def swarm_load(n_fields=64, n_ions=65536, n_steps=20000):
+    """Auxiliary ion swarm (Sec. II.C) at the size a mobility table is built:
+    64 field values up to 5 MV/m, He+ in He at 1 atm; FP32 and FP64 device
+    time (CUDA events around the call, which includes its small copies), and
+    the oracle on one core for a bounded sample."""
+    import torch
+
+    import oracle
+    from paper_1508_02892_gb300 import hybrid, workloads as W
+    fields = W.swarm_fields(n_fields, 5e6)
+    out = {"fields": n_fields, "ions_per_field": n_ions, "steps": n_steps,
+           "unit": "ion-steps/s", "data": "synthetic: He+/He cross-section fits quoted with Tables 2/3"}
+    s = torch.cuda.current_stream()
+    for prec, name in ((W.FP32_SPLIT, "fp32"), (W.FP64, "fp64")):
+        p = W.swarm_params(n_ions=n_ions, n_steps=n_steps, n_relax=n_steps // 5, precision=prec)
+        hybrid.swarm_run(dict(p, n_steps=200, n_relax=100), fields[:2])      # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        res, rc = hybrid.swarm_run(p, fields)
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"value": n_fields * n_ions * n_steps / (ms / 1e3), "ms": ms, "rc": rc,
+                     "mobility_at_5MV_m": res[-1]["mobility"]}
+    p = W.swarm_params(n_ions=200, n_steps=2000, n_relax=400)
+    t0 = time.perf_counter()
+    oracle.swarm_run(p, 1e6)
+    dt = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": 200 * 2000 / dt, "cores": 1, "kind": "oracle",
+                           "sample": "200 ions x 2000 steps at 1 MV/m"}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -349,6 +382,10 @@ def run_ours(args):
                "note": "admission from host parameters and tables (pageable), per-chunk host read of all "
                        "moments, eviction, all inside the wall-clock region"}
 
+    swarm = None
+    if rank == 0 and not args.no_swarm:
+        swarm = swarm_load(n_ions=args.swarm_ions, n_steps=args.swarm_steps)
+
     serving = None
     if args.serve_requests > 0:
         # every rank serves its round-robin share of the requests on its GPU
@@ -398,6 +435,8 @@ def run_ours(args):
         line["e2e"] = e2e
     if serving:
         line["serving"] = serving
+    if swarm:
+        line["swarm"] = swarm
     if cpu:
         line["cpu_baseline"] = cpu
     line["device_index_guards"] = hybrid.debug_checks()
@@ -421,6 +460,10 @@ def main():
     ap.add_argument("--lanes", type=int, default=0, help="fixed lane count instead of the autotuner's")
     ap.add_argument("--serve-requests", type=int, default=100, help="config-4 serving requests (0: none)")
     ap.add_argument("--serve-steps", type=int, default=5000)
+    ap.add_argument("--no-swarm", action="store_true")
+    ap.add_argument("--swarm-ions", type=int, default=65536, help="ions per field of the swarm run")
+    ap.add_argument("--swarm-steps", type=int, default=20000)
+    ap.add_argument("--only-swarm", action="store_true", help="run and print the ion-swarm measurement alone")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -431,6 +474,14 @@ def main():
         import oracle
         oracle.build()
         run_reference(args)
+        return
+    if args.only_swarm:
+        import torch
+
+        import __graft_entry__ as G
+        G.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps({"swarm": swarm_load(n_ions=args.swarm_ions, n_steps=args.swarm_steps)}), flush=True)
         return
     run_ours(args)
 

@@ -37,6 +37,7 @@ extern "C" {
 /* ------------------------------------------------------------ status codes */
 #define HYB_OK 0
 #define HYB_WARN_DT_NULLCOLL 1  /* nu_max*dt > 0.1: coarser than the time-step rule of Sec. II.A */
+#define HYB_WARN_NU_MAX 2       /* ion swarm: a collision frequency exceeded nu_max (result biased) */
 #define HYB_ERR_ARG (-1)        /* invalid argument or parameter */
 #define HYB_ERR_OOM (-2)        /* device memory, or the batch's HBM cap, exhausted */
 #define HYB_ERR_CAPACITY (-3)   /* particle store full: births were dropped */
@@ -286,6 +287,73 @@ hyb_batch *hyb_discharge_batch(hyb_discharge *h);
  * kernels; out[3..5] the same for the field kernel.  A failed guard skips the
  * access it protects, so a nonzero site means results are not to be trusted. */
 int hyb_debug_checks(uint64_t out[6]);
+
+/* ------------------------------------------------ auxiliary ion swarm
+ *
+ * The auxiliary Monte Carlo of Sec. II.C that gives the ion mobility and the
+ * momentum-exchange frequency of the fluid model: ions of one species move in
+ * a prescribed constant field E0 (along z) through a homogeneous, periodic
+ * domain and collide with the neutral gas at T_N by the null-collision method
+ * (a neutral velocity drawn from the Maxwellian at T_N for every candidate,
+ * acceptance R2 nu_max < N Q_m(eps) g), scattering isotropically in the
+ * centre-of-mass frame on Q_m = Q_i + 2 Q_b.  The cross sections are the
+ * He+/He fits quoted with Tables 2/3: Q_i = 7.63e-20/sqrt(eps),
+ * Q_b = 1e-19/[(eps/1000)^0.15 (1+eps/1000)^0.25 (1+5/eps)^0.15] m^2, with eps
+ * = M_r g^2/2 in eV and g the relative speed.  HYB_SWARM_QI_ONLY keeps Q_i
+ * alone (N Q g independent of g: a Maxwell-molecule gas).  The drift u is the
+ * ensemble mean of v_z over steps n_relax..n_steps-1; mobility = u/E0 and, by
+ * Eq. 2.6, nu = e/(M mobility).
+ *
+ * Random numbers: Philox4x32-10 keyed by the ion id (ion i of field f has id
+ * f*n_ions + i), counter (step, seed_lo, seed_hi, call): call 0 = (R1, R2,
+ * two Box-Muller uniforms), call 1 = (two Box-Muller uniforms, the scattering
+ * direction cos and phi); the initial Maxwellian at T_i0 is drawn at step
+ * 0xFFFFFFFF. */
+#define HYB_SWARM_QM 0       /* Q_m = Q_i + 2 Q_b (the paper's prescription) */
+#define HYB_SWARM_QI_ONLY 1  /* Q_i only: constant collision frequency */
+
+typedef struct hyb_swarm_params {
+    double gas_mass_amu;   /* 0: helium, 4.002602 */
+    double ion_mass_amu;   /* 0: the gas mass */
+    double pressure_pa, gas_temp_k;
+    double ion_temp0_k;    /* initial Maxwellian of the ions */
+    double dt_s;
+    double nu_max;         /* null-collision bound, s^-1 (0: the largest N Q_m g up to eps_max_ev) */
+    double eps_max_ev;     /* relative energy covered by the computed bound (0: 100 eV) */
+    int64_t n_ions;        /* ions per field value */
+    int64_t n_steps;       /* steps per run (< 2^32) */
+    int64_t n_relax;       /* steps before the averaging window */
+    int32_t xs_model;      /* HYB_SWARM_QM or HYB_SWARM_QI_ONLY */
+    int32_t precision;     /* HYB_FP64 (FP64 velocities and arithmetic) or HYB_FP32_SPLIT (FP32) */
+    uint64_t seed;
+} hyb_swarm_params;
+
+typedef struct hyb_swarm_result {
+    double e_field;        /* V/m, as given */
+    double drift;          /* m/s: mean v_z over the window */
+    double mean_energy_ev; /* mean kinetic energy over the window */
+    double mobility;       /* drift / e_field (0 at zero field) */
+    double nu_exchange;    /* e / (M mobility), Eq. 2.6 (0 at zero field) */
+    double nu_max, p_max;  /* the bound used and 1 - exp(-nu_max dt) */
+    int64_t candidates, collisions, overruns; /* overruns: candidates with N Q_m g > nu_max */
+} hyb_swarm_result;
+
+/* Run the swarm at n_fields field values (host array, V/m) at once; out[f]
+ * (host, n_fields entries) receives the results.  v_out: NULL, or a device
+ * array of 3*n_ions*n_fields doubles that receives every ion's final
+ * velocity (ion i of field f at 3*(f*n_ions + i)).  Allocates and frees its
+ * own small device scratch; synchronous on `stream`.  Returns
+ * HYB_WARN_NU_MAX (> 0, results filled) when some candidate's collision
+ * frequency exceeded nu_max. */
+int hyb_swarm_run(const hyb_swarm_params *p, int32_t n_fields, const double *e_field, hyb_swarm_result *out,
+                  double *v_out, void *stream);
+
+/* Transport tables for the ion fluid (the tab_eon_td / tab_mu / tab_nu of
+ * hyb_params) from swarm runs at E = (E/N) N for the n increasing E/N values
+ * (Td, host); at E/N = 0 the table takes the values of the lowest positive
+ * point.  tab_mu, tab_nu: host arrays of n values. */
+int hyb_swarm_tables(const hyb_swarm_params *p, int32_t n, const double *eon_td, double *tab_mu, double *tab_nu,
+                     void *stream);
 
 /* The field of a particle set, computed without allocating device memory.
  * The paper has no counterpart: this is a service for callers that cannot

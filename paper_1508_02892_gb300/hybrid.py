@@ -75,6 +75,20 @@ class Profile(C.Structure):
 
 _lib = None
 
+class SwarmParams(C.Structure):
+    _fields_ = [("gas_mass_amu", C.c_double), ("ion_mass_amu", C.c_double), ("pressure_pa", C.c_double),
+                ("gas_temp_k", C.c_double), ("ion_temp0_k", C.c_double), ("dt_s", C.c_double),
+                ("nu_max", C.c_double), ("eps_max_ev", C.c_double), ("n_ions", C.c_int64), ("n_steps", C.c_int64),
+                ("n_relax", C.c_int64), ("xs_model", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint64)]
+
+
+class SwarmResult(C.Structure):
+    _fields_ = [("e_field", C.c_double), ("drift", C.c_double), ("mean_energy_ev", C.c_double),
+                ("mobility", C.c_double), ("nu_exchange", C.c_double), ("nu_max", C.c_double),
+                ("p_max", C.c_double), ("candidates", C.c_int64), ("collisions", C.c_int64),
+                ("overruns", C.c_int64)]
+
+
 class Tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("sort_interval", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("field_threads", C.c_int32), ("rate", C.c_double)]
@@ -112,6 +126,9 @@ EXPORTS = {
     "hyb_batch_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(Tuning)]),
     "hyb_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Tuning)]),
     "hyb_discharge_batch": (C.c_void_p, [C.c_void_p]),
+    "hyb_swarm_run": (C.c_int, [C.POINTER(SwarmParams), C.c_int32, _pd, C.POINTER(SwarmResult), C.c_void_p,
+                                C.c_void_p]),
+    "hyb_swarm_tables": (C.c_int, [C.POINTER(SwarmParams), C.c_int32, _pd, _pd, _pd, C.c_void_p]),
     "hyb_debug_checks": (C.c_int, [C.POINTER(C.c_uint64)]),
     "hyb_field_from_particles_noalloc": (C.c_int, [C.POINTER(Params), C.c_int64, C.c_void_p, C.c_void_p,
                                                    C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -386,3 +403,36 @@ class Batch:
         r, n, b = C.c_int32(0), C.c_int64(0), C.c_int64(0)
         _check(lib().hyb_batch_stats(self.h, C.byref(r), C.byref(n), C.byref(b)))
         return {"running": r.value, "particles": n.value, "bytes": b.value}
+
+
+def _swarm_struct(params: dict):
+    p = SwarmParams()
+    for name, _ in SwarmParams._fields_:
+        if name in params:
+            setattr(p, name, params[name])
+    return p
+
+
+def swarm_run(params: dict, fields, velocities=None, stream=None):
+    """hyb_swarm_run at the given field values (V/m).  velocities: None, or a
+    device buffer (an object with data_ptr(), 3 * n_ions * len(fields)
+    doubles) that receives the final ion velocities.  Returns one dict per
+    field and the return code (HYB_WARN_NU_MAX when the bound was exceeded)."""
+    p = _swarm_struct(params)
+    f = _arr(fields)
+    out = (SwarmResult * f.size)()
+    rc = _check(lib().hyb_swarm_run(C.byref(p), f.size, f.ctypes.data_as(_pd), out,
+                                    velocities.data_ptr() if velocities is not None else None,
+                                    _default_stream(stream)))
+    return [{k: getattr(r, k) for k, _ in SwarmResult._fields_} for r in out], rc
+
+
+def swarm_tables(params: dict, eon_td, stream=None):
+    """hyb_swarm_tables: mobility and exchange-frequency tables over E/N (Td)."""
+    p = _swarm_struct(params)
+    x = _arr(eon_td)
+    mu, nu = np.zeros(x.size), np.zeros(x.size)
+    rc = _check(lib().hyb_swarm_tables(C.byref(p), x.size, x.ctypes.data_as(_pd), mu.ctypes.data_as(_pd),
+                                       nu.ctypes.data_as(_pd), _default_stream(stream)))
+    return mu, nu, rc
+

@@ -50,7 +50,8 @@ def test_binding_structs_match_header_field_order():
     from paper_1508_02892_gb300 import hybrid
     with open(os.path.join(ROOT, "include", "hybrid1d.h")) as f:
         src = f.read()
-    for cname, py in (("hyb_params", hybrid.Params), ("hyb_tuning", hybrid.Tuning), ("hyb_profile", hybrid.Profile)):
+    for cname, py in (("hyb_params", hybrid.Params), ("hyb_tuning", hybrid.Tuning), ("hyb_profile", hybrid.Profile),
+                      ("hyb_swarm_params", hybrid.SwarmParams), ("hyb_swarm_result", hybrid.SwarmResult)):
         assert _struct_fields(src, cname) == [f for f, _ in py._fields_], cname
 
 

@@ -99,6 +99,15 @@ def _table2(E):
     return (1.18 - 0.185 * E / E0) * 1e-3 if E < E0 else 0.94 * (E0 / E) ** 0.3 * 1e-3
 
 
+def _table2_ok(E, mu, rel=0.08):
+    """Within rel of Table 2; the paper's two-piece fit jumps by 5.5 % at E0 =
+    1.47 MV/m, so within 5 % of E0 either branch counts."""
+    E0 = 1.47e6
+    branches = [(1.18 - 0.185 * E / E0) * 1e-3, 0.94 * (E0 / E) ** 0.3 * 1e-3] if abs(E / E0 - 1) < 0.05 \
+        else [_table2(E)]
+    return any(abs(mu / b - 1) <= rel for b in branches)
+
+
 def _table3(u):
     """Table 3 of the paper: He+ momentum-exchange frequency fit, 1e10 s^-1."""
     u0 = 2e3
@@ -114,7 +123,7 @@ def test_mobility_reproduces_the_paper_tables(E):
     p = W.swarm_params(n_ions=400, n_steps=16000, n_relax=3000, seed=21)
     r = oracle.swarm_run(p, E)
     assert r["overruns"] == 0
-    assert r["mobility"] == pytest.approx(_table2(E), rel=0.08)
+    assert _table2_ok(E, r["mobility"])
     assert r["nu_exchange"] == pytest.approx(_table3(r["drift"]), rel=0.08)
     # Eq. 2.6 ties the two outputs
     assert r["nu_exchange"] * r["mobility"] * M_HE / QE == pytest.approx(1.0, rel=1e-12)
