@@ -34,24 +34,43 @@ struct SwarmConst {
     uint32_t seed_lo, seed_hi;
 };
 
+// the math functions in the precision of the build; the FP32 build takes the
+// hardware approximations (relative error near 2^-21, far below the Monte
+// Carlo noise), the FP64 build the accurate library functions
+__device__ __forceinline__ float m_pow(float a, float b) { return __powf(a, b); }
+__device__ __forceinline__ double m_pow(double a, double b) { return pow(a, b); }
+__device__ __forceinline__ float m_sqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double m_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float m_log(float a) { return __logf(a); }
+__device__ __forceinline__ double m_log(double a) { return log(a); }
+__device__ __forceinline__ float m_fmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double m_fmax(double a, double b) { return fmax(a, b); }
+
 // Q_b of the He+/He fit at relative energy eps > 0 (eV)
 template <typename T>
 __device__ __forceinline__ T q_back(T eps)
 {
-    return T(1e-19) / (pow(eps / T(1000), T(0.15)) * pow(T(1) + eps / T(1000), T(0.25)) * pow(T(1) + T(5) / eps, T(0.15)));
+    return T(1e-19) / (m_pow(eps / T(1000), T(0.15)) * m_pow(T(1) + eps / T(1000), T(0.25)) *
+                       m_pow(T(1) + T(5) / eps, T(0.15)));
 }
 
-// N Q_m(eps(g)) g, eps = M_r g^2 / 2 in eV; at g = 0 the limit (Q_i g finite,
-// Q_b g -> 0)
+// the instance constants of the collision frequency in the build's precision
 template <typename T>
-__device__ __forceinline__ T swarm_nu(const SwarmConst &c, T g)
+struct NuConst {
+    T ngas, m_red, limit;  // limit: the g -> 0 value N Q_i g (Q_b g -> 0)
+    int xs_model;
+};
+
+// N Q_m(eps(g)) g, eps = M_r g^2 / 2 in eV
+template <typename T>
+__device__ __forceinline__ T swarm_nu(const NuConst<T> &c, T g)
 {
     const T e = T(1.602176634e-19);
-    if (!(g > T(0))) return T(c.ngas) * T(7.63e-20) * sqrt(T(2) * e / T(c.m_red));
-    const T eps = T(0.5) * T(c.m_red) * g * g / e;
-    T q = T(7.63e-20) / sqrt(eps);
+    if (!(g > T(0))) return c.limit;
+    const T eps = T(0.5) * c.m_red * g * g / e;
+    T q = T(7.63e-20) / m_sqrt(eps);
     if (c.xs_model == HYB_SWARM_QM) q += T(2) * q_back(eps);
-    return T(c.ngas) * q * g;
+    return c.ngas * q * g;
 }
 
 template <typename T>
@@ -62,12 +81,12 @@ template <>
 __device__ __forceinline__ float u01<float>(uint32_t x) { return u01f(x); }
 
 __device__ __forceinline__ void sin_cos(double x, double *s, double *c) { sincos(x, s, c); }
-__device__ __forceinline__ void sin_cos(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sin_cos(float x, float *s, float *c) { __sincosf(x, s, c); }
 
 template <typename T>
 __device__ __forceinline__ void box_muller(T u1, T u2, T &g1, T &g2)
 {
-    const T r = sqrt(T(-2) * log(u1));
+    const T r = m_sqrt(T(-2) * m_log(u1));
     T s, c;
     sin_cos(T(6.283185307179586476925286766559) * u2, &s, &c);
     g1 = r * c;
@@ -94,6 +113,12 @@ __global__ void __launch_bounds__(kSwarmBlock) k_swarm(SwarmConst c, const doubl
         const T vt0 = T(c.vt0), vtn = T(c.vtn);
         const T M = T(c.M), mn = T(c.mn);
         const T nu_max = T(c.nu_max), p_max = T(c.p_max);
+        NuConst<T> nc;
+        nc.ngas = T(c.ngas);
+        nc.m_red = T(c.m_red);
+        nc.limit = T(c.ngas) * T(7.63e-20) * m_sqrt(T(2) * T(1.602176634e-19) / T(c.m_red));
+        nc.xs_model = c.xs_model;
+        const T mt = M + mn;
         T vx, vy, vz;
         T p_vz = T(0), p_v2 = T(0);
         int run = 0;
@@ -118,17 +143,16 @@ __global__ void __launch_bounds__(kSwarmBlock) k_swarm(SwarmConst c, const doubl
                 box_muller(u01<T>(w.x), u01<T>(w.y), a3, a4);
                 const T Vx = vtn * a1, Vy = vtn * a2, Vz = vtn * a3;
                 const T gx = vx - Vx, gy = vy - Vy, gz = vz - Vz;
-                const T g = sqrt(gx * gx + gy * gy + gz * gz);
-                const T nu = swarm_nu<T>(c, g);
+                const T g = m_sqrt(gx * gx + gy * gy + gz * gz);
+                const T nu = swarm_nu<T>(nc, g);
                 n_over += nu > nu_max ? 1ull : 0ull;
                 if (u01<T>(r.y) * nu_max < nu) {
                     ++n_coll;
                     // isotropic in the centre-of-mass frame
                     const T ct = T(1) - T(2) * u01<T>(w.z);
-                    const T st = sqrt(fmax(T(0), T(1) - ct * ct));
+                    const T st = m_sqrt(m_fmax(T(0), T(1) - ct * ct));
                     T sn, cs;
                     sin_cos(T(6.283185307179586476925286766559) * u01<T>(w.w), &sn, &cs);
-                    const T mt = M + mn;
                     const T fg = mn / mt * g;
                     vx = (M * vx + mn * Vx) / mt + fg * (st * cs);
                     vy = (M * vy + mn * Vy) / mt + fg * (st * sn);
