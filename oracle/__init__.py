@@ -64,7 +64,7 @@ class OrcParams(C.Structure):
         ("xs_exc", C.POINTER(C.c_double)), ("xs_ion", C.POINTER(C.c_double)),
         ("n_xs", C.c_int32), ("e_exc_ev", C.c_double), ("e_iz_ev", C.c_double),
         ("seed", C.c_uint64), ("eedf_bins", C.c_int32), ("eedf_max_ev", C.c_double),
-        ("flags", C.c_int32),
+        ("flags", C.c_int32), ("power_w_m2", C.c_double), ("power_alpha", C.c_double),
     ]
 
 
@@ -127,6 +127,7 @@ def lib():
                 "orc_fluid_update": (i64, [vp, pd, pd, pd, pd, pd]),
                 "orc_particle_step_one": (C.c_int, [vp, pd, u32, pd, u64, pd, pd, pu64]),
                 "orc_swarm_run": (None, [C.POINTER(OrcSwarmParams), C.POINTER(OrcSwarmResult), pd]),
+                "orc_get_power": (None, [vp, pd, pi64]),
                 "orc_swarm_nu": (dbl, [dbl, dbl, C.c_int, dbl]),
                 "orc_swarm_nu_bound": (dbl, [dbl, dbl, C.c_int, dbl]),
                 "orc_swarm_qi": (dbl, [dbl]),
@@ -326,6 +327,14 @@ class Oracle:
         flux = np.zeros(2)
         clamps = lib().orc_fluid_update(self.h, _dp(E), _dp(gsrc), _dp(ni), _dp(gam), _dp(flux))
         return ni, gam, flux, int(clamps)
+
+    def power(self):
+        """(current RF amplitude, last period's absorbed power per m^2, finished
+        periods, steps per period) of the Eq. 2.9 control."""
+        d = np.zeros(2)
+        i = np.zeros(2, dtype=np.int64)
+        lib().orc_get_power(self.h, _dp(d), i.ctypes.data_as(C.POINTER(C.c_int64)))
+        return {"v_rf": d[0], "p_last": d[1], "periods": int(i[0]), "steps_per_period": int(i[1])}
 
     def particle_step_one(self, E, step, state4, pid):
         E = np.ascontiguousarray(E, dtype=np.float64)

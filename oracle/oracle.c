@@ -74,6 +74,8 @@ typedef struct orc_params {
     int32_t eedf_bins;
     double eedf_max_ev;
     int32_t flags;
+    double power_w_m2;      /* prescribed absorbed power P0 per m^2 (Eq. 2.9); 0: fixed amplitude */
+    double power_alpha;     /* the relaxation parameter alpha of Eq. 2.9 */
 } orc_params;
 
 typedef struct part {
@@ -103,6 +105,12 @@ typedef struct orc_sim {
     int64_t births_iz, births_see[2], losses[2], coll[4], n_clamp;
     int64_t status;
     double flux_in[2];      /* ion flux into each wall, from the last fluid update */
+    /* power control (Eq. 2.9) */
+    double u_rf;            /* current RF amplitude U^N */
+    double pw_acc;          /* sum over the period so far of V J dt */
+    double pw_last;         /* P_abs of the last finished period */
+    int64_t pw_steps;       /* steps per RF period */
+    int64_t pw_count, pw_periods;
 } orc_sim;
 
 /* ---------------------------------------------------------------- RNG ---- */
@@ -649,7 +657,32 @@ static void emit_secondaries(orc_sim *s, uint32_t n)
 
 static double drive(const orc_sim *s, double t)
 {
-    return s->p.v_dc_v + s->p.v_rf_amp_v * sin(TWO_PI * s->p.f_rf_hz * t);
+    return s->p.v_dc_v + s->u_rf * sin(TWO_PI * s->p.f_rf_hz * t);
+}
+
+/* Absorbed power and the amplitude update of Eq. 2.9.  Per step the power per
+ * m^2 delivered through the driven electrode (z = 0) is V J, with V at mid-step
+ * and J the total current density along +z there: the ion flux e Gamma_i(0),
+ * the electrons absorbed at and emitted from that electrode (+e and -e times
+ * their number x w / dt), and the displacement current eps0 (E_0^{n+1} -
+ * E_0^n)/dt.  Summed over an RF period of round(1/(f dt)) steps and divided
+ * by its duration this is P_abs^N; then U^{N+1} = U^N (1 - alpha (P_abs^N -
+ * P0)/P0) holds for the next period. */
+static void power_step(orc_sim *s, double v_old, double v_new, double e0_old, double e0_new, int64_t d_loss0,
+                       int64_t d_see0)
+{
+    const double v_mid = 0.5 * (v_old + v_new);
+    const double j = Q_E * s->gam[0] + Q_E * s->w * (double)(d_loss0 - d_see0) / s->dt +
+                     EPS0 * (e0_new - e0_old) / s->dt;
+    s->pw_acc += v_mid * j * s->dt;
+    if (++s->pw_count == s->pw_steps) {
+        s->pw_last = s->pw_acc / ((double)s->pw_steps * s->dt);
+        if (s->p.power_w_m2 > 0.0 && s->p.power_alpha > 0.0)
+            s->u_rf = s->u_rf * (1.0 - s->p.power_alpha * (s->pw_last - s->p.power_w_m2) / s->p.power_w_m2);
+        s->pw_acc = 0.0;
+        s->pw_count = 0;
+        s->pw_periods++;
+    }
 }
 
 static double node_volume(const orc_sim *s, int j)
@@ -686,6 +719,9 @@ static void step_once(orc_sim *s)
 {
     int G = s->G;
     uint32_t n = (uint32_t)s->step;
+    const double e0_old = s->E[0];
+    const double v_old = drive(s, (double)s->step * s->dt);
+    const int64_t loss0_before = s->losses[0], see0_before = s->births_see[0];
     memset(s->dep_n, 0, sizeof(double) * G);
     memset(s->dep_e, 0, sizeof(double) * G);
     memset(s->s_iz, 0, sizeof(double) * G);
@@ -739,9 +775,11 @@ static void step_once(orc_sim *s)
         s->acc_we[j] += s->dep_e[j];
     }
     s->n_samples++;
+    const double v_new = drive(s, (double)(s->step + 1) * s->dt);
     s->step++;
     /* secondaries of the next step, from the ion wall flux just computed */
     emit_secondaries(s, (uint32_t)s->step);
+    power_step(s, v_old, v_new, e0_old, s->E[0], s->losses[0] - loss0_before, s->births_see[0] - see0_before);
 }
 
 int orc_step(orc_sim *s, int64_t nsteps)
@@ -798,6 +836,9 @@ orc_sim *orc_create(const orc_params *p)
     if (s->p.eedf_bins <= 0) s->p.eedf_bins = 256;
     if (s->p.eedf_max_ev <= 0) s->p.eedf_max_ev = 64.0;
     if (s->p.see_energy_ev <= 0) s->p.see_energy_ev = 1.0;
+    s->u_rf = p->v_rf_amp_v;
+    s->pw_steps = p->f_rf_hz > 0 ? llround(1.0 / (p->f_rf_hz * p->dt_s)) : 0;
+    if (s->pw_steps < 1) s->pw_steps = INT64_MAX;  /* no RF period: no update */
 
     s->G = p->n_cells + 1;
     s->L = p->gap_m;
@@ -1121,3 +1162,14 @@ void orc_swarm_run(const orc_swarm_params *p, orc_swarm_result *res, double *v_o
     res->collisions = coll;
     res->overruns = over;
 }
+
+/* power control state: the current amplitude, the last period's absorbed
+ * power, the finished periods and the steps per period */
+void orc_get_power(const orc_sim *s, double out[2], int64_t iout[2])
+{
+    out[0] = s->u_rf;
+    out[1] = s->pw_last;
+    iout[0] = s->pw_periods;
+    iout[1] = s->pw_steps;
+}
+

@@ -95,12 +95,13 @@ def base_params(**kw) -> dict:
              n0_m3=1e16, te0_ev=2.0, weight=0.0, gamma_see=0.0, see_energy_ev=1.0,
              ion_model=ION_DD_CONST, ion_mass_amu=0.0, gas_mass_amu=0.0, mu_const=1.0e-3,
              seed=1, eedf_bins=256, eedf_max_ev=64.0, flags=0, precision=FP64,
-             capacity_factor=2.0, sort_interval=0)
+             capacity_factor=2.0, sort_interval=0, power_w_m2=0.0, power_alpha=0.0)
     p.update(kw)
     gas = p["gas"]
-    p.update(xs_tables(gas))
     kind = "he" if gas == GAS_HE else "heavy"
-    p.update(ion_tables(kind, p["pressure_pa"], p["gas_temp_k"]))
+    # the stand-in tables, unless the caller gave tables of its own
+    for k, v in {**xs_tables(gas), **ion_tables(kind, p["pressure_pa"], p["gas_temp_k"])}.items():
+        p.setdefault(k, v)
     return p
 
 
