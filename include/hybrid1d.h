@@ -100,6 +100,8 @@ typedef struct hyb_params {
     int32_t precision;          /* HYB_FP64 or HYB_FP32_SPLIT */
     double capacity_factor;     /* particle store = factor * n_particles (min 4096); 0: 2 */
     int32_t sort_interval;      /* steps between cell sorts; 0: library default */
+    double power_w_m2;          /* prescribed absorbed power P0 per m^2 of electrode (Eq. 2.9); 0: fixed amplitude */
+    double power_alpha;         /* alpha of Eq. 2.9: after each RF period U <- U (1 - alpha (P_abs - P0)/P0) */
 } hyb_params;
 
 /* Time averages since creation or the last hyb_reset_moments (Sec. III
@@ -133,6 +135,12 @@ typedef struct hyb_counters {
     int64_t clamps;             /* ion densities clamped at zero */
     int64_t pushes;             /* particle pushes done (particle-steps) */
     uint32_t status;            /* bit set of HYB_STATUS_* below */
+    double v_rf_amp_v;          /* current RF amplitude (changes under power control) */
+    double power_last_w_m2;     /* absorbed power per m^2 of the last finished RF period (Eq. 2.9):
+                                   mean over round(1/(f dt)) steps of V J, V at mid-step, J the total
+                                   current density along +z at the driven electrode (ions, electrons
+                                   absorbed and emitted there, displacement) */
+    int64_t power_periods;      /* finished RF periods */
 } hyb_counters;
 
 #define HYB_STATUS_CAPACITY 1u

@@ -132,6 +132,8 @@ int validate(const hyb_params *p)
     }
     if (!isfinite(p->v_rf_amp_v) || !isfinite(p->f_rf_hz) || !isfinite(p->v_dc_v))
         return fail(HYB_ERR_NONFINITE, "non-finite drive");
+    if (!(p->power_w_m2 >= 0) || !(p->power_alpha >= 0) || !isfinite(p->power_w_m2) || !isfinite(p->power_alpha))
+        return fail(HYB_ERR_ARG, "power target and alpha must be finite and non-negative");
     return HYB_OK;
 }
 
@@ -236,6 +238,10 @@ void derive(const hyb_params &p, InstDev &K, std::vector<double> &xs, std::vecto
     K.gamma_see = p.gamma_see;
     K.see_speed = sqrt(2.0 * kQe * (p.see_energy_ev > 0 ? p.see_energy_ev : 1.0) / kMe);
     K.v_rf = p.v_rf_amp_v;
+    K.pw_target = p.power_w_m2;
+    K.pw_alpha = p.power_alpha;
+    K.pw_steps = p.f_rf_hz > 0 ? llround(1.0 / (p.f_rf_hz * p.dt_s)) : 0;
+    if (K.pw_steps < 1) K.pw_steps = INT64_MAX;  // no RF period: no update
     K.f_rf = p.f_rf_hz;
     K.v_dc = p.v_dc_v;
     K.mu_const = p.mu_const;
@@ -969,6 +975,9 @@ int read_counters(hyb_batch *b, int slot, hyb_counters *c)
     c->pushes = (int64_t)K.ctr[C_PUSH];
     c->status = K.status;
     c->particles = live_count(K);
+    c->v_rf_amp_v = K.v_rf;
+    c->power_last_w_m2 = K.pw_last;
+    c->power_periods = K.pw_periods;
     return rc;
 }
 

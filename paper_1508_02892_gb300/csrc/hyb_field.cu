@@ -526,6 +526,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
     if (t == 0) {
         if (red.count) K->ctr[C_CLAMP] += red.count;
         K->n_samples += 1;
+        const double v_old = K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)K->step * dt));
         const double g0 = gfin[0], gN = gfin[G - 1];
         K->flux_in[0] = g0 < 0.0 ? -g0 : 0.0;
         K->flux_in[1] = gN > 0.0 ? gN : 0.0;
@@ -552,6 +553,24 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
         K->n_slots = s_base + tot;
         K->ctr[C_SEE0] += s_cnt[0];
         K->ctr[C_SEE1] += s_cnt[1];
+        // Absorbed power (Eq. 2.9): V J dt per step at the driven electrode, V at
+        // mid-step, J along +z = ion flux + electrons absorbed (+) and emitted (-)
+        // there + displacement current; at the end of an RF period P_abs and the
+        // amplitude of the next period
+        const unsigned long long l0 = K->ctr[C_LOSS0];
+        const int64_t d_loss0 = (int64_t)(l0 - K->pw_loss0), d_see0 = s_cnt[0];
+        K->pw_loss0 = l0;
+        const double v_mid = 0.5 * (v_old + fc.phi0);
+        const double jz = kQe * gfin[0] + kQe * w * (double)(d_loss0 - d_see0) / dt + kEps0 * (K->E[0] - s_E[0]) / dt;
+        K->pw_acc += v_mid * jz * dt;
+        if (++K->pw_count == K->pw_steps) {
+            K->pw_last = K->pw_acc / ((double)K->pw_steps * dt);
+            if (K->pw_target > 0.0 && K->pw_alpha > 0.0)
+                K->v_rf = K->v_rf * (1.0 - K->pw_alpha * (K->pw_last - K->pw_target) / K->pw_target);
+            K->pw_acc = 0.0;
+            K->pw_count = 0;
+            K->pw_periods += 1;
+        }
     }
     __syncthreads();
     const int ntot = s_cnt[0] + s_cnt[1];

@@ -72,6 +72,11 @@ struct InstDev {
     int64_t n_base;                   // live count = n_base + births - losses
     unsigned int status;
     int32_t init_pending;             // field kernel runs in initial-solve mode
+    // power control (Eq. 2.9); v_rf above is the current amplitude
+    double pw_target, pw_alpha;       // P0 per m^2 (0: fixed amplitude), alpha
+    double pw_acc, pw_last;           // sum of V J dt in the running period; P_abs of the last one
+    int64_t pw_steps, pw_count, pw_periods;
+    unsigned long long pw_loss0;      // electrons absorbed at z = 0 up to the last step
 };
 
 enum { C_BIRTH_IZ = 0, C_SEE0, C_SEE1, C_LOSS0, C_LOSS1, C_EL, C_EXC, C_IZ, C_NULL, C_CLAMP, C_PUSH };

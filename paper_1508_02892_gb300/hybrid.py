@@ -42,7 +42,8 @@ class Params(C.Structure):
         ("xs_ev", _pd), ("xs_el", _pd), ("xs_exc", _pd), ("xs_ion", _pd), ("n_xs", C.c_int32),
         ("e_exc_ev", C.c_double), ("e_iz_ev", C.c_double), ("seed", C.c_uint64),
         ("eedf_bins", C.c_int32), ("eedf_max_ev", C.c_double), ("precision", C.c_int32),
-        ("capacity_factor", C.c_double), ("sort_interval", C.c_int32),
+        ("capacity_factor", C.c_double), ("sort_interval", C.c_int32), ("power_w_m2", C.c_double),
+        ("power_alpha", C.c_double),
     ]
 
 
@@ -58,7 +59,8 @@ class Fields(C.Structure):
 class Counters(C.Structure):
     _fields_ = [("step", C.c_int64), ("particles", C.c_int64), ("births_ionization", C.c_int64),
                 ("births_see", C.c_int64 * 2), ("losses", C.c_int64 * 2), ("collisions", C.c_int64 * 4),
-                ("clamps", C.c_int64), ("pushes", C.c_int64), ("status", C.c_uint32)]
+                ("clamps", C.c_int64), ("pushes", C.c_int64), ("status", C.c_uint32), ("v_rf_amp_v", C.c_double),
+                ("power_last_w_m2", C.c_double), ("power_periods", C.c_int64)]
 
 
 class Info(C.Structure):
@@ -223,7 +225,8 @@ def _counters(call):
             "births_see0": c.births_see[0], "births_see1": c.births_see[1], "losses0": c.losses[0],
             "losses1": c.losses[1], "elastic": c.collisions[0], "excitation": c.collisions[1],
             "ionization": c.collisions[2], "null": c.collisions[3], "clamps": c.clamps, "pushes": c.pushes,
-            "status": c.status}
+            "status": c.status, "v_rf": c.v_rf_amp_v, "power_last": c.power_last_w_m2,
+            "power_periods": c.power_periods}
 
 
 def _particles(call, cap):

@@ -32,17 +32,17 @@ def test_library_exports_every_declared_symbol():
 
 def _struct_fields(src, name):
     body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)      # comments, also over several lines
     fields = []
-    for line in body.split("\n"):
-        line = re.sub(r"/\*.*?\*/", "", line).strip()
-        if not line:
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
             continue
-        for decl in line.rstrip(";").split(";"):
-            decl = decl.strip()
-            if not decl:
-                continue
-            names = re.findall(r"\*?\s*(\w+)\s*(?:,|$)", decl.split(None, 1)[1] if " " in decl else decl)
-            fields += [n for n in names if n not in ("const", "double", "int32_t", "int64_t", "uint64_t")]
+        decl = re.sub(r"^(const\s+)?\w+\s*", "", decl)     # the type
+        for part in decl.split(","):
+            m = re.match(r"\s*\*?\s*(\w+)", part)
+            if m:
+                fields.append(m.group(1))
     return fields
 
 
@@ -51,7 +51,8 @@ def test_binding_structs_match_header_field_order():
     with open(os.path.join(ROOT, "include", "hybrid1d.h")) as f:
         src = f.read()
     for cname, py in (("hyb_params", hybrid.Params), ("hyb_tuning", hybrid.Tuning), ("hyb_profile", hybrid.Profile),
-                      ("hyb_swarm_params", hybrid.SwarmParams), ("hyb_swarm_result", hybrid.SwarmResult)):
+                      ("hyb_swarm_params", hybrid.SwarmParams), ("hyb_swarm_result", hybrid.SwarmResult),
+                      ("hyb_counters", hybrid.Counters)):
         assert _struct_fields(src, cname) == [f for f, _ in py._fields_], cname
 
 

@@ -97,6 +97,44 @@ def test_fp64_dd_table_ragged_sizes():
     _check_all(g, o, p)
 
 
+def test_fp64_power_control_over_three_periods():
+    """Eq. 2.9 with an RF period of 30 steps.  Through the first period (the
+    amplitude changes only at its end) states, counters and grids agree with the
+    oracle to the usual FP64 tolerances.  The absorbed power contains the
+    displacement current eps0 (E_0^{n+1} - E_0^n)/dt, a difference about 1e-3 of
+    E_0 itself, so the 1e-14 rounding differences of the two Poisson solvers
+    (prefix scans here, Thomas in the oracle) reach about 1e-11 in P_abs and, fed
+    back through the amplitude, in the particles: after three periods the
+    amplitude and the power are compared to 1e-8 and the particles to 1e-9."""
+    p = W.config1(precision=W.FP64, n_particles=20000, te0_ev=8.0, ion_model=W.ION_FULL, gamma_see=0.2,
+                  weight=2e6, v_rf_amp_v=200.0, f_rf_hz=1.0 / (30 * 2e-13), power_w_m2=5e4, power_alpha=0.2,
+                  seed=31)
+    g, o = _run_pair(p, 30)
+    _check_all(g, o, p)
+    pw, c = o.power(), g.counters()
+    assert c["power_periods"] == pw["periods"] == 1
+    scale = 8.8541878128e-12 * 2 * np.pi * p["f_rf_hz"] * 200.0 ** 2 / p["gap_m"]
+    assert abs(c["power_last"] - pw["p_last"]) <= 1e-9 * scale
+    g.advance(60)
+    o.step(60)
+    pw, c = o.power(), g.counters()
+    assert c["power_periods"] == pw["periods"] == 3
+    assert c["v_rf"] == pytest.approx(pw["v_rf"], rel=1e-8)
+    assert c["v_rf"] != 200.0
+    assert abs(c["power_last"] - pw["p_last"]) <= 1e-8 * scale
+    assert_particles_close(g.particles(), o.particles(), p["gap_m"], 1e-9)
+
+
+def test_power_control_vacuum_closed_form():
+    p = W.config1(precision=W.FP64, n_particles=0, n0_m3=0.0, weight=1.0, f_rf_hz=1.0 / (200 * 2e-13),
+                  v_rf_amp_v=150.0, power_w_m2=1000.0, power_alpha=0.1)
+    g = _gpu(p)
+    g.advance(600)
+    c = g.counters()
+    assert c["power_periods"] == 3
+    assert c["v_rf"] == pytest.approx(150.0 * 1.1 ** 3, rel=1e-9)
+
+
 def test_empty_discharge():
     p = W.config1(precision=W.FP64, n_particles=0, n0_m3=1e16, weight=1e9)
     g, o = _run_pair(p, 20)
