@@ -31,7 +31,7 @@ OUT_NONE, OUT_ELASTIC, OUT_EXC, OUT_ION, OUT_NULL, OUT_LOST0, OUT_LOST1 = range(
 FLAG_THERMAL_GAS = 2
 
 COUNTER_NAMES = ("step", "particles", "births_iz", "births_see0", "births_see1", "losses0",
-                 "losses1", "elastic", "excitation", "ionization", "null", "clamps", "status")
+                 "losses1", "elastic", "excitation", "ionization", "null", "clamps", "status", "recombinations")
 
 
 def build(force: bool = False) -> str:
@@ -65,6 +65,7 @@ class OrcParams(C.Structure):
         ("n_xs", C.c_int32), ("e_exc_ev", C.c_double), ("e_iz_ev", C.c_double),
         ("seed", C.c_uint64), ("eedf_bins", C.c_int32), ("eedf_max_ev", C.c_double),
         ("flags", C.c_int32), ("power_w_m2", C.c_double), ("power_alpha", C.c_double),
+        ("xs_rec", C.POINTER(C.c_double)),
     ]
 
 
@@ -205,6 +206,11 @@ class Oracle:
                 arr = np.ascontiguousarray(params.get(name, np.zeros(1)), dtype=np.float64)
                 self._keep[name] = arr
                 setattr(p, name, _dp(arr))
+            elif name == "xs_rec":
+                if params.get("xs_rec") is not None:
+                    arr = np.ascontiguousarray(params["xs_rec"], dtype=np.float64)
+                    self._keep[name] = arr
+                    setattr(p, name, _dp(arr))
             elif name in ("n_tab", "n_xs"):
                 continue
             elif name in params:
@@ -282,7 +288,7 @@ class Oracle:
         return out
 
     def counters(self):
-        out = (C.c_int64 * 13)()
+        out = (C.c_int64 * len(COUNTER_NAMES))()
         lib().orc_get_counters(self.h, out)
         return dict(zip(COUNTER_NAMES, (int(x) for x in out)))
 

@@ -76,6 +76,7 @@ typedef struct orc_params {
     int32_t flags;
     double power_w_m2;      /* prescribed absorbed power P0 per m^2 (Eq. 2.9); 0: fixed amplitude */
     double power_alpha;     /* the relaxation parameter alpha of Eq. 2.9 */
+    const double *xs_rec;   /* electron-ion recombination cross section at xs_ev (NULL: none) */
 } orc_params;
 
 typedef struct part {
@@ -87,7 +88,7 @@ typedef struct orc_sim {
     orc_params p;
     /* owned copies of the tables */
     double *tab_eon, *tab_mu, *tab_nu, *tab_u;
-    double *xs_ev, *xs_el, *xs_exc, *xs_ion;
+    double *xs_ev, *xs_el, *xs_exc, *xs_ion, *xs_rec;
     /* derived */
     int G;                  /* nodes */
     double L, dz, dt, ngas, w, m_gas, m_ion, e_lo, e_hi, inv_dlog, nu_max, p_max;
@@ -102,7 +103,8 @@ typedef struct orc_sim {
     int64_t n_samples;
     /* bookkeeping */
     int64_t step;
-    int64_t births_iz, births_see[2], losses[2], coll[4], n_clamp;
+    int64_t births_iz, births_see[2], losses[2], coll[4], n_clamp, recomb;
+    double rec_svmax;       /* bound of sigma_rec(E) v(E) over the table */
     int64_t status;
     double flux_in[2];      /* ion flux into each wall, from the last fluid update */
     /* power control (Eq. 2.9) */
@@ -562,6 +564,45 @@ static int mcc_one(const orc_sim *s, uint32_t n, part *q, part *child)
     return OUT_NULL;
 }
 
+/* Recombination test of one electron after its charge assignment (Sec. II.D):
+ * candidate if R3 < P_rec = 1 - exp(-nu_rec,max dt), real if R4 nu_rec,max <
+ * n_i(z) sigma_rec(E) v with n_i interpolated (CIC) at the electron.  A
+ * recombined electron is removed and its ion leaves the ion density through
+ * the source term of Eq. 2.4 (a CIC sink in s_iz).  Draws: call 2, (R3, R4). */
+static int recombine(orc_sim *s, uint32_t n, const part *q, double rec_numax, double rec_pmax)
+{
+    double u[4];
+    draws(s, q->id, n, 2, u);
+    if (!(u[0] < rec_pmax)) return 0;
+    int c;
+    double o;
+    locate(s, q->z, &c, &o);
+    double nil = (1.0 - o) * s->ni[c] + o * s->ni[c + 1];
+    double en = energy_ev(q);
+    double speed = sqrt(q->vx * q->vx + q->vy * q->vy + q->vz * q->vz);
+    int i;
+    double f;
+    if (en <= s->e_lo) {
+        i = 0;
+        f = 0.0;
+    } else if (en >= s->e_hi) {
+        i = s->p.n_xs - 2;
+        f = 1.0;
+    } else {
+        double x = log(en / s->e_lo) * s->inv_dlog;
+        i = (int)floor(x);
+        if (i < 0) i = 0;
+        if (i > s->p.n_xs - 2) i = s->p.n_xs - 2;
+        f = (en - s->xs_ev[i]) / (s->xs_ev[i + 1] - s->xs_ev[i]);
+    }
+    double sig = s->xs_rec[i] + f * (s->xs_rec[i + 1] - s->xs_rec[i]);
+    if (!(u[1] * rec_numax < nil * sig * speed)) return 0;
+    s->recomb++;
+    s->s_iz[c] -= 1.0 - o;
+    s->s_iz[c + 1] -= o;
+    return 1;
+}
+
 /* One particle through the whole per-particle part of step n, given E^n:
  * push, wall test, MCC.  Exposed for sampled checks of large runs. */
 int orc_particle_step_one(const orc_sim *s, const double *E, uint32_t n, const double in[4], uint64_t id,
@@ -726,6 +767,16 @@ static void step_once(orc_sim *s)
     memset(s->dep_e, 0, sizeof(double) * G);
     memset(s->s_iz, 0, sizeof(double) * G);
     int64_t n0 = s->np;
+    /* electron-ion recombination (Sec. II.D): a null-collision procedure of its
+     * own on the non-uniform ion density, nu_rec,max = max_z n_i * max sigma v */
+    double rec_numax = 0.0, rec_pmax = 0.0;
+    if (s->xs_rec) {
+        double nimax = 0.0;
+        for (int j = 0; j < G; ++j)
+            if (s->ni[j] > nimax) nimax = s->ni[j];
+        rec_numax = nimax * s->rec_svmax;
+        rec_pmax = -expm1(-rec_numax * s->dt);
+    }
     part *kids = NULL;
     int64_t nk = 0, ck = 0;
     int64_t keep = 0;
@@ -737,6 +788,7 @@ static void step_once(orc_sim *s)
             continue;
         }
         deposit_one(s, &q, 1);
+        if (s->xs_rec && recombine(s, n, &q, rec_numax, rec_pmax)) continue;
         part ch;
         int oc = mcc_one(s, n, &q, &ch);
         if (oc == OUT_ELASTIC) s->coll[0]++;
@@ -828,10 +880,11 @@ orc_sim *orc_create(const orc_params *p)
     s->xs_el = dup(p->xs_el, p->n_xs);
     s->xs_exc = dup(p->xs_exc, p->n_xs);
     s->xs_ion = dup(p->xs_ion, p->n_xs);
+    s->xs_rec = p->xs_rec ? dup(p->xs_rec, p->n_xs) : NULL;
     s->tab_eon = dup(p->tab_eon_td, p->n_tab);
     s->tab_mu = dup(p->tab_mu, p->n_tab);
     s->tab_nu = dup(p->tab_nu, p->n_tab);
-    s->p.xs_ev = s->p.xs_el = s->p.xs_exc = s->p.xs_ion = NULL;
+    s->p.xs_ev = s->p.xs_el = s->p.xs_exc = s->p.xs_ion = s->p.xs_rec = NULL;
     s->p.tab_eon_td = s->p.tab_mu = s->p.tab_nu = NULL;
     if (s->p.eedf_bins <= 0) s->p.eedf_bins = 256;
     if (s->p.eedf_max_ev <= 0) s->p.eedf_max_ev = 64.0;
@@ -869,6 +922,17 @@ orc_sim *orc_create(const orc_params *p)
         if (nu > s->nu_max) s->nu_max = nu;
     }
     s->p_max = 1.0 - exp(-s->nu_max * s->dt);
+    /* recombination: sigma_rec v is bounded on each table segment by the larger
+     * endpoint cross section times the speed at the upper end (the lookup is
+     * linear in energy between nodes) */
+    s->rec_svmax = 0.0;
+    if (s->xs_rec) {
+        for (int i = 0; i + 1 < p->n_xs; ++i) {
+            double sg = fmax(s->xs_rec[i], s->xs_rec[i + 1]);
+            double v = sqrt(2.0 * Q_E * s->xs_ev[i + 1] / M_E);
+            if (sg * v > s->rec_svmax) s->rec_svmax = sg * v;
+        }
+    }
 
     int G = s->G;
     s->ni = (double *)calloc(G, sizeof(double));
@@ -896,7 +960,7 @@ orc_sim *orc_create(const orc_params *p)
 void orc_destroy(orc_sim *s)
 {
     if (!s) return;
-    double *bufs[] = {s->tab_eon, s->tab_mu, s->tab_nu, s->tab_u, s->xs_ev, s->xs_el, s->xs_exc, s->xs_ion,
+    double *bufs[] = {s->tab_eon, s->tab_mu, s->tab_nu, s->tab_u, s->xs_ev, s->xs_el, s->xs_exc, s->xs_ion, s->xs_rec,
                       s->ni, s->gam, s->phi, s->E, s->ne, s->dep_n, s->dep_e, s->s_iz, s->gsrc,
                       s->acc_ne, s->acc_ni, s->acc_gi, s->acc_wn, s->acc_we, s->eedf};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) free(bufs[i]);
@@ -979,7 +1043,7 @@ void orc_get_eedf_counts(const orc_sim *s, double *out)
 
 /* counters: step, particles, births_iz, births_see0, births_see1, losses0,
  * losses1, elastic, excitation, ionization, null, clamps, status */
-void orc_get_counters(const orc_sim *s, int64_t out[13])
+void orc_get_counters(const orc_sim *s, int64_t out[14])
 {
     out[0] = s->step;
     out[1] = s->np;
@@ -994,6 +1058,7 @@ void orc_get_counters(const orc_sim *s, int64_t out[13])
     out[10] = s->coll[3];
     out[11] = s->n_clamp;
     out[12] = s->status;
+    out[13] = s->recomb;
 }
 
 void orc_get_flux_in(const orc_sim *s, double out[2])

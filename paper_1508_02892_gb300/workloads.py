@@ -200,3 +200,13 @@ def swarm_fields(n: int = 64, e_max: float = 5e6) -> np.ndarray:
     """Field values for a mobility table: n points evenly spaced in (0, e_max]."""
     return np.linspace(e_max / n, e_max, n)
 
+
+def recombination_table(k_m3_s: float, gas: int = GAS_HE) -> np.ndarray:
+    """Stand-in electron-ion recombination cross section on the electron
+    cross-section grid: sigma(E) = k / v(E), i.e. a rate coefficient sigma v = k
+    (m^3/s) independent of energy at the table nodes.  The paper names the
+    process (Sec. II.D) but gives no data for it."""
+    ev = xs_tables(gas)["xs_ev"]
+    v = np.sqrt(2.0 * 1.602176634e-19 * ev / 9.1093837015e-31)
+    return k_m3_s / v
+
