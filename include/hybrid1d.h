@@ -102,6 +102,10 @@ typedef struct hyb_params {
     int32_t sort_interval;      /* steps between cell sorts; 0: library default */
     double power_w_m2;          /* prescribed absorbed power P0 per m^2 of electrode (Eq. 2.9); 0: fixed amplitude */
     double power_alpha;         /* alpha of Eq. 2.9: after each RF period U <- U (1 - alpha (P_abs - P0)/P0) */
+    const double *xs_rec;       /* host, NULL or the electron-ion recombination cross section (m^2) at
+                                   xs_ev: a null-collision process of its own on the ion density
+                                   (Sec. II.D); a recombined electron is removed and its ion leaves
+                                   n_i through the source term of Eq. 2.4 */
 } hyb_params;
 
 /* Time averages since creation or the last hyb_reset_moments (Sec. III
@@ -141,6 +145,7 @@ typedef struct hyb_counters {
                                    current density along +z at the driven electrode (ions, electrons
                                    absorbed and emitted there, displacement) */
     int64_t power_periods;      /* finished RF periods */
+    int64_t recombinations;     /* electrons removed by electron-ion recombination */
 } hyb_counters;
 
 #define HYB_STATUS_CAPACITY 1u

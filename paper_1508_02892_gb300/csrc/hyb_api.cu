@@ -134,6 +134,11 @@ int validate(const hyb_params *p)
         return fail(HYB_ERR_NONFINITE, "non-finite drive");
     if (!(p->power_w_m2 >= 0) || !(p->power_alpha >= 0) || !isfinite(p->power_w_m2) || !isfinite(p->power_alpha))
         return fail(HYB_ERR_ARG, "power target and alpha must be finite and non-negative");
+    if (p->xs_rec) {
+        if (!finite_all(p->xs_rec, p->n_xs)) return fail(HYB_ERR_NONFINITE, "non-finite recombination cross section");
+        for (int i = 0; i < p->n_xs; ++i)
+            if (p->xs_rec[i] < 0) return fail(HYB_ERR_ARG, "negative recombination cross section");
+    }
     return HYB_OK;
 }
 
@@ -173,6 +178,9 @@ Layout layout_of(const hyb_params &p)
     add(32 * (size_t)p.n_xs);                           // xs
     add(16 * (size_t)p.n_xs);                           // xsf
     add(32 * (size_t)(p.n_tab > 0 ? p.n_tab : 1));      // tab
+    add(8 * (size_t)p.n_xs);                            // xs_rec
+    add(4 * (size_t)p.n_xs);                            // xs_recf
+    add(4 * (size_t)G);                                 // nif
     L.total = o;
     return L;
 }
@@ -284,6 +292,16 @@ void derive(const hyb_params &p, InstDev &K, std::vector<double> &xs, std::vecto
         xsf[i] = make_float4((float)p.xs_ev[i], (float)(scale * p.xs_el[i]), (float)(scale * p.xs_exc[i]),
                              (float)(scale * p.xs_ion[i]));
     }
+    // recombination (Sec. II.D): sigma_rec v bounded on each table segment by the
+    // larger endpoint cross section times the speed at the upper end
+    K.rec_on = p.xs_rec != nullptr;
+    K.rec_svmax = 0.0;
+    if (K.rec_on)
+        for (int i = 0; i + 1 < p.n_xs; ++i) {
+            const double sg = fmax(p.xs_rec[i], p.xs_rec[i + 1]);
+            const double v = sqrt(2.0 * kQe * p.xs_ev[i + 1] / kMe);
+            if (sg * v > K.rec_svmax) K.rec_svmax = sg * v;
+        }
     const int nt = K.n_tab > 0 ? K.n_tab : 1;
     tab.assign(4 * (size_t)nt, 0.0);
     for (int k = 0; k < K.n_tab; ++k) {
@@ -323,6 +341,9 @@ void bind_pointers(const hyb_params &p, const Layout &L, char *base, InstDev &K)
     K.xs = (const double *)(base + L.off[k++]);
     K.xsf = (const float4 *)(base + L.off[k++]);
     K.tab = (const double *)(base + L.off[k++]);
+    K.xs_rec = (const double *)(base + L.off[k++]);
+    K.xs_recf = (const float *)(base + L.off[k++]);
+    K.nif = (float *)(base + L.off[k++]);
 }
 
 }  // namespace
@@ -348,6 +369,7 @@ struct hyb_batch {
     cudaEvent_t ev_fork = nullptr, ev_join[kMaxLanes] = {};
     int blocks_per_sm = 0;                 // electron grid = SMs x this (0: occupancy limit)
     int field_threads = 256;               // threads of an instance's field block
+    bool any_rec = false;                  // some admitted discharge has recombination
     int occ_per_sm = 0;
     std::vector<Slot> slots;
     int64_t hbm_cap = 0, hbm_used = 0;
@@ -377,7 +399,7 @@ namespace {
 int64_t live_count(const InstDev &K)
 {
     return K.n_base + (int64_t)(K.ctr[C_BIRTH_IZ] + K.ctr[C_SEE0] + K.ctr[C_SEE1]) -
-           (int64_t)(K.ctr[C_LOSS0] + K.ctr[C_LOSS1]);
+           (int64_t)(K.ctr[C_LOSS0] + K.ctr[C_LOSS1] + K.ctr[C_REC]);
 }
 
 int fetch_inst(hyb_batch *b, int slot)
@@ -482,7 +504,7 @@ int launch_step(hyb_batch *b, int k, int lane, cudaStream_t s)
     int rc;
     const int n = lane_count(b, lane);
     if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k)))) return rc;
-    CK(launch_electron_step(lane_inst(b, lane), n, lane_prefix(b, lane), b->precision, b->cfg, s));
+    CK(launch_electron_step(lane_inst(b, lane), n, lane_prefix(b, lane), b->precision, b->cfg, s, b->any_rec));
     if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k + 1)))) return rc;
     CK(launch_field(lane_inst(b, lane), n, lane_prefix(b, lane), lane_ticket(b, lane), b->precision == HYB_FP32_SPLIT,
                     b->max_nodes, b->field_threads, s));
@@ -693,6 +715,15 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     CK(cudaMemcpyAsync((void *)S.h.xs, xs.data(), 8 * xs.size(), cudaMemcpyHostToDevice, b->stream));
     CK(cudaMemcpyAsync((void *)S.h.xsf, xsf.data(), 16 * xsf.size(), cudaMemcpyHostToDevice, b->stream));
     CK(cudaMemcpyAsync((void *)S.h.tab, tab.data(), 8 * tab.size(), cudaMemcpyHostToDevice, b->stream));
+    std::vector<double> xr(p->n_xs, 0.0);
+    std::vector<float> xrf(p->n_xs, 0.0f);
+    if (p->xs_rec)
+        for (int i = 0; i < p->n_xs; ++i) {
+            xr[i] = p->xs_rec[i];
+            xrf[i] = S.h.rec_svmax > 0 ? (float)(p->xs_rec[i] / S.h.rec_svmax) : 0.0f;
+        }
+    CK(cudaMemcpyAsync((void *)S.h.xs_rec, xr.data(), 8 * xr.size(), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync((void *)S.h.xs_recf, xrf.data(), 4 * xrf.size(), cudaMemcpyHostToDevice, b->stream));
     S.h.active = 0;
     S.h.cur = 0;
     S.h.step = 0;
@@ -715,7 +746,12 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     S.reported = false;
     S.p = *p;
     S.p.tab_eon_td = S.p.tab_mu = S.p.tab_nu = nullptr;
-    S.p.xs_ev = S.p.xs_el = S.p.xs_exc = S.p.xs_ion = nullptr;
+    S.p.xs_ev = S.p.xs_el = S.p.xs_exc = S.p.xs_ion = S.p.xs_rec = nullptr;
+    if (S.h.rec_on && !b->any_rec) {  // the electron step switches to its recombination variant
+        b->any_rec = true;
+        rc = drop_graph(b);
+        if (rc) return rc;
+    }
     S.mem = mem;
     S.bytes = (int64_t)L.total;
     S.target = S.h.target_step;
@@ -978,6 +1014,7 @@ int read_counters(hyb_batch *b, int slot, hyb_counters *c)
     c->v_rf_amp_v = K.v_rf;
     c->power_last_w_m2 = K.pw_last;
     c->power_periods = K.pw_periods;
+    c->recombinations = (int64_t)K.ctr[C_REC];
     return rc;
 }
 

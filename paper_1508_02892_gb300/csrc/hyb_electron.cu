@@ -66,12 +66,12 @@ __device__ __forceinline__ void deposit_pair(T *arr, bool on, int c, T w0, T w1,
 // Per-thread event counts; the split kernel packs two 16-bit counts per word
 // (a thread handles far fewer than 65536 particles of one segment).
 struct SegCounters {
-    unsigned el = 0, exc = 0, iz = 0, nul = 0, loss0 = 0, loss1 = 0, overflow = 0, push = 0;
+    unsigned el = 0, exc = 0, iz = 0, nul = 0, loss0 = 0, loss1 = 0, overflow = 0, push = 0, rec = 0;
     int cmin = INT32_MAX, cmax = -1;
 };
 
 struct PackedCounters {
-    unsigned el_exc = 0, iz_nul = 0, loss = 0, push_ovf = 0;
+    unsigned el_exc = 0, iz_nul = 0, loss = 0, push_ovf = 0, rec = 0;
     int cmin = INT32_MAX, cmax = -1;
     __device__ void unpack(SegCounters &s) const
     {
@@ -83,6 +83,7 @@ struct PackedCounters {
         s.loss1 = loss >> 16;
         s.push = push_ovf & 0xFFFFu;
         s.overflow = push_ovf >> 16;
+        s.rec = rec;
         s.cmin = cmin;
         s.cmax = cmax;
     }
@@ -223,7 +224,7 @@ __device__ __forceinline__ void row_deposit(WarpRow &row, int &base, InstDev *K,
     atomicAdd(&row.e1[j], __float2uint_rn(o * en * kFixE));
 }
 
-template <int MODE>
+template <int MODE, bool REC>
 __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *smem, PackedCounters &cnt)
 {
     const int nc = K->n_cells;
@@ -353,12 +354,14 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             // kVec particles' draws are formed together (independent chains).
             uint4 rk[kVec];
             draw_n<kVec>(pre, ids, sl, 0u, rk);
+            uint4 rq[kVec];
+            if (REC) draw_n<kVec>(pre, ids, sl, 2u, rq);
 #pragma unroll
             for (int k = 0; k < kVec; ++k) {
                 // computed for every lane without branches, so that the kVec
                 // chains interleave; only candidates keep their outcome
                 const float en = ens[k];
-                const bool cand = cc[k] >= 0 && cc[k] < nc && u01f(rk[k].x) < pmax;
+                bool cand = cc[k] >= 0 && cc[k] < nc && u01f(rk[k].x) < pmax;
                 const float speed = sqrtf(vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
                 // table segment: below the table the first node's values,
                 // above it the last node's
@@ -371,6 +374,23 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 const float s_el = above ? hi.y : lo.y + f * (hi.y - lo.y);
                 const float s_ex = en < e_exc ? 0.f : (above ? hi.z : lo.z + f * (hi.z - lo.z));
                 const float s_iz = en < e_iz ? 0.f : (above ? hi.w : lo.w + f * (hi.w - lo.w));
+                if (REC && cc[k] >= 0 && cc[k] < nc && u01f(rq[k].x) < K->f_rec_pmax) {
+                    // electron-ion recombination (Sec. II.D), in units of nu_rec,max:
+                    // R4 < (n_i / max n_i)(sigma_rec / max sigma_rec v) v
+                    const int cr = cc[k];
+                    const float rl = __ldg(&K->xs_recf[kk]), rh = __ldg(&K->xs_recf[kk + 1]);
+                    const float sr = above ? rh : rl + f * (rh - rl);
+                    const float nr = (1.f - oo[k]) * __ldg(&K->nif[cr]) + oo[k] * __ldg(&K->nif[cr + 1]);
+                    if (u01f(rq[k].y) < nr * sr * speed) {
+                        cnt.rec += 1u;
+                        cand = false;
+                        cc[k] = kDeadCell;
+                        if (HYB_CHECK(cr >= 0 && cr + 1 < G, 4, cr, G)) {
+                            atomicAdd(&K->s_iz[cr], -(1.0 - (double)oo[k]));
+                            atomicAdd(&K->s_iz[cr + 1], -(double)oo[k]);
+                        }
+                    }
+                }
                 const float t0 = s_el * speed, t1 = t0 + s_ex * speed, t2 = t1 + s_iz * speed;
                 const float r2 = u01f(rk[k].y);
                 const bool hit = cand && r2 < t2;
@@ -512,6 +532,28 @@ __device__ __forceinline__ void locate_d(double z, double dz, int nc, int &c, do
     }
 }
 
+// sigma_rec(E) with the same log-index, linear-in-energy lookup
+__device__ __forceinline__ double xs_rec_d(const double *__restrict__ xr, const double *__restrict__ xs, int n,
+                                           double e_lo, double e_hi, double inv_dlog, double en)
+{
+    int i;
+    double f;
+    if (en <= e_lo) {
+        i = 0;
+        f = 0.0;
+    } else if (en >= e_hi) {
+        i = n - 2;
+        f = 1.0;
+    } else {
+        const double x = log(en / e_lo) * inv_dlog;
+        i = (int)floor(x);
+        if (i < 0) i = 0;
+        if (i > n - 2) i = n - 2;
+        f = (en - xs[4 * i]) / (xs[4 * (i + 1)] - xs[4 * i]);
+    }
+    return xr[i] + f * (xr[i + 1] - xr[i]);
+}
+
 __device__ __forceinline__ void xs_eval_d(const double *__restrict__ xs, int n, double e_lo, double e_hi,
                                           double inv_dlog, double e_exc, double e_iz, double en, double sig[3])
 {
@@ -546,7 +588,7 @@ __device__ __forceinline__ void iso_dir_d(double u_cos, double u_phi, double d[3
     d[2] = ct;
 }
 
-template <int MODE>
+template <int MODE, bool REC>
 __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *smem, SegCounters &cnt)
 {
     const int nc = K->n_cells;
@@ -617,6 +659,24 @@ __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *sm
             cnt.cmax = max(cnt.cmax, c);
         }
 
+        if (REC && MODE == 0 && alive && K->rec_on) {
+            // electron-ion recombination (Sec. II.D): candidate if R3 < P_rec,
+            // real if R4 nu_rec,max < n_i(z) sigma_rec(E) v; the electron is
+            // removed and its ion leaves through a CIC sink in the ion source
+            const uint4 rq = draw(id, step, sl, sh, 2);
+            if (u01d(rq.x) < K->rec_pmax) {
+                const double nil = (1.0 - o) * K->ni[c] + o * K->ni[c + 1];
+                const double speed = sqrt(vx * vx + vy * vy + vz * vz);
+                const double sig = xs_rec_d(K->xs_rec, xs, nxs, e_lo, e_hi, inv_dlog, en);
+                if (u01d(rq.y) * K->rec_numax < nil * sig * speed) {
+                    ++cnt.rec;
+                    alive = false;
+                    P.z[i] = -1.0;
+                    atomicAdd(&sd_iz[c], -(1.0 - o));
+                    atomicAdd(&sd_iz[c + 1], -o);
+                }
+            }
+        }
         bool has_child = false;
         double cvx = 0.0, cvy = 0.0, cvz = 0.0;
         uint64_t cid = 0;
@@ -691,16 +751,16 @@ __device__ __forceinline__ double sum_value(double q) { return q; }
 template <int MODE>
 __device__ void flush_segment_split(InstDev *K, unsigned char *smem, const SegCounters &cnt)
 {
-    __shared__ unsigned s_ctr2[8];
-    if (threadIdx.x < 8) s_ctr2[threadIdx.x] = 0u;
+    __shared__ unsigned s_ctr2[9];
+    if (threadIdx.x < 9) s_ctr2[threadIdx.x] = 0u;
     __syncthreads();
-    const unsigned v[8] = {cnt.el, cnt.exc, cnt.iz, cnt.nul, cnt.loss0, cnt.loss1, cnt.overflow, cnt.push};
-    unsigned tot[8];
+    const unsigned v[9] = {cnt.el, cnt.exc, cnt.iz, cnt.nul, cnt.loss0, cnt.loss1, cnt.overflow, cnt.push, cnt.rec};
+    unsigned tot[9];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) tot[k] = __reduce_add_sync(kFull, v[k]);
+    for (int k = 0; k < 9; ++k) tot[k] = __reduce_add_sync(kFull, v[k]);
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 9; ++k)
             if (tot[k]) atomicAdd(&s_ctr2[k], tot[k]);
     }
     __syncthreads();
@@ -717,6 +777,7 @@ __device__ void flush_segment_split(InstDev *K, unsigned char *smem, const SegCo
             if (s_ctr2[2]) atomicAdd(&K->ctr[C_BIRTH_IZ], (unsigned long long)s_ctr2[2]);
             if (s_ctr2[6]) atomicOr(&K->status, (unsigned)HYB_STATUS_CAPACITY);
             if (s_ctr2[7]) atomicAdd(&K->ctr[C_PUSH], (unsigned long long)s_ctr2[7]);
+            if (s_ctr2[8]) atomicAdd(&K->ctr[C_REC], (unsigned long long)s_ctr2[8]);
         }
     }
     __syncthreads();
@@ -725,23 +786,23 @@ __device__ void flush_segment_split(InstDev *K, unsigned char *smem, const SegCo
 template <typename S, int MODE>
 __device__ void flush_segment(InstDev *K, unsigned char *smem, const SegCounters &cnt)
 {
-    __shared__ unsigned s_ctr[8];
+    __shared__ unsigned s_ctr[9];
     __shared__ int s_cmin, s_cmax;
-    if (threadIdx.x < 8) s_ctr[threadIdx.x] = 0u;
+    if (threadIdx.x < 9) s_ctr[threadIdx.x] = 0u;
     if (threadIdx.x == 0) {
         s_cmin = INT32_MAX;
         s_cmax = -1;
     }
     __syncthreads();
-    const unsigned v[8] = {cnt.el, cnt.exc, cnt.iz, cnt.nul, cnt.loss0, cnt.loss1, cnt.overflow, cnt.push};
+    const unsigned v[9] = {cnt.el, cnt.exc, cnt.iz, cnt.nul, cnt.loss0, cnt.loss1, cnt.overflow, cnt.push, cnt.rec};
     const int mn = __reduce_min_sync(kFull, cnt.cmin);
     const int mx = __reduce_max_sync(kFull, cnt.cmax);
-    unsigned tot[8];
+    unsigned tot[9];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) tot[k] = __reduce_add_sync(kFull, v[k]);
+    for (int k = 0; k < 9; ++k) tot[k] = __reduce_add_sync(kFull, v[k]);
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 9; ++k)
             if (tot[k]) atomicAdd(&s_ctr[k], tot[k]);
         atomicMin(&s_cmin, mn);
         atomicMax(&s_cmax, mx);
@@ -776,6 +837,7 @@ __device__ void flush_segment(InstDev *K, unsigned char *smem, const SegCounters
             if (s_ctr[2]) atomicAdd(&K->ctr[C_BIRTH_IZ], (unsigned long long)s_ctr[2]);
             if (s_ctr[6]) atomicOr(&K->status, (unsigned)HYB_STATUS_CAPACITY);
             if (s_ctr[7]) atomicAdd(&K->ctr[C_PUSH], (unsigned long long)s_ctr[7]);
+            if (s_ctr[8]) atomicAdd(&K->ctr[C_REC], (unsigned long long)s_ctr[8]);
         }
     }
     __syncthreads();
@@ -815,7 +877,7 @@ __device__ __forceinline__ void for_block_runs(InstDev *__restrict__ insts, int 
     }
 }
 
-template <int PREC, int MODE>
+template <int PREC, int MODE, bool REC = false>
 __global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 3 : 2) k_electron(InstDev *__restrict__ insts,
                                                                                        int n_max,
                                                                                        const int64_t *__restrict__ prefix)
@@ -825,11 +887,11 @@ __global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 3 : 2) k_elec
         SegCounters cnt;
         if (PREC == HYB_FP32_SPLIT) {
             PackedCounters pc;
-            segment_split<MODE>(K, a, b, smem, pc);
+            segment_split<MODE, REC>(K, a, b, smem, pc);
             pc.unpack(cnt);
             flush_segment_split<MODE>(K, smem, cnt);
         } else {
-            segment_fp64<MODE>(K, a, b, smem, cnt);
+            segment_fp64<MODE, REC>(K, a, b, smem, cnt);
             flush_segment<double, MODE>(K, smem, cnt);
         }
     });
@@ -1016,10 +1078,10 @@ __global__ void k_set_active(InstDev *K, int active, int64_t target_step)
     K->target_step = target_step;
 }
 
-template <int PREC, int MODE>
+template <int PREC, int MODE, bool REC = false>
 cudaError_t launch_k(InstDev *inst, int n_max, const int64_t *prefix, LaunchCfg cfg, cudaStream_t s)
 {
-    k_electron<PREC, MODE><<<cfg.grid, cfg.block, cfg.smem, s>>>(inst, n_max, prefix);
+    k_electron<PREC, MODE, REC><<<cfg.grid, cfg.block, cfg.smem, s>>>(inst, n_max, prefix);
     return cudaGetLastError();
 }
 
@@ -1039,6 +1101,8 @@ void configure_kernels()
     cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_electron<HYB_FP64, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_electron<HYB_FP64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_electron<HYB_FP64, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     configure_field_kernel();
 }
 
@@ -1061,8 +1125,12 @@ size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins)
 }
 
 cudaError_t launch_electron_step(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
-                                 cudaStream_t s)
+                                 cudaStream_t s, bool rec)
 {
+    // the variant with the recombination test when some discharge needs it
+    if (rec)
+        return precision == HYB_FP32_SPLIT ? launch_k<HYB_FP32_SPLIT, 0, true>(inst, n_max, prefix, cfg, s)
+                                           : launch_k<HYB_FP64, 0, true>(inst, n_max, prefix, cfg, s);
     return precision == HYB_FP32_SPLIT ? launch_k<HYB_FP32_SPLIT, 0>(inst, n_max, prefix, cfg, s)
                                        : launch_k<HYB_FP64, 0>(inst, n_max, prefix, cfg, s);
 }

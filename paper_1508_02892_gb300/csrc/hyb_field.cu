@@ -436,6 +436,21 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
         __syncthreads();
     }
 
+    if (K->rec_on) {
+        // bound of the next electron step's recombination test (Sec. II.D):
+        // nu_rec,max = max_z n_i * max sigma_rec v; the split mode reads n_i / max n_i
+        double m = 0.0;
+        for (int j = j0; j < j1; ++j) m = fmax(m, s_ni[j]);
+        const double nimax = block_max(m, red);
+        if (t == 0) {
+            K->rec_numax = nimax * K->rec_svmax;
+            K->rec_pmax = -expm1(-K->rec_numax * dt);
+            K->f_rec_pmax = (float)K->rec_pmax;
+        }
+        const double inv = nimax > 0.0 ? 1.0 / nimax : 0.0;
+        for (int j = j0; j < j1; ++j) K->nif[j] = (float)(s_ni[j] * inv);
+    }
+
     // ------------------------------------------------------------- Poisson
     const double phi0 = fc.phi0;
     double *s_rho = s_A;

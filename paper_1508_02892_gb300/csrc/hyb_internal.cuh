@@ -68,7 +68,7 @@ struct InstDev {
     int64_t n_slots_step;             // slots processed by the current step
     int64_t n_samples;
     double flux_in[2];
-    unsigned long long ctr[11];       // births_iz, see0, see1, loss0, loss1, el, exc, iz, null, clamps, pushes
+    unsigned long long ctr[12];       // births_iz, see0, see1, loss0, loss1, el, exc, iz, null, clamps, pushes, rec
     int64_t n_base;                   // live count = n_base + births - losses
     unsigned int status;
     int32_t init_pending;             // field kernel runs in initial-solve mode
@@ -77,9 +77,17 @@ struct InstDev {
     double pw_acc, pw_last;           // sum of V J dt in the running period; P_abs of the last one
     int64_t pw_steps, pw_count, pw_periods;
     unsigned long long pw_loss0;      // electrons absorbed at z = 0 up to the last step
+    // electron-ion recombination (Sec. II.D)
+    int32_t rec_on, pad1;
+    double rec_svmax;                 // bound of sigma_rec v over the table
+    const double *xs_rec;             // [n_xs] sigma_rec (FP64 mode)
+    const float *xs_recf;             // [n_xs] sigma_rec / rec_svmax (split mode)
+    float *nif;                       // [G] n_i / max n_i, written by the field kernel (split mode)
+    double rec_numax, rec_pmax;       // max n_i * rec_svmax and 1 - exp(-rec_numax dt), for the next step
+    float f_rec_pmax, pad2;
 };
 
-enum { C_BIRTH_IZ = 0, C_SEE0, C_SEE1, C_LOSS0, C_LOSS1, C_EL, C_EXC, C_IZ, C_NULL, C_CLAMP, C_PUSH };
+enum { C_BIRTH_IZ = 0, C_SEE0, C_SEE1, C_LOSS0, C_LOSS1, C_EL, C_EXC, C_IZ, C_NULL, C_CLAMP, C_PUSH, C_REC };
 
 // ------------------------------------------------------------ self-checks
 // Every dynamic index of the kernels is guarded: the first failed guard of a
@@ -220,7 +228,8 @@ struct LaunchCfg {
 
 // electron kernels (hyb_electron.cu)
 cudaError_t launch_electron_step(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
-                                 cudaStream_t s);
+                                 cudaStream_t s,
+                                 bool rec = false);
 cudaError_t launch_deposit_init(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
                                 cudaStream_t s);
 cudaError_t launch_load(InstDev *inst, int64_t n, double vth, int precision, cudaStream_t s);

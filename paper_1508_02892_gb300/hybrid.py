@@ -43,7 +43,7 @@ class Params(C.Structure):
         ("e_exc_ev", C.c_double), ("e_iz_ev", C.c_double), ("seed", C.c_uint64),
         ("eedf_bins", C.c_int32), ("eedf_max_ev", C.c_double), ("precision", C.c_int32),
         ("capacity_factor", C.c_double), ("sort_interval", C.c_int32), ("power_w_m2", C.c_double),
-        ("power_alpha", C.c_double),
+        ("power_alpha", C.c_double), ("xs_rec", _pd),
     ]
 
 
@@ -60,7 +60,7 @@ class Counters(C.Structure):
     _fields_ = [("step", C.c_int64), ("particles", C.c_int64), ("births_ionization", C.c_int64),
                 ("births_see", C.c_int64 * 2), ("losses", C.c_int64 * 2), ("collisions", C.c_int64 * 4),
                 ("clamps", C.c_int64), ("pushes", C.c_int64), ("status", C.c_uint32), ("v_rf_amp_v", C.c_double),
-                ("power_last_w_m2", C.c_double), ("power_periods", C.c_int64)]
+                ("power_last_w_m2", C.c_double), ("power_periods", C.c_int64), ("recombinations", C.c_int64)]
 
 
 class Info(C.Structure):
@@ -182,7 +182,7 @@ def make_params(d: dict):
     keep = {}
     p = Params()
     for name, ctype in Params._fields_:
-        if name in ("tab_eon_td", "tab_mu", "tab_nu", "xs_ev", "xs_el", "xs_exc", "xs_ion"):
+        if name in ("tab_eon_td", "tab_mu", "tab_nu", "xs_ev", "xs_el", "xs_exc", "xs_ion", "xs_rec"):
             if name in d and d[name] is not None:
                 a = _arr(d[name])
                 keep[name] = a
@@ -226,7 +226,7 @@ def _counters(call):
             "losses1": c.losses[1], "elastic": c.collisions[0], "excitation": c.collisions[1],
             "ionization": c.collisions[2], "null": c.collisions[3], "clamps": c.clamps, "pushes": c.pushes,
             "status": c.status, "v_rf": c.v_rf_amp_v, "power_last": c.power_last_w_m2,
-            "power_periods": c.power_periods}
+            "power_periods": c.power_periods, "recombinations": c.recombinations}
 
 
 def _particles(call, cap):

@@ -48,7 +48,7 @@ def assert_grid_close(a, b, tol, name=""):
 
 
 COUNTERS = ("step", "particles", "births_iz", "births_see0", "births_see1", "losses0", "losses1", "elastic",
-            "excitation", "ionization", "null", "clamps")
+            "excitation", "ionization", "null", "clamps", "recombinations")
 
 
 def _run_pair(p, steps):
@@ -135,6 +135,30 @@ def test_power_control_vacuum_closed_form():
     assert c["v_rf"] == pytest.approx(150.0 * 1.1 ** 3, rel=1e-9)
 
 
+def test_fp64_recombination_matches_oracle():
+    """Electron-ion recombination (Sec. II.D) with a stand-in rate coefficient
+    large enough for tens of events per step: the removed electrons, their ion
+    sink and everything downstream agree with the oracle."""
+    p = W.config1(precision=W.FP64, n_particles=20000, te0_ev=6.0, ion_model=W.ION_DD_TABLE, weight=2e6,
+                  v_rf_amp_v=300.0, xs_rec=W.recombination_table(1e-6), seed=41)
+    g, o = _run_pair(p, 100)
+    assert o.counters()["recombinations"] > 500
+    _check_all(g, o, p)
+
+
+def test_split_recombination_counts_track_the_oracle():
+    """FP32 split mode draws the same numbers, so its recombination count over
+    300 steps stays within a few per cent of the FP64 oracle's."""
+    for seed in (51, 52):
+        p = W.config1(precision=W.FP32_SPLIT, te0_ev=6.0, xs_rec=W.recombination_table(1e-6), seed=seed)
+        g, o = _gpu(p), oracle.Oracle(p)
+        g.advance(300)
+        o.step(300)
+        a, b = g.counters()["recombinations"], o.counters()["recombinations"]
+        assert b > 1000 and abs(a - b) <= 0.03 * b, (a, b)
+        g.close()
+
+
 def test_empty_discharge():
     p = W.config1(precision=W.FP64, n_particles=0, n0_m3=1e16, weight=1e9)
     g, o = _run_pair(p, 20)
@@ -180,7 +204,8 @@ def test_batch_matches_single_runs_fp64(lanes, sort_interval, field_threads):
     ps = [W.config1(precision=W.FP64, n_particles=5000, n_cells=80, seed=21, te0_ev=6.0),
           W.config1(precision=W.FP64, n_particles=12000, n_cells=150, seed=22, ion_model=W.ION_FULL,
                     gamma_see=0.2, weight=2e6, v_rf_amp_v=300.0),
-          W.config1(precision=W.FP64, n_particles=777, n_cells=33, seed=23, ion_model=W.ION_DD_TABLE)]
+          W.config1(precision=W.FP64, n_particles=777, n_cells=33, seed=23, ion_model=W.ION_DD_TABLE),
+          W.config1(precision=W.FP64, n_particles=3000, n_cells=60, seed=24, xs_rec=W.recombination_table(2e-6))]
     b = hybrid.Batch(4, hybrid.HYB_FP64)
     t = b.set_tuning(lanes=lanes, sort_interval=sort_interval, field_threads=field_threads)
     assert t["sort_interval"] == sort_interval and 1 <= t["lanes"] <= lanes and t["field_threads"] == field_threads
