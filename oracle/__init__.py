@@ -27,6 +27,7 @@ _lock = threading.Lock()
 _lib = None
 
 GRID_NE, GRID_NI, GRID_GAMMA, GRID_PHI, GRID_E, GRID_GSRC = range(6)
+ION_KINETIC = 3
 OUT_NONE, OUT_ELASTIC, OUT_EXC, OUT_ION, OUT_NULL, OUT_LOST0, OUT_LOST1 = range(7)
 FLAG_THERMAL_GAS = 2
 
@@ -129,6 +130,8 @@ def lib():
                 "orc_particle_step_one": (C.c_int, [vp, pd, u32, pd, u64, pd, pd, pu64]),
                 "orc_swarm_run": (None, [C.POINTER(OrcSwarmParams), C.POINTER(OrcSwarmResult), pd]),
                 "orc_get_power": (None, [vp, pd, pi64]),
+                "orc_get_ion_counters": (None, [vp, pi64]),
+                "orc_get_ions": (None, [vp, pd, pd, pd, pd, pu64]),
                 "orc_swarm_nu": (dbl, [dbl, dbl, C.c_int, dbl]),
                 "orc_swarm_nu_bound": (dbl, [dbl, dbl, C.c_int, dbl]),
                 "orc_swarm_qi": (dbl, [dbl]),
@@ -333,6 +336,20 @@ class Oracle:
         flux = np.zeros(2)
         clamps = lib().orc_fluid_update(self.h, _dp(E), _dp(gsrc), _dp(ni), _dp(gam), _dp(flux))
         return ni, gam, flux, int(clamps)
+
+    def ion_counters(self):
+        """Kinetic ions: number, losses at z = 0 and z = L, collision candidates,
+        real collisions."""
+        out = (C.c_int64 * 5)()
+        lib().orc_get_ion_counters(self.h, out)
+        return dict(zip(("ions", "losses0", "losses1", "candidates", "collisions"), (int(x) for x in out)))
+
+    def ions(self):
+        n = self.ion_counters()["ions"]
+        z, vx, vy, vz = (np.zeros(max(n, 1)) for _ in range(4))
+        ids = np.zeros(max(n, 1), dtype=np.uint64)
+        lib().orc_get_ions(self.h, _dp(z), _dp(vx), _dp(vy), _dp(vz), ids.ctypes.data_as(C.POINTER(C.c_uint64)))
+        return {"z": z[:n], "vx": vx[:n], "vy": vy[:n], "vz": vz[:n], "id": ids[:n]}
 
     def power(self):
         """(current RF amplitude, last period's absorbed power per m^2, finished

@@ -41,6 +41,7 @@
 #define ION_DD_CONST 0
 #define ION_DD_TABLE 1
 #define ION_FULL 2
+#define ION_KINETIC 3   /* ions as macroparticles (the paper's fully kinetic comparison model) */
 
 /* test-only switches of the oracle */
 #define FLAG_THERMAL_GAS 2  /* elastic scattering off a Maxwellian target at T_g */
@@ -113,7 +114,16 @@ typedef struct orc_sim {
     double pw_last;         /* P_abs of the last finished period */
     int64_t pw_steps;       /* steps per RF period */
     int64_t pw_count, pw_periods;
+    /* kinetic ions */
+    part *ip;
+    int64_t nip, icap;
+    double *dep_ni, *dep_gi;
+    double mi_red, nu_max_i, p_max_i, vt_gas;
+    int64_t ion_losses[2], ion_coll, ion_cand;
 } orc_sim;
+
+double orc_swarm_nu(double ngas, double m_red, int xs_model, double g);
+double orc_swarm_nu_bound(double ngas, double m_red, int xs_model, double eps_max);
 
 /* ---------------------------------------------------------------- RNG ---- */
 
@@ -422,6 +432,15 @@ static void push_particle(orc_sim *s, const part *q)
         s->pp = (part *)realloc(s->pp, sizeof(part) * (size_t)s->cap);
     }
     s->pp[s->np++] = *q;
+}
+
+static void push_ion(orc_sim *s, const part *q)
+{
+    if (s->nip == s->icap) {
+        s->icap = s->icap ? 2 * s->icap : 1024;
+        s->ip = (part *)realloc(s->ip, sizeof(part) * (size_t)s->icap);
+    }
+    s->ip[s->nip++] = *q;
 }
 
 /* Cell index and CIC offset of position z (Eq. 1.1 with CIC shape). */
@@ -744,14 +763,121 @@ static void solve_field(orc_sim *s, double t)
     free(rho);
 }
 
+/* Ion density (and flux) from the ions' CIC charge assignment. */
+static void ion_grids(orc_sim *s)
+{
+    for (int j = 0; j < s->G; ++j) {
+        s->ni[j] = s->w * s->dep_ni[j] / node_volume(s, j);
+        s->gam[j] = s->w * s->dep_gi[j] / node_volume(s, j);
+    }
+}
+
 /* Deposit the current particles and solve for E at the current time (start of
  * a run, or after the particles were replaced). */
 void orc_init_field(orc_sim *s)
 {
     memset(s->dep_n, 0, sizeof(double) * s->G);
     for (int64_t i = 0; i < s->np; ++i) deposit_one(s, &s->pp[i], 0);
+    if (s->p.ion_model == ION_KINETIC) {
+        memset(s->dep_ni, 0, sizeof(double) * s->G);
+        memset(s->dep_gi, 0, sizeof(double) * s->G);
+        for (int64_t i = 0; i < s->nip; ++i) {
+            int c;
+            double o;
+            locate(s, s->ip[i].z, &c, &o);
+            s->dep_ni[c] += 1.0 - o;
+            s->dep_ni[c + 1] += o;
+            s->dep_gi[c] += (1.0 - o) * s->ip[i].vz;
+            s->dep_gi[c + 1] += o * s->ip[i].vz;
+        }
+        ion_grids(s);
+    }
     solve_field(s, (double)s->step * s->dt);
     memset(s->dep_n, 0, sizeof(double) * s->G);
+}
+
+/* The kinetic-ion part of step n (the paper's fully kinetic comparison model,
+ * with the ion-neutral collisions of the auxiliary Monte Carlo, Sec. II.C):
+ * every ionization of this step adds an ion at the child electron's position
+ * (id = the child's id) with a velocity from the gas Maxwellian (call 4 at
+ * step n); then every ion is pushed in E^n (CIC gather, leapfrog), removed at
+ * the walls (the count per wall is that wall's ion flux for gamma emission),
+ * assigned (CIC) to the ion density and flux, and collides with the gas:
+ * null-collision with a neutral from the gas Maxwellian, acceptance on
+ * N Q_m(eps) g, Q_m = Q_i + 2 Q_b, isotropic in the centre-of-mass frame
+ * (calls 5 and 6 at step n). */
+static void ion_step(orc_sim *s, uint32_t n, const double *kz, const uint64_t *kid, int64_t nk)
+{
+    for (int64_t i = 0; i < nk; ++i) {
+        part q;
+        q.id = kid[i];
+        q.z = kz[i];
+        double a[4], g1, g2, g3, g4;
+        draws(s, q.id, n, 4, a);
+        gauss2(a[0], a[1], &g1, &g2);
+        gauss2(a[2], a[3], &g3, &g4);
+        q.vx = s->vt_gas * g1;
+        q.vy = s->vt_gas * g2;
+        q.vz = s->vt_gas * g3;
+        push_ion(s, &q);
+    }
+    const int G = s->G;
+    memset(s->dep_ni, 0, sizeof(double) * G);
+    memset(s->dep_gi, 0, sizeof(double) * G);
+    const double M = s->m_ion, mn = s->m_gas;
+    int64_t lost[2] = {0, 0}, keep = 0;
+    for (int64_t i = 0; i < s->nip; ++i) {
+        part q = s->ip[i];
+        int c;
+        double o;
+        locate(s, q.z, &c, &o);
+        double ep = (1.0 - o) * s->E[c] + o * s->E[c + 1];
+        q.vz = q.vz + (Q_E / M) * ep * s->dt;
+        q.z = q.z + q.vz * s->dt;
+        if (q.z < 0.0) {
+            lost[0]++;
+            continue;
+        }
+        if (q.z >= s->L) {
+            lost[1]++;
+            continue;
+        }
+        locate(s, q.z, &c, &o);
+        s->dep_ni[c] += 1.0 - o;
+        s->dep_ni[c + 1] += o;
+        s->dep_gi[c] += (1.0 - o) * q.vz;
+        s->dep_gi[c + 1] += o * q.vz;
+        double u[4], w[4];
+        draws(s, q.id, n, 5, u);
+        if (u[0] < s->p_max_i) {
+            s->ion_cand++;
+            draws(s, q.id, n, 6, w);
+            double b1, b2, b3, b4;
+            gauss2(u[2], u[3], &b1, &b2);
+            gauss2(w[0], w[1], &b3, &b4);
+            double V[3] = {s->vt_gas * b1, s->vt_gas * b2, s->vt_gas * b3};
+            double v[3] = {q.vx, q.vy, q.vz};
+            double gx = v[0] - V[0], gy = v[1] - V[1], gz = v[2] - V[2];
+            double g = sqrt(gx * gx + gy * gy + gz * gz);
+            double nu = orc_swarm_nu(s->ngas, s->mi_red, 0, g);
+            if (u[1] * s->nu_max_i < nu) {
+                s->ion_coll++;
+                double d[3];
+                iso_dir(w[2], w[3], d);
+                for (int k = 0; k < 3; ++k) v[k] = (M * v[k] + mn * V[k]) / (M + mn) + mn / (M + mn) * g * d[k];
+                q.vx = v[0];
+                q.vy = v[1];
+                q.vz = v[2];
+            }
+        }
+        s->ip[keep++] = q;
+    }
+    s->nip = keep;
+    s->ion_losses[0] += lost[0];
+    s->ion_losses[1] += lost[1];
+    s->flux_in[0] = (double)lost[0] * s->w / s->dt;
+    s->flux_in[1] = (double)lost[1] * s->w / s->dt;
+    ion_grids(s);
 }
 
 /* One full step n -> n+1 (Secs. II.A and II.D), ending with the gamma
@@ -811,12 +937,21 @@ static void step_once(orc_sim *s)
         s->pp[keep++] = q;
     }
     s->np = keep;
-    for (int64_t i = 0; i < nk; ++i) push_particle(s, &kids[i]);
+    double *kids_z = (double *)malloc(sizeof(double) * (size_t)(nk ? nk : 1));
+    uint64_t *kids_id = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nk ? nk : 1));
+    for (int64_t i = 0; i < nk; ++i) {
+        kids_z[i] = kids[i].z;
+        kids_id[i] = kids[i].id;
+        push_particle(s, &kids[i]);
+    }
     free(kids);
 
     /* coupling: ion source, fluid ions, Poisson */
     for (int j = 0; j < G; ++j) s->gsrc[j] = s->w * s->s_iz[j] / (node_volume(s, j) * s->dt);
-    s->n_clamp += orc_fluid_update(s, s->E, s->gsrc, s->ni, s->gam, s->flux_in);
+    if (s->p.ion_model == ION_KINETIC)
+        ion_step(s, n, kids_z, kids_id, nk);
+    else
+        s->n_clamp += orc_fluid_update(s, s->E, s->gsrc, s->ni, s->gam, s->flux_in);
     solve_field(s, (double)(s->step + 1) * s->dt);
 
     for (int j = 0; j < G; ++j) {
@@ -826,6 +961,8 @@ static void step_once(orc_sim *s)
         s->acc_wn[j] += s->dep_n[j];
         s->acc_we[j] += s->dep_e[j];
     }
+    free(kids_z);
+    free(kids_id);
     s->n_samples++;
     const double v_new = drive(s, (double)(s->step + 1) * s->dt);
     s->step++;
@@ -868,6 +1005,28 @@ static void load_particles(orc_sim *s)
         q.vy = vth * g2;
         q.vz = vth * g3;
         push_particle(s, &q);
+    }
+}
+
+/* Kinetic ions: n_particles ions, ids 2^61 + i, uniform in [0, L), Maxwellian
+ * at the gas temperature, drawn at step 0xFFFFFFFF with calls 4 (position and
+ * a Box-Muller pair) and 5 (a second pair). */
+static void load_ions(orc_sim *s)
+{
+    for (int64_t j = 0; j < s->p.n_particles; ++j) {
+        part q;
+        q.id = (1ull << 61) + (uint64_t)j;
+        double a[4], b[4];
+        draws(s, q.id, 0xFFFFFFFFu, 4, a);
+        draws(s, q.id, 0xFFFFFFFFu, 5, b);
+        q.z = a[0] * s->L;
+        double g1, g2, g3, g4;
+        gauss2(a[1], a[2], &g1, &g2);
+        gauss2(b[0], b[1], &g3, &g4);
+        q.vx = s->vt_gas * g1;
+        q.vy = s->vt_gas * g2;
+        q.vz = s->vt_gas * g3;
+        push_ion(s, &q);
     }
 }
 
@@ -952,6 +1111,15 @@ orc_sim *orc_create(const orc_params *p)
     s->eedf = (double *)calloc(s->p.eedf_bins + 1, sizeof(double));
     for (int j = 0; j < G; ++j) s->ni[j] = p->n0_m3;
 
+    if (p->ion_model == ION_KINETIC) {
+        s->dep_ni = (double *)calloc(G, sizeof(double));
+        s->dep_gi = (double *)calloc(G, sizeof(double));
+        s->mi_red = s->m_ion * s->m_gas / (s->m_ion + s->m_gas);
+        s->nu_max_i = orc_swarm_nu_bound(s->ngas, s->mi_red, 0, 100.0);
+        s->p_max_i = -expm1(-s->nu_max_i * s->dt);
+        s->vt_gas = sqrt(K_B * p->gas_temp_k / s->m_gas);
+        load_ions(s);
+    }
     load_particles(s);
     orc_init_field(s);
     return s;
@@ -961,10 +1129,12 @@ void orc_destroy(orc_sim *s)
 {
     if (!s) return;
     double *bufs[] = {s->tab_eon, s->tab_mu, s->tab_nu, s->tab_u, s->xs_ev, s->xs_el, s->xs_exc, s->xs_ion, s->xs_rec,
+                      s->dep_ni, s->dep_gi,
                       s->ni, s->gam, s->phi, s->E, s->ne, s->dep_n, s->dep_e, s->s_iz, s->gsrc,
                       s->acc_ne, s->acc_ni, s->acc_gi, s->acc_wn, s->acc_we, s->eedf};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) free(bufs[i]);
     free(s->pp);
+    free(s->ip);
     free(s);
 }
 
@@ -1236,5 +1406,37 @@ void orc_get_power(const orc_sim *s, double out[2], int64_t iout[2])
     out[1] = s->pw_last;
     iout[0] = s->pw_periods;
     iout[1] = s->pw_steps;
+}
+
+/* kinetic ions: number, losses at z = 0 and z = L, candidates, real collisions */
+void orc_get_ion_counters(const orc_sim *s, int64_t out[5])
+{
+    out[0] = s->nip;
+    out[1] = s->ion_losses[0];
+    out[2] = s->ion_losses[1];
+    out[3] = s->ion_cand;
+    out[4] = s->ion_coll;
+}
+
+static int ion_by_id(const void *a, const void *b)
+{
+    uint64_t x = ((const part *)a)->id, y = ((const part *)b)->id;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* the ions, sorted by id */
+void orc_get_ions(orc_sim *s, double *z, double *vx, double *vy, double *vz, uint64_t *id)
+{
+    part *t = (part *)malloc(sizeof(part) * (size_t)(s->nip ? s->nip : 1));
+    memcpy(t, s->ip, sizeof(part) * (size_t)s->nip);
+    qsort(t, (size_t)s->nip, sizeof(part), ion_by_id);
+    for (int64_t i = 0; i < s->nip; ++i) {
+        z[i] = t[i].z;
+        vx[i] = t[i].vx;
+        vy[i] = t[i].vy;
+        vz[i] = t[i].vz;
+        id[i] = t[i].id;
+    }
+    free(t);
 }
 

@@ -26,7 +26,7 @@ ATM = 101325.0
 KB_INPUT = 1.380649e-23   # only to turn E/N into E when sampling the printed fits
 
 GAS_HE, GAS_AR = 0, 1
-ION_DD_CONST, ION_DD_TABLE, ION_FULL = 0, 1, 2
+ION_DD_CONST, ION_DD_TABLE, ION_FULL, ION_KINETIC = 0, 1, 2, 3
 FP64, FP32_SPLIT = 0, 1
 
 HE_EXC_EV, HE_IZ_EV = 19.8, 24.6
