@@ -54,6 +54,11 @@ extern "C" {
 #define HYB_ION_DD_CONST 0      /* drift-diffusion, constant mobility, T_i = T_gas (Eqs. 2.5-2.7) */
 #define HYB_ION_DD_TABLE 1      /* drift-diffusion, mu(E) table, T_i from Eq. 2.8 */
 #define HYB_ION_FULL 2          /* momentum equation with inertia, Eq. 2.3, nu(u) table */
+#define HYB_ION_KINETIC 3       /* ions as macroparticles (the paper's fully kinetic comparison model):
+                                   He+ with the electrons' weight, pushed in E every step, removed at
+                                   the walls, colliding with the gas as in the auxiliary Monte Carlo of
+                                   Sec. II.C (Q_m = Q_i + 2 Q_b, thermal target); one new ion per
+                                   ionization, at the new electron's position */
 
 #define HYB_FP64 0              /* particles and grids in FP64 */
 #define HYB_FP32_SPLIT 1        /* particles as (cell, FP32 offset) + FP32 velocity; FP64 grids */
@@ -146,6 +151,9 @@ typedef struct hyb_counters {
                                    absorbed and emitted there, displacement) */
     int64_t power_periods;      /* finished RF periods */
     int64_t recombinations;     /* electrons removed by electron-ion recombination */
+    int64_t ions;               /* kinetic ions: live ion macroparticles (0 for the fluid models) */
+    int64_t ion_losses[2];      /* kinetic ions removed at z = 0 and z = L */
+    int64_t ion_collisions;     /* real ion-neutral collisions of the kinetic ions */
 } hyb_counters;
 
 #define HYB_STATUS_CAPACITY 1u
@@ -199,7 +207,14 @@ int hyb_read_particles(hyb_discharge *h, double *z, double *vx, double *vy, doub
 int hyb_write_particles(hyb_discharge *h, int64_t n, const double *z, const double *vx, const double *vy,
                         const double *vz, const uint64_t *id);
 
-/* Overwrite the ion density (host, n_nodes values) and re-solve the field. */
+/* Kinetic ions (HYB_ION_KINETIC): the live ions sorted by id into host arrays
+ * of cap entries (any may be NULL), *n their number; HYB_ERR_STATE for the
+ * fluid ion models, HYB_ERR_ARG if they do not fit. */
+int hyb_read_ions(hyb_discharge *h, double *z, double *vx, double *vy, double *vz, uint64_t *id, int64_t cap,
+                  int64_t *n);
+
+/* Overwrite the ion density (host, n_nodes values) and re-solve the field
+ * (fluid ion models; HYB_ERR_STATE for kinetic ions). */
 int hyb_write_ion_density(hyb_discharge *h, const double *ni);
 
 int hyb_destroy(hyb_discharge *h);
@@ -233,6 +248,9 @@ int hyb_batch_read_moments(hyb_batch *b, int32_t slot, hyb_moments *out);
 int hyb_batch_read_counters(hyb_batch *b, int32_t slot, hyb_counters *out);
 int hyb_batch_read_particles(hyb_batch *b, int32_t slot, double *z, double *vx, double *vy, double *vz,
                              uint64_t *id, int64_t cap, int64_t *n);
+
+int hyb_batch_read_ions(hyb_batch *b, int32_t slot, double *z, double *vx, double *vy, double *vz, uint64_t *id,
+                        int64_t cap, int64_t *n);
 
 /* Free a slot and its memory (waits for the GPU). */
 int hyb_batch_evict(hyb_batch *b, int32_t slot);

@@ -62,6 +62,7 @@ struct Slot {
     bool reported = false;
     hyb_params p{};
     InstDev h{};
+    InstDev hi{};  // kinetic ions: the ion descriptor
     void *mem = nullptr;
     int64_t bytes = 0;
     int64_t target = 0;
@@ -101,7 +102,9 @@ int validate(const hyb_params *p)
     if (p->n_particles < 0 || p->n0_m3 < 0 || p->te0_ev < 0 || p->weight < 0 || p->gamma_see < 0)
         return fail(HYB_ERR_ARG, "negative particle count, density, temperature, weight or gamma");
     if (p->precision != HYB_FP64 && p->precision != HYB_FP32_SPLIT) return fail(HYB_ERR_ARG, "unknown precision");
-    if (p->ion_model < HYB_ION_DD_CONST || p->ion_model > HYB_ION_FULL) return fail(HYB_ERR_ARG, "unknown ion model");
+    if (p->ion_model < HYB_ION_DD_CONST || p->ion_model > HYB_ION_KINETIC) return fail(HYB_ERR_ARG, "unknown ion model");
+    if (p->ion_model == HYB_ION_KINETIC && p->xs_rec)
+        return fail(HYB_ERR_ARG, "recombination is built for the fluid ion models only");
     if (p->eedf_bins < 0 || p->eedf_bins > 4096) return fail(HYB_ERR_ARG, "eedf_bins must be in [0, 4096]");
     if (!p->xs_ev || !p->xs_el || !p->xs_exc || !p->xs_ion || p->n_xs < 2)
         return fail(HYB_ERR_ARG, "cross-section tables missing");
@@ -115,7 +118,7 @@ int validate(const hyb_params *p)
         if (p->xs_el[i] < 0 || p->xs_exc[i] < 0 || p->xs_ion[i] < 0)
             return fail(HYB_ERR_ARG, "negative cross section");
     if (p->e_exc_ev < 0 || p->e_iz_ev < 0) return fail(HYB_ERR_ARG, "negative threshold");
-    if (p->ion_model != HYB_ION_DD_CONST) {
+    if (p->ion_model == HYB_ION_DD_TABLE || p->ion_model == HYB_ION_FULL) {
         if (!p->tab_eon_td || !p->tab_mu || !p->tab_nu || p->n_tab < 2 || p->n_tab > 256)
             return fail(HYB_ERR_ARG, "ion transport tables missing or longer than 256");
         if (!finite_all(p->tab_eon_td, p->n_tab) || !finite_all(p->tab_mu, p->n_tab) ||
@@ -181,6 +184,13 @@ Layout layout_of(const hyb_params &p)
     add(8 * (size_t)p.n_xs);                            // xs_rec
     add(4 * (size_t)p.n_xs);                            // xs_recf
     add(4 * (size_t)G);                                 // nif
+    if (p.ion_model == HYB_ION_KINETIC) {
+        for (int b = 0; b < 2; ++b)
+            for (int k = 0; k < 5; ++k) add(8 * cap);   // ion z, vx, vy, vz, id
+        add(4 * (size_t)G);                             // ion cell counts
+        add(8 * (size_t)G);                             // dep_ni
+        add(8 * (size_t)G);                             // dep_gi
+    }
     L.total = o;
     return L;
 }
@@ -222,7 +232,7 @@ void derive(const hyb_params &p, InstDev &K, std::vector<double> &xs, std::vecto
     K.G = p.n_cells + 1;
     K.ion_model = p.ion_model;
     K.n_xs = p.n_xs;
-    K.n_tab = p.ion_model == HYB_ION_DD_CONST ? 0 : p.n_tab;
+    K.n_tab = (p.ion_model == HYB_ION_DD_TABLE || p.ion_model == HYB_ION_FULL) ? p.n_tab : 0;
     K.eedf_bins = bins_of(p);
     K.capacity = capacity_of(p);
     K.L = p.gap_m;
@@ -292,6 +302,14 @@ void derive(const hyb_params &p, InstDev &K, std::vector<double> &xs, std::vecto
         xsf[i] = make_float4((float)p.xs_ev[i], (float)(scale * p.xs_el[i]), (float)(scale * p.xs_exc[i]),
                              (float)(scale * p.xs_ion[i]));
     }
+    // kinetic ions: the collision bound of the auxiliary Monte Carlo over
+    // relative energies up to 100 eV, and the gas Maxwellian
+    if (p.ion_model == HYB_ION_KINETIC) {
+        K.mi_red = K.m_ion * K.m_gas / (K.m_ion + K.m_gas);
+        K.nu_max_i = swarm_nu_bound(K.ngas, K.mi_red, 100.0);
+        K.p_max_i = -expm1(-K.nu_max_i * K.dt);
+        K.vt_gas = sqrt(kKb * p.gas_temp_k / K.m_gas);
+    }
     // recombination (Sec. II.D): sigma_rec v bounded on each table segment by the
     // larger endpoint cross section times the speed at the upper end
     K.rec_on = p.xs_rec != nullptr;
@@ -312,7 +330,7 @@ void derive(const hyb_params &p, InstDev &K, std::vector<double> &xs, std::vecto
     }
 }
 
-void bind_pointers(const hyb_params &p, const Layout &L, char *base, InstDev &K)
+void bind_pointers(const hyb_params &p, const Layout &L, char *base, InstDev &K, InstDev *ion_out)
 {
     int k = 0;
     for (int b = 0; b < 2; ++b) {
@@ -344,6 +362,23 @@ void bind_pointers(const hyb_params &p, const Layout &L, char *base, InstDev &K)
     K.xs_rec = (const double *)(base + L.off[k++]);
     K.xs_recf = (const float *)(base + L.off[k++]);
     K.nif = (float *)(base + L.off[k++]);
+    if (p.ion_model == HYB_ION_KINETIC) {
+        // the ion descriptor starts as a copy of this one; here the ion buffers
+        // go to I (its fields buf and cell_cnt), the shared sums to K
+        InstDev &I = *ion_out;
+        for (int b = 0; b < 2; ++b) {
+            PartBuf &B = I.buf[b];
+            memset(&B, 0, sizeof B);
+            B.z = (double *)(base + L.off[k++]);
+            B.vxd = (double *)(base + L.off[k++]);
+            B.vyd = (double *)(base + L.off[k++]);
+            B.vzd = (double *)(base + L.off[k++]);
+            B.id = (uint64_t *)(base + L.off[k++]);
+        }
+        I.cell_cnt = (int32_t *)(base + L.off[k++]);
+        K.dep_ni = (double *)(base + L.off[k++]);
+        K.dep_gi = (double *)(base + L.off[k++]);
+    }
 }
 
 }  // namespace
@@ -370,6 +405,10 @@ struct hyb_batch {
     int blocks_per_sm = 0;                 // electron grid = SMs x this (0: occupancy limit)
     int field_threads = 256;               // threads of an instance's field block
     bool any_rec = false;                  // some admitted discharge has recombination
+    bool any_kin = false;                  // some admitted discharge has kinetic ions
+    InstDev *d_inst_ion = nullptr;         // ion descriptors, slot for slot (zero: none)
+    int64_t *d_prefix_ion = nullptr;       // kMaxLanes x (max_inst + 1)
+    int64_t *d_prefix1_ion = nullptr;
     int occ_per_sm = 0;
     std::vector<Slot> slots;
     int64_t hbm_cap = 0, hbm_used = 0;
@@ -441,11 +480,15 @@ int configure(hyb_batch *b, int nodes, int bins)
 }
 
 int lane_first(const hyb_batch *b, int k) { return k * b->per_lane; }
+InstDev *lane_inst_ion(const hyb_batch *b, int k);
+int64_t *lane_prefix_ion(const hyb_batch *b, int k);
 int lane_count(const hyb_batch *b, int k) { return std::max(0, std::min(b->per_lane, b->max_inst - k * b->per_lane)); }
 int64_t *lane_prefix(const hyb_batch *b, int k) { return b->d_prefix + (size_t)k * (b->max_inst + 1); }
 unsigned *lane_ticket(const hyb_batch *b, int k) { return b->d_ticket + k; }
 cudaStream_t lane_stream(const hyb_batch *b, int k) { return k == 0 ? b->stream : b->lstream[k]; }
 InstDev *lane_inst(const hyb_batch *b, int k) { return b->d_inst + lane_first(b, k); }
+InstDev *lane_inst_ion(const hyb_batch *b, int k) { return b->d_inst_ion + lane_first(b, k); }
+int64_t *lane_prefix_ion(const hyb_batch *b, int k) { return b->d_prefix_ion + (size_t)k * (b->max_inst + 1); }
 
 // Chunk prefixes of every lane (after an admission, eviction or relayout).
 int prefix_all(hyb_batch *b)
@@ -457,6 +500,10 @@ int prefix_all(hyb_batch *b)
 
 constexpr int kSortKernels = 5;
 constexpr int kChunkTarget = 100;  // steps per captured graph (a multiple of the sort interval)
+
+// kernels per lane of a step and of a sort
+int step_kernels(const hyb_batch *b) { return 2 + (b->any_kin ? 2 : 0); }
+int sort_kernels(const hyb_batch *b) { return kSortKernels + (b->any_kin ? 1 + kSortKernels : 0); }
 
 int chunk_len(const hyb_batch *b)
 {
@@ -504,7 +551,12 @@ int launch_step(hyb_batch *b, int k, int lane, cudaStream_t s)
     int rc;
     const int n = lane_count(b, lane);
     if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k)))) return rc;
-    CK(launch_electron_step(lane_inst(b, lane), n, lane_prefix(b, lane), b->precision, b->cfg, s, b->any_rec));
+    CK(launch_electron_step(lane_inst(b, lane), n, lane_prefix(b, lane), b->precision, b->cfg, s, b->any_rec,
+                            b->any_kin));
+    if (b->any_kin) {  // the ions of the step, after the electrons' births
+        CK(launch_ion_prefix(lane_inst_ion(b, lane), n, lane_prefix_ion(b, lane), s));
+        CK(launch_ion_step(lane_inst_ion(b, lane), n, lane_prefix_ion(b, lane), 0, b->cfg.grid, b->max_nodes, s));
+    }
     if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k + 1)))) return rc;
     CK(launch_field(lane_inst(b, lane), n, lane_prefix(b, lane), lane_ticket(b, lane), b->precision == HYB_FP32_SPLIT,
                     b->max_nodes, b->field_threads, s));
@@ -520,6 +572,10 @@ int launch_sort_all(hyb_batch *b, int j, int lane, cudaStream_t s)
     const size_t s0 = 3 * (size_t)chunk_len(b) + 2 * (size_t)j;
     if (b->profiling && (rc = record(s, lane_event(b, lane, s0)))) return rc;
     CK(launch_sort(lane_inst(b, lane), lane_count(b, lane), lane_prefix(b, lane), b->precision, b->cfg, s));
+    if (b->any_kin) {  // compaction and cell sort of the ions (FP64 layout)
+        CK(launch_ion_prefix(lane_inst_ion(b, lane), lane_count(b, lane), lane_prefix_ion(b, lane), s));
+        CK(launch_sort(lane_inst_ion(b, lane), lane_count(b, lane), lane_prefix_ion(b, lane), HYB_FP64, b->cfg, s));
+    }
     if (b->profiling && (rc = record(s, lane_event(b, lane, s0 + 1)))) return rc;
     return HYB_OK;
 }
@@ -635,6 +691,11 @@ int reinit_slot(hyb_batch *b, int slot, bool sort)
     InstDev *K = &b->d_inst[slot];
     CK(launch_prefix_one(K, b->d_prefix1, b->stream));
     CK(launch_deposit_init(K, 1, b->d_prefix1, b->precision, b->cfg, b->stream));
+    if (b->slots[slot].h.ion) {  // kinetic ions: their charge assignment first
+        InstDev *I = &b->d_inst_ion[slot];
+        CK(launch_prefix_one(I, b->d_prefix1_ion, b->stream));
+        CK(launch_ion_step(I, 1, b->d_prefix1_ion, 1, b->cfg.grid, b->max_nodes, b->stream));
+    }
     CK(launch_field(K, 1, b->d_prefix1, b->d_ticket1, b->precision == HYB_FP32_SPLIT, b->max_nodes, b->field_threads,
                     b->stream));
     if (sort) {
@@ -707,7 +768,7 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
         return fail(HYB_ERR_OOM, "cudaMallocAsync(%zu): %s", L.total, cudaGetErrorString(e));
     }
     char *base = (char *)mem;
-    bind_pointers(*p, L, base, S.h);
+    bind_pointers(*p, L, base, S.h, &S.hi);
     CK(cudaMemsetAsync(base + L.grid_off, 0, L.total - L.grid_off, b->stream));
     const int G = S.h.G;
     std::vector<double> ni(G, p->n0_m3);
@@ -733,7 +794,31 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     S.h.n_base = p->n_particles;
     S.h.init_pending = 1;
     if (p->n_particles > S.h.capacity) return fail(HYB_ERR_CAPACITY, "n_particles exceeds capacity");
+    const bool kin = p->ion_model == HYB_ION_KINETIC;
+    if (kin) {
+        // the ion descriptor: the electron one's constants and grids, the ion
+        // buffers bound above, FP64 particles, its own counts
+        InstDev I = S.h;
+        I.buf[0] = S.hi.buf[0];
+        I.buf[1] = S.hi.buf[1];
+        I.cell_cnt = S.hi.cell_cnt;
+        I.precision = HYB_FP64;
+        I.cur = 0;
+        I.n_slots = (unsigned long long)p->n_particles;
+        I.n_slots_step = p->n_particles;
+        I.n_base = p->n_particles;
+        I.init_pending = 0;
+        I.ion = nullptr;
+        I.elec = &b->d_inst[slot];
+        S.hi = I;
+        S.h.ion = &b->d_inst_ion[slot];
+        CK(cudaMemcpyAsync(&b->d_inst_ion[slot], &S.hi, sizeof(InstDev), cudaMemcpyHostToDevice, b->stream));
+    } else {
+        S.h.ion = nullptr;
+        CK(cudaMemsetAsync(&b->d_inst_ion[slot], 0, sizeof(InstDev), b->stream));
+    }
     CK(cudaMemcpyAsync(&b->d_inst[slot], &S.h, sizeof(InstDev), cudaMemcpyHostToDevice, b->stream));
+    if (kin) CK(launch_load_ions(&b->d_inst_ion[slot], p->n_particles, b->stream));
     CK(cudaStreamSynchronize(b->stream));  // host staging vectors go out of scope
     const double vth = sqrt(kQe * p->te0_ev / kMe);
     CK(launch_load(&b->d_inst[slot], p->n_particles, vth, p->precision, b->stream));
@@ -749,6 +834,11 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     S.p.xs_ev = S.p.xs_el = S.p.xs_exc = S.p.xs_ion = S.p.xs_rec = nullptr;
     if (S.h.rec_on && !b->any_rec) {  // the electron step switches to its recombination variant
         b->any_rec = true;
+        rc = drop_graph(b);
+        if (rc) return rc;
+    }
+    if (kin && !b->any_kin) {  // from now on every step also runs the ion kernels
+        b->any_kin = true;
         rc = drop_graph(b);
         if (rc) return rc;
     }
@@ -782,7 +872,7 @@ int advance(hyb_batch *b, int64_t n)
                 if (rc) return rc;
             }
             CK(cudaGraphLaunch(b->graph, b->stream));
-            b->launches += b->lanes * (2 * (int64_t)GL + kSortKernels * (int64_t)(GL / b->sort_interval));
+            b->launches += b->lanes * (step_kernels(b) * (int64_t)GL + sort_kernels(b) * (int64_t)(GL / b->sort_interval));
             b->steps += GL;
             n -= GL;
             b->pending = b->profiling;
@@ -795,7 +885,7 @@ int advance(hyb_batch *b, int64_t n)
             if (rc) return rc;
             if (sort_now && (rc = launch_sort_all(b, 0, lane, b->stream))) return rc;
         }
-        b->launches += b->lanes * (2 + (sort_now ? kSortKernels : 0));
+        b->launches += b->lanes * (step_kernels(b) + (sort_now ? sort_kernels(b) : 0));
         b->steps += 1;
         --n;
         b->since_sort = sort_now ? 0 : b->since_sort + 1;
@@ -1015,6 +1105,16 @@ int read_counters(hyb_batch *b, int slot, hyb_counters *c)
     c->power_last_w_m2 = K.pw_last;
     c->power_periods = K.pw_periods;
     c->recombinations = (int64_t)K.ctr[C_REC];
+    c->ions = c->ion_losses[0] = c->ion_losses[1] = c->ion_collisions = 0;
+    if (b->slots[slot].h.ion) {
+        InstDev I{};
+        CK(cudaMemcpyAsync(&I, &b->d_inst_ion[slot], sizeof I, cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        c->ion_losses[0] = (int64_t)I.ctr[C_LOSS0];
+        c->ion_losses[1] = (int64_t)I.ctr[C_LOSS1];
+        c->ion_collisions = (int64_t)I.ctr[C_EL];
+        c->ions = I.n_base + (int64_t)K.ctr[C_BIRTH_IZ] - c->ion_losses[0] - c->ion_losses[1];
+    }
     return rc;
 }
 
@@ -1073,11 +1173,50 @@ int read_particles(hyb_batch *b, int slot, double *z, double *vx, double *vy, do
     return rc;
 }
 
+// the kinetic ions of a slot, alive ones sorted by id
+int read_ions(hyb_batch *b, int slot, double *z, double *vx, double *vy, double *vz, uint64_t *id, int64_t cap,
+              int64_t *n)
+{
+    int rc = check_slot(b, slot);
+    if (rc) return rc;
+    if (!b->slots[slot].h.ion) return fail(HYB_ERR_STATE, "the discharge has fluid ions");
+    rc = sync_status(b, slot);
+    InstDev I{};
+    CK(cudaMemcpy(&I, &b->d_inst_ion[slot], sizeof I, cudaMemcpyDeviceToHost));
+    const int64_t ns = std::min((int64_t)I.n_slots, I.capacity);
+    const PartBuf P = I.buf[I.cur];
+    std::vector<double> hz(ns), hx(ns), hy(ns), hv(ns);
+    std::vector<uint64_t> hid(ns);
+    if (ns > 0) {
+        CK(cudaMemcpy(hid.data(), P.id, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(hz.data(), P.z, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(hx.data(), P.vxd, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(hy.data(), P.vyd, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(hv.data(), P.vzd, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+    }
+    std::vector<int64_t> idx;
+    for (int64_t i = 0; i < ns; ++i)
+        if (hz[i] >= 0.0) idx.push_back(i);
+    std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t c) { return hid[a] < hid[c]; });
+    *n = (int64_t)idx.size();
+    if (*n > cap) return fail(HYB_ERR_ARG, "%lld ions exceed the buffers (%lld)", (long long)*n, (long long)cap);
+    for (size_t k = 0; k < idx.size(); ++k) {
+        const int64_t i = idx[k];
+        if (z) z[k] = hz[i];
+        if (vx) vx[k] = hx[i];
+        if (vy) vy[k] = hy[i];
+        if (vz) vz[k] = hv[i];
+        if (id) id[k] = hid[i];
+    }
+    return rc;
+}
+
 int free_slot(hyb_batch *b, int slot)
 {
     Slot &S = b->slots[slot];
     if (!S.used) return HYB_OK;
     CK(launch_set_active(&b->d_inst[slot], 0, 0, b->stream));
+    CK(cudaMemsetAsync(&b->d_inst_ion[slot], 0, sizeof(InstDev), b->stream));  // before its buffers go
     int rc = prefix_all(b);
     if (rc) return rc;
     CK(cudaFreeAsync(S.mem, b->stream));
@@ -1136,6 +1275,11 @@ int hyb_batch_create(int32_t max_instances, int32_t precision, int64_t hbm_cap_b
     CK(cudaMemset(b->d_ticket, 0, sizeof(unsigned) * (kMaxLanes + 1)));
     b->d_ticket1 = b->d_ticket + kMaxLanes;
     CK(cudaMallocHost(&b->h_stage, sizeof(InstDev) * (size_t)max_instances));
+    CK(cudaMalloc(&b->d_inst_ion, sizeof(InstDev) * (size_t)max_instances));
+    CK(cudaMemset(b->d_inst_ion, 0, sizeof(InstDev) * (size_t)max_instances));
+    CK(cudaMalloc(&b->d_prefix_ion, sizeof(int64_t) * np));
+    CK(cudaMemset(b->d_prefix_ion, 0, sizeof(int64_t) * np));
+    CK(cudaMalloc(&b->d_prefix1_ion, sizeof(int64_t) * 2));
     int rc = configure(b, 3, 2);
     if (rc) return rc;
     rc = set_lanes(b, std::min(kDefaultLanes, max_instances));
@@ -1194,6 +1338,13 @@ int hyb_batch_read_particles(hyb_batch *b, int32_t slot, double *z, double *vx, 
     return read_particles(b, slot, z, vx, vy, vz, id, cap, n);
 }
 
+int hyb_batch_read_ions(hyb_batch *b, int32_t slot, double *z, double *vx, double *vy, double *vz, uint64_t *id,
+                        int64_t cap, int64_t *n)
+{
+    if (!n) return fail(HYB_ERR_ARG, "NULL argument");
+    return read_ions(b, slot, z, vx, vy, vz, id, cap, n);
+}
+
 int hyb_batch_evict(hyb_batch *b, int32_t slot)
 {
     int rc = check_slot(b, slot);
@@ -1240,6 +1391,9 @@ int hyb_batch_destroy(hyb_batch *b)
     cudaFree(b->d_prefix);
     cudaFree(b->d_prefix1);
     cudaFree(b->d_ticket);
+    cudaFree(b->d_inst_ion);
+    cudaFree(b->d_prefix_ion);
+    cudaFree(b->d_prefix1_ion);
     cudaFreeHost(b->h_stage);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -1479,9 +1633,17 @@ int hyb_write_particles(hyb_discharge *h, int64_t n, const double *z, const doub
     return HYB_OK;
 }
 
+int hyb_read_ions(hyb_discharge *h, double *z, double *vx, double *vy, double *vz, uint64_t *id, int64_t cap,
+                  int64_t *n)
+{
+    if (!h || !n) return fail(HYB_ERR_ARG, "NULL argument");
+    return read_ions(h->b, h->slot, z, vx, vy, vz, id, cap, n);
+}
+
 int hyb_write_ion_density(hyb_discharge *h, const double *ni)
 {
     if (!h || !ni) return fail(HYB_ERR_ARG, "NULL argument");
+    if (h->b->slots[h->slot].h.ion) return fail(HYB_ERR_STATE, "kinetic ions: the ion density follows the ions");
     hyb_batch *b = h->b;
     const Slot &S = b->slots[h->slot];
     if (!finite_all(ni, S.h.G)) return fail(HYB_ERR_NONFINITE, "non-finite ion density");

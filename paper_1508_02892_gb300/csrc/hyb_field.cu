@@ -253,7 +253,29 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
 
     const Fluid F{K->ion_model, K->n_tab, K->tab, K->mu_const, K->ngas, K->kT_gas, K->m_ion, K->m_gas};
     double *gfin = s_g;
-    if (FAST && !init) {
+    const bool kin = K->ion_model == HYB_ION_KINETIC;
+    if (kin) {
+        // kinetic ions: n_i and Gamma_i from the ions' charge assignment of this
+        // step (at initialisation, of the loaded ions)
+        for (int j = j0; j < j1; ++j) {
+            const double vol = node_volume(j, G, dz);
+            const double nn = w * K->dep_ni[j] / vol;
+            const double gg = w * K->dep_gi[j] / vol;
+            s_ni[j] = nn;
+            s_g[j] = gg;
+            K->ni[j] = nn;
+            K->gam[j] = gg;
+            K->dep_ni[j] = 0.0;
+            K->dep_gi[j] = 0.0;
+            if (!init) {
+                K->gsrc[j] = w * K->s_iz[j] / (vol * dt);
+                K->acc_ni[j] += nn;
+                K->acc_gi[j] += gg;
+            }
+        }
+        __syncthreads();
+    }
+    if (FAST && !init && !kin) {
         // ------------------------------------ ion fluid, FP32 coefficients
         for (int j = t; j < 4 * K->n_tab; j += T) s_tabf[j] = (float)K->tab[j];
         __syncthreads();
@@ -347,7 +369,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
         if (clamps) atomicAdd(&red.count, clamps);
         __syncthreads();
     }
-    if (!FAST && !init) {
+    if (!FAST && !init && !kin) {
         // ---------------------------------------------------------- ion fluid
         if (K->ion_model == HYB_ION_FULL) {
             // Eq. 2.3: nu at u^n = Gamma^{n-1/2}/n^n, advection semi-implicit
@@ -542,9 +564,18 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
         if (red.count) K->ctr[C_CLAMP] += red.count;
         K->n_samples += 1;
         const double v_old = K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)K->step * dt));
-        const double g0 = gfin[0], gN = gfin[G - 1];
-        K->flux_in[0] = g0 < 0.0 ? -g0 : 0.0;
-        K->flux_in[1] = gN > 0.0 ? gN : 0.0;
+        if (kin) {  // the ions removed at each wall this step
+            const InstDev *I = K->ion;
+            const unsigned long long l0 = I->ctr[C_LOSS0], l1 = I->ctr[C_LOSS1];
+            K->flux_in[0] = (double)(l0 - K->ion_loss_prev[0]) * w / dt;
+            K->flux_in[1] = (double)(l1 - K->ion_loss_prev[1]) * w / dt;
+            K->ion_loss_prev[0] = l0;
+            K->ion_loss_prev[1] = l1;
+        } else {
+            const double g0 = gfin[0], gN = gfin[G - 1];
+            K->flux_in[0] = g0 < 0.0 ? -g0 : 0.0;
+            K->flux_in[1] = gN > 0.0 ? gN : 0.0;
+        }
         K->step += 1;
         const uint32_t n = (uint32_t)K->step;
         s_cnt[0] = s_cnt[1] = 0;

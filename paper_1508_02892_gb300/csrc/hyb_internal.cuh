@@ -85,6 +85,14 @@ struct InstDev {
     float *nif;                       // [G] n_i / max n_i, written by the field kernel (split mode)
     double rec_numax, rec_pmax;       // max n_i * rec_svmax and 1 - exp(-rec_numax dt), for the next step
     float f_rec_pmax, pad2;
+    // kinetic ions (HYB_ION_KINETIC): the ion population lives in a second
+    // descriptor of this layout (FP64 particles, its own sort buffers and
+    // counters) that points back to the electron one
+    InstDev *ion;                     // electron descriptor: its ions (NULL: fluid ions)
+    InstDev *elec;                    // ion descriptor: its electrons
+    double *dep_ni, *dep_gi;          // per-step CIC sums of the ions: count and v_z
+    double mi_red, nu_max_i, p_max_i, vt_gas;
+    unsigned long long ion_loss_prev[2];
 };
 
 enum { C_BIRTH_IZ = 0, C_SEE0, C_SEE1, C_LOSS0, C_LOSS1, C_EL, C_EXC, C_IZ, C_NULL, C_CLAMP, C_PUSH, C_REC };
@@ -229,7 +237,14 @@ struct LaunchCfg {
 // electron kernels (hyb_electron.cu)
 cudaError_t launch_electron_step(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
                                  cudaStream_t s,
-                                 bool rec = false);
+                                 bool rec = false, bool kin = false);
+// kinetic ions: initial load, the per-step snapshot prefix over a lane's ion
+// descriptors, and the ion step (mode 0) or deposit alone (mode 1)
+cudaError_t launch_load_ions(InstDev *ion, int64_t n, cudaStream_t s);
+double swarm_nu_bound(double ngas, double m_red, double eps_max);
+cudaError_t launch_ion_prefix(InstDev *ions, int n_max, int64_t *prefix, cudaStream_t s);
+cudaError_t launch_ion_step(InstDev *ions, int n_max, const int64_t *prefix, int mode, int grid, int max_nodes,
+                            cudaStream_t s);
 cudaError_t launch_deposit_init(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
                                 cudaStream_t s);
 cudaError_t launch_load(InstDev *inst, int64_t n, double vth, int precision, cudaStream_t s);

@@ -232,6 +232,9 @@ int swarm_fail(int code, const char *msg)
 
 }  // namespace
 
+// the same bound for the kinetic ions of a discharge (Q_m = Q_i + 2 Q_b)
+double swarm_nu_bound(double ngas, double m_red, double eps_max) { return nu_bound(ngas, m_red, HYB_SWARM_QM, eps_max); }
+
 }  // namespace hyb
 
 using namespace hyb;

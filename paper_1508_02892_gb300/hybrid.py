@@ -60,7 +60,8 @@ class Counters(C.Structure):
     _fields_ = [("step", C.c_int64), ("particles", C.c_int64), ("births_ionization", C.c_int64),
                 ("births_see", C.c_int64 * 2), ("losses", C.c_int64 * 2), ("collisions", C.c_int64 * 4),
                 ("clamps", C.c_int64), ("pushes", C.c_int64), ("status", C.c_uint32), ("v_rf_amp_v", C.c_double),
-                ("power_last_w_m2", C.c_double), ("power_periods", C.c_int64), ("recombinations", C.c_int64)]
+                ("power_last_w_m2", C.c_double), ("power_periods", C.c_int64), ("recombinations", C.c_int64),
+                ("ions", C.c_int64), ("ion_losses", C.c_int64 * 2), ("ion_collisions", C.c_int64)]
 
 
 class Info(C.Structure):
@@ -109,6 +110,10 @@ EXPORTS = {
                                      C.POINTER(C.c_int64)]),
     "hyb_write_particles": (C.c_int, [C.c_void_p, C.c_int64, _pd, _pd, _pd, _pd, C.POINTER(C.c_uint64)]),
     "hyb_write_ion_density": (C.c_int, [C.c_void_p, _pd]),
+    "hyb_read_ions": (C.c_int, [C.c_void_p, _pd, _pd, _pd, _pd, C.POINTER(C.c_uint64), C.c_int64,
+                                C.POINTER(C.c_int64)]),
+    "hyb_batch_read_ions": (C.c_int, [C.c_void_p, C.c_int32, _pd, _pd, _pd, _pd, C.POINTER(C.c_uint64), C.c_int64,
+                                      C.POINTER(C.c_int64)]),
     "hyb_destroy": (C.c_int, [C.c_void_p]),
     "hyb_batch_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.POINTER(C.c_void_p)]),
     "hyb_footprint": (C.c_int, [C.POINTER(Params), C.POINTER(C.c_int64)]),
@@ -226,7 +231,8 @@ def _counters(call):
             "losses1": c.losses[1], "elastic": c.collisions[0], "excitation": c.collisions[1],
             "ionization": c.collisions[2], "null": c.collisions[3], "clamps": c.clamps, "pushes": c.pushes,
             "status": c.status, "v_rf": c.v_rf_amp_v, "power_last": c.power_last_w_m2,
-            "power_periods": c.power_periods, "recombinations": c.recombinations}
+            "power_periods": c.power_periods, "recombinations": c.recombinations, "ions": c.ions,
+            "ion_losses0": c.ion_losses[0], "ion_losses1": c.ion_losses[1], "ion_collisions": c.ion_collisions}
 
 
 def _particles(call, cap):
@@ -294,6 +300,11 @@ class Discharge:
     def particles(self, cap=None):
         cap = int(cap or self.info["capacity"])
         return _particles(lambda *a: lib().hyb_read_particles(self.h, *a), cap)
+
+    def ions(self, cap=None):
+        """Kinetic ions (sorted by id)."""
+        cap = int(cap or self.info["capacity"])
+        return _particles(lambda *a: lib().hyb_read_ions(self.h, *a), cap)
 
     def set_particles(self, z, vx, vy, vz, ids):
         z, vx, vy, vz = (_arr(a) for a in (z, vx, vy, vz))
@@ -372,6 +383,10 @@ class Batch:
     def particles(self, slot, cap=None):
         cap = int(cap or self._shape[slot][2])
         return _particles(lambda *a: lib().hyb_batch_read_particles(self.h, int(slot), *a), cap)
+
+    def ions(self, slot, cap=None):
+        cap = int(cap or self._shape[slot][2])
+        return _particles(lambda *a: lib().hyb_batch_read_ions(self.h, int(slot), *a), cap)
 
     def evict(self, slot):
         _check(lib().hyb_batch_evict(self.h, int(slot)))
