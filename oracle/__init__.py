@@ -32,7 +32,8 @@ OUT_NONE, OUT_ELASTIC, OUT_EXC, OUT_ION, OUT_NULL, OUT_LOST0, OUT_LOST1 = range(
 FLAG_THERMAL_GAS = 2
 
 COUNTER_NAMES = ("step", "particles", "births_iz", "births_see0", "births_see1", "losses0",
-                 "losses1", "elastic", "excitation", "ionization", "null", "clamps", "status", "recombinations")
+                 "losses1", "elastic", "excitation", "ionization", "null", "clamps", "status", "recombinations",
+                 "births_penning", "births_pooling")
 
 
 def build(force: bool = False) -> str:
@@ -66,7 +67,10 @@ class OrcParams(C.Structure):
         ("n_xs", C.c_int32), ("e_exc_ev", C.c_double), ("e_iz_ev", C.c_double),
         ("seed", C.c_uint64), ("eedf_bins", C.c_int32), ("eedf_max_ev", C.c_double),
         ("flags", C.c_int32), ("power_w_m2", C.c_double), ("power_alpha", C.c_double),
-        ("xs_rec", C.POINTER(C.c_double)),
+        ("xs_rec", C.POINTER(C.c_double)), ("metastables", C.c_int32), ("met_diff_m2s", C.c_double),
+        ("met_n0_m3", C.c_double), ("penning_rate_m3s", C.c_double), ("penning_target_m3", C.c_double),
+        ("penning_energy_ev", C.c_double), ("pooling_rate_m3s", C.c_double), ("pooling_energy_ev", C.c_double),
+        ("gamma_met", C.c_double),
     ]
 
 
@@ -131,6 +135,8 @@ def lib():
                 "orc_swarm_run": (None, [C.POINTER(OrcSwarmParams), C.POINTER(OrcSwarmResult), pd]),
                 "orc_get_power": (None, [vp, pd, pi64]),
                 "orc_get_ion_counters": (None, [vp, pi64]),
+                "orc_get_metastables": (None, [vp, pd, pd, pd]),
+                "orc_set_metastables": (None, [vp, pd]),
                 "orc_get_ions": (None, [vp, pd, pd, pd, pd, pu64]),
                 "orc_swarm_nu": (dbl, [dbl, dbl, C.c_int, dbl]),
                 "orc_swarm_nu_bound": (dbl, [dbl, dbl, C.c_int, dbl]),
@@ -336,6 +342,18 @@ class Oracle:
         flux = np.zeros(2)
         clamps = lib().orc_fluid_update(self.h, _dp(E), _dp(gsrc), _dp(ni), _dp(gam), _dp(flux))
         return ni, gam, flux, int(clamps)
+
+    def metastables(self):
+        """Metastable density now, its time average, and the flux into each
+        wall in the last step."""
+        met, avg, flux = np.zeros(self.G), np.zeros(self.G), np.zeros(2)
+        lib().orc_get_metastables(self.h, _dp(met), _dp(avg), _dp(flux))
+        return {"met": met, "avg": avg, "flux": flux}
+
+    def set_metastables(self, met):
+        v = np.ascontiguousarray(met, dtype=np.float64)
+        assert v.size == self.G
+        lib().orc_set_metastables(self.h, _dp(v))
 
     def ion_counters(self):
         """Kinetic ions: number, losses at z = 0 and z = L, collision candidates,

@@ -78,6 +78,15 @@ typedef struct orc_params {
     double power_w_m2;      /* prescribed absorbed power P0 per m^2 (Eq. 2.9); 0: fixed amplitude */
     double power_alpha;     /* the relaxation parameter alpha of Eq. 2.9 */
     const double *xs_rec;   /* electron-ion recombination cross section at xs_ev (NULL: none) */
+    int32_t metastables;    /* 1: a metastable density fed by the excitation events (Sec. II.D) */
+    double met_diff_m2s;    /* diffusion coefficient of the metastables */
+    double met_n0_m3;       /* initial metastable density at the interior nodes */
+    double penning_rate_m3s;  /* R of Penning ionization of the admixture by the metastables */
+    double penning_target_m3; /* n_N, density of the admixture the metastables ionize */
+    double penning_energy_ev; /* energy of a Penning electron, E_* - E_I */
+    double pooling_rate_m3s;  /* R of metastable pooling (two metastables -> ion + electron) */
+    double pooling_energy_ev; /* energy of a pooling electron */
+    double gamma_met;       /* secondary-electron yield of metastables at the electrodes */
 } orc_params;
 
 typedef struct part {
@@ -120,6 +129,10 @@ typedef struct orc_sim {
     double *dep_ni, *dep_gi;
     double mi_red, nu_max_i, p_max_i, vt_gas;
     int64_t ion_losses[2], ion_coll, ion_cand;
+    /* metastables and their reactions (Sec. II.D) */
+    double *met, *s_met, *acc_met;
+    double flux_met[2];     /* metastables reaching each wall per m^2 and s in the last step */
+    int64_t births_pen, births_pool;
 } orc_sim;
 
 double orc_swarm_nu(double ngas, double m_red, int xs_model, double g);
@@ -670,15 +683,16 @@ static void deposit_one(orc_sim *s, const part *q, int sample)
     s->eedf[b] += 1.0;
 }
 
-/* gamma secondaries (Sec. II.D): per wall, gamma Gamma_i S dt / N_p/sp
- * superparticles, integer part plus one more with the probability of the
- * fractional part.  Born with energy see_energy_ev, Lambertian direction,
+/* gamma secondaries (Sec. II.D): per wall, (gamma_i Gamma_i + gamma_* Gamma_*)
+ * S dt / N_p/sp superparticles (ions and metastables striking the wall), integer
+ * part plus one more with the probability of the fractional part.  Born with energy see_energy_ev, Lambertian direction,
  * a random fraction of one push inside the wall. */
 static void emit_secondaries(orc_sim *s, uint32_t n)
 {
-    if (s->p.gamma_see <= 0.0 || s->w <= 0.0) return;
+    if ((s->p.gamma_see <= 0.0 && s->p.gamma_met <= 0.0) || s->w <= 0.0) return;
     for (int wall = 0; wall < 2; ++wall) {
-        double ns = s->p.gamma_see * s->flux_in[wall] * s->dt / s->w;
+        /* heavy particles of both kinds (ions, metastables) hitting the wall */
+        double ns = (s->p.gamma_see * s->flux_in[wall] + s->p.gamma_met * s->flux_met[wall]) * s->dt / s->w;
         if (!(ns > 0.0)) continue;
         double k = floor(ns);
         double frac = ns - k;
@@ -880,6 +894,95 @@ static void ion_step(orc_sim *s, uint32_t n, const double *kz, const uint64_t *k
     ion_grids(s);
 }
 
+/* Metastables and the ionization they cause (Sec. II.D).  Every excitation
+ * event of the step adds N_p/sp/dV to the metastable density n_m (CIC at the
+ * electron); here, from the density n_m^n at the start of the step:
+ *  - Penning ionization of the admixture, Delta N_e = R_P n_m n_N dt dV, and
+ *    metastable pooling, Delta N_e = R_pool n_m^2 dt dV, per interior node j
+ *    (dV = dz S): Delta N_e / N_p/sp superparticles, the integer part plus one
+ *    with the probability of the fraction (the Bernoulli draw keyed by the
+ *    process and j, call 3); each new electron is placed uniformly in the
+ *    node's cell [z_j - dz/2, z_j + dz/2) with the process's energy and an
+ *    isotropic direction (call 2 of its own id), and its ion enters the ion
+ *    source (CIC) as an ionization's would;
+ *  - then the explicit update of the metastable density,
+ *    n_m^{n+1} = n_m + dt [D d2n_m/dz2 + S_m - R_P n_N n_m - 2 R_pool n_m^2]
+ *    at the interior nodes, n_m = 0 at the electrodes (absorbing walls); the
+ *    flux into a wall is D n_m(next node)/dz plus what the excitation events
+ *    put on the wall node, and it drives gamma emission with gamma_m.
+ * Ids of the new electrons: bit 62 set, process 2 (Penning) or 3 (pooling) in
+ * bits 60-61, the step in bits 20-51, the running index k in bits 0-19. */
+static void metastable_step(orc_sim *s, uint32_t n)
+{
+    const int G = s->G;
+    const double dz = s->dz, dt = s->dt, w = s->w;
+    const double rate[2] = {s->p.penning_rate_m3s, s->p.pooling_rate_m3s};
+    const double energy[2] = {s->p.penning_energy_ev, s->p.pooling_energy_ev};
+    for (int proc = 0; proc < 2; ++proc) {
+        if (!(rate[proc] > 0.0) || !(w > 0.0)) continue;
+        const double sp = sqrt(2.0 * Q_E * energy[proc] / M_E);
+        int64_t k = 0;
+        for (int j = 1; j <= G - 2; ++j) {
+            const double nm = s->met[j];
+            const double dn = proc == 0 ? rate[0] * nm * s->p.penning_target_m3 * dt * dz
+                                        : rate[1] * nm * nm * dt * dz;
+            const double m = dn / w;
+            if (!(m > 0.0)) continue;
+            const double fl = floor(m);
+            double u[4];
+            draws(s, 0xFFFFFFFF00000000ull | ((uint64_t)(proc + 1) << 24) | (uint64_t)j, n, 3, u);
+            int64_t cnt = (int64_t)fl + (u[0] < m - fl ? 1 : 0);
+            for (int64_t b = 0; b < cnt; ++b) {
+                if (k >= (1 << 20) - 1) {
+                    s->status |= 8;
+                    break;
+                }
+                part q;
+                q.id = (1ull << 62) | ((uint64_t)(2 + proc) << 60) | ((uint64_t)n << 20) | (uint64_t)k;
+                double v[4];
+                draws(s, q.id, n, 2, v);
+                q.z = ((double)j - 0.5 + v[0]) * dz;
+                double ct = 1.0 - 2.0 * v[1];
+                double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+                double ph = TWO_PI * v[2];
+                q.vx = sp * st * cos(ph);
+                q.vy = sp * st * sin(ph);
+                q.vz = sp * ct;
+                push_particle(s, &q);
+                int c;
+                double o;
+                locate(s, q.z, &c, &o);
+                s->s_iz[c] += 1.0 - o;
+                s->s_iz[c + 1] += o;
+                if (proc == 0)
+                    s->births_pen++;
+                else
+                    s->births_pool++;
+                ++k;
+            }
+        }
+    }
+    double *old = (double *)malloc(sizeof(double) * G);
+    memcpy(old, s->met, sizeof(double) * G);
+    const double D = s->p.met_diff_m2s;
+    const double kp = s->p.penning_rate_m3s * s->p.penning_target_m3, kq = s->p.pooling_rate_m3s;
+    for (int j = 1; j <= G - 2; ++j) {
+        const double src = w * s->s_met[j] / (dz * dt);
+        const double lap = D * (old[j + 1] - 2.0 * old[j] + old[j - 1]) / (dz * dz);
+        const double loss = kp * old[j] + 2.0 * kq * old[j] * old[j];
+        double nn = old[j] + dt * (lap + src - loss);
+        if (nn < 0.0) {
+            nn = 0.0;
+            s->n_clamp++;
+        }
+        s->met[j] = nn;
+    }
+    s->met[0] = s->met[G - 1] = 0.0;
+    s->flux_met[0] = D * old[1] / dz + w * s->s_met[0] / dt;
+    s->flux_met[1] = D * old[G - 2] / dz + w * s->s_met[G - 1] / dt;
+    free(old);
+}
+
 /* One full step n -> n+1 (Secs. II.A and II.D), ending with the gamma
  * secondaries that will take part in step n+1. */
 static void step_once(orc_sim *s)
@@ -892,6 +995,7 @@ static void step_once(orc_sim *s)
     memset(s->dep_n, 0, sizeof(double) * G);
     memset(s->dep_e, 0, sizeof(double) * G);
     memset(s->s_iz, 0, sizeof(double) * G);
+    if (s->met) memset(s->s_met, 0, sizeof(double) * G);
     int64_t n0 = s->np;
     /* electron-ion recombination (Sec. II.D): a null-collision procedure of its
      * own on the non-uniform ion density, nu_rec,max = max_z n_i * max sigma v */
@@ -918,7 +1022,16 @@ static void step_once(orc_sim *s)
         part ch;
         int oc = mcc_one(s, n, &q, &ch);
         if (oc == OUT_ELASTIC) s->coll[0]++;
-        if (oc == OUT_EXC) s->coll[1]++;
+        if (oc == OUT_EXC) {
+            s->coll[1]++;
+            if (s->met) {  /* a metastable at the electron's position */
+                int c;
+                double o;
+                locate(s, q.z, &c, &o);
+                s->s_met[c] += 1.0 - o;
+                s->s_met[c + 1] += o;
+            }
+        }
         if (oc == OUT_NULL) s->coll[3]++;
         if (oc == OUT_ION) {
             s->coll[2]++;
@@ -946,6 +1059,7 @@ static void step_once(orc_sim *s)
     }
     free(kids);
 
+    if (s->met) metastable_step(s, n);
     /* coupling: ion source, fluid ions, Poisson */
     for (int j = 0; j < G; ++j) s->gsrc[j] = s->w * s->s_iz[j] / (node_volume(s, j) * s->dt);
     if (s->p.ion_model == ION_KINETIC)
@@ -960,6 +1074,7 @@ static void step_once(orc_sim *s)
         s->acc_gi[j] += s->gam[j];
         s->acc_wn[j] += s->dep_n[j];
         s->acc_we[j] += s->dep_e[j];
+        if (s->met) s->acc_met[j] += s->met[j];
     }
     free(kids_z);
     free(kids_id);
@@ -1033,6 +1148,10 @@ static void load_ions(orc_sim *s)
 orc_sim *orc_create(const orc_params *p)
 {
     if (p->n_cells < 2 || p->n_xs < 2 || p->gap_m <= 0 || p->dt_s <= 0) return NULL;
+    /* metastables: explicit diffusion stable (D dt/dz^2 <= 1/2), fluid ions only */
+    if (p->metastables && (p->ion_model == ION_KINETIC || p->met_diff_m2s < 0 ||
+                           p->met_diff_m2s * p->dt_s * p->n_cells * p->n_cells > 0.5 * p->gap_m * p->gap_m))
+        return NULL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     s->p = *p;
     s->xs_ev = dup(p->xs_ev, p->n_xs);
@@ -1110,6 +1229,12 @@ orc_sim *orc_create(const orc_params *p)
     s->acc_we = (double *)calloc(G, sizeof(double));
     s->eedf = (double *)calloc(s->p.eedf_bins + 1, sizeof(double));
     for (int j = 0; j < G; ++j) s->ni[j] = p->n0_m3;
+    if (p->metastables) {
+        s->met = (double *)calloc(G, sizeof(double));
+        s->s_met = (double *)calloc(G, sizeof(double));
+        s->acc_met = (double *)calloc(G, sizeof(double));
+        for (int j = 1; j <= G - 2; ++j) s->met[j] = p->met_n0_m3;
+    }
 
     if (p->ion_model == ION_KINETIC) {
         s->dep_ni = (double *)calloc(G, sizeof(double));
@@ -1131,7 +1256,7 @@ void orc_destroy(orc_sim *s)
     double *bufs[] = {s->tab_eon, s->tab_mu, s->tab_nu, s->tab_u, s->xs_ev, s->xs_el, s->xs_exc, s->xs_ion, s->xs_rec,
                       s->dep_ni, s->dep_gi,
                       s->ni, s->gam, s->phi, s->E, s->ne, s->dep_n, s->dep_e, s->s_iz, s->gsrc,
-                      s->acc_ne, s->acc_ni, s->acc_gi, s->acc_wn, s->acc_we, s->eedf};
+                      s->acc_ne, s->acc_ni, s->acc_gi, s->acc_wn, s->acc_we, s->eedf, s->met, s->s_met, s->acc_met};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) free(bufs[i]);
     free(s->pp);
     free(s->ip);
@@ -1212,8 +1337,9 @@ void orc_get_eedf_counts(const orc_sim *s, double *out)
 }
 
 /* counters: step, particles, births_iz, births_see0, births_see1, losses0,
- * losses1, elastic, excitation, ionization, null, clamps, status */
-void orc_get_counters(const orc_sim *s, int64_t out[14])
+ * losses1, elastic, excitation, ionization, null, clamps, status,
+ * recombinations, Penning births, pooling births */
+void orc_get_counters(const orc_sim *s, int64_t out[16])
 {
     out[0] = s->step;
     out[1] = s->np;
@@ -1229,6 +1355,25 @@ void orc_get_counters(const orc_sim *s, int64_t out[14])
     out[11] = s->n_clamp;
     out[12] = s->status;
     out[13] = s->recomb;
+    out[14] = s->births_pen;
+    out[15] = s->births_pool;
+}
+
+/* metastables: the density now, its time average, and the wall fluxes of the
+ * last step */
+void orc_get_metastables(const orc_sim *s, double *met, double *avg, double flux[2])
+{
+    for (int j = 0; j < s->G; ++j) {
+        met[j] = s->met ? s->met[j] : 0.0;
+        avg[j] = (s->met && s->n_samples) ? s->acc_met[j] / s->n_samples : 0.0;
+    }
+    flux[0] = s->flux_met[0];
+    flux[1] = s->flux_met[1];
+}
+
+void orc_set_metastables(orc_sim *s, const double *met)
+{
+    if (s->met) memcpy(s->met, met, sizeof(double) * s->G);
 }
 
 void orc_get_flux_in(const orc_sim *s, double out[2])

@@ -95,13 +95,28 @@ def base_params(**kw) -> dict:
              n0_m3=1e16, te0_ev=2.0, weight=0.0, gamma_see=0.0, see_energy_ev=1.0,
              ion_model=ION_DD_CONST, ion_mass_amu=0.0, gas_mass_amu=0.0, mu_const=1.0e-3,
              seed=1, eedf_bins=256, eedf_max_ev=64.0, flags=0, precision=FP64,
-             capacity_factor=2.0, sort_interval=0, power_w_m2=0.0, power_alpha=0.0)
+             capacity_factor=2.0, sort_interval=0, power_w_m2=0.0, power_alpha=0.0, metastables=0,
+             met_diff_m2s=0.0, met_n0_m3=0.0, penning_rate_m3s=0.0, penning_target_m3=0.0, penning_energy_ev=0.0,
+             pooling_rate_m3s=0.0, pooling_energy_ev=0.0, gamma_met=0.0)
     p.update(kw)
     gas = p["gas"]
     kind = "he" if gas == GAS_HE else "heavy"
     # the stand-in tables, unless the caller gave tables of its own
     for k, v in {**xs_tables(gas), **ion_tables(kind, p["pressure_pa"], p["gas_temp_k"])}.items():
         p.setdefault(k, v)
+    return p
+
+
+def metastable_params(**kw) -> dict:
+    """He metastables with a N2 admixture (Sec. II.D reactions), stand-in values
+    of the usual order of magnitude: D p = 470 cm^2 Torr/s at 1 atm, Penning
+    ionization of N2 at 7e-17 m^3/s by a 10 ppm admixture, pooling at 1.5e-15
+    m^3/s; electron energies E_exc - E_I(N2) and 2 E_exc - E_iz with Table 1's
+    19.8 and 24.6 eV."""
+    p = dict(metastables=1, met_diff_m2s=6.2e-5, met_n0_m3=0.0, penning_rate_m3s=7e-17,
+             penning_target_m3=1e-5 * ATM / (1.380649e-23 * 300.0), penning_energy_ev=19.8 - 15.58,
+             pooling_rate_m3s=1.5e-15, pooling_energy_ev=2 * 19.8 - 24.6, gamma_met=0.0)
+    p.update(kw)
     return p
 
 
