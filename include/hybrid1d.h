@@ -111,6 +111,26 @@ typedef struct hyb_params {
                                    xs_ev: a null-collision process of its own on the ion density
                                    (Sec. II.D); a recombined electron is removed and its ion leaves
                                    n_i through the source term of Eq. 2.4 */
+    /* Metastables and the ionization they cause (Sec. II.D).  With metastables = 1
+     * every excitation event adds N_p/sp/dV to a metastable density n_m (CIC at
+     * the electron).  Per step, from n_m at the start of the step, each interior
+     * node j yields Delta N_e / N_p/sp new electrons (integer part plus a
+     * Bernoulli draw on the fraction), with Delta N_e = R_P n_m n_N dt dz for
+     * Penning ionization and R_pool n_m^2 dt dz for pooling.  They are placed
+     * uniformly in [z_j - dz/2, z_j + dz/2), isotropic, at the process's
+     * energy, and their ions enter the ion source.  Then
+     *   n_m <- n_m + dt (D n_m'' + S_m - R_P n_N n_m - 2 R_pool n_m^2),
+     * with n_m = 0 at the electrodes.  The metastables reaching the walls emit
+     * secondaries with gamma_met.  Fluid ion models only; D dt/dz^2 <= 1/2. */
+    int32_t metastables;        /* 0: off, 1: on */
+    double met_diff_m2s;        /* D of the metastables, m^2/s */
+    double met_n0_m3;           /* initial n_m at the interior nodes */
+    double penning_rate_m3s;    /* R_P, Penning ionization of the admixture */
+    double penning_target_m3;   /* n_N, density of the admixture */
+    double penning_energy_ev;   /* energy of a Penning electron (E_* - E_I) */
+    double pooling_rate_m3s;    /* R_pool, two metastables -> ion + electron */
+    double pooling_energy_ev;   /* energy of a pooling electron */
+    double gamma_met;           /* secondary yield of a metastable striking an electrode */
 } hyb_params;
 
 /* Time averages since creation or the last hyb_reset_moments (Sec. III
@@ -154,6 +174,8 @@ typedef struct hyb_counters {
     int64_t ions;               /* kinetic ions: live ion macroparticles (0 for the fluid models) */
     int64_t ion_losses[2];      /* kinetic ions removed at z = 0 and z = L */
     int64_t ion_collisions;     /* real ion-neutral collisions of the kinetic ions */
+    int64_t births_penning;     /* electrons born by Penning ionization */
+    int64_t births_pooling;     /* electrons born by metastable pooling */
 } hyb_counters;
 
 #define HYB_STATUS_CAPACITY 1u
@@ -213,6 +235,17 @@ int hyb_write_particles(hyb_discharge *h, int64_t n, const double *z, const doub
 int hyb_read_ions(hyb_discharge *h, double *z, double *vx, double *vy, double *vz, uint64_t *id, int64_t cap,
                   int64_t *n);
 
+/* Metastables (metastables = 1): host buffers of n_nodes values for the density
+ * after the last step and its time average (either may be NULL), and flux[2],
+ * the metastables that reached z = 0 and z = L per m^2 and s in the last step
+ * (may be NULL).  HYB_ERR_STATE without metastables. */
+int hyb_read_metastables(hyb_discharge *h, double *met, double *avg, double *flux);
+
+/* Overwrite the metastable density (host, n_nodes values; the electrode nodes
+ * must be 0).  HYB_ERR_STATE without metastables, HYB_ERR_ARG for negative or
+ * non-finite values or a non-zero electrode node. */
+int hyb_write_metastables(hyb_discharge *h, const double *met);
+
 /* Overwrite the ion density (host, n_nodes values) and re-solve the field
  * (fluid ion models; HYB_ERR_STATE for kinetic ions). */
 int hyb_write_ion_density(hyb_discharge *h, const double *ni);
@@ -249,6 +282,7 @@ int hyb_batch_read_counters(hyb_batch *b, int32_t slot, hyb_counters *out);
 int hyb_batch_read_particles(hyb_batch *b, int32_t slot, double *z, double *vx, double *vy, double *vz,
                              uint64_t *id, int64_t cap, int64_t *n);
 
+int hyb_batch_read_metastables(hyb_batch *b, int32_t slot, double *met, double *avg, double *flux);
 int hyb_batch_read_ions(hyb_batch *b, int32_t slot, double *z, double *vx, double *vy, double *vz, uint64_t *id,
                         int64_t cap, int64_t *n);
 

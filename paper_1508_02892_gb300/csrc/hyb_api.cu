@@ -142,6 +142,19 @@ int validate(const hyb_params *p)
         for (int i = 0; i < p->n_xs; ++i)
             if (p->xs_rec[i] < 0) return fail(HYB_ERR_ARG, "negative recombination cross section");
     }
+    if (p->metastables != 0 && p->metastables != 1) return fail(HYB_ERR_ARG, "metastables must be 0 or 1");
+    if (!(p->gamma_met >= 0) || !isfinite(p->gamma_met)) return fail(HYB_ERR_ARG, "gamma_met must be finite and >= 0");
+    if (p->metastables) {
+        if (p->ion_model == HYB_ION_KINETIC)
+            return fail(HYB_ERR_ARG, "metastables are built for the fluid ion models only");
+        const double v[7] = {p->met_diff_m2s,      p->met_n0_m3,        p->penning_rate_m3s, p->penning_target_m3,
+                             p->penning_energy_ev, p->pooling_rate_m3s, p->pooling_energy_ev};
+        for (double x : v)
+            if (!(x >= 0) || !isfinite(x)) return fail(HYB_ERR_ARG, "metastable parameters must be finite and >= 0");
+        // explicit diffusion: D dt / dz^2 <= 1/2
+        if (p->met_diff_m2s * p->dt_s * p->n_cells * p->n_cells > 0.5 * p->gap_m * p->gap_m)
+            return fail(HYB_ERR_UNSTABLE, "metastable diffusion: D dt/dz^2 > 1/2");
+    }
     return HYB_OK;
 }
 
@@ -184,6 +197,11 @@ Layout layout_of(const hyb_params &p)
     add(8 * (size_t)p.n_xs);                            // xs_rec
     add(4 * (size_t)p.n_xs);                            // xs_recf
     add(4 * (size_t)G);                                 // nif
+    if (p.metastables) {
+        add(8 * (size_t)G);                             // met
+        add(8 * (size_t)G);                             // s_met
+        add(8 * (size_t)G);                             // acc_met
+    }
     if (p.ion_model == HYB_ION_KINETIC) {
         for (int b = 0; b < 2; ++b)
             for (int k = 0; k < 5; ++k) add(8 * cap);   // ion z, vx, vy, vz, id
@@ -320,6 +338,16 @@ void derive(const hyb_params &p, InstDev &K, std::vector<double> &xs, std::vecto
             const double v = sqrt(2.0 * kQe * p.xs_ev[i + 1] / kMe);
             if (sg * v > K.rec_svmax) K.rec_svmax = sg * v;
         }
+    // metastables and their reactions (Sec. II.D)
+    K.met_on = p.metastables ? 1 : 0;
+    K.met_D = p.met_diff_m2s;
+    K.met_rp = p.penning_rate_m3s;
+    K.met_nn = p.penning_target_m3;
+    K.met_kp = p.penning_rate_m3s * p.penning_target_m3;
+    K.met_kq = p.pooling_rate_m3s;
+    K.met_sp[0] = sqrt(2.0 * kQe * p.penning_energy_ev / kMe);
+    K.met_sp[1] = sqrt(2.0 * kQe * p.pooling_energy_ev / kMe);
+    K.gamma_met = p.gamma_met;
     const int nt = K.n_tab > 0 ? K.n_tab : 1;
     tab.assign(4 * (size_t)nt, 0.0);
     for (int k = 0; k < K.n_tab; ++k) {
@@ -362,6 +390,11 @@ void bind_pointers(const hyb_params &p, const Layout &L, char *base, InstDev &K,
     K.xs_rec = (const double *)(base + L.off[k++]);
     K.xs_recf = (const float *)(base + L.off[k++]);
     K.nif = (float *)(base + L.off[k++]);
+    if (p.metastables) {
+        K.met = (double *)(base + L.off[k++]);
+        K.s_met = (double *)(base + L.off[k++]);
+        K.acc_met = (double *)(base + L.off[k++]);
+    }
     if (p.ion_model == HYB_ION_KINETIC) {
         // the ion descriptor starts as a copy of this one; here the ion buffers
         // go to I (its fields buf and cell_cnt), the shared sums to K
@@ -404,7 +437,7 @@ struct hyb_batch {
     cudaEvent_t ev_fork = nullptr, ev_join[kMaxLanes] = {};
     int blocks_per_sm = 0;                 // electron grid = SMs x this (0: occupancy limit)
     int field_threads = 256;               // threads of an instance's field block
-    bool any_rec = false;                  // some admitted discharge has recombination
+    bool any_chem = false;                 // some admitted discharge has recombination or metastables
     bool any_kin = false;                  // some admitted discharge has kinetic ions
     InstDev *d_inst_ion = nullptr;         // ion descriptors, slot for slot (zero: none)
     int64_t *d_prefix_ion = nullptr;       // kMaxLanes x (max_inst + 1)
@@ -437,7 +470,7 @@ namespace {
 
 int64_t live_count(const InstDev &K)
 {
-    return K.n_base + (int64_t)(K.ctr[C_BIRTH_IZ] + K.ctr[C_SEE0] + K.ctr[C_SEE1]) -
+    return K.n_base + (int64_t)(K.ctr[C_BIRTH_IZ] + K.ctr[C_SEE0] + K.ctr[C_SEE1] + K.ctr[C_PEN] + K.ctr[C_POOL]) -
            (int64_t)(K.ctr[C_LOSS0] + K.ctr[C_LOSS1] + K.ctr[C_REC]);
 }
 
@@ -551,7 +584,7 @@ int launch_step(hyb_batch *b, int k, int lane, cudaStream_t s)
     int rc;
     const int n = lane_count(b, lane);
     if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k)))) return rc;
-    CK(launch_electron_step(lane_inst(b, lane), n, lane_prefix(b, lane), b->precision, b->cfg, s, b->any_rec,
+    CK(launch_electron_step(lane_inst(b, lane), n, lane_prefix(b, lane), b->precision, b->cfg, s, b->any_chem,
                             b->any_kin));
     if (b->any_kin) {  // the ions of the step, after the electrons' births
         CK(launch_ion_prefix(lane_inst_ion(b, lane), n, lane_prefix_ion(b, lane), s));
@@ -785,6 +818,9 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
         }
     CK(cudaMemcpyAsync((void *)S.h.xs_rec, xr.data(), 8 * xr.size(), cudaMemcpyHostToDevice, b->stream));
     CK(cudaMemcpyAsync((void *)S.h.xs_recf, xrf.data(), 4 * xrf.size(), cudaMemcpyHostToDevice, b->stream));
+    std::vector<double> met0(G, p->met_n0_m3);  // metastables: n0 inside, 0 at the electrodes
+    met0[0] = met0[G - 1] = 0.0;
+    if (p->metastables) CK(cudaMemcpyAsync(S.h.met, met0.data(), 8 * (size_t)G, cudaMemcpyHostToDevice, b->stream));
     S.h.active = 0;
     S.h.cur = 0;
     S.h.step = 0;
@@ -832,8 +868,9 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     S.p = *p;
     S.p.tab_eon_td = S.p.tab_mu = S.p.tab_nu = nullptr;
     S.p.xs_ev = S.p.xs_el = S.p.xs_exc = S.p.xs_ion = S.p.xs_rec = nullptr;
-    if (S.h.rec_on && !b->any_rec) {  // the electron step switches to its recombination variant
-        b->any_rec = true;
+    if ((S.h.rec_on || S.h.met_on) && !b->any_chem) {
+        // the electron step switches to its variant with recombination and the metastable source
+        b->any_chem = true;
         rc = drop_graph(b);
         if (rc) return rc;
     }
@@ -1105,6 +1142,8 @@ int read_counters(hyb_batch *b, int slot, hyb_counters *c)
     c->power_last_w_m2 = K.pw_last;
     c->power_periods = K.pw_periods;
     c->recombinations = (int64_t)K.ctr[C_REC];
+    c->births_penning = (int64_t)K.ctr[C_PEN];
+    c->births_pooling = (int64_t)K.ctr[C_POOL];
     c->ions = c->ion_losses[0] = c->ion_losses[1] = c->ion_collisions = 0;
     if (b->slots[slot].h.ion) {
         InstDev I{};
@@ -1207,6 +1246,27 @@ int read_ions(hyb_batch *b, int slot, double *z, double *vx, double *vy, double 
         if (vy) vy[k] = hy[i];
         if (vz) vz[k] = hv[i];
         if (id) id[k] = hid[i];
+    }
+    return rc;
+}
+
+// the metastable density, its time average and the last wall fluxes of a slot
+int read_metastables(hyb_batch *b, int slot, double *met, double *avg, double *flux)
+{
+    int rc = check_slot(b, slot);
+    if (rc) return rc;
+    if (!b->slots[slot].h.met_on) return fail(HYB_ERR_STATE, "the discharge has no metastables");
+    rc = sync_status(b, slot);
+    const InstDev &K = b->h_stage[slot];
+    const int G = K.G;
+    if (met) CK(cudaMemcpy(met, K.met, 8 * (size_t)G, cudaMemcpyDeviceToHost));
+    if (avg) {
+        CK(cudaMemcpy(avg, K.acc_met, 8 * (size_t)G, cudaMemcpyDeviceToHost));
+        for (int j = 0; j < G; ++j) avg[j] = K.n_samples ? avg[j] / (double)K.n_samples : 0.0;
+    }
+    if (flux) {
+        flux[0] = K.flux_met[0];
+        flux[1] = K.flux_met[1];
     }
     return rc;
 }
@@ -1336,6 +1396,11 @@ int hyb_batch_read_particles(hyb_batch *b, int32_t slot, double *z, double *vx, 
                              int64_t cap, int64_t *n)
 {
     return read_particles(b, slot, z, vx, vy, vz, id, cap, n);
+}
+
+int hyb_batch_read_metastables(hyb_batch *b, int32_t slot, double *met, double *avg, double *flux)
+{
+    return read_metastables(b, slot, met, avg, flux);
 }
 
 int hyb_batch_read_ions(hyb_batch *b, int32_t slot, double *z, double *vx, double *vy, double *vz, uint64_t *id,
@@ -1559,6 +1624,7 @@ int hyb_reset_moments(hyb_discharge *h)
     const size_t bytes = 8 * (size_t)K.G;
     double *acc[5] = {K.acc_ne, K.acc_ni, K.acc_gi, K.acc_wn, K.acc_we};
     for (int k = 0; k < 5; ++k) CK(cudaMemsetAsync(acc[k], 0, bytes, b->stream));
+    if (K.met_on) CK(cudaMemsetAsync(K.acc_met, 0, bytes, b->stream));
     CK(cudaMemsetAsync(K.eedf, 0, 8 * (size_t)(K.eedf_bins + 1), b->stream));
     K.n_samples = 0;
     CK(cudaMemcpyAsync(&b->d_inst[h->slot], &K, sizeof K, cudaMemcpyHostToDevice, b->stream));
@@ -1638,6 +1704,27 @@ int hyb_read_ions(hyb_discharge *h, double *z, double *vx, double *vy, double *v
 {
     if (!h || !n) return fail(HYB_ERR_ARG, "NULL argument");
     return read_ions(h->b, h->slot, z, vx, vy, vz, id, cap, n);
+}
+
+int hyb_read_metastables(hyb_discharge *h, double *met, double *avg, double *flux)
+{
+    if (!h) return fail(HYB_ERR_ARG, "NULL handle");
+    return read_metastables(h->b, h->slot, met, avg, flux);
+}
+
+int hyb_write_metastables(hyb_discharge *h, const double *met)
+{
+    if (!h || !met) return fail(HYB_ERR_ARG, "NULL argument");
+    hyb_batch *b = h->b;
+    const InstDev &K = b->slots[h->slot].h;
+    if (!K.met_on) return fail(HYB_ERR_STATE, "the discharge has no metastables");
+    const int G = K.G;
+    for (int j = 0; j < G; ++j)
+        if (!(met[j] >= 0.0) || !isfinite(met[j])) return fail(HYB_ERR_ARG, "metastable density %d invalid", j);
+    if (met[0] != 0.0 || met[G - 1] != 0.0) return fail(HYB_ERR_ARG, "the electrode nodes must be 0");
+    CK(cudaStreamSynchronize(b->stream));
+    CK(cudaMemcpy(K.met, met, 8 * (size_t)G, cudaMemcpyHostToDevice));
+    return HYB_OK;
 }
 
 int hyb_write_ion_density(hyb_discharge *h, const double *ni)

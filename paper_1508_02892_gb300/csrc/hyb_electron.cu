@@ -264,7 +264,7 @@ __device__ __forceinline__ void row_deposit(WarpRow &row, int &base, InstDev *K,
     atomicAdd(&row.e1[j], __float2uint_rn(o * en * kFixE));
 }
 
-template <int MODE, bool REC, bool KIN>
+template <int MODE, bool CHEM, bool KIN>
 __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *smem, PackedCounters &cnt)
 {
     const int nc = K->n_cells;
@@ -394,8 +394,8 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             // kVec particles' draws are formed together (independent chains).
             uint4 rk[kVec];
             draw_n<kVec>(pre, ids, sl, 0u, rk);
-            uint4 rq[kVec];
-            if (REC) draw_n<kVec>(pre, ids, sl, 2u, rq);
+            uint4 rq[kVec] = {};
+            if (CHEM && K->rec_on) draw_n<kVec>(pre, ids, sl, 2u, rq);
 #pragma unroll
             for (int k = 0; k < kVec; ++k) {
                 // computed for every lane without branches, so that the kVec
@@ -414,7 +414,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 const float s_el = above ? hi.y : lo.y + f * (hi.y - lo.y);
                 const float s_ex = en < e_exc ? 0.f : (above ? hi.z : lo.z + f * (hi.z - lo.z));
                 const float s_iz = en < e_iz ? 0.f : (above ? hi.w : lo.w + f * (hi.w - lo.w));
-                if (REC && cc[k] >= 0 && cc[k] < nc && u01f(rq[k].x) < K->f_rec_pmax) {
+                if (CHEM && cc[k] >= 0 && cc[k] < nc && u01f(rq[k].x) < K->f_rec_pmax) {
                     // electron-ion recombination (Sec. II.D), in units of nu_rec,max:
                     // R4 < (n_i / max n_i)(sigma_rec / max sigma_rec v) v
                     const int cr = cc[k];
@@ -455,6 +455,14 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 vy[k] = scat ? sp * dy : vy[k];
                 vz[k] = scat ? sp * dzz : vz[k];
                 cnt.el_exc += scat ? (kind == 1u ? 1u : (1u << 16)) : 0u;
+                if (CHEM && scat && kind == 2u && K->met_on) {
+                    // a metastable at the electron (Sec. II.D), CIC
+                    const int cm = cc[k];
+                    if (HYB_CHECK(cm >= 0 && cm + 1 < G, 4, cm, G)) {
+                        atomicAdd(&K->s_met[cm], 1.0 - (double)oo[k]);
+                        atomicAdd(&K->s_met[cm + 1], (double)oo[k]);
+                    }
+                }
                 coll |= (hit && kind == 3u) ? (3u << (2 * k)) : 0u;
                 ru[k] = make_uint2(rk[k].z, rk[k].w);
                 cnt.iz_nul += (cand && !hit) ? (1u << 16) : 0u;
@@ -629,7 +637,7 @@ __device__ __forceinline__ void iso_dir_d(double u_cos, double u_phi, double d[3
     d[2] = ct;
 }
 
-template <int MODE, bool REC, bool KIN>
+template <int MODE, bool CHEM, bool KIN>
 __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *smem, SegCounters &cnt)
 {
     const int nc = K->n_cells;
@@ -700,7 +708,7 @@ __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *sm
             cnt.cmax = max(cnt.cmax, c);
         }
 
-        if (REC && MODE == 0 && alive && K->rec_on) {
+        if (CHEM && MODE == 0 && alive && K->rec_on) {
             // electron-ion recombination (Sec. II.D): candidate if R3 < P_rec,
             // real if R4 nu_rec,max < n_i(z) sigma_rec(E) v; the electron is
             // removed and its ion leaves through a CIC sink in the ion source
@@ -746,6 +754,10 @@ __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *sm
                     vy = sp * d[1];
                     vz = sp * d[2];
                     ++cnt.exc;
+                    if (CHEM && K->met_on) {  // a metastable at the electron (Sec. II.D), CIC
+                        atomicAdd(&K->s_met[c], 1.0 - o);
+                        atomicAdd(&K->s_met[c + 1], o);
+                    }
                 } else if (rr < nu_el + nu_ex + nu_iz) {
                     const uint4 r1 = draw(id, step, sl, sh, 1);
                     const double de = en - e_iz;
@@ -919,7 +931,7 @@ __device__ __forceinline__ void for_block_runs(InstDev *__restrict__ insts, int 
     }
 }
 
-template <int PREC, int MODE, bool REC = false, bool KIN = false>
+template <int PREC, int MODE, bool CHEM = false, bool KIN = false>
 __global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 3 : 2) k_electron(InstDev *__restrict__ insts,
                                                                                        int n_max,
                                                                                        const int64_t *__restrict__ prefix)
@@ -929,11 +941,11 @@ __global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 3 : 2) k_elec
         SegCounters cnt;
         if (PREC == HYB_FP32_SPLIT) {
             PackedCounters pc;
-            segment_split<MODE, REC, KIN>(K, a, b, smem, pc);
+            segment_split<MODE, CHEM, KIN>(K, a, b, smem, pc);
             pc.unpack(cnt);
             flush_segment_split<MODE>(K, smem, cnt);
         } else {
-            segment_fp64<MODE, REC, KIN>(K, a, b, smem, cnt);
+            segment_fp64<MODE, CHEM, KIN>(K, a, b, smem, cnt);
             flush_segment<double, MODE>(K, smem, cnt);
         }
     });
@@ -1287,10 +1299,10 @@ __global__ void k_set_active(InstDev *K, int active, int64_t target_step)
     K->target_step = target_step;
 }
 
-template <int PREC, int MODE, bool REC = false, bool KIN = false>
+template <int PREC, int MODE, bool CHEM = false, bool KIN = false>
 cudaError_t launch_k(InstDev *inst, int n_max, const int64_t *prefix, LaunchCfg cfg, cudaStream_t s)
 {
-    k_electron<PREC, MODE, REC, KIN><<<cfg.grid, cfg.block, cfg.smem, s>>>(inst, n_max, prefix);
+    k_electron<PREC, MODE, CHEM, KIN><<<cfg.grid, cfg.block, cfg.smem, s>>>(inst, n_max, prefix);
     return cudaGetLastError();
 }
 
@@ -1340,18 +1352,19 @@ size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins)
 }
 
 cudaError_t launch_electron_step(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
-                                 cudaStream_t s, bool rec, bool kin)
+                                 cudaStream_t s, bool chem, bool kin)
 {
-    // the variants with the recombination test and with ion births when some
+    // the variants with the reactions of Sec. II.D beyond the neutral MCC
+    // (recombination test, metastable source) and with ion births, when some
     // discharge of the batch needs them
     const bool sp = precision == HYB_FP32_SPLIT;
-    if (rec && kin)
+    if (chem && kin)
         return sp ? launch_k<HYB_FP32_SPLIT, 0, true, true>(inst, n_max, prefix, cfg, s)
                   : launch_k<HYB_FP64, 0, true, true>(inst, n_max, prefix, cfg, s);
     if (kin)
         return sp ? launch_k<HYB_FP32_SPLIT, 0, false, true>(inst, n_max, prefix, cfg, s)
                   : launch_k<HYB_FP64, 0, false, true>(inst, n_max, prefix, cfg, s);
-    if (rec)
+    if (chem)
         return sp ? launch_k<HYB_FP32_SPLIT, 0, true>(inst, n_max, prefix, cfg, s)
                   : launch_k<HYB_FP64, 0, true>(inst, n_max, prefix, cfg, s);
     return sp ? launch_k<HYB_FP32_SPLIT, 0>(inst, n_max, prefix, cfg, s) : launch_k<HYB_FP64, 0>(inst, n_max, prefix, cfg, s);

@@ -200,6 +200,154 @@ struct FluidF {
     }
 };
 
+// Metastables and the ionization they cause (Sec. II.D), from n_m^n at the
+// start of the step:
+//  - Penning (Delta N_e = R_P n_N n_m dt dz) and pooling (R_pool n_m^2 dt dz)
+//    electrons per interior node j: the integer part of Delta N_e / N_p/sp plus
+//    one with the probability of the fraction (call 3 of the key of the process
+//    and j); numbered k = 0, 1, ... in node order per process, each placed
+//    uniformly in [z_j - dz/2, z_j + dz/2) at the process's energy with an
+//    isotropic direction (call 2 of its id), appended after this step's
+//    children, its ion added to the ion source (CIC);
+//  - the explicit update n_m += dt (D n_m'' + S_m - R_P n_N n_m - 2 R_pool n_m^2)
+//    at the interior nodes, n_m = 0 at the electrodes, and the flux into each
+//    wall (D n_m(next node)/dz plus the excitation sources on the wall node).
+// Delta N_e of one node: R_P n_m n_N dt dz (Penning) or R_pool n_m^2 dt dz (pooling)
+__device__ __forceinline__ double birth_mean(const InstDev *K, int proc, double nm, double dt, double dz)
+{
+    return proc == 0 ? K->met_rp * nm * K->met_nn * dt * dz : K->met_kq * nm * nm * dt * dz;
+}
+
+// old: G doubles of shared scratch.
+__device__ void metastable_step(InstDev *K, double *old, Red &red, int j0, int j1)
+{
+    const int G = K->G;
+    const double dz = K->dz, dt = K->dt, w = K->w;
+    const uint32_t n = (uint32_t)K->step;
+    const double kp = K->met_kp, kq = K->met_kq;
+    __shared__ unsigned long long s_base;
+    __shared__ int64_t s_tot[2];
+    int64_t mine[2] = {0, 0};
+    // counts per node, kept in the scratch row until the update below
+    for (int j = j0; j < j1; ++j) {
+        const double nm = K->met[j];
+        old[j] = nm;
+    }
+    double part[2] = {0.0, 0.0};
+    for (int proc = 0; proc < 2; ++proc) {
+        const double r = proc == 0 ? kp : kq;
+        if (!(r > 0.0) || !(w > 0.0)) continue;
+        for (int j = max(j0, 1); j < min(j1, G - 1); ++j) {
+            const double nm = old[j];
+            const double m = birth_mean(K, proc, nm, dt, dz) / w;
+            if (!(m > 0.0)) continue;
+            const double fl = floor(m);
+            const uint4 u = draw(0xFFFFFFFF00000000ull | ((uint64_t)(proc + 1) << 24) | (uint64_t)j, n, K->seed_lo,
+                                 K->seed_hi, 3);
+            part[proc] += fl + (u01d(u.x) < m - fl ? 1.0 : 0.0);
+        }
+    }
+    double tot[2];
+    const double off0 = block_exscan(part[0], red, &tot[0]);
+    const double off1 = block_exscan(part[1], red, &tot[1]);
+    const int64_t cap = (1 << 20) - 1;
+    if (threadIdx.x == 0) {
+        s_tot[0] = (int64_t)tot[0] < cap ? (int64_t)tot[0] : cap;
+        s_tot[1] = (int64_t)tot[1] < cap ? (int64_t)tot[1] : cap;
+        if ((int64_t)tot[0] > cap || (int64_t)tot[1] > cap) K->status |= HYB_STATUS_EMIT_CAP;
+        s_base = K->n_slots;
+        K->n_slots = s_base + (unsigned long long)(s_tot[0] + s_tot[1]);
+        K->ctr[C_PEN] += (unsigned long long)s_tot[0];
+        K->ctr[C_POOL] += (unsigned long long)s_tot[1];
+    }
+    __syncthreads();
+    mine[0] = (int64_t)off0;
+    mine[1] = (int64_t)off1;
+    const PartBuf P = K->buf[K->cur];
+    for (int proc = 0; proc < 2; ++proc) {
+        const double r = proc == 0 ? kp : kq;
+        if (!(r > 0.0) || !(w > 0.0) || part[proc] == 0.0) continue;
+        const double sp = K->met_sp[proc];
+        int64_t k = mine[proc];
+        for (int j = max(j0, 1); j < min(j1, G - 1) && k < s_tot[proc]; ++j) {
+            const double nm = old[j];
+            const double m = birth_mean(K, proc, nm, dt, dz) / w;
+            if (!(m > 0.0)) continue;
+            const double fl = floor(m);
+            const uint4 u = draw(0xFFFFFFFF00000000ull | ((uint64_t)(proc + 1) << 24) | (uint64_t)j, n, K->seed_lo,
+                                 K->seed_hi, 3);
+            const int64_t cnt = (int64_t)fl + (u01d(u.x) < m - fl ? 1 : 0);
+            for (int64_t b = 0; b < cnt && k < s_tot[proc]; ++b, ++k) {
+                const uint64_t id = (1ull << 62) | ((uint64_t)(2 + proc) << 60) | ((uint64_t)n << 20) | (uint64_t)k;
+                const uint4 v = draw(id, n, K->seed_lo, K->seed_hi, 2);
+                const double z = ((double)j - 0.5 + u01d(v.x)) * dz;
+                const double ct = 1.0 - 2.0 * u01d(v.y);
+                const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+                const double ph = kTwoPi * u01d(v.z);
+                const double vx = sp * st * cos(ph), vy = sp * st * sin(ph), vz = sp * ct;
+                // the ion of the event (CIC), as for an impact ionization
+                const double x = z / dz;
+                const double f = floor(x);
+                int c = (int)f;
+                double o = x - f;
+                if (c >= K->n_cells) {
+                    c = K->n_cells - 1;
+                    o = 1.0;
+                }
+                if (HYB_CHECK(c >= 0 && c + 1 < G, 21, c, G)) {
+                    atomicAdd(&K->s_iz[c], 1.0 - o);
+                    atomicAdd(&K->s_iz[c + 1], o);
+                }
+                const unsigned long long slot = s_base + (unsigned long long)(proc == 0 ? k : s_tot[0] + k);
+                if (slot >= (unsigned long long)K->capacity) {
+                    atomicOr(&K->status, (unsigned)HYB_STATUS_CAPACITY);
+                    continue;
+                }
+                P.id[slot] = id;
+                if (K->precision == HYB_FP32_SPLIT) {
+                    P.c[slot] = c;
+                    P.o[slot] = (float)o;
+                    P.vxf[slot] = (float)vx;
+                    P.vyf[slot] = (float)vy;
+                    P.vzf[slot] = (float)vz;
+                } else {
+                    P.z[slot] = z;
+                    P.vxd[slot] = vx;
+                    P.vyd[slot] = vy;
+                    P.vzd[slot] = vz;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // the density update from the old values
+    const double D = K->met_D;
+    unsigned long long clamps = 0;
+    for (int j = j0; j < j1; ++j) {
+        double nn = 0.0;
+        if (j >= 1 && j <= G - 2) {
+            const double src = w * K->s_met[j] / (dz * dt);
+            const double lap = D * (old[j + 1] - 2.0 * old[j] + old[j - 1]) / (dz * dz);
+            const double loss = kp * old[j] + 2.0 * kq * old[j] * old[j];
+            nn = old[j] + dt * (lap + src - loss);
+            if (nn < 0.0) {
+                nn = 0.0;
+                ++clamps;
+            }
+        }
+        K->met[j] = nn;
+        K->acc_met[j] += nn;
+    }
+    if (clamps) atomicAdd(&red.count, clamps);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        K->flux_met[0] = D * old[1] / dz + w * K->s_met[0] / dt;
+        K->flux_met[1] = D * old[G - 2] / dz + w * K->s_met[G - 1] / dt;
+    }
+    __syncthreads();
+    for (int j = j0; j < j1; ++j) K->s_met[j] = 0.0;
+}
+
 template <bool FAST>
 __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, FieldConsts &fc)
 {
@@ -250,6 +398,8 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
         fc.tfac = (float)((mi + mn) / (5.0 * mi + 3.0 * mn) * mn);
     }
     __syncthreads();
+
+    if (K->met_on && !init) metastable_step(K, s_d, red, j0, j1);
 
     const Fluid F{K->ion_model, K->n_tab, K->tab, K->mu_const, K->ngas, K->kT_gas, K->m_ion, K->m_gas};
     double *gfin = s_g;
@@ -579,9 +729,10 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
         K->step += 1;
         const uint32_t n = (uint32_t)K->step;
         s_cnt[0] = s_cnt[1] = 0;
-        if (K->gamma_see > 0.0 && w > 0.0) {
+        if ((K->gamma_see > 0.0 || K->gamma_met > 0.0) && w > 0.0) {
             for (int wall = 0; wall < 2; ++wall) {
-                const double ns = K->gamma_see * K->flux_in[wall] * dt / w;
+                // ions and metastables striking the wall (Sec. II.D)
+                const double ns = (K->gamma_see * K->flux_in[wall] + K->gamma_met * K->flux_met[wall]) * dt / w;
                 if (!(ns > 0.0)) continue;
                 const double k = floor(ns);
                 const double frac = ns - k;

@@ -68,7 +68,8 @@ struct InstDev {
     int64_t n_slots_step;             // slots processed by the current step
     int64_t n_samples;
     double flux_in[2];
-    unsigned long long ctr[12];       // births_iz, see0, see1, loss0, loss1, el, exc, iz, null, clamps, pushes, rec
+    unsigned long long ctr[14];       // births_iz, see0, see1, loss0, loss1, el, exc, iz, null, clamps, pushes, rec,
+                                      // Penning births, pooling births
     int64_t n_base;                   // live count = n_base + births - losses
     unsigned int status;
     int32_t init_pending;             // field kernel runs in initial-solve mode
@@ -92,10 +93,18 @@ struct InstDev {
     InstDev *elec;                    // ion descriptor: its electrons
     double *dep_ni, *dep_gi;          // per-step CIC sums of the ions: count and v_z
     double mi_red, nu_max_i, p_max_i, vt_gas;
+    // metastables and the ionization they cause (Sec. II.D)
+    int32_t met_on, pad3;
+    double met_D, met_kp, met_kq;     // D, R_P n_N, R_pool
+    double met_rp, met_nn;            // R_P and n_N
+    double met_sp[2];                 // speeds of Penning and pooling electrons
+    double gamma_met;
+    double *met, *s_met, *acc_met;    // [G] n_m, this step's CIC excitation sums, time sum of n_m
+    double flux_met[2];               // metastables into each wall in the last step, m^-2 s^-1
     unsigned long long ion_loss_prev[2];
 };
 
-enum { C_BIRTH_IZ = 0, C_SEE0, C_SEE1, C_LOSS0, C_LOSS1, C_EL, C_EXC, C_IZ, C_NULL, C_CLAMP, C_PUSH, C_REC };
+enum { C_BIRTH_IZ = 0, C_SEE0, C_SEE1, C_LOSS0, C_LOSS1, C_EL, C_EXC, C_IZ, C_NULL, C_CLAMP, C_PUSH, C_REC, C_PEN, C_POOL };
 
 // ------------------------------------------------------------ self-checks
 // Every dynamic index of the kernels is guarded: the first failed guard of a
@@ -237,7 +246,7 @@ struct LaunchCfg {
 // electron kernels (hyb_electron.cu)
 cudaError_t launch_electron_step(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
                                  cudaStream_t s,
-                                 bool rec = false, bool kin = false);
+                                 bool chem = false, bool kin = false);
 // kinetic ions: initial load, the per-step snapshot prefix over a lane's ion
 // descriptors, and the ion step (mode 0) or deposit alone (mode 1)
 cudaError_t launch_load_ions(InstDev *ion, int64_t n, cudaStream_t s);

@@ -43,7 +43,10 @@ class Params(C.Structure):
         ("e_exc_ev", C.c_double), ("e_iz_ev", C.c_double), ("seed", C.c_uint64),
         ("eedf_bins", C.c_int32), ("eedf_max_ev", C.c_double), ("precision", C.c_int32),
         ("capacity_factor", C.c_double), ("sort_interval", C.c_int32), ("power_w_m2", C.c_double),
-        ("power_alpha", C.c_double), ("xs_rec", _pd),
+        ("power_alpha", C.c_double), ("xs_rec", _pd), ("metastables", C.c_int32), ("met_diff_m2s", C.c_double),
+        ("met_n0_m3", C.c_double), ("penning_rate_m3s", C.c_double), ("penning_target_m3", C.c_double),
+        ("penning_energy_ev", C.c_double), ("pooling_rate_m3s", C.c_double), ("pooling_energy_ev", C.c_double),
+        ("gamma_met", C.c_double),
     ]
 
 
@@ -61,7 +64,8 @@ class Counters(C.Structure):
                 ("births_see", C.c_int64 * 2), ("losses", C.c_int64 * 2), ("collisions", C.c_int64 * 4),
                 ("clamps", C.c_int64), ("pushes", C.c_int64), ("status", C.c_uint32), ("v_rf_amp_v", C.c_double),
                 ("power_last_w_m2", C.c_double), ("power_periods", C.c_int64), ("recombinations", C.c_int64),
-                ("ions", C.c_int64), ("ion_losses", C.c_int64 * 2), ("ion_collisions", C.c_int64)]
+                ("ions", C.c_int64), ("ion_losses", C.c_int64 * 2), ("ion_collisions", C.c_int64),
+                ("births_penning", C.c_int64), ("births_pooling", C.c_int64)]
 
 
 class Info(C.Structure):
@@ -110,6 +114,9 @@ EXPORTS = {
                                      C.POINTER(C.c_int64)]),
     "hyb_write_particles": (C.c_int, [C.c_void_p, C.c_int64, _pd, _pd, _pd, _pd, C.POINTER(C.c_uint64)]),
     "hyb_write_ion_density": (C.c_int, [C.c_void_p, _pd]),
+    "hyb_read_metastables": (C.c_int, [C.c_void_p, _pd, _pd, _pd]),
+    "hyb_write_metastables": (C.c_int, [C.c_void_p, _pd]),
+    "hyb_batch_read_metastables": (C.c_int, [C.c_void_p, C.c_int32, _pd, _pd, _pd]),
     "hyb_read_ions": (C.c_int, [C.c_void_p, _pd, _pd, _pd, _pd, C.POINTER(C.c_uint64), C.c_int64,
                                 C.POINTER(C.c_int64)]),
     "hyb_batch_read_ions": (C.c_int, [C.c_void_p, C.c_int32, _pd, _pd, _pd, _pd, C.POINTER(C.c_uint64), C.c_int64,
@@ -232,7 +239,8 @@ def _counters(call):
             "ionization": c.collisions[2], "null": c.collisions[3], "clamps": c.clamps, "pushes": c.pushes,
             "status": c.status, "v_rf": c.v_rf_amp_v, "power_last": c.power_last_w_m2,
             "power_periods": c.power_periods, "recombinations": c.recombinations, "ions": c.ions,
-            "ion_losses0": c.ion_losses[0], "ion_losses1": c.ion_losses[1], "ion_collisions": c.ion_collisions}
+            "ion_losses0": c.ion_losses[0], "ion_losses1": c.ion_losses[1], "ion_collisions": c.ion_collisions,
+            "births_penning": c.births_penning, "births_pooling": c.births_pooling}
 
 
 def _particles(call, cap):
@@ -323,6 +331,21 @@ class Discharge:
         ni = _arr(ni)
         _check(lib().hyb_write_ion_density(self.h, ni.ctypes.data_as(_pd)))
 
+    def metastables(self):
+        """Metastable density, its time average, and the flux into each wall in
+        the last step."""
+        return _metastables(lambda *a: lib().hyb_read_metastables(self.h, *a), self.info["n_nodes"])
+
+    def set_metastables(self, met):
+        met = _arr(met)
+        _check(lib().hyb_write_metastables(self.h, met.ctypes.data_as(_pd)))
+
+
+def _metastables(call, G):
+    met, avg, flux = np.zeros(G), np.zeros(G), np.zeros(2)
+    _check(call(met.ctypes.data_as(_pd), avg.ctypes.data_as(_pd), flux.ctypes.data_as(_pd)))
+    return {"met": met, "avg": avg, "flux": flux}
+
 
 def footprint(params: dict) -> int:
     p, keep = make_params(params)
@@ -383,6 +406,9 @@ class Batch:
     def particles(self, slot, cap=None):
         cap = int(cap or self._shape[slot][2])
         return _particles(lambda *a: lib().hyb_batch_read_particles(self.h, int(slot), *a), cap)
+
+    def metastables(self, slot):
+        return _metastables(lambda *a: lib().hyb_batch_read_metastables(self.h, int(slot), *a), self._shape[slot][0])
 
     def ions(self, slot, cap=None):
         cap = int(cap or self._shape[slot][2])
