@@ -261,6 +261,74 @@ def swarm_load(n_fields=64, n_ions=65536, n_steps=20000):
     return out
 
 
+def variants_load(params, stream, flush, n_inst=16, chunks=3):
+    """The widened paths on the first `n_inst` discharges of the batched
+    workload (FP32 split electrons, one lane, per-kernel CUDA events): the
+    plain step; recombination with metastables, Penning and pooling (the
+    electron kernel's chemistry variant and the metastable field step);
+    power control (Eq. 2.9); and fully kinetic ions (FP64 ions: the electron
+    kernel's ion-birth variant, k_ion and the ion sort), whose k_ion is
+    measured against the HBM roofline at 72 algorithmic bytes per ion-step.
+    Electron particle-steps/s over `chunks` timed chunks (L2 flushed between
+    them), and the device time per step of each kernel interval."""
+    import torch
+
+    from paper_1508_02892_gb300 import hybrid, workloads as W
+    sub = [dict(p) for p in params[:n_inst]]
+    mods = {
+        "plain": {},
+        "recombination_metastables": dict(xs_rec=W.recombination_table(1e-12),
+                                          **W.metastable_params(met_n0_m3=1e19, gamma_met=0.05)),
+        "power_control": dict(power_w_m2=2e5, power_alpha=0.1),
+        "kinetic_ions": dict(ion_model=W.ION_KINETIC),
+    }
+    peak, peak_kind = peaks()
+    out = {"instances": n_inst, "chunks": chunks, "chunk_steps": CHUNK, "unit": "particle-steps/s",
+           "initial_particles": sum(p["n_particles"] for p in sub)}
+    for name, mod in mods.items():
+        b = hybrid.Batch(n_inst, hybrid.HYB_FP32_SPLIT, stream=stream.cuda_stream)
+        slots = [b.admit(dict(p, capacity_factor=2.5, **mod)) for p in sub]
+        b.set_tuning(lanes=1)
+        b.advance(CHUNK)                       # warm-up (graph capture)
+        b.set_profiling(True)
+        b.advance(CHUNK)
+        torch.cuda.synchronize()
+        b.profile(reset=True)
+        c0 = [b.counters(s) for s in slots]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for _ in range(chunks):
+            flush.zero_()
+            e0.record(stream)
+            b.advance(CHUNK)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        prof = b.profile()
+        c1 = [b.counters(s) for s in slots]
+        n = sum(y["pushes"] - x["pushes"] for x, y in zip(c0, c1))
+        steps = chunks * CHUNK
+        r = {"value": n / (ms / 1e3), "ms_per_step": ms / steps,
+             "electron_ms_per_step": prof["ms_electron"] / steps, "field_ms_per_step": prof["ms_field"] / steps,
+             "sort_ms_per_step": prof["ms_sort"] / steps,
+             "status": max(c["status"] for c in c1)}
+        if name == "recombination_metastables":
+            r["events"] = {k: sum(y[k] - x[k] for x, y in zip(c0, c1))
+                           for k in ("recombinations", "births_penning", "births_pooling")}
+        if name == "kinetic_ions":
+            ni = sum(y["ion_pushes"] - x["ion_pushes"] for x, y in zip(c0, c1))
+            avg = prof["ms_ion"] / max(prof["n_ion"], 1)
+            ach = 72.0 * ni / max(prof["n_ion"], 1) / (avg / 1e3) / 1e9
+            r["ion_steps_per_s"] = ni / (ms / 1e3)
+            r["ion_roofline"] = {"kernel": "k_ion_prefix + k_ion<0>", "bound": "hbm", "bytes_per_unit": 72,
+                                 "units_per_launch": ni / max(prof["n_ion"], 1), "avg_launch_ms": avg,
+                                 "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                 "peak_kind": peak_kind}
+        out[name] = r
+        b.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -384,6 +452,10 @@ def run_ours(args):
                "note": "admission from host parameters and tables (pageable), per-chunk host read of all "
                        "moments, eviction, all inside the wall-clock region"}
 
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = variants_load(params, stream, flush)
+
     swarm = None
     if rank == 0 and not args.no_swarm:
         swarm = swarm_load(n_ions=args.swarm_ions, n_steps=args.swarm_steps)
@@ -439,6 +511,8 @@ def run_ours(args):
         line["serving"] = serving
     if swarm:
         line["swarm"] = swarm
+    if variants:
+        line["variants"] = variants
     if cpu:
         line["cpu_baseline"] = cpu
     line["device_index_guards"] = hybrid.debug_checks()
@@ -463,6 +537,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=100, help="config-4 serving requests (0: none)")
     ap.add_argument("--serve-steps", type=int, default=5000)
     ap.add_argument("--no-swarm", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the widened-path measurements")
     ap.add_argument("--swarm-ions", type=int, default=65536, help="ions per field of the swarm run")
     ap.add_argument("--swarm-steps", type=int, default=20000)
     ap.add_argument("--only-swarm", action="store_true", help="run and print the ion-swarm measurement alone")

@@ -176,6 +176,7 @@ typedef struct hyb_counters {
     int64_t ion_collisions;     /* real ion-neutral collisions of the kinetic ions */
     int64_t births_penning;     /* electrons born by Penning ionization */
     int64_t births_pooling;     /* electrons born by metastable pooling */
+    int64_t ion_pushes;         /* kinetic ions: ion-steps advanced (pushes), for throughput */
 } hyb_counters;
 
 #define HYB_STATUS_CAPACITY 1u
@@ -303,6 +304,8 @@ typedef struct hyb_profile {
     int64_t steps;              /* lockstep steps enqueued */
     double ms_electron, ms_field, ms_sort; /* summed device time of the timed launches */
     int64_t n_electron, n_field, n_sort;   /* timed launches */
+    double ms_ion;              /* kinetic ions: summed device time of the per-step ion kernels */
+    int64_t n_ion;              /* timed ion steps */
 } hyb_profile;
 
 int hyb_batch_set_profiling(hyb_batch *b, int32_t on);

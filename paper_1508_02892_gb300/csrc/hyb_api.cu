@@ -457,8 +457,8 @@ struct hyb_batch {
     bool profiling = false;
     bool pending = false;         // events of the last graph launch not read yet
     std::vector<cudaEvent_t> ev;  // per lane: 3 per step + 2 per sort of a chunk
-    double ms[3] = {0, 0, 0};
-    int64_t nt[3] = {0, 0, 0};
+    double ms[4] = {0, 0, 0, 0};  // electron, field, sort, ion
+    int64_t nt[4] = {0, 0, 0, 0};
 };
 
 struct hyb_discharge {
@@ -548,7 +548,7 @@ int chunk_len(const hyb_batch *b)
 size_t events_per_lane(const hyb_batch *b)
 {
     const int GL = chunk_len(b);
-    return 3 * (size_t)GL + 2 * (size_t)(GL / b->sort_interval);
+    return 4 * (size_t)GL + 2 * (size_t)(GL / b->sort_interval);
 }
 
 int ensure_events(hyb_batch *b)
@@ -578,22 +578,25 @@ int record(cudaStream_t s, cudaEvent_t e)
 cudaEvent_t lane_event(const hyb_batch *b, int lane, size_t i) { return b->ev[(size_t)lane * events_per_lane(b) + i]; }
 
 // One step of one lane on stream s; with profiling, the lane's events
-// 3k..3k+2 bracket the two kernels.
+// 4k..4k+3 bracket the electron kernel, the ion kernels (kinetic ions) and
+// the field kernel.
 int launch_step(hyb_batch *b, int k, int lane, cudaStream_t s)
 {
     int rc;
     const int n = lane_count(b, lane);
-    if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k)))) return rc;
+    const size_t e = 4 * (size_t)k;
+    if (b->profiling && (rc = record(s, lane_event(b, lane, e)))) return rc;
     CK(launch_electron_step(lane_inst(b, lane), n, lane_prefix(b, lane), b->precision, b->cfg, s, b->any_chem,
                             b->any_kin));
+    if (b->profiling && (rc = record(s, lane_event(b, lane, e + 1)))) return rc;
     if (b->any_kin) {  // the ions of the step, after the electrons' births
         CK(launch_ion_prefix(lane_inst_ion(b, lane), n, lane_prefix_ion(b, lane), s));
         CK(launch_ion_step(lane_inst_ion(b, lane), n, lane_prefix_ion(b, lane), 0, b->cfg.grid, b->max_nodes, s));
     }
-    if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k + 1)))) return rc;
+    if (b->profiling && (rc = record(s, lane_event(b, lane, e + 2)))) return rc;
     CK(launch_field(lane_inst(b, lane), n, lane_prefix(b, lane), lane_ticket(b, lane), b->precision == HYB_FP32_SPLIT,
                     b->max_nodes, b->field_threads, s));
-    if (b->profiling && (rc = record(s, lane_event(b, lane, 3 * (size_t)k + 2)))) return rc;
+    if (b->profiling && (rc = record(s, lane_event(b, lane, e + 3)))) return rc;
     return HYB_OK;
 }
 
@@ -602,7 +605,7 @@ int launch_step(hyb_batch *b, int k, int lane, cudaStream_t s)
 int launch_sort_all(hyb_batch *b, int j, int lane, cudaStream_t s)
 {
     int rc;
-    const size_t s0 = 3 * (size_t)chunk_len(b) + 2 * (size_t)j;
+    const size_t s0 = 4 * (size_t)chunk_len(b) + 2 * (size_t)j;
     if (b->profiling && (rc = record(s, lane_event(b, lane, s0)))) return rc;
     CK(launch_sort(lane_inst(b, lane), lane_count(b, lane), lane_prefix(b, lane), b->precision, b->cfg, s));
     if (b->any_kin) {  // compaction and cell sort of the ions (FP64 layout)
@@ -618,17 +621,22 @@ int launch_sort_all(hyb_batch *b, int j, int lane, cudaStream_t s)
 int collect_times(hyb_batch *b, int steps, int sorts)
 {
     CK(cudaStreamSynchronize(b->stream));
-    const size_t s0 = 3 * (size_t)chunk_len(b);
+    const size_t s0 = 4 * (size_t)chunk_len(b);
     for (int lane = 0; lane < b->lanes; ++lane) {
         for (int k = 0; k < steps; ++k) {
-            float t0 = 0.f, t1 = 0.f;
-            CK(cudaEventElapsedTime(&t0, lane_event(b, lane, 3 * (size_t)k), lane_event(b, lane, 3 * (size_t)k + 1)));
-            CK(cudaEventElapsedTime(&t1, lane_event(b, lane, 3 * (size_t)k + 1),
-                                    lane_event(b, lane, 3 * (size_t)k + 2)));
+            const size_t e = 4 * (size_t)k;
+            float t0 = 0.f, ti = 0.f, t1 = 0.f;
+            CK(cudaEventElapsedTime(&t0, lane_event(b, lane, e), lane_event(b, lane, e + 1)));
+            CK(cudaEventElapsedTime(&ti, lane_event(b, lane, e + 1), lane_event(b, lane, e + 2)));
+            CK(cudaEventElapsedTime(&t1, lane_event(b, lane, e + 2), lane_event(b, lane, e + 3)));
             b->ms[0] += t0;
             b->ms[1] += t1;
             b->nt[0] += 1;
             b->nt[1] += 1;
+            if (b->any_kin) {
+                b->ms[3] += ti;
+                b->nt[3] += 1;
+            }
         }
         for (int j = 0; j < sorts; ++j) {
             float t = 0.f;
@@ -1144,7 +1152,7 @@ int read_counters(hyb_batch *b, int slot, hyb_counters *c)
     c->recombinations = (int64_t)K.ctr[C_REC];
     c->births_penning = (int64_t)K.ctr[C_PEN];
     c->births_pooling = (int64_t)K.ctr[C_POOL];
-    c->ions = c->ion_losses[0] = c->ion_losses[1] = c->ion_collisions = 0;
+    c->ions = c->ion_losses[0] = c->ion_losses[1] = c->ion_collisions = c->ion_pushes = 0;
     if (b->slots[slot].h.ion) {
         InstDev I{};
         CK(cudaMemcpyAsync(&I, &b->d_inst_ion[slot], sizeof I, cudaMemcpyDeviceToHost, b->stream));
@@ -1152,6 +1160,7 @@ int read_counters(hyb_batch *b, int slot, hyb_counters *c)
         c->ion_losses[0] = (int64_t)I.ctr[C_LOSS0];
         c->ion_losses[1] = (int64_t)I.ctr[C_LOSS1];
         c->ion_collisions = (int64_t)I.ctr[C_EL];
+        c->ion_pushes = (int64_t)I.ctr[C_PUSH];
         c->ions = I.n_base + (int64_t)K.ctr[C_BIRTH_IZ] - c->ion_losses[0] - c->ion_losses[1];
     }
     return rc;
@@ -1512,9 +1521,11 @@ int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset)
     out->n_electron = b->nt[0];
     out->n_field = b->nt[1];
     out->n_sort = b->nt[2];
+    out->ms_ion = b->ms[3];
+    out->n_ion = b->nt[3];
     if (reset) {
-        b->ms[0] = b->ms[1] = b->ms[2] = 0.0;
-        b->nt[0] = b->nt[1] = b->nt[2] = 0;
+        b->ms[0] = b->ms[1] = b->ms[2] = b->ms[3] = 0.0;
+        b->nt[0] = b->nt[1] = b->nt[2] = b->nt[3] = 0;
     }
     return HYB_OK;
 }

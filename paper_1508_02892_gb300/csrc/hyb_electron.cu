@@ -1010,9 +1010,9 @@ __device__ __forceinline__ double ion_nu(double ngas, double m_red, double g)
 }
 
 // ions [a, b) of ion descriptor I; ctr: losses at z = 0, at z = L,
-// collision candidates, real collisions.  MODE 1: charge assignment only.
+// collision candidates, real collisions, pushes.  MODE 1: charge assignment only.
 template <int MODE>
-__device__ void segment_ion(InstDev *I, int64_t a, int64_t b, unsigned char *smem, unsigned ctr[4])
+__device__ void segment_ion(InstDev *I, int64_t a, int64_t b, unsigned char *smem, unsigned ctr[5])
 {
     InstDev *K = I->elec;
     const int G = K->G, nc = K->n_cells;
@@ -1043,6 +1043,7 @@ __device__ void segment_ion(InstDev *I, int64_t a, int64_t b, unsigned char *sme
         int c = 0;
         double o = 0.0;
         if (MODE == 0 && alive) {
+            ++ctr[4];
             locate_d(z, dz, nc, c, o);
             const double ep = (1.0 - o) * E[c] + o * E[c + 1];
             vz = vz + (kQe / M) * ep * dt;
@@ -1094,21 +1095,21 @@ template <int MODE>
 __global__ void __launch_bounds__(kBlock) k_ion(InstDev *__restrict__ ions, int n_max, const int64_t *__restrict__ prefix)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned s_c[4];
+    __shared__ unsigned s_c[5];
     for_block_runs(ions, n_max, prefix, [&](InstDev *I, int64_t a, int64_t b) {
-        unsigned ctr[4] = {0u, 0u, 0u, 0u};
-        if (threadIdx.x < 4) s_c[threadIdx.x] = 0u;
+        unsigned ctr[5] = {0u, 0u, 0u, 0u, 0u};
+        if (threadIdx.x < 5) s_c[threadIdx.x] = 0u;
         segment_ion<MODE>(I, a, b, smem, ctr);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 5; ++k) {
             const unsigned t = __reduce_add_sync(kFull, ctr[k]);
             if ((threadIdx.x & 31) == 0 && t) atomicAdd(&s_c[k], t);
         }
         __syncthreads();
         if (threadIdx.x == 0 && MODE == 0) {
-            const int map[4] = {C_LOSS0, C_LOSS1, C_NULL, C_EL};
+            const int map[5] = {C_LOSS0, C_LOSS1, C_NULL, C_EL, C_PUSH};
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < 5; ++k)
                 if (s_c[k]) atomicAdd(&I->ctr[map[k]], (unsigned long long)s_c[k]);
         }
         __syncthreads();

@@ -65,7 +65,7 @@ class Counters(C.Structure):
                 ("clamps", C.c_int64), ("pushes", C.c_int64), ("status", C.c_uint32), ("v_rf_amp_v", C.c_double),
                 ("power_last_w_m2", C.c_double), ("power_periods", C.c_int64), ("recombinations", C.c_int64),
                 ("ions", C.c_int64), ("ion_losses", C.c_int64 * 2), ("ion_collisions", C.c_int64),
-                ("births_penning", C.c_int64), ("births_pooling", C.c_int64)]
+                ("births_penning", C.c_int64), ("births_pooling", C.c_int64), ("ion_pushes", C.c_int64)]
 
 
 class Info(C.Structure):
@@ -77,7 +77,7 @@ class Info(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("steps", C.c_int64), ("ms_electron", C.c_double),
                 ("ms_field", C.c_double), ("ms_sort", C.c_double), ("n_electron", C.c_int64),
-                ("n_field", C.c_int64), ("n_sort", C.c_int64)]
+                ("n_field", C.c_int64), ("n_sort", C.c_int64), ("ms_ion", C.c_double), ("n_ion", C.c_int64)]
 
 
 _lib = None
@@ -240,7 +240,7 @@ def _counters(call):
             "status": c.status, "v_rf": c.v_rf_amp_v, "power_last": c.power_last_w_m2,
             "power_periods": c.power_periods, "recombinations": c.recombinations, "ions": c.ions,
             "ion_losses0": c.ion_losses[0], "ion_losses1": c.ion_losses[1], "ion_collisions": c.ion_collisions,
-            "births_penning": c.births_penning, "births_pooling": c.births_pooling}
+            "births_penning": c.births_penning, "births_pooling": c.births_pooling, "ion_pushes": c.ion_pushes}
 
 
 def _particles(call, cap):

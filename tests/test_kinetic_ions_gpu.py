@@ -83,6 +83,27 @@ def test_fp64_kinetic_ions_match_the_oracle():
     assert c["births_iz"] > 100 and ic["losses0"] + ic["losses1"] > 0 and ic["collisions"] > 0
     _check(g, o, p)
     g.close()
+    # the ion-step counter: in step 0 every loaded ion and every ion born in it moves
+    g1 = hybrid.Discharge(p)
+    g1.advance(1)
+    c1 = g1.counters()
+    assert c1["ion_pushes"] == p["n_particles"] + c1["births_iz"]
+    g1.close()
+
+
+def test_ion_kernels_have_their_own_profile_interval():
+    from paper_1508_02892_gb300 import hybrid
+    p = _kinetic(n_particles=5000, n_cells=60)
+    b = hybrid.Batch(2, hybrid.HYB_FP64)
+    s = b.admit(p)
+    b.set_tuning(lanes=1)
+    b.set_profiling(True)
+    b.advance(40)
+    prof = b.profile()
+    assert prof["n_ion"] == prof["n_electron"] == 40 and prof["ms_ion"] > 0
+    c = b.counters(s)
+    assert c["ion_pushes"] > 40 * p["n_particles"] // 2
+    b.close()
 
 
 def test_fp64_kinetic_ions_ragged_and_resorted():
