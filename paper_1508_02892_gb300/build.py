@@ -1,6 +1,6 @@
 """Build the CUDA library libhybrid1d.so for sm_103a (in-tree, no cmake).
 
-The three translation units are compiled in parallel with nvcc and linked into
+The translation units are compiled in parallel with nvcc and linked into
 ``paper_1508_02892_gb300/_build/libhybrid1d.so``.  Host code is compiled with
 ``-ffp-contract=off`` so that the host-side derived constants do not depend on
 the host CPU (x86 here, Arm on the GPU machines).
@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhybrid1d.so")
-SOURCES = ["hyb_electron.cu", "hyb_field.cu", "hyb_api.cu", "hyb_noalloc.cu", "hyb_swarm.cu"]
+SOURCES = ["hyb_electron.cu", "hyb_ion.cu", "hyb_field.cu", "hyb_api.cu", "hyb_noalloc.cu", "hyb_swarm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -47,7 +47,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     lib = LIB
     extra = []
     os.makedirs(out_dir, exist_ok=True)
-    headers = [os.path.join(CSRC, "hyb_internal.cuh"), os.path.join(ROOT, "include", "hybrid1d.h")]
+    headers = [os.path.join(CSRC, "hyb_internal.cuh"), os.path.join(CSRC, "hyb_device.cuh"),
+               os.path.join(ROOT, "include", "hybrid1d.h")]
     objs = []
     jobs = []
     for src in SOURCES:

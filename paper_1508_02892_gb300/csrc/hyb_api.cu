@@ -203,8 +203,13 @@ Layout layout_of(const hyb_params &p)
         add(8 * (size_t)G);                             // acc_met
     }
     if (p.ion_model == HYB_ION_KINETIC) {
-        for (int b = 0; b < 2; ++b)
-            for (int k = 0; k < 5; ++k) add(8 * cap);   // ion z, vx, vy, vz, id
+        for (int b = 0; b < 2; ++b) {                   // ion buffers in the batch's precision
+            if (p.precision == HYB_FP32_SPLIT)
+                for (int k = 0; k < 5; ++k) add(4 * cap);  // c, o, vx, vy, vz
+            else
+                for (int k = 0; k < 4; ++k) add(8 * cap);  // z, vx, vy, vz
+            add(8 * cap);                                  // id
+        }
         add(4 * (size_t)G);                             // ion cell counts
         add(8 * (size_t)G);                             // dep_ni
         add(8 * (size_t)G);                             // dep_gi
@@ -327,6 +332,15 @@ void derive(const hyb_params &p, InstDev &K, std::vector<double> &xs, std::vecto
         K.nu_max_i = swarm_nu_bound(K.ngas, K.mi_red, 100.0);
         K.p_max_i = -expm1(-K.nu_max_i * K.dt);
         K.vt_gas = sqrt(kKb * p.gas_temp_k / K.m_gas);
+        K.fi_qm_dt = (float)(kQe / K.m_ion * K.dt);
+        K.fi_ngas = (float)K.ngas;
+        K.fi_half_mr_q = (float)(0.5 * K.mi_red / kQe);
+        K.fi_numax = (float)K.nu_max_i;
+        K.fi_pmax = (float)K.p_max_i;
+        K.fi_vt = (float)K.vt_gas;
+        K.fi_cm_a = (float)(K.m_ion / (K.m_ion + K.m_gas));
+        K.fi_cm_b = (float)(K.m_gas / (K.m_ion + K.m_gas));
+        K.fi_nu0 = (float)(K.ngas * 7.63e-20 * sqrt(2.0 * kQe / K.mi_red));
     }
     // recombination (Sec. II.D): sigma_rec v bounded on each table segment by the
     // larger endpoint cross section times the speed at the upper end
@@ -402,10 +416,18 @@ void bind_pointers(const hyb_params &p, const Layout &L, char *base, InstDev &K,
         for (int b = 0; b < 2; ++b) {
             PartBuf &B = I.buf[b];
             memset(&B, 0, sizeof B);
-            B.z = (double *)(base + L.off[k++]);
-            B.vxd = (double *)(base + L.off[k++]);
-            B.vyd = (double *)(base + L.off[k++]);
-            B.vzd = (double *)(base + L.off[k++]);
+            if (p.precision == HYB_FP32_SPLIT) {
+                B.c = (int32_t *)(base + L.off[k++]);
+                B.o = (float *)(base + L.off[k++]);
+                B.vxf = (float *)(base + L.off[k++]);
+                B.vyf = (float *)(base + L.off[k++]);
+                B.vzf = (float *)(base + L.off[k++]);
+            } else {
+                B.z = (double *)(base + L.off[k++]);
+                B.vxd = (double *)(base + L.off[k++]);
+                B.vyd = (double *)(base + L.off[k++]);
+                B.vzd = (double *)(base + L.off[k++]);
+            }
             B.id = (uint64_t *)(base + L.off[k++]);
         }
         I.cell_cnt = (int32_t *)(base + L.off[k++]);
@@ -591,7 +613,8 @@ int launch_step(hyb_batch *b, int k, int lane, cudaStream_t s)
     if (b->profiling && (rc = record(s, lane_event(b, lane, e + 1)))) return rc;
     if (b->any_kin) {  // the ions of the step, after the electrons' births
         CK(launch_ion_prefix(lane_inst_ion(b, lane), n, lane_prefix_ion(b, lane), s));
-        CK(launch_ion_step(lane_inst_ion(b, lane), n, lane_prefix_ion(b, lane), 0, b->cfg.grid, b->max_nodes, s));
+        CK(launch_ion_step(lane_inst_ion(b, lane), n, lane_prefix_ion(b, lane), 0, b->cfg.grid, b->max_nodes,
+                           b->precision, s));
     }
     if (b->profiling && (rc = record(s, lane_event(b, lane, e + 2)))) return rc;
     CK(launch_field(lane_inst(b, lane), n, lane_prefix(b, lane), lane_ticket(b, lane), b->precision == HYB_FP32_SPLIT,
@@ -608,9 +631,9 @@ int launch_sort_all(hyb_batch *b, int j, int lane, cudaStream_t s)
     const size_t s0 = 4 * (size_t)chunk_len(b) + 2 * (size_t)j;
     if (b->profiling && (rc = record(s, lane_event(b, lane, s0)))) return rc;
     CK(launch_sort(lane_inst(b, lane), lane_count(b, lane), lane_prefix(b, lane), b->precision, b->cfg, s));
-    if (b->any_kin) {  // compaction and cell sort of the ions (FP64 layout)
+    if (b->any_kin) {  // compaction and cell sort of the ions (the batch's layout)
         CK(launch_ion_prefix(lane_inst_ion(b, lane), lane_count(b, lane), lane_prefix_ion(b, lane), s));
-        CK(launch_sort(lane_inst_ion(b, lane), lane_count(b, lane), lane_prefix_ion(b, lane), HYB_FP64, b->cfg, s));
+        CK(launch_sort(lane_inst_ion(b, lane), lane_count(b, lane), lane_prefix_ion(b, lane), b->precision, b->cfg, s));
     }
     if (b->profiling && (rc = record(s, lane_event(b, lane, s0 + 1)))) return rc;
     return HYB_OK;
@@ -735,7 +758,7 @@ int reinit_slot(hyb_batch *b, int slot, bool sort)
     if (b->slots[slot].h.ion) {  // kinetic ions: their charge assignment first
         InstDev *I = &b->d_inst_ion[slot];
         CK(launch_prefix_one(I, b->d_prefix1_ion, b->stream));
-        CK(launch_ion_step(I, 1, b->d_prefix1_ion, 1, b->cfg.grid, b->max_nodes, b->stream));
+        CK(launch_ion_step(I, 1, b->d_prefix1_ion, 1, b->cfg.grid, b->max_nodes, b->precision, b->stream));
     }
     CK(launch_field(K, 1, b->d_prefix1, b->d_ticket1, b->precision == HYB_FP32_SPLIT, b->max_nodes, b->field_threads,
                     b->stream));
@@ -841,12 +864,12 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     const bool kin = p->ion_model == HYB_ION_KINETIC;
     if (kin) {
         // the ion descriptor: the electron one's constants and grids, the ion
-        // buffers bound above, FP64 particles, its own counts
+        // buffers bound above, particles in the batch's precision, its own counts
         InstDev I = S.h;
         I.buf[0] = S.hi.buf[0];
         I.buf[1] = S.hi.buf[1];
         I.cell_cnt = S.hi.cell_cnt;
-        I.precision = HYB_FP64;
+        I.precision = p->precision;
         I.cur = 0;
         I.n_slots = (unsigned long long)p->n_particles;
         I.n_slots_step = p->n_particles;
@@ -1166,14 +1189,12 @@ int read_counters(hyb_batch *b, int slot, hyb_counters *c)
     return rc;
 }
 
-int read_particles(hyb_batch *b, int slot, double *z, double *vx, double *vy, double *vz, uint64_t *id, int64_t cap,
-                   int64_t *n)
+// The live particles of descriptor K's first ns slots, sorted by id, into
+// host arrays of cap entries (any may be NULL); split-mode positions become
+// z = (c + o) dz.
+int gather_sorted(const InstDev &K, int64_t ns, double *z, double *vx, double *vy, double *vz, uint64_t *id,
+                  int64_t cap, int64_t *n, const char *what)
 {
-    int rc = check_slot(b, slot);
-    if (rc) return rc;
-    rc = sync_status(b, slot);
-    const InstDev &K = b->h_stage[slot];
-    const int64_t ns = (int64_t)K.n_slots;
     const PartBuf P = K.buf[K.cur];
     std::vector<double> hz(ns), hx(ns), hy(ns), hv(ns);
     std::vector<uint64_t> hid(ns);
@@ -1209,7 +1230,7 @@ int read_particles(hyb_batch *b, int slot, double *z, double *vx, double *vy, do
         if (alive[i]) idx.push_back(i);
     std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t c) { return hid[a] < hid[c]; });
     *n = (int64_t)idx.size();
-    if (*n > cap) return fail(HYB_ERR_ARG, "%lld live particles exceed the buffers (%lld)", (long long)*n, (long long)cap);
+    if (*n > cap) return fail(HYB_ERR_ARG, "%lld %s exceed the buffers (%lld)", (long long)*n, what, (long long)cap);
     for (size_t k = 0; k < idx.size(); ++k) {
         const int64_t i = idx[k];
         if (z) z[k] = hz[i];
@@ -1218,7 +1239,18 @@ int read_particles(hyb_batch *b, int slot, double *z, double *vx, double *vy, do
         if (vz) vz[k] = hv[i];
         if (id) id[k] = hid[i];
     }
-    return rc;
+    return HYB_OK;
+}
+
+int read_particles(hyb_batch *b, int slot, double *z, double *vx, double *vy, double *vz, uint64_t *id, int64_t cap,
+                   int64_t *n)
+{
+    int rc = check_slot(b, slot);
+    if (rc) return rc;
+    rc = sync_status(b, slot);
+    const InstDev &K = b->h_stage[slot];
+    const int rg = gather_sorted(K, (int64_t)K.n_slots, z, vx, vy, vz, id, cap, n, "live particles");
+    return rg ? rg : rc;
 }
 
 // the kinetic ions of a slot, alive ones sorted by id
@@ -1231,32 +1263,8 @@ int read_ions(hyb_batch *b, int slot, double *z, double *vx, double *vy, double 
     rc = sync_status(b, slot);
     InstDev I{};
     CK(cudaMemcpy(&I, &b->d_inst_ion[slot], sizeof I, cudaMemcpyDeviceToHost));
-    const int64_t ns = std::min((int64_t)I.n_slots, I.capacity);
-    const PartBuf P = I.buf[I.cur];
-    std::vector<double> hz(ns), hx(ns), hy(ns), hv(ns);
-    std::vector<uint64_t> hid(ns);
-    if (ns > 0) {
-        CK(cudaMemcpy(hid.data(), P.id, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(hz.data(), P.z, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(hx.data(), P.vxd, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(hy.data(), P.vyd, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(hv.data(), P.vzd, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
-    }
-    std::vector<int64_t> idx;
-    for (int64_t i = 0; i < ns; ++i)
-        if (hz[i] >= 0.0) idx.push_back(i);
-    std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t c) { return hid[a] < hid[c]; });
-    *n = (int64_t)idx.size();
-    if (*n > cap) return fail(HYB_ERR_ARG, "%lld ions exceed the buffers (%lld)", (long long)*n, (long long)cap);
-    for (size_t k = 0; k < idx.size(); ++k) {
-        const int64_t i = idx[k];
-        if (z) z[k] = hz[i];
-        if (vx) vx[k] = hx[i];
-        if (vy) vy[k] = hy[i];
-        if (vz) vz[k] = hv[i];
-        if (id) id[k] = hid[i];
-    }
-    return rc;
+    const int rg = gather_sorted(I, std::min((int64_t)I.n_slots, I.capacity), z, vx, vy, vz, id, cap, n, "ions");
+    return rg ? rg : rc;
 }
 
 // the metastable density, its time average and the last wall fluxes of a slot
@@ -1535,8 +1543,11 @@ hyb_batch *hyb_discharge_batch(hyb_discharge *h) { return h ? h->b : nullptr; }
 int hyb_debug_checks(uint64_t out[6])
 {
     if (!out) return fail(HYB_ERR_ARG, "NULL output");
-    unsigned long long e[3], f[3];
+    unsigned long long e[3], f[3], g[3];
     read_checks_electron(e);
+    read_checks_ion(g);
+    if (e[0] == 0 && e[1] == 0 && e[2] == 0)  // the particle kernels: electrons first, then the ions
+        for (int k = 0; k < 3; ++k) e[k] = g[k];
     read_checks_field(f);
     for (int k = 0; k < 3; ++k) {
         out[k] = e[k];

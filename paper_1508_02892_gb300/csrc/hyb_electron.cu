@@ -13,55 +13,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "hyb_internal.cuh"
+#include "hyb_device.cuh"
 
 namespace hyb {
 
 namespace {
-
-constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kBlock = 256;
-
-__device__ __forceinline__ unsigned lanemask_lt()
-{
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-template <typename T>
-struct WarpSum;
-
-template <>
-struct WarpSum<double> {
-    __device__ static double run(double v)
-    {
-#pragma unroll
-        for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
-        return v;
-    }
-};
-
-// Add (w0 at node c, w1 at node c+1) for every lane that has `on`; when every
-// participating lane has the same c, sum over the warp first.
-template <typename T>
-__device__ __forceinline__ void deposit_pair(T *arr, bool on, int c, T w0, T w1, int G)
-{
-    if (on && !HYB_CHECK(c >= 0 && c + 1 < G, 4, c, G)) on = false;
-    const int kmin = __reduce_min_sync(kFull, on ? c : INT32_MAX);
-    const int kmax = __reduce_max_sync(kFull, on ? c : -1);
-    if (kmin == kmax) {
-        T a = WarpSum<T>::run(on ? w0 : T(0));
-        T b = WarpSum<T>::run(on ? w1 : T(0));
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&arr[kmin], a);
-            atomicAdd(&arr[kmin + 1], b);
-        }
-    } else if (on) {
-        atomicAdd(&arr[c], w0);
-        atomicAdd(&arr[c + 1], w1);
-    }
-}
 
 // Per-thread event counts; the split kernel packs two 16-bit counts per word
 // (a thread handles far fewer than 65536 particles of one segment).
@@ -147,18 +103,14 @@ __device__ __forceinline__ void append_children<double>(InstDev *K, const PartBu
     }
 }
 
-// Kinetic ions: one new ion per ionization, at the new electron's position z,
-// id = the new electron's id, velocity from the gas Maxwellian (draw call 4
-// at the step); one atomic per warp on the ion descriptor.  All lanes call.
-__device__ __forceinline__ void gauss_pair(double u1, double u2, double &g1, double &g2)
-{
-    const double r = sqrt(-2.0 * log(u1));
-    const double ph = kTwoPi * u2;
-    g1 = r * cos(ph);
-    g2 = r * sin(ph);
-}
-
-__device__ __forceinline__ void append_ion(InstDev *K, bool has, double z, uint64_t cid, uint32_t step)
+// Kinetic ions: one new ion per ionization, at the new electron's position
+// (z, or its cell and offset in split mode), id = the new electron's id,
+// velocity from the gas Maxwellian (draw call 4 at the step); one atomic per
+// warp on the ion descriptor.  All lanes call.  The ions are in the batch's
+// precision: FP64 beside FP64 electrons, split beside split ones.
+template <int PREC>
+__device__ __forceinline__ void append_ion(InstDev *K, bool has, int c, float o, double z, uint64_t cid,
+                                           uint32_t step)
 {
     InstDev *I = K->ion;
     if (!I) return;  // a discharge with fluid ions in a batch that has kinetic ones
@@ -176,15 +128,28 @@ __device__ __forceinline__ void append_ion(InstDev *K, bool has, double z, uint6
         return;
     }
     const uint4 a = draw(cid, step, K->seed_lo, K->seed_hi, 4);
-    double g1, g2, g3, g4;
-    gauss_pair(u01d(a.x), u01d(a.y), g1, g2);
-    gauss_pair(u01d(a.z), u01d(a.w), g3, g4);
     const PartBuf P = I->buf[I->cur];
-    P.z[slot] = z;
-    P.vxd[slot] = K->vt_gas * g1;
-    P.vyd[slot] = K->vt_gas * g2;
-    P.vzd[slot] = K->vt_gas * g3;
     P.id[slot] = cid;
+    if (PREC == HYB_FP32_SPLIT) {
+        float s1, c1;
+        const float r1 = sqrtf(-2.f * __logf(u01f(a.x)));
+        __sincosf(6.283185307179586f * u01f(a.y), &s1, &c1);
+        const float r2 = sqrtf(-2.f * __logf(u01f(a.z)));
+        const float vt = K->fi_vt;
+        P.c[slot] = c;
+        P.o[slot] = o;
+        P.vxf[slot] = vt * (r1 * c1);
+        P.vyf[slot] = vt * (r1 * s1);
+        P.vzf[slot] = vt * (r2 * __cosf(6.283185307179586f * u01f(a.w)));
+    } else {
+        double g1, g2, g3, g4;
+        gauss_pair(u01d(a.x), u01d(a.y), g1, g2);
+        gauss_pair(u01d(a.z), u01d(a.w), g3, g4);
+        P.z[slot] = z;
+        P.vxd[slot] = K->vt_gas * g1;
+        P.vyd[slot] = K->vt_gas * g2;
+        P.vzd[slot] = K->vt_gas * g3;
+    }
 }
 
 // ------------------------------------------------------------ FP32 split
@@ -535,7 +500,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 }
                 unsigned ovf = 0;
                 append_children<float>(K, P, capacity, has_child, ck, ok, 0.0, cvx, cvy, cvz, cid, ovf);
-                if (KIN) append_ion(K, has_child, ((double)ck + (double)ok) * K->dz, cid, step);
+                if (KIN) append_ion<HYB_FP32_SPLIT>(K, has_child, ck, ok, 0.0, cid, step);
                 cnt.push_ovf |= ovf << 16;
                 coll &= ~(3u << (2 * k));
             }
@@ -568,18 +533,6 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
 //
 // Same step in FP64 with the position z, written in the same order of
 // operations as a plain FP64 program would use, so the two agree to rounding.
-
-__device__ __forceinline__ void locate_d(double z, double dz, int nc, int &c, double &o)
-{
-    const double x = z / dz;
-    const double f = floor(x);
-    c = (int)f;
-    o = x - f;
-    if (c >= nc) {
-        c = nc - 1;
-        o = 1.0;
-    }
-}
 
 // sigma_rec(E) with the same log-index, linear-in-energy lookup
 __device__ __forceinline__ double xs_rec_d(const double *__restrict__ xr, const double *__restrict__ xs, int n,
@@ -625,16 +578,6 @@ __device__ __forceinline__ void xs_eval_d(const double *__restrict__ xs, int n, 
     for (int k = 0; k < 3; ++k) sig[k] = xs[4 * i + 1 + k] + f * (xs[4 * (i + 1) + 1 + k] - xs[4 * i + 1 + k]);
     if (en < e_exc) sig[1] = 0.0;
     if (en < e_iz) sig[2] = 0.0;
-}
-
-__device__ __forceinline__ void iso_dir_d(double u_cos, double u_phi, double d[3])
-{
-    const double ct = 1.0 - 2.0 * u_cos;
-    const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-    const double ph = kTwoPi * u_phi;
-    d[0] = st * cos(ph);
-    d[1] = st * sin(ph);
-    d[2] = ct;
 }
 
 template <int MODE, bool CHEM, bool KIN>
@@ -785,7 +728,7 @@ __device__ void segment_fp64(InstDev *K, int64_t a, int64_t b, unsigned char *sm
         }
         if (MODE == 0) {
             append_children<double>(K, P, capacity, has_child, 0, 0.0, z, cvx, cvy, cvz, cid, cnt.overflow);
-            if (KIN) append_ion(K, has_child, z, cid, step);
+            if (KIN) append_ion<HYB_FP64>(K, has_child, 0, 0.f, z, cid, step);
             if (alive) {
                 P.z[i] = z;
                 P.vxd[i] = vx;
@@ -897,40 +840,6 @@ __device__ void flush_segment(InstDev *K, unsigned char *smem, const SegCounters
     __syncthreads();
 }
 
-// This block's contiguous run of kChunk-slot chunks, split by instance:
-// fn(K, a, b) for each instance touched, with a a multiple of kChunk.
-template <class F>
-__device__ __forceinline__ void for_block_runs(InstDev *__restrict__ insts, int n_max,
-                                               const int64_t *__restrict__ prefix, F &&fn)
-{
-    const int64_t total = prefix[n_max];
-    if (total <= 0) return;
-    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
-    const int64_t c0 = (int64_t)blockIdx.x * per;
-    if (c0 >= total) return;
-    const int64_t c1 = c0 + per < total ? c0 + per : total;
-    int lo = 0, hi = n_max;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (prefix[mid] <= c0)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    int64_t ch = c0;
-    for (int i = lo; i < n_max && ch < c1; ++i) {
-        const int64_t p0 = prefix[i], p1 = prefix[i + 1];
-        if (p1 <= ch) continue;
-        const int64_t e = c1 < p1 ? c1 : p1;
-        InstDev *K = &insts[i];
-        const int64_t n = K->n_slots_step;
-        const int64_t a = (ch - p0) * kChunk;
-        const int64_t b = (e - p0) * kChunk < n ? (e - p0) * kChunk : n;
-        if (HYB_CHECK(p1 - p0 == chunks_of(n) && (K->cur & ~1) == 0, 12, i, p1 - p0)) fn(K, a, b);
-        ch = e;
-    }
-}
-
 template <int PREC, int MODE, bool CHEM = false, bool KIN = false>
 __global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 3 : 2) k_electron(InstDev *__restrict__ insts,
                                                                                        int n_max,
@@ -987,174 +896,6 @@ __global__ void k_load(InstDev *K, int64_t n, double vth, int prec)
             P.vzd[j] = vz;
         }
     }
-}
-
-// ------------------------------------------------------------ kinetic ions
-// The paper's fully kinetic comparison model: He+ macroparticles with the
-// electrons' weight, FP64, in a second descriptor per discharge.  Each step,
-// after the electrons: push in E^n (CIC gather, leapfrog), removal at the
-// walls (their counts are the wall fluxes), CIC assignment of the ion density
-// and flux, and collisions with the gas as in the auxiliary Monte Carlo of
-// Sec. II.C: null collision against a neutral from the gas Maxwellian,
-// acceptance on N Q_m(eps) g with Q_m = Q_i + 2 Q_b, isotropic in the
-// centre-of-mass frame (draw calls 5 and 6 at the step).
-
-// N Q_m(eps) g for He+ on He; eps = M_r g^2 / 2 in eV
-__device__ __forceinline__ double ion_nu(double ngas, double m_red, double g)
-{
-    if (!(g > 0.0)) return ngas * 7.63e-20 * sqrt(2.0 * kQe / m_red);
-    const double eps = 0.5 * m_red * g * g / kQe;
-    double q = 7.63e-20 / sqrt(eps);
-    q += 2.0 * (1e-19 / (pow(eps / 1000.0, 0.15) * pow(1.0 + eps / 1000.0, 0.25) * pow(1.0 + 5.0 / eps, 0.15)));
-    return ngas * q * g;
-}
-
-// ions [a, b) of ion descriptor I; ctr: losses at z = 0, at z = L,
-// collision candidates, real collisions, pushes.  MODE 1: charge assignment only.
-template <int MODE>
-__device__ void segment_ion(InstDev *I, int64_t a, int64_t b, unsigned char *smem, unsigned ctr[5])
-{
-    InstDev *K = I->elec;
-    const int G = K->G, nc = K->n_cells;
-    const double dz = K->dz, dt = K->dt, L = K->L;
-    const double *__restrict__ E = K->E;
-    const uint32_t step = (uint32_t)K->step;
-    const uint32_t sl = K->seed_lo, sh = K->seed_hi;
-    const double M = K->m_ion, mn = K->m_gas, ngas = K->ngas, mr = K->mi_red;
-    const double numax = K->nu_max_i, pmax = K->p_max_i, vt = K->vt_gas;
-    const PartBuf P = I->buf[I->cur];
-    double *sd_n = reinterpret_cast<double *>(smem);
-    double *sd_g = sd_n + G;
-    if (!HYB_CHECK(b <= I->capacity && a >= 0, 14, b, I->capacity)) b = a;
-    for (int j = threadIdx.x; j < 2 * G; j += blockDim.x) sd_n[j] = 0.0;
-    __syncthreads();
-    for (int64_t base = a; base < b; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        double z = i < b ? P.z[i] : -1.0;
-        bool alive = z >= 0.0 && z < L;
-        double vx = 0.0, vy = 0.0, vz = 0.0;
-        uint64_t id = 0;
-        if (alive) {
-            vx = P.vxd[i];
-            vy = P.vyd[i];
-            vz = P.vzd[i];
-            if (MODE == 0) id = P.id[i];
-        }
-        int c = 0;
-        double o = 0.0;
-        if (MODE == 0 && alive) {
-            ++ctr[4];
-            locate_d(z, dz, nc, c, o);
-            const double ep = (1.0 - o) * E[c] + o * E[c + 1];
-            vz = vz + (kQe / M) * ep * dt;
-            z = z + vz * dt;
-            if (!(z >= 0.0 && z < L)) {
-                ++ctr[z < 0.0 ? 0 : 1];
-                alive = false;
-                P.z[i] = -1.0;
-            }
-        }
-        if (alive) locate_d(z, dz, nc, c, o);
-        deposit_pair<double>(sd_n, alive, c, 1.0 - o, o, G);
-        deposit_pair<double>(sd_g, alive, c, (1.0 - o) * vz, o * vz, G);
-        if (MODE == 0 && alive) {
-            const uint4 u = draw(id, step, sl, sh, 5);
-            if (u01d(u.x) < pmax) {
-                ++ctr[2];
-                const uint4 w = draw(id, step, sl, sh, 6);
-                double b1, b2, b3, b4;
-                gauss_pair(u01d(u.z), u01d(u.w), b1, b2);
-                gauss_pair(u01d(w.x), u01d(w.y), b3, b4);
-                const double Vx = vt * b1, Vy = vt * b2, Vz = vt * b3;
-                const double gx = vx - Vx, gy = vy - Vy, gz = vz - Vz;
-                const double g = sqrt(gx * gx + gy * gy + gz * gz);
-                if (u01d(u.y) * numax < ion_nu(ngas, mr, g)) {
-                    ++ctr[3];
-                    double d[3];
-                    iso_dir_d(u01d(w.z), u01d(w.w), d);
-                    vx = (M * vx + mn * Vx) / (M + mn) + mn / (M + mn) * g * d[0];
-                    vy = (M * vy + mn * Vy) / (M + mn) + mn / (M + mn) * g * d[1];
-                    vz = (M * vz + mn * Vz) / (M + mn) + mn / (M + mn) * g * d[2];
-                }
-            }
-            P.z[i] = z;
-            P.vxd[i] = vx;
-            P.vyd[i] = vy;
-            P.vzd[i] = vz;
-        }
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < G; j += blockDim.x) {
-        if (sd_n[j] != 0.0) atomicAdd(&K->dep_ni[j], sd_n[j]);
-        if (sd_g[j] != 0.0) atomicAdd(&K->dep_gi[j], sd_g[j]);
-    }
-    __syncthreads();
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(kBlock) k_ion(InstDev *__restrict__ ions, int n_max, const int64_t *__restrict__ prefix)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned s_c[5];
-    for_block_runs(ions, n_max, prefix, [&](InstDev *I, int64_t a, int64_t b) {
-        unsigned ctr[5] = {0u, 0u, 0u, 0u, 0u};
-        if (threadIdx.x < 5) s_c[threadIdx.x] = 0u;
-        segment_ion<MODE>(I, a, b, smem, ctr);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const unsigned t = __reduce_add_sync(kFull, ctr[k]);
-            if ((threadIdx.x & 31) == 0 && t) atomicAdd(&s_c[k], t);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && MODE == 0) {
-            const int map[5] = {C_LOSS0, C_LOSS1, C_NULL, C_EL, C_PUSH};
-#pragma unroll
-            for (int k = 0; k < 5; ++k)
-                if (s_c[k]) atomicAdd(&I->ctr[map[k]], (unsigned long long)s_c[k]);
-        }
-        __syncthreads();
-    });
-}
-
-// ions 0..n-1 of a discharge: ids 2^61 + i, uniform in [0, L), gas
-// Maxwellian; draws at step 0xFFFFFFFF, calls 4 and 5
-__global__ void k_load_ions(InstDev *I, int64_t n)
-{
-    const PartBuf P = I->buf[I->cur];
-    if (!HYB_CHECK(n <= I->capacity, 9, n, I->capacity)) return;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t id = (1ull << 61) + (uint64_t)j;
-        const uint4 a = draw(id, 0xFFFFFFFFu, I->seed_lo, I->seed_hi, 4);
-        const uint4 b = draw(id, 0xFFFFFFFFu, I->seed_lo, I->seed_hi, 5);
-        double g1, g2, g3, g4;
-        gauss_pair(u01d(a.y), u01d(a.z), g1, g2);
-        gauss_pair(u01d(b.x), u01d(b.y), g3, g4);
-        P.z[j] = u01d(a.x) * I->L;
-        P.vxd[j] = I->vt_gas * g1;
-        P.vyd[j] = I->vt_gas * g2;
-        P.vzd[j] = I->vt_gas * g3;
-        P.id[j] = id;
-    }
-}
-
-// the ions to step now are all slots in use (including this step's births),
-// and an ion descriptor runs while its discharge does
-__global__ void __launch_bounds__(HYB_MAX_INSTANCES) k_ion_prefix(InstDev *ions, int n_max, int64_t *prefix)
-{
-    __shared__ int64_t s_buf[HYB_MAX_INSTANCES];
-    const int t = threadIdx.x;
-    if (t < n_max) {
-        InstDev *I = &ions[t];
-        if (I->elec) {
-            I->active = I->elec->active;
-            const int64_t n = (int64_t)I->n_slots;
-            I->n_slots_step = n < I->capacity ? n : I->capacity;
-        } else {
-            I->active = 0;
-        }
-    }
-    __syncthreads();
-    block_chunk_prefix(ions, n_max, prefix, s_buf);
 }
 
 // --------------------------------------------------------------- cell sort
@@ -1329,8 +1070,7 @@ void configure_kernels()
     cudaFuncSetAttribute(k_electron<HYB_FP64, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_electron<HYB_FP64, 0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_ion<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_ion<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    configure_ion_kernels();
     configure_field_kernel();
 }
 
@@ -1420,32 +1160,6 @@ cudaError_t launch_prefix_one(InstDev *inst, int64_t *prefix, cudaStream_t s)
 cudaError_t launch_set_active(InstDev *inst, int active, int64_t target_step, cudaStream_t s)
 {
     k_set_active<<<1, 32, 0, s>>>(inst, active, target_step);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_load_ions(InstDev *ion, int64_t n, cudaStream_t s)
-{
-    if (n <= 0) return cudaSuccess;
-    int grid = (int)((n + 255) / 256);
-    if (grid > 4096) grid = 4096;
-    k_load_ions<<<grid, 256, 0, s>>>(ion, n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ion_prefix(InstDev *ions, int n_max, int64_t *prefix, cudaStream_t s)
-{
-    k_ion_prefix<<<1, HYB_MAX_INSTANCES, 0, s>>>(ions, n_max, prefix);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ion_step(InstDev *ions, int n_max, const int64_t *prefix, int mode, int grid, int max_nodes,
-                            cudaStream_t s)
-{
-    const size_t smem = 16 * (size_t)max_nodes;
-    if (mode == 0)
-        k_ion<0><<<grid, kBlock, smem, s>>>(ions, n_max, prefix);
-    else
-        k_ion<1><<<grid, kBlock, smem, s>>>(ions, n_max, prefix);
     return cudaGetLastError();
 }
 

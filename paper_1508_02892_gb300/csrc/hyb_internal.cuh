@@ -87,12 +87,16 @@ struct InstDev {
     double rec_numax, rec_pmax;       // max n_i * rec_svmax and 1 - exp(-rec_numax dt), for the next step
     float f_rec_pmax, pad2;
     // kinetic ions (HYB_ION_KINETIC): the ion population lives in a second
-    // descriptor of this layout (FP64 particles, its own sort buffers and
-    // counters) that points back to the electron one
+    // descriptor of this layout (particles in the batch's precision, its own
+    // sort buffers and counters) that points back to the electron one
     InstDev *ion;                     // electron descriptor: its ions (NULL: fluid ions)
     InstDev *elec;                    // ion descriptor: its electrons
     double *dep_ni, *dep_gi;          // per-step CIC sums of the ions: count and v_z
     double mi_red, nu_max_i, p_max_i, vt_gas;
+    // FP32 copies for the split-mode ion kernel: (e/M) dt, N, 0.5 M_r / e,
+    // the collision bound, P_max, gas thermal speed, M/(M+m), m/(M+m), and
+    // N Q_m g in the limit g -> 0
+    float fi_qm_dt, fi_ngas, fi_half_mr_q, fi_numax, fi_pmax, fi_vt, fi_cm_a, fi_cm_b, fi_nu0, pad4;
     // metastables and the ionization they cause (Sec. II.D)
     int32_t met_on, pad3;
     double met_D, met_kp, met_kq;     // D, R_P n_N, R_pool
@@ -247,13 +251,15 @@ struct LaunchCfg {
 cudaError_t launch_electron_step(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
                                  cudaStream_t s,
                                  bool chem = false, bool kin = false);
-// kinetic ions: initial load, the per-step snapshot prefix over a lane's ion
-// descriptors, and the ion step (mode 0) or deposit alone (mode 1)
+// kinetic ions (hyb_ion.cu): initial load, the per-step snapshot prefix over a
+// lane's ion descriptors, and the ion step (mode 0) or deposit alone (mode 1)
 cudaError_t launch_load_ions(InstDev *ion, int64_t n, cudaStream_t s);
 double swarm_nu_bound(double ngas, double m_red, double eps_max);
 cudaError_t launch_ion_prefix(InstDev *ions, int n_max, int64_t *prefix, cudaStream_t s);
 cudaError_t launch_ion_step(InstDev *ions, int n_max, const int64_t *prefix, int mode, int grid, int max_nodes,
-                            cudaStream_t s);
+                            int precision, cudaStream_t s);
+void configure_ion_kernels();
+void read_checks_ion(unsigned long long out[3]);
 cudaError_t launch_deposit_init(InstDev *inst, int n_max, const int64_t *prefix, int precision, LaunchCfg cfg,
                                 cudaStream_t s);
 cudaError_t launch_load(InstDev *inst, int64_t n, double vth, int precision, cudaStream_t s);

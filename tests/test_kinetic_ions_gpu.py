@@ -5,9 +5,10 @@ FP64: the electrons, the ions (by id), every counter, the fields and the
 moments agree with the oracle to the tolerances of the other FP64 parity tests
 (1e-12 per particle, 1e-11 on grids); both sides draw the same Philox numbers
 (ion birth velocity call 4, ion collisions calls 5 and 6).  Inside a batch
-with fluid-ion discharges every discharge gives what it gives alone.  FP32
-split electrons with FP64 ions: exact ion bookkeeping and the ion count within
-a few per cent of the oracle's.
+with fluid-ion discharges every discharge gives what it gives alone.  Split
+mode (electrons and ions as cell + FP32 offset, FP32 velocities): exact ion
+bookkeeping, and the ion count, collisions and profiles within a few per cent
+of the oracle's.
 """
 import numpy as np
 import pytest
@@ -154,10 +155,12 @@ def test_kinetic_and_fluid_discharges_share_a_batch():
         b.close()
 
 
-def test_split_electrons_with_kinetic_ions():
-    """FP32 split electrons, FP64 ions: the ion count follows births minus
-    wall losses exactly, n_i integrates to w N_i, and over 300 steps the count
-    stays within 3 % of the FP64 oracle's."""
+def test_split_electrons_and_ions_track_the_oracle():
+    """Split mode: electrons and ions as cell + FP32 offset with FP32
+    velocities, the ion collisions in FP32.  The ion count follows births minus
+    wall losses exactly and n_i integrates to w N_i (FP32 sums); over 300
+    steps the ion count, the ion collisions, the time-averaged n_i profile and
+    the mean ion energy stay close to the FP64 oracle's."""
     from paper_1508_02892_gb300 import hybrid
     p = _kinetic(precision=W.FP32_SPLIT, n_particles=40000, seed=67)
     g, o = hybrid.Discharge(p), oracle.Oracle(p)
@@ -174,10 +177,47 @@ def test_split_electrons_with_kinetic_ions():
     dz = p["gap_m"] / (G - 1)
     dv = np.full(G, dz)
     dv[0] = dv[-1] = dz / 2
-    assert (ni * dv).sum() == pytest.approx(p["weight"] * c["ions"], rel=1e-12)
+    assert (ni * dv).sum() == pytest.approx(p["weight"] * c["ions"], rel=1e-5)
     ic = o.ion_counters()
     assert abs(c["ions"] - ic["ions"]) <= 0.03 * ic["ions"], (c["ions"], ic["ions"])
+    assert abs(c["ion_collisions"] - ic["collisions"]) <= 0.03 * ic["collisions"]
+    ma, mb = g.moments(), o.moments()
+    assert np.linalg.norm(ma["ni"] - mb["ni"]) / np.linalg.norm(mb["ni"]) < 0.02
+    oi = o.ions()
+    e_g = np.mean(ions["vx"] ** 2 + ions["vy"] ** 2 + ions["vz"] ** 2)
+    e_o = np.mean(oi["vx"] ** 2 + oi["vy"] ** 2 + oi["vz"] ** 2)
+    assert e_g == pytest.approx(e_o, rel=0.03)
     g.close()
+
+
+def test_split_batch_with_kinetic_and_fluid_discharges():
+    """A split batch holding kinetic and fluid discharges: every discharge
+    keeps its bookkeeping and matches its single run statistically."""
+    from paper_1508_02892_gb300 import hybrid
+    ps = [_kinetic(precision=W.FP32_SPLIT, n_particles=20000, n_cells=150, seed=81),
+          W.config1(precision=W.FP32_SPLIT, n_particles=20000, n_cells=120, seed=82, te0_ev=6.0),
+          _kinetic(precision=W.FP32_SPLIT, n_particles=8000, n_cells=90, seed=83, te0_ev=12.0)]
+    b = hybrid.Batch(3, hybrid.HYB_FP32_SPLIT)
+    b.set_tuning(lanes=2)
+    slots = [b.admit(q) for q in ps]
+    b.advance(200)
+    for s, q in zip(slots, ps):
+        ca = b.counters(s)
+        assert ca["status"] == 0 and ca["step"] == 200
+        g = hybrid.Discharge(q)
+        g.advance(200)
+        cb = g.counters()
+        if q["ion_model"] == W.ION_KINETIC:
+            assert ca["ions"] == q["n_particles"] + ca["births_iz"] - ca["ion_losses0"] - ca["ion_losses1"]
+            assert b.ions(s)["id"].size == ca["ions"]
+            assert abs(ca["ions"] - cb["ions"]) <= 0.03 * cb["ions"]
+        else:
+            assert ca["ions"] == 0
+        ma, mb = b.moments(s), g.moments()
+        for k in ("ne", "ni"):
+            assert np.linalg.norm(ma[k] - mb[k]) / np.linalg.norm(mb[k]) < 0.03, (s, k)
+        g.close()
+    b.close()
 
 
 def test_ion_density_is_not_writable_for_kinetic_ions():
