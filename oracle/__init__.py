@@ -132,6 +132,7 @@ def lib():
                 "orc_poisson": (None, [C.c_int, dbl, pd, dbl, dbl, pd, pd]),
                 "orc_fluid_update": (i64, [vp, pd, pd, pd, pd, pd]),
                 "orc_particle_step_one": (C.c_int, [vp, pd, u32, pd, u64, pd, pd, pu64]),
+                "orc_ion_step_one": (C.c_int, [vp, pd, u32, pd, u64, pd]),
                 "orc_swarm_run": (None, [C.POINTER(OrcSwarmParams), C.POINTER(OrcSwarmResult), pd]),
                 "orc_get_power": (None, [vp, pd, pi64]),
                 "orc_get_ion_counters": (None, [vp, pi64]),
@@ -376,6 +377,16 @@ class Oracle:
         i = np.zeros(2, dtype=np.int64)
         lib().orc_get_power(self.h, _dp(d), i.ctypes.data_as(C.POINTER(C.c_int64)))
         return {"v_rf": d[0], "p_last": d[1], "periods": int(i[0]), "steps_per_period": int(i[1])}
+
+    def ion_step_one(self, E, step, state4, iid):
+        """One kinetic ion's push, wall test and gas collision of step `step` in
+        the field E: (outcome, new state); outcome OUT_LOST0/1, or 0 (no
+        candidate), 1 (null collision), 2 (collided)."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        inp = np.ascontiguousarray(state4, dtype=np.float64)
+        out = np.zeros(4)
+        oc = lib().orc_ion_step_one(self.h, _dp(E), int(step), _dp(inp), int(iid), _dp(out))
+        return int(oc), out
 
     def particle_step_one(self, E, step, state4, pid):
         E = np.ascontiguousarray(E, dtype=np.float64)

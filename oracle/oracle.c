@@ -810,6 +810,67 @@ void orc_init_field(orc_sim *s)
     memset(s->dep_n, 0, sizeof(double) * s->G);
 }
 
+/* One ion's push in E (CIC gather, leapfrog); 1 or 2 if it left through
+ * z = 0 or z = L (then it is removed), else 0. */
+static int ion_push(const orc_sim *s, const double *E, part *q)
+{
+    int c;
+    double o;
+    locate(s, q->z, &c, &o);
+    double ep = (1.0 - o) * E[c] + o * E[c + 1];
+    q->vz = q->vz + (Q_E / s->m_ion) * ep * s->dt;
+    q->z = q->z + q->vz * s->dt;
+    if (q->z < 0.0) return 1;
+    if (q->z >= s->L) return 2;
+    return 0;
+}
+
+/* One ion's collision with the gas in step n (Sec. II.C): null-collision test
+ * R < P_max (call 5), a neutral from the gas Maxwellian (Box-Muller on calls 5
+ * and 6), acceptance on R' nu_max < N Q_m(eps) g, isotropic scattering in the
+ * centre-of-mass frame.  0: no candidate, 1: null collision, 2: collided. */
+static int ion_collide(const orc_sim *s, uint32_t n, part *q)
+{
+    const double M = s->m_ion, mn = s->m_gas;
+    double u[4], w[4];
+    draws(s, q->id, n, 5, u);
+    if (!(u[0] < s->p_max_i)) return 0;
+    draws(s, q->id, n, 6, w);
+    double b1, b2, b3, b4;
+    gauss2(u[2], u[3], &b1, &b2);
+    gauss2(w[0], w[1], &b3, &b4);
+    double V[3] = {s->vt_gas * b1, s->vt_gas * b2, s->vt_gas * b3};
+    double v[3] = {q->vx, q->vy, q->vz};
+    double gx = v[0] - V[0], gy = v[1] - V[1], gz = v[2] - V[2];
+    double g = sqrt(gx * gx + gy * gy + gz * gz);
+    double nu = orc_swarm_nu(s->ngas, s->mi_red, 0, g);
+    if (!(u[1] * s->nu_max_i < nu)) return 1;
+    double d[3];
+    iso_dir(w[2], w[3], d);
+    for (int k = 0; k < 3; ++k) v[k] = (M * v[k] + mn * V[k]) / (M + mn) + mn / (M + mn) * g * d[k];
+    q->vx = v[0];
+    q->vy = v[1];
+    q->vz = v[2];
+    return 2;
+}
+
+/* One ion's part of step n from `in` (z, vx, vy, vz) in the field E, for the
+ * tests that step sampled ions of a large run one by one: OUT_LOST0/1 if it
+ * left, else 0 (no candidate), 1 (null collision) or 2 (collided); out gets
+ * the new state. */
+int orc_ion_step_one(const orc_sim *s, const double *E, uint32_t n, const double in[4], uint64_t id,
+                     double out[4])
+{
+    part q = {in[0], in[1], in[2], in[3], id};
+    const int w = ion_push(s, E, &q);
+    int oc = w ? (w == 1 ? OUT_LOST0 : OUT_LOST1) : ion_collide(s, n, &q);
+    out[0] = q.z;
+    out[1] = q.vx;
+    out[2] = q.vy;
+    out[3] = q.vz;
+    return oc;
+}
+
 /* The kinetic-ion part of step n (the paper's fully kinetic comparison model,
  * with the ion-neutral collisions of the auxiliary Monte Carlo, Sec. II.C):
  * every ionization of this step adds an ion at the child electron's position
@@ -838,52 +899,24 @@ static void ion_step(orc_sim *s, uint32_t n, const double *kz, const uint64_t *k
     const int G = s->G;
     memset(s->dep_ni, 0, sizeof(double) * G);
     memset(s->dep_gi, 0, sizeof(double) * G);
-    const double M = s->m_ion, mn = s->m_gas;
     int64_t lost[2] = {0, 0}, keep = 0;
     for (int64_t i = 0; i < s->nip; ++i) {
         part q = s->ip[i];
+        const int w = ion_push(s, s->E, &q);
+        if (w) {
+            lost[w - 1]++;
+            continue;
+        }
         int c;
         double o;
-        locate(s, q.z, &c, &o);
-        double ep = (1.0 - o) * s->E[c] + o * s->E[c + 1];
-        q.vz = q.vz + (Q_E / M) * ep * s->dt;
-        q.z = q.z + q.vz * s->dt;
-        if (q.z < 0.0) {
-            lost[0]++;
-            continue;
-        }
-        if (q.z >= s->L) {
-            lost[1]++;
-            continue;
-        }
         locate(s, q.z, &c, &o);
         s->dep_ni[c] += 1.0 - o;
         s->dep_ni[c + 1] += o;
         s->dep_gi[c] += (1.0 - o) * q.vz;
         s->dep_gi[c + 1] += o * q.vz;
-        double u[4], w[4];
-        draws(s, q.id, n, 5, u);
-        if (u[0] < s->p_max_i) {
-            s->ion_cand++;
-            draws(s, q.id, n, 6, w);
-            double b1, b2, b3, b4;
-            gauss2(u[2], u[3], &b1, &b2);
-            gauss2(w[0], w[1], &b3, &b4);
-            double V[3] = {s->vt_gas * b1, s->vt_gas * b2, s->vt_gas * b3};
-            double v[3] = {q.vx, q.vy, q.vz};
-            double gx = v[0] - V[0], gy = v[1] - V[1], gz = v[2] - V[2];
-            double g = sqrt(gx * gx + gy * gy + gz * gz);
-            double nu = orc_swarm_nu(s->ngas, s->mi_red, 0, g);
-            if (u[1] * s->nu_max_i < nu) {
-                s->ion_coll++;
-                double d[3];
-                iso_dir(w[2], w[3], d);
-                for (int k = 0; k < 3; ++k) v[k] = (M * v[k] + mn * V[k]) / (M + mn) + mn / (M + mn) * g * d[k];
-                q.vx = v[0];
-                q.vy = v[1];
-                q.vz = v[2];
-            }
-        }
+        const int oc = ion_collide(s, n, &q);
+        if (oc >= 1) s->ion_cand++;
+        if (oc == 2) s->ion_coll++;
         s->ip[keep++] = q;
     }
     s->nip = keep;
