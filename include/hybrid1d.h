@@ -317,7 +317,7 @@ int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset);
  *                  advanced by its own chain of launches; inside a captured
  *                  chunk the chains run as parallel graph branches, so the
  *                  field kernels of one group overlap the electron kernels of
- *                  the others (1..8 and at most max_instances; a batch starts
+ *                  the others (1..16 and at most max_instances; a batch starts
  *                  with min(4, max_instances));
  *   sort_interval  steps between cell sorts (1..1000, default 20);
  *   blocks_per_sm  electron-kernel blocks per SM (0: the occupancy limit);
@@ -339,8 +339,8 @@ int hyb_batch_get_tuning(hyb_batch *b, hyb_tuning *out);
 int hyb_batch_set_tuning(hyb_batch *b, const hyb_tuning *t);
 
 /* Time candidate configurations on the batch's own running discharges and
- * keep the fastest: lanes in {1, 2, 4, 8}, then the sort interval in
- * {10, 20, 50}, then the electron grid at the occupancy limit or twice it,
+ * keep the fastest: lanes in {1, 2, 4, 8, 16}, then the sort interval in
+ * {10, 20, 50, 100}, then the electron grid at the occupancy limit or twice it,
  * then the field block size in {256, 512, 1024}.
  * Each trial advances every running discharge by one untimed chunk and then
  * by trial_steps rounded up to whole chunks (100 steps): those are real steps

@@ -46,7 +46,7 @@ int fail(int code, const char *fmt, ...)
 
 constexpr int kDefaultSort = 20;
 constexpr int kElectronBlock = 256;
-constexpr int kMaxLanes = 8;
+constexpr int kMaxLanes = 16;
 constexpr int kDefaultLanes = 4;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1062,7 +1062,7 @@ int autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *out)
             best.rate = r;
         }
     };
-    const int lane_opts[4] = {1, 2, 4, 8};
+    const int lane_opts[5] = {1, 2, 4, 8, 16};
     for (int l : lane_opts) {
         if (l > std::min(kMaxLanes, b->max_inst)) break;
         hyb_tuning t = best;
@@ -1070,7 +1070,7 @@ int autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *out)
         if (l == best.lanes && best.rate >= 0) continue;
         trial(t);
     }
-    const int sort_opts[3] = {10, 20, 50};
+    const int sort_opts[4] = {10, 20, 50, 100};
     const hyb_tuning after_lanes = best;
     for (int k : sort_opts) {
         if (k == after_lanes.sort_interval) continue;
