@@ -536,7 +536,7 @@ def main():
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--tune-steps", type=int, default=200)
+    ap.add_argument("--tune-steps", type=int, default=500)
     ap.add_argument("--lanes", type=int, default=0, help="fixed lane count instead of the autotuner's")
     ap.add_argument("--serve-requests", type=int, default=100, help="config-4 serving requests (0: none)")
     ap.add_argument("--serve-steps", type=int, default=5000)

@@ -301,7 +301,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
 
-        unsigned coll = 0u;      // 2 bits per particle: 1 elastic, 2 excitation, 3 ionization
+        unsigned coll = 0u;      // bit k: slot k ionized (handled in the warp pass below)
         uint2 ru[kVec];          // direction draws of the colliding particles
         float ens[kVec];         // kinetic energies (eV) after the push
         bool live[kVec];
@@ -428,7 +428,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                         atomicAdd(&K->s_met[cm + 1], (double)oo[k]);
                     }
                 }
-                coll |= (hit && kind == 3u) ? (3u << (2 * k)) : 0u;
+                coll |= (hit && kind == 3u) ? (1u << k) : 0u;
                 ru[k] = make_uint2(rk[k].z, rk[k].w);
                 cnt.iz_nul += (cand && !hit) ? (1u << 16) : 0u;
             }
@@ -438,71 +438,57 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             iter = 0;
         }
         if (MODE == 0) {
-            // real collisions of the warp, one particle per lane per pass:
-            // isotropic new direction; elastic energy loss (2m/M)(1 - cos chi),
-            // excitation loss, or ionization with a child electron (Sec. II.D)
+            // ionizations of the warp, one particle per lane per pass: split
+            // E - E_iz between the scattered and the ejected electron, both
+            // isotropic, the child appended with its ion source (Sec. II.D)
             while (__any_sync(kFull, coll != 0u)) {
-                const int k = (coll & 3u) ? 0 : 1;
-                const unsigned kind = (coll >> (2 * k)) & 3u;
+                const int k = (coll & 1u) ? 0 : 1;
                 bool has_child = false;
                 float cvx = 0.f, cvy = 0.f, cvz = 0.f;
                 uint64_t cid = 0;
                 int ck = 0;
                 float ok = 0.f;
-                if (kind) {
+                if (coll) {
                     const float px = k ? vx[1] : vx[0], py = k ? vy[1] : vy[0], pz = k ? vz[1] : vz[0];
                     const uint2 rr = k ? ru[1] : ru[0];
                     const uint64_t pid = k ? ids[1] : ids[0];
                     ck = k ? cc[1] : cc[0];
                     ok = k ? oo[1] : oo[0];
-                    const float v2 = px * px + py * py + pz * pz;
-                    const float en = half_m_q * v2;
+                    const float en = half_m_q * (px * px + py * py + pz * pz);
                     const float ct = 1.f - 2.f * u01f(rr.x);
                     const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
                     float sn, cs;
                     __sincosf(6.283185307179586f * u01f(rr.y), &sn, &cs);
-                    const float dx = st * cs, dy = st * sn, dz = ct;
-                    float sp;
-                    if (kind == 1u) {  // elastic, lab-frame isotropic
-                        const float rs = rsqrtf(v2);
-                        const float cchi = (px * dx + py * dy + pz * dz) * rs;
-                        sp = v2 * rs * sqrtf(1.f - two_mM * (1.f - cchi));
-                        cnt.el_exc += 1u;
-                    } else if (kind == 2u) {  // excitation
-                        sp = sqrtf(two_q_m * (en - e_exc));
-                        cnt.el_exc += 1u << 16;
-                    } else {  // ionization: split E - E_iz, eject a new electron
-                        const uint4 r1 = draw_pre(pre, pid, sl, 1u);
-                        const float de = en - e_iz;
-                        const float e_ej = u01f(r1.x) * de;
-                        sp = sqrtf(two_q_m * (de - e_ej));
-                        const float cj = 1.f - 2.f * u01f(r1.y);
-                        const float sj = sqrtf(fmaxf(0.f, 1.f - cj * cj));
-                        float snj, csj;
-                        __sincosf(6.283185307179586f * u01f(r1.z), &snj, &csj);
-                        const float spj = sqrtf(two_q_m * e_ej);
-                        cvx = spj * sj * csj;
-                        cvy = spj * sj * snj;
-                        cvz = spj * cj;
-                        cid = child_id(pid, step);
-                        has_child = true;
-                        cnt.iz_nul += 1u;
-                        if (HYB_CHECK(ck >= 0 && ck + 1 < G, 4, ck, G)) {
-                            atomicAdd(&K->s_iz[ck], 1.0 - ok);
-                            atomicAdd(&K->s_iz[ck + 1], (double)ok);
-                        }
+                    const uint4 r1 = draw_pre(pre, pid, sl, 1u);
+                    const float de = en - e_iz;
+                    const float e_ej = u01f(r1.x) * de;
+                    const float sp = sqrtf(two_q_m * (de - e_ej));
+                    const float cj = 1.f - 2.f * u01f(r1.y);
+                    const float sj = sqrtf(fmaxf(0.f, 1.f - cj * cj));
+                    float snj, csj;
+                    __sincosf(6.283185307179586f * u01f(r1.z), &snj, &csj);
+                    const float spj = sqrtf(two_q_m * e_ej);
+                    cvx = spj * sj * csj;
+                    cvy = spj * sj * snj;
+                    cvz = spj * cj;
+                    cid = child_id(pid, step);
+                    has_child = true;
+                    cnt.iz_nul += 1u;
+                    if (HYB_CHECK(ck >= 0 && ck + 1 < G, 4, ck, G)) {
+                        atomicAdd(&K->s_iz[ck], 1.0 - ok);
+                        atomicAdd(&K->s_iz[ck + 1], (double)ok);
                     }
                     if (k) {
-                        vx[1] = sp * dx, vy[1] = sp * dy, vz[1] = sp * dz;
+                        vx[1] = sp * (st * cs), vy[1] = sp * (st * sn), vz[1] = sp * ct;
                     } else {
-                        vx[0] = sp * dx, vy[0] = sp * dy, vz[0] = sp * dz;
+                        vx[0] = sp * (st * cs), vy[0] = sp * (st * sn), vz[0] = sp * ct;
                     }
                 }
                 unsigned ovf = 0;
                 append_children<float>(K, P, capacity, has_child, ck, ok, 0.0, cvx, cvy, cvz, cid, ovf);
                 if (KIN) append_ion<HYB_FP32_SPLIT>(K, has_child, ck, ok, 0.0, cid, step);
                 cnt.push_ovf |= ovf << 16;
-                coll &= ~(3u << (2 * k));
+                coll &= ~(1u << k);
             }
         }
         if (MODE == 0) {
