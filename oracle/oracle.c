@@ -709,7 +709,7 @@ static void emit_secondaries(orc_sim *s, uint32_t n)
             part q;
             q.id = orc_see_id(wall, n, (uint32_t)j);
             double v[4];
-            draws(s, q.id, n, 2, v);
+            draws(s, q.id, n, 7, v);
             double ct = sqrt(v[0]);
             double st = sqrt(fmax(0.0, 1.0 - ct * ct));
             double ph = TWO_PI * v[1];
@@ -936,7 +936,7 @@ static void ion_step(orc_sim *s, uint32_t n, const double *kz, const uint64_t *k
  *    with the probability of the fraction (the Bernoulli draw keyed by the
  *    process and j, call 3); each new electron is placed uniformly in the
  *    node's cell [z_j - dz/2, z_j + dz/2) with the process's energy and an
- *    isotropic direction (call 2 of its own id), and its ion enters the ion
+ *    isotropic direction (call 7 of its own id), and its ion enters the ion
  *    source (CIC) as an ionization's would;
  *  - then the explicit update of the metastable density,
  *    n_m^{n+1} = n_m + dt [D d2n_m/dz2 + S_m - R_P n_N n_m - 2 R_pool n_m^2]
@@ -973,7 +973,7 @@ static void metastable_step(orc_sim *s, uint32_t n)
                 part q;
                 q.id = (1ull << 62) | ((uint64_t)(2 + proc) << 60) | ((uint64_t)n << 20) | (uint64_t)k;
                 double v[4];
-                draws(s, q.id, n, 2, v);
+                draws(s, q.id, n, 7, v);
                 q.z = ((double)j - 0.5 + v[0]) * dz;
                 double ct = 1.0 - 2.0 * v[1];
                 double st = sqrt(fmax(0.0, 1.0 - ct * ct));

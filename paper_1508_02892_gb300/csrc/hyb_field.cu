@@ -207,7 +207,7 @@ struct FluidF {
 //    one with the probability of the fraction (call 3 of the key of the process
 //    and j); numbered k = 0, 1, ... in node order per process, each placed
 //    uniformly in [z_j - dz/2, z_j + dz/2) at the process's energy with an
-//    isotropic direction (call 2 of its id), appended after this step's
+//    isotropic direction (call 7 of its id), appended after this step's
 //    children, its ion added to the ion source (CIC);
 //  - the explicit update n_m += dt (D n_m'' + S_m - R_P n_N n_m - 2 R_pool n_m^2)
 //    at the interior nodes, n_m = 0 at the electrodes, and the flux into each
@@ -279,7 +279,7 @@ __device__ void metastable_step(InstDev *K, double *old, Red &red, int j0, int j
             const int64_t cnt = (int64_t)fl + (u01d(u.x) < m - fl ? 1 : 0);
             for (int64_t b = 0; b < cnt && k < s_tot[proc]; ++b, ++k) {
                 const uint64_t id = (1ull << 62) | ((uint64_t)(2 + proc) << 60) | ((uint64_t)n << 20) | (uint64_t)k;
-                const uint4 v = draw(id, n, K->seed_lo, K->seed_hi, 2);
+                const uint4 v = draw(id, n, K->seed_lo, K->seed_hi, 7);
                 const double z = ((double)j - 0.5 + u01d(v.x)) * dz;
                 const double ct = 1.0 - 2.0 * u01d(v.y);
                 const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
@@ -779,7 +779,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
             const int wall = k < s_cnt[0] ? 0 : 1;
             const uint32_t j = (uint32_t)(wall == 0 ? k : k - s_cnt[0]);
             const uint64_t id = see_id(wall, n, j);
-            const uint4 r = draw(id, n, K->seed_lo, K->seed_hi, 2);
+            const uint4 r = draw(id, n, K->seed_lo, K->seed_hi, 7);
             const double ct = sqrt(u01d(r.x));
             const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
             const double ph = kTwoPi * u01d(r.y);
