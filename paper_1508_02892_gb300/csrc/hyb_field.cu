@@ -218,13 +218,18 @@ __device__ __forceinline__ double birth_mean(const InstDev *K, int proc, double 
     return proc == 0 ? K->met_rp * nm * K->met_nn * dt * dz : K->met_kq * nm * nm * dt * dz;
 }
 
-// old: G doubles of shared scratch.
-__device__ void metastable_step(InstDev *K, double *old, Red &red, int j0, int j1)
+// old, cnt0, cnt1: G doubles each of shared scratch (n_m at the start of the
+// step, the per-node Penning and pooling counts).  The split mode multiplies by
+// reciprocals where the FP64 mode divides as the oracle does (an FP64 division
+// is a long instruction sequence at this part's FP64 rate).
+template <bool FAST>
+__device__ void metastable_step(InstDev *K, double *old, double *cnt0, double *cnt1, Red &red, int j0, int j1)
 {
     const int G = K->G;
     const double dz = K->dz, dt = K->dt, w = K->w;
     const uint32_t n = (uint32_t)K->step;
     const double kp = K->met_kp, kq = K->met_kq;
+    const double inv_w = w > 0.0 ? 1.0 / w : 0.0;
     __shared__ unsigned long long s_base;
     __shared__ int64_t s_tot[2];
     int64_t mine[2] = {0, 0};
@@ -235,16 +240,21 @@ __device__ void metastable_step(InstDev *K, double *old, Red &red, int j0, int j
     }
     double part[2] = {0.0, 0.0};
     for (int proc = 0; proc < 2; ++proc) {
+        double *cnt = proc == 0 ? cnt0 : cnt1;
         const double r = proc == 0 ? kp : kq;
-        if (!(r > 0.0) || !(w > 0.0)) continue;
-        for (int j = max(j0, 1); j < min(j1, G - 1); ++j) {
-            const double nm = old[j];
-            const double m = birth_mean(K, proc, nm, dt, dz) / w;
-            if (!(m > 0.0)) continue;
-            const double fl = floor(m);
-            const uint4 u = draw(0xFFFFFFFF00000000ull | ((uint64_t)(proc + 1) << 24) | (uint64_t)j, n, K->seed_lo,
-                                 K->seed_hi, 3);
-            part[proc] += fl + (u01d(u.x) < m - fl ? 1.0 : 0.0);
+        for (int j = j0; j < j1; ++j) {
+            double c = 0.0;
+            double m = 0.0;
+            if (j >= 1 && j <= G - 2 && r > 0.0 && w > 0.0)
+                m = FAST ? birth_mean(K, proc, old[j], dt, dz) * inv_w : birth_mean(K, proc, old[j], dt, dz) / w;
+            if (m > 0.0) {
+                const double fl = floor(m);
+                const uint4 u = draw(0xFFFFFFFF00000000ull | ((uint64_t)(proc + 1) << 24) | (uint64_t)j, n,
+                                     K->seed_lo, K->seed_hi, 3);
+                c = fl + (u01d(u.x) < m - fl ? 1.0 : 0.0);
+            }
+            cnt[j] = c;
+            part[proc] += c;
         }
     }
     double tot[2];
@@ -265,18 +275,12 @@ __device__ void metastable_step(InstDev *K, double *old, Red &red, int j0, int j
     mine[1] = (int64_t)off1;
     const PartBuf P = K->buf[K->cur];
     for (int proc = 0; proc < 2; ++proc) {
-        const double r = proc == 0 ? kp : kq;
-        if (!(r > 0.0) || !(w > 0.0) || part[proc] == 0.0) continue;
+        if (part[proc] == 0.0) continue;
+        const double *cnts = proc == 0 ? cnt0 : cnt1;
         const double sp = K->met_sp[proc];
         int64_t k = mine[proc];
         for (int j = max(j0, 1); j < min(j1, G - 1) && k < s_tot[proc]; ++j) {
-            const double nm = old[j];
-            const double m = birth_mean(K, proc, nm, dt, dz) / w;
-            if (!(m > 0.0)) continue;
-            const double fl = floor(m);
-            const uint4 u = draw(0xFFFFFFFF00000000ull | ((uint64_t)(proc + 1) << 24) | (uint64_t)j, n, K->seed_lo,
-                                 K->seed_hi, 3);
-            const int64_t cnt = (int64_t)fl + (u01d(u.x) < m - fl ? 1 : 0);
+            const int64_t cnt = (int64_t)cnts[j];
             for (int64_t b = 0; b < cnt && k < s_tot[proc]; ++b, ++k) {
                 const uint64_t id = (1ull << 62) | ((uint64_t)(2 + proc) << 60) | ((uint64_t)n << 20) | (uint64_t)k;
                 const uint4 v = draw(id, n, K->seed_lo, K->seed_hi, 7);
@@ -322,12 +326,14 @@ __device__ void metastable_step(InstDev *K, double *old, Red &red, int j0, int j
     __syncthreads();
     // the density update from the old values
     const double D = K->met_D;
+    const double c_src = w / (dz * dt), c_lap = D / (dz * dz);
     unsigned long long clamps = 0;
     for (int j = j0; j < j1; ++j) {
         double nn = 0.0;
         if (j >= 1 && j <= G - 2) {
-            const double src = w * K->s_met[j] / (dz * dt);
-            const double lap = D * (old[j + 1] - 2.0 * old[j] + old[j - 1]) / (dz * dz);
+            const double src = FAST ? K->s_met[j] * c_src : w * K->s_met[j] / (dz * dt);
+            const double lap = FAST ? c_lap * (old[j + 1] - 2.0 * old[j] + old[j - 1])
+                                    : D * (old[j + 1] - 2.0 * old[j] + old[j - 1]) / (dz * dz);
             const double loss = kp * old[j] + 2.0 * kq * old[j] * old[j];
             nn = old[j] + dt * (lap + src - loss);
             if (nn < 0.0) {
@@ -399,7 +405,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
     }
     __syncthreads();
 
-    if (K->met_on && !init) metastable_step(K, s_d, red, j0, j1);
+    if (K->met_on && !init) metastable_step<FAST>(K, s_d, s_x, s_ib, red, j0, j1);
 
     const Fluid F{K->ion_model, K->n_tab, K->tab, K->mu_const, K->ngas, K->kT_gas, K->m_ion, K->m_gas};
     double *gfin = s_g;
