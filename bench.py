@@ -404,6 +404,21 @@ def variants_load(params, stream, flush, n_inst=16, chunks=3, only=None):
                                  "units_per_launch": ni / max(prof["n_ion"], 1), "avg_launch_ms": avg,
                                  "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                                  "peak_kind": peak_kind}
+        # the oracle beside it: one host core, the four smallest of these
+        # discharges with the same change, three steps each
+        import oracle
+        small = sorted(sub, key=lambda q: q["n_particles"])[:4]
+        n_o, t_o = 0, 0.0
+        for q in small:
+            o = oracle.Oracle(dict(q, capacity_factor=2.5, **mod))
+            for _ in range(3):
+                n_o += o.n_particles
+                t0 = time.perf_counter()
+                o.step(1)
+                t_o += time.perf_counter() - t0
+            o.close()
+        r["cpu_baseline"] = {"value": n_o / t_o, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"the 4 smallest of the {n_inst} discharges, 3 steps each, {n_o} particle-steps"}
         out[name] = r
         b.close()
     return out
