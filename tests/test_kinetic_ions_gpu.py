@@ -232,3 +232,18 @@ def test_ion_density_is_not_writable_for_kinetic_ions():
     with pytest.raises(hybrid.HybError):
         f.ions()
     f.close()
+
+
+def test_empty_kinetic_discharge():
+    """No electrons and no ions: the kinetic path runs, nothing is born, the
+    field is the vacuum field, and the result equals the oracle's."""
+    from paper_1508_02892_gb300 import hybrid
+    p = _kinetic(n_particles=0, n0_m3=0.0, weight=1e6, n_cells=40)
+    g, o = hybrid.Discharge(p), oracle.Oracle(p)
+    g.advance(20)
+    o.step(20)
+    c = g.counters()
+    assert c["status"] == 0 and c["ions"] == 0 and c["particles"] == 0 and c["ion_pushes"] == 0
+    assert g.ions()["id"].size == 0
+    _check(g, o, p)
+    g.close()

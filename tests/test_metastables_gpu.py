@@ -166,3 +166,18 @@ def test_metastable_parameters_are_checked():
     with pytest.raises(hybrid.HybError):
         f.metastables()
     f.close()
+
+
+def test_electrons_from_metastables_alone():
+    """Degenerate start: no electrons at all, only metastables.  Every electron
+    then comes from Penning and pooling ionization; the run equals the
+    oracle's in FP64."""
+    from paper_1508_02892_gb300 import hybrid
+    p = _params(n_particles=0, weight=2e6, n_cells=70, met_n0_m3=2e19, seed=78)
+    g, o = hybrid.Discharge(p), oracle.Oracle(p)
+    g.advance(60)
+    o.step(60)
+    c = o.counters()
+    assert c["births_penning"] + c["births_pooling"] > 100 and c["particles"] > 0
+    _check(g, o, p)
+    g.close()
