@@ -58,7 +58,9 @@ extern "C" {
                                    He+ with the electrons' weight, pushed in E every step, removed at
                                    the walls, colliding with the gas as in the auxiliary Monte Carlo of
                                    Sec. II.C (Q_m = Q_i + 2 Q_b, thermal target); one new ion per
-                                   ionization, at the new electron's position */
+                                   ionization, at the new electron's position; the ions take the
+                                   precision of the discharge (FP64 or split); not combined with
+                                   recombination or metastables (HYB_ERR_ARG) */
 
 #define HYB_FP64 0              /* particles and grids in FP64 */
 #define HYB_FP32_SPLIT 1        /* particles as (cell, FP32 offset) + FP32 velocity; FP64 grids */
