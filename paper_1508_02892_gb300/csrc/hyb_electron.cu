@@ -274,18 +274,21 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
         float oo[kVec], vx[kVec], vy[kVec], vz[kVec];
         uint64_t ids[kVec];
         if (full) {
-            const int2 c2 = *reinterpret_cast<const int2 *>(P.c + i0);
-            const float2 o2 = *reinterpret_cast<const float2 *>(P.o + i0);
-            const float2 x2 = *reinterpret_cast<const float2 *>(P.vxf + i0);
-            const float2 y2 = *reinterpret_cast<const float2 *>(P.vyf + i0);
-            const float2 z2 = *reinterpret_cast<const float2 *>(P.vzf + i0);
+            // streaming (evict-first) loads and stores: the particle state is
+            // touched once per step and should not displace the field, the
+            // cross-section table or the deposit rows in L1 and L2
+            const int2 c2 = __ldcs(reinterpret_cast<const int2 *>(P.c + i0));
+            const float2 o2 = __ldcs(reinterpret_cast<const float2 *>(P.o + i0));
+            const float2 x2 = __ldcs(reinterpret_cast<const float2 *>(P.vxf + i0));
+            const float2 y2 = __ldcs(reinterpret_cast<const float2 *>(P.vyf + i0));
+            const float2 z2 = __ldcs(reinterpret_cast<const float2 *>(P.vzf + i0));
             cc[0] = c2.x, cc[1] = c2.y;
             oo[0] = o2.x, oo[1] = o2.y;
             vx[0] = x2.x, vx[1] = x2.y;
             vy[0] = y2.x, vy[1] = y2.y;
             vz[0] = z2.x, vz[1] = z2.y;
             if (MODE == 0) {
-                const ulonglong2 d0 = *reinterpret_cast<const ulonglong2 *>(P.id + i0);
+                const ulonglong2 d0 = __ldcs(reinterpret_cast<const ulonglong2 *>(P.id + i0));
                 ids[0] = d0.x, ids[1] = d0.y;
             }
         } else {
@@ -493,11 +496,11 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
         }
         if (MODE == 0) {
             if (full) {
-                *reinterpret_cast<int2 *>(P.c + i0) = make_int2(cc[0], cc[1]);
-                *reinterpret_cast<float2 *>(P.o + i0) = make_float2(oo[0], oo[1]);
-                *reinterpret_cast<float2 *>(P.vxf + i0) = make_float2(vx[0], vx[1]);
-                *reinterpret_cast<float2 *>(P.vyf + i0) = make_float2(vy[0], vy[1]);
-                *reinterpret_cast<float2 *>(P.vzf + i0) = make_float2(vz[0], vz[1]);
+                __stcs(reinterpret_cast<int2 *>(P.c + i0), make_int2(cc[0], cc[1]));
+                __stcs(reinterpret_cast<float2 *>(P.o + i0), make_float2(oo[0], oo[1]));
+                __stcs(reinterpret_cast<float2 *>(P.vxf + i0), make_float2(vx[0], vx[1]));
+                __stcs(reinterpret_cast<float2 *>(P.vyf + i0), make_float2(vy[0], vy[1]));
+                __stcs(reinterpret_cast<float2 *>(P.vzf + i0), make_float2(vz[0], vz[1]));
             } else {
 #pragma unroll
                 for (int k = 0; k < kVec; ++k) {
@@ -928,18 +931,20 @@ __global__ void __launch_bounds__(kBlock) k_sort_pass(InstDev *__restrict__ inst
             if (PHASE == 1) {
                 pos = __shfl_sync(peers, pos, leader) + __popc(peers & lanemask_lt());
                 if (!HYB_CHECK(pos >= 0 && pos < K->capacity, 8, pos, K->capacity)) continue;
-                D.id[pos] = S.id[i];
+                // streaming (evict-first) accesses: the particle state is read
+                // and written once, and should not displace the tables
+                __stcs(&D.id[pos], __ldcs(&S.id[i]));
                 if (PREC == HYB_FP32_SPLIT) {
-                    D.c[pos] = c;
-                    D.o[pos] = S.o[i];
-                    D.vxf[pos] = S.vxf[i];
-                    D.vyf[pos] = S.vyf[i];
-                    D.vzf[pos] = S.vzf[i];
+                    __stcs(&D.c[pos], c);
+                    __stcs(&D.o[pos], __ldcs(&S.o[i]));
+                    __stcs(&D.vxf[pos], __ldcs(&S.vxf[i]));
+                    __stcs(&D.vyf[pos], __ldcs(&S.vyf[i]));
+                    __stcs(&D.vzf[pos], __ldcs(&S.vzf[i]));
                 } else {
-                    D.z[pos] = S.z[i];
-                    D.vxd[pos] = S.vxd[i];
-                    D.vyd[pos] = S.vyd[i];
-                    D.vzd[pos] = S.vzd[i];
+                    __stcs(&D.z[pos], __ldcs(&S.z[i]));
+                    __stcs(&D.vxd[pos], __ldcs(&S.vxd[i]));
+                    __stcs(&D.vyd[pos], __ldcs(&S.vyd[i]));
+                    __stcs(&D.vzd[pos], __ldcs(&S.vzd[i]));
                 }
             }
         }

@@ -205,16 +205,16 @@ __device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned cha
         int c[2];
         float o[2], vx[2], vy[2], vz[2];
         uint64_t id[2];
-        if (full) {
-            const int2 c2 = *reinterpret_cast<const int2 *>(P.c + i0);
-            const float2 o2 = *reinterpret_cast<const float2 *>(P.o + i0);
-            const float2 x2 = *reinterpret_cast<const float2 *>(P.vxf + i0);
-            const float2 y2 = *reinterpret_cast<const float2 *>(P.vyf + i0);
-            const float2 z2 = *reinterpret_cast<const float2 *>(P.vzf + i0);
+        if (full) {  // streaming (evict-first) accesses, as the electron kernel
+            const int2 c2 = __ldcs(reinterpret_cast<const int2 *>(P.c + i0));
+            const float2 o2 = __ldcs(reinterpret_cast<const float2 *>(P.o + i0));
+            const float2 x2 = __ldcs(reinterpret_cast<const float2 *>(P.vxf + i0));
+            const float2 y2 = __ldcs(reinterpret_cast<const float2 *>(P.vyf + i0));
+            const float2 z2 = __ldcs(reinterpret_cast<const float2 *>(P.vzf + i0));
             c[0] = c2.x, c[1] = c2.y, o[0] = o2.x, o[1] = o2.y;
             vx[0] = x2.x, vx[1] = x2.y, vy[0] = y2.x, vy[1] = y2.y, vz[0] = z2.x, vz[1] = z2.y;
             if (MODE == 0) {
-                const ulonglong2 d2 = *reinterpret_cast<const ulonglong2 *>(P.id + i0);
+                const ulonglong2 d2 = __ldcs(reinterpret_cast<const ulonglong2 *>(P.id + i0));
                 id[0] = d2.x, id[1] = d2.y;
             } else {
                 id[0] = id[1] = 0ull;
@@ -306,11 +306,11 @@ __device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned cha
                 }
             }
             if (full) {
-                *reinterpret_cast<int2 *>(P.c + i0) = make_int2(c[0], c[1]);
-                *reinterpret_cast<float2 *>(P.o + i0) = make_float2(o[0], o[1]);
-                *reinterpret_cast<float2 *>(P.vxf + i0) = make_float2(vx[0], vx[1]);
-                *reinterpret_cast<float2 *>(P.vyf + i0) = make_float2(vy[0], vy[1]);
-                *reinterpret_cast<float2 *>(P.vzf + i0) = make_float2(vz[0], vz[1]);
+                __stcs(reinterpret_cast<int2 *>(P.c + i0), make_int2(c[0], c[1]));
+                __stcs(reinterpret_cast<float2 *>(P.o + i0), make_float2(o[0], o[1]));
+                __stcs(reinterpret_cast<float2 *>(P.vxf + i0), make_float2(vx[0], vx[1]));
+                __stcs(reinterpret_cast<float2 *>(P.vyf + i0), make_float2(vy[0], vy[1]));
+                __stcs(reinterpret_cast<float2 *>(P.vzf + i0), make_float2(vz[0], vz[1]));
             } else {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
