@@ -83,3 +83,34 @@ def test_ion_bookkeeping_is_exact():
         assert fl[1] == pytest.approx(l1 * o.weight / p["dt_s"], rel=1e-12, abs=1e-30)
         prev, iprev = c, ic
     assert births > 0
+
+
+def test_ion_push_closed_form_and_walls():
+    """One ion step in a uniform field without a collision (no candidate, or a
+    null one) is the leapfrog with the ion's mass: v' = v + (e/M) E dt,
+    z' = z + v' dt, exactly; an ion crossing z = 0 or z = L is removed there."""
+    p = _no_electron_collisions(n_particles=1, weight=1e-3, v_rf_amp_v=0.0)
+    o = oracle.Oracle(p)
+    G = o.G
+    L, dt = p["gap_m"], p["dt_s"]
+    E0 = 3.0e6
+    E = np.full(G, E0)
+    M = M_HE
+    rng = np.random.default_rng(7)
+    plain = 0
+    for k in range(400):
+        z = rng.uniform(0.05, 0.95) * L
+        v = rng.normal(0.0, 800.0, 3)
+        oc, out = o.ion_step_one(E, 5, [z, v[0], v[1], v[2]], (1 << 61) + k)
+        if oc == 2:
+            continue
+        plain += 1
+        vz = v[2] + QE / M * E0 * dt
+        assert oc in (0, 1)
+        np.testing.assert_allclose(out, [z + vz * dt, v[0], v[1], vz], rtol=1e-15, atol=0)
+    assert plain > 300
+    # walls: an ion placed just inside z = 0 moving out, and one just inside z = L
+    oc, _ = o.ion_step_one(E * 0, 5, [1e-12, 0.0, 0.0, -1e3], 1 << 61)
+    assert oc == oracle.OUT_LOST0
+    oc, _ = o.ion_step_one(E * 0, 5, [L - 1e-12, 0.0, 0.0, 1e3], 1 << 61)
+    assert oc == oracle.OUT_LOST1
