@@ -82,3 +82,22 @@ def test_host_validation_rejects_bad_params():
     assert e.value.code == -4
     p = workloads.config1(n_particles=100)
     assert hybrid.footprint(p) > 0
+
+
+def test_workload_dicts_fill_every_parameter():
+    """Every scalar field of hyb_params has a value in the workload dicts (so
+    no parameter silently takes 0), and the oracle's parameter struct has the
+    same physics fields."""
+    import oracle
+    from paper_1508_02892_gb300 import hybrid, workloads as W
+    p = W.config1()
+    tables = {"tab_eon_td", "tab_mu", "tab_nu", "xs_ev", "xs_el", "xs_exc", "xs_ion", "xs_rec", "n_tab", "n_xs"}
+    for name, _ in hybrid.Params._fields_:
+        if name in tables:
+            continue
+        assert name in p, name
+    # the method's parameters are named alike on both sides (the library adds
+    # layout-only ones: precision, capacity, sort interval)
+    lib_names = {n for n, _ in hybrid.Params._fields_} - {"precision", "capacity_factor", "sort_interval"}
+    orc_names = {n for n, _ in oracle.OrcParams._fields_} - {"flags"}
+    assert lib_names == orc_names, (lib_names ^ orc_names)
