@@ -23,6 +23,12 @@
  *   - counter-based Philox4x32-10 (Salmon et al., SC'11) keyed by particle id
  *     and step replaces the paper's xorshift128 (Sec. II.A), so that results do
  *     not depend on particle order.
+ * Beyond the step itself the oracle carries the rest of Secs. II.C-II.D: the
+ * auxiliary ion-swarm Monte Carlo (mobility and exchange-frequency tables),
+ * the power-controlled voltage (Eq. 2.9), electron-ion recombination as a
+ * null-collision process on the non-uniform ion density, metastables with
+ * Penning and pooling ionization, and the fully kinetic ions of the paper's
+ * comparison model.
  * Each function below names the passage it follows.
  */
 #include <math.h>
