@@ -284,7 +284,9 @@ int hyb_batch_read_moments(hyb_batch *b, int32_t slot, hyb_moments *out);
 int hyb_batch_read_counters(hyb_batch *b, int32_t slot, hyb_counters *out);
 int hyb_batch_read_particles(hyb_batch *b, int32_t slot, double *z, double *vx, double *vy, double *vz,
                              uint64_t *id, int64_t cap, int64_t *n);
-
+/* The same reads for the discharge in `slot` as hyb_read_metastables and
+ * hyb_read_ions (same buffers, layout and errors; HYB_ERR_ARG for an empty
+ * slot). */
 int hyb_batch_read_metastables(hyb_batch *b, int32_t slot, double *met, double *avg, double *flux);
 int hyb_batch_read_ions(hyb_batch *b, int32_t slot, double *z, double *vx, double *vy, double *vz, uint64_t *id,
                         int64_t cap, int64_t *n);
