@@ -36,19 +36,25 @@ COUNTER_NAMES = ("step", "particles", "births_iz", "births_see0", "births_see1",
                  "births_penning", "births_pooling")
 
 
-def build(force: bool = False) -> str:
+SRC = _SRC
+
+
+def build(force: bool = False, src: str | None = None, out: str | None = None) -> str:
     """Compile oracle.c into _build/liboracle.so (gcc, -O2, no FP contraction so
-    that x86 and Arm give the same bits)."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    that x86 and Arm give the same bits).  `src`/`out` build another copy of
+    the source (the mutation tests plant mistakes in such a copy)."""
+    src = src or _SRC
+    out = out or _LIB_PATH
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(src)):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-Wall", "-o", tmp, _SRC, "-lm"]
+           "-Wall", "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, out)
+    return out
 
 
 class OrcParams(C.Structure):
@@ -96,60 +102,74 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            vp, i64, u64, u32, i32, dbl = C.c_void_p, C.c_int64, C.c_uint64, C.c_uint32, C.c_int32, C.c_double
-            pd = C.POINTER(C.c_double)
-            pu64 = C.POINTER(C.c_uint64)
-            pi64 = C.POINTER(C.c_int64)
-            pu32 = C.POINTER(C.c_uint32)
-            sig = {
-                "orc_create": (vp, [C.POINTER(OrcParams)]),
-                "orc_destroy": (None, [vp]),
-                "orc_step": (C.c_int, [vp, i64]),
-                "orc_num_particles": (i64, [vp]),
-                "orc_num_nodes": (C.c_int, [vp]),
-                "orc_get_particles": (None, [vp, pd, pd, pd, pd, pu64]),
-                "orc_set_particles": (None, [vp, i64, pd, pd, pd, pd, pu64]),
-                "orc_get_grid": (None, [vp, C.c_int, pd]),
-                "orc_set_grid": (None, [vp, C.c_int, pd]),
-                "orc_get_moments": (i64, [vp, pd, pd, pd, pd, pd]),
-                "orc_get_eedf_counts": (None, [vp, pd]),
-                "orc_get_counters": (None, [vp, pi64]),
-                "orc_get_flux_in": (None, [vp, pd]),
-                "orc_set_flux_in": (None, [vp, pd]),
-                "orc_emit_only": (i64, [vp, u32]),
-                "orc_init_field": (None, [vp]),
-                "orc_xs_eval": (None, [vp, dbl, pd]),
-                "orc_nu_max": (dbl, [vp]),
-                "orc_p_max": (dbl, [vp]),
-                "orc_weight": (dbl, [vp]),
-                "orc_ngas": (dbl, [vp]),
-                "orc_philox4x32_10": (None, [pu32, pu32, pu32]),
-                "orc_u01": (dbl, [u32]),
-                "orc_mix64": (u64, [u64]),
-                "orc_child_id": (u64, [u64, u32]),
-                "orc_see_id": (u64, [C.c_int, u32, u32]),
-                "orc_poisson": (None, [C.c_int, dbl, pd, dbl, dbl, pd, pd]),
-                "orc_fluid_update": (i64, [vp, pd, pd, pd, pd, pd]),
-                "orc_particle_step_one": (C.c_int, [vp, pd, u32, pd, u64, pd, pd, pu64]),
-                "orc_ion_step_one": (C.c_int, [vp, pd, u32, pd, u64, pd]),
-                "orc_swarm_run": (None, [C.POINTER(OrcSwarmParams), C.POINTER(OrcSwarmResult), pd]),
-                "orc_get_power": (None, [vp, pd, pi64]),
-                "orc_get_ion_counters": (None, [vp, pi64]),
-                "orc_get_metastables": (None, [vp, pd, pd, pd]),
-                "orc_set_metastables": (None, [vp, pd]),
-                "orc_get_ions": (None, [vp, pd, pd, pd, pd, pu64]),
-                "orc_swarm_nu": (dbl, [dbl, dbl, C.c_int, dbl]),
-                "orc_swarm_nu_bound": (dbl, [dbl, dbl, C.c_int, dbl]),
-                "orc_swarm_qi": (dbl, [dbl]),
-                "orc_swarm_qb": (dbl, [dbl]),
-            }
-            for name, (res, args) in sig.items():
-                fn = getattr(L, name)
-                fn.restype = res
-                fn.argtypes = args
-            _lib = L
+            _lib = load(build())
     return _lib
+
+
+def use_library(L) -> None:
+    """Route every later call of this module to the library L (from load());
+    the mutation tests swap a planted-mistake copy in and back out."""
+    global _lib
+    with _lock:
+        _lib = L
+
+
+def load(path: str):
+    """Load a compiled copy of oracle.c and declare its signatures."""
+    L = C.CDLL(path)
+    vp, i64, u64, u32, i32, dbl = C.c_void_p, C.c_int64, C.c_uint64, C.c_uint32, C.c_int32, C.c_double
+    pd = C.POINTER(C.c_double)
+    pu64 = C.POINTER(C.c_uint64)
+    pi64 = C.POINTER(C.c_int64)
+    pu32 = C.POINTER(C.c_uint32)
+    sig = {
+        "orc_create": (vp, [C.POINTER(OrcParams)]),
+        "orc_destroy": (None, [vp]),
+        "orc_step": (C.c_int, [vp, i64]),
+        "orc_num_particles": (i64, [vp]),
+        "orc_num_nodes": (C.c_int, [vp]),
+        "orc_get_particles": (None, [vp, pd, pd, pd, pd, pu64]),
+        "orc_set_particles": (None, [vp, i64, pd, pd, pd, pd, pu64]),
+        "orc_get_grid": (None, [vp, C.c_int, pd]),
+        "orc_set_grid": (None, [vp, C.c_int, pd]),
+        "orc_get_moments": (i64, [vp, pd, pd, pd, pd, pd]),
+        "orc_get_eedf_counts": (None, [vp, pd]),
+        "orc_get_counters": (None, [vp, pi64]),
+        "orc_get_flux_in": (None, [vp, pd]),
+        "orc_set_flux_in": (None, [vp, pd]),
+        "orc_emit_only": (i64, [vp, u32]),
+        "orc_init_field": (None, [vp]),
+        "orc_xs_eval": (None, [vp, dbl, pd]),
+        "orc_nu_max": (dbl, [vp]),
+        "orc_p_max": (dbl, [vp]),
+        "orc_weight": (dbl, [vp]),
+        "orc_ngas": (dbl, [vp]),
+        "orc_philox4x32_10": (None, [pu32, pu32, pu32]),
+        "orc_u01": (dbl, [u32]),
+        "orc_mix64": (u64, [u64]),
+        "orc_child_id": (u64, [u64, u32]),
+        "orc_see_id": (u64, [C.c_int, u32, u32]),
+        "orc_poisson": (None, [C.c_int, dbl, pd, dbl, dbl, pd, pd]),
+        "orc_fluid_update": (i64, [vp, pd, pd, pd, pd, pd]),
+        "orc_particle_step_one": (C.c_int, [vp, pd, u32, pd, u64, pd, pd, pu64]),
+        "orc_ion_step_one": (C.c_int, [vp, pd, u32, pd, u64, pd]),
+        "orc_swarm_run": (None, [C.POINTER(OrcSwarmParams), C.POINTER(OrcSwarmResult), pd]),
+        "orc_get_power": (None, [vp, pd, pi64]),
+        "orc_get_ion_counters": (None, [vp, pi64]),
+        "orc_get_metastables": (None, [vp, pd, pd, pd]),
+        "orc_set_metastables": (None, [vp, pd]),
+        "orc_get_ions": (None, [vp, pd, pd, pd, pd, pu64]),
+        "orc_swarm_nu": (dbl, [dbl, dbl, C.c_int, dbl]),
+        "orc_swarm_nu_bound": (dbl, [dbl, dbl, C.c_int, dbl]),
+        "orc_swarm_qi": (dbl, [dbl]),
+        "orc_swarm_qb": (dbl, [dbl]),
+        "orc_ion_transport": (None, [vp, dbl, dbl, pd]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
 
 
 # ----------------------------------------------------------------- helpers ---
@@ -335,6 +355,13 @@ class Oracle:
     @property
     def ngas(self):
         return lib().orc_ngas(self.h)
+
+    def transport(self, e_abs, u_abs=0.0):
+        """(mu, T_i in J, D, nu) the fluid update takes at field |E| and drift
+        speed |u| (Sec. II.B-II.C, Eqs. 2.7-2.8)."""
+        out = np.zeros(4)
+        lib().orc_ion_transport(self.h, float(e_abs), float(u_abs), _dp(out))
+        return tuple(float(x) for x in out)
 
     def fluid_update(self, E, gsrc, ni, gam):
         E, gsrc = (np.ascontiguousarray(a, dtype=np.float64) for a in (E, gsrc))

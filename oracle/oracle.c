@@ -291,6 +291,19 @@ static double exch_freq(const orc_sim *s, double u_abs)
     return interp_lin(s->tab_u, s->tab_nu, s->p.n_tab, u_abs);
 }
 
+/* The transport coefficients the fluid update takes at field |E| and drift
+ * speed |u|: out = {mu (Sec. II.C), T_i in J (Eq. 2.8), D = mu T_i / e
+ * (Eq. 2.7), nu (Sec. II.B)}.  Read by the tests. */
+void orc_ion_transport(const orc_sim *s, double e_abs, double u_abs, double out[4])
+{
+    double mu = mobility(s, e_abs);
+    double t = ion_temp(s, mu, e_abs);
+    out[0] = mu;
+    out[1] = t;
+    out[2] = mu * t / Q_E;
+    out[3] = exch_freq(s, u_abs);
+}
+
 /* ------------------------------------------------------------ Poisson ---- */
 
 /* -eps0 phi'' = rho on the uniform grid, 3-point differences, Dirichlet ends,

@@ -177,7 +177,7 @@ def test_split_electrons_and_ions_track_the_oracle():
     dz = p["gap_m"] / (G - 1)
     dv = np.full(G, dz)
     dv[0] = dv[-1] = dz / 2
-    assert (ni * dv).sum() == pytest.approx(p["weight"] * c["ions"], rel=1e-5)
+    assert (ni * dv).sum() == pytest.approx(p["weight"] * c["ions"], rel=1e-5, abs=0)
     ic = o.ion_counters()
     assert abs(c["ions"] - ic["ions"]) <= 0.03 * ic["ions"], (c["ions"], ic["ions"])
     assert abs(c["ion_collisions"] - ic["collisions"]) <= 0.03 * ic["collisions"]
@@ -186,7 +186,7 @@ def test_split_electrons_and_ions_track_the_oracle():
     oi = o.ions()
     e_g = np.mean(ions["vx"] ** 2 + ions["vy"] ** 2 + ions["vz"] ** 2)
     e_o = np.mean(oi["vx"] ** 2 + oi["vy"] ** 2 + oi["vz"] ** 2)
-    assert e_g == pytest.approx(e_o, rel=0.03)
+    assert e_g == pytest.approx(e_o, rel=0.03, abs=0)
     g.close()
 
 

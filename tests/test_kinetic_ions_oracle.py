@@ -41,7 +41,7 @@ def test_ion_drift_matches_the_paper_mobility():
     u = np.mean(drift)
     E0 = 1.47e6
     mu = (1.18 - 0.185 * E / E0) * 1e-3
-    assert u == pytest.approx(mu * E, rel=0.08)
+    assert u == pytest.approx(mu * E, rel=0.08, abs=0)
     assert abs(np.mean(drift[:5]) - np.mean(drift[5:])) < 0.03 * u     # stationary
 
 
@@ -77,7 +77,7 @@ def test_ion_bookkeeping_is_exact():
         l0, l1 = ic["losses0"] - iprev["losses0"], ic["losses1"] - iprev["losses1"]
         assert ic["ions"] == iprev["ions"] + d_iz - l0 - l1
         ni = o.grid(oracle.GRID_NI)
-        assert (ni * dv).sum() == pytest.approx(o.weight * ic["ions"], rel=1e-12)
+        assert (ni * dv).sum() == pytest.approx(o.weight * ic["ions"], rel=1e-12, abs=0)
         fl = o.flux_in()
         assert fl[0] == pytest.approx(l0 * o.weight / p["dt_s"], rel=1e-12, abs=1e-30)
         assert fl[1] == pytest.approx(l1 * o.weight / p["dt_s"], rel=1e-12, abs=1e-30)

@@ -93,7 +93,7 @@ def test_child_and_secondary_ids_disjoint():
 def test_gas_density_ideal_gas():
     o = oracle.Oracle(W.config1(n_particles=10))
     # Loschmidt-type number at 1 atm, 300 K: 2.4463e25 m^-3
-    assert o.ngas == pytest.approx(2.44631e25, rel=1e-5)
+    assert o.ngas == pytest.approx(2.44631e25, rel=1e-5, abs=0)
 
 
 def test_xs_lookup_matches_bruteforce_interpolation():
@@ -128,7 +128,7 @@ def test_nu_max_bounds_collision_frequency():
     nu = np.array([o.ngas * o.xs(e).sum() * _speed(e) for e in es])
     assert nu.max() <= o.nu_max * (1 + 1e-12)
     assert nu.max() >= o.nu_max * (1 - 1e-3)
-    assert o.p_max == pytest.approx(-math.expm1(-o.nu_max * p["dt_s"]), rel=1e-14)
+    assert o.p_max == pytest.approx(-math.expm1(-o.nu_max * p["dt_s"]), rel=1e-14, abs=0)
 
 
 # ---------------------------------------------------------------- pusher ---
@@ -172,7 +172,7 @@ def test_cic_gather_exact_for_linear_field():
         vz = v[2] - QE / ME * (a0 + b0 * z) * dt
         assert oc == oracle.OUT_NONE
         assert out[3] == pytest.approx(vz, rel=1e-12, abs=1e-9)
-        assert out[0] == pytest.approx(z + vz * dt, rel=1e-13)
+        assert out[0] == pytest.approx(z + vz * dt, rel=1e-13, abs=0)
         assert out[1] == v[0] and out[2] == v[1]
 
 
@@ -205,12 +205,12 @@ def test_cic_deposit_partition_and_first_moment():
     dv = np.full(G, dz)
     dv[0] = dv[-1] = dz / 2
     cnt = ne * dv / w
-    assert cnt.sum() == pytest.approx(1000, rel=1e-13)                 # partition of unity
-    assert (cnt * np.linspace(0, L, G)).sum() == pytest.approx(z.sum(), rel=1e-12)  # CIC keeps the centroid
+    assert cnt.sum() == pytest.approx(1000, rel=1e-13, abs=0)                 # partition of unity
+    assert (cnt * np.linspace(0, L, G)).sum() == pytest.approx(z.sum(), rel=1e-12, abs=0)  # CIC keeps the centroid
     # one particle: only its two nodes, with weights 1-o and o
     o.set_particles(np.array([0.3 * dz + 7 * dz]), np.zeros(1), np.zeros(1), np.zeros(1), np.zeros(1, np.uint64))
     cnt = o.grid(oracle.GRID_NE) * dv / w
-    assert cnt[7] == pytest.approx(0.7, rel=1e-12) and cnt[8] == pytest.approx(0.3, rel=1e-12)
+    assert cnt[7] == pytest.approx(0.7, rel=1e-12, abs=0) and cnt[8] == pytest.approx(0.3, rel=1e-12, abs=0)
     assert np.count_nonzero(cnt) == 2
 
 
@@ -223,7 +223,7 @@ def test_null_collision_rate_constant_sigma():
     p = _set_xs(_quiet(gap_m=1.0, n_cells=10, gas_mass_amu=1e15), el=sig)
     o = oracle.Oracle(p)
     nu_max_cf = o.ngas * sig * _speed(1000.0)
-    assert o.nu_max == pytest.approx(nu_max_cf, rel=1e-12)
+    assert o.nu_max == pytest.approx(nu_max_cf, rel=1e-12, abs=0)
     o.set_particles(*_iso_particles(n, ev, 1.0, 1))
     o.step(steps)
     c = o.counters()
@@ -267,14 +267,14 @@ def test_process_selection_energy_losses_and_isotropy():
         outs[i] = oc
         e1 = 0.5 * ME * (out[1:] ** 2).sum() / QE
         if oc == oracle.OUT_EXC:
-            assert e1 == pytest.approx(ev - 1.0, rel=1e-12)
+            assert e1 == pytest.approx(ev - 1.0, rel=1e-12, abs=0)
         elif oc == oracle.OUT_ION:
             e2 = 0.5 * ME * (child[1:] ** 2).sum() / QE
-            assert e1 + e2 == pytest.approx(ev - 2.0, rel=1e-12)
+            assert e1 + e2 == pytest.approx(ev - 2.0, rel=1e-12, abs=0)
             assert cid == oracle.child_id(int(ids[i]), 3)
             assert child[0] == out[0]
         elif oc == oracle.OUT_ELASTIC:
-            assert e1 == pytest.approx(ev, rel=1e-9)
+            assert e1 == pytest.approx(ev, rel=1e-9, abs=0)
         if oc in (oracle.OUT_ELASTIC, oracle.OUT_EXC, oracle.OUT_ION):
             cts.append(out[3] / np.linalg.norm(out[1:]))
     nu = o.ngas * np.array([3e-20, 2e-20, 1e-20]) * _speed(ev)
@@ -311,7 +311,7 @@ def test_elastic_energy_relaxation_cold_gas():
     want = ev0 * (1 - prob * 2 * ME / (M_amu * AMU)) ** steps
     assert abs(e.mean() - want) < 4.5 * e.std() / math.sqrt(n) + 2e-4 * want
     cont = ev0 * math.exp(-2 * ME / (M_amu * AMU) * nu0 * steps * dt)
-    assert e.mean() == pytest.approx(cont, rel=0.02)
+    assert e.mean() == pytest.approx(cont, rel=0.02, abs=0)
 
 
 def test_maxwellian_relaxation_thermal_gas():
@@ -334,7 +334,7 @@ def test_maxwellian_relaxation_thermal_gas():
     for comp in ("vx", "vy", "vz"):
         assert stats.kstest(st[comp] / sd, "norm").pvalue > 1e-4
     e = 0.5 * ME * (st["vx"] ** 2 + st["vy"] ** 2 + st["vz"] ** 2) / QE
-    assert e.mean() == pytest.approx(1.5 * kt_ev, rel=4.5 * math.sqrt(2 / 3 / n))
+    assert e.mean() == pytest.approx(1.5 * kt_ev, rel=4.5 * math.sqrt(2 / 3 / n), abs=0)
 
 
 # ------------------------------------------------------------- Poisson ---
@@ -347,7 +347,7 @@ def test_poisson_uniform_charge_closed_form():
     np.testing.assert_allclose(phi, want, rtol=0, atol=1e-12 * np.abs(want).max())
     wantE = V / L - rho0 * (L - 2 * z) / (2 * EPS0)
     np.testing.assert_allclose(E, wantE, rtol=0, atol=1e-9 * np.abs(wantE).max())
-    assert EPS0 * (E[-1] - E[0]) == pytest.approx(rho0 * L, rel=1e-9)
+    assert EPS0 * (E[-1] - E[0]) == pytest.approx(rho0 * L, rel=1e-9, abs=0)
 
 
 def test_poisson_gauss_law_random_charge():
@@ -389,8 +389,8 @@ def test_dd_pure_diffusion_variance_grows_2Dt():
         n, gam, flux, cl = o.fluid_update(E, np.zeros(G), n, gam)
         assert cl == 0
     var = (n * z ** 2).sum() / n.sum() - ((n * z).sum() / n.sum()) ** 2
-    assert n.sum() == pytest.approx(m0, rel=1e-12)
-    assert var - var0 == pytest.approx(2 * D * steps * dt, rel=1e-6)
+    assert n.sum() == pytest.approx(m0, rel=1e-12, abs=0)
+    assert var - var0 == pytest.approx(2 * D * steps * dt, rel=1e-6, abs=0)
 
 
 def test_dd_pure_drift_centroid_moves_at_mu_E():
@@ -406,7 +406,7 @@ def test_dd_pure_drift_centroid_moves_at_mu_E():
     for _ in range(steps):
         n, gam, flux, cl = o.fluid_update(E, np.zeros(G), n, gam)
     c1 = (n * z).sum() / n.sum()
-    assert c1 - c0 == pytest.approx(mu * E0 * steps * dt, rel=1e-6)
+    assert c1 - c0 == pytest.approx(mu * E0 * steps * dt, rel=1e-6, abs=0)
 
 
 def _const_tables(p, mu0, nu0):
@@ -452,7 +452,7 @@ def test_fluid_discrete_conservation(model):
     assert cl == 0
     lhs = (dv * (n1 - n)).sum()
     rhs = dt * (dv * src).sum() - dt * (g1[-1] - g1[0])
-    assert lhs == pytest.approx(rhs, rel=1e-9)
+    assert lhs == pytest.approx(rhs, rel=1e-9, abs=0)
     assert flux[0] == max(-g1[0], 0.0) and flux[1] == max(g1[-1], 0.0)
     # the wall flux follows the alpha switch: field-driven, only into the wall
     assert (g1[0] == 0.0) == (E[0] >= 0.0)
@@ -463,10 +463,10 @@ def test_table2_table3_consistency_through_eq_2_6():
     with open(os.path.join(GOLD, "table2_table3_consistency.txt")) as f:
         kv = dict(l.split() for l in f if l.strip() and not l.startswith("#"))
     t = W.ion_tables("he", W.ATM, 300.0)
-    assert t["tab_mu"][0] == pytest.approx(float(kv["mu0_m2_per_Vs"]), rel=1e-12)
-    assert t["tab_nu"][0] == pytest.approx(float(kv["nu0_per_s"]), rel=1e-12)
+    assert t["tab_mu"][0] == pytest.approx(float(kv["mu0_m2_per_Vs"]), rel=1e-12, abs=0)
+    assert t["tab_nu"][0] == pytest.approx(float(kv["nu0_per_s"]), rel=1e-12, abs=0)
     M = 4.002602 * AMU
-    assert QE / (M * t["tab_mu"][0]) == pytest.approx(t["tab_nu"][0], rel=float(kv["rel_tol"]))
+    assert QE / (M * t["tab_mu"][0]) == pytest.approx(t["tab_nu"][0], rel=float(kv["rel_tol"]), abs=0)
 
 
 # --------------------------------------------------------- gamma emission ---
@@ -540,7 +540,7 @@ def test_step_bookkeeping_exact():
         seen_see += see
         assert c["particles"] == prev["particles"] + births + see - d["losses0"] - d["losses1"]
         ne = o.grid(oracle.GRID_NE)
-        assert (ne * dv).sum() == pytest.approx(w * (c["particles"] - births - see), rel=1e-12)
+        assert (ne * dv).sum() == pytest.approx(w * (c["particles"] - births - see), rel=1e-12, abs=0)
         ni = o.grid(oracle.GRID_NI)
         g = o.grid(oracle.GRID_GAMMA)
         src = o.grid(oracle.GRID_GSRC)
@@ -564,7 +564,7 @@ def test_moments_time_average_and_eedf_normalisation():
     assert m["n_samples"] == 20
     np.testing.assert_allclose(m["ne"], ne_sum / 20, rtol=1e-13)
     de = p["eedf_max_ev"] / p["eedf_bins"]
-    assert m["eedf"][:-1].sum() * de + m["eedf"][-1] == pytest.approx(1.0, rel=1e-12)
+    assert m["eedf"][:-1].sum() * de + m["eedf"][-1] == pytest.approx(1.0, rel=1e-12, abs=0)
     # mean energy of a 2 eV Maxwellian, early in the run: 3 eV
     ebar = m["ebar"][m["ebar"] > 0]
     assert 2.0 < np.median(ebar) < 4.0

@@ -57,7 +57,7 @@ def test_fp64_swarm_matches_oracle_ion_by_ion(xs_model):
         _compare_ions(vg[f], vo)
         vt = math.sqrt(1.380649e-23 * 300.0 / M_HE)
         assert abs(g["drift"] - r["drift"]) <= 1e-12 * vt
-        assert g["mean_energy_ev"] == pytest.approx(r["mean_energy_ev"], rel=1e-12)
+        assert g["mean_energy_ev"] == pytest.approx(r["mean_energy_ev"], rel=1e-12, abs=0)
 
 
 def test_computed_bound_matches_the_oracle():
@@ -65,7 +65,7 @@ def test_computed_bound_matches_the_oracle():
     p = W.swarm_params(n_ions=64, n_steps=200, n_relax=100, eps_max_ev=20.0)
     res, _ = hybrid.swarm_run(p, [1e6])
     r = oracle.swarm_run(p, 1e6)
-    assert res[0]["nu_max"] == pytest.approx(r["nu_max"], rel=1e-12)
+    assert res[0]["nu_max"] == pytest.approx(r["nu_max"], rel=1e-12, abs=0)
 
 
 def test_fp32_mobility_close_to_the_fp64_oracle():
@@ -76,7 +76,7 @@ def test_fp32_mobility_close_to_the_fp64_oracle():
     assert rc == 0
     for f, E in enumerate(fields):
         r = oracle.swarm_run(p, E, id_base=f * p["n_ions"])
-        assert res[f]["mobility"] == pytest.approx(r["mobility"], rel=0.02)
+        assert res[f]["mobility"] == pytest.approx(r["mobility"], rel=0.02, abs=0)
 
 
 def test_table_size_run_sampled_against_the_oracle():

@@ -52,7 +52,7 @@ def test_maxwell_gas_drift_follows_the_exact_recursion():
                        dt_s=dt, seed=3)
     r = oracle.swarm_run(p, E)
     P = -math.expm1(-nu * dt)
-    assert r["p_max"] == pytest.approx(P, rel=1e-14)
+    assert r["p_max"] == pytest.approx(P, rel=1e-14, abs=0)
     assert r["collisions"] == r["candidates"]          # nu_max = nu: no null collisions
     q = 1.0 - P * 0.5                                   # m_N / (M + m_N) = 1/2
     a = QE * E / M_HE * dt
@@ -62,10 +62,10 @@ def test_maxwell_gas_drift_follows_the_exact_recursion():
         if n >= n_relax:
             acc += m
     expect = acc / (n_steps - n_relax)
-    assert r["drift"] == pytest.approx(expect, rel=0.02)
+    assert r["drift"] == pytest.approx(expect, rel=0.02, abs=0)
     # the recursion's fixed point tends to the continuum drift e E / (M_r nu), M_r = M/2
     m_inf = q * a / (1.0 - q)
-    assert m_inf == pytest.approx(QE * E / (M_HE / 2 * nu), rel=2e-3)
+    assert m_inf == pytest.approx(QE * E / (M_HE / 2 * nu), rel=2e-3, abs=0)
     # candidates: binomial with probability P over n_ions * n_steps trials
     trials = n_ions * n_steps
     assert abs(r["candidates"] - P * trials) < 5 * math.sqrt(trials * P * (1 - P))
@@ -87,7 +87,7 @@ def test_zero_field_relaxes_to_the_gas_maxwellian():
     assert r["overruns"] == 0
     vt = math.sqrt(KB * 300.0 / M_HE)
     mean_e = 1.5 * KB * 300.0 / QE
-    assert r["mean_energy_ev"] == pytest.approx(mean_e, rel=0.03)
+    assert r["mean_energy_ev"] == pytest.approx(mean_e, rel=0.03, abs=0)
     assert abs(r["drift"]) < 0.02 * vt
     for k in range(3):
         assert stats.kstest(v[:, k] / vt, "norm").pvalue > 1e-3
@@ -124,6 +124,6 @@ def test_mobility_reproduces_the_paper_tables(E):
     r = oracle.swarm_run(p, E)
     assert r["overruns"] == 0
     assert _table2_ok(E, r["mobility"])
-    assert r["nu_exchange"] == pytest.approx(_table3(r["drift"]), rel=0.08)
+    assert r["nu_exchange"] == pytest.approx(_table3(r["drift"]), rel=0.08, abs=0)
     # Eq. 2.6 ties the two outputs
-    assert r["nu_exchange"] * r["mobility"] * M_HE / QE == pytest.approx(1.0, rel=1e-12)
+    assert r["nu_exchange"] * r["mobility"] * M_HE / QE == pytest.approx(1.0, rel=1e-12, abs=0)

@@ -58,7 +58,7 @@ def test_kinetic_ions_full_size_and_sampled_against_oracle():
     assert after["id"].size == c["ions"] and np.unique(after["id"]).size == after["id"].size
     assert np.all((after["z"] >= 0) & (after["z"] < p["gap_m"]))
     ni = g.fields()["ni"]
-    assert (ni * _dv(ni.size, p["gap_m"])).sum() == pytest.approx(g.info["weight"] * c["ions"], rel=1e-5)
+    assert (ni * _dv(ni.size, p["gap_m"])).sum() == pytest.approx(g.info["weight"] * c["ions"], rel=1e-5, abs=0)
     # sampled ions against the oracle's one-ion step
     o = oracle.Oracle(dict(p, n_particles=1))
     rng = np.random.default_rng(5)
@@ -120,7 +120,7 @@ def test_metastable_inventory_full_size():
         m, c = g.metastables(), g.counters()
         now = m["met"][1:-1].sum() * dz
         expect = inv + w * (c["excitation"] - exc) - dt * m["flux"].sum()
-        assert now == pytest.approx(expect, rel=1e-9)
+        assert now == pytest.approx(expect, rel=1e-9, abs=0)
         inv, exc = now, c["excitation"]
     g.close()
 
@@ -144,9 +144,9 @@ def test_power_control_full_size_follows_eq_2_9():
     g.advance(40)
     c1 = g.counters()
     assert c1["power_periods"] == 1
-    assert c1["v_rf"] == pytest.approx(U0 * (1.0 - alpha * (c1["power_last"] - P0) / P0), rel=1e-12)
+    assert c1["v_rf"] == pytest.approx(U0 * (1.0 - alpha * (c1["power_last"] - P0) / P0), rel=1e-12, abs=0)
     g.advance(40)
     c2 = g.counters()
     assert c2["power_periods"] == 2
-    assert c2["v_rf"] == pytest.approx(c1["v_rf"] * (1.0 - alpha * (c2["power_last"] - P0) / P0), rel=1e-12)
+    assert c2["v_rf"] == pytest.approx(c1["v_rf"] * (1.0 - alpha * (c2["power_last"] - P0) / P0), rel=1e-12, abs=0)
     g.close()
