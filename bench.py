@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 BYTES_SPLIT = 48   # per particle-step: read c,o,v,id (28 B) + write c,o,v (20 B)
 BYTES_FP64 = 72    # read z,v,id (40 B) + write z,v (32 B)
 CHUNK = 100
+TUNE_KEYS = ("lanes", "sort_interval", "blocks_per_sm", "field_threads", "field_cluster")
 METRIC = "electron particle-steps/s, FP32-batched vs FP64 plain, 1 GB300; p50/p99 latency"
 
 
@@ -457,7 +458,12 @@ def run_ours(args):
     # launch configuration picked by the library's autotuner on this workload
     # (its trial chunks are real steps of the runs and count as warm-up)
     if args.lanes > 0:
-        tuning = b.set_tuning(lanes=args.lanes)
+        fixed = {"lanes": args.lanes}
+        if args.sort_interval > 0:
+            fixed["sort_interval"] = args.sort_interval
+        if args.field_cluster >= 0:
+            fixed["field_cluster"] = args.field_cluster
+        tuning = b.set_tuning(**fixed)
     elif args.tune_steps > 0:
         tuning = b.autotune(args.tune_steps)
     else:
@@ -523,8 +529,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b2 = hybrid.Batch(args.instances, hybrid.HYB_FP32_SPLIT, stream=stream.cuda_stream)
-        b2.set_tuning(lanes=tuning["lanes"], sort_interval=tuning["sort_interval"],
-                      blocks_per_sm=tuning["blocks_per_sm"], field_threads=tuning["field_threads"])
+        b2.set_tuning(**{k: tuning[k] for k in TUNE_KEYS})
         s2 = [b2.admit(p) for p in params]
         h2d = 0
         for p in params:
@@ -560,7 +565,7 @@ def run_ours(args):
         # every rank serves its round-robin share of the requests on its GPU
         barrier()
         serving = serve_load(args, stream, rank, world,
-                             tuning={k: tuning[k] for k in ("lanes", "sort_interval", "blocks_per_sm", "field_threads")})
+                             tuning={k: tuning[k] for k in TUNE_KEYS})
         wall_ms, steps_all = shard.aggregate(serving["wall_s"] * 1e3, serving["particle_steps"], device="cuda")
         serving["throughput_all_ranks"] = steps_all / (wall_ms / 1e3)
         serving["latency_ranks"] = "rank 0's requests" if world > 1 else "all requests"
@@ -584,7 +589,7 @@ def run_ours(args):
                                f"1e4-2e6 electrons log-uniform, 100-400 V, DD/full ions), FP32 split, "
                                f"{CHUNK}-step CUDA-graph chunks", "instances": args.instances,
                    "initial_particles_per_gpu": total_particles, "chunk_steps": CHUNK,
-                   "tuning": {k: tuning[k] for k in ("lanes", "sort_interval", "blocks_per_sm", "field_threads")},
+                   "tuning": {k: tuning[k] for k in TUNE_KEYS},
                    "l2": "256 MB buffer written between timed chunks; particle store > L2"},
         "p50_ms_per_chunk": lat_sorted[len(lat) // 2], "p99_ms_per_chunk": lat_sorted[min(len(lat) - 1,
                                                                                            int(0.99 * len(lat)))],
@@ -631,6 +636,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--tune-steps", type=int, default=500)
     ap.add_argument("--lanes", type=int, default=0, help="fixed lane count instead of the autotuner's")
+    ap.add_argument("--sort-interval", type=int, default=0, help="with --lanes: fixed sort interval")
+    ap.add_argument("--field-cluster", type=int, default=-1, help="with --lanes: fixed field cluster size (0: auto)")
     ap.add_argument("--serve-requests", type=int, default=100, help="config-4 serving requests (0: none)")
     ap.add_argument("--serve-steps", type=int, default=5000)
     ap.add_argument("--no-swarm", action="store_true")

@@ -325,9 +325,11 @@ int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset);
  *                  with min(4, max_instances));
  *   sort_interval  steps between cell sorts (1..1000, default 20);
  *   blocks_per_sm  electron-kernel blocks per SM (0: the occupancy limit);
- *   field_threads  threads of each instance's field block: 256, 512 or 1024
- *                  (default 256: a small block shares an SM with electron
- *                  blocks of other lanes; a large one finishes sooner alone).
+ *   field_threads  threads of each CTA of an instance's field step: 256, 512
+ *                  or 1024 (default 256);
+ *   field_cluster  CTAs (a thread-block cluster) over which each instance's
+ *                  field step is split: 1, 2, 4 or 8; 0 (default) picks about
+ *                  one grid node per thread for the batch's largest grid.
  * rate is filled by hyb_batch_autotune with the particle-steps/s it measured
  * for the returned choice, and is ignored by hyb_batch_set_tuning. */
 typedef struct hyb_tuning {
@@ -335,6 +337,8 @@ typedef struct hyb_tuning {
     int32_t sort_interval;
     int32_t blocks_per_sm;
     int32_t field_threads;
+    int32_t field_cluster;
+    int32_t pad0;
     double rate;
 } hyb_tuning;
 
@@ -345,7 +349,8 @@ int hyb_batch_set_tuning(hyb_batch *b, const hyb_tuning *t);
 /* Time candidate configurations on the batch's own running discharges and
  * keep the fastest: lanes in {1, 2, 4, 8, 16}, then the sort interval in
  * {10, 20, 50, 100}, then the electron grid at the occupancy limit or twice it,
- * then the field block size in {256, 512, 1024}.
+ * then the field block size in {256, 512, 1024}, then the field cluster in
+ * {automatic, 1, 2, 4, 8}.
  * Each trial advances every running discharge by one untimed chunk and then
  * by trial_steps rounded up to whole chunks (100 steps): those are real steps
  * of the runs.  Profiling must be off.  *chosen may be NULL. */
@@ -353,6 +358,14 @@ int hyb_batch_autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *chosen);
 
 /* The batch behind a single discharge (for profiling and statistics). */
 hyb_batch *hyb_discharge_batch(hyb_discharge *h);
+
+/* Test hook: split = 1 makes the field step of an FP64 batch take the split
+ * mode's arithmetic (reciprocals of the instance constants, table slopes,
+ * Newton reciprocals), everything else staying FP64, so that the rounding of
+ * that arithmetic can be measured against the FP64 mode alone; split = 0
+ * restores the batch's own.  A split-mode batch always takes it.  Waits for
+ * the GPU; the next chunk re-captures its graph.  Errors: HYB_ERR_ARG. */
+int hyb_batch_set_field_arith(hyb_batch *b, int32_t split);
 
 /* First failed device index guard since load: out[0] = guard site (0:
  * none), out[1] = index, out[2] = bound, for the electron, sort and load

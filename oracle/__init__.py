@@ -424,3 +424,29 @@ class Oracle:
         oc = lib().orc_particle_step_one(self.h, _dp(E), int(step), _dp(inp), int(pid), _dp(out),
                                          _dp(child), C.byref(cid))
         return oc, out, child, int(cid.value)
+
+
+# ------------------------------------------------------------- ensembles ---
+
+def _moments_after(job):
+    params, steps = job
+    o = Oracle(params)
+    o.step(steps)
+    out = o.moments()
+    out["counters"] = o.counters()
+    o.close()
+    return out
+
+
+def run_ensemble(params_list, steps, processes=None):
+    """Time-averaged moments (and counters) of each discharge after `steps`
+    steps, the discharges spread over `processes` spawned processes (never
+    forked: the caller may hold a GPU context)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    jobs = [(p, int(steps)) for p in params_list]
+    n = max(1, min(len(jobs), processes or os.cpu_count() or 1))
+    if n == 1:
+        return [_moments_after(j) for j in jobs]
+    with ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_moments_after, jobs))

@@ -289,6 +289,32 @@ void derive(const hyb_params &p, InstDev &K, std::vector<double> &xs, std::vecto
     K.kT_gas = kKb * p.gas_temp_k;
     K.seed_lo = (uint32_t)p.seed;
     K.seed_hi = (uint32_t)(p.seed >> 32);
+    {
+        // field-step constants (Secs. II.B-II.D)
+        FieldK &f = K.fk;
+        const double dz = K.dz, dt = K.dt, w = K.w, mi = K.m_ion, mn = K.m_gas;
+        f.h = dt / (2.0 * dz);
+        f.qdt_m = kQe * dt / mi;
+        f.h_m = f.h / mi;
+        f.c_in = dt / (2.0 * dz);
+        f.c_wall = dt / dz;
+        f.gs_in = w / (dz * dt);
+        f.gs_wall = w / (0.5 * dz * dt);
+        f.hdt = 0.5 * dt;
+        f.tfac = (mi + mn) / (5.0 * mi + 3.0 * mn) * mn;
+        f.inv_ngas_td = 1e21 / K.ngas;
+        f.inv_qe = 1.0 / kQe;
+        f.inv2dz = 1.0 / (2.0 * dz);
+        f.dt_dz = dt / dz;
+        f.dt_2dz = dt / (2.0 * dz);
+        f.h_mion = f.h / mi;
+        f.w_in = w / dz;
+        f.w_wall = 2.0 * w / dz;
+        f.c_src = dz * dz / kEps0;
+        f.inv_dz = 1.0 / dz;
+        f.half_inv_dz = 0.5 / dz;
+        f.c_gauss = dz / (2.0 * kEps0);
+    }
     // nu_max over the table nodes and P_max (Sec. II.A)
     double nu_max = 0.0;
     for (int i = 0; i < p.n_xs; ++i) {
@@ -458,9 +484,11 @@ struct hyb_batch {
     cudaStream_t lstream[kMaxLanes] = {};  // lane k > 0 (lane 0 uses `stream`)
     cudaEvent_t ev_fork = nullptr, ev_join[kMaxLanes] = {};
     int blocks_per_sm = 0;                 // electron grid = SMs x this (0: occupancy limit)
-    int field_threads = 256;               // threads of an instance's field block
+    int field_threads = 256;               // threads of each CTA of an instance's field step
+    int field_cluster = 0;                 // CTAs per instance's field step (0: from the largest grid)
     bool any_chem = false;                 // some admitted discharge has recombination or metastables
     bool any_kin = false;                  // some admitted discharge has kinetic ions
+    bool field_split = false;              // FP64 batch whose field step takes the split-mode arithmetic
     InstDev *d_inst_ion = nullptr;         // ion descriptors, slot for slot (zero: none)
     int64_t *d_prefix_ion = nullptr;       // kMaxLanes x (max_inst + 1)
     int64_t *d_prefix1_ion = nullptr;
@@ -535,6 +563,8 @@ int configure(hyb_batch *b, int nodes, int bins)
 }
 
 int lane_first(const hyb_batch *b, int k) { return k * b->per_lane; }
+// the field step takes the split mode's arithmetic (reciprocals, table slopes)
+bool field_fast(const hyb_batch *b) { return b->precision == HYB_FP32_SPLIT || b->field_split; }
 InstDev *lane_inst_ion(const hyb_batch *b, int k);
 int64_t *lane_prefix_ion(const hyb_batch *b, int k);
 int lane_count(const hyb_batch *b, int k) { return std::max(0, std::min(b->per_lane, b->max_inst - k * b->per_lane)); }
@@ -617,8 +647,8 @@ int launch_step(hyb_batch *b, int k, int lane, cudaStream_t s)
                            b->precision, s));
     }
     if (b->profiling && (rc = record(s, lane_event(b, lane, e + 2)))) return rc;
-    CK(launch_field(lane_inst(b, lane), n, lane_prefix(b, lane), lane_ticket(b, lane), b->precision == HYB_FP32_SPLIT,
-                    b->max_nodes, b->field_threads, s));
+    CK(launch_field(lane_inst(b, lane), n, lane_prefix(b, lane), lane_ticket(b, lane), field_fast(b),
+                    b->max_nodes, b->field_threads, s, b->field_cluster));
     if (b->profiling && (rc = record(s, lane_event(b, lane, e + 3)))) return rc;
     return HYB_OK;
 }
@@ -760,8 +790,8 @@ int reinit_slot(hyb_batch *b, int slot, bool sort)
         CK(launch_prefix_one(I, b->d_prefix1_ion, b->stream));
         CK(launch_ion_step(I, 1, b->d_prefix1_ion, 1, b->cfg.grid, b->max_nodes, b->precision, b->stream));
     }
-    CK(launch_field(K, 1, b->d_prefix1, b->d_ticket1, b->precision == HYB_FP32_SPLIT, b->max_nodes, b->field_threads,
-                    b->stream));
+    CK(launch_field(K, 1, b->d_prefix1, b->d_ticket1, field_fast(b), b->max_nodes, b->field_threads,
+                    b->stream, b->field_cluster));
     if (sort) {
         CK(launch_prefix_one(K, b->d_prefix1, b->stream));
         CK(launch_sort(K, 1, b->d_prefix1, b->precision, b->cfg, b->stream));
@@ -987,6 +1017,9 @@ int set_tuning(hyb_batch *b, const hyb_tuning &t)
     if (t.blocks_per_sm < 0 || t.blocks_per_sm > 64) return fail(HYB_ERR_ARG, "blocks_per_sm must be in [0, 64]");
     if (t.field_threads != 256 && t.field_threads != 512 && t.field_threads != 1024)
         return fail(HYB_ERR_ARG, "field_threads must be 256, 512 or 1024");
+    if (t.field_cluster != 0 && t.field_cluster != 1 && t.field_cluster != 2 && t.field_cluster != 4 &&
+        t.field_cluster != 8)
+        return fail(HYB_ERR_ARG, "field_cluster must be 0, 1, 2, 4 or 8");
     int rc = flush_pending(b);
     if (rc) return rc;
     if (t.lanes != b->lanes && (rc = set_lanes(b, t.lanes))) return rc;
@@ -998,6 +1031,10 @@ int set_tuning(hyb_batch *b, const hyb_tuning &t)
     if (t.field_threads != b->field_threads) {
         if ((rc = drop_graph(b))) return rc;
         b->field_threads = t.field_threads;
+    }
+    if (t.field_cluster != b->field_cluster) {
+        if ((rc = drop_graph(b))) return rc;
+        b->field_cluster = t.field_cluster;
     }
     if (t.blocks_per_sm != b->blocks_per_sm) {
         b->blocks_per_sm = t.blocks_per_sm;
@@ -1014,6 +1051,7 @@ hyb_tuning get_tuning(const hyb_batch *b)
     t.sort_interval = b->sort_interval;
     t.blocks_per_sm = b->blocks_per_sm;
     t.field_threads = b->field_threads;
+    t.field_cluster = b->field_cluster;
     t.rate = 0.0;
     return t;
 }
@@ -1090,6 +1128,14 @@ int autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *out)
         if (f == after_grid.field_threads) continue;
         hyb_tuning t = after_grid;
         t.field_threads = f;
+        trial(t);
+    }
+    const hyb_tuning after_field = best;
+    const int cluster_opts[5] = {0, 1, 2, 4, 8};
+    for (int c : cluster_opts) {
+        if (c == after_field.field_cluster) continue;
+        hyb_tuning t = after_field;
+        t.field_cluster = c;
         trial(t);
     }
     cudaEventDestroy(e0);
@@ -1539,6 +1585,15 @@ int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset)
 }
 
 hyb_batch *hyb_discharge_batch(hyb_discharge *h) { return h ? h->b : nullptr; }
+
+int hyb_batch_set_field_arith(hyb_batch *b, int32_t split)
+{
+    if (!b) return fail(HYB_ERR_ARG, "NULL batch");
+    if (split != 0 && split != 1) return fail(HYB_ERR_ARG, "split must be 0 or 1");
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(HYB_ERR_CUDA, "stream synchronisation failed");
+    b->field_split = split == 1;
+    return drop_graph(b);
+}
 
 int hyb_debug_checks(uint64_t out[6])
 {

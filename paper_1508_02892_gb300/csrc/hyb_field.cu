@@ -1,108 +1,244 @@
-// hyb_field.cu -- the per-instance FP64 grid kernel of each step (arXiv
+// hyb_field.cu -- the per-instance FP64 grid step of each step (arXiv
 // 1508.02892, Secs. II.B-II.D): electron density from the CIC sums, the ion
 // fluid update (drift-diffusion, Eqs. 2.5-2.8, or the full model, Eq. 2.3,
 // then continuity, Eq. 2.4), the Poisson solve and field, the time sums, and
 // the gamma secondaries that will take part in the next step.
 //
-// One CTA of 1024 threads per instance, all node arrays in shared memory
-// (7 x n_nodes doubles), thread t owning a contiguous run of nodes.
+// Each instance's grid is split over a thread-block cluster of up to 8 CTAs
+// (one GPU): CTA r of the cluster owns a contiguous run of nodes and keeps it,
+// with one halo node on each side, in shared memory (8 node arrays).  The FP64
+// work of a step (about a hundred FP64 instructions per node at this part's
+// FP64 rate of two FMA per cycle per SM) is so spread over several SMs.
+//   * Each CTA keeps kHalo + 1 nodes beyond its run on each side, loaded from
+//     global memory (the inputs of the step), and computes the drift-diffusion
+//     fluxes and the Jacobi sweeps of the full model on that wider range
+//     itself: a sweep spoils one node per side, so up to kHalo - 1 sweeps need
+//     no exchange between CTAs at all.  Above that the remaining sweeps pass
+//     the edge values into the neighbours' shared memory (distributed shared
+//     memory) with a cluster barrier each.
+//   * Block scans and maxima combine the CTAs' totals through distributed
+//     shared memory; every CTA combines them in the same order, so all of
+//     them hold the same bits.
 //   * Poisson: the constant-coefficient tridiagonal system is solved in closed
-//     form by two block prefix scans (phi = linear part + discrete double
-//     integral of the charge) instead of the serial Thomas recursion.
+//     form: phi = linear part + discrete double integral of the charge, the
+//     running sum S and the running sum of S formed by one associative scan
+//     instead of the serial Thomas recursion.
 //   * Full-model flux: the tridiagonal system of Eq. 2.3 is diagonally
 //     dominant with ratio r = max (|a|+|c|)/b (a Courant number); it is solved
 //     by Jacobi sweeps, ceil(ln 2^-60 / ln r) of them, which bounds the error
 //     by 2^-60 of the initial one.  r >= 1/2 is reported as unstable.
+//   * The instance constants are formed on the host; the drive sin(2 pi f t)
+//     by one thread beside the others' work.
+// All transport coefficients (mu, T_i, D, nu) and both solves are FP64 in
+// both precision modes; the split mode multiplies by reciprocals of the
+// instance constants where the FP64 mode divides as a plain program would.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "hyb_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hyb {
 
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kArrays = 7;
+constexpr int kArrays = 8;
+constexpr int kMaxCluster = 8;
+constexpr int kSlots = 16;    // reductions across the cluster per step (at most 8 are used)
+constexpr int kMaxTab = 256;  // rows of a transport table staged in shared memory
+constexpr size_t kMaxDynSmem = 160 * 1024;  // node arrays of one CTA, at most
+constexpr int kHalo = 10;     // nodes computed beyond a CTA's run on each side (plus one input node)
 
 struct Red {
-    double w[32];
-    double total;
+    double w[32], wx[32];            // warp totals and their block prefixes
+    double p[3][32], px[3][32];      // the same for the Poisson pair scan
+    double before, all;              // cluster offset and total of the last reduction
+    double cpre[3], ctot[3];         // cluster prefix and total of the pair scan
+    double phi0, v_old;              // drive at the end and at the start of the step
     int flag;
-    int iters;
     unsigned long long count;
 };
 
-// Instance constants of the field step, formed once per block by thread 0
-// (each the same expression the per-node code would evaluate, so results do
-// not change; FP64 division, sin and log are long instruction sequences on
-// this part's FP64 rate).
-struct FieldConsts {
-    double h, inv2dz, qdt_m, h_m, c_in, c_wall, gs_in, gs_wall;  // split-mode fluid
-    double dt_dz, dt_2dz, h_mion;                                // FP64-mode fluid
-    double w_in, w_wall, c_src, inv_dz, half_inv_dz, c_gauss;    // split-mode Poisson
-    double phi0;
-    float inv_ngas_td, tfac;
+// This CTA's place in its instance's cluster.  Ranks 0..nown-1 own nodes
+// [rank P, min(G, (rank + 1) P)); higher ranks own none and only take part in
+// the barriers.
+struct Clu {
+    int rank, size, nown, P, c0, c1;
 };
 
-// Exclusive block scan of one double per thread; *total gets the sum.
-__device__ double block_exscan(double v, Red &r, double *total)
+__device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
+// the two halves of a cluster barrier, for work between them
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ T *cl_remote(T *p, int rank)
+{
+    return cg::this_cluster().map_shared_rank(p, (unsigned)rank);
+}
+
+// Cluster-wide exclusive scan (or max, MAX = true) of one double per thread:
+// the block result is published in this CTA's slot, and after the cluster
+// barrier the first warp reads every CTA's slot and combines them with the
+// same butterfly in every CTA.  Slots are used once per launch, so no CTA can
+// overwrite a slot another one is still reading.  Two block barriers and one
+// cluster barrier.
+template <bool MAX>
+__device__ double cl_reduce(double v, Red &r, const Clu &cu, double *slots, int &ph, double *total)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double x = v;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const double y = __shfl_up_sync(kFull, x, d);
-        if (lane >= d) x += y;
+        if (MAX) {
+            x = fmax(x, __shfl_xor_sync(kFull, x, d));
+        } else {
+            const double y = __shfl_up_sync(kFull, x, d);
+            if (lane >= d) x += y;
+        }
     }
     if (lane == 31) r.w[wid] = x;
     __syncthreads();
+    const int s = ph++;
     if (wid == 0) {
-        double t = lane < nw ? r.w[lane] : 0.0;
+        double y = lane < nw ? r.w[lane] : 0.0;
+        if (MAX) {
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) y = fmax(y, __shfl_xor_sync(kFull, y, d));
+            if (lane == 0) slots[s] = y;
+        } else {
+            double inc = y;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const double z = __shfl_up_sync(kFull, inc, d);
+                if (lane >= d) inc += z;
+            }
+            r.wx[lane] = inc - y;
+            if (lane == 31) slots[s] = inc;
+        }
+    }
+    cl_sync();
+    if (wid == 0) {
+        const int q = lane;
+        double c = q < cu.size ? *cl_remote(&slots[s], q) : 0.0;
+        double cb = q < cu.rank ? c : 0.0;
+#pragma unroll
+        for (int d = 16; d; d >>= 1) {
+            if (MAX) {
+                c = fmax(c, __shfl_xor_sync(kFull, c, d));
+            } else {
+                c += __shfl_xor_sync(kFull, c, d);
+                cb += __shfl_xor_sync(kFull, cb, d);
+            }
+        }
+        if (lane == 0) {
+            r.before = cb;
+            r.all = c;
+        }
+    }
+    __syncthreads();
+    if (total) *total = r.all;
+    return MAX ? r.all : r.wx[wid] + (x - v) + r.before;
+}
+
+// Element of the Poisson scan over a run of nodes: the sum of the sources s,
+// the sum over the run of the running sums of s, and the node count.  Runs
+// combine associatively: (a then b) = (s_a + s_b, t_a + t_b + m_b s_a, m_a + m_b).
+struct Pair {
+    double s, t, m;
+};
+
+__device__ __forceinline__ Pair pcomb(const Pair &a, const Pair &b) { return Pair{a.s + b.s, a.t + b.t + b.m * a.s, a.m + b.m}; }
+
+__device__ __forceinline__ Pair pshfl_up(const Pair &x, int d)
+{
+    return Pair{__shfl_up_sync(kFull, x.s, d), __shfl_up_sync(kFull, x.t, d), __shfl_up_sync(kFull, x.m, d)};
+}
+
+__device__ __forceinline__ Pair pshfl(const Pair &x, int src)
+{
+    return Pair{__shfl_sync(kFull, x.s, src), __shfl_sync(kFull, x.t, src), __shfl_sync(kFull, x.m, src)};
+}
+
+// Exclusive scan of one Pair per thread over the instance's nodes (threads in
+// order within a CTA, CTAs in rank order); *tot gets the total.  Uses three
+// slots; two block barriers and one cluster barrier.
+__device__ Pair pair_scan(Pair v, Red &r, const Clu &cu, double *slots, int &ph, Pair *tot)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const Pair zero{0.0, 0.0, 0.0};
+    Pair x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const Pair y = pshfl_up(x, d);
+        if (lane >= d) x = pcomb(y, x);
+    }
+    Pair xe = pshfl_up(x, 1);
+    if (lane == 0) xe = zero;
+    if (lane == 31) {
+        r.p[0][wid] = x.s;
+        r.p[1][wid] = x.t;
+        r.p[2][wid] = x.m;
+    }
+    __syncthreads();
+    const int s = ph;
+    ph += 3;
+    if (wid == 0) {
+        Pair y = lane < nw ? Pair{r.p[0][lane], r.p[1][lane], r.p[2][lane]} : zero;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const double y = __shfl_up_sync(kFull, t, d);
-            if (lane >= d) t += y;
+            const Pair z = pshfl_up(y, d);
+            if (lane >= d) y = pcomb(z, y);
         }
-        r.w[lane] = t;
+        Pair ye = pshfl_up(y, 1);
+        if (lane == 0) ye = zero;
+        r.px[0][lane] = ye.s;
+        r.px[1][lane] = ye.t;
+        r.px[2][lane] = ye.m;
+        if (lane == 31) {
+            slots[s] = y.s;
+            slots[s + 1] = y.t;
+            slots[s + 2] = y.m;
+        }
+    }
+    cl_sync();
+    if (wid == 0) {
+        const int q = lane;
+        Pair c = q < cu.size ? Pair{*cl_remote(&slots[s], q), *cl_remote(&slots[s + 1], q), *cl_remote(&slots[s + 2], q)}
+                             : zero;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const Pair z = pshfl_up(c, d);
+            if (lane >= d) c = pcomb(z, c);
+        }
+        Pair ce = pshfl_up(c, 1);
+        if (lane == 0) ce = zero;
+        const Pair pre = pshfl(ce, cu.rank), all = pshfl(c, 31);
+        if (lane == 0) {
+            r.cpre[0] = pre.s, r.cpre[1] = pre.t, r.cpre[2] = pre.m;
+            r.ctot[0] = all.s, r.ctot[1] = all.t, r.ctot[2] = all.m;
+        }
     }
     __syncthreads();
-    const double off = wid ? r.w[wid - 1] : 0.0;
-    if (total) *total = r.w[nw - 1];
-    __syncthreads();
-    return off + x - v;
+    *tot = Pair{r.ctot[0], r.ctot[1], r.ctot[2]};
+    return pcomb(Pair{r.cpre[0], r.cpre[1], r.cpre[2]}, pcomb(Pair{r.px[0][wid], r.px[1][wid], r.px[2][wid]}, xe));
 }
 
-__device__ double block_max(double v, Red &r)
+// Jacobi sweeps for a contraction ratio r: ceil(ln 2^-60 / ln r), 1..64 (the
+// same in every thread and CTA: the same r and instructions)
+__device__ __forceinline__ int sweeps_for(double r)
 {
-#pragma unroll
-    for (int d = 16; d; d >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, d));
-    if ((threadIdx.x & 31) == 0) r.w[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double m = threadIdx.x < (blockDim.x >> 5) ? r.w[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int d = 16; d; d >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, d));
-        if (threadIdx.x == 0) r.total = fmax(m, 0.0);
-    }
-    __syncthreads();
-    const double m = r.total;
-    __syncthreads();
-    return m;
-}
-
-// Jacobi sweeps for a contraction ratio r: ceil(ln 2^-60 / ln r), 1..64,
-// formed by thread 0 and shared
-__device__ int jacobi_iters(double r, Red &red)
-{
-    if (threadIdx.x == 0) {
-        int iters = 1;
-        if (r > 1e-300) iters = (int)ceil(-41.58883083359672 / log(r));
-        red.iters = iters < 1 ? 1 : (iters > 64 ? 64 : iters);
-    }
-    __syncthreads();
-    return red.iters;
+    const float lr = logf(fminf((float)r, 0.999f));
+    const int it = (int)ceilf(-41.58883f / lr);
+    return it < 1 ? 1 : (it > 64 ? 64 : it);
 }
 
 // linear interpolation in a 4-column table, clamped at the ends
@@ -124,7 +260,7 @@ __device__ double interp_lin(const double *tab, int n, int cx, int cy, double v)
 
 struct Fluid {
     int model, n_tab;
-    const double *tab;
+    const double *tab;  // shared-memory copy of the instance's table
     double mu_const, ngas, kT, mi, mn;
 
     // ion mobility at |E| (Sec. II.C, tabulated Tables 2/4)
@@ -152,53 +288,97 @@ struct Fluid {
     }
 };
 
-__device__ __forceinline__ double node_volume(int j, int G, double dz) { return (j == 0 || j == G - 1) ? 0.5 * dz : dz; }
+// Split mode: the same coefficients in FP64 with fewer FP64 instructions (this
+// part issues FP64 at two FMA per cycle per SM): the table is staged with the
+// slope of every segment (8 columns: E/N, mu, d mu/d(E/N), u, nu, d nu/du),
+// so a lookup is the search and one FMA, and reciprocals start from the FP32
+// reciprocal with two Newton steps.  Values differ from the FP64 mode's by
+// rounding only.
+constexpr int kTabCols = 8;
 
-// FP32 copy of the transport coefficients for the split mode: the table is
-// staged in shared memory and mu(E), T_i, nu(u) are evaluated in FP32; the
-// state (n, Gamma) and every difference of neighbouring values stay FP64.
-constexpr int kMaxTab = 256;
-
-__device__ __forceinline__ float interp_linf(const float *tab, int n, int cx, int cy, float v)
+__device__ __forceinline__ double lookup_slope(const double *tab, const float *xf, int n, int cx, int cy, int cs,
+                                              double v)
 {
     if (v <= tab[cx]) return tab[cy];
-    if (v >= tab[4 * (n - 1) + cx]) return tab[4 * (n - 1) + cy];
+    if (v >= tab[kTabCols * (n - 1) + cx]) return tab[kTabCols * (n - 1) + cy];
+    // bracket on the FP32 copy of the abscissa, then exact FP64 checks against
+    // the neighbouring nodes, so that x_lo <= v < x_lo+1 in FP64
+    const float vf = (float)v;
     int lo = 0, hi = n - 1;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (tab[4 * mid + cx] <= v)
+        if (xf[mid] <= vf)
             lo = mid;
         else
             hi = mid;
     }
-    const float f = __fdividef(v - tab[4 * lo + cx], tab[4 * (lo + 1) + cx] - tab[4 * lo + cx]);
-    return tab[4 * lo + cy] + f * (tab[4 * (lo + 1) + cy] - tab[4 * lo + cy]);
+    while (lo > 0 && v < tab[kTabCols * lo + cx]) --lo;
+    while (lo < n - 2 && v >= tab[kTabCols * (lo + 1) + cx]) ++lo;
+    return tab[kTabCols * lo + cy] + (v - tab[kTabCols * lo + cx]) * tab[kTabCols * lo + cs];
 }
 
-struct FluidF {
-    int model, n_tab;
-    const float *tab;  // shared memory
-    float mu_const, inv_ngas_td, kT, tfac;
+// 1/x for a normal positive x in the FP32 range: FP32 reciprocal, then two
+// Newton steps r <- r (2 - x r), each squaring the relative error
+__device__ __forceinline__ double rcp_nr(double x)
+{
+    double r = (double)(1.0f / (float)x);
+    r = r * (2.0 - x * r);
+    r = r * (2.0 - x * r);
+    return r;
+}
 
-    __device__ float mobility(float e_abs) const
+struct FluidFast {
+    int model, n_tab;
+    const double *tab;  // kTabCols columns
+    const float *xf;    // FP32 copies of the E/N column, then of the u column
+    double mu_const, kT, tfac, inv_ngas_td;
+
+    __device__ double mobility(double e_abs) const
     {
         if (model == HYB_ION_DD_CONST) return mu_const;
-        return interp_linf(tab, n_tab, 0, 1, e_abs * inv_ngas_td);
+        return lookup_slope(tab, xf, n_tab, 0, 1, 2, e_abs * inv_ngas_td);
     }
-    __device__ float temp(float mu, float e_abs) const
+    __device__ double temp(double mu, double e_abs) const
     {
         if (model == HYB_ION_DD_CONST) return kT;
-        const float ud = mu * e_abs;
+        const double ud = mu * e_abs;
         return kT + tfac * ud * ud;
     }
-    __device__ float exch(float u_abs) const { return interp_linf(tab, n_tab, 3, 2, u_abs); }
+    __device__ double exch(double u_abs) const { return lookup_slope(tab, xf + kMaxTab, n_tab, 3, 4, 5, u_abs); }
     __device__ double wall(int w, double n, double E) const
     {
         const bool into = w == 0 ? (E < 0.0) : (E > 0.0);
         if (!into) return 0.0;
-        return (double)mobility(fabsf((float)E)) * n * E;
+        return mobility(fabs(E)) * n * E;
     }
 };
+
+// Stage an instance's table {E/N, mu, nu, u} in shared memory: as it is
+// (FP64 mode) or with the segment slopes (split mode)
+template <bool FAST>
+__device__ void stage_table(const InstDev *K, double *s_tab, float *s_tabf)
+{
+    const int n = K->n_tab;
+    if constexpr (!FAST) {
+        for (int j = threadIdx.x; j < 4 * n; j += blockDim.x) s_tab[j] = K->tab[j];
+    } else {
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const double *a = K->tab + 4 * k;
+            double *o = s_tab + kTabCols * k;
+            o[0] = a[0];
+            o[1] = a[1];
+            o[3] = a[3];
+            o[4] = a[2];
+            o[2] = k + 1 < n ? (a[5] - a[1]) / (a[4] - a[0]) : 0.0;
+            o[5] = k + 1 < n ? (a[6] - a[2]) / (a[7] - a[3]) : 0.0;
+            o[6] = o[7] = 0.0;
+            s_tabf[k] = (float)a[0];
+            s_tabf[kMaxTab + k] = (float)a[3];
+        }
+    }
+}
+
+__device__ __forceinline__ double node_volume(int j, int G, double dz) { return (j == 0 || j == G - 1) ? 0.5 * dz : dz; }
 
 // Metastables and the ionization they cause (Sec. II.D), from n_m^n at the
 // start of the step:
@@ -218,26 +398,29 @@ __device__ __forceinline__ double birth_mean(const InstDev *K, int proc, double 
     return proc == 0 ? K->met_rp * nm * K->met_nn * dt * dz : K->met_kq * nm * nm * dt * dz;
 }
 
-// old, cnt0, cnt1: G doubles each of shared scratch (n_m at the start of the
-// step, the per-node Penning and pooling counts).  The split mode multiplies by
-// reciprocals where the FP64 mode divides as the oracle does (an FP64 division
-// is a long instruction sequence at this part's FP64 rate).
+// old, cnt0, cnt1: node arrays (global node index) used as scratch: n_m at the
+// start of the step on the loaded range [L0, L1), the per-node Penning and
+// pooling counts of the thread's run [j0, j1).  The split mode multiplies by
+// reciprocals where the FP64 mode divides as the oracle does.
 template <bool FAST>
-__device__ void metastable_step(InstDev *K, double *old, double *cnt0, double *cnt1, Red &red, int j0, int j1)
+__device__ void metastable_step(InstDev *K, double *old, double *cnt0, double *cnt1, Red &red, const Clu &cu,
+                                double *slots, int &ph, int j0, int j1, int L0, int L1)
 {
     const int G = K->G;
+    const int T = blockDim.x, t = threadIdx.x;
     const double dz = K->dz, dt = K->dt, w = K->w;
     const uint32_t n = (uint32_t)K->step;
     const double kp = K->met_kp, kq = K->met_kq;
     const double inv_w = w > 0.0 ? 1.0 / w : 0.0;
     __shared__ unsigned long long s_base;
     __shared__ int64_t s_tot[2];
-    int64_t mine[2] = {0, 0};
-    // counts per node, kept in the scratch row until the update below
-    for (int j = j0; j < j1; ++j) {
-        const double nm = K->met[j];
-        old[j] = nm;
-    }
+    // the slot base, read by rank 0 before its update below and by the other
+    // ranks from rank 0's shared memory after the cluster barriers
+    if (t == 0 && cu.rank == 0) s_base = K->n_slots;
+    // n_m at the start of the step (the neighbours write theirs only after
+    // the cluster barriers below)
+    for (int j = L0 + t; j < L1; j += T) old[j] = K->met[j];
+    __syncthreads();
     double part[2] = {0.0, 0.0};
     for (int proc = 0; proc < 2; ++proc) {
         double *cnt = proc == 0 ? cnt0 : cnt1;
@@ -258,21 +441,23 @@ __device__ void metastable_step(InstDev *K, double *old, double *cnt0, double *c
         }
     }
     double tot[2];
-    const double off0 = block_exscan(part[0], red, &tot[0]);
-    const double off1 = block_exscan(part[1], red, &tot[1]);
+    const double off0 = cl_reduce<false>(part[0], red, cu, slots, ph, &tot[0]);
+    const double off1 = cl_reduce<false>(part[1], red, cu, slots, ph, &tot[1]);
     const int64_t cap = (1 << 20) - 1;
-    if (threadIdx.x == 0) {
+    if (t == 0) {
         s_tot[0] = (int64_t)tot[0] < cap ? (int64_t)tot[0] : cap;
         s_tot[1] = (int64_t)tot[1] < cap ? (int64_t)tot[1] : cap;
-        if ((int64_t)tot[0] > cap || (int64_t)tot[1] > cap) K->status |= HYB_STATUS_EMIT_CAP;
-        s_base = K->n_slots;
-        K->n_slots = s_base + (unsigned long long)(s_tot[0] + s_tot[1]);
-        K->ctr[C_PEN] += (unsigned long long)s_tot[0];
-        K->ctr[C_POOL] += (unsigned long long)s_tot[1];
+        if (cu.rank == 0) {
+            if ((int64_t)tot[0] > cap || (int64_t)tot[1] > cap) atomicOr(&K->status, (unsigned)HYB_STATUS_EMIT_CAP);
+            K->n_slots = s_base + (unsigned long long)(s_tot[0] + s_tot[1]);
+            K->ctr[C_PEN] += (unsigned long long)s_tot[0];
+            K->ctr[C_POOL] += (unsigned long long)s_tot[1];
+        } else {
+            s_base = *cl_remote(&s_base, 0);
+        }
     }
     __syncthreads();
-    mine[0] = (int64_t)off0;
-    mine[1] = (int64_t)off1;
+    const int64_t mine[2] = {(int64_t)off0, (int64_t)off1};
     const PartBuf P = K->buf[K->cur];
     for (int proc = 0; proc < 2; ++proc) {
         if (part[proc] == 0.0) continue;
@@ -287,8 +472,8 @@ __device__ void metastable_step(InstDev *K, double *old, double *cnt0, double *c
                 const double z = ((double)j - 0.5 + u01d(v.x)) * dz;
                 const double ct = 1.0 - 2.0 * u01d(v.y);
                 const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-                const double ph = kTwoPi * u01d(v.z);
-                const double vx = sp * st * cos(ph), vy = sp * st * sin(ph), vz = sp * ct;
+                const double ph2 = kTwoPi * u01d(v.z);
+                const double vx = sp * st * cos(ph2), vy = sp * st * sin(ph2), vz = sp * ct;
                 // the ion of the event (CIC), as for an impact ionization
                 const double x = z / dz;
                 const double f = floor(x);
@@ -323,7 +508,6 @@ __device__ void metastable_step(InstDev *K, double *old, double *cnt0, double *c
             }
         }
     }
-    __syncthreads();
     // the density update from the old values
     const double D = K->met_D;
     const double c_src = w / (dz * dt), c_lap = D / (dz * dz);
@@ -343,77 +527,74 @@ __device__ void metastable_step(InstDev *K, double *old, double *cnt0, double *c
         }
         K->met[j] = nn;
         K->acc_met[j] += nn;
+        // the flux into each wall, by the thread that owns the wall node
+        if (j == 0) K->flux_met[0] = D * old[1] / dz + w * K->s_met[0] / dt;
+        if (j == G - 1) K->flux_met[1] = D * old[G - 2] / dz + w * K->s_met[G - 1] / dt;
     }
     if (clamps) atomicAdd(&red.count, clamps);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        K->flux_met[0] = D * old[1] / dz + w * K->s_met[0] / dt;
-        K->flux_met[1] = D * old[G - 2] / dz + w * K->s_met[G - 1] / dt;
-    }
     __syncthreads();
     for (int j = j0; j < j1; ++j) K->s_met[j] = 0.0;
 }
 
 template <bool FAST>
-__device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, FieldConsts &fc)
+__device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const double *s_tab, const float *s_tabf,
+                           const Clu &cu, double *slots)
 {
     const int G = K->G;
     const int T = blockDim.x;
     const int t = threadIdx.x;
-    const int per = (G + T - 1) / T;
-    const int j0 = min(t * per, G), j1 = min(j0 + per, G);
+    const int c0 = cu.c0, c1 = cu.c1;
+    const bool own = c1 > c0;
+    // the thread's contiguous run of the CTA's nodes (for the scans)
+    const int pt = own ? (c1 - c0 + T - 1) / T : 0;
+    const int j0 = min(c0 + t * pt, c1), j1 = min(j0 + pt, c1);
+    // nodes loaded from global memory, and the wider range computed here
+    const int L0 = own ? max(0, c0 - kHalo - 1) : c0, L1 = own ? min(G, c1 + kHalo + 1) : c0;
+    const int e0 = own ? max(0, c0 - kHalo) : c0, e1 = own ? min(G, c1 + kHalo) : c0;
+    const FieldK &fk = K->fk;
     const double dz = K->dz, dt = K->dt, w = K->w;
     const bool init = K->init_pending != 0;
+    const bool kin = K->ion_model == HYB_ION_KINETIC;
+    int ph = 0;
 
-    double *s_ni = sm;
-    double *s_E = sm + G;
-    double *s_g = sm + 2 * G;
-    double *s_A = sm + 3 * G;
-    double *s_ib = sm + 4 * G;
-    double *s_d = sm + 5 * G;
-    double *s_x = sm + 6 * G;
+    // node arrays: base pointers (local index 0 = node c0 - kHalo - 1) and
+    // views indexed by the global node number
+    double *b_ni = sm, *b_E = sm + lw, *b_g = sm + 2 * lw, *b_A = sm + 3 * lw;
+    double *b_ib = sm + 4 * lw, *b_d = sm + 5 * lw, *b_x = sm + 6 * lw, *b_cp = sm + 7 * lw;
+    const int sh = kHalo + 1 - c0;
+    double *s_ni = b_ni + sh, *s_E = b_E + sh, *s_g = b_g + sh, *s_A = b_A + sh;
+    double *s_ib = b_ib + sh, *s_d = b_d + sh, *s_x = b_x + sh, *s_cp = b_cp + sh;
 
-    for (int j = j0; j < j1; ++j) {
-        s_ni[j] = K->ni[j];
-        s_E[j] = K->E[j];
-        s_g[j] = K->gam[j];
-    }
-    if (t == 0) {
+    // the drive at the end of the step (and at its start, for the absorbed
+    // power), by the last thread beside the others' work
+    if (t == T - 1) {
         red.flag = 0;
         red.count = 0ull;
-        const double mi = K->m_ion, mn = K->m_gas;
-        fc.h = dt / (2.0 * dz);
-        fc.inv2dz = 1.0 / (2.0 * dz);
-        fc.qdt_m = kQe * dt / mi;
-        fc.h_m = fc.h / mi;
-        fc.c_in = dt * fc.inv2dz;
-        fc.c_wall = dt / dz;
-        fc.gs_in = w / (dz * dt);
-        fc.gs_wall = w / (0.5 * dz * dt);
-        fc.dt_dz = dt / dz;
-        fc.dt_2dz = dt / (2.0 * dz);
-        fc.h_mion = fc.h / K->m_ion;
-        fc.w_in = w / dz;
-        fc.w_wall = 2.0 * w / dz;
-        fc.c_src = dz * dz / kEps0;
-        fc.inv_dz = 1.0 / dz;
-        fc.half_inv_dz = 0.5 / dz;
-        fc.c_gauss = dz / (2.0 * kEps0);
-        fc.phi0 = K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)(K->step + (init ? 0 : 1)) * dt));
-        fc.inv_ngas_td = (float)(1e21 / K->ngas);
-        fc.tfac = (float)((mi + mn) / (5.0 * mi + 3.0 * mn) * mn);
+        red.phi0 = K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)(K->step + (init ? 0 : 1)) * dt));
+        red.v_old = (cu.rank == 0 && !init) ? K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)K->step * dt)) : 0.0;
+    }
+    // inputs of the step (every write of these globals comes after at least
+    // one cluster barrier)
+    if (!kin) {
+        for (int j = L0 + t; j < L1; j += T) {
+            s_ni[j] = K->ni[j];
+            s_E[j] = K->E[j];
+            s_g[j] = K->gam[j];
+        }
+    } else {
+        for (int j = c0 + t; j < c1; j += T) s_E[j] = K->E[j];
     }
     __syncthreads();
 
-    if (K->met_on && !init) metastable_step<FAST>(K, s_d, s_x, s_ib, red, j0, j1);
+    if (K->met_on && !init) metastable_step<FAST>(K, s_d, s_x, s_ib, red, cu, slots, ph, j0, j1, L0, L1);
 
-    const Fluid F{K->ion_model, K->n_tab, K->tab, K->mu_const, K->ngas, K->kT_gas, K->m_ion, K->m_gas};
+    const Fluid F{K->ion_model, K->n_tab, s_tab, K->mu_const, K->ngas, K->kT_gas, K->m_ion, K->m_gas};
+    const FluidFast FF{K->ion_model, K->n_tab, s_tab, s_tabf, K->mu_const, K->kT_gas, fk.tfac, fk.inv_ngas_td};
     double *gfin = s_g;
-    const bool kin = K->ion_model == HYB_ION_KINETIC;
     if (kin) {
         // kinetic ions: n_i and Gamma_i from the ions' charge assignment of this
         // step (at initialisation, of the loaded ions)
-        for (int j = j0; j < j1; ++j) {
+        for (int j = c0 + t; j < c1; j += T) {
             const double vol = node_volume(j, G, dz);
             const double nn = w * K->dep_ni[j] / vol;
             const double gg = w * K->dep_gi[j] / vol;
@@ -431,153 +612,112 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
         }
         __syncthreads();
     }
-    if (FAST && !init && !kin) {
-        // ------------------------------------ ion fluid, FP32 coefficients
-        for (int j = t; j < 4 * K->n_tab; j += T) s_tabf[j] = (float)K->tab[j];
-        __syncthreads();
-        const FluidF FF{K->ion_model, K->n_tab, s_tabf, (float)K->mu_const, fc.inv_ngas_td, (float)K->kT_gas,
-                        fc.tfac};
-        const double h = fc.h;
-        const double inv2dz = fc.inv2dz;
-        if (K->ion_model == HYB_ION_FULL) {
-            const double qdt_m = fc.qdt_m, h_m = fc.h_m;
-            const float hdt = (float)(0.5 * dt);
-            for (int j = j0; j < j1; ++j) {
-                const double nj = s_ni[j];
-                const float A = nj >= K->n_floor ? (float)s_g[j] / (float)nj : 0.f;
-                s_A[j] = h * (double)A;  // h Gamma/n, the advection coefficient
-                const float ea = fabsf((float)s_E[j]);
-                s_x[j] = nj * (double)FF.temp(FF.mobility(ea), ea);
-            }
-            __syncthreads();
-            float rmax = 0.f;
-            for (int j = j0; j < j1; ++j) {
-                if (j == 0 || j == G - 1) continue;
-                const float nu = FF.exch(fabsf((float)(s_A[j] / h)));
-                const float ib = 1.f / (1.f + nu * hdt);
-                s_d[j] = s_g[j] * (double)(1.f - nu * hdt) + qdt_m * s_ni[j] * s_E[j] - h_m * (s_x[j + 1] - s_x[j - 1]);
-                s_ib[j] = (double)ib;
-                rmax = fmaxf(rmax, (fabsf((float)s_A[j - 1]) + fabsf((float)s_A[j + 1])) * ib);
-            }
-            const double r = block_max((double)rmax, red);
-            if (t == 0) {
-                const double g0 = FF.wall(0, s_ni[0], s_E[0]);
-                const double gN = FF.wall(1, s_ni[G - 1], s_E[G - 1]);
-                s_g[0] = g0;
-                s_x[0] = g0;
-                s_g[G - 1] = gN;
-                s_x[G - 1] = gN;
-                if (r >= 0.5) atomicOr(&K->status, (unsigned)HYB_STATUS_UNSTABLE);
-            }
-            const int iters = jacobi_iters(r, red);
-            double *X = s_g, *Y = s_x;
-            for (int it = 0; it < iters; ++it) {
-                for (int j = j0; j < j1; ++j) {
-                    if (j == 0 || j == G - 1) continue;
-                    Y[j] = (s_d[j] + s_A[j - 1] * X[j - 1] - s_A[j + 1] * X[j + 1]) * s_ib[j];
-                }
-                __syncthreads();
-                double *tmp = X;
-                X = Y;
-                Y = tmp;
-            }
-            gfin = X;
-        } else {
-            for (int j = j0; j < j1; ++j) {
-                if (j == 0) {
-                    s_x[j] = FF.wall(0, s_ni[0], s_E[0]);
-                } else if (j == G - 1) {
-                    s_x[j] = FF.wall(1, s_ni[G - 1], s_E[G - 1]);
-                } else {
-                    const float ea = fabsf((float)s_E[j]);
-                    const float mu = FF.mobility(ea);
-                    const float D = mu * FF.temp(mu, ea) * (float)(1.0 / kQe);
-                    s_x[j] = (double)mu * s_ni[j] * s_E[j] - (double)D * ((s_ni[j + 1] - s_ni[j - 1]) * inv2dz);
-                }
-            }
-            __syncthreads();
-            gfin = s_x;
-        }
-        unsigned long long clamps = 0;
-        const double c_in = fc.c_in, c_wall = fc.c_wall;
-        const double gs_in = fc.gs_in, gs_wall = fc.gs_wall;
-        for (int j = j0; j < j1; ++j) {
-            const bool wall = j == 0 || j == G - 1;
-            const double gs = K->s_iz[j] * (wall ? gs_wall : gs_in);
-            double nn;
-            if (j == 0)
-                nn = s_ni[0] - c_wall * (gfin[1] - gfin[0]) + dt * gs;
-            else if (j == G - 1)
-                nn = s_ni[G - 1] - c_wall * (gfin[G - 1] - gfin[G - 2]) + dt * gs;
-            else
-                nn = s_ni[j] - c_in * (gfin[j + 1] - gfin[j - 1]) + dt * gs;
-            if (nn < 0.0) {
-                nn = 0.0;
-                ++clamps;
-            }
-            s_ni[j] = nn;
-            K->ni[j] = nn;
-            K->gam[j] = gfin[j];
-            K->gsrc[j] = gs;
-            K->acc_ni[j] += nn;
-            K->acc_gi[j] += gfin[j];
-        }
-        if (clamps) atomicAdd(&red.count, clamps);
-        __syncthreads();
-    }
-    if (!FAST && !init && !kin) {
+    if (!init && !kin) {
         // ---------------------------------------------------------- ion fluid
         if (K->ion_model == HYB_ION_FULL) {
-            // Eq. 2.3: nu at u^n = Gamma^{n-1/2}/n^n, advection semi-implicit
-            for (int j = j0; j < j1; ++j) {
+            // Eq. 2.3: nu at u^n = Gamma^{n-1/2}/n^n, advection semi-implicit;
+            // A = Gamma/n and n T on the loaded range
+            for (int j = L0 + t; j < L1; j += T) {
                 const double nj = s_ni[j];
-                s_A[j] = nj >= K->n_floor ? s_g[j] / nj : 0.0;
                 const double ea = fabs(s_E[j]);
-                s_x[j] = nj * F.temp(F.mobility(ea), ea);
+                if (FAST) {
+                    s_A[j] = nj >= K->n_floor ? s_g[j] * rcp_nr(nj) : 0.0;
+                    s_x[j] = nj * FF.temp(FF.mobility(ea), ea);
+                } else {
+                    s_A[j] = nj >= K->n_floor ? s_g[j] / nj : 0.0;
+                    s_x[j] = nj * F.temp(F.mobility(ea), ea);
+                }
             }
             __syncthreads();
-            const double h = fc.h;
+            const double h = fk.h;
             double rmax = 0.0;
-            for (int j = j0; j < j1; ++j) {
+            for (int j = e0 + t; j < e1; j += T) {
                 if (j == 0 || j == G - 1) continue;
-                const double nu = F.exch(fabs(s_A[j]));
-                const double b = 1.0 + nu * dt / 2.0;
-                s_d[j] = s_g[j] * (1.0 - nu * dt / 2.0) + kQe * s_ni[j] * s_E[j] * dt / K->m_ion -
-                         fc.h_mion * (s_x[j + 1] - s_x[j - 1]);
-                s_ib[j] = 1.0 / b;
-                rmax = fmax(rmax, (fabs(h * s_A[j - 1]) + fabs(h * s_A[j + 1])) / b);
-            }
-            const double r = block_max(rmax, red);
-            // Dirichlet wall rows (field-driven wall flux), both Jacobi buffers
-            if (t == 0) {
-                const double g0 = F.wall(0, s_ni[0], s_E[0]);
-                const double gN = F.wall(1, s_ni[G - 1], s_E[G - 1]);
-                s_g[0] = g0;
-                s_x[0] = g0;
-                s_g[G - 1] = gN;
-                s_x[G - 1] = gN;
-                if (r >= 0.5) atomicOr(&K->status, (unsigned)HYB_STATUS_UNSTABLE);
-            }
-            const int iters = jacobi_iters(r, red);
-            double *X = s_g, *Y = s_x;
-            for (int it = 0; it < iters; ++it) {
-                for (int j = j0; j < j1; ++j) {
-                    if (j == 0 || j == G - 1) continue;
-                    Y[j] = (s_d[j] + h * s_A[j - 1] * X[j - 1] - h * s_A[j + 1] * X[j + 1]) * s_ib[j];
+                double q;
+                if (FAST) {
+                    // the row divided by its diagonal: Y_j = dd_j + cm_j X_{j-1} - cp_j X_{j+1}
+                    const double nu = FF.exch(fabs(s_A[j]));
+                    const double ib = rcp_nr(1.0 + nu * fk.hdt);
+                    const double d = s_g[j] * (1.0 - nu * fk.hdt) + fk.qdt_m * s_ni[j] * s_E[j] -
+                                     fk.h_m * (s_x[j + 1] - s_x[j - 1]);
+                    const double cm = h * s_A[j - 1] * ib, cp = h * s_A[j + 1] * ib;
+                    s_d[j] = d * ib;
+                    s_ib[j] = cm;
+                    s_cp[j] = cp;
+                    q = fabs(cm) + fabs(cp);
+                } else {
+                    const double nu = F.exch(fabs(s_A[j]));
+                    const double b = 1.0 + nu * dt / 2.0;
+                    s_d[j] = s_g[j] * (1.0 - nu * dt / 2.0) + kQe * s_ni[j] * s_E[j] * dt / K->m_ion -
+                             fk.h_mion * (s_x[j + 1] - s_x[j - 1]);
+                    s_ib[j] = 1.0 / b;
+                    q = (fabs(h * s_A[j - 1]) + fabs(h * s_A[j + 1])) / b;
                 }
-                __syncthreads();
+                if (j >= c0 && j < c1) rmax = fmax(rmax, q);
+            }
+            const double r = cl_reduce<true>(rmax, red, cu, slots, ph, nullptr);
+            // both sweep buffers start from Gamma^{n-1/2}, with the Dirichlet
+            // wall rows (field-driven wall flux); the nodes at the ends of the
+            // loaded range keep their value through the local sweeps
+            for (int j = L0 + t; j < L1; j += T) {
+                double v = s_g[j];
+                if (j == 0 || j == G - 1) {
+                    const int wl = j == 0 ? 0 : 1;
+                    v = FAST ? FF.wall(wl, s_ni[j], s_E[j]) : F.wall(wl, s_ni[j], s_E[j]);
+                }
+                s_g[j] = v;
+                s_x[j] = v;
+            }
+            if (t == 0 && cu.rank == 0 && r >= 0.5) atomicOr(&K->status, (unsigned)HYB_STATUS_UNSTABLE);
+            const int iters = sweeps_for(r);
+            const int nloc = min(iters, kHalo - 1);
+            __syncthreads();
+            double *X = s_g, *Y = s_x;
+            double *bX = b_g, *bY = b_x;
+            // local sweeps over the computed range: after k of them the k
+            // nodes at each end are spoiled, the CTA's run and one node on
+            // each side are exact
+            for (int it = 0; it < iters; ++it) {
+                const bool local = it < nloc;
+                const int a = local ? e0 : c0, b = local ? e1 : c1;
+                for (int j = a + t; j < b; j += T) {
+                    if (j == 0 || j == G - 1) continue;
+                    if (FAST)
+                        Y[j] = s_d[j] + s_ib[j] * X[j - 1] - s_cp[j] * X[j + 1];
+                    else
+                        Y[j] = (s_d[j] + h * s_A[j - 1] * X[j - 1] - h * s_A[j + 1] * X[j + 1]) * s_ib[j];
+                }
+                if (local) {
+                    __syncthreads();
+                } else {
+                    // beyond kHalo - 1 sweeps: the CTA's edge values go to the
+                    // neighbours' halo nodes each sweep
+                    __syncthreads();
+                    if (t == 0 && own && cu.rank > 0) *cl_remote(&bY[cu.P + kHalo + 1], cu.rank - 1) = Y[c0];
+                    if (t == 1 && own && cu.rank + 1 < cu.nown) *cl_remote(&bY[kHalo], cu.rank + 1) = Y[c1 - 1];
+                    cl_sync();
+                }
                 double *tmp = X;
                 X = Y;
                 Y = tmp;
+                tmp = bX;
+                bX = bY;
+                bY = tmp;
             }
             gfin = X;
         } else {
-            // Eq. 2.5 at level n (explicit drift-diffusion)
-            for (int j = j0; j < j1; ++j) {
-                if (j == 0) {
-                    s_x[j] = F.wall(0, s_ni[0], s_E[0]);
-                } else if (j == G - 1) {
-                    s_x[j] = F.wall(1, s_ni[G - 1], s_E[G - 1]);
+            // Eq. 2.5 at level n (explicit drift-diffusion), on the CTA's run
+            // and one node beyond it on each side
+            const int a = own ? max(0, c0 - 1) : c0, b = own ? min(G, c1 + 1) : c0;
+            for (int j = a + t; j < b; j += T) {
+                if (j == 0 || j == G - 1) {
+                    const int wl = j == 0 ? 0 : 1;
+                    s_x[j] = FAST ? FF.wall(wl, s_ni[j], s_E[j]) : F.wall(wl, s_ni[j], s_E[j]);
+                } else if (FAST) {
+                    const double ea = fabs(s_E[j]);
+                    const double mu = FF.mobility(ea);
+                    const double D = mu * FF.temp(mu, ea) * fk.inv_qe;
+                    s_x[j] = mu * s_ni[j] * s_E[j] - D * ((s_ni[j + 1] - s_ni[j - 1]) * fk.inv2dz);
                 } else {
                     const double ea = fabs(s_E[j]);
                     const double mu = F.mobility(ea);
@@ -590,15 +730,17 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
         }
         // ------------------------------------- continuity, Eq. 2.4 (G^n source)
         unsigned long long clamps = 0;
-        for (int j = j0; j < j1; ++j) {
-            const double gs = w * K->s_iz[j] / (node_volume(j, G, dz) * dt);
+        for (int j = c0 + t; j < c1; j += T) {
+            const bool wall = j == 0 || j == G - 1;
+            const double gs = FAST ? K->s_iz[j] * (wall ? fk.gs_wall : fk.gs_in)
+                                   : w * K->s_iz[j] / (node_volume(j, G, dz) * dt);
             double nn;
             if (j == 0)
-                nn = s_ni[0] - fc.dt_dz * (gfin[1] - gfin[0]) + dt * gs;
+                nn = s_ni[0] - (FAST ? fk.c_wall : fk.dt_dz) * (gfin[1] - gfin[0]) + dt * gs;
             else if (j == G - 1)
-                nn = s_ni[G - 1] - fc.dt_dz * (gfin[G - 1] - gfin[G - 2]) + dt * gs;
+                nn = s_ni[G - 1] - (FAST ? fk.c_wall : fk.dt_dz) * (gfin[G - 1] - gfin[G - 2]) + dt * gs;
             else
-                nn = s_ni[j] - fc.dt_2dz * (gfin[j + 1] - gfin[j - 1]) + dt * gs;
+                nn = s_ni[j] - (FAST ? fk.c_in : fk.dt_2dz) * (gfin[j + 1] - gfin[j - 1]) + dt * gs;
             if (nn < 0.0) {
                 nn = 0.0;
                 ++clamps;
@@ -618,108 +760,105 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
         // bound of the next electron step's recombination test (Sec. II.D):
         // nu_rec,max = max_z n_i * max sigma_rec v; the split mode reads n_i / max n_i
         double m = 0.0;
-        for (int j = j0; j < j1; ++j) m = fmax(m, s_ni[j]);
-        const double nimax = block_max(m, red);
-        if (t == 0) {
+        for (int j = c0 + t; j < c1; j += T) m = fmax(m, s_ni[j]);
+        const double nimax = cl_reduce<true>(m, red, cu, slots, ph, nullptr);
+        if (t == 0 && cu.rank == 0) {
             K->rec_numax = nimax * K->rec_svmax;
             K->rec_pmax = -expm1(-K->rec_numax * dt);
             K->f_rec_pmax = (float)K->rec_pmax;
         }
         const double inv = nimax > 0.0 ? 1.0 / nimax : 0.0;
-        for (int j = j0; j < j1; ++j) K->nif[j] = (float)(s_ni[j] * inv);
+        for (int j = c0 + t; j < c1; j += T) K->nif[j] = (float)(s_ni[j] * inv);
     }
 
     // ------------------------------------------------------------- Poisson
-    const double phi0 = fc.phi0;
+    // -eps0 phi'' = e (n_i - n_e): with s_j = dz^2 rho_j / eps0 (interior),
+    // S_j = sum_{k<=j} s_k and T_j = sum_{k<j} S_k,
+    //   d_0 = (phi_N - phi_0 + T_{G-1})/(G-1),  d_j = d_0 - S_j,
+    //   phi_j = phi_0 + j d_0 - T_j,  E from the d_j (Gauss at the walls)
     double *s_rho = s_A;
-    double *s_S = s_ib;
-    double *s_phi = s_d;
-    double part = 0.0;
-    // the split mode multiplies by reciprocals where the FP64 mode divides (as
-    // the oracle does); FP64 division is a long instruction sequence here
-    const double w_in = fc.w_in, w_wall = fc.w_wall, c_src = fc.c_src;
-    for (int j = j0; j < j1; ++j) {
-        const double ne = FAST ? K->dep_n[j] * ((j == 0 || j == G - 1) ? w_wall : w_in)
-                               : w * K->dep_n[j] / node_volume(j, G, dz);
-        K->ne[j] = ne;
-        const double rho = kQe * (s_ni[j] - ne);
-        s_rho[j] = rho;
-        const double sj = (j >= 1 && j <= G - 2) ? (FAST ? rho * c_src : dz * dz * rho / kEps0) : 0.0;
-        part += sj;
-        s_S[j] = part;  // local inclusive
-        if (!init) {
-            K->acc_ne[j] += ne;
-            K->acc_wn[j] += K->dep_n[j];
-            K->acc_we[j] += K->dep_e[j];
+    double *s_s = s_ib;
+    Pair mine{0.0, 0.0, (double)(j1 - j0)};
+    {
+        double loc = 0.0;
+        for (int j = j0; j < j1; ++j) {
+            const double ne = FAST ? K->dep_n[j] * ((j == 0 || j == G - 1) ? fk.w_wall : fk.w_in)
+                                   : w * K->dep_n[j] / node_volume(j, G, dz);
+            K->ne[j] = ne;
+            const double rho = kQe * (s_ni[j] - ne);
+            s_rho[j] = rho;
+            const double sj = (j >= 1 && j <= G - 2) ? (FAST ? rho * fk.c_src : dz * dz * rho / kEps0) : 0.0;
+            s_s[j] = sj;
+            loc += sj;
+            mine.t += loc;
+            if (!init) {
+                K->acc_ne[j] += ne;
+                K->acc_wn[j] += K->dep_n[j];
+                K->acc_we[j] += K->dep_e[j];
+            }
+            K->dep_n[j] = 0.0;
+            K->dep_e[j] = 0.0;
+            K->s_iz[j] = 0.0;
         }
-        K->dep_n[j] = 0.0;
-        K->dep_e[j] = 0.0;
-        K->s_iz[j] = 0.0;
+        mine.s = loc;
     }
-    // S_j = sum_{k=1..j} s_k
-    const double off = block_exscan(part, red, nullptr);
-    double ssum = 0.0;
-    for (int j = j0; j < j1; ++j) {
-        s_S[j] += off;
-        if (j <= G - 2) ssum += s_S[j];
-    }
-    double stot;
-    block_exscan(ssum, red, &stot);
-    // d_0 = (phi_N - phi_0 + sum_{j=0}^{G-2} S_j)/(G-1); d_j = d_0 - S_j
-    const double d0 = FAST ? (0.0 - phi0 + stot) * K->inv_gm1 : (0.0 - phi0 + stot) / (double)(G - 1);
-    double dpart = 0.0;
-    for (int j = j0; j < j1; ++j) {
-        const double dj = j <= G - 2 ? d0 - s_S[j] : 0.0;
-        s_phi[j] = dpart;  // local exclusive
-        dpart += dj;
-    }
-    const double doff = block_exscan(dpart, red, nullptr);
-    for (int j = j0; j < j1; ++j) s_phi[j] = phi0 + doff + s_phi[j];
-    __syncthreads();
-    if (t == 0) s_phi[G - 1] = 0.0;
-    __syncthreads();
+    Pair all;
+    const Pair pre = pair_scan(mine, red, cu, slots, ph, &all);
+    // this CTA reads no other CTA's shared memory from here on
+    cl_arrive();
+    const double phi0 = red.phi0;
+    const double d0 = FAST ? (0.0 - phi0 + (all.t - all.s)) * K->inv_gm1 : (0.0 - phi0 + (all.t - all.s)) / (double)(G - 1);
     int bad = 0;
-    const double inv_dz = fc.inv_dz, half_inv_dz = fc.half_inv_dz, c_gauss = fc.c_gauss;
+    double S = pre.s, Tx = pre.t;
     for (int j = j0; j < j1; ++j) {
+        const double Sprev = S, Tj = Tx;
+        S += s_s[j];
+        Tx += S;
         double e;
         if (FAST) {
             if (j == 0)
-                e = -d0 * inv_dz - s_rho[0] * c_gauss;
+                e = -d0 * fk.inv_dz - s_rho[0] * fk.c_gauss;
             else if (j == G - 1)
-                e = -(d0 - s_S[G - 2]) * inv_dz + s_rho[G - 1] * c_gauss;
+                e = -(d0 - Sprev) * fk.inv_dz + s_rho[G - 1] * fk.c_gauss;
             else
-                e = -((d0 - s_S[j]) + (d0 - s_S[j - 1])) * half_inv_dz;
+                e = -((d0 - S) + (d0 - Sprev)) * fk.half_inv_dz;
         } else if (j == 0) {
             e = -d0 / dz - s_rho[0] * dz / (2.0 * kEps0);
         } else if (j == G - 1) {
-            e = -(d0 - s_S[G - 2]) / dz + s_rho[G - 1] * dz / (2.0 * kEps0);
+            e = -(d0 - Sprev) / dz + s_rho[G - 1] * dz / (2.0 * kEps0);
         } else {
-            e = -((d0 - s_S[j]) + (d0 - s_S[j - 1])) / (2.0 * dz);
+            e = -((d0 - S) + (d0 - Sprev)) / (2.0 * dz);
         }
         K->E[j] = e;
         K->Ef[j] = (float)e;
-        K->phi[j] = s_phi[j];
+        K->phi[j] = j == G - 1 ? 0.0 : phi0 + (double)j * d0 - Tj;
         if (!isfinite(e) || !isfinite(s_ni[j])) bad = 1;
     }
     if (bad) red.flag = 1;
     __syncthreads();
-    if (red.flag && t == 0) atomicOr(&K->status, (unsigned)HYB_STATUS_NONFINITE);
+    if (t == 0) {
+        if (red.flag) atomicOr(&K->status, (unsigned)HYB_STATUS_NONFINITE);
+        if (red.count && !init) atomicAdd(&K->ctr[C_CLAMP], red.count);
+    }
 
     if (init) {
-        if (t == 0) {
+        if (t == 0 && cu.rank == 0) {
             K->n_slots_step = (int64_t)K->n_slots;
             K->init_pending = 0;
         }
         return;
     }
+    // rank 0 finishes the step: the other CTAs' writes it reads (the wall
+    // flux at z = L, the metastable flux there) came before the cluster
+    // barrier of the Poisson scan
+    if (cu.rank != 0) return;
 
     // ------------------------------------------- bookkeeping, gamma emission
     __shared__ int s_cnt[2];
     __shared__ unsigned long long s_base;
     if (t == 0) {
-        if (red.count) K->ctr[C_CLAMP] += red.count;
         K->n_samples += 1;
-        const double v_old = K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)K->step * dt));
+        const double v_old = red.v_old;
         if (kin) {  // the ions removed at each wall this step
             const InstDev *I = K->ion;
             const unsigned long long l0 = I->ctr[C_LOSS0], l1 = I->ctr[C_LOSS1];
@@ -728,7 +867,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
             K->ion_loss_prev[0] = l0;
             K->ion_loss_prev[1] = l1;
         } else {
-            const double g0 = gfin[0], gN = gfin[G - 1];
+            const double g0 = gfin[0], gN = K->gam[G - 1];
             K->flux_in[0] = g0 < 0.0 ? -g0 : 0.0;
             K->flux_in[1] = gN > 0.0 ? gN : 0.0;
         }
@@ -746,7 +885,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
                 int64_t c = (int64_t)k + (u01d(r.x) < frac ? 1 : 0);
                 if (c > (1 << 20) - 1) {
                     c = (1 << 20) - 1;
-                    K->status |= HYB_STATUS_EMIT_CAP;
+                    atomicOr(&K->status, (unsigned)HYB_STATUS_EMIT_CAP);
                 }
                 s_cnt[wall] = (int)c;
             }
@@ -763,7 +902,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
         const unsigned long long l0 = K->ctr[C_LOSS0];
         const int64_t d_loss0 = (int64_t)(l0 - K->pw_loss0), d_see0 = s_cnt[0];
         K->pw_loss0 = l0;
-        const double v_mid = 0.5 * (v_old + fc.phi0);
+        const double v_mid = 0.5 * (v_old + phi0);
         const double jz = kQe * gfin[0] + kQe * w * (double)(d_loss0 - d_see0) / dt + kEps0 * (K->E[0] - s_E[0]) / dt;
         K->pw_acc += v_mid * jz * dt;
         if (++K->pw_count == K->pw_steps) {
@@ -788,9 +927,9 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
             const uint4 r = draw(id, n, K->seed_lo, K->seed_hi, 7);
             const double ct = sqrt(u01d(r.x));
             const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-            const double ph = kTwoPi * u01d(r.y);
+            const double phw = kTwoPi * u01d(r.y);
             const double vn = sp * ct;
-            const double vx = sp * st * cos(ph), vy = sp * st * sin(ph);
+            const double vx = sp * st * cos(phw), vy = sp * st * sin(phw);
             double vz, z;
             if (wall == 0) {
                 vz = vn;
@@ -831,7 +970,7 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
     if (t == 0) {
         unsigned long long ns = K->n_slots;
         if (ns > (unsigned long long)K->capacity) {
-            K->status |= HYB_STATUS_CAPACITY;
+            atomicOr(&K->status, (unsigned)HYB_STATUS_CAPACITY);
             ns = (unsigned long long)K->capacity;
             K->n_slots = ns;
         }
@@ -840,25 +979,52 @@ __device__ void field_body(InstDev *K, double *sm, Red &red, float *s_tabf, Fiel
     }
 }
 
+
+// grid (cluster size, instances); cluster (cluster size, 1, 1); lw = doubles
+// of one node array (nodes per owning CTA + 2 kHalo + 2)
 template <bool FAST, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_field(InstDev *insts, int n_max, int64_t *prefix, unsigned *ticket,
-                                                   int max_nodes)
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 3 : 1) k_field(InstDev *insts, int n_max, int64_t *prefix, unsigned *ticket,
+                                                   int max_nodes, int lw)
 {
     extern __shared__ __align__(16) double sm[];
     __shared__ Red red;
-    __shared__ float s_tabf[FAST ? 4 * kMaxTab : 1];
-    __shared__ FieldConsts fc;
-    InstDev *K = &insts[blockIdx.x];
+    __shared__ double s_slots[kSlots];
+    __shared__ double s_tab[kTabCols * kMaxTab];
+    __shared__ float s_tabf[FAST ? 2 * kMaxTab : 1];
+    InstDev *K = &insts[blockIdx.y];
     const bool run = K->active || K->init_pending;
-    if (run && HYB_CHECK(K->G >= 3 && K->G <= max_nodes && K->n_tab <= kMaxTab, 20, K->G, max_nodes))
-        field_body<FAST>(K, sm, red, s_tabf, fc);
+    // every CTA of the cluster takes the same branch (one instance per cluster)
+    bool body = false;
+    if (run && HYB_CHECK(K->G >= 3 && K->G <= max_nodes && K->n_tab <= kMaxTab, 20, K->G, max_nodes)) {
+        const int G = K->G;
+        Clu cu;
+        cu.rank = (int)cg::this_cluster().block_rank();
+        cu.size = (int)gridDim.x;
+        // at least two nodes per owning CTA, and no more than the arrays hold
+        int nown = min(cu.size, max(1, G / 2));
+        int P = (G + nown - 1) / nown;
+        nown = (G + P - 1) / P;
+        cu.nown = nown;
+        cu.P = P;
+        cu.c0 = min(cu.rank * P, G);
+        cu.c1 = cu.rank < nown ? min(cu.c0 + P, G) : cu.c0;
+        if (HYB_CHECK(P + 2 * kHalo + 2 <= lw, 22, P, lw)) {
+            stage_table<FAST>(K, s_tab, s_tabf);
+            field_body<FAST>(K, sm, lw, red, s_tab, s_tabf, cu, s_slots);
+            body = true;
+        }
+    }
+    // no CTA leaves while another may still read its shared memory: the body
+    // arrived at the cluster barrier after its last read of another CTA's
+    // shared memory; the other paths arrive here
+    if (!body) cl_arrive();
+    cl_wait();
     // the last block to finish computes the chunk prefix of the next step
     __shared__ bool s_last;
     __shared__ int64_t s_buf[HYB_MAX_INSTANCES];
-    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
         if (s_last) __threadfence();
     }
     __syncthreads();
@@ -868,9 +1034,22 @@ __global__ void __launch_bounds__(THREADS) k_field(InstDev *insts, int n_max, in
     }
 }
 
+// CTAs per instance's cluster for a launch: about one node per thread, at
+// most 8 (the portable cluster size); 1 for small grids
+int cluster_size(int max_nodes, int threads)
+{
+    const int c = (max_nodes + threads - 1) / threads;
+    return c < 1 ? 1 : (c > kMaxCluster ? kMaxCluster : c);
+}
+
+int array_len(int max_nodes, int csize) { return (max_nodes + csize - 1) / csize + 2 * kHalo + 4; }
+
 }  // namespace
 
-size_t field_smem_bytes(int max_nodes) { return (size_t)kArrays * 8 * (size_t)max_nodes; }
+size_t field_smem_bytes(int max_nodes, int threads)
+{
+    return (size_t)kArrays * 8 * (size_t)array_len(max_nodes, cluster_size(max_nodes, threads));
+}
 
 void read_checks_field(unsigned long long out[3])
 {
@@ -880,7 +1059,7 @@ void read_checks_field(unsigned long long out[3])
 
 void configure_field_kernel()
 {
-    const int sm = (int)field_smem_bytes(kMaxNodes);
+    const int sm = (int)kMaxDynSmem;
     cudaFuncSetAttribute(k_field<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_field<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_field<false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -889,33 +1068,92 @@ void configure_field_kernel()
     cudaFuncSetAttribute(k_field<true, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
-template <bool FAST>
-cudaError_t launch_field_t(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, int max_nodes, int threads,
-                           cudaStream_t s)
+namespace {
+
+template <bool FAST, int THREADS>
+cudaLaunchConfig_t field_cfg(int n_max, int lw, int csize, cudaStream_t s, cudaLaunchAttribute *at)
 {
-    const size_t smem = field_smem_bytes(max_nodes);
-    if (threads == 256)
-        k_field<FAST, 256><<<n_max, 256, smem, s>>>(inst, n_max, prefix, ticket, max_nodes);
-    else if (threads == 512)
-        k_field<FAST, 512><<<n_max, 512, smem, s>>>(inst, n_max, prefix, ticket, max_nodes);
-    else if (threads == 1024)
-        k_field<FAST, 1024><<<n_max, 1024, smem, s>>>(inst, n_max, prefix, ticket, max_nodes);
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)csize, (unsigned)n_max, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)kArrays * 8 * (size_t)lw;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
 }
 
-// `fast`: FP32 transport coefficients (split mode); FP64 throughout otherwise.
-// max_nodes bounds the node count of every instance launched (shared memory
-// is sized for it; a larger instance is skipped by the device guard);
-// threads: 256, 512 or 1024 per instance's block.
-cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, bool fast, int max_nodes,
-                         int threads, cudaStream_t s)
+// Clusters of csize CTAs that the GPU holds at once (cached per shape)
+template <bool FAST, int THREADS>
+int active_clusters(int lw, int csize)
 {
-    if (max_nodes < 3 || max_nodes > kMaxNodes || n_max > HYB_MAX_INSTANCES || n_max > threads)
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> memo;
+    std::lock_guard<std::mutex> g(mu);
+    const auto key = std::make_pair(lw, csize);
+    auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = field_cfg<FAST, THREADS>(1, lw, csize, nullptr, at);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_field<FAST, THREADS>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    memo[key] = n;
+    return n;
+}
+
+template <bool FAST, int THREADS>
+cudaError_t launch_cl(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, int max_nodes, int csize,
+                      cudaStream_t s)
+{
+    if (csize <= 0) {
+        // about one node per thread, but no more CTAs per instance than lets
+        // every instance's cluster be resident at once (one wave)
+        csize = cluster_size(max_nodes, THREADS);
+        while (csize > 1 && active_clusters<FAST, THREADS>(array_len(max_nodes, csize), csize) < n_max) --csize;
+    }
+    // at least as many CTAs as the node arrays need to fit in shared memory
+    while (csize < kMaxCluster && (size_t)kArrays * 8 * (size_t)array_len(max_nodes, csize) > kMaxDynSmem) ++csize;
+    if (csize > kMaxCluster || (size_t)kArrays * 8 * (size_t)array_len(max_nodes, csize) > kMaxDynSmem)
         return cudaErrorInvalidValue;
-    return fast ? launch_field_t<true>(inst, n_max, prefix, ticket, max_nodes, threads, s)
-                : launch_field_t<false>(inst, n_max, prefix, ticket, max_nodes, threads, s);
+    const int lw = array_len(max_nodes, csize);
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = field_cfg<FAST, THREADS>(n_max, lw, csize, s, at);
+    return cudaLaunchKernelEx(&cfg, k_field<FAST, THREADS>, inst, n_max, prefix, ticket, max_nodes, lw);
+}
+
+template <bool FAST>
+cudaError_t launch_field_t(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, int max_nodes, int threads,
+                           int csize, cudaStream_t s)
+{
+    if (threads == 256) return launch_cl<FAST, 256>(inst, n_max, prefix, ticket, max_nodes, csize, s);
+    if (threads == 512) return launch_cl<FAST, 512>(inst, n_max, prefix, ticket, max_nodes, csize, s);
+    if (threads == 1024) return launch_cl<FAST, 1024>(inst, n_max, prefix, ticket, max_nodes, csize, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// `fast`: reciprocals of the instance constants (split mode); divisions as a
+// plain FP64 program writes them otherwise.  max_nodes bounds the node count
+// of every instance launched (shared memory is sized for it; a larger
+// instance is skipped by the device guard); threads: 256, 512 or 1024 per
+// CTA; csize: CTAs per instance (1..8; raised until the node arrays fit in
+// shared memory), 0 = about one node per thread within one wave of clusters.
+cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, bool fast, int max_nodes,
+                         int threads, cudaStream_t s, int csize)
+{
+    if (max_nodes < 3 || max_nodes > kMaxNodes || n_max > HYB_MAX_INSTANCES || n_max > threads ||
+        csize > kMaxCluster)
+        return cudaErrorInvalidValue;
+    return fast ? launch_field_t<true>(inst, n_max, prefix, ticket, max_nodes, threads, csize, s)
+                : launch_field_t<false>(inst, n_max, prefix, ticket, max_nodes, threads, csize, s);
 }
 
 }  // namespace hyb

@@ -34,6 +34,15 @@ struct PartBuf {
     uint64_t *id;
 };
 
+// Constants of the field step, formed on the host at admission (the same
+// expressions a per-step evaluation would use)
+struct FieldK {
+    double h, qdt_m, h_m, c_in, c_wall, gs_in, gs_wall;   // split-mode fluid
+    double hdt, tfac, inv_ngas_td, inv_qe, inv2dz;        // split-mode transport
+    double dt_dz, dt_2dz, h_mion;                         // FP64-mode fluid
+    double w_in, w_wall, c_src, inv_dz, half_inv_dz, c_gauss;  // split-mode Poisson
+};
+
 // Everything a kernel needs about one discharge.  Lives in device memory; the
 // host writes it at admission and the kernels update the mutable tail.
 struct InstDev {
@@ -44,6 +53,7 @@ struct InstDev {
     double e_lo, e_hi, inv_dlog, e_exc, e_iz, two_mM, gamma_see, see_speed;
     double v_rf, f_rf, v_dc, mu_const, kT_gas;
     double inv_gm1;  // 1 / (G - 1)
+    FieldK fk;
     uint32_t seed_lo, seed_hi;
     // FP32 copies for the split-mode electron kernel
     float f_dt_dz, f_qm_dt, f_half_m_q, f_two_q_m, f_pmax, f_e_lo, f_e_hi, f_inv_e_lo, f_inv_dlog;
@@ -271,8 +281,8 @@ size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins);
 
 // field kernel (hyb_field.cu)
 cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned int *ticket, bool fast, int max_nodes,
-                         int threads, cudaStream_t s);
-size_t field_smem_bytes(int max_nodes);
+                         int threads, cudaStream_t s, int csize = 0);
+size_t field_smem_bytes(int max_nodes, int threads);
 void configure_field_kernel();
 
 // first failed self-check of each translation unit (zeros in the normal build)

@@ -98,7 +98,8 @@ class SwarmResult(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("sort_interval", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("field_threads", C.c_int32), ("rate", C.c_double)]
+                ("field_threads", C.c_int32), ("field_cluster", C.c_int32), ("pad0", C.c_int32),
+                ("rate", C.c_double)]
 
 
 EXPORTS = {
@@ -140,6 +141,7 @@ EXPORTS = {
     "hyb_batch_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(Tuning)]),
     "hyb_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Tuning)]),
     "hyb_discharge_batch": (C.c_void_p, [C.c_void_p]),
+    "hyb_batch_set_field_arith": (C.c_int, [C.c_void_p, C.c_int32]),
     "hyb_swarm_run": (C.c_int, [C.POINTER(SwarmParams), C.c_int32, _pd, C.POINTER(SwarmResult), C.c_void_p,
                                 C.c_void_p]),
     "hyb_swarm_tables": (C.c_int, [C.POINTER(SwarmParams), C.c_int32, _pd, _pd, _pd, C.c_void_p]),
@@ -305,6 +307,22 @@ class Discharge:
     def reset_moments(self):
         _check(lib().hyb_reset_moments(self.h))
 
+    def set_tuning(self, **kw):
+        """Launch layout of the batch behind this discharge (fields of
+        hyb_tuning: lanes, sort_interval, blocks_per_sm, field_threads,
+        field_cluster)."""
+        bh = lib().hyb_discharge_batch(self.h)
+        t = Tuning()
+        _check(lib().hyb_batch_get_tuning(bh, C.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _check(lib().hyb_batch_set_tuning(bh, C.byref(t)))
+
+    def set_field_arith(self, split):
+        """Test hook: the field step takes the split mode's arithmetic (1) or
+        the batch's own (0)."""
+        _check(lib().hyb_batch_set_field_arith(lib().hyb_discharge_batch(self.h), int(split)))
+
     def particles(self, cap=None):
         cap = int(cap or self.info["capacity"])
         return _particles(lambda *a: lib().hyb_read_particles(self.h, *a), cap)
@@ -429,12 +447,14 @@ class Batch:
         _check(lib().hyb_batch_get_tuning(self.h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
-    def set_tuning(self, lanes=None, sort_interval=None, blocks_per_sm=None, field_threads=None):
+    def set_tuning(self, lanes=None, sort_interval=None, blocks_per_sm=None, field_threads=None,
+                   field_cluster=None):
         cur = self.tuning()
         t = Tuning(int(lanes if lanes is not None else cur["lanes"]),
                    int(sort_interval if sort_interval is not None else cur["sort_interval"]),
                    int(blocks_per_sm if blocks_per_sm is not None else cur["blocks_per_sm"]),
-                   int(field_threads if field_threads is not None else cur["field_threads"]), 0.0)
+                   int(field_threads if field_threads is not None else cur["field_threads"]),
+                   int(field_cluster if field_cluster is not None else cur["field_cluster"]), 0, 0.0)
         _check(lib().hyb_batch_set_tuning(self.h, C.byref(t)))
         return self.tuning()
 

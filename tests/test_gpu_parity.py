@@ -97,6 +97,78 @@ def test_fp64_dd_table_ragged_sizes():
     _check_all(g, o, p)
 
 
+@pytest.mark.parametrize("cluster", [1, 2, 8])
+def test_fp64_field_cluster_sizes(cluster):
+    """The field step split over 1, 2 or 8 CTAs of a cluster gives the oracle's
+    result to the FP64 tolerances (full fluid with gamma emission and
+    ionization, 333 cells: halo exchanges, cluster scans and the wall rows all
+    take part; only summation order differs)."""
+    p = W.config1(precision=W.FP64, n_particles=15000, n_cells=333, te0_ev=15.0, v_rf_amp_v=400.0,
+                  gamma_see=0.3, ion_model=W.ION_FULL, weight=2e5, seed=17)
+    g = _gpu(p)
+    g.set_tuning(field_cluster=cluster)
+    o = oracle.Oracle(p)
+    g.advance(80)
+    o.step(80)
+    assert o.counters()["ionization"] > 0
+    _check_all(g, o, p)
+
+
+def test_fp64_full_fluid_many_sweeps_exchange_edges():
+    """A coarse step (dt 5e-11 s) and a strong DC field make the Eq. 2.3
+    contraction ratio r large enough for more Jacobi sweeps than a CTA's halo
+    covers (r > 0.0098: more than 9), so the later sweeps pass edge values
+    between the CTAs of the cluster; the result still equals the oracle's
+    Thomas solve to the FP64 tolerances."""
+    p = W.config1(precision=W.FP64, gap_m=1e-3, n_cells=400, n_particles=4000, dt_s=5e-11, v_rf_amp_v=0.0,
+                  v_dc_v=2500.0, ion_model=W.ION_FULL, seed=23)
+    g = _gpu(p)
+    g.set_tuning(field_cluster=4)
+    o = oracle.Oracle(p)
+    G, dz, dt = p["n_cells"] + 1, p["gap_m"] / p["n_cells"], p["dt_s"]
+    rmax = 0.0
+    for _ in range(6):
+        f = o.fields()
+        n, gam, E = f["ni"], f["gamma"], f["E"]
+        A = np.where(n >= 1e-6 * p["n0_m3"], gam / np.where(n > 0, n, 1.0), 0.0)
+        nu = np.array([o.transport(abs(E[j]), abs(A[j]))[3] for j in range(G)])
+        h = dt / (2 * dz)
+        r = (np.abs(h * A[:-2]) + np.abs(h * A[2:])) / (1 + nu[1:-1] * dt / 2)
+        rmax = max(rmax, r.max())
+        g.advance(5)
+        o.step(5)
+    assert rmax > 0.0098, rmax        # ceil(ln 2^-60 / ln r) > 9 sweeps
+    assert rmax < 0.5
+    _check_all(g, o, p)
+
+
+SPLIT_FIELD_CASES = {
+    "dd_const": dict(),
+    "full_gamma": dict(n_particles=20000, te0_ev=15.0, v_rf_amp_v=400.0, gamma_see=0.3, ion_model=W.ION_FULL,
+                       weight=2e5, seed=7),
+    "dd_table_ragged": dict(n_particles=12345, n_cells=333, te0_ev=6.0, ion_model=W.ION_DD_TABLE, gamma_see=0.1,
+                            seed=11),
+}
+
+
+@pytest.mark.parametrize("case,cluster", [("dd_const", 0), ("full_gamma", 8), ("dd_table_ragged", 4)])
+def test_split_field_arithmetic_against_oracle(case, cluster):
+    """The split mode's field step (FP64 values; reciprocals of the instance
+    constants, table slopes and Newton reciprocals in place of divisions) run
+    on FP64 particles: it differs from the oracle by rounding only, so the FP64
+    tolerances hold.  This checks the field arithmetic of the production path
+    against the oracle directly, without the FP32 particles' statistics."""
+    p = W.config1(precision=W.FP64, **SPLIT_FIELD_CASES[case])
+    g = _gpu(p)
+    g.set_field_arith(1)
+    if cluster:
+        g.set_tuning(field_cluster=cluster)
+    o = oracle.Oracle(p)
+    g.advance(100)
+    o.step(100)
+    _check_all(g, o, p)
+
+
 def test_fp64_power_control_over_three_periods():
     """Eq. 2.9 with an RF period of 30 steps.  Through the first period (the
     amplitude changes only at its end) states, counters and grids agree with the
