@@ -20,6 +20,8 @@ import statistics
 import subprocess
 import sys
 import threading
+
+import numpy as np
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -280,6 +282,135 @@ def run_fp64_plain(params, chunks=2, steps=20):
     d.close()
     return {"value": n / (ms / 1e3), "unit": "particle-steps/s", "particles": int(p["n_particles"]),
             "steps": chunks * steps, "dtype": "f64"}
+
+
+def _oracle_rate(p, steps):
+    """The oracle as it stands on one host core: particle-steps/s of `steps`
+    PIC steps of discharge p (its construction and initial load not timed)."""
+    import oracle
+    o = oracle.Oracle(p)
+    n = 0
+    t = 0.0
+    for _ in range(steps):
+        k = o.n_particles
+        t0 = time.perf_counter()
+        o.step(1)
+        t += time.perf_counter() - t0
+        n += k
+    o.close()
+    return n / t, n, t
+
+
+def single_config_load(name, p, stream, flush, chunks=3, oracle_particles=200000, oracle_steps=5):
+    """One discharge of a single-instance workload as a one-slot batch (one
+    lane, sort every 100 steps): whole-step particle-steps/s over `chunks`
+    graph chunks (CUDA events), the electron kernel's fraction of the HBM
+    roofline from one profiled chunk, and the oracle on one host core on a
+    bounded sample: the same discharge with `oracle_particles` electrons
+    (weight scaled to keep the density), `oracle_steps` steps."""
+    import torch
+
+    from paper_1508_02892_gb300 import hybrid
+    b = hybrid.Batch(1, p["precision"], stream=stream.cuda_stream)
+    s = b.admit(p)
+    b.set_tuning(lanes=1, sort_interval=100)
+    b.advance(CHUNK)
+    torch.cuda.synchronize()
+    c0 = b.counters(s)["pushes"]
+    ms = 0.0
+    for _ in range(chunks):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.advance(CHUNK)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    n = b.counters(s)["pushes"] - c0
+    b.set_profiling(True)
+    b.profile(reset=True)
+    q0 = b.counters(s)["pushes"]
+    flush.zero_()
+    b.advance(CHUNK)
+    torch.cuda.synchronize()
+    prof = b.profile()
+    nq = b.counters(s)["pushes"] - q0
+    b.set_profiling(False)
+    status = b.counters(s)["status"]
+    b.close()
+    peak, peak_kind = peaks()
+    per_launch = nq / max(prof["n_electron"], 1)
+    avg_ms = prof["ms_electron"] / max(prof["n_electron"], 1)
+    bpu = BYTES_SPLIT if p["precision"] == 1 else BYTES_FP64
+    achieved = bpu * per_launch / (avg_ms / 1e3) / 1e9
+    q = dict(p)
+    q["weight"] = p["n0_m3"] * p["gap_m"] / p["n_particles"] if not p.get("weight") else p["weight"]
+    q["weight"] *= p["n_particles"] / oracle_particles
+    q["n_particles"] = oracle_particles
+    orate, on, ot = _oracle_rate(q, oracle_steps)
+    return {"workload": name, "value": n / (ms / 1e3), "unit": "particle-steps/s", "particles": int(p["n_particles"]),
+            "cells": int(p["n_cells"]), "steps_timed": chunks * CHUNK, "status": int(status),
+            "kernel_ms_per_step": {"electron": prof["ms_electron"] / max(prof["n_electron"], 1),
+                                   "field": prof["ms_field"] / max(prof["n_field"], 1)},
+            "roofline": {"kernel": "k_electron", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "bytes_per_unit": bpu,
+                         "units_per_launch": per_launch, "avg_launch_ms": avg_ms},
+            "cpu_oracle": {"value": orate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                           "sample": f"the same discharge with {oracle_particles} electrons (density kept), "
+                                     f"{oracle_steps} steps, {on} particle-steps in {ot:.1f} s"}}
+
+
+def config1_full(stream):
+    """Config 1 as stated: FP64 plain method, one discharge, 2000 steps, on the
+    GPU (CUDA events around the whole run) and in the oracle on one host core,
+    both in full."""
+    import torch
+
+    from paper_1508_02892_gb300 import hybrid, workloads as W
+    p = W.config1(precision=W.FP64)
+    d = hybrid.Discharge(p, stream=stream.cuda_stream)
+    d.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d.advance(2000)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    c = d.counters()
+    d.close()
+    orate, on, ot = _oracle_rate(p, 2000)
+    return {"workload": "config 1: He 0.5 mm / 200 cells, 2e4 electrons, DD constant mobility, FP64, 2000 steps",
+            "gpu": {"value": c["pushes"] / (ms / 1e3), "unit": "particle-steps/s", "ms": ms, "pushes": c["pushes"]},
+            "cpu_oracle": {"value": orate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                           "sample": f"the whole run: 2000 steps, {on} particle-steps in {ot:.1f} s"}}
+
+
+def accuracy_load(params, stream, n=8, n_e=30000, steps=300):
+    """The split path against the FP64 oracle on discharges of the benchmarked
+    mix: the first n discharges with n_e electrons each (weight scaled to
+    keep the density), `steps` steps, as one split batch and in the oracle
+    (spawned processes).  L2-relative error of each time-averaged moment, the
+    largest and the mean over the discharges."""
+    import oracle
+    from paper_1508_02892_gb300 import hybrid
+    plist = []
+    for p in params[:n]:
+        q = dict(p)
+        q["weight"] = p["n0_m3"] * p["gap_m"] / n_e
+        q["n_particles"] = n_e
+        plist.append(q)
+    orc = oracle.run_ensemble(plist, steps)
+    b = hybrid.Batch(len(plist), hybrid.HYB_FP32_SPLIT, stream=stream.cuda_stream)
+    slots = [b.admit(q, steps) for q in plist]
+    b.advance(steps)
+    gpu = [b.moments(s) for s in slots]
+    b.close()
+    out = {}
+    for k in ("ne", "ni", "ebar", "gamma", "eedf"):
+        errs = [float(np.linalg.norm(g[k] - o[k]) / max(np.linalg.norm(o[k]), 1e-300)) for g, o in zip(gpu, orc)]
+        out[k] = {"max_l2": max(errs), "mean_l2": sum(errs) / len(errs)}
+    return {"sample": f"first {len(plist)} discharges of the mix, {n_e} electrons each, {steps} steps, split batch "
+                      f"vs the FP64 oracle (same random numbers)", "l2": out}
 
 
 def serve_load(args, stream, rank=0, world=1, tuning=None):
@@ -556,6 +687,19 @@ def run_ours(args):
     if rank == 0 and not args.no_variants:
         variants = variants_load(params, stream, flush)
 
+    configs = None
+    accuracy = None
+    if rank == 0 and not args.no_configs:
+        from paper_1508_02892_gb300 import workloads as W
+        configs = {"config1_fp64_full": config1_full(stream),
+                   "config2": single_config_load("config 2: He 1 mm / 1000 cells, 2e6 electrons, full fluid, "
+                                                 "gamma 0.1, FP32 split", W.config2(), stream, flush,
+                                                 oracle_particles=200000, oracle_steps=20),
+                   "config5": single_config_load("config 5: Ar 1 mm / 4000 cells, 5e7 electrons, full fluid, "
+                                                 "gamma 0.15, dt 1e-13 s, FP32 split", W.config5(), stream, flush,
+                                                 oracle_particles=500000, oracle_steps=20)}
+        accuracy = accuracy_load(params, stream)
+
     swarm = None
     if rank == 0 and not args.no_swarm:
         swarm = swarm_load(n_ions=args.swarm_ions, n_steps=args.swarm_steps)
@@ -615,6 +759,10 @@ def run_ours(args):
         line["swarm"] = swarm
     if variants:
         line["variants"] = variants
+    if configs:
+        line["configs"] = configs
+    if accuracy:
+        line["accuracy"] = accuracy
     if cpu:
         line["cpu_baseline"] = cpu
     line["device_index_guards"] = hybrid.debug_checks()
@@ -649,6 +797,7 @@ def main():
     ap.add_argument("--swarm-steps", type=int, default=20000)
     ap.add_argument("--only-swarm", action="store_true", help="run and print the ion-swarm measurement alone")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip configs 1, 2, 5 and the accuracy check")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

@@ -442,25 +442,31 @@ int hyb_swarm_tables(const hyb_swarm_params *p, int32_t n, const double *eon_td,
 
 /* The field of a particle set, computed without allocating device memory.
  * The paper has no counterpart: this is a service for callers that cannot
- * call cudaMalloc, such as host loops being recorded into a CUDA graph (an
- * allocation is not allowed while a stream is captured) or applications that
- * reserve all device memory up front and hand out fixed buffers.  It does what
- * hyb_write_particles followed by hyb_read_fields does for a discharge of
- * these parameters: CIC charge assignment of the n electrons at positions z,
- * electron density, and the Poisson solve with the ion density ni and the
- * drive at time t (phi(0) = v_dc_v + v_rf_amp_v sin(2 pi f_rf_hz t),
- * phi(L) = 0).  Uses gap_m, n_cells, weight (or n0_m3, n_particles) and the
- * drive of p; the rest of p is ignored.
- *   z:      device, n positions (m), FP64; positions outside [0, L) are skipped
+ * call cudaMalloc, such as applications that reserve all device memory up
+ * front and hand out fixed buffers, or that must not let an allocation
+ * synchronise the device under other work.  It does what hyb_write_particles
+ * followed by hyb_read_fields does for a discharge of these parameters: CIC
+ * charge assignment of the n electrons at positions z, electron density, and
+ * the Poisson solve with the ion density ni and the drive at time t
+ * (phi(0) = v_dc_v + v_rf_amp_v sin(2 pi f_rf_hz t), phi(L) = 0).  Uses
+ * gap_m, n_cells, weight (or n0_m3, n_particles) and the drive of p; the rest
+ * of p is ignored, power_w_m2 and power_alpha included: for a power-controlled
+ * discharge (Eq. 2.9) pass its current amplitude (hyb_counters.v_rf) in
+ * v_rf_amp_v.
+ *   z:      device, n positions (m), FP64; positions outside [0, L) and
+ *           non-finite ones add no charge, z within rounding below L lands on
+ *           the last node
  *   ni:     device, n_cells + 1 ion densities (m^-3)
  *   ne, phi, efield: device outputs, n_cells + 1 doubles each
  *   stream: cudaStream_t or NULL; the call returns before the GPU is done.
  * The node sums go to one file-scope device array of HYB_MAX_CELLS + 1 doubles
  * (32 KB, held by every GPU that loads the library until the process exits);
  * n_cells above HYB_MAX_CELLS is rejected with HYB_ERR_ARG.  The first call on
- * a device looks up that array's device address and sets a kernel attribute,
- * so make it before any stream capture.  Every call clears the array and then
- * uses it: calls whose GPU work overlaps (other streams, other threads) race. */
+ * a device looks up that array's device address and sets a kernel attribute
+ * for the device's current context, so make that first call before any
+ * stream capture, and do not use the call across a cudaDeviceReset of that
+ * device in the same process.  Every call clears the array and then uses it:
+ * calls whose GPU work overlaps (other streams, other threads) race. */
 int hyb_field_from_particles_noalloc(const hyb_params *p, int64_t n, const double *z, const double *ni, double t,
                                      double *ne, double *phi, double *efield, void *stream);
 

@@ -1204,6 +1204,20 @@ orc_sim *orc_create(const orc_params *p)
     if (p->metastables && (p->ion_model == ION_KINETIC || p->met_diff_m2s < 0 ||
                            p->met_diff_m2s * p->dt_s * p->n_cells * p->n_cells > 0.5 * p->gap_m * p->gap_m))
         return NULL;
+    /* explicit drift-diffusion (Eq. 2.5 into Eq. 2.4): u^2 dt <= 2 D and
+     * D dt / dz^2 <= 1/2 at the drive's field across the empty gap */
+    if (p->ion_model == ION_DD_CONST || p->ion_model == ION_DD_TABLE) {
+        double e = (fabs(p->v_dc_v) + fabs(p->v_rf_amp_v)) / p->gap_m;
+        double kt = K_B * p->gas_temp_k, mu = p->mu_const, t = kt;
+        if (p->ion_model == ION_DD_TABLE) {
+            mu = interp_lin(p->tab_eon_td, p->tab_mu, p->n_tab, e / (p->pressure_pa / kt) * 1e21);
+            double mn = (p->gas_mass_amu > 0 ? p->gas_mass_amu : (p->gas == 1 ? 39.948 : 4.002602)) * AMU;
+            double mi = p->ion_mass_amu > 0 ? p->ion_mass_amu * AMU : mn;
+            t = kt + (mi + mn) / (5.0 * mi + 3.0 * mn) * mn * (mu * e) * (mu * e);
+        }
+        double d = mu * t / Q_E, u = mu * e, dz = p->gap_m / p->n_cells;
+        if (u * u * p->dt_s > 2.0 * d || d * p->dt_s > 0.5 * dz * dz) return NULL;
+    }
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     s->p = *p;
     s->xs_ev = dup(p->xs_ev, p->n_xs);

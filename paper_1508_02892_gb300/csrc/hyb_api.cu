@@ -91,6 +91,22 @@ bool finite_all(const double *x, int n)
     return true;
 }
 
+// linear interpolation in (x, y), x increasing, clamped at the ends
+double interp_clamped(const double *x, const double *y, int n, double v)
+{
+    if (v <= x[0]) return y[0];
+    if (v >= x[n - 1]) return y[n - 1];
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (x[mid] <= v)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return y[lo] + (v - x[lo]) / (x[lo + 1] - x[lo]) * (y[lo + 1] - y[lo]);
+}
+
 int validate(const hyb_params *p)
 {
     if (!p) return fail(HYB_ERR_ARG, "params is NULL");
@@ -141,6 +157,26 @@ int validate(const hyb_params *p)
         if (!finite_all(p->xs_rec, p->n_xs)) return fail(HYB_ERR_NONFINITE, "non-finite recombination cross section");
         for (int i = 0; i < p->n_xs; ++i)
             if (p->xs_rec[i] < 0) return fail(HYB_ERR_ARG, "negative recombination cross section");
+    }
+    if (p->ion_model == HYB_ION_DD_CONST || p->ion_model == HYB_ION_DD_TABLE) {
+        // explicit drift-diffusion (Eq. 2.5 at level n into Eq. 2.4): the
+        // centred scheme needs u^2 dt <= 2 D and D dt / dz^2 <= 1/2, checked at
+        // the field of the drive across the empty gap, (|V_dc| + |V_rf|) / L,
+        // with D from Eq. 2.7 (Eq. 2.8 temperature for the tabulated model)
+        const double e = (fabs(p->v_dc_v) + fabs(p->v_rf_amp_v)) / p->gap_m;
+        const double kT = kKb * p->gas_temp_k;
+        double mu = p->mu_const, T = kT;
+        if (p->ion_model == HYB_ION_DD_TABLE) {
+            const double eon = e / (p->pressure_pa / kT) * 1e21;
+            mu = interp_clamped(p->tab_eon_td, p->tab_mu, p->n_tab, eon);
+            const double mn = mass_gas_amu(*p) * kAmu;
+            const double mi = p->ion_mass_amu > 0 ? p->ion_mass_amu * kAmu : mn;
+            const double ud = mu * e;
+            T = kT + (mi + mn) / (5.0 * mi + 3.0 * mn) * mn * ud * ud;
+        }
+        const double D = mu * T / kQe, u = mu * e, dz = p->gap_m / p->n_cells;
+        if (u * u * p->dt_s > 2.0 * D || D * p->dt_s > 0.5 * dz * dz)
+            return fail(HYB_ERR_UNSTABLE, "drift-diffusion: u^2 dt > 2 D or D dt/dz^2 > 1/2 at the drive's field");
     }
     if (p->metastables != 0 && p->metastables != 1) return fail(HYB_ERR_ARG, "metastables must be 0 or 1");
     if (!(p->gamma_met >= 0) || !isfinite(p->gamma_met)) return fail(HYB_ERR_ARG, "gamma_met must be finite and >= 0");

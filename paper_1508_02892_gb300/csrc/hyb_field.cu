@@ -707,24 +707,31 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
             gfin = X;
         } else {
             // Eq. 2.5 at level n (explicit drift-diffusion), on the CTA's run
-            // and one node beyond it on each side
+            // and one node beyond it on each side; the centred explicit scheme
+            // holds while u^2 dt <= 2 D and D dt <= dz^2 / 2 (checked on the run)
             const int a = own ? max(0, c0 - 1) : c0, b = own ? min(G, c1 + 1) : c0;
+            bool unstable = false;
             for (int j = a + t; j < b; j += T) {
                 if (j == 0 || j == G - 1) {
                     const int wl = j == 0 ? 0 : 1;
                     s_x[j] = FAST ? FF.wall(wl, s_ni[j], s_E[j]) : F.wall(wl, s_ni[j], s_E[j]);
-                } else if (FAST) {
-                    const double ea = fabs(s_E[j]);
-                    const double mu = FF.mobility(ea);
-                    const double D = mu * FF.temp(mu, ea) * fk.inv_qe;
+                    continue;
+                }
+                const double ea = fabs(s_E[j]);
+                double mu, D;
+                if (FAST) {
+                    mu = FF.mobility(ea);
+                    D = mu * FF.temp(mu, ea) * fk.inv_qe;
                     s_x[j] = mu * s_ni[j] * s_E[j] - D * ((s_ni[j + 1] - s_ni[j - 1]) * fk.inv2dz);
                 } else {
-                    const double ea = fabs(s_E[j]);
-                    const double mu = F.mobility(ea);
-                    const double D = mu * F.temp(mu, ea) / kQe;
+                    mu = F.mobility(ea);
+                    D = mu * F.temp(mu, ea) / kQe;
                     s_x[j] = mu * s_ni[j] * s_E[j] - D * (s_ni[j + 1] - s_ni[j - 1]) / (2.0 * dz);
                 }
+                const double u = mu * ea;
+                if (j >= c0 && j < c1 && (u * u * dt > 2.0 * D || D * dt > 0.5 * dz * dz)) unstable = true;
             }
+            if (unstable) atomicOr(&K->status, (unsigned)HYB_STATUS_UNSTABLE);
             __syncthreads();
             gfin = s_x;
         }

@@ -17,6 +17,8 @@ namespace {
 constexpr int kNaMaxNodes = HYB_MAX_CELLS + 1;  // 4001 nodes, 32 KB
 constexpr int kNaThreads = 1024;
 constexpr int kNaMaxDevices = 64;
+// k_na_field keeps at most 8 nodes per thread in a local array
+static_assert((kNaMaxNodes + kNaThreads - 1) / kNaThreads <= 8, "raise the local array of k_na_field");
 
 // Scratch shared by every call on a device: the CIC node sums.  Its host-side
 // name is only a stand-in; kernels get the device address looked up below.

@@ -409,10 +409,17 @@ class Batch:
         _check(lib().hyb_batch_advance(self.h, int(n)))
 
     def poll(self):
+        done, rc = self.poll_status()
+        _check(rc)
+        return done
+
+    def poll_status(self):
+        """(slots finished or failed since the last poll, return code): a
+        failed slot is listed with the others and its error is the code."""
         done = (C.c_int32 * self.max_instances)()
         n = C.c_int32(0)
-        _check(lib().hyb_batch_poll(self.h, done, self.max_instances, C.byref(n)))
-        return [done[i] for i in range(n.value)]
+        rc = lib().hyb_batch_poll(self.h, done, self.max_instances, C.byref(n))
+        return [done[i] for i in range(n.value)], int(rc)
 
     def moments(self, slot):
         G, nb, _ = self._shape[slot]

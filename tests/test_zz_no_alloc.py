@@ -1,9 +1,9 @@
 """The allocation-free field entry point against the regular path.
 
 hyb_field_from_particles_noalloc is for callers that cannot allocate device
-memory, for example a host loop that is being captured into a CUDA graph or
-an application that reserved all device memory up front; it keeps its node
-sums in a fixed file-scope device array instead.  Given the same particles,
+memory, for example an application that reserved all device memory up front
+and hands out fixed buffers; it keeps its node sums in a fixed file-scope
+device array instead.  Given the same particles,
 ion density and time, its electron density, potential and field must equal
 what hyb_write_particles followed by hyb_read_fields gives for a discharge
 with the same parameters, to the FP64 grid tolerance of the other parity
@@ -69,6 +69,47 @@ def test_noalloc_field_matches_regular_path_on_two_calls():
         _close(ne.cpu().numpy(), ref["ne"], "ne")
         _close(phi.cpu().numpy(), ref["phi"], "phi")
         _close(E.cpu().numpy(), ref["E"], "E")
+
+
+def test_noalloc_edge_positions_against_a_host_cic_sum():
+    """Positions below 0, at L and NaN add no charge; a position within
+    rounding below L lands on the last node; the rest follow the CIC sum."""
+    import torch
+
+    from paper_1508_02892_gb300 import hybrid
+    lib = hybrid.lib()
+    p = W.config1(precision=W.FP64, n_cells=97, weight=2e8)
+    G, L = p["n_cells"] + 1, p["gap_m"]
+    dz = L / p["n_cells"]
+    s = W.random_particles(5000, L, 2.0, seed=41)
+    z = np.concatenate([s["z"], [-dz, L, np.nan, np.nextafter(L, 0.0), 0.0]])
+    host = np.zeros(G)
+    for zi in z:
+        if not (0.0 <= zi < L):
+            continue
+        x = zi / dz
+        c = int(np.floor(x))
+        o = x - c
+        if c >= p["n_cells"]:
+            c, o = p["n_cells"] - 1, 1.0
+        host[c] += 1.0 - o
+        host[c + 1] += o
+    dv = np.full(G, dz)
+    dv[0] = dv[-1] = dz / 2
+    want = p["weight"] * host / dv
+    assert host[-1] > 0.99                       # the particle just below L sits on the last node
+    zt = torch.tensor(z, dtype=torch.float64, device="cuda")
+    ni = torch.zeros(G, dtype=torch.float64, device="cuda")
+    ne = torch.empty(G, dtype=torch.float64, device="cuda")
+    phi = torch.empty(G, dtype=torch.float64, device="cuda")
+    E = torch.empty(G, dtype=torch.float64, device="cuda")
+    P, keep = hybrid.make_params(p)
+    for _ in range(2):
+        rc = lib.hyb_field_from_particles_noalloc(C.byref(P), z.size, zt.data_ptr(), ni.data_ptr(), 0.0,
+                                                  ne.data_ptr(), phi.data_ptr(), E.data_ptr(), None)
+        assert rc == 0, lib.hyb_last_error()
+        torch.cuda.synchronize()
+        _close(ne.cpu().numpy(), want, "ne")
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
