@@ -35,8 +35,8 @@ MUTANTS = [
     ("collision term, implicit half dropped", "b[k] = 1.0 + nu * dt / 2.0;", "b[k] = 1.0 + nu * dt;"),
     ("mobility abscissa without the Td scale", "double eon_td = e_abs / s->ngas * 1e21;",
      "double eon_td = e_abs / s->ngas;"),
-    ("Eq. 2.8 masses swapped in the factor", "(mi + mn) / (5.0 * mi + 3.0 * mn) * mn",
-     "(mi + mn) / (5.0 * mn + 3.0 * mi) * mn"),
+    ("Eq. 2.8 masses swapped in the factor", "return t + (mi + mn) / (5.0 * mi + 3.0 * mn) * mn",
+     "return t + (mi + mn) / (5.0 * mn + 3.0 * mi) * mn"),
     ("Eq. 2.8 ion mass for the neutral one", "(mi + mn) / (5.0 * mi + 3.0 * mn) * mn * ud * ud",
      "(mi + mn) / (5.0 * mi + 3.0 * mn) * mi * ud * ud"),
     ("Eq. 2.7 diffusion without the field-heated temperature",
