@@ -328,8 +328,10 @@ int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset);
  *   field_threads  threads of each CTA of an instance's field step: 256, 512
  *                  or 1024 (default 256);
  *   field_cluster  CTAs (a thread-block cluster) over which each instance's
- *                  field step is split: 1, 2, 4 or 8; 0 (default) picks about
- *                  one grid node per thread for the batch's largest grid.
+ *                  field step is split: 1, 2, 4, 8 or 16; 0 (default) picks
+ *                  about one grid node per half warp for the batch's largest
+ *                  grid (at most 8 when the batch has several lanes), as
+ *                  many as let every instance's cluster be resident at once.
  * rate is filled by hyb_batch_autotune with the particle-steps/s it measured
  * for the returned choice, and is ignored by hyb_batch_set_tuning. */
 typedef struct hyb_tuning {
@@ -350,7 +352,7 @@ int hyb_batch_set_tuning(hyb_batch *b, const hyb_tuning *t);
  * keep the fastest: lanes in {1, 2, 4, 8, 16}, then the sort interval in
  * {10, 20, 50, 100}, then the electron grid at the occupancy limit or twice it,
  * then the field block size in {256, 512, 1024}, then the field cluster in
- * {automatic, 1, 2, 4, 8}.
+ * {automatic, 1, 2, 4, 8, 16}.
  * Each trial advances every running discharge by one untimed chunk and then
  * by trial_steps rounded up to whole chunks (100 steps): those are real steps
  * of the runs.  Profiling must be off.  *chosen may be NULL. */

@@ -601,6 +601,10 @@ int configure(hyb_batch *b, int nodes, int bins)
 int lane_first(const hyb_batch *b, int k) { return k * b->per_lane; }
 // the field step takes the split mode's arithmetic (reciprocals, table slopes)
 bool field_fast(const hyb_batch *b) { return b->precision == HYB_FP32_SPLIT || b->field_split; }
+// CTAs per instance's field step: the tuning's, or automatic; with several
+// lanes at most 8, which the GPU co-schedules beside other lanes' electron
+// blocks more readily than 16 (measured on the 64-discharge mix)
+int field_cluster_of(const hyb_batch *b) { return b->field_cluster > 0 ? b->field_cluster : (b->lanes > 1 ? -8 : 0); }
 InstDev *lane_inst_ion(const hyb_batch *b, int k);
 int64_t *lane_prefix_ion(const hyb_batch *b, int k);
 int lane_count(const hyb_batch *b, int k) { return std::max(0, std::min(b->per_lane, b->max_inst - k * b->per_lane)); }
@@ -684,7 +688,7 @@ int launch_step(hyb_batch *b, int k, int lane, cudaStream_t s)
     }
     if (b->profiling && (rc = record(s, lane_event(b, lane, e + 2)))) return rc;
     CK(launch_field(lane_inst(b, lane), n, lane_prefix(b, lane), lane_ticket(b, lane), field_fast(b),
-                    b->max_nodes, b->field_threads, s, b->field_cluster));
+                    b->max_nodes, b->field_threads, s, field_cluster_of(b)));
     if (b->profiling && (rc = record(s, lane_event(b, lane, e + 3)))) return rc;
     return HYB_OK;
 }
@@ -827,7 +831,7 @@ int reinit_slot(hyb_batch *b, int slot, bool sort)
         CK(launch_ion_step(I, 1, b->d_prefix1_ion, 1, b->cfg.grid, b->max_nodes, b->precision, b->stream));
     }
     CK(launch_field(K, 1, b->d_prefix1, b->d_ticket1, field_fast(b), b->max_nodes, b->field_threads,
-                    b->stream, b->field_cluster));
+                    b->stream, field_cluster_of(b)));
     if (sort) {
         CK(launch_prefix_one(K, b->d_prefix1, b->stream));
         CK(launch_sort(K, 1, b->d_prefix1, b->precision, b->cfg, b->stream));
@@ -1054,8 +1058,8 @@ int set_tuning(hyb_batch *b, const hyb_tuning &t)
     if (t.field_threads != 256 && t.field_threads != 512 && t.field_threads != 1024)
         return fail(HYB_ERR_ARG, "field_threads must be 256, 512 or 1024");
     if (t.field_cluster != 0 && t.field_cluster != 1 && t.field_cluster != 2 && t.field_cluster != 4 &&
-        t.field_cluster != 8)
-        return fail(HYB_ERR_ARG, "field_cluster must be 0, 1, 2, 4 or 8");
+        t.field_cluster != 8 && t.field_cluster != 16)
+        return fail(HYB_ERR_ARG, "field_cluster must be 0, 1, 2, 4, 8 or 16");
     int rc = flush_pending(b);
     if (rc) return rc;
     if (t.lanes != b->lanes && (rc = set_lanes(b, t.lanes))) return rc;
@@ -1167,7 +1171,7 @@ int autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *out)
         trial(t);
     }
     const hyb_tuning after_field = best;
-    const int cluster_opts[5] = {0, 1, 2, 4, 8};
+    const int cluster_opts[6] = {0, 1, 2, 4, 8, 16};
     for (int c : cluster_opts) {
         if (c == after_field.field_cluster) continue;
         hyb_tuning t = after_field;

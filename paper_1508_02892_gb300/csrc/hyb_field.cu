@@ -4,7 +4,7 @@
 // then continuity, Eq. 2.4), the Poisson solve and field, the time sums, and
 // the gamma secondaries that will take part in the next step.
 //
-// Each instance's grid is split over a thread-block cluster of up to 8 CTAs
+// Each instance's grid is split over a thread-block cluster of up to 16 CTAs
 // (one GPU): CTA r of the cluster owns a contiguous run of nodes and keeps it,
 // with one halo node on each side, in shared memory (8 node arrays).  The FP64
 // work of a step (about a hundred FP64 instructions per node at this part's
@@ -51,7 +51,7 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kArrays = 8;
-constexpr int kMaxCluster = 8;
+constexpr int kMaxCluster = 16;  // non-portable cluster size (a GB300 GPC holds 19 SMs)
 constexpr int kSlots = 16;    // reductions across the cluster per step (at most 8 are used)
 constexpr int kMaxTab = 256;  // rows of a transport table staged in shared memory
 constexpr size_t kMaxDynSmem = 160 * 1024;  // node arrays of one CTA, at most
@@ -1041,11 +1041,12 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 3 : 1) k_field(InstD
     }
 }
 
-// CTAs per instance's cluster for a launch: about one node per thread, at
-// most 8 (the portable cluster size); 1 for small grids
+// CTAs per instance's cluster for a launch: about one node per half warp of
+// the CTA's threads (the FP64 work of a CTA grows with its nodes at this
+// part's FP64 rate), at most 16; 1 for small grids
 int cluster_size(int max_nodes, int threads)
 {
-    const int c = (max_nodes + threads - 1) / threads;
+    const int c = (max_nodes + threads / 2 - 1) / (threads / 2);
     return c < 1 ? 1 : (c > kMaxCluster ? kMaxCluster : c);
 }
 
@@ -1064,15 +1065,23 @@ void read_checks_field(unsigned long long out[3])
         out[0] = out[1] = out[2] = 0ull;
 }
 
+namespace {
+template <bool FAST, int THREADS>
+void configure_one()
+{
+    cudaFuncSetAttribute(k_field<FAST, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
+    cudaFuncSetAttribute(k_field<FAST, THREADS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+}  // namespace
+
 void configure_field_kernel()
 {
-    const int sm = (int)kMaxDynSmem;
-    cudaFuncSetAttribute(k_field<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_field<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_field<false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_field<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_field<false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_field<true, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    configure_one<false, 256>();
+    configure_one<true, 256>();
+    configure_one<false, 512>();
+    configure_one<true, 512>();
+    configure_one<false, 1024>();
+    configure_one<true, 1024>();
 }
 
 namespace {
@@ -1120,9 +1129,12 @@ cudaError_t launch_cl(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticke
                       cudaStream_t s)
 {
     if (csize <= 0) {
-        // about one node per thread, but no more CTAs per instance than lets
-        // every instance's cluster be resident at once (one wave)
+        // about one node per half warp (at most -csize when csize < 0), but
+        // no more CTAs per instance than lets every instance's cluster be
+        // resident at once (one wave)
+        const int cap = csize < 0 ? -csize : kMaxCluster;
         csize = cluster_size(max_nodes, THREADS);
+        if (csize > cap) csize = cap;
         while (csize > 1 && active_clusters<FAST, THREADS>(array_len(max_nodes, csize), csize) < n_max) --csize;
     }
     // at least as many CTAs as the node arrays need to fit in shared memory
@@ -1151,13 +1163,14 @@ cudaError_t launch_field_t(InstDev *inst, int n_max, int64_t *prefix, unsigned *
 // plain FP64 program writes them otherwise.  max_nodes bounds the node count
 // of every instance launched (shared memory is sized for it; a larger
 // instance is skipped by the device guard); threads: 256, 512 or 1024 per
-// CTA; csize: CTAs per instance (1..8; raised until the node arrays fit in
-// shared memory), 0 = about one node per thread within one wave of clusters.
+// CTA; csize: CTAs per instance (1..16; raised until the node arrays fit in
+// shared memory), 0 = about one node per half warp, as many as fit in one
+// wave of clusters; -m the same with at most m.
 cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, bool fast, int max_nodes,
                          int threads, cudaStream_t s, int csize)
 {
     if (max_nodes < 3 || max_nodes > kMaxNodes || n_max > HYB_MAX_INSTANCES || n_max > threads ||
-        csize > kMaxCluster)
+        csize > kMaxCluster || csize < -kMaxCluster)
         return cudaErrorInvalidValue;
     return fast ? launch_field_t<true>(inst, n_max, prefix, ticket, max_nodes, threads, csize, s)
                 : launch_field_t<false>(inst, n_max, prefix, ticket, max_nodes, threads, csize, s);

@@ -21,7 +21,7 @@ constexpr int32_t kDeadCell = INT32_MIN;  // cell index of a removed split-mode 
 constexpr int kMaxNodes = HYB_MAX_CELLS + 1;
 // Particle kernels split each instance's slots into chunks of kChunk slots;
 // prefix arrays hold chunk counts of the running instances.
-constexpr int kChunk = 2048;
+constexpr int kChunk = 256;
 
 __host__ __device__ __forceinline__ int64_t chunks_of(int64_t n) { return (n + kChunk - 1) / kChunk; }
 
