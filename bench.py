@@ -413,23 +413,28 @@ def accuracy_load(params, stream, n=8, n_e=30000, steps=300):
                       f"vs the FP64 oracle (same random numbers)", "l2": out}
 
 
-def serve_load(args, stream, rank=0, world=1, tuning=None):
+def serve_load(args, stream, rank=0, world=1, tuning=None, n_requests=None, rate_hz=20.0):
     """Config-4 serving: Poisson arrivals (20/s) of discharges from the batched
     ranges, 1e4..4e6 electrons, each advanced by `serve_steps` steps, admitted
     under a 120 GB HBM cap into one resident batch (continuous batching);
-    requests are dealt to ranks round-robin."""
+    requests are dealt to ranks round-robin.  A higher rate_hz keeps the
+    queue full (the server's capacity rather than the offered load)."""
     from paper_1508_02892_gb300 import hybrid, workloads as W
     from paper_1508_02892_gb300.serve import Server, summarize
     from paper_1508_02892_gb300 import shard
-    reqs = shard.rank_share(W.config4_requests(n_requests=args.serve_requests, steps=args.serve_steps), rank, world)
+    n_req = args.serve_requests if n_requests is None else n_requests
+    reqs = shard.rank_share(W.config4_requests(n_requests=n_req, rate_hz=rate_hz, steps=args.serve_steps), rank,
+                            world)
     srv = Server(max_slots=64, hbm_cap_bytes=120e9, precision=hybrid.HYB_FP32_SPLIT, stream=stream.cuda_stream,
-                 tuning=tuning)
+                 tuning=tuning, pipelined=args.serve_mode == "pipelined")
     t0 = time.perf_counter()
     out = srv.run(reqs, keep=("counters",))
     wall = time.perf_counter() - t0
     srv.close()
     s = summarize(out, wall)
-    s.update({"rate_hz": 20.0, "steps_per_request": args.serve_steps, "hbm_cap_gb": 120,
+    offered = sum(r["steps"] * r["params"]["n_particles"] for r in reqs) / max(reqs[-1]["arrival_s"], 1e-9)
+    s.update({"mode": args.serve_mode, "rate_hz": rate_hz, "steps_per_request": args.serve_steps, "hbm_cap_gb": 120,
+              "offered_particle_steps_per_s": offered,
               "peak_admitted_gb": srv.max_bytes / 1e9, "failed": sum(1 for r in out if r["status"] != 0)})
     return s
 
@@ -713,6 +718,13 @@ def run_ours(args):
         wall_ms, steps_all = shard.aggregate(serving["wall_s"] * 1e3, serving["particle_steps"], device="cuda")
         serving["throughput_all_ranks"] = steps_all / (wall_ms / 1e3)
         serving["latency_ranks"] = "rank 0's requests" if world > 1 else "all requests"
+        if args.serve_saturated > 0:
+            # arrivals faster than the GPU serves them: the queue stays full
+            sat = serve_load(args, stream, rank, world, tuning={k: tuning[k] for k in TUNE_KEYS},
+                             n_requests=args.serve_saturated, rate_hz=200.0)
+            wall_ms, steps_all = shard.aggregate(sat["wall_s"] * 1e3, sat["particle_steps"], device="cuda")
+            sat["throughput_all_ranks"] = steps_all / (wall_ms / 1e3)
+            serving["saturated"] = sat
 
     fp64 = None
     if rank == 0 and not args.no_fp64:
@@ -786,7 +798,11 @@ def main():
     ap.add_argument("--lanes", type=int, default=0, help="fixed lane count instead of the autotuner's")
     ap.add_argument("--sort-interval", type=int, default=0, help="with --lanes: fixed sort interval")
     ap.add_argument("--field-cluster", type=int, default=-1, help="with --lanes: fixed field cluster size (0: auto)")
-    ap.add_argument("--serve-requests", type=int, default=100, help="config-4 serving requests (0: none)")
+    ap.add_argument("--serve-requests", type=int, default=1000, help="config-4 serving requests (0: none)")
+    ap.add_argument("--serve-saturated", type=int, default=300,
+                    help="requests of a second serving run at 200/s (queue kept full; 0: none)")
+    ap.add_argument("--serve-mode", default="pipelined", choices=["pipelined", "plain"],
+                    help="request loop: one chunk queued ahead of the one being read (pipelined), or not")
     ap.add_argument("--serve-steps", type=int, default=5000)
     ap.add_argument("--no-swarm", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the widened-path measurements")

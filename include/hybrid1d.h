@@ -279,6 +279,26 @@ int hyb_batch_advance(hyb_batch *b, int64_t n_steps);
  * count since the last poll (cap entries at most). */
 int hyb_batch_poll(hyb_batch *b, int32_t *done, int32_t cap, int32_t *n_done);
 
+/* Serving without host waits on the batch's stream.  hyb_batch_snapshot
+ * queues, in stream order after the work queued so far, a copy of every
+ * slot's status and counters to pinned host memory (at most 3 not yet
+ * polled).  hyb_batch_poll_snapshot waits for the oldest such snapshot only
+ * (not for work queued after it) and reports, like hyb_batch_poll, the slots
+ * that had finished or failed by then (a slot admitted after a snapshot was
+ * queued is not in it).  hyb_batch_read_finished gives such a slot's counters
+ * from that snapshot and its time-averaged moments, read on a side stream
+ * beside whatever the batch's stream runs meanwhile (a finished slot is idle
+ * on the GPU); either output may be NULL; the slot is then evicted as usual.
+ * Admission and eviction queue their copies and kernels without waiting for
+ * the stream, so a request loop can keep one chunk queued ahead of the one
+ * whose results it reads.  Errors: HYB_ERR_STATE (no snapshot, too many
+ * queued, slot not reported or still running), HYB_ERR_ARG, HYB_ERR_CUDA, and
+ * the slot's own error code (HYB_ERR_CAPACITY, HYB_ERR_NONFINITE,
+ * HYB_ERR_UNSTABLE) when it failed. */
+int hyb_batch_snapshot(hyb_batch *b);
+int hyb_batch_poll_snapshot(hyb_batch *b, int32_t *done, int32_t cap, int32_t *n_done);
+int hyb_batch_read_finished(hyb_batch *b, int32_t slot, hyb_counters *counters, hyb_moments *moments);
+
 /* Per-slot reads (wait for the GPU first). */
 int hyb_batch_read_moments(hyb_batch *b, int32_t slot, hyb_moments *out);
 int hyb_batch_read_counters(hyb_batch *b, int32_t slot, hyb_counters *out);

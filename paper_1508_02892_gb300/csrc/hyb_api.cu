@@ -66,6 +66,7 @@ struct Slot {
     void *mem = nullptr;
     int64_t bytes = 0;
     int64_t target = 0;
+    int64_t admit_after = 0;  // snapshots queued before the admission (they do not show it)
 };
 
 double mass_gas_amu(const hyb_params &p)
@@ -545,6 +546,25 @@ struct hyb_batch {
     std::vector<cudaEvent_t> ev;  // per lane: 3 per step + 2 per sort of a chunk
     double ms[4] = {0, 0, 0, 0};  // electron, field, sort, ion
     int64_t nt[4] = {0, 0, 0, 0};
+    // serving without host waits on the batch's stream: status snapshots taken
+    // in stream order (a ring, consumed oldest first), a side stream for reads
+    // of finished slots, pinned staging buffers for admissions
+    static constexpr int kSnaps = 4;
+    InstDev *h_snap[kSnaps] = {};      // pinned, max_inst entries each
+    InstDev *h_snap_ion[kSnaps] = {};  // pinned, the ion descriptors
+    cudaEvent_t ev_snap[kSnaps] = {};
+    int snap_head = 0, snap_count = 0;  // next to consume, snapshots in flight
+    int snap_last = -1;                 // the snapshot last consumed (kept until the next poll)
+    int64_t snap_issued = 0;            // snapshots ever queued
+    int64_t snap_seq[kSnaps] = {};      // sequence number of each ring entry
+    cudaStream_t rstream = nullptr;
+    struct Staging {
+        char *p = nullptr;
+        size_t n = 0;
+        cudaEvent_t ev = nullptr;
+        bool used = false;
+    };
+    std::vector<Staging> stage;
 };
 
 struct hyb_discharge {
@@ -860,6 +880,40 @@ int set_mutable(hyb_batch *b, int slot, int64_t n_slots, int init_pending)
     return HYB_OK;
 }
 
+// A pinned staging buffer of at least `need` bytes whose earlier copies have
+// completed (a new one if none is free); stage_release records the copies
+// queued from it.
+int stage_acquire(hyb_batch *b, size_t need, char **out)
+{
+    for (auto &x : b->stage) {
+        if (x.used || x.n < need) continue;
+        const cudaError_t q = cudaEventQuery(x.ev);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return fail(HYB_ERR_CUDA, "staging event: %s", cudaGetErrorString(q));
+        x.used = true;
+        *out = x.p;
+        return HYB_OK;
+    }
+    hyb_batch::Staging x;
+    x.n = need > ((size_t)256 << 10) ? need : ((size_t)256 << 10);
+    CK(cudaHostAlloc((void **)&x.p, x.n, cudaHostAllocDefault));
+    CK(cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming));
+    x.used = true;
+    b->stage.push_back(x);
+    *out = x.p;
+    return HYB_OK;
+}
+
+int stage_release(hyb_batch *b, char *p)
+{
+    for (auto &x : b->stage)
+        if (x.p == p) {
+            x.used = false;
+            CK(cudaEventRecord(x.ev, b->stream));
+        }
+    return HYB_OK;
+}
+
 int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
 {
     int rc = validate(p);
@@ -905,11 +959,6 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     bind_pointers(*p, L, base, S.h, &S.hi);
     CK(cudaMemsetAsync(base + L.grid_off, 0, L.total - L.grid_off, b->stream));
     const int G = S.h.G;
-    std::vector<double> ni(G, p->n0_m3);
-    CK(cudaMemcpyAsync(S.h.ni, ni.data(), 8 * (size_t)G, cudaMemcpyHostToDevice, b->stream));
-    CK(cudaMemcpyAsync((void *)S.h.xs, xs.data(), 8 * xs.size(), cudaMemcpyHostToDevice, b->stream));
-    CK(cudaMemcpyAsync((void *)S.h.xsf, xsf.data(), 16 * xsf.size(), cudaMemcpyHostToDevice, b->stream));
-    CK(cudaMemcpyAsync((void *)S.h.tab, tab.data(), 8 * tab.size(), cudaMemcpyHostToDevice, b->stream));
     std::vector<double> xr(p->n_xs, 0.0);
     std::vector<float> xrf(p->n_xs, 0.0f);
     if (p->xs_rec)
@@ -917,11 +966,6 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
             xr[i] = p->xs_rec[i];
             xrf[i] = S.h.rec_svmax > 0 ? (float)(p->xs_rec[i] / S.h.rec_svmax) : 0.0f;
         }
-    CK(cudaMemcpyAsync((void *)S.h.xs_rec, xr.data(), 8 * xr.size(), cudaMemcpyHostToDevice, b->stream));
-    CK(cudaMemcpyAsync((void *)S.h.xs_recf, xrf.data(), 4 * xrf.size(), cudaMemcpyHostToDevice, b->stream));
-    std::vector<double> met0(G, p->met_n0_m3);  // metastables: n0 inside, 0 at the electrodes
-    met0[0] = met0[G - 1] = 0.0;
-    if (p->metastables) CK(cudaMemcpyAsync(S.h.met, met0.data(), 8 * (size_t)G, cudaMemcpyHostToDevice, b->stream));
     S.h.active = 0;
     S.h.cur = 0;
     S.h.step = 0;
@@ -949,14 +993,47 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
         I.elec = &b->d_inst[slot];
         S.hi = I;
         S.h.ion = &b->d_inst_ion[slot];
-        CK(cudaMemcpyAsync(&b->d_inst_ion[slot], &S.hi, sizeof(InstDev), cudaMemcpyHostToDevice, b->stream));
     } else {
         S.h.ion = nullptr;
-        CK(cudaMemsetAsync(&b->d_inst_ion[slot], 0, sizeof(InstDev), b->stream));
     }
-    CK(cudaMemcpyAsync(&b->d_inst[slot], &S.h, sizeof(InstDev), cudaMemcpyHostToDevice, b->stream));
+    // every host input goes through one pinned staging buffer, so that the
+    // copies are queued without the host waiting for the work already queued
+    const size_t sz_grid = 8 * (size_t)G;
+    const size_t need = 2 * sz_grid + 8 * xs.size() + 16 * xsf.size() + 8 * tab.size() + 8 * xr.size() +
+                        4 * xrf.size() + 2 * sizeof(InstDev) + 8 * 16;
+    char *st = nullptr;
+    int rc2 = stage_acquire(b, need, &st);
+    if (rc2) return rc2;
+    size_t off = 0;
+    auto put = [&](void *dev, const void *src, size_t n) -> cudaError_t {
+        off = (off + 15) & ~(size_t)15;
+        memcpy(st + off, src, n);
+        const cudaError_t e2 = cudaMemcpyAsync(dev, st + off, n, cudaMemcpyHostToDevice, b->stream);
+        off += n;
+        return e2;
+    };
+    {
+        std::vector<double> ni(G, p->n0_m3);
+        CK(put(S.h.ni, ni.data(), sz_grid));
+    }
+    CK(put((void *)S.h.xs, xs.data(), 8 * xs.size()));
+    CK(put((void *)S.h.xsf, xsf.data(), 16 * xsf.size()));
+    CK(put((void *)S.h.tab, tab.data(), 8 * tab.size()));
+    CK(put((void *)S.h.xs_rec, xr.data(), 8 * xr.size()));
+    CK(put((void *)S.h.xs_recf, xrf.data(), 4 * xrf.size()));
+    if (p->metastables) {
+        std::vector<double> met0(G, p->met_n0_m3);  // metastables: n0 inside, 0 at the electrodes
+        met0[0] = met0[G - 1] = 0.0;
+        CK(put(S.h.met, met0.data(), sz_grid));
+    }
+    if (kin)
+        CK(put(&b->d_inst_ion[slot], &S.hi, sizeof(InstDev)));
+    else
+        CK(cudaMemsetAsync(&b->d_inst_ion[slot], 0, sizeof(InstDev), b->stream));
+    CK(put(&b->d_inst[slot], &S.h, sizeof(InstDev)));
+    rc2 = stage_release(b, st);
+    if (rc2) return rc2;
     if (kin) CK(launch_load_ions(&b->d_inst_ion[slot], p->n_particles, b->stream));
-    CK(cudaStreamSynchronize(b->stream));  // host staging vectors go out of scope
     const double vth = sqrt(kQe * p->te0_ev / kMe);
     CK(launch_load(&b->d_inst[slot], p->n_particles, vth, p->precision, b->stream));
     rc = reinit_slot(b, slot, true);
@@ -983,6 +1060,7 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     S.mem = mem;
     S.bytes = (int64_t)L.total;
     S.target = S.h.target_step;
+    S.admit_after = b->snap_issued;
     b->hbm_used += S.bytes;
     *slot_out = slot;
     if (S.h.nu_max * S.h.dt > 0.1) {
@@ -1202,21 +1280,17 @@ int check_slot(hyb_batch *b, int slot)
     return HYB_OK;
 }
 
-int read_moments(hyb_batch *b, int slot, hyb_moments *out)
+// time-averaged moments of a discharge with descriptor K, copied on stream s
+int moments_of(const InstDev &K, cudaStream_t s, hyb_moments *out)
 {
-    int rc = check_slot(b, slot);
-    if (rc) return rc;
-    if (!out) return fail(HYB_ERR_ARG, "NULL output");
-    rc = sync_status(b, slot);
-    const InstDev &K = b->h_stage[slot];
     const int G = K.G, nb = K.eedf_bins;
     std::vector<double> acc(5 * (size_t)G);
     std::vector<unsigned long long> eedf(nb + 1);
     double *src[5] = {K.acc_ne, K.acc_ni, K.acc_gi, K.acc_wn, K.acc_we};
     for (int k = 0; k < 5; ++k)
-        CK(cudaMemcpyAsync(acc.data() + (size_t)k * G, src[k], 8 * (size_t)G, cudaMemcpyDeviceToHost, b->stream));
-    CK(cudaMemcpyAsync(eedf.data(), K.eedf, 8 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, b->stream));
-    CK(cudaStreamSynchronize(b->stream));
+        CK(cudaMemcpyAsync(acc.data() + (size_t)k * G, src[k], 8 * (size_t)G, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(eedf.data(), K.eedf, 8 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     const int64_t ns = K.n_samples;
     out->n_samples = ns;
     for (int j = 0; j < G; ++j) {
@@ -1231,16 +1305,22 @@ int read_moments(hyb_batch *b, int slot, hyb_moments *out)
         for (int k = 0; k < nb; ++k) out->eedf[k] = tot > 0 ? (double)eedf[k] / (tot * K.bin_w) : 0.0;
         out->eedf[nb] = tot > 0 ? (double)eedf[nb] / tot : 0.0;
     }
-    return rc;
+    return HYB_OK;
 }
 
-int read_counters(hyb_batch *b, int slot, hyb_counters *c)
+int read_moments(hyb_batch *b, int slot, hyb_moments *out)
 {
     int rc = check_slot(b, slot);
     if (rc) return rc;
-    if (!c) return fail(HYB_ERR_ARG, "NULL output");
+    if (!out) return fail(HYB_ERR_ARG, "NULL output");
     rc = sync_status(b, slot);
-    const InstDev &K = b->h_stage[slot];
+    const int r2 = moments_of(b->h_stage[slot], b->stream, out);
+    return r2 ? r2 : rc;
+}
+
+// counters from a discharge's descriptor (and its ion descriptor, if any)
+void fill_counters(const InstDev &K, const InstDev *I, hyb_counters *c)
+{
     c->step = K.step;
     c->births_ionization = (int64_t)K.ctr[C_BIRTH_IZ];
     c->births_see[0] = (int64_t)K.ctr[C_SEE0];
@@ -1262,22 +1342,31 @@ int read_counters(hyb_batch *b, int slot, hyb_counters *c)
     c->births_penning = (int64_t)K.ctr[C_PEN];
     c->births_pooling = (int64_t)K.ctr[C_POOL];
     c->ions = c->ion_losses[0] = c->ion_losses[1] = c->ion_collisions = c->ion_pushes = 0;
-    if (b->slots[slot].h.ion) {
-        InstDev I{};
+    if (I) {
+        c->ion_losses[0] = (int64_t)I->ctr[C_LOSS0];
+        c->ion_losses[1] = (int64_t)I->ctr[C_LOSS1];
+        c->ion_collisions = (int64_t)I->ctr[C_EL];
+        c->ion_pushes = (int64_t)I->ctr[C_PUSH];
+        c->ions = I->n_base + (int64_t)K.ctr[C_BIRTH_IZ] - c->ion_losses[0] - c->ion_losses[1];
+    }
+}
+
+int read_counters(hyb_batch *b, int slot, hyb_counters *c)
+{
+    int rc = check_slot(b, slot);
+    if (rc) return rc;
+    if (!c) return fail(HYB_ERR_ARG, "NULL output");
+    rc = sync_status(b, slot);
+    InstDev I{};
+    const bool kin = b->slots[slot].h.ion != nullptr;
+    if (kin) {
         CK(cudaMemcpyAsync(&I, &b->d_inst_ion[slot], sizeof I, cudaMemcpyDeviceToHost, b->stream));
         CK(cudaStreamSynchronize(b->stream));
-        c->ion_losses[0] = (int64_t)I.ctr[C_LOSS0];
-        c->ion_losses[1] = (int64_t)I.ctr[C_LOSS1];
-        c->ion_collisions = (int64_t)I.ctr[C_EL];
-        c->ion_pushes = (int64_t)I.ctr[C_PUSH];
-        c->ions = I.n_base + (int64_t)K.ctr[C_BIRTH_IZ] - c->ion_losses[0] - c->ion_losses[1];
     }
+    fill_counters(b->h_stage[slot], kin ? &I : nullptr, c);
     return rc;
 }
 
-// The live particles of descriptor K's first ns slots, sorted by id, into
-// host arrays of cap entries (any may be NULL); split-mode positions become
-// z = (c + o) dz.
 int gather_sorted(const InstDev &K, int64_t ns, double *z, double *vx, double *vy, double *vz, uint64_t *id,
                   int64_t cap, int64_t *n, const char *what)
 {
@@ -1382,8 +1471,7 @@ int free_slot(hyb_batch *b, int slot)
     CK(cudaMemsetAsync(&b->d_inst_ion[slot], 0, sizeof(InstDev), b->stream));  // before its buffers go
     int rc = prefix_all(b);
     if (rc) return rc;
-    CK(cudaFreeAsync(S.mem, b->stream));
-    CK(cudaStreamSynchronize(b->stream));
+    CK(cudaFreeAsync(S.mem, b->stream));  // in stream order: later admissions allocate after it
     b->hbm_used -= S.bytes;
     S = Slot{};
     return HYB_OK;
@@ -1491,6 +1579,79 @@ int hyb_batch_poll(hyb_batch *b, int32_t *done, int32_t cap, int32_t *n_done)
     return rc;
 }
 
+int hyb_batch_snapshot(hyb_batch *b)
+{
+    if (!b) return fail(HYB_ERR_ARG, "NULL batch");
+    // one entry stays for the snapshot last polled, which reads may still use
+    if (b->snap_count >= hyb_batch::kSnaps - 1)
+        return fail(HYB_ERR_STATE, "%d snapshots not yet polled", b->snap_count);
+    const int k = (b->snap_head + b->snap_count) % hyb_batch::kSnaps;
+    if (!b->h_snap[k]) {
+        CK(cudaHostAlloc((void **)&b->h_snap[k], sizeof(InstDev) * (size_t)b->max_inst, cudaHostAllocDefault));
+        CK(cudaHostAlloc((void **)&b->h_snap_ion[k], sizeof(InstDev) * (size_t)b->max_inst, cudaHostAllocDefault));
+        CK(cudaEventCreateWithFlags(&b->ev_snap[k], cudaEventDisableTiming));
+    }
+    CK(cudaMemcpyAsync(b->h_snap[k], b->d_inst, sizeof(InstDev) * (size_t)b->max_inst, cudaMemcpyDeviceToHost,
+                       b->stream));
+    if (b->any_kin)
+        CK(cudaMemcpyAsync(b->h_snap_ion[k], b->d_inst_ion, sizeof(InstDev) * (size_t)b->max_inst,
+                           cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaEventRecord(b->ev_snap[k], b->stream));
+    b->snap_seq[k] = b->snap_issued++;
+    ++b->snap_count;
+    return HYB_OK;
+}
+
+int hyb_batch_poll_snapshot(hyb_batch *b, int32_t *done, int32_t cap, int32_t *n_done)
+{
+    if (!b || !n_done) return fail(HYB_ERR_ARG, "NULL argument");
+    if (b->snap_count == 0) return fail(HYB_ERR_STATE, "no snapshot to poll");
+    const int k = b->snap_head;
+    CK(cudaEventSynchronize(b->ev_snap[k]));
+    b->snap_head = (k + 1) % hyb_batch::kSnaps;
+    --b->snap_count;
+    b->snap_last = k;
+    int m = 0;
+    int rc = HYB_OK;
+    for (int i = 0; i < b->max_inst; ++i) {
+        Slot &S = b->slots[i];
+        if (!S.used || S.reported) continue;
+        if (b->snap_seq[k] < S.admit_after) continue;  // admitted after the snapshot was queued
+        const InstDev &K = b->h_snap[k][i];
+        const bool finished = S.target > 0 && K.step >= S.target && !K.active;
+        const bool failed = (K.status & (HYB_STATUS_NONFINITE | HYB_STATUS_CAPACITY | HYB_STATUS_UNSTABLE)) != 0;
+        if (finished || failed) {
+            if (m < cap && done) done[m] = i;
+            ++m;
+            S.reported = true;
+            if (failed && rc == HYB_OK) rc = status_code(K.status);
+        }
+    }
+    *n_done = m < cap ? m : cap;
+    return rc;
+}
+
+int hyb_batch_read_finished(hyb_batch *b, int32_t slot, hyb_counters *counters, hyb_moments *moments)
+{
+    if (!b) return fail(HYB_ERR_ARG, "NULL batch");
+    if (slot < 0 || slot >= b->max_inst || !b->slots[slot].used) return fail(HYB_ERR_ARG, "no discharge in slot %d", slot);
+    if (b->snap_last < 0 || !b->slots[slot].reported)
+        return fail(HYB_ERR_STATE, "slot %d was not reported by hyb_batch_poll_snapshot", slot);
+    const InstDev &K = b->h_snap[b->snap_last][slot];
+    if (K.active) return fail(HYB_ERR_STATE, "slot %d is still running", slot);
+    if (counters)
+        fill_counters(K, b->slots[slot].h.ion ? &b->h_snap_ion[b->snap_last][slot] : nullptr, counters);
+    if (moments) {
+        if (!b->rstream) CK(cudaStreamCreateWithFlags(&b->rstream, cudaStreamNonBlocking));
+        // the slot has been idle on the GPU since the snapshot: read it beside
+        // the chunks queued after it
+        CK(cudaStreamWaitEvent(b->rstream, b->ev_snap[b->snap_last], 0));
+        const int rc = moments_of(K, b->rstream, moments);
+        if (rc) return rc;
+    }
+    return status_code(K.status);
+}
+
 int hyb_batch_read_moments(hyb_batch *b, int32_t slot, hyb_moments *out) { return read_moments(b, slot, out); }
 
 int hyb_batch_read_counters(hyb_batch *b, int32_t slot, hyb_counters *out) { return read_counters(b, slot, out); }
@@ -1563,6 +1724,16 @@ int hyb_batch_destroy(hyb_batch *b)
     cudaFree(b->d_prefix_ion);
     cudaFree(b->d_prefix1_ion);
     cudaFreeHost(b->h_stage);
+    for (int k = 0; k < hyb_batch::kSnaps; ++k) {
+        if (b->h_snap[k]) cudaFreeHost(b->h_snap[k]);
+        if (b->h_snap_ion[k]) cudaFreeHost(b->h_snap_ion[k]);
+        if (b->ev_snap[k]) cudaEventDestroy(b->ev_snap[k]);
+    }
+    for (auto &x : b->stage) {
+        cudaFreeHost(x.p);
+        cudaEventDestroy(x.ev);
+    }
+    if (b->rstream) cudaStreamDestroy(b->rstream);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return HYB_OK;

@@ -128,6 +128,9 @@ EXPORTS = {
     "hyb_batch_admit": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_int64, C.POINTER(C.c_int32)]),
     "hyb_batch_advance": (C.c_int, [C.c_void_p, C.c_int64]),
     "hyb_batch_poll": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]),
+    "hyb_batch_snapshot": (C.c_int, [C.c_void_p]),
+    "hyb_batch_poll_snapshot": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]),
+    "hyb_batch_read_finished": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "hyb_batch_read_moments": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Moments)]),
     "hyb_batch_read_counters": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Counters)]),
     "hyb_batch_read_particles": (C.c_int, [C.c_void_p, C.c_int32, _pd, _pd, _pd, _pd, C.POINTER(C.c_uint64),
@@ -235,6 +238,10 @@ def _moments(call, G, nb):
 def _counters(call):
     c = Counters()
     _check(call(C.byref(c)))
+    return _counters_dict(c)
+
+
+def _counters_dict(c):
     return {"step": c.step, "particles": c.particles, "births_iz": c.births_ionization,
             "births_see0": c.births_see[0], "births_see1": c.births_see[1], "losses0": c.losses[0],
             "losses1": c.losses[1], "elastic": c.collisions[0], "excitation": c.collisions[1],
@@ -412,6 +419,40 @@ class Batch:
         done, rc = self.poll_status()
         _check(rc)
         return done
+
+    def snapshot(self):
+        """Queue a status snapshot after the work queued so far."""
+        _check(lib().hyb_batch_snapshot(self.h))
+
+    def poll_snapshot(self):
+        """(slots finished or failed as of the oldest queued snapshot, return
+        code); waits for that snapshot only."""
+        done = (C.c_int32 * self.max_instances)()
+        n = C.c_int32(0)
+        rc = lib().hyb_batch_poll_snapshot(self.h, done, self.max_instances, C.byref(n))
+        if rc < 0 and rc not in (-3, -4, -7):   # a slot's own failure is reported with it
+            _check(rc)
+        return [done[i] for i in range(n.value)], int(rc)
+
+    def read_finished(self, slot, moments=True):
+        """Counters (from the snapshot) and, if asked, moments (side stream)
+        of a slot that poll_snapshot reported: (counters, moments or None,
+        return code)."""
+        G, nb = self._shape[slot][0], self._shape[slot][1]
+        c = Counters()
+        m = None
+        mc = None
+        if moments:
+            m = {k: np.zeros(G) for k in ("ne", "ni", "gamma", "ebar")}
+            m["eedf"] = np.zeros(nb + 1)
+            mc = Moments(m["ne"].ctypes.data_as(_pd), m["ni"].ctypes.data_as(_pd), m["gamma"].ctypes.data_as(_pd),
+                         m["ebar"].ctypes.data_as(_pd), m["eedf"].ctypes.data_as(_pd), 0)
+        rc = lib().hyb_batch_read_finished(self.h, int(slot), C.byref(c), C.byref(mc) if mc is not None else None)
+        if rc < 0 and rc not in (-3, -4, -7):
+            _check(rc)
+        if m is not None:
+            m["n_samples"] = int(mc.n_samples)
+        return _counters_dict(c), m, int(rc)
 
     def poll_status(self):
         """(slots finished or failed since the last poll, return code): a
