@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 BYTES_SPLIT = 48   # per particle-step: read c,o,v,id (28 B) + write c,o,v (20 B)
 BYTES_FP64 = 72    # read z,v,id (40 B) + write z,v (32 B)
 CHUNK = 100
-TUNE_KEYS = ("lanes", "sort_interval", "blocks_per_sm", "field_threads", "field_cluster")
+TUNE_KEYS = ("lanes", "sort_interval", "blocks_per_sm", "field_threads", "field_cluster", "electron_threads")
 METRIC = "electron particle-steps/s, FP32-batched vs FP64 plain, 1 GB300; p50/p99 latency"
 
 
@@ -599,6 +599,8 @@ def run_ours(args):
             fixed["sort_interval"] = args.sort_interval
         if args.field_cluster >= 0:
             fixed["field_cluster"] = args.field_cluster
+        if args.electron_threads > 0:
+            fixed["electron_threads"] = args.electron_threads
         tuning = b.set_tuning(**fixed)
     elif args.tune_steps > 0:
         tuning = b.autotune(args.tune_steps)
@@ -798,6 +800,7 @@ def main():
     ap.add_argument("--lanes", type=int, default=0, help="fixed lane count instead of the autotuner's")
     ap.add_argument("--sort-interval", type=int, default=0, help="with --lanes: fixed sort interval")
     ap.add_argument("--field-cluster", type=int, default=-1, help="with --lanes: fixed field cluster size (0: auto)")
+    ap.add_argument("--electron-threads", type=int, default=0, help="with --lanes: electron block size (128/256/512)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="config-4 serving requests (0: none)")
     ap.add_argument("--serve-saturated", type=int, default=300,
                     help="requests of a second serving run at 200/s (queue kept full; 0: none)")

@@ -296,6 +296,12 @@ int hyb_batch_poll(hyb_batch *b, int32_t *done, int32_t cap, int32_t *n_done);
  * the slot's own error code (HYB_ERR_CAPACITY, HYB_ERR_NONFINITE,
  * HYB_ERR_UNSTABLE) when it failed. */
 int hyb_batch_snapshot(hyb_batch *b);
+/* Waits at most timeout_s seconds (host clock) for the work queued on the
+ * batch's stream: HYB_OK when it has finished, HYB_ERR_TIMEOUT when the limit
+ * passed first (the work goes on; the caller may wait again or give up on the
+ * batch).  It polls the stream, so no call of this library blocks a request
+ * loop longer than the loop allows.  Errors: HYB_ERR_ARG, HYB_ERR_CUDA. */
+int hyb_batch_wait(hyb_batch *b, double timeout_s);
 int hyb_batch_poll_snapshot(hyb_batch *b, int32_t *done, int32_t cap, int32_t *n_done);
 int hyb_batch_read_finished(hyb_batch *b, int32_t slot, hyb_counters *counters, hyb_moments *moments);
 
@@ -351,7 +357,10 @@ int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset);
  *                  field step is split: 1, 2, 4, 8 or 16; 0 (default) picks
  *                  about one grid node per half warp for the batch's largest
  *                  grid (at most 8 when the batch has several lanes), as
- *                  many as let every instance's cluster be resident at once.
+ *                  many as let every instance's cluster be resident at once;
+ *   electron_threads  threads of an electron-kernel block in split mode: 128,
+ *                  256 or 512 (0 or 256: default); the FP64 path and the
+ *                  variants with reactions or ion births keep 256.
  * rate is filled by hyb_batch_autotune with the particle-steps/s it measured
  * for the returned choice, and is ignored by hyb_batch_set_tuning. */
 typedef struct hyb_tuning {
@@ -360,7 +369,7 @@ typedef struct hyb_tuning {
     int32_t blocks_per_sm;
     int32_t field_threads;
     int32_t field_cluster;
-    int32_t pad0;
+    int32_t electron_threads;
     double rate;
 } hyb_tuning;
 
@@ -372,7 +381,8 @@ int hyb_batch_set_tuning(hyb_batch *b, const hyb_tuning *t);
  * keep the fastest: lanes in {1, 2, 4, 8, 16}, then the sort interval in
  * {10, 20, 50, 100}, then the electron grid at the occupancy limit or twice it,
  * then the field block size in {256, 512, 1024}, then the field cluster in
- * {automatic, 1, 2, 4, 8, 16}.
+ * {automatic, 1, 2, 4, 8, 16}, then (split mode, no reaction or ion-birth
+ * variant) the electron block size in {128, 256, 512}.
  * Each trial advances every running discharge by one untimed chunk and then
  * by trial_steps rounded up to whole chunks (100 steps): those are real steps
  * of the runs.  Profiling must be off.  *chosen may be NULL. */

@@ -10,9 +10,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "hyb_internal.cuh"
@@ -523,6 +525,7 @@ struct hyb_batch {
     int blocks_per_sm = 0;                 // electron grid = SMs x this (0: occupancy limit)
     int field_threads = 256;               // threads of each CTA of an instance's field step
     int field_cluster = 0;                 // CTAs per instance's field step (0: from the largest grid)
+    int electron_threads = 256;            // threads of the default split-mode electron block
     bool any_chem = false;                 // some admitted discharge has recombination or metastables
     bool any_kin = false;                  // some admitted discharge has kinetic ions
     bool field_split = false;              // FP64 batch whose field step takes the split-mode arithmetic
@@ -604,18 +607,35 @@ int drop_graph(hyb_batch *b)
     return HYB_OK;
 }
 
+// threads of an electron-kernel block: the tuning's for the default split
+// step, 256 for the FP64 path and the reaction and ion-birth variants
+int electron_threads_of(const hyb_batch *b)
+{
+    return (b->precision != HYB_FP32_SPLIT || b->any_chem || b->any_kin) ? kElectronBlock : b->electron_threads;
+}
+
+// electron launch shape (block, shared memory, grid) for the current grids,
+// EEDF and block size
+int reconfigure(hyb_batch *b)
+{
+    const int th = electron_threads_of(b);
+    b->cfg.block = th;
+    // the deposit pass at admission and the reaction variants run 256-thread
+    // blocks with this shared memory: room for at least 256 threads' rows
+    b->cfg.smem = electron_smem_bytes(b->precision, b->max_nodes, b->max_bins, std::max(th, kElectronBlock));
+    int per_sm = electron_blocks_per_sm(b->precision, b->cfg.smem, th);
+    if (per_sm < 1) return fail(HYB_ERR_ARG, "grid too large for the electron kernel's shared memory");
+    b->occ_per_sm = per_sm;
+    b->cfg.grid = b->num_sms * (b->blocks_per_sm > 0 ? b->blocks_per_sm : per_sm);
+    return drop_graph(b);
+}
+
 int configure(hyb_batch *b, int nodes, int bins)
 {
     if (nodes <= b->max_nodes && bins <= b->max_bins) return HYB_OK;
     b->max_nodes = std::max(b->max_nodes, nodes);
     b->max_bins = std::max(b->max_bins, bins);
-    b->cfg.block = kElectronBlock;
-    b->cfg.smem = electron_smem_bytes(b->precision, b->max_nodes, b->max_bins);
-    int per_sm = electron_blocks_per_sm(b->precision, b->cfg.smem);
-    if (per_sm < 1) return fail(HYB_ERR_ARG, "grid too large for the electron kernel's shared memory");
-    b->occ_per_sm = per_sm;
-    b->cfg.grid = b->num_sms * (b->blocks_per_sm > 0 ? b->blocks_per_sm : per_sm);
-    return drop_graph(b);
+    return reconfigure(b);
 }
 
 int lane_first(const hyb_batch *b, int k) { return k * b->per_lane; }
@@ -1049,12 +1069,12 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     if ((S.h.rec_on || S.h.met_on) && !b->any_chem) {
         // the electron step switches to its variant with recombination and the metastable source
         b->any_chem = true;
-        rc = drop_graph(b);
+        rc = reconfigure(b);
         if (rc) return rc;
     }
     if (kin && !b->any_kin) {  // from now on every step also runs the ion kernels
         b->any_kin = true;
-        rc = drop_graph(b);
+        rc = reconfigure(b);
         if (rc) return rc;
     }
     S.mem = mem;
@@ -1138,6 +1158,8 @@ int set_tuning(hyb_batch *b, const hyb_tuning &t)
     if (t.field_cluster != 0 && t.field_cluster != 1 && t.field_cluster != 2 && t.field_cluster != 4 &&
         t.field_cluster != 8 && t.field_cluster != 16)
         return fail(HYB_ERR_ARG, "field_cluster must be 0, 1, 2, 4, 8 or 16");
+    const int eth = t.electron_threads == 0 ? kElectronBlock : t.electron_threads;
+    if (eth != 128 && eth != 256 && eth != 512) return fail(HYB_ERR_ARG, "electron_threads must be 0, 128, 256 or 512");
     int rc = flush_pending(b);
     if (rc) return rc;
     if (t.lanes != b->lanes && (rc = set_lanes(b, t.lanes))) return rc;
@@ -1153,6 +1175,10 @@ int set_tuning(hyb_batch *b, const hyb_tuning &t)
     if (t.field_cluster != b->field_cluster) {
         if ((rc = drop_graph(b))) return rc;
         b->field_cluster = t.field_cluster;
+    }
+    if (eth != b->electron_threads) {
+        b->electron_threads = eth;
+        if (b->max_nodes > 0 && (rc = reconfigure(b))) return rc;
     }
     if (t.blocks_per_sm != b->blocks_per_sm) {
         b->blocks_per_sm = t.blocks_per_sm;
@@ -1170,6 +1196,7 @@ hyb_tuning get_tuning(const hyb_batch *b)
     t.blocks_per_sm = b->blocks_per_sm;
     t.field_threads = b->field_threads;
     t.field_cluster = b->field_cluster;
+    t.electron_threads = b->electron_threads;
     t.rate = 0.0;
     return t;
 }
@@ -1255,6 +1282,16 @@ int autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *out)
         hyb_tuning t = after_field;
         t.field_cluster = c;
         trial(t);
+    }
+    if (b->precision == HYB_FP32_SPLIT && !b->any_chem && !b->any_kin) {
+        const hyb_tuning after_cluster = best;
+        const int thread_opts[3] = {128, 256, 512};
+        for (int th : thread_opts) {
+            if (th == after_cluster.electron_threads) continue;
+            hyb_tuning t = after_cluster;
+            t.electron_threads = th;
+            trial(t);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1577,6 +1614,22 @@ int hyb_batch_poll(hyb_batch *b, int32_t *done, int32_t cap, int32_t *n_done)
     }
     *n_done = k < cap ? k : cap;
     return rc;
+}
+
+int hyb_batch_wait(hyb_batch *b, double timeout_s)
+{
+    if (!b) return fail(HYB_ERR_ARG, "NULL batch");
+    if (!(timeout_s >= 0)) return fail(HYB_ERR_ARG, "timeout must be non-negative");
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t q = cudaStreamQuery(b->stream);
+        if (q == cudaSuccess) return HYB_OK;
+        if (q != cudaErrorNotReady) return fail(HYB_ERR_CUDA, "cudaStreamQuery: %s", cudaGetErrorString(q));
+        const double waited = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (waited >= timeout_s)
+            return fail(HYB_ERR_TIMEOUT, "the batch's queued work did not finish within %.3g s", timeout_s);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
 }
 
 int hyb_batch_snapshot(hyb_batch *b)

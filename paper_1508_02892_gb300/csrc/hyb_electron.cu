@@ -252,6 +252,14 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     unsigned *s_eedf = reinterpret_cast<unsigned *>(smem);
     WarpRow *rows = reinterpret_cast<WarpRow *>(smem + 4 * (((nb + 2) + 3) & ~3));
     if (!HYB_CHECK(b <= capacity && a >= 0 && (a & (kVec - 1)) == 0, 10, b, capacity)) b = a;
+    {
+        // the histogram and one deposit row per warp must fit in the launch's
+        // dynamic shared memory
+        unsigned dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        const size_t need = 4 * (size_t)(((nb + 2) + 3) & ~3) + sizeof(WarpRow) * (size_t)(blockDim.x >> 5);
+        if (!HYB_CHECK(need <= (size_t)dyn, 13, need, dyn)) return;
+    }
     for (int j = threadIdx.x; j <= nb + 1; j += blockDim.x) s_eedf[j] = 0u;
     {
         unsigned *r = reinterpret_cast<unsigned *>(rows);
@@ -829,10 +837,11 @@ __device__ void flush_segment(InstDev *K, unsigned char *smem, const SegCounters
     __syncthreads();
 }
 
-template <int PREC, int MODE, bool CHEM = false, bool KIN = false>
-__global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 3 : 2) k_electron(InstDev *__restrict__ insts,
-                                                                                       int n_max,
-                                                                                       const int64_t *__restrict__ prefix)
+// THREADS: 256 for every variant; the default split-mode step is also built
+// for 128 and 512 (a tuning choice), the register budget per thread the same
+template <int PREC, int MODE, bool CHEM = false, bool KIN = false, int THREADS = kBlock>
+__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 6 : (THREADS == 512 ? 1 : (PREC == HYB_FP32_SPLIT ? 3 : 2)))
+    k_electron(InstDev *__restrict__ insts, int n_max, const int64_t *__restrict__ prefix)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     for_block_runs(insts, n_max, prefix, [&](InstDev *K, int64_t a, int64_t b) {
@@ -1032,10 +1041,10 @@ __global__ void k_set_active(InstDev *K, int active, int64_t target_step)
     K->target_step = target_step;
 }
 
-template <int PREC, int MODE, bool CHEM = false, bool KIN = false>
+template <int PREC, int MODE, bool CHEM = false, bool KIN = false, int THREADS = kBlock>
 cudaError_t launch_k(InstDev *inst, int n_max, const int64_t *prefix, LaunchCfg cfg, cudaStream_t s)
 {
-    k_electron<PREC, MODE, CHEM, KIN><<<cfg.grid, cfg.block, cfg.smem, s>>>(inst, n_max, prefix);
+    k_electron<PREC, MODE, CHEM, KIN, THREADS><<<cfg.grid, THREADS, cfg.smem, s>>>(inst, n_max, prefix);
     return cudaGetLastError();
 }
 
@@ -1061,24 +1070,32 @@ void configure_kernels()
     cudaFuncSetAttribute(k_electron<HYB_FP64, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_electron<HYB_FP64, 0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0, false, false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         most);
+    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0, false, false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         most);
     configure_ion_kernels();
     configure_field_kernel();
 }
 
-int electron_blocks_per_sm(int precision, size_t smem)
+int electron_blocks_per_sm(int precision, size_t smem, int threads)
 {
     int n = 0;
-    if (precision == HYB_FP32_SPLIT)
+    if (precision == HYB_FP32_SPLIT && threads == 128)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_electron<HYB_FP32_SPLIT, 0, false, false, 128>, 128, smem);
+    else if (precision == HYB_FP32_SPLIT && threads == 512)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_electron<HYB_FP32_SPLIT, 0, false, false, 512>, 512, smem);
+    else if (precision == HYB_FP32_SPLIT)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_electron<HYB_FP32_SPLIT, 0>, kBlock, smem);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_electron<HYB_FP64, 0>, kBlock, smem);
     return n;
 }
 
-size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins)
+size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins, int threads)
 {
     if (precision == HYB_FP32_SPLIT)  // EEDF histogram and one deposit row per warp
-        return 4 * (size_t)(((eedf_bins + 2) + 3) & ~3) + sizeof(WarpRow) * (kBlock / 32) + 16;
+        return 4 * (size_t)(((eedf_bins + 2) + 3) & ~3) + sizeof(WarpRow) * (size_t)(threads / 32) + 16;
     const size_t el = 8;
     return 3 * el * (size_t)max_nodes + 4 * (size_t)(eedf_bins + 1) + 16;
 }
@@ -1099,6 +1116,8 @@ cudaError_t launch_electron_step(InstDev *inst, int n_max, const int64_t *prefix
     if (chem)
         return sp ? launch_k<HYB_FP32_SPLIT, 0, true>(inst, n_max, prefix, cfg, s)
                   : launch_k<HYB_FP64, 0, true>(inst, n_max, prefix, cfg, s);
+    if (sp && cfg.block == 128) return launch_k<HYB_FP32_SPLIT, 0, false, false, 128>(inst, n_max, prefix, cfg, s);
+    if (sp && cfg.block == 512) return launch_k<HYB_FP32_SPLIT, 0, false, false, 512>(inst, n_max, prefix, cfg, s);
     return sp ? launch_k<HYB_FP32_SPLIT, 0>(inst, n_max, prefix, cfg, s) : launch_k<HYB_FP64, 0>(inst, n_max, prefix, cfg, s);
 }
 

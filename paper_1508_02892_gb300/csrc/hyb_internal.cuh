@@ -277,7 +277,7 @@ cudaError_t launch_sort(InstDev *inst, int n_max, int64_t *prefix, int precision
 cudaError_t launch_prefix(InstDev *inst, int n_max, int64_t *prefix, cudaStream_t s);
 cudaError_t launch_prefix_one(InstDev *inst, int64_t *prefix, cudaStream_t s);
 cudaError_t launch_set_active(InstDev *inst, int active, int64_t target_step, cudaStream_t s);
-size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins);
+size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins, int threads = 256);
 
 // field kernel (hyb_field.cu)
 cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned int *ticket, bool fast, int max_nodes,
@@ -294,6 +294,6 @@ void set_last_error(const char *msg);
 
 // one-time kernel attributes and occupancy (hyb_electron.cu)
 void configure_kernels();
-int electron_blocks_per_sm(int precision, size_t smem);
+int electron_blocks_per_sm(int precision, size_t smem, int threads = 256);
 
 }  // namespace hyb

@@ -98,7 +98,7 @@ class SwarmResult(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("sort_interval", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("field_threads", C.c_int32), ("field_cluster", C.c_int32), ("pad0", C.c_int32),
+                ("field_threads", C.c_int32), ("field_cluster", C.c_int32), ("electron_threads", C.c_int32),
                 ("rate", C.c_double)]
 
 
@@ -129,6 +129,7 @@ EXPORTS = {
     "hyb_batch_advance": (C.c_int, [C.c_void_p, C.c_int64]),
     "hyb_batch_poll": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]),
     "hyb_batch_snapshot": (C.c_int, [C.c_void_p]),
+    "hyb_batch_wait": (C.c_int, [C.c_void_p, C.c_double]),
     "hyb_batch_poll_snapshot": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]),
     "hyb_batch_read_finished": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "hyb_batch_read_moments": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Moments)]),
@@ -420,6 +421,15 @@ class Batch:
         _check(rc)
         return done
 
+    def wait(self, timeout_s):
+        """Wait at most timeout_s for the queued work: True when done, False
+        when the limit passed first (HYB_ERR_TIMEOUT)."""
+        rc = lib().hyb_batch_wait(self.h, float(timeout_s))
+        if rc == -5:
+            return False
+        _check(rc)
+        return True
+
     def snapshot(self):
         """Queue a status snapshot after the work queued so far."""
         _check(lib().hyb_batch_snapshot(self.h))
@@ -496,13 +506,14 @@ class Batch:
         return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
     def set_tuning(self, lanes=None, sort_interval=None, blocks_per_sm=None, field_threads=None,
-                   field_cluster=None):
+                   field_cluster=None, electron_threads=None):
         cur = self.tuning()
         t = Tuning(int(lanes if lanes is not None else cur["lanes"]),
                    int(sort_interval if sort_interval is not None else cur["sort_interval"]),
                    int(blocks_per_sm if blocks_per_sm is not None else cur["blocks_per_sm"]),
                    int(field_threads if field_threads is not None else cur["field_threads"]),
-                   int(field_cluster if field_cluster is not None else cur["field_cluster"]), 0, 0.0)
+                   int(field_cluster if field_cluster is not None else cur["field_cluster"]),
+                   int(electron_threads if electron_threads is not None else cur["electron_threads"]), 0.0)
         _check(lib().hyb_batch_set_tuning(self.h, C.byref(t)))
         return self.tuning()
 

@@ -116,3 +116,21 @@ def test_failed_slot_is_reported_evicted_and_others_finish():
         np.testing.assert_allclose(q["z"], parts["z"], rtol=0, atol=1e-15 * good[0]["gap_m"])
         np.testing.assert_allclose(q["vz"], parts["vz"], rtol=1e-13, atol=1e-6)
     b.close()
+
+
+@pytest.mark.gpu
+def test_bounded_wait_reports_timeout_and_the_work_goes_on():
+    """hyb_batch_wait returns HYB_ERR_TIMEOUT when the queued work outlasts its
+    limit (a host-side poll of the stream: nothing on the GPU waits), and the
+    work completes when waited for again."""
+    from paper_1508_02892_gb300 import build, hybrid
+    build.build()
+    b = hybrid.Batch(2, hybrid.HYB_FP32_SPLIT)
+    s = b.admit(W.config2(n_particles=2_000_000), 1000)
+    assert b.wait(60.0)
+    b.advance(1000)                                # about 50 ms of queued work
+    assert b.wait(1e-4) is False
+    assert b.wait(120.0) is True
+    c = b.counters(s)
+    assert c["step"] == 1000 and c["status"] == 0
+    b.close()

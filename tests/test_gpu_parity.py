@@ -296,6 +296,29 @@ def test_batch_matches_single_runs_fp64(lanes, sort_interval, field_threads):
     b.close()
 
 
+@pytest.mark.parametrize("threads", [128, 512])
+def test_split_electron_block_sizes_track_the_default(threads):
+    """The split electron step built for 128 or 512 threads per block takes the
+    same steps as the default 256: the same random numbers, fixed-point
+    deposit rows, only the order of the FP64 flushes differs."""
+    from paper_1508_02892_gb300 import hybrid
+    p = W.config1(precision=W.FP32_SPLIT, n_particles=30000, seed=71, te0_ev=6.0)
+    out = {}
+    for th in (256, threads):
+        b = hybrid.Batch(1, hybrid.HYB_FP32_SPLIT)
+        b.set_tuning(electron_threads=th)
+        s = b.admit(p, 200)
+        b.advance(200)
+        assert b.tuning()["electron_threads"] == th
+        out[th] = (b.moments(s), b.counters(s))
+        b.close()
+    (ma, ca), (mb, cb) = out[256], out[threads]
+    assert cb["status"] == 0 and cb["step"] == 200
+    assert abs(ca["elastic"] - cb["elastic"]) <= 1e-3 * ca["elastic"]
+    for k in ("ne", "ebar", "gamma", "eedf"):
+        assert np.linalg.norm(ma[k] - mb[k]) / np.linalg.norm(ma[k]) < 1e-3, k
+
+
 def test_autotune_keeps_a_valid_configuration():
     """The autotuner's trials are real steps: afterwards every discharge has
     advanced, particle bookkeeping still holds and the choice is in range."""
