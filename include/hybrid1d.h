@@ -382,7 +382,7 @@ int hyb_batch_set_tuning(hyb_batch *b, const hyb_tuning *t);
  * {10, 20, 50, 100}, then the electron grid at the occupancy limit or twice it,
  * then the field block size in {256, 512, 1024}, then the field cluster in
  * {automatic, 1, 2, 4, 8, 16}, then (split mode, no reaction or ion-birth
- * variant) the electron block size in {128, 256, 512}.
+ * variant) the electron block size in {128, 256, 512}, then the lanes again.
  * Each trial advances every running discharge by one untimed chunk and then
  * by trial_steps rounded up to whole chunks (100 steps): those are real steps
  * of the runs.  Profiling must be off.  *chosen may be NULL. */

@@ -1293,6 +1293,16 @@ int autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *out)
             trial(t);
         }
     }
+    // the lane count once more, with everything else as chosen (how well the
+    // lanes overlap depends on the block sizes)
+    const hyb_tuning after_threads = best;
+    for (int l : lane_opts) {
+        if (l > std::min(kMaxLanes, b->max_inst)) break;
+        if (l == after_threads.lanes) continue;
+        hyb_tuning t = after_threads;
+        t.lanes = l;
+        trial(t);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
