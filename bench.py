@@ -347,7 +347,7 @@ def single_config_load(name, p, stream, flush, chunks=3, oracle_particles=200000
     q["weight"] = p["n0_m3"] * p["gap_m"] / p["n_particles"] if not p.get("weight") else p["weight"]
     q["weight"] *= p["n_particles"] / oracle_particles
     q["n_particles"] = oracle_particles
-    orate, on, ot = _oracle_rate(q, oracle_steps)
+    orate, on, ot = _oracle_rate(q, oracle_steps) if oracle_steps > 0 else (None, 0, 0.0)
     return {"workload": name, "value": n / (ms / 1e3), "unit": "particle-steps/s", "particles": int(p["n_particles"]),
             "cells": int(p["n_cells"]), "steps_timed": chunks * CHUNK, "status": int(status),
             "kernel_ms_per_step": {"electron": prof["ms_electron"] / max(prof["n_electron"], 1),
@@ -355,9 +355,10 @@ def single_config_load(name, p, stream, flush, chunks=3, oracle_particles=200000
             "roofline": {"kernel": "k_electron", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "bytes_per_unit": bpu,
                          "units_per_launch": per_launch, "avg_launch_ms": avg_ms},
-            "cpu_oracle": {"value": orate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                           "sample": f"the same discharge with {oracle_particles} electrons (density kept), "
-                                     f"{oracle_steps} steps, {on} particle-steps in {ot:.1f} s"}}
+            "cpu_oracle": None if orate is None else
+            {"value": orate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+             "sample": f"the same discharge with {oracle_particles} electrons (density kept), "
+                       f"{oracle_steps} steps, {on} particle-steps in {ot:.1f} s"}}
 
 
 def config1_full(stream):
@@ -815,6 +816,9 @@ def main():
     ap.add_argument("--swarm-ions", type=int, default=65536, help="ions per field of the swarm run")
     ap.add_argument("--swarm-steps", type=int, default=20000)
     ap.add_argument("--only-swarm", action="store_true", help="run and print the ion-swarm measurement alone")
+    ap.add_argument("--only-config", type=int, default=0, choices=[0, 2, 5],
+                    help="run and print one single-instance workload alone (2: He 1000 cells, 2e6 electrons; "
+                         "5: Ar 4000 cells, 5e7 electrons)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip configs 1, 2, 5 and the accuracy check")
     ap.add_argument("--no-fp64", action="store_true")
@@ -834,6 +838,21 @@ def main():
         G.build()
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         print(json.dumps({"swarm": swarm_load(n_ions=args.swarm_ions, n_steps=args.swarm_steps)}), flush=True)
+        return
+    if args.only_config:
+        import torch
+
+        import __graft_entry__ as G
+        from paper_1508_02892_gb300 import workloads as W
+        G.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+        p = W.config2() if args.only_config == 2 else W.config5()
+        out = single_config_load(f"config {args.only_config}", p, stream, flush, chunks=max(args.steps // CHUNK, 1),
+                                 oracle_particles=200000, oracle_steps=0 if args.no_cpu else 20)
+        print(json.dumps({f"config{args.only_config}": out}), flush=True)
         return
     if args.only_variants:
         import torch

@@ -232,7 +232,7 @@ Layout layout_of(const hyb_params &p)
     add(8 * (size_t)(nb + 1));                          // eedf
     add(32 * (size_t)p.n_xs);                           // xs
     add(16 * (size_t)p.n_xs);                           // xsf
-    add(32 * (size_t)(p.n_tab > 0 ? p.n_tab : 1));      // tab
+    add((32 + 8 * kTabCols + 8) * (size_t)(p.n_tab > 0 ? p.n_tab : 1));  // tab, tabx, tabf
     add(8 * (size_t)p.n_xs);                            // xs_rec
     add(4 * (size_t)p.n_xs);                            // xs_recf
     add(4 * (size_t)G);                                 // nif
@@ -428,12 +428,28 @@ void derive(const hyb_params &p, InstDev &K, std::vector<double> &xs, std::vecto
     K.met_sp[1] = sqrt(2.0 * kQe * p.pooling_energy_ev / kMe);
     K.gamma_met = p.gamma_met;
     const int nt = K.n_tab > 0 ? K.n_tab : 1;
-    tab.assign(4 * (size_t)nt, 0.0);
+    // the table as given, then the split-mode layout (with the slope of each
+    // segment, formed once here), then the FP32 abscissae (two per double)
+    tab.assign((4 + kTabCols + 1) * (size_t)nt, 0.0);
     for (int k = 0; k < K.n_tab; ++k) {
         tab[4 * k + 0] = p.tab_eon_td[k];
         tab[4 * k + 1] = p.tab_mu[k];
         tab[4 * k + 2] = p.tab_nu[k];
         tab[4 * k + 3] = p.tab_mu[k] * p.tab_eon_td[k] * 1e-21 * K.ngas;
+    }
+    double *x = tab.data() + 4 * (size_t)nt;
+    float *xf = reinterpret_cast<float *>(x + kTabCols * (size_t)nt);
+    for (int k = 0; k < K.n_tab; ++k) {
+        const double *a = tab.data() + 4 * k;
+        double *o = x + kTabCols * k;
+        o[0] = a[0];
+        o[1] = a[1];
+        o[3] = a[3];
+        o[4] = a[2];
+        o[2] = k + 1 < K.n_tab ? (a[5] - a[1]) / (a[4] - a[0]) : 0.0;
+        o[5] = k + 1 < K.n_tab ? (a[6] - a[2]) / (a[7] - a[3]) : 0.0;
+        xf[k] = (float)a[0];
+        xf[K.n_tab + k] = (float)a[3];
     }
 }
 
@@ -466,6 +482,11 @@ void bind_pointers(const hyb_params &p, const Layout &L, char *base, InstDev &K,
     K.xs = (const double *)(base + L.off[k++]);
     K.xsf = (const float4 *)(base + L.off[k++]);
     K.tab = (const double *)(base + L.off[k++]);
+    {
+        const size_t nt = (size_t)(p.n_tab > 0 ? p.n_tab : 1);
+        K.tabx = K.tab + 4 * nt;
+        K.tabf = (const float *)(K.tabx + kTabCols * nt);
+    }
     K.xs_rec = (const double *)(base + L.off[k++]);
     K.xs_recf = (const float *)(base + L.off[k++]);
     K.nif = (float *)(base + L.off[k++]);

@@ -63,9 +63,26 @@ struct Red {
     double before, all;              // cluster offset and total of the last reduction
     double cpre[3], ctot[3];         // cluster prefix and total of the pair scan
     double phi0, v_old;              // drive at the end and at the start of the step
+    double gN;                       // Gamma_i at z = L, written by the CTA that owns node G - 1 (into rank 0's copy)
+    double E0;                       // E at z = 0 after the step (rank 0)
     int flag;
     unsigned long long count;
 };
+
+// What rank 0's bookkeeping at the end of the step reads of the descriptor,
+// loaded at the start of the step beside the other CTAs' work: all of it is
+// written only by that bookkeeping (previous steps), by earlier kernels or by
+// the host before the launch.  The metastable fluxes and the slot count, which
+// the metastable step of this launch may change, are read again after it.
+struct Book {
+    int64_t step, n_samples, pw_count, pw_steps, pw_periods, capacity, target_step;
+    unsigned long long n_slots, see0, see1, loss0, pw_loss0, ion_l0, ion_l1, ion_prev0, ion_prev1;
+    double gamma_see, gamma_met, flux_met0, flux_met1, pw_acc, pw_target, pw_alpha, v_rf, see_speed, L;
+    uint32_t seed_lo, seed_hi;
+    int precision, n_cells;
+    PartBuf P;
+};
+
 
 // This CTA's place in its instance's cluster.  Ranks 0..nown-1 own nodes
 // [rank P, min(G, (rank + 1) P)); higher ranks own none and only take part in
@@ -289,12 +306,11 @@ struct Fluid {
 };
 
 // Split mode: the same coefficients in FP64 with fewer FP64 instructions (this
-// part issues FP64 at two FMA per cycle per SM): the table is staged with the
-// slope of every segment (8 columns: E/N, mu, d mu/d(E/N), u, nu, d nu/du),
-// so a lookup is the search and one FMA, and reciprocals start from the FP32
-// reciprocal with two Newton steps.  Values differ from the FP64 mode's by
-// rounding only.
-constexpr int kTabCols = 8;
+// part issues FP64 at two FMA per cycle per SM): the table comes with the
+// slope of every segment (kTabCols columns: E/N, mu, d mu/d(E/N), u, nu,
+// d nu/du, formed at admission), so a lookup is the search and one FMA, and
+// reciprocals start from the FP32 reciprocal with two Newton steps.  Values
+// differ from the FP64 mode's by rounding only.
 
 __device__ __forceinline__ double lookup_slope(const double *tab, const float *xf, int n, int cx, int cy, int cs,
                                               double v)
@@ -353,27 +369,23 @@ struct FluidFast {
     }
 };
 
-// Stage an instance's table {E/N, mu, nu, u} in shared memory: as it is
-// (FP64 mode) or with the segment slopes (split mode)
+// Stage an instance's table in shared memory: {E/N, mu, nu, u} as it is (FP64
+// mode), or the split-mode layout with the segment slopes and the FP32
+// abscissae (16-byte copies).  Read after the next block barrier.
 template <bool FAST>
-__device__ void stage_table(const InstDev *K, double *s_tab, float *s_tabf)
+__device__ void stage_table(const InstDev *K, int n, double *s_tab, float *s_tabf)
 {
-    const int n = K->n_tab;
     if constexpr (!FAST) {
-        for (int j = threadIdx.x; j < 4 * n; j += blockDim.x) s_tab[j] = K->tab[j];
+        const double *tab = K->tab;
+        for (int j = threadIdx.x; j < 4 * n; j += blockDim.x) s_tab[j] = tab[j];
     } else {
+        const double2 *src = reinterpret_cast<const double2 *>(K->tabx);
+        const float *srcf = K->tabf;
+        double2 *dst = reinterpret_cast<double2 *>(s_tab);
+        for (int j = threadIdx.x; j < kTabCols / 2 * n; j += blockDim.x) dst[j] = src[j];
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const double *a = K->tab + 4 * k;
-            double *o = s_tab + kTabCols * k;
-            o[0] = a[0];
-            o[1] = a[1];
-            o[3] = a[3];
-            o[4] = a[2];
-            o[2] = k + 1 < n ? (a[5] - a[1]) / (a[4] - a[0]) : 0.0;
-            o[5] = k + 1 < n ? (a[6] - a[2]) / (a[7] - a[3]) : 0.0;
-            o[6] = o[7] = 0.0;
-            s_tabf[k] = (float)a[0];
-            s_tabf[kMaxTab + k] = (float)a[3];
+            s_tabf[k] = srcf[k];
+            s_tabf[kMaxTab + k] = srcf[n + k];
         }
     }
 }
@@ -567,11 +579,48 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
 
     // the drive at the end of the step (and at its start, for the absorbed
     // power), by the last thread beside the others' work
+    __shared__ Book bk;
     if (t == T - 1) {
         red.flag = 0;
         red.count = 0ull;
         red.phi0 = K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)(K->step + (init ? 0 : 1)) * dt));
         red.v_old = (cu.rank == 0 && !init) ? K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)K->step * dt)) : 0.0;
+    }
+    if (t == T - 2 && cu.rank == 0 && !init) {
+        bk.step = K->step;
+        bk.n_samples = K->n_samples;
+        bk.pw_count = K->pw_count;
+        bk.pw_steps = K->pw_steps;
+        bk.pw_periods = K->pw_periods;
+        bk.capacity = K->capacity;
+        bk.target_step = K->target_step;
+        bk.n_slots = K->n_slots;
+        bk.see0 = K->ctr[C_SEE0];
+        bk.see1 = K->ctr[C_SEE1];
+        bk.loss0 = K->ctr[C_LOSS0];
+        bk.pw_loss0 = K->pw_loss0;
+        if (kin) {
+            const InstDev *I = K->ion;
+            bk.ion_l0 = I->ctr[C_LOSS0];
+            bk.ion_l1 = I->ctr[C_LOSS1];
+            bk.ion_prev0 = K->ion_loss_prev[0];
+            bk.ion_prev1 = K->ion_loss_prev[1];
+        }
+        bk.gamma_see = K->gamma_see;
+        bk.gamma_met = K->gamma_met;
+        bk.flux_met0 = K->flux_met[0];
+        bk.flux_met1 = K->flux_met[1];
+        bk.pw_acc = K->pw_acc;
+        bk.pw_target = K->pw_target;
+        bk.pw_alpha = K->pw_alpha;
+        bk.v_rf = K->v_rf;
+        bk.see_speed = K->see_speed;
+        bk.L = K->L;
+        bk.seed_lo = K->seed_lo;
+        bk.seed_hi = K->seed_hi;
+        bk.precision = K->precision;
+        bk.n_cells = K->n_cells;
+        bk.P = K->buf[K->cur];
     }
     // inputs of the step (every write of these globals comes after at least
     // one cluster barrier)
@@ -755,6 +804,7 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
             s_ni[j] = nn;
             K->ni[j] = nn;
             K->gam[j] = gfin[j];
+            if (j == G - 1) *cl_remote(&red.gN, 0) = gfin[j];
             K->gsrc[j] = gs;
             K->acc_ni[j] += nn;
             K->acc_gi[j] += gfin[j];
@@ -838,6 +888,7 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
         }
         K->E[j] = e;
         K->Ef[j] = (float)e;
+        if (j == 0) red.E0 = e;
         K->phi[j] = j == G - 1 ? 0.0 : phi0 + (double)j * d0 - Tj;
         if (!isfinite(e) || !isfinite(s_ni[j])) bad = 1;
     }
@@ -861,34 +912,42 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
     if (cu.rank != 0) return;
 
     // ------------------------------------------- bookkeeping, gamma emission
+    // (the descriptor's values from the prefetch bk, written back here)
     __shared__ int s_cnt[2];
     __shared__ unsigned long long s_base;
     if (t == 0) {
-        K->n_samples += 1;
+        K->n_samples = bk.n_samples + 1;
         const double v_old = red.v_old;
+        double f_in[2];
         if (kin) {  // the ions removed at each wall this step
-            const InstDev *I = K->ion;
-            const unsigned long long l0 = I->ctr[C_LOSS0], l1 = I->ctr[C_LOSS1];
-            K->flux_in[0] = (double)(l0 - K->ion_loss_prev[0]) * w / dt;
-            K->flux_in[1] = (double)(l1 - K->ion_loss_prev[1]) * w / dt;
-            K->ion_loss_prev[0] = l0;
-            K->ion_loss_prev[1] = l1;
+            f_in[0] = (double)(bk.ion_l0 - bk.ion_prev0) * w / dt;
+            f_in[1] = (double)(bk.ion_l1 - bk.ion_prev1) * w / dt;
+            K->ion_loss_prev[0] = bk.ion_l0;
+            K->ion_loss_prev[1] = bk.ion_l1;
         } else {
-            const double g0 = gfin[0], gN = K->gam[G - 1];
-            K->flux_in[0] = g0 < 0.0 ? -g0 : 0.0;
-            K->flux_in[1] = gN > 0.0 ? gN : 0.0;
+            const double g0 = gfin[0], gN = red.gN;
+            f_in[0] = g0 < 0.0 ? -g0 : 0.0;
+            f_in[1] = gN > 0.0 ? gN : 0.0;
         }
-        K->step += 1;
-        const uint32_t n = (uint32_t)K->step;
+        K->flux_in[0] = f_in[0];
+        K->flux_in[1] = f_in[1];
+        const int64_t step = bk.step + 1;
+        K->step = step;
+        const uint32_t n = (uint32_t)step;
         s_cnt[0] = s_cnt[1] = 0;
-        if ((K->gamma_see > 0.0 || K->gamma_met > 0.0) && w > 0.0) {
+        if ((bk.gamma_see > 0.0 || bk.gamma_met > 0.0) && w > 0.0) {
+            double f_met[2] = {bk.flux_met0, bk.flux_met1};
+            if (K->met_on) {
+                f_met[0] = K->flux_met[0];
+                f_met[1] = K->flux_met[1];
+            }
             for (int wall = 0; wall < 2; ++wall) {
                 // ions and metastables striking the wall (Sec. II.D)
-                const double ns = (K->gamma_see * K->flux_in[wall] + K->gamma_met * K->flux_met[wall]) * dt / w;
+                const double ns = (bk.gamma_see * f_in[wall] + bk.gamma_met * f_met[wall]) * dt / w;
                 if (!(ns > 0.0)) continue;
                 const double k = floor(ns);
                 const double frac = ns - k;
-                const uint4 r = draw(0xFFFFFFFFFFFFFF00ull | (uint64_t)wall, n, K->seed_lo, K->seed_hi, 3);
+                const uint4 r = draw(0xFFFFFFFFFFFFFF00ull | (uint64_t)wall, n, bk.seed_lo, bk.seed_hi, 3);
                 int64_t c = (int64_t)k + (u01d(r.x) < frac ? 1 : 0);
                 if (c > (1 << 20) - 1) {
                     c = (1 << 20) - 1;
@@ -897,36 +956,42 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
                 s_cnt[wall] = (int)c;
             }
         }
-        s_base = K->n_slots;
+        const unsigned long long base = K->met_on ? K->n_slots : bk.n_slots;
+        s_base = base;
         const unsigned long long tot = (unsigned long long)(s_cnt[0] + s_cnt[1]);
-        K->n_slots = s_base + tot;
-        K->ctr[C_SEE0] += s_cnt[0];
-        K->ctr[C_SEE1] += s_cnt[1];
+        K->n_slots = base + tot;
+        K->ctr[C_SEE0] = bk.see0 + s_cnt[0];
+        K->ctr[C_SEE1] = bk.see1 + s_cnt[1];
         // Absorbed power (Eq. 2.9): V J dt per step at the driven electrode, V at
         // mid-step, J along +z = ion flux + electrons absorbed (+) and emitted (-)
         // there + displacement current; at the end of an RF period P_abs and the
         // amplitude of the next period
-        const unsigned long long l0 = K->ctr[C_LOSS0];
-        const int64_t d_loss0 = (int64_t)(l0 - K->pw_loss0), d_see0 = s_cnt[0];
+        const unsigned long long l0 = bk.loss0;
+        const int64_t d_loss0 = (int64_t)(l0 - bk.pw_loss0), d_see0 = s_cnt[0];
         K->pw_loss0 = l0;
         const double v_mid = 0.5 * (v_old + phi0);
-        const double jz = kQe * gfin[0] + kQe * w * (double)(d_loss0 - d_see0) / dt + kEps0 * (K->E[0] - s_E[0]) / dt;
-        K->pw_acc += v_mid * jz * dt;
-        if (++K->pw_count == K->pw_steps) {
-            K->pw_last = K->pw_acc / ((double)K->pw_steps * dt);
-            if (K->pw_target > 0.0 && K->pw_alpha > 0.0)
-                K->v_rf = K->v_rf * (1.0 - K->pw_alpha * (K->pw_last - K->pw_target) / K->pw_target);
+        const double jz = kQe * gfin[0] + kQe * w * (double)(d_loss0 - d_see0) / dt + kEps0 * (red.E0 - s_E[0]) / dt;
+        const double acc = bk.pw_acc + v_mid * jz * dt;
+        const int64_t cnt = bk.pw_count + 1;
+        if (cnt == bk.pw_steps) {
+            const double last = acc / ((double)bk.pw_steps * dt);
+            K->pw_last = last;
+            if (bk.pw_target > 0.0 && bk.pw_alpha > 0.0)
+                K->v_rf = bk.v_rf * (1.0 - bk.pw_alpha * (last - bk.pw_target) / bk.pw_target);
             K->pw_acc = 0.0;
             K->pw_count = 0;
-            K->pw_periods += 1;
+            K->pw_periods = bk.pw_periods + 1;
+        } else {
+            K->pw_acc = acc;
+            K->pw_count = cnt;
         }
     }
     __syncthreads();
     const int ntot = s_cnt[0] + s_cnt[1];
     if (ntot) {
-        const PartBuf P = K->buf[K->cur];
-        const uint32_t n = (uint32_t)K->step;
-        const double sp = K->see_speed, L = K->L;
+        const PartBuf P = bk.P;
+        const uint32_t n = (uint32_t)(bk.step + 1);
+        const double sp = bk.see_speed, L = bk.L;
         for (int k = t; k < ntot; k += T) {
             const int wall = k < s_cnt[0] ? 0 : 1;
             const uint32_t j = (uint32_t)(wall == 0 ? k : k - s_cnt[0]);
@@ -946,18 +1011,18 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
                 z = L - u01d(r.z) * vn * dt;
             }
             const unsigned long long slot = s_base + (unsigned long long)k;
-            if (slot >= (unsigned long long)K->capacity) {
+            if (slot >= (unsigned long long)bk.capacity) {
                 atomicOr(&K->status, (unsigned)HYB_STATUS_CAPACITY);
                 continue;
             }
             P.id[slot] = id;
-            if (K->precision == HYB_FP32_SPLIT) {
+            if (bk.precision == HYB_FP32_SPLIT) {
                 const double x = z / dz;
                 const double f = floor(x);
                 int c = (int)f;
                 double o = x - f;
-                if (c >= K->n_cells) {
-                    c = K->n_cells - 1;
+                if (c >= bk.n_cells) {
+                    c = bk.n_cells - 1;
                     o = 1.0;
                 }
                 P.c[slot] = c;
@@ -973,16 +1038,15 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
             }
         }
     }
-    __syncthreads();
     if (t == 0) {
-        unsigned long long ns = K->n_slots;
-        if (ns > (unsigned long long)K->capacity) {
+        unsigned long long ns = s_base + (unsigned long long)ntot;
+        if (ns > (unsigned long long)bk.capacity) {
             atomicOr(&K->status, (unsigned)HYB_STATUS_CAPACITY);
-            ns = (unsigned long long)K->capacity;
+            ns = (unsigned long long)bk.capacity;
             K->n_slots = ns;
         }
         K->n_slots_step = (int64_t)ns;
-        if (K->target_step > 0 && K->step >= K->target_step) K->active = 0;
+        if (bk.target_step > 0 && bk.step + 1 >= bk.target_step) K->active = 0;
     }
 }
 
@@ -996,14 +1060,15 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 3 : 1) k_field(InstD
     extern __shared__ __align__(16) double sm[];
     __shared__ Red red;
     __shared__ double s_slots[kSlots];
-    __shared__ double s_tab[kTabCols * kMaxTab];
+    __shared__ __align__(16) double s_tab[kTabCols * kMaxTab];
     __shared__ float s_tabf[FAST ? 2 * kMaxTab : 1];
     InstDev *K = &insts[blockIdx.y];
-    const bool run = K->active || K->init_pending;
+    // the descriptor's fields read here, loaded together
+    const int act = K->active, ini = K->init_pending, G = K->G, n_tab = K->n_tab;
+    const bool run = (act | ini) != 0;
     // every CTA of the cluster takes the same branch (one instance per cluster)
     bool body = false;
-    if (run && HYB_CHECK(K->G >= 3 && K->G <= max_nodes && K->n_tab <= kMaxTab, 20, K->G, max_nodes)) {
-        const int G = K->G;
+    if (run && HYB_CHECK(G >= 3 && G <= max_nodes && n_tab <= kMaxTab, 20, G, max_nodes)) {
         Clu cu;
         cu.rank = (int)cg::this_cluster().block_rank();
         cu.size = (int)gridDim.x;
@@ -1016,7 +1081,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 3 : 1) k_field(InstD
         cu.c0 = min(cu.rank * P, G);
         cu.c1 = cu.rank < nown ? min(cu.c0 + P, G) : cu.c0;
         if (HYB_CHECK(P + 2 * kHalo + 2 <= lw, 22, P, lw)) {
-            stage_table<FAST>(K, s_tab, s_tabf);
+            stage_table<FAST>(K, n_tab, s_tab, s_tabf);
             field_body<FAST>(K, sm, lw, red, s_tab, s_tabf, cu, s_slots);
             body = true;
         }

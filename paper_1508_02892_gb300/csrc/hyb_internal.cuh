@@ -43,6 +43,10 @@ struct FieldK {
     double w_in, w_wall, c_src, inv_dz, half_inv_dz, c_gauss;  // split-mode Poisson
 };
 
+// Columns of a transport-table row in the split-mode field kernel: E/N, mu,
+// d mu/d(E/N), u, nu, d nu/du and two of padding (rows of 64 bytes)
+constexpr int kTabCols = 8;
+
 // Everything a kernel needs about one discharge.  Lives in device memory; the
 // host writes it at admission and the kernels update the mutable tail.
 struct InstDev {
@@ -62,6 +66,8 @@ struct InstDev {
     const double *xs;    // [n_xs][4] {E, sigma_el, sigma_exc, sigma_ion}
     const float4 *xsf;   // [n_xs] {E, N sigma_el/nu_max, N sigma_exc/nu_max, N sigma_ion/nu_max}
     const double *tab;   // [n_tab][4] {E/N (Td), mu, nu, u = mu E}
+    const double *tabx;  // [n_tab][kTabCols] the same with segment slopes (the split-mode field kernel's layout)
+    const float *tabf;   // [2][n_tab] FP32 copies of the E/N and u columns
     // particles (double-buffered for the cell sort)
     PartBuf buf[2];
     // grids, n_nodes entries
