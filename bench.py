@@ -301,7 +301,7 @@ def _oracle_rate(p, steps):
     return n / t, n, t
 
 
-def single_config_load(name, p, stream, flush, chunks=3, oracle_particles=200000, oracle_steps=5):
+def single_config_load(name, p, stream, flush, chunks=3, oracle_particles=200000, oracle_steps=5, tuning=None):
     """One discharge of a single-instance workload as a one-slot batch (one
     lane, sort every 100 steps): whole-step particle-steps/s over `chunks`
     graph chunks (CUDA events), the electron kernel's fraction of the HBM
@@ -313,7 +313,7 @@ def single_config_load(name, p, stream, flush, chunks=3, oracle_particles=200000
     from paper_1508_02892_gb300 import hybrid
     b = hybrid.Batch(1, p["precision"], stream=stream.cuda_stream)
     s = b.admit(p)
-    b.set_tuning(lanes=1, sort_interval=100)
+    b.set_tuning(**dict({"lanes": 1, "sort_interval": 100}, **(tuning or {})))
     b.advance(CHUNK)
     torch.cuda.synchronize()
     c0 = b.counters(s)["pushes"]
@@ -850,8 +850,14 @@ def main():
         torch.cuda.set_stream(stream)
         flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
         p = W.config2() if args.only_config == 2 else W.config5()
+        tuning = {}
+        if args.sort_interval > 0:
+            tuning["sort_interval"] = args.sort_interval
+        if args.field_cluster >= 0:
+            tuning["field_cluster"] = args.field_cluster
         out = single_config_load(f"config {args.only_config}", p, stream, flush, chunks=max(args.steps // CHUNK, 1),
-                                 oracle_particles=200000, oracle_steps=0 if args.no_cpu else 20)
+                                 oracle_particles=200000, oracle_steps=0 if args.no_cpu else 20, tuning=tuning)
+        out["tuning"] = tuning
         print(json.dumps({f"config{args.only_config}": out}), flush=True)
         return
     if args.only_variants:

@@ -354,9 +354,10 @@ int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset);
  *   field_threads  threads of each CTA of an instance's field step: 256, 512
  *                  or 1024 (default 256);
  *   field_cluster  CTAs (a thread-block cluster) over which each instance's
- *                  field step is split: 1, 2, 4, 8 or 16; 0 (default) picks
- *                  about one grid node per half warp for the batch's largest
- *                  grid (at most 8 when the batch has several lanes), as
+ *                  field step is split: 1..16; 0 (default) picks about one
+ *                  computed node (a CTA's run of the grid and 10 halo nodes
+ *                  on each side) per half warp for the batch's largest grid
+ *                  (at most 8 CTAs when the batch has several lanes), as
  *                  many as let every instance's cluster be resident at once;
  *   electron_threads  threads of an electron-kernel block in split mode: 128,
  *                  256 or 512 (0 or 256: default); the FP64 path and the

@@ -1176,9 +1176,7 @@ int set_tuning(hyb_batch *b, const hyb_tuning &t)
     if (t.blocks_per_sm < 0 || t.blocks_per_sm > 64) return fail(HYB_ERR_ARG, "blocks_per_sm must be in [0, 64]");
     if (t.field_threads != 256 && t.field_threads != 512 && t.field_threads != 1024)
         return fail(HYB_ERR_ARG, "field_threads must be 256, 512 or 1024");
-    if (t.field_cluster != 0 && t.field_cluster != 1 && t.field_cluster != 2 && t.field_cluster != 4 &&
-        t.field_cluster != 8 && t.field_cluster != 16)
-        return fail(HYB_ERR_ARG, "field_cluster must be 0, 1, 2, 4, 8 or 16");
+    if (t.field_cluster < 0 || t.field_cluster > 16) return fail(HYB_ERR_ARG, "field_cluster must be in [0, 16]");
     const int eth = t.electron_threads == 0 ? kElectronBlock : t.electron_threads;
     if (eth != 128 && eth != 256 && eth != 512) return fail(HYB_ERR_ARG, "electron_threads must be 0, 128, 256 or 512");
     int rc = flush_pending(b);

@@ -312,6 +312,19 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
 
+        {
+            // the warp's next group of particles into L1 while this one is
+            // pushed (a prefetch holds no registers)
+            const int64_t inx = i0 + 32 * kVec;
+            if (inx + kVec <= wb) {
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(P.c + inx));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(P.o + inx));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(P.vxf + inx));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(P.vyf + inx));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(P.vzf + inx));
+                if (MODE == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(P.id + inx));
+            }
+        }
         unsigned coll = 0u;      // bit k: slot k ionized (handled in the warp pass below)
         uint2 ru[kVec];          // direction draws of the colliding particles
         float ens[kVec];         // kinetic energies (eV) after the push

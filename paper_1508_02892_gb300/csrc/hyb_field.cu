@@ -79,7 +79,7 @@ struct Book {
     unsigned long long n_slots, see0, see1, loss0, pw_loss0, ion_l0, ion_l1, ion_prev0, ion_prev1;
     double gamma_see, gamma_met, flux_met0, flux_met1, pw_acc, pw_target, pw_alpha, v_rf, see_speed, L;
     uint32_t seed_lo, seed_hi;
-    int precision, n_cells;
+    int precision, n_cells, met_on;
     PartBuf P;
 };
 
@@ -620,6 +620,7 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
         bk.seed_hi = K->seed_hi;
         bk.precision = K->precision;
         bk.n_cells = K->n_cells;
+        bk.met_on = K->met_on;
         bk.P = K->buf[K->cur];
     }
     // inputs of the step (every write of these globals comes after at least
@@ -912,51 +913,55 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
     if (cu.rank != 0) return;
 
     // ------------------------------------------- bookkeeping, gamma emission
-    // (the descriptor's values from the prefetch bk, written back here)
+    // (the descriptor's values from the prefetch bk, written back here).  The
+    // two walls' emission counts and the displacement-current term run on
+    // three warps side by side: this part issues FP64 at a low rate per SM
+    // sub-partition, so one thread's dependent FP64 chain is slow.
     __shared__ int s_cnt[2];
     __shared__ unsigned long long s_base;
-    if (t == 0) {
-        K->n_samples = bk.n_samples + 1;
-        const double v_old = red.v_old;
-        double f_in[2];
-        if (kin) {  // the ions removed at each wall this step
-            f_in[0] = (double)(bk.ion_l0 - bk.ion_prev0) * w / dt;
-            f_in[1] = (double)(bk.ion_l1 - bk.ion_prev1) * w / dt;
-            K->ion_loss_prev[0] = bk.ion_l0;
-            K->ion_loss_prev[1] = bk.ion_l1;
+    __shared__ double s_disp;
+    const int64_t step = bk.step + 1;
+    const uint32_t n_step = (uint32_t)step;
+    if ((t & 31) == 0 && t < 64) {
+        // wall t / 32: flux of ions into it, then the electrons that ions and
+        // metastables striking it emit (Sec. II.D)
+        const int wall = t >> 5;
+        double f_in;
+        if (kin) {  // the ions removed at the wall this step
+            const unsigned long long l = wall == 0 ? bk.ion_l0 : bk.ion_l1;
+            f_in = (double)(l - (wall == 0 ? bk.ion_prev0 : bk.ion_prev1)) * w / dt;
+            K->ion_loss_prev[wall] = l;
         } else {
-            const double g0 = gfin[0], gN = red.gN;
-            f_in[0] = g0 < 0.0 ? -g0 : 0.0;
-            f_in[1] = gN > 0.0 ? gN : 0.0;
+            const double g = wall == 0 ? gfin[0] : red.gN;
+            f_in = wall == 0 ? (g < 0.0 ? -g : 0.0) : (g > 0.0 ? g : 0.0);
         }
-        K->flux_in[0] = f_in[0];
-        K->flux_in[1] = f_in[1];
-        const int64_t step = bk.step + 1;
-        K->step = step;
-        const uint32_t n = (uint32_t)step;
-        s_cnt[0] = s_cnt[1] = 0;
+        K->flux_in[wall] = f_in;
+        int cnt = 0;
         if ((bk.gamma_see > 0.0 || bk.gamma_met > 0.0) && w > 0.0) {
-            double f_met[2] = {bk.flux_met0, bk.flux_met1};
-            if (K->met_on) {
-                f_met[0] = K->flux_met[0];
-                f_met[1] = K->flux_met[1];
-            }
-            for (int wall = 0; wall < 2; ++wall) {
-                // ions and metastables striking the wall (Sec. II.D)
-                const double ns = (bk.gamma_see * f_in[wall] + bk.gamma_met * f_met[wall]) * dt / w;
-                if (!(ns > 0.0)) continue;
+            const double f_met = bk.met_on ? K->flux_met[wall] : (wall == 0 ? bk.flux_met0 : bk.flux_met1);
+            const double ns = (bk.gamma_see * f_in + bk.gamma_met * f_met) * dt / w;
+            if (ns > 0.0) {
                 const double k = floor(ns);
                 const double frac = ns - k;
-                const uint4 r = draw(0xFFFFFFFFFFFFFF00ull | (uint64_t)wall, n, bk.seed_lo, bk.seed_hi, 3);
+                const uint4 r = draw(0xFFFFFFFFFFFFFF00ull | (uint64_t)wall, n_step, bk.seed_lo, bk.seed_hi, 3);
                 int64_t c = (int64_t)k + (u01d(r.x) < frac ? 1 : 0);
                 if (c > (1 << 20) - 1) {
                     c = (1 << 20) - 1;
                     atomicOr(&K->status, (unsigned)HYB_STATUS_EMIT_CAP);
                 }
-                s_cnt[wall] = (int)c;
+                cnt = (int)c;
             }
         }
-        const unsigned long long base = K->met_on ? K->n_slots : bk.n_slots;
+        s_cnt[wall] = cnt;
+    } else if (t == 64) {
+        s_disp = kEps0 * (red.E0 - s_E[0]) / dt;
+    } else if (t == 96) {
+        K->n_samples = bk.n_samples + 1;
+        K->step = step;
+    }
+    __syncthreads();
+    if (t == 0) {
+        const unsigned long long base = bk.met_on ? K->n_slots : bk.n_slots;
         s_base = base;
         const unsigned long long tot = (unsigned long long)(s_cnt[0] + s_cnt[1]);
         K->n_slots = base + tot;
@@ -969,8 +974,8 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
         const unsigned long long l0 = bk.loss0;
         const int64_t d_loss0 = (int64_t)(l0 - bk.pw_loss0), d_see0 = s_cnt[0];
         K->pw_loss0 = l0;
-        const double v_mid = 0.5 * (v_old + phi0);
-        const double jz = kQe * gfin[0] + kQe * w * (double)(d_loss0 - d_see0) / dt + kEps0 * (red.E0 - s_E[0]) / dt;
+        const double v_mid = 0.5 * (red.v_old + phi0);
+        const double jz = kQe * gfin[0] + kQe * w * (double)(d_loss0 - d_see0) / dt + s_disp;
         const double acc = bk.pw_acc + v_mid * jz * dt;
         const int64_t cnt = bk.pw_count + 1;
         if (cnt == bk.pw_steps) {
@@ -990,13 +995,13 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
     const int ntot = s_cnt[0] + s_cnt[1];
     if (ntot) {
         const PartBuf P = bk.P;
-        const uint32_t n = (uint32_t)(bk.step + 1);
+        const uint32_t n = n_step;
         const double sp = bk.see_speed, L = bk.L;
         for (int k = t; k < ntot; k += T) {
             const int wall = k < s_cnt[0] ? 0 : 1;
             const uint32_t j = (uint32_t)(wall == 0 ? k : k - s_cnt[0]);
             const uint64_t id = see_id(wall, n, j);
-            const uint4 r = draw(id, n, K->seed_lo, K->seed_hi, 7);
+            const uint4 r = draw(id, n, bk.seed_lo, bk.seed_hi, 7);
             const double ct = sqrt(u01d(r.x));
             const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
             const double phw = kTwoPi * u01d(r.y);
@@ -1091,6 +1096,15 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 3 : 1) k_field(InstD
     // shared memory; the other paths arrive here
     if (!body) cl_arrive();
     cl_wait();
+    if (n_max == 1) {
+        // one instance: the chunk prefix of the next step from what rank 0's
+        // thread 0 itself wrote at the end of the step
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            prefix[0] = 0;
+            prefix[1] = K->active ? chunks_of(K->n_slots_step) : 0;
+        }
+        return;
+    }
     // the last block to finish computes the chunk prefix of the next step
     __shared__ bool s_last;
     __shared__ int64_t s_buf[HYB_MAX_INSTANCES];
@@ -1106,12 +1120,15 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 3 : 1) k_field(InstD
     }
 }
 
-// CTAs per instance's cluster for a launch: about one node per half warp of
-// the CTA's threads (the FP64 work of a CTA grows with its nodes at this
-// part's FP64 rate), at most 16; 1 for small grids
+// CTAs per instance's cluster for a launch: the nodes a CTA computes (its run
+// and kHalo on each side) about one per half warp of its threads, so that with
+// 256 threads each SM sub-partition's FP64 pipe serves one warp of nodes (the
+// FP64 work of a CTA grows with its nodes at this part's FP64 rate); at most
+// 16; 1 for small grids
 int cluster_size(int max_nodes, int threads)
 {
-    const int c = (max_nodes + threads / 2 - 1) / (threads / 2);
+    const int per = threads / 2 - 2 * kHalo;
+    const int c = (max_nodes + per - 1) / per;
     return c < 1 ? 1 : (c > kMaxCluster ? kMaxCluster : c);
 }
 

@@ -97,9 +97,9 @@ def test_fp64_dd_table_ragged_sizes():
     _check_all(g, o, p)
 
 
-@pytest.mark.parametrize("cluster", [1, 2, 8, 16])
+@pytest.mark.parametrize("cluster", [1, 2, 3, 8, 10, 16])
 def test_fp64_field_cluster_sizes(cluster):
-    """The field step split over 1, 2, 8 or 16 CTAs of a cluster gives the oracle's
+    """The field step split over 1, 2, 3, 8, 10 or 16 CTAs of a cluster gives the oracle's
     result to the FP64 tolerances (full fluid with gamma emission and
     ionization, 333 cells: halo exchanges, cluster scans and the wall rows all
     take part; only summation order differs)."""
