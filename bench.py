@@ -301,19 +301,25 @@ def _oracle_rate(p, steps):
     return n / t, n, t
 
 
-def single_config_load(name, p, stream, flush, chunks=3, oracle_particles=200000, oracle_steps=5, tuning=None):
-    """One discharge of a single-instance workload as a one-slot batch (one
-    lane, sort every 100 steps): whole-step particle-steps/s over `chunks`
-    graph chunks (CUDA events), the electron kernel's fraction of the HBM
-    roofline from one profiled chunk, and the oracle on one host core on a
-    bounded sample: the same discharge with `oracle_particles` electrons
-    (weight scaled to keep the density), `oracle_steps` steps."""
+def single_config_load(name, p, stream, flush, chunks=3, oracle_particles=200000, oracle_steps=5, tuning=None,
+                       tune_steps=0):
+    """One discharge of a single-instance workload as a one-slot batch, its
+    launch layout from the library's autotuner (`tune_steps`-step trials on
+    the discharge itself) or fixed (`tuning`; default one lane, sort every
+    100 steps): whole-step particle-steps/s over `chunks` graph chunks (CUDA
+    events), the electron kernel's fraction of the HBM roofline from one
+    profiled chunk, and the oracle on one host core on a bounded sample: the
+    same discharge with `oracle_particles` electrons (weight scaled to keep the
+    density), `oracle_steps` steps."""
     import torch
 
     from paper_1508_02892_gb300 import hybrid
     b = hybrid.Batch(1, p["precision"], stream=stream.cuda_stream)
     s = b.admit(p)
-    b.set_tuning(**dict({"lanes": 1, "sort_interval": 100}, **(tuning or {})))
+    if tune_steps > 0 and not tuning:
+        chosen = b.autotune(tune_steps)
+    else:
+        chosen = b.set_tuning(**dict({"lanes": 1, "sort_interval": 100}, **(tuning or {})))
     b.advance(CHUNK)
     torch.cuda.synchronize()
     c0 = b.counters(s)["pushes"]
@@ -349,6 +355,7 @@ def single_config_load(name, p, stream, flush, chunks=3, oracle_particles=200000
     q["n_particles"] = oracle_particles
     orate, on, ot = _oracle_rate(q, oracle_steps) if oracle_steps > 0 else (None, 0, 0.0)
     return {"workload": name, "value": n / (ms / 1e3), "unit": "particle-steps/s", "particles": int(p["n_particles"]),
+            "tuning": {k: chosen[k] for k in TUNE_KEYS},
             "cells": int(p["n_cells"]), "steps_timed": chunks * CHUNK, "status": int(status),
             "kernel_ms_per_step": {"electron": prof["ms_electron"] / max(prof["n_electron"], 1),
                                    "field": prof["ms_field"] / max(prof["n_field"], 1)},
@@ -702,10 +709,12 @@ def run_ours(args):
         configs = {"config1_fp64_full": config1_full(stream),
                    "config2": single_config_load("config 2: He 1 mm / 1000 cells, 2e6 electrons, full fluid, "
                                                  "gamma 0.1, FP32 split", W.config2(), stream, flush,
-                                                 oracle_particles=200000, oracle_steps=20),
+                                                 oracle_particles=200000, oracle_steps=20,
+                                                 tune_steps=min(args.tune_steps, 200)),
                    "config5": single_config_load("config 5: Ar 1 mm / 4000 cells, 5e7 electrons, full fluid, "
                                                  "gamma 0.15, dt 1e-13 s, FP32 split", W.config5(), stream, flush,
-                                                 oracle_particles=500000, oracle_steps=20)}
+                                                 oracle_particles=500000, oracle_steps=20,
+                                                 tune_steps=min(args.tune_steps, 200))}
         accuracy = accuracy_load(params, stream)
 
     swarm = None
@@ -856,8 +865,8 @@ def main():
         if args.field_cluster >= 0:
             tuning["field_cluster"] = args.field_cluster
         out = single_config_load(f"config {args.only_config}", p, stream, flush, chunks=max(args.steps // CHUNK, 1),
-                                 oracle_particles=200000, oracle_steps=0 if args.no_cpu else 20, tuning=tuning)
-        out["tuning"] = tuning
+                                 oracle_particles=200000, oracle_steps=0 if args.no_cpu else 20, tuning=tuning,
+                                 tune_steps=min(args.tune_steps, 200))
         print(json.dumps({f"config{args.only_config}": out}), flush=True)
         return
     if args.only_variants:

@@ -155,12 +155,10 @@ __device__ __forceinline__ void append_ion(InstDev *K, bool has, int c, float o,
 // ------------------------------------------------------------ FP32 split
 //
 // Position = (cell c, offset o in [0,1)).  Constants are the f_* copies.
-// Each thread takes kVec consecutive particles (16-byte vector loads and
-// stores), pushes, deposits and collides them one after the other, and keeps
-// a run of CIC weights for one cell in registers; the runs of a warp are merged
-// with shuffles when the warp spans one or two cells (the usual case once the
-// particles are sorted by cell), so a shared-memory atomic serves many
-// particles.
+// Each thread takes kVec consecutive particles (one vector load and store per
+// array), pushes them, deposits them into its warp's row of fixed-point cell
+// sums in shared memory (below) and collides them, the kVec chains side by
+// side.
 
 constexpr int kVec = 2;  // the collision pass below picks between two slots
 
