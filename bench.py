@@ -30,7 +30,8 @@ sys.path.insert(0, ROOT)
 BYTES_SPLIT = 48   # per particle-step: read c,o,v,id (28 B) + write c,o,v (20 B)
 BYTES_FP64 = 72    # read z,v,id (40 B) + write z,v (32 B)
 CHUNK = 100
-TUNE_KEYS = ("lanes", "sort_interval", "blocks_per_sm", "field_threads", "field_cluster", "electron_threads")
+TUNE_KEYS = ("lanes", "sort_interval", "blocks_per_sm", "field_threads", "field_cluster", "electron_threads",
+             "particles_per_thread")
 METRIC = "electron particle-steps/s, FP32-batched vs FP64 plain, 1 GB300; p50/p99 latency"
 
 
@@ -609,6 +610,8 @@ def run_ours(args):
             fixed["field_cluster"] = args.field_cluster
         if args.electron_threads > 0:
             fixed["electron_threads"] = args.electron_threads
+        if args.particles_per_thread > 0:
+            fixed["particles_per_thread"] = args.particles_per_thread
         tuning = b.set_tuning(**fixed)
     elif args.tune_steps > 0:
         tuning = b.autotune(args.tune_steps)
@@ -811,6 +814,7 @@ def main():
     ap.add_argument("--sort-interval", type=int, default=0, help="with --lanes: fixed sort interval")
     ap.add_argument("--field-cluster", type=int, default=-1, help="with --lanes: fixed field cluster size (0: auto)")
     ap.add_argument("--electron-threads", type=int, default=0, help="with --lanes: electron block size (128/256/512)")
+    ap.add_argument("--particles-per-thread", type=int, default=0, help="with --lanes: electron particles per thread (2/4)")
     ap.add_argument("--serve-requests", type=int, default=1000, help="config-4 serving requests (0: none)")
     ap.add_argument("--serve-saturated", type=int, default=300,
                     help="requests of a second serving run at 200/s (queue kept full; 0: none)")
@@ -864,6 +868,10 @@ def main():
             tuning["sort_interval"] = args.sort_interval
         if args.field_cluster >= 0:
             tuning["field_cluster"] = args.field_cluster
+        if args.electron_threads > 0:
+            tuning["electron_threads"] = args.electron_threads
+        if args.particles_per_thread > 0:
+            tuning["particles_per_thread"] = args.particles_per_thread
         out = single_config_load(f"config {args.only_config}", p, stream, flush, chunks=max(args.steps // CHUNK, 1),
                                  oracle_particles=200000, oracle_steps=0 if args.no_cpu else 20, tuning=tuning,
                                  tune_steps=min(args.tune_steps, 200))

@@ -361,7 +361,10 @@ int hyb_batch_profile(hyb_batch *b, hyb_profile *out, int32_t reset);
  *                  many as let every instance's cluster be resident at once;
  *   electron_threads  threads of an electron-kernel block in split mode: 128,
  *                  256 or 512 (0 or 256: default); the FP64 path and the
- *                  variants with reactions or ion births keep 256.
+ *                  variants with reactions or ion births keep 256;
+ *   particles_per_thread  consecutive particles each electron thread takes in
+ *                  split mode: 2 or 4 (0 or 2: default); the same variants
+ *                  keep 2.
  * rate is filled by hyb_batch_autotune with the particle-steps/s it measured
  * for the returned choice, and is ignored by hyb_batch_set_tuning. */
 typedef struct hyb_tuning {
@@ -371,6 +374,7 @@ typedef struct hyb_tuning {
     int32_t field_threads;
     int32_t field_cluster;
     int32_t electron_threads;
+    int32_t particles_per_thread;
     double rate;
 } hyb_tuning;
 

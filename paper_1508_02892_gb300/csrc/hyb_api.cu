@@ -547,6 +547,7 @@ struct hyb_batch {
     int field_threads = 256;               // threads of each CTA of an instance's field step
     int field_cluster = 0;                 // CTAs per instance's field step (0: from the largest grid)
     int electron_threads = 256;            // threads of the default split-mode electron block
+    int electron_ppt = 2;                  // particles per thread of the default split-mode electron step
     bool any_chem = false;                 // some admitted discharge has recombination or metastables
     bool any_kin = false;                  // some admitted discharge has kinetic ions
     bool field_split = false;              // FP64 batch whose field step takes the split-mode arithmetic
@@ -635,16 +636,25 @@ int electron_threads_of(const hyb_batch *b)
     return (b->precision != HYB_FP32_SPLIT || b->any_chem || b->any_kin) ? kElectronBlock : b->electron_threads;
 }
 
+// particles per electron thread: the tuning's for the default split step, 2
+// for the others
+int electron_ppt_of(const hyb_batch *b)
+{
+    return (b->precision != HYB_FP32_SPLIT || b->any_chem || b->any_kin) ? 2 : b->electron_ppt;
+}
+
 // electron launch shape (block, shared memory, grid) for the current grids,
 // EEDF and block size
 int reconfigure(hyb_batch *b)
 {
     const int th = electron_threads_of(b);
+    const int ppt = electron_ppt_of(b);
     b->cfg.block = th;
+    b->cfg.ppt = ppt;
     // the deposit pass at admission and the reaction variants run 256-thread
     // blocks with this shared memory: room for at least 256 threads' rows
     b->cfg.smem = electron_smem_bytes(b->precision, b->max_nodes, b->max_bins, std::max(th, kElectronBlock));
-    int per_sm = electron_blocks_per_sm(b->precision, b->cfg.smem, th);
+    int per_sm = electron_blocks_per_sm(b->precision, b->cfg.smem, th, ppt);
     if (per_sm < 1) return fail(HYB_ERR_ARG, "grid too large for the electron kernel's shared memory");
     b->occ_per_sm = per_sm;
     b->cfg.grid = b->num_sms * (b->blocks_per_sm > 0 ? b->blocks_per_sm : per_sm);
@@ -1179,6 +1189,8 @@ int set_tuning(hyb_batch *b, const hyb_tuning &t)
     if (t.field_cluster < 0 || t.field_cluster > 16) return fail(HYB_ERR_ARG, "field_cluster must be in [0, 16]");
     const int eth = t.electron_threads == 0 ? kElectronBlock : t.electron_threads;
     if (eth != 128 && eth != 256 && eth != 512) return fail(HYB_ERR_ARG, "electron_threads must be 0, 128, 256 or 512");
+    const int ppt = t.particles_per_thread == 0 ? 2 : t.particles_per_thread;
+    if (ppt != 2 && ppt != 4) return fail(HYB_ERR_ARG, "particles_per_thread must be 0, 2 or 4");
     int rc = flush_pending(b);
     if (rc) return rc;
     if (t.lanes != b->lanes && (rc = set_lanes(b, t.lanes))) return rc;
@@ -1195,8 +1207,9 @@ int set_tuning(hyb_batch *b, const hyb_tuning &t)
         if ((rc = drop_graph(b))) return rc;
         b->field_cluster = t.field_cluster;
     }
-    if (eth != b->electron_threads) {
+    if (eth != b->electron_threads || ppt != b->electron_ppt) {
         b->electron_threads = eth;
+        b->electron_ppt = ppt;
         if (b->max_nodes > 0 && (rc = reconfigure(b))) return rc;
     }
     if (t.blocks_per_sm != b->blocks_per_sm) {
@@ -1216,6 +1229,7 @@ hyb_tuning get_tuning(const hyb_batch *b)
     t.field_threads = b->field_threads;
     t.field_cluster = b->field_cluster;
     t.electron_threads = b->electron_threads;
+    t.particles_per_thread = b->electron_ppt;
     t.rate = 0.0;
     return t;
 }
@@ -1303,14 +1317,18 @@ int autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *out)
         trial(t);
     }
     if (b->precision == HYB_FP32_SPLIT && !b->any_chem && !b->any_kin) {
+        // the default split step's block size and particles per thread
         const hyb_tuning after_cluster = best;
         const int thread_opts[3] = {128, 256, 512};
-        for (int th : thread_opts) {
-            if (th == after_cluster.electron_threads) continue;
-            hyb_tuning t = after_cluster;
-            t.electron_threads = th;
-            trial(t);
-        }
+        const int ppt_opts[2] = {2, 4};
+        for (int th : thread_opts)
+            for (int v : ppt_opts) {
+                if (th == after_cluster.electron_threads && v == after_cluster.particles_per_thread) continue;
+                hyb_tuning t = after_cluster;
+                t.electron_threads = th;
+                t.particles_per_thread = v;
+                trial(t);
+            }
     }
     // the lane count once more, with everything else as chosen (how well the
     // lanes overlap depends on the block sizes)

@@ -155,12 +155,12 @@ __device__ __forceinline__ void append_ion(InstDev *K, bool has, int c, float o,
 // ------------------------------------------------------------ FP32 split
 //
 // Position = (cell c, offset o in [0,1)).  Constants are the f_* copies.
-// Each thread takes kVec consecutive particles (one vector load and store per
-// array), pushes them, deposits them into its warp's row of fixed-point cell
-// sums in shared memory (below) and collides them, the kVec chains side by
-// side.
+// Each thread takes V consecutive particles (V = 2 or 4, a tuning choice; one
+// vector load and store per array), pushes them, deposits them into its
+// warp's row of fixed-point cell sums in shared memory (below) and collides
+// them, the V chains side by side.
 
-constexpr int kVec = 2;  // the collision pass below picks between two slots
+constexpr int kVec = 2;  // particles per thread of the default step
 
 // Per-warp deposit rows in shared memory: for kWin cells starting at `base`,
 // 32-bit fixed-point sums of the particle count, the CIC weight to the upper
@@ -170,10 +170,53 @@ constexpr int kVec = 2;  // the collision pass below picks between two slots
 // kFlushIters iterations (which bounds the fixed-point range), when the warp
 // moves past the row, and at the end of the segment.
 constexpr int kWin = 64;
-constexpr int kFlushIters = 16;        // <= 16 * 32 * kVec = 1024 particles per cell between flushes
+constexpr int kFlushParticles = 1024;  // a warp flushes its row after this many particles per lane group
 constexpr float kFixW = 1048576.0f;    // 2^20: CIC weight, 1024 x 2^20 = 2^30
 constexpr float kFixE = 1024.0f;       // 2^10: weight x energy (eV), 1024 x 2047 x 2^10 < 2^31
 constexpr float kMaxFixE = 2047.0f;
+
+// a[k] and a[k] = v for a run-time k of a register array (selects, no local
+// memory)
+template <typename T, int N>
+__device__ __forceinline__ T pick(const T (&a)[N], int k)
+{
+    T r = a[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j) r = k == j ? a[j] : r;
+    return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ void put(T (&a)[N], int k, T v)
+{
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        if (k == j) a[j] = v;
+}
+
+// V consecutive 4-byte values as one vector access (V = 2: 8 bytes, 4: 16)
+template <int V, typename T>
+__device__ __forceinline__ void load_vec(const T *p, T (&out)[V])
+{
+    static_assert(sizeof(T) == 4 && (V == 2 || V == 4), "4-byte values, 2 or 4 of them");
+    if constexpr (V == 2) {
+        const uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
+        out[0] = __builtin_bit_cast(T, u.x), out[1] = __builtin_bit_cast(T, u.y);
+    } else {
+        const uint4 u = __ldcs(reinterpret_cast<const uint4 *>(p));
+        out[0] = __builtin_bit_cast(T, u.x), out[1] = __builtin_bit_cast(T, u.y);
+        out[2] = __builtin_bit_cast(T, u.z), out[3] = __builtin_bit_cast(T, u.w);
+    }
+}
+template <int V, typename T>
+__device__ __forceinline__ void store_vec(T *p, const T (&v)[V])
+{
+    if constexpr (V == 2) {
+        __stcs(reinterpret_cast<uint2 *>(p), make_uint2(__builtin_bit_cast(uint32_t, v[0]), __builtin_bit_cast(uint32_t, v[1])));
+    } else {
+        __stcs(reinterpret_cast<uint4 *>(p), make_uint4(__builtin_bit_cast(uint32_t, v[0]), __builtin_bit_cast(uint32_t, v[1]),
+                                                        __builtin_bit_cast(uint32_t, v[2]), __builtin_bit_cast(uint32_t, v[3])));
+    }
+}
 
 struct WarpRow {
     unsigned n[kWin], a1[kWin], e0[kWin], e1[kWin];
@@ -227,9 +270,11 @@ __device__ __forceinline__ void row_deposit(WarpRow &row, int &base, InstDev *K,
     atomicAdd(&row.e1[j], __float2uint_rn(o * en * kFixE));
 }
 
-template <int MODE, bool CHEM, bool KIN>
+template <int MODE, bool CHEM, bool KIN, int V = kVec>
 __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *smem, PackedCounters &cnt)
 {
+    static_assert(V == 2 || V == 4, "2 or 4 particles per thread");
+    constexpr int kFlushIters = kFlushParticles / (32 * V);
     const int nc = K->n_cells;
     const int G = K->G;
     const int nb = K->eedf_bins;
@@ -249,7 +294,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     // shared memory: EEDF histogram, then one deposit row per warp
     unsigned *s_eedf = reinterpret_cast<unsigned *>(smem);
     WarpRow *rows = reinterpret_cast<WarpRow *>(smem + 4 * (((nb + 2) + 3) & ~3));
-    if (!HYB_CHECK(b <= capacity && a >= 0 && (a & (kVec - 1)) == 0, 10, b, capacity)) b = a;
+    if (!HYB_CHECK(b <= capacity && a >= 0 && (a & (V - 1)) == 0, 10, b, capacity)) b = a;
     {
         // the histogram and one deposit row per warp must fit in the launch's
         // dynamic shared memory
@@ -265,41 +310,39 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     }
     __syncthreads();
 
-    // each warp sweeps a contiguous part of [a, b) in groups of 32 * kVec
+    // each warp sweeps a contiguous part of [a, b) in groups of 32 * V
     const int nwarps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t per = (((b - a) + nwarps - 1) / nwarps + 32 * kVec - 1) / (32 * kVec) * (32 * kVec);
+    const int64_t per = (((b - a) + nwarps - 1) / nwarps + 32 * V - 1) / (32 * V) * (32 * V);
     const int64_t wa = a + per * wid;
     const int64_t wb = wa + per < b ? wa + per : b;
     WarpRow &row = rows[wid];
     int rbase = INT32_MIN / 2;
     int iter = 0;
-    for (int64_t base = wa; base < wb; base += 32 * kVec) {
-        const int64_t i0 = base + (int64_t)lane * kVec;
-        const bool full = i0 + kVec <= wb;
-        int cc[kVec];
-        float oo[kVec], vx[kVec], vy[kVec], vz[kVec];
-        uint64_t ids[kVec];
+    for (int64_t base = wa; base < wb; base += 32 * V) {
+        const int64_t i0 = base + (int64_t)lane * V;
+        const bool full = i0 + V <= wb;
+        int cc[V];
+        float oo[V], vx[V], vy[V], vz[V];
+        uint64_t ids[V];
         if (full) {
             // streaming (evict-first) loads and stores: the particle state is
             // touched once per step and should not displace the field, the
             // cross-section table or the deposit rows in L1 and L2
-            const int2 c2 = __ldcs(reinterpret_cast<const int2 *>(P.c + i0));
-            const float2 o2 = __ldcs(reinterpret_cast<const float2 *>(P.o + i0));
-            const float2 x2 = __ldcs(reinterpret_cast<const float2 *>(P.vxf + i0));
-            const float2 y2 = __ldcs(reinterpret_cast<const float2 *>(P.vyf + i0));
-            const float2 z2 = __ldcs(reinterpret_cast<const float2 *>(P.vzf + i0));
-            cc[0] = c2.x, cc[1] = c2.y;
-            oo[0] = o2.x, oo[1] = o2.y;
-            vx[0] = x2.x, vx[1] = x2.y;
-            vy[0] = y2.x, vy[1] = y2.y;
-            vz[0] = z2.x, vz[1] = z2.y;
+            load_vec<V>(P.c + i0, cc);
+            load_vec<V>(P.o + i0, oo);
+            load_vec<V>(P.vxf + i0, vx);
+            load_vec<V>(P.vyf + i0, vy);
+            load_vec<V>(P.vzf + i0, vz);
             if (MODE == 0) {
-                const ulonglong2 d0 = __ldcs(reinterpret_cast<const ulonglong2 *>(P.id + i0));
-                ids[0] = d0.x, ids[1] = d0.y;
+#pragma unroll
+                for (int k = 0; k < V; k += 2) {
+                    const ulonglong2 d0 = __ldcs(reinterpret_cast<const ulonglong2 *>(P.id + i0 + k));
+                    ids[k] = d0.x, ids[k + 1] = d0.y;
+                }
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < kVec; ++k) {
+            for (int k = 0; k < V; ++k) {
                 const bool in = i0 + k < wb;
                 cc[k] = in ? P.c[i0 + k] : kDeadCell;
                 oo[k] = in ? P.o[i0 + k] : 0.f;
@@ -313,8 +356,8 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
         {
             // the warp's next group of particles into L1 while this one is
             // pushed (a prefetch holds no registers)
-            const int64_t inx = i0 + 32 * kVec;
-            if (inx + kVec <= wb) {
+            const int64_t inx = i0 + 32 * V;
+            if (inx + V <= wb) {
                 asm volatile("prefetch.global.L1 [%0];" ::"l"(P.c + inx));
                 asm volatile("prefetch.global.L1 [%0];" ::"l"(P.o + inx));
                 asm volatile("prefetch.global.L1 [%0];" ::"l"(P.vxf + inx));
@@ -324,11 +367,11 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             }
         }
         unsigned coll = 0u;      // bit k: slot k ionized (handled in the warp pass below)
-        uint2 ru[kVec];          // direction draws of the colliding particles
-        float ens[kVec];         // kinetic energies (eV) after the push
-        bool live[kVec];
+        uint2 ru[V];          // direction draws of the colliding particles
+        float ens[V];         // kinetic energies (eV) after the push
+        bool live[V];
 #pragma unroll
-        for (int k = 0; k < kVec; ++k) {
+        for (int k = 0; k < V; ++k) {
             // leapfrog with the CIC-gathered field (Sec. II.A), formed for every
             // lane and kept for the live ones; the gather index is clamped so
             // that no out-of-range address is formed
@@ -362,13 +405,13 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
         }
         // CIC charge assignment and energy moment, then the EEDF sample
 #pragma unroll
-        for (int k = 0; k < kVec; ++k)
+        for (int k = 0; k < V; ++k)
             row_deposit(row, rbase, K, live[k] ? cc[k] : -1, oo[k], MODE == 0 ? ens[k] : 0.f, G);
         if (MODE == 0) {
             // EEDF sample: bin nb is the overflow (also NaN), bin nb + 1 takes the
             // removed particles and is never read
 #pragma unroll
-            for (int k = 0; k < kVec; ++k) {
+            for (int k = 0; k < V; ++k) {
                 const float en = ens[k];
                 int bin = (int)(en * bin_inv);
                 bin = (bin > nb || bin < 0 || !(en >= 0.f)) ? nb : bin;
@@ -378,14 +421,14 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
         if (MODE == 0) {
             // modified null-collision method: every particle draws R1 < P_max;
             // the process is the first k with R2 nu_max < sum_{i<=k} nu_i.  The
-            // kVec particles' draws are formed together (independent chains).
-            uint4 rk[kVec];
-            draw_n<kVec>(pre, ids, sl, 0u, rk);
-            uint4 rq[kVec] = {};
-            if (CHEM && K->rec_on) draw_n<kVec>(pre, ids, sl, 2u, rq);
+            // V particles' draws are formed together (independent chains).
+            uint4 rk[V];
+            draw_n<V>(pre, ids, sl, 0u, rk);
+            uint4 rq[V] = {};
+            if (CHEM && K->rec_on) draw_n<V>(pre, ids, sl, 2u, rq);
 #pragma unroll
-            for (int k = 0; k < kVec; ++k) {
-                // computed for every lane without branches, so that the kVec
+            for (int k = 0; k < V; ++k) {
+                // computed for every lane without branches, so that the V
                 // chains interleave; only candidates keep their outcome
                 const float en = ens[k];
                 bool cand = cc[k] >= 0 && cc[k] < nc && u01f(rk[k].x) < pmax;
@@ -464,18 +507,18 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             // E - E_iz between the scattered and the ejected electron, both
             // isotropic, the child appended with its ion source (Sec. II.D)
             while (__any_sync(kFull, coll != 0u)) {
-                const int k = (coll & 1u) ? 0 : 1;
+                const int k = coll ? __ffs(coll) - 1 : 0;
                 bool has_child = false;
                 float cvx = 0.f, cvy = 0.f, cvz = 0.f;
                 uint64_t cid = 0;
                 int ck = 0;
                 float ok = 0.f;
                 if (coll) {
-                    const float px = k ? vx[1] : vx[0], py = k ? vy[1] : vy[0], pz = k ? vz[1] : vz[0];
-                    const uint2 rr = k ? ru[1] : ru[0];
-                    const uint64_t pid = k ? ids[1] : ids[0];
-                    ck = k ? cc[1] : cc[0];
-                    ok = k ? oo[1] : oo[0];
+                    const float px = pick(vx, k), py = pick(vy, k), pz = pick(vz, k);
+                    const uint2 rr = pick(ru, k);
+                    const uint64_t pid = pick(ids, k);
+                    ck = pick(cc, k);
+                    ok = pick(oo, k);
                     const float en = half_m_q * (px * px + py * py + pz * pz);
                     const float ct = 1.f - 2.f * u01f(rr.x);
                     const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
@@ -500,11 +543,9 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                         atomicAdd(&K->s_iz[ck], 1.0 - ok);
                         atomicAdd(&K->s_iz[ck + 1], (double)ok);
                     }
-                    if (k) {
-                        vx[1] = sp * (st * cs), vy[1] = sp * (st * sn), vz[1] = sp * ct;
-                    } else {
-                        vx[0] = sp * (st * cs), vy[0] = sp * (st * sn), vz[0] = sp * ct;
-                    }
+                    put(vx, k, sp * (st * cs));
+                    put(vy, k, sp * (st * sn));
+                    put(vz, k, sp * ct);
                 }
                 unsigned ovf = 0;
                 append_children<float>(K, P, capacity, has_child, ck, ok, 0.0, cvx, cvy, cvz, cid, ovf);
@@ -515,14 +556,14 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
         }
         if (MODE == 0) {
             if (full) {
-                __stcs(reinterpret_cast<int2 *>(P.c + i0), make_int2(cc[0], cc[1]));
-                __stcs(reinterpret_cast<float2 *>(P.o + i0), make_float2(oo[0], oo[1]));
-                __stcs(reinterpret_cast<float2 *>(P.vxf + i0), make_float2(vx[0], vx[1]));
-                __stcs(reinterpret_cast<float2 *>(P.vyf + i0), make_float2(vy[0], vy[1]));
-                __stcs(reinterpret_cast<float2 *>(P.vzf + i0), make_float2(vz[0], vz[1]));
+                store_vec<V>(P.c + i0, cc);
+                store_vec<V>(P.o + i0, oo);
+                store_vec<V>(P.vxf + i0, vx);
+                store_vec<V>(P.vyf + i0, vy);
+                store_vec<V>(P.vzf + i0, vz);
             } else {
 #pragma unroll
-                for (int k = 0; k < kVec; ++k) {
+                for (int k = 0; k < V; ++k) {
                     if (i0 + k < wb) {
                         P.c[i0 + k] = cc[k];
                         P.o[i0 + k] = oo[k];
@@ -848,10 +889,18 @@ __device__ void flush_segment(InstDev *K, unsigned char *smem, const SegCounters
     __syncthreads();
 }
 
+// Blocks per SM the register budget is set for: 80 registers a thread with two
+// particles per thread (a third of the file at 256 threads), 128 with four
+constexpr int electron_min_blocks(int prec, int threads, int ppt)
+{
+    return ppt == 4 ? (threads == 128 ? 4 : (threads == 512 ? 1 : 2))
+                    : (threads == 128 ? 6 : (threads == 512 ? 1 : (prec == HYB_FP32_SPLIT ? 3 : 2)));
+}
+
 // THREADS: 256 for every variant; the default split-mode step is also built
-// for 128 and 512 (a tuning choice), the register budget per thread the same
-template <int PREC, int MODE, bool CHEM = false, bool KIN = false, int THREADS = kBlock>
-__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 6 : (THREADS == 512 ? 1 : (PREC == HYB_FP32_SPLIT ? 3 : 2)))
+// for 128 and 512 (a tuning choice), and with four particles per thread (PPT)
+template <int PREC, int MODE, bool CHEM = false, bool KIN = false, int THREADS = kBlock, int PPT = kVec>
+__global__ void __launch_bounds__(THREADS, electron_min_blocks(PREC, THREADS, PPT))
     k_electron(InstDev *__restrict__ insts, int n_max, const int64_t *__restrict__ prefix)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -859,7 +908,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 6 : (THREADS == 512 
         SegCounters cnt;
         if (PREC == HYB_FP32_SPLIT) {
             PackedCounters pc;
-            segment_split<MODE, CHEM, KIN>(K, a, b, smem, pc);
+            segment_split<MODE, CHEM, KIN, PPT>(K, a, b, smem, pc);
             pc.unpack(cnt);
             flush_segment_split<MODE>(K, smem, cnt);
         } else {
@@ -1052,10 +1101,10 @@ __global__ void k_set_active(InstDev *K, int active, int64_t target_step)
     K->target_step = target_step;
 }
 
-template <int PREC, int MODE, bool CHEM = false, bool KIN = false, int THREADS = kBlock>
+template <int PREC, int MODE, bool CHEM = false, bool KIN = false, int THREADS = kBlock, int PPT = kVec>
 cudaError_t launch_k(InstDev *inst, int n_max, const int64_t *prefix, LaunchCfg cfg, cudaStream_t s)
 {
-    k_electron<PREC, MODE, CHEM, KIN, THREADS><<<cfg.grid, THREADS, cfg.smem, s>>>(inst, n_max, prefix);
+    k_electron<PREC, MODE, CHEM, KIN, THREADS, PPT><<<cfg.grid, THREADS, cfg.smem, s>>>(inst, n_max, prefix);
     return cudaGetLastError();
 }
 
@@ -1069,30 +1118,40 @@ void read_checks_electron(unsigned long long out[3])
 
 void configure_kernels()
 {
-    // opt in to the full 227 KB of shared memory per block
-    const int most = 227 * 1024;
-    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_electron<HYB_FP64, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_electron<HYB_FP64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_electron<HYB_FP64, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_electron<HYB_FP64, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_electron<HYB_FP64, 0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0, false, false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         most);
-    cudaFuncSetAttribute(k_electron<HYB_FP32_SPLIT, 0, false, false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         most);
+    // opt in to all the shared memory a block may have
+    allow_max_dynamic_smem(k_electron<HYB_FP32_SPLIT, 0>);
+    allow_max_dynamic_smem(k_electron<HYB_FP32_SPLIT, 1>);
+    allow_max_dynamic_smem(k_electron<HYB_FP64, 0>);
+    allow_max_dynamic_smem(k_electron<HYB_FP64, 1>);
+    allow_max_dynamic_smem(k_electron<HYB_FP32_SPLIT, 0, true>);
+    allow_max_dynamic_smem(k_electron<HYB_FP64, 0, true>);
+    allow_max_dynamic_smem(k_electron<HYB_FP32_SPLIT, 0, false, true>);
+    allow_max_dynamic_smem(k_electron<HYB_FP64, 0, false, true>);
+    allow_max_dynamic_smem(k_electron<HYB_FP32_SPLIT, 0, true, true>);
+    allow_max_dynamic_smem(k_electron<HYB_FP64, 0, true, true>);
+    allow_max_dynamic_smem(k_electron<HYB_FP32_SPLIT, 0, false, false, 128>);
+    allow_max_dynamic_smem(k_electron<HYB_FP32_SPLIT, 0, false, false, 512>);
+    allow_max_dynamic_smem(k_electron<HYB_FP32_SPLIT, 0, false, false, 128, 4>);
+    allow_max_dynamic_smem(k_electron<HYB_FP32_SPLIT, 0, false, false, 256, 4>);
+    allow_max_dynamic_smem(k_electron<HYB_FP32_SPLIT, 0, false, false, 512, 4>);
     configure_ion_kernels();
     configure_field_kernel();
 }
 
-int electron_blocks_per_sm(int precision, size_t smem, int threads)
+int electron_blocks_per_sm(int precision, size_t smem, int threads, int ppt)
 {
     int n = 0;
-    if (precision == HYB_FP32_SPLIT && threads == 128)
+    if (precision == HYB_FP32_SPLIT && ppt == 4) {
+        if (threads == 128)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_electron<HYB_FP32_SPLIT, 0, false, false, 128, 4>, 128,
+                                                          smem);
+        else if (threads == 512)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_electron<HYB_FP32_SPLIT, 0, false, false, 512, 4>, 512,
+                                                          smem);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_electron<HYB_FP32_SPLIT, 0, false, false, 256, 4>, 256,
+                                                          smem);
+    } else if (precision == HYB_FP32_SPLIT && threads == 128)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_electron<HYB_FP32_SPLIT, 0, false, false, 128>, 128, smem);
     else if (precision == HYB_FP32_SPLIT && threads == 512)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_electron<HYB_FP32_SPLIT, 0, false, false, 512>, 512, smem);
@@ -1127,6 +1186,11 @@ cudaError_t launch_electron_step(InstDev *inst, int n_max, const int64_t *prefix
     if (chem)
         return sp ? launch_k<HYB_FP32_SPLIT, 0, true>(inst, n_max, prefix, cfg, s)
                   : launch_k<HYB_FP64, 0, true>(inst, n_max, prefix, cfg, s);
+    if (sp && cfg.ppt == 4) {
+        if (cfg.block == 128) return launch_k<HYB_FP32_SPLIT, 0, false, false, 128, 4>(inst, n_max, prefix, cfg, s);
+        if (cfg.block == 512) return launch_k<HYB_FP32_SPLIT, 0, false, false, 512, 4>(inst, n_max, prefix, cfg, s);
+        return launch_k<HYB_FP32_SPLIT, 0, false, false, 256, 4>(inst, n_max, prefix, cfg, s);
+    }
     if (sp && cfg.block == 128) return launch_k<HYB_FP32_SPLIT, 0, false, false, 128>(inst, n_max, prefix, cfg, s);
     if (sp && cfg.block == 512) return launch_k<HYB_FP32_SPLIT, 0, false, false, 512>(inst, n_max, prefix, cfg, s);
     return sp ? launch_k<HYB_FP32_SPLIT, 0>(inst, n_max, prefix, cfg, s) : launch_k<HYB_FP64, 0>(inst, n_max, prefix, cfg, s);

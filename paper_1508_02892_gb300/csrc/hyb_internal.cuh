@@ -258,9 +258,28 @@ __device__ __forceinline__ void block_chunk_prefix(InstDev *insts, int n_max, in
     if (t < n_max) prefix[t + 1] = s_buf[t];
 }
 
+// Opt a kernel in to all the dynamic shared memory a block may have beside
+// its static shared memory (the opt-in limit counts both)
+template <typename Kern>
+inline void allow_max_dynamic_smem(Kern kernel)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes a;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&a, (const void *)kernel) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)a.sharedSizeBytes) != cudaSuccess)
+        cudaGetLastError();
+}
+
 struct LaunchCfg {
     int grid, block;
     size_t smem;
+    int ppt;  // particles per thread of the default split-mode electron step (2 or 4)
 };
 
 // electron kernels (hyb_electron.cu)
@@ -300,6 +319,6 @@ void set_last_error(const char *msg);
 
 // one-time kernel attributes and occupancy (hyb_electron.cu)
 void configure_kernels();
-int electron_blocks_per_sm(int precision, size_t smem, int threads = 256);
+int electron_blocks_per_sm(int precision, size_t smem, int threads = 256, int ppt = 2);
 
 }  // namespace hyb

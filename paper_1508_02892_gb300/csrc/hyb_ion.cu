@@ -425,11 +425,10 @@ void read_checks_ion(unsigned long long out[3])
 
 void configure_ion_kernels()
 {
-    const int most = 227 * 1024;
-    cudaFuncSetAttribute(k_ion<HYB_FP64, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_ion<HYB_FP64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_ion<HYB_FP32_SPLIT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_ion<HYB_FP32_SPLIT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    allow_max_dynamic_smem(k_ion<HYB_FP64, 0>);
+    allow_max_dynamic_smem(k_ion<HYB_FP64, 1>);
+    allow_max_dynamic_smem(k_ion<HYB_FP32_SPLIT, 0>);
+    allow_max_dynamic_smem(k_ion<HYB_FP32_SPLIT, 1>);
 }
 
 cudaError_t launch_load_ions(InstDev *ion, int64_t n, cudaStream_t s)

@@ -99,7 +99,7 @@ class SwarmResult(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("sort_interval", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("field_threads", C.c_int32), ("field_cluster", C.c_int32), ("electron_threads", C.c_int32),
-                ("rate", C.c_double)]
+                ("particles_per_thread", C.c_int32), ("rate", C.c_double)]
 
 
 EXPORTS = {
@@ -318,7 +318,7 @@ class Discharge:
     def set_tuning(self, **kw):
         """Launch layout of the batch behind this discharge (fields of
         hyb_tuning: lanes, sort_interval, blocks_per_sm, field_threads,
-        field_cluster)."""
+        field_cluster, electron_threads, particles_per_thread)."""
         bh = lib().hyb_discharge_batch(self.h)
         t = Tuning()
         _check(lib().hyb_batch_get_tuning(bh, C.byref(t)))
@@ -506,14 +506,16 @@ class Batch:
         return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
     def set_tuning(self, lanes=None, sort_interval=None, blocks_per_sm=None, field_threads=None,
-                   field_cluster=None, electron_threads=None):
+                   field_cluster=None, electron_threads=None, particles_per_thread=None):
         cur = self.tuning()
         t = Tuning(int(lanes if lanes is not None else cur["lanes"]),
                    int(sort_interval if sort_interval is not None else cur["sort_interval"]),
                    int(blocks_per_sm if blocks_per_sm is not None else cur["blocks_per_sm"]),
                    int(field_threads if field_threads is not None else cur["field_threads"]),
                    int(field_cluster if field_cluster is not None else cur["field_cluster"]),
-                   int(electron_threads if electron_threads is not None else cur["electron_threads"]), 0.0)
+                   int(electron_threads if electron_threads is not None else cur["electron_threads"]),
+                   int(particles_per_thread if particles_per_thread is not None else cur["particles_per_thread"]),
+                   0.0)
         _check(lib().hyb_batch_set_tuning(self.h, C.byref(t)))
         return self.tuning()
 

@@ -97,6 +97,16 @@ def test_fp64_dd_table_ragged_sizes():
     _check_all(g, o, p)
 
 
+def test_fp64_largest_grid_uses_opt_in_shared_memory():
+    """4000 cells (the largest grid of the workloads): the FP64 electron step
+    keeps three FP64 node sums per block in shared memory, 96 KB, beyond the
+    48 KB a block gets without opting in; the opt-in is the block's limit less
+    its static shared memory.  The step still matches the oracle."""
+    p = W.config1(precision=W.FP64, n_particles=6000, n_cells=4000, gap_m=1e-3, te0_ev=6.0, seed=29)
+    g, o = _run_pair(p, 8)
+    _check_all(g, o, p)
+
+
 @pytest.mark.parametrize("cluster", [1, 2, 3, 8, 10, 16])
 def test_fp64_field_cluster_sizes(cluster):
     """The field step split over 1, 2, 3, 8, 10 or 16 CTAs of a cluster gives the oracle's
@@ -296,23 +306,25 @@ def test_batch_matches_single_runs_fp64(lanes, sort_interval, field_threads):
     b.close()
 
 
-@pytest.mark.parametrize("threads", [128, 512])
-def test_split_electron_block_sizes_track_the_default(threads):
-    """The split electron step built for 128 or 512 threads per block takes the
-    same steps as the default 256: the same random numbers, fixed-point
-    deposit rows, only the order of the FP64 flushes differs."""
+@pytest.mark.parametrize("threads,ppt", [(128, 2), (512, 2), (256, 4), (128, 4)])
+def test_split_electron_block_sizes_track_the_default(threads, ppt):
+    """The split electron step built for 128 or 512 threads per block, or with
+    four particles per thread, takes the same steps as the default (256
+    threads, two particles each): the same random numbers, fixed-point deposit
+    rows, only the order of the FP64 flushes differs."""
     from paper_1508_02892_gb300 import hybrid
     p = W.config1(precision=W.FP32_SPLIT, n_particles=30000, seed=71, te0_ev=6.0)
     out = {}
-    for th in (256, threads):
+    for key in ((256, 2), (threads, ppt)):
         b = hybrid.Batch(1, hybrid.HYB_FP32_SPLIT)
-        b.set_tuning(electron_threads=th)
+        b.set_tuning(electron_threads=key[0], particles_per_thread=key[1])
         s = b.admit(p, 200)
         b.advance(200)
-        assert b.tuning()["electron_threads"] == th
-        out[th] = (b.moments(s), b.counters(s))
+        t = b.tuning()
+        assert (t["electron_threads"], t["particles_per_thread"]) == key
+        out[key] = (b.moments(s), b.counters(s))
         b.close()
-    (ma, ca), (mb, cb) = out[256], out[threads]
+    (ma, ca), (mb, cb) = out[(256, 2)], out[(threads, ppt)]
     assert cb["status"] == 0 and cb["step"] == 200
     assert abs(ca["elastic"] - cb["elastic"]) <= 1e-3 * ca["elastic"]
     for k in ("ne", "ebar", "gamma", "eedf"):
@@ -330,6 +342,7 @@ def test_autotune_keeps_a_valid_configuration():
     t = b.autotune(100)
     assert 1 <= t["lanes"] <= 3 and t["sort_interval"] in (10, 20, 50, 100) and t["rate"] > 0
     assert t["field_threads"] in (256, 512, 1024)
+    assert t["electron_threads"] in (128, 256, 512) and t["particles_per_thread"] in (2, 4)
     assert b.tuning()["lanes"] == t["lanes"]
     steps = [b.counters(s)["step"] for s in slots]
     assert min(steps) == max(steps) >= 200
