@@ -128,13 +128,16 @@ __device__ __forceinline__ float ion_nu_f(const InstDev *K, float g)
     return K->fi_ngas * q * g;
 }
 
-// CIC of two values per lane into a shared row: value v_k of the lane's ion k
-// (k = 0, 1; ion k in cell c_k with offset o_k) adds (1 - o_k) v_k to node c_k
-// and o_k v_k to node c_k + 1.  When the warp's live ions lie in one cell or
-// two neighbouring ones (the usual case, ions being sorted by cell) the three
-// touched nodes are summed over the warp and lane 0 adds them; otherwise every
-// lane adds its own.
-__device__ __forceinline__ void deposit_two(float *arr, const bool on[2], const int c[2], const float o[2],
+// CIC of two values per lane into the FP64 global sums: value v_k of the
+// lane's ion k (k = 0, 1; ion k in cell c_k with offset o_k) adds (1 - o_k) v_k
+// to node c_k and o_k v_k to node c_k + 1.  When the warp's live ions lie in
+// one cell or two neighbouring ones (the usual case, ions being sorted by cell
+// and barely moving between sorts) the three touched nodes are summed over the
+// warp in FP32 and lane 0 adds them; otherwise every lane adds its own.  (A
+// block-private FP32 row in shared memory was slower: a shared-memory FP32
+// atomic add is a compare-and-swap loop, and the block's warps, in step over
+// neighbouring ions, contended on the same nodes.)
+__device__ __forceinline__ void deposit_two(double *arr, const bool on[2], const int c[2], const float o[2],
                                             const float v[2], int G)
 {
     bool ok[2];
@@ -163,27 +166,27 @@ __device__ __forceinline__ void deposit_two(float *arr, const bool on[2], const 
         s1 = WarpSum<float>::run(s1);
         if (kmax > kmin) s2 = WarpSum<float>::run(s2);
         if ((threadIdx.x & 31) == 0) {
-            if (s0 != 0.f) atomicAdd(&arr[kmin], s0);
-            if (s1 != 0.f) atomicAdd(&arr[kmin + 1], s1);
-            if (kmax > kmin && s2 != 0.f) atomicAdd(&arr[kmin + 2], s2);
+            if (s0 != 0.f) atomicAdd(&arr[kmin], (double)s0);
+            if (s1 != 0.f) atomicAdd(&arr[kmin + 1], (double)s1);
+            if (kmax > kmin && s2 != 0.f) atomicAdd(&arr[kmin + 2], (double)s2);
         }
     } else {
 #pragma unroll
         for (int k = 0; k < 2; ++k)
             if (ok[k]) {
-                atomicAdd(&arr[c[k]], (1.f - o[k]) * v[k]);
-                atomicAdd(&arr[c[k] + 1], o[k] * v[k]);
+                atomicAdd(&arr[c[k]], (double)((1.f - o[k]) * v[k]));
+                atomicAdd(&arr[c[k] + 1], (double)(o[k] * v[k]));
             }
     }
 }
 
 // split-mode ions [a, b): cell + FP32 offset, FP32 velocities, two ions per
 // thread (8- and 16-byte vector accesses; a is a multiple of the chunk size, so
-// the pair is aligned) whose Philox chains and pushes interleave; the ion
-// density and flux go to block-private FP32 shared rows (summed per warp when
-// the lanes share a cell), flushed into the FP64 global sums
+// the pair is aligned) whose Philox chains and pushes interleave, each warp
+// sweeping its own contiguous part of [a, b); the ion density and flux go to
+// the FP64 global sums (summed per warp when the lanes share a cell)
 template <int MODE>
-__device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned char *smem, unsigned ctr[5])
+__device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned ctr[5])
 {
     InstDev *K = I->elec;
     const int G = K->G, nc = K->n_cells;
@@ -193,15 +196,16 @@ __device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned cha
     const float qm_dt = K->fi_qm_dt, dt_dz = K->f_dt_dz;
     const float numax = K->fi_numax, pmax = K->fi_pmax, vt = K->fi_vt, ca = K->fi_cm_a, cb = K->fi_cm_b;
     const PartBuf P = I->buf[I->cur];
-    float *sd_n = reinterpret_cast<float *>(smem);
-    float *sd_g = sd_n + G;
+    double *dep_n = K->dep_ni, *dep_g = K->dep_gi;
     if (!HYB_CHECK(b <= I->capacity && a >= 0 && (a & 1) == 0, 14, b, I->capacity)) b = a;
-    for (int j = threadIdx.x; j < 2 * G; j += blockDim.x) sd_n[j] = 0.f;
-    __syncthreads();
     const PhiloxPre pre = philox_pre(step, sh);
-    for (int64_t base = a; base < b; base += 2 * (int64_t)blockDim.x) {
-        const int64_t i0 = base + 2 * (int64_t)threadIdx.x;
-        const bool full = i0 + 1 < b;
+    const int nwarps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t per = (((b - a) + nwarps - 1) / nwarps + 63) / 64 * 64;
+    const int64_t wa = a + per * wid;
+    const int64_t wb = wa + per < b ? wa + per : b;
+    for (int64_t base = wa; base < wb; base += 64) {
+        const int64_t i0 = base + 2 * (int64_t)lane;
+        const bool full = i0 + 1 < wb;
         int c[2];
         float o[2], vx[2], vy[2], vz[2];
         uint64_t id[2];
@@ -222,7 +226,7 @@ __device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned cha
         } else {
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const bool in = i0 + k < b;
+                const bool in = i0 + k < wb;
                 c[k] = in ? P.c[i0 + k] : kDeadCell;
                 o[k] = in ? P.o[i0 + k] : 0.f;
                 vx[k] = in ? P.vxf[i0 + k] : 0.f;
@@ -259,8 +263,8 @@ __device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned cha
             }
         }
         const float one[2] = {1.f, 1.f};
-        deposit_two(sd_n, alive, c, o, one, G);
-        deposit_two(sd_g, alive, c, o, vz, G);
+        deposit_two(dep_n, alive, c, o, one, G);
+        deposit_two(dep_g, alive, c, o, vz, G);
         if (MODE == 0) {
             uint4 u[2];
             draw_n<2>(pre, id, sl, 5u, u);
@@ -314,7 +318,7 @@ __device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned cha
             } else {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    if (i0 + k < b) {
+                    if (i0 + k < wb) {
                         P.c[i0 + k] = c[k];
                         P.o[i0 + k] = o[k];
                         P.vxf[i0 + k] = vx[k];
@@ -325,12 +329,6 @@ __device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned cha
             }
         }
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < G; j += blockDim.x) {
-        if (sd_n[j] != 0.f) atomicAdd(&K->dep_ni[j], (double)sd_n[j]);
-        if (sd_g[j] != 0.f) atomicAdd(&K->dep_gi[j], (double)sd_g[j]);
-    }
-    __syncthreads();
 }
 
 template <int PREC, int MODE>
@@ -342,7 +340,7 @@ __global__ void __launch_bounds__(kBlock, PREC == HYB_FP32_SPLIT ? 3 : 2) k_ion(
         unsigned ctr[5] = {0u, 0u, 0u, 0u, 0u};
         if (threadIdx.x < 5) s_c[threadIdx.x] = 0u;
         if (PREC == HYB_FP32_SPLIT)
-            segment_ion_split<MODE>(I, a, b, smem, ctr);
+            segment_ion_split<MODE>(I, a, b, ctr);
         else
             segment_ion_fp64<MODE>(I, a, b, smem, ctr);
 #pragma unroll
@@ -449,12 +447,11 @@ cudaError_t launch_ion_prefix(InstDev *ions, int n_max, int64_t *prefix, cudaStr
 cudaError_t launch_ion_step(InstDev *ions, int n_max, const int64_t *prefix, int mode, int grid, int max_nodes,
                             int precision, cudaStream_t s)
 {
-    if (precision == HYB_FP32_SPLIT) {
-        const size_t smem = 8 * (size_t)max_nodes;
+    if (precision == HYB_FP32_SPLIT) {  // no shared rows: the deposit goes to the global sums
         if (mode == 0)
-            k_ion<HYB_FP32_SPLIT, 0><<<grid, kBlock, smem, s>>>(ions, n_max, prefix);
+            k_ion<HYB_FP32_SPLIT, 0><<<grid, kBlock, 0, s>>>(ions, n_max, prefix);
         else
-            k_ion<HYB_FP32_SPLIT, 1><<<grid, kBlock, smem, s>>>(ions, n_max, prefix);
+            k_ion<HYB_FP32_SPLIT, 1><<<grid, kBlock, 0, s>>>(ions, n_max, prefix);
     } else {
         const size_t smem = 16 * (size_t)max_nodes;
         if (mode == 0)
