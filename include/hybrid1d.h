@@ -305,6 +305,22 @@ int hyb_batch_wait(hyb_batch *b, double timeout_s);
 int hyb_batch_poll_snapshot(hyb_batch *b, int32_t *done, int32_t cap, int32_t *n_done);
 int hyb_batch_read_finished(hyb_batch *b, int32_t slot, hyb_counters *counters, hyb_moments *moments);
 
+/* Moments of running discharges without a host wait on the batch's stream.
+ * hyb_batch_snapshot_moments queues, in stream order after the work queued so
+ * far, a copy of every taken slot's time sums (n_e, n_i, Gamma_i, the
+ * electron-weighted energy), EEDF counts and sample count: one packing kernel
+ * and one device-to-host copy into pinned memory owned by the batch (two
+ * snapshots are kept in turn; queueing a third waits for the copies of the
+ * first, long done in a chunked loop).  hyb_batch_read_snapshot_moments fills
+ * `out` (the layout of hyb_read_moments) for `slot` from the snapshot queued
+ * last, waiting for that snapshot's copy only, not for the work queued after
+ * it; so a loop can queue chunk n + 1 and then read chunk n's moments while
+ * the GPU runs.  Errors: HYB_ERR_ARG; HYB_ERR_STATE when no snapshot was queued
+ * or the slot was empty then, or has been re-admitted since with another grid;
+ * HYB_ERR_CUDA. */
+int hyb_batch_snapshot_moments(hyb_batch *b);
+int hyb_batch_read_snapshot_moments(hyb_batch *b, int32_t slot, hyb_moments *out);
+
 /* Per-slot reads (wait for the GPU first). */
 int hyb_batch_read_moments(hyb_batch *b, int32_t slot, hyb_moments *out);
 int hyb_batch_read_counters(hyb_batch *b, int32_t slot, hyb_counters *out);

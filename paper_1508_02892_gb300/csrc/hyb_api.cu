@@ -583,6 +583,21 @@ struct hyb_batch {
     int64_t snap_issued = 0;            // snapshots ever queued
     int64_t snap_seq[kSnaps] = {};      // sequence number of each ring entry
     cudaStream_t rstream = nullptr;
+    // moments snapshots (hyb_batch_snapshot_moments): every taken slot's time
+    // sums packed by one kernel and copied to pinned memory in stream order,
+    // two entries used in turn
+    struct MomentSnap {
+        int64_t *h_off = nullptr;   // pinned, max_inst + 1 offsets (doubles) into the packed data
+        double *h = nullptr;        // pinned, the packed data
+        size_t cap = 0;             // doubles h holds
+        cudaEvent_t ev = nullptr;
+        bool queued = false;
+    };
+    MomentSnap msnap[2];
+    int msnap_cur = -1;             // the entry last queued
+    int64_t *d_moff = nullptr;      // device copy of the offsets
+    double *d_mpack = nullptr;      // device packed data
+    size_t mpack_cap = 0;
     struct Staging {
         char *p = nullptr;
         size_t n = 0;
@@ -1365,17 +1380,36 @@ int check_slot(hyb_batch *b, int slot)
 }
 
 // time-averaged moments of a discharge with descriptor K, copied on stream s
-int moments_of(const InstDev &K, cudaStream_t s, hyb_moments *out)
+// Pack each slot's time sums (n_e, n_i, Gamma_i, electron weight, weight x
+// energy), its EEDF counts and its sample count into one buffer: slot i's
+// block is out[off[i] .. off[i + 1]), 5 G + nb + 2 doubles (the counts as their
+// bit patterns), or empty for a slot not taken.  A block whose size does not
+// match the slot's descriptor gets a NaN sample count.
+__global__ void k_pack_moments(const InstDev *insts, const int64_t *off, double *out)
 {
+    const int slot = blockIdx.x;
+    const int64_t a = off[slot], n = off[slot + 1] - a;
+    if (n <= 0) return;
+    const InstDev &K = insts[slot];
     const int G = K.G, nb = K.eedf_bins;
-    std::vector<double> acc(5 * (size_t)G);
-    std::vector<unsigned long long> eedf(nb + 1);
-    double *src[5] = {K.acc_ne, K.acc_ni, K.acc_gi, K.acc_wn, K.acc_we};
+    double *o = out + a;
+    if (n != 5 * (int64_t)G + nb + 2) {
+        if (threadIdx.x == 0) o[n - 1] = __longlong_as_double(0x7FF8000000000000ll);
+        return;
+    }
+    const double *src[5] = {K.acc_ne, K.acc_ni, K.acc_gi, K.acc_wn, K.acc_we};
     for (int k = 0; k < 5; ++k)
-        CK(cudaMemcpyAsync(acc.data() + (size_t)k * G, src[k], 8 * (size_t)G, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(eedf.data(), K.eedf, 8 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const int64_t ns = K.n_samples;
+        for (int j = threadIdx.x; j < G; j += blockDim.x) o[(size_t)k * G + j] = src[k][j];
+    for (int j = threadIdx.x; j <= nb; j += blockDim.x) o[5 * (size_t)G + j] = __longlong_as_double((long long)K.eedf[j]);
+    if (threadIdx.x == 0) o[5 * (size_t)G + nb + 1] = __longlong_as_double((long long)K.n_samples);
+}
+
+// The time averages of hyb_read_moments from the time sums acc (5 G: n_e,
+// n_i, Gamma_i, electron weight, weight x energy), the EEDF counts and the
+// sample count
+void moments_from_sums(const double *acc, const unsigned long long *eedf, int64_t ns, int G, int nb, double bin_w,
+                       hyb_moments *out)
+{
     out->n_samples = ns;
     for (int j = 0; j < G; ++j) {
         if (out->ne) out->ne[j] = ns ? acc[j] / ns : 0.0;
@@ -1386,9 +1420,22 @@ int moments_of(const InstDev &K, cudaStream_t s, hyb_moments *out)
     if (out->eedf) {
         double tot = 0.0;
         for (int k = 0; k <= nb; ++k) tot += (double)eedf[k];
-        for (int k = 0; k < nb; ++k) out->eedf[k] = tot > 0 ? (double)eedf[k] / (tot * K.bin_w) : 0.0;
+        for (int k = 0; k < nb; ++k) out->eedf[k] = tot > 0 ? (double)eedf[k] / (tot * bin_w) : 0.0;
         out->eedf[nb] = tot > 0 ? (double)eedf[nb] / tot : 0.0;
     }
+}
+
+int moments_of(const InstDev &K, cudaStream_t s, hyb_moments *out)
+{
+    const int G = K.G, nb = K.eedf_bins;
+    std::vector<double> acc(5 * (size_t)G);
+    std::vector<unsigned long long> eedf(nb + 1);
+    double *src[5] = {K.acc_ne, K.acc_ni, K.acc_gi, K.acc_wn, K.acc_we};
+    for (int k = 0; k < 5; ++k)
+        CK(cudaMemcpyAsync(acc.data() + (size_t)k * G, src[k], 8 * (size_t)G, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(eedf.data(), K.eedf, 8 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    moments_from_sums(acc.data(), eedf.data(), K.n_samples, G, nb, K.bin_w, out);
     return HYB_OK;
 }
 
@@ -1752,6 +1799,76 @@ int hyb_batch_read_finished(hyb_batch *b, int32_t slot, hyb_counters *counters, 
     return status_code(K.status);
 }
 
+int hyb_batch_snapshot_moments(hyb_batch *b)
+{
+    if (!b) return fail(HYB_ERR_ARG, "NULL batch");
+    const int k = (b->msnap_cur + 1) % 2;
+    hyb_batch::MomentSnap &M = b->msnap[k];
+    if (!M.ev) {
+        CK(cudaEventCreateWithFlags(&M.ev, cudaEventDisableTiming));
+        CK(cudaHostAlloc((void **)&M.h_off, sizeof(int64_t) * ((size_t)b->max_inst + 1), cudaHostAllocDefault));
+    }
+    // the entry's previous copies (two snapshots back) are done before its
+    // buffers are written again
+    if (M.queued) CK(cudaEventSynchronize(M.ev));
+    int64_t total = 0;
+    for (int i = 0; i < b->max_inst; ++i) {
+        M.h_off[i] = total;
+        const Slot &S = b->slots[i];
+        if (S.used) total += 5 * (int64_t)S.h.G + S.h.eedf_bins + 2;
+    }
+    M.h_off[b->max_inst] = total;
+    if ((size_t)total > b->mpack_cap) {
+        // a larger packing buffer: wait for the work that may still use the old one
+        CK(cudaStreamSynchronize(b->stream));
+        cudaFree(b->d_mpack);
+        b->d_mpack = nullptr;
+        b->mpack_cap = 0;
+        CK(cudaMalloc((void **)&b->d_mpack, 8 * (size_t)total));
+        b->mpack_cap = (size_t)total;
+    }
+    if (!b->d_moff) CK(cudaMalloc((void **)&b->d_moff, sizeof(int64_t) * ((size_t)b->max_inst + 1)));
+    if ((size_t)total > M.cap) {
+        if (M.h) cudaFreeHost(M.h);
+        M.h = nullptr;
+        M.cap = 0;
+        CK(cudaHostAlloc((void **)&M.h, 8 * (size_t)total, cudaHostAllocDefault));
+        M.cap = (size_t)total;
+    }
+    CK(cudaMemcpyAsync(b->d_moff, M.h_off, sizeof(int64_t) * ((size_t)b->max_inst + 1), cudaMemcpyHostToDevice,
+                       b->stream));
+    if (total > 0) {
+        k_pack_moments<<<b->max_inst, 256, 0, b->stream>>>(b->d_inst, b->d_moff, b->d_mpack);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(M.h, b->d_mpack, 8 * (size_t)total, cudaMemcpyDeviceToHost, b->stream));
+    }
+    CK(cudaEventRecord(M.ev, b->stream));
+    M.queued = true;
+    b->msnap_cur = k;
+    return HYB_OK;
+}
+
+int hyb_batch_read_snapshot_moments(hyb_batch *b, int32_t slot, hyb_moments *out)
+{
+    if (!b || !out) return fail(HYB_ERR_ARG, "NULL argument");
+    if (slot < 0 || slot >= b->max_inst) return fail(HYB_ERR_ARG, "slot %d out of range", slot);
+    if (b->msnap_cur < 0) return fail(HYB_ERR_STATE, "no moments snapshot queued");
+    hyb_batch::MomentSnap &M = b->msnap[b->msnap_cur];
+    const int64_t a = M.h_off[slot], n = M.h_off[slot + 1] - a;
+    if (n <= 0) return fail(HYB_ERR_STATE, "slot %d was empty when the snapshot was queued", slot);
+    CK(cudaEventSynchronize(M.ev));
+    const double *d = M.h + a;
+    const int64_t ns_bits = (int64_t)__builtin_bit_cast(uint64_t, d[n - 1]);
+    const int nb = b->slots[slot].used ? b->slots[slot].h.eedf_bins : -1;
+    const int G = b->slots[slot].used ? b->slots[slot].h.G : -1;
+    if (d[n - 1] != d[n - 1] || nb < 0 || n != 5 * (int64_t)G + nb + 2)
+        return fail(HYB_ERR_STATE, "slot %d changed since the snapshot was queued", slot);
+    std::vector<unsigned long long> eedf(nb + 1);
+    memcpy(eedf.data(), d + 5 * (size_t)G, 8 * (size_t)(nb + 1));
+    moments_from_sums(d, eedf.data(), ns_bits, G, nb, b->slots[slot].h.bin_w, out);
+    return HYB_OK;
+}
+
 int hyb_batch_read_moments(hyb_batch *b, int32_t slot, hyb_moments *out) { return read_moments(b, slot, out); }
 
 int hyb_batch_read_counters(hyb_batch *b, int32_t slot, hyb_counters *out) { return read_counters(b, slot, out); }
@@ -1833,6 +1950,13 @@ int hyb_batch_destroy(hyb_batch *b)
         cudaFreeHost(x.p);
         cudaEventDestroy(x.ev);
     }
+    for (auto &m : b->msnap) {
+        if (m.h_off) cudaFreeHost(m.h_off);
+        if (m.h) cudaFreeHost(m.h);
+        if (m.ev) cudaEventDestroy(m.ev);
+    }
+    cudaFree(b->d_moff);
+    cudaFree(b->d_mpack);
     if (b->rstream) cudaStreamDestroy(b->rstream);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;

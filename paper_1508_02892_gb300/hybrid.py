@@ -146,6 +146,8 @@ EXPORTS = {
     "hyb_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Tuning)]),
     "hyb_discharge_batch": (C.c_void_p, [C.c_void_p]),
     "hyb_batch_set_field_arith": (C.c_int, [C.c_void_p, C.c_int32]),
+    "hyb_batch_snapshot_moments": (C.c_int, [C.c_void_p]),
+    "hyb_batch_read_snapshot_moments": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Moments)]),
     "hyb_swarm_run": (C.c_int, [C.POINTER(SwarmParams), C.c_int32, _pd, C.POINTER(SwarmResult), C.c_void_p,
                                 C.c_void_p]),
     "hyb_swarm_tables": (C.c_int, [C.POINTER(SwarmParams), C.c_int32, _pd, _pd, _pd, C.c_void_p]),
@@ -475,6 +477,17 @@ class Batch:
     def moments(self, slot):
         G, nb, _ = self._shape[slot]
         return _moments(lambda m: lib().hyb_batch_read_moments(self.h, int(slot), m), G, nb)
+
+    def snapshot_moments(self):
+        """Queue a copy of every taken slot's time sums after the work queued
+        so far (no host wait)."""
+        _check(lib().hyb_batch_snapshot_moments(self.h))
+
+    def snapshot_read_moments(self, slot):
+        """Moments of `slot` as of the snapshot queued last (waits for that
+        snapshot's copy only)."""
+        G, nb, _ = self._shape[slot]
+        return _moments(lambda m: lib().hyb_batch_read_snapshot_moments(self.h, int(slot), m), G, nb)
 
     def counters(self, slot):
         return _counters(lambda c: lib().hyb_batch_read_counters(self.h, int(slot), c))

@@ -97,3 +97,36 @@ def test_split_results_same_alone_and_in_the_mix():
             err = np.linalg.norm(r["moments"][k] - mb[k]) / np.linalg.norm(mb[k])
             assert err < 0.02, (r["tag"], k, err)
         g.close()
+
+
+def test_moments_snapshot_reads_while_the_next_chunk_runs():
+    """hyb_batch_snapshot_moments copies every slot's time sums in stream
+    order: read after the next chunk was queued, a snapshot gives exactly the
+    moments a synchronous read gave at the same point, and the next snapshot
+    the later ones; an empty slot and a batch without a snapshot are refused."""
+    from paper_1508_02892_gb300 import hybrid
+    b = hybrid.Batch(4, hybrid.HYB_FP32_SPLIT)
+    ps = [W.config1(precision=W.FP32_SPLIT, n_particles=n, n_cells=c, seed=s)
+          for n, c, s in ((20000, 200, 61), (9000, 97, 62), (15000, 333, 63))]
+    slots = [b.admit(p) for p in ps]
+    with pytest.raises(hybrid.HybError):
+        b.snapshot_read_moments(slots[0])
+    b.advance(100)
+    direct = [b.moments(s) for s in slots]
+    b.snapshot_moments()
+    b.advance(100)                       # queued behind the snapshot
+    for s, d in zip(slots, direct):
+        m = b.snapshot_read_moments(s)
+        assert m["n_samples"] == d["n_samples"]
+        for k in ("ne", "ni", "gamma", "ebar", "eedf"):
+            assert np.array_equal(m[k], d[k]), k
+    b.snapshot_moments()
+    for s in slots:
+        m, d = b.snapshot_read_moments(s), b.moments(s)
+        assert m["n_samples"] == d["n_samples"] == 200
+        for k in ("ne", "ni", "gamma", "ebar", "eedf"):
+            assert np.array_equal(m[k], d[k]), k
+    free = [k for k in range(4) if k not in slots][0]
+    rc = hybrid.lib().hyb_batch_read_snapshot_moments(b.h, free, hybrid.Moments())
+    assert rc == -8, rc  # HYB_ERR_STATE
+    b.close()
