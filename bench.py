@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 BYTES_SPLIT = 48   # per particle-step: read c,o,v,id (28 B) + write c,o,v (20 B)
 BYTES_FP64 = 72    # read z,v,id (40 B) + write z,v (32 B)
 CHUNK = 100
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 TUNE_KEYS = ("lanes", "sort_interval", "blocks_per_sm", "field_threads", "field_cluster", "electron_threads",
              "particles_per_thread")
 METRIC = "electron particle-steps/s, FP32-batched vs FP64 plain, 1 GB300; p50/p99 latency"
@@ -103,9 +104,10 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_push():
-    """DRAM bytes per particle push of the electron kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
+def electron_profile_value(key):
+    """A per-push figure (`dram_bytes_per_push`, `warp_instructions_per_push`)
+    of the electron kernel from the committed ncu summary, if it was taken on
+    the current kernel source."""
     path = os.path.join(ROOT, "profiles", "electron_split_config3_ncu.txt")
     try:
         kv = {}
@@ -116,9 +118,31 @@ def traffic_per_push():
                     kv[k.strip()] = (v.split() or [""])[0]
         if kv.get("kernel_source_sha256_16") != kernel_hash():
             return None
-        return float(kv["dram_bytes_per_push"])
+        return float(kv[key])
     except Exception:
         return None
+
+
+def traffic_per_push():
+    """DRAM bytes per particle push of the electron kernel (committed ncu summary)."""
+    return electron_profile_value("dram_bytes_per_push")
+
+
+def issue_roofline(per_launch, avg_ms, sm_mhz):
+    """The electron kernel against its instruction-issue ceiling: warp
+    instructions per push (committed ncu summary) x pushes per launch / launch
+    time, against every SM sub-partition issuing one warp instruction per cycle
+    at the median SM clock sampled during the timed region."""
+    import torch
+    ipp = electron_profile_value("warp_instructions_per_push")
+    if ipp is None or not sm_mhz:
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = sms * 4 * sm_mhz * 1e6
+    achieved = ipp * per_launch / (avg_ms / 1e3)
+    return {"bound": "alu", "unit": "warp instructions/s", "warp_instructions_per_push": ipp,
+            "achieved": achieved, "peak": peak, "frac": achieved / peak,
+            "peak_note": f"{sms} SMs x 4 sub-partitions x 1 warp instruction per cycle x {sm_mhz:.0f} MHz"}
 
 
 def workload(rank=0, n_inst=64, scale=1.0):
@@ -779,6 +803,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind,
                      "traffic": (tpp * per_launch if tpp is not None else None),
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                     "issue": issue_roofline(per_launch, avg_ms, (clk or {}).get("sm_mhz")),
                      "kernel": "k_electron<FP32_SPLIT>", "bytes_per_unit": BYTES_SPLIT,
                      "units_per_launch": per_launch, "avg_launch_ms": avg_ms,
                      "timed": f"electron kernel alone (1 lane), CUDA events around each launch of "
