@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhybrid1d.so")
-SOURCES = ["hyb_electron.cu", "hyb_ion.cu", "hyb_field.cu", "hyb_api.cu", "hyb_noalloc.cu", "hyb_swarm.cu"]
+SOURCES = ["hyb_electron.cu", "hyb_sort.cu", "hyb_ion.cu", "hyb_field.cu", "hyb_api.cu", "hyb_noalloc.cu",
+           "hyb_swarm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -2033,10 +2033,14 @@ int hyb_batch_set_field_arith(hyb_batch *b, int32_t split)
 int hyb_debug_checks(uint64_t out[6])
 {
     if (!out) return fail(HYB_ERR_ARG, "NULL output");
-    unsigned long long e[3], f[3], g[3];
+    unsigned long long e[3], f[3], g[3], h[3];
     read_checks_electron(e);
+    read_checks_sort(h);
     read_checks_ion(g);
-    if (e[0] == 0 && e[1] == 0 && e[2] == 0)  // the particle kernels: electrons first, then the ions
+    // the particle kernels: electrons first, then the sort, then the ions
+    if (e[0] == 0 && e[1] == 0 && e[2] == 0)
+        for (int k = 0; k < 3; ++k) e[k] = h[k];
+    if (e[0] == 0 && e[1] == 0 && e[2] == 0)
         for (int k = 0; k < 3; ++k) e[k] = g[k];
     read_checks_field(f);
     for (int k = 0; k < 3; ++k) {

@@ -956,129 +956,6 @@ __global__ void k_load(InstDev *K, int64_t n, double vth, int prec)
     }
 }
 
-// --------------------------------------------------------------- cell sort
-// Counting sort by cell every few steps: removes dead slots, folds the
-// appended births in, and restores cell locality for the deposit.
-
-template <int PREC>
-__device__ __forceinline__ bool cell_of(const PartBuf &P, int64_t i, double dz, int nc, int &c)
-{
-    if (PREC == HYB_FP32_SPLIT) {
-        c = P.c[i];
-        return c >= 0;
-    }
-    const double z = P.z[i];
-    if (z < 0.0) return false;
-    double o;
-    locate_d(z, dz, nc, c, o);
-    return true;
-}
-
-template <int PREC, int PHASE>  // PHASE 0: count, 1: scatter
-__global__ void __launch_bounds__(kBlock) k_sort_pass(InstDev *__restrict__ insts, int n_max,
-                                                      const int64_t *__restrict__ prefix)
-{
-    const int lane = threadIdx.x & 31;
-    for_block_runs(insts, n_max, prefix, [&](InstDev *K, int64_t a, int64_t b) {
-        const PartBuf S = K->buf[K->cur];
-        const PartBuf D = K->buf[K->cur ^ 1];
-        if (!HYB_CHECK(b <= K->capacity, 11, b, K->capacity)) return;
-        int32_t *cnt = K->cell_cnt;
-        const double dz = K->dz;
-        const int nc = K->n_cells;
-        for (int64_t base = a; base < b; base += blockDim.x) {
-            const int64_t i = base + threadIdx.x;
-            int c = -1;
-            bool alive = i < b && cell_of<PREC>(S, i, dz, nc, c);
-            if (alive && !HYB_CHECK(c < nc, 7, c, nc)) alive = false;
-            const unsigned act = __ballot_sync(kFull, alive);
-            if (!alive) continue;
-            const unsigned peers = __match_any_sync(act, c);
-            const int leader = __ffs(peers) - 1;
-            int pos = 0;
-            if (lane == leader) pos = atomicAdd(&cnt[c], __popc(peers));
-            if (PHASE == 1) {
-                pos = __shfl_sync(peers, pos, leader) + __popc(peers & lanemask_lt());
-                if (!HYB_CHECK(pos >= 0 && pos < K->capacity, 8, pos, K->capacity)) continue;
-                // streaming (evict-first) accesses: the particle state is read
-                // and written once, and should not displace the tables
-                __stcs(&D.id[pos], __ldcs(&S.id[i]));
-                if (PREC == HYB_FP32_SPLIT) {
-                    __stcs(&D.c[pos], c);
-                    __stcs(&D.o[pos], __ldcs(&S.o[i]));
-                    __stcs(&D.vxf[pos], __ldcs(&S.vxf[i]));
-                    __stcs(&D.vyf[pos], __ldcs(&S.vyf[i]));
-                    __stcs(&D.vzf[pos], __ldcs(&S.vzf[i]));
-                } else {
-                    __stcs(&D.z[pos], __ldcs(&S.z[i]));
-                    __stcs(&D.vxd[pos], __ldcs(&S.vxd[i]));
-                    __stcs(&D.vyd[pos], __ldcs(&S.vyd[i]));
-                    __stcs(&D.vzd[pos], __ldcs(&S.vzd[i]));
-                }
-            }
-        }
-    });
-}
-
-// Exclusive scan of the cell counts, one CTA per sorted instance; the total
-// goes to cell_cnt[n_cells].
-__global__ void __launch_bounds__(1024) k_sort_scan(InstDev *insts, const int64_t *prefix)
-{
-    InstDev *K = &insts[blockIdx.x];
-    if (prefix[blockIdx.x + 1] == prefix[blockIdx.x]) return;
-    int32_t *cnt = K->cell_cnt;
-    const int nc = K->n_cells;
-    __shared__ int32_t s_warp[32];
-    __shared__ int32_t s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int base = 0; base < nc; base += blockDim.x) {
-        const int j = base + threadIdx.x;
-        const int32_t v = j < nc ? cnt[j] : 0;
-        int32_t x = v;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int32_t y = __shfl_up_sync(kFull, x, d);
-            if ((threadIdx.x & 31) >= d) x += y;
-        }
-        if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = x;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            int32_t w = threadIdx.x < (blockDim.x >> 5) ? s_warp[threadIdx.x] : 0;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int32_t y = __shfl_up_sync(kFull, w, d);
-                if ((int)threadIdx.x >= d) w += y;
-            }
-            s_warp[threadIdx.x] = w;
-        }
-        __syncthreads();
-        const int32_t warp_off = (threadIdx.x >> 5) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
-        const int32_t carry = s_carry;
-        if (j < nc) cnt[j] = carry + warp_off + x - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) s_carry = carry + warp_off + x;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) cnt[nc] = s_carry;
-}
-
-// After the scatter: flip the buffers, set the slot counts, clear the counts.
-__global__ void k_sort_finish(InstDev *insts, const int64_t *prefix)
-{
-    InstDev *K = &insts[blockIdx.x];
-    if (prefix[blockIdx.x + 1] == prefix[blockIdx.x]) return;
-    __shared__ int32_t total;
-    if (threadIdx.x == 0) total = K->cell_cnt[K->n_cells];
-    __syncthreads();
-    for (int j = threadIdx.x; j <= K->n_cells; j += blockDim.x) K->cell_cnt[j] = 0;
-    if (threadIdx.x == 0) {
-        K->cur ^= 1;
-        K->n_slots = (unsigned long long)total;
-        K->n_slots_step = total;
-    }
-}
-
 __global__ void __launch_bounds__(HYB_MAX_INSTANCES) k_prefix(InstDev *insts, int n_max, int64_t *prefix)
 {
     __shared__ int64_t s_buf[HYB_MAX_INSTANCES];
@@ -1209,24 +1086,6 @@ cudaError_t launch_load(InstDev *inst, int64_t n, double vth, int precision, cud
     int grid = (int)((n + 255) / 256);
     if (grid > 152 * 16) grid = 152 * 16;
     k_load<<<grid, 256, 0, s>>>(inst, n, vth, precision);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sort(InstDev *inst, int n_max, int64_t *prefix, int precision, LaunchCfg cfg, cudaStream_t s)
-{
-    if (precision == HYB_FP32_SPLIT) {
-        k_sort_pass<HYB_FP32_SPLIT, 0><<<cfg.grid, kBlock, 0, s>>>(inst, n_max, prefix);
-    } else {
-        k_sort_pass<HYB_FP64, 0><<<cfg.grid, kBlock, 0, s>>>(inst, n_max, prefix);
-    }
-    k_sort_scan<<<n_max, 1024, 0, s>>>(inst, prefix);
-    if (precision == HYB_FP32_SPLIT) {
-        k_sort_pass<HYB_FP32_SPLIT, 1><<<cfg.grid, kBlock, 0, s>>>(inst, n_max, prefix);
-    } else {
-        k_sort_pass<HYB_FP64, 1><<<cfg.grid, kBlock, 0, s>>>(inst, n_max, prefix);
-    }
-    k_sort_finish<<<n_max, 256, 0, s>>>(inst, prefix);
-    k_prefix<<<1, HYB_MAX_INSTANCES, 0, s>>>(inst, n_max, prefix);
     return cudaGetLastError();
 }
 

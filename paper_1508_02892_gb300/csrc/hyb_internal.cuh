@@ -312,6 +312,7 @@ void configure_field_kernel();
 
 // first failed self-check of each translation unit (zeros in the normal build)
 void read_checks_electron(unsigned long long out[3]);
+void read_checks_sort(unsigned long long out[3]);
 void read_checks_field(unsigned long long out[3]);
 
 // sets the message hyb_last_error() returns (hyb_api.cu)
