@@ -636,7 +636,14 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
     }
     __syncthreads();
 
-    if (K->met_on && !init) metastable_step<FAST>(K, s_d, s_x, s_ib, red, cu, slots, ph, j0, j1, L0, L1);
+    if (K->met_on && !init) {
+        metastable_step<FAST>(K, s_d, s_x, s_ib, red, cu, slots, ph, j0, j1, L0, L1);
+        // the metastables' ionization adds to the ion source also at the
+        // neighbouring CTAs' edge nodes, which read it in the continuity pass:
+        // a cluster barrier orders those additions before (the drift-diffusion
+        // path has none of its own in between)
+        cl_sync();
+    }
 
     const Fluid F{K->ion_model, K->n_tab, s_tab, K->mu_const, K->ngas, K->kT_gas, K->m_ion, K->m_gas};
     const FluidFast FF{K->ion_model, K->n_tab, s_tab, s_tabf, K->mu_const, K->kT_gas, fk.tfac, fk.inv_ngas_td};

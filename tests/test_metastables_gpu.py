@@ -86,6 +86,22 @@ def test_fp64_metastables_match_the_oracle():
     g.close()
 
 
+def test_fp64_metastables_drift_diffusion_on_eight_ctas():
+    """Drift-diffusion ions (no cluster barrier of their own before the
+    continuity pass) with the field step on 8 CTAs: the metastables'
+    ionization adds to the ion source at neighbouring CTAs' edge nodes, and
+    every addition must be in before the continuity pass reads it."""
+    from paper_1508_02892_gb300 import hybrid
+    p = _params(n_cells=333, seed=79)
+    g, o = hybrid.Discharge(p), oracle.Oracle(p)
+    g.set_tuning(field_cluster=8)
+    g.advance(100)
+    o.step(100)
+    assert o.counters()["births_penning"] > 500
+    _check(g, o, p)
+    g.close()
+
+
 def test_fp64_written_profile_ragged_grid_full_fluid():
     """A metastable profile written through the API on a ragged grid with the
     full ion fluid and a sort every 9 steps."""
