@@ -773,8 +773,12 @@ int launch_step(hyb_batch *b, int k, int lane, cudaStream_t s)
                            b->precision, s));
     }
     if (b->profiling && (rc = record(s, lane_event(b, lane, e + 2)))) return rc;
+    // with one lane the field step may start while the particle kernel's last
+    // blocks finish (with several, the other lanes fill that time and early
+    // field CTAs would hold SMs they need)
+    const bool early = b->lanes == 1 && !b->profiling && !b->any_kin;
     CK(launch_field(lane_inst(b, lane), n, lane_prefix(b, lane), lane_ticket(b, lane), field_fast(b),
-                    b->max_nodes, b->field_threads, s, field_cluster_of(b)));
+                    b->max_nodes, b->field_threads, s, field_cluster_of(b), early));
     if (b->profiling && (rc = record(s, lane_event(b, lane, e + 3)))) return rc;
     return HYB_OK;
 }

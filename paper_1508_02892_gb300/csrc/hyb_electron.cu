@@ -904,6 +904,10 @@ __global__ void __launch_bounds__(THREADS, electron_min_blocks(PREC, THREADS, PP
     k_electron(InstDev *__restrict__ insts, int n_max, const int64_t *__restrict__ prefix)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    // a field step launched to start early may be scheduled once every block
+    // of this grid has started (it waits for this grid's end before reading
+    // any of its results)
+    asm volatile("griddepcontrol.launch_dependents;");
     for_block_runs(insts, n_max, prefix, [&](InstDev *K, int64_t a, int64_t b) {
         SegCounters cnt;
         if (PREC == HYB_FP32_SPLIT) {

@@ -92,6 +92,10 @@ struct Clu {
 };
 
 __device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
+// Wait until the kernel this launch programmatically depends on (the step's
+// particle kernel, when the launch allows an early start) has finished and its
+// writes are visible; returns at once otherwise
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 // the two halves of a cluster barrier, for work between them
 __device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
@@ -586,6 +590,21 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
         red.phi0 = K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)(K->step + (init ? 0 : 1)) * dt));
         red.v_old = (cu.rank == 0 && !init) ? K->v_dc + K->v_rf * sin(kTwoPi * K->f_rf * ((double)K->step * dt)) : 0.0;
     }
+    // inputs of the step (every write of these globals comes after at least
+    // one cluster barrier)
+    if (!kin) {
+        for (int j = L0 + t; j < L1; j += T) {
+            s_ni[j] = K->ni[j];
+            s_E[j] = K->E[j];
+            s_g[j] = K->gam[j];
+        }
+    } else {
+        for (int j = c0 + t; j < c1; j += T) s_E[j] = K->E[j];
+    }
+    // everything above comes from the previous field step or the host; the
+    // electron sums, counters and slot counts below from this step's particle
+    // kernel, which a launch allowed to start early (one lane) waits for here
+    grid_dep_wait();
     if (t == T - 2 && cu.rank == 0 && !init) {
         bk.step = K->step;
         bk.n_samples = K->n_samples;
@@ -622,17 +641,6 @@ __device__ void field_body(InstDev *K, double *sm, int lw, Red &red, const doubl
         bk.n_cells = K->n_cells;
         bk.met_on = K->met_on;
         bk.P = K->buf[K->cur];
-    }
-    // inputs of the step (every write of these globals comes after at least
-    // one cluster barrier)
-    if (!kin) {
-        for (int j = L0 + t; j < L1; j += T) {
-            s_ni[j] = K->ni[j];
-            s_E[j] = K->E[j];
-            s_g[j] = K->gam[j];
-        }
-    } else {
-        for (int j = c0 + t; j < c1; j += T) s_E[j] = K->E[j];
     }
     __syncthreads();
 
@@ -1103,6 +1111,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 3 : 1) k_field(InstD
     // shared memory; the other paths arrive here
     if (!body) cl_arrive();
     cl_wait();
+    grid_dep_wait();  // a CTA without a body still writes the prefix below
     if (n_max == 1) {
         // one instance: the chunk prefix of the next step from what rank 0's
         // thread 0 itself wrote at the end of the step
@@ -1176,7 +1185,7 @@ void configure_field_kernel()
 namespace {
 
 template <bool FAST, int THREADS>
-cudaLaunchConfig_t field_cfg(int n_max, int lw, int csize, cudaStream_t s, cudaLaunchAttribute *at)
+cudaLaunchConfig_t field_cfg(int n_max, int lw, int csize, cudaStream_t s, cudaLaunchAttribute *at, bool early = false)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)csize, (unsigned)n_max, 1);
@@ -1189,6 +1198,13 @@ cudaLaunchConfig_t field_cfg(int n_max, int lw, int csize, cudaStream_t s, cudaL
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    if (early) {
+        // programmatic dependent launch: the CTAs may start while the
+        // preceding particle kernel finishes, and wait in the kernel
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.numAttrs = 2;
+    }
     return cfg;
 }
 
@@ -1215,7 +1231,7 @@ int active_clusters(int lw, int csize)
 
 template <bool FAST, int THREADS>
 cudaError_t launch_cl(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, int max_nodes, int csize,
-                      cudaStream_t s)
+                      cudaStream_t s, bool early)
 {
     if (csize <= 0) {
         // about one node per half warp (at most -csize when csize < 0), but
@@ -1231,18 +1247,18 @@ cudaError_t launch_cl(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticke
     if (csize > kMaxCluster || (size_t)kArrays * 8 * (size_t)array_len(max_nodes, csize) > kMaxDynSmem)
         return cudaErrorInvalidValue;
     const int lw = array_len(max_nodes, csize);
-    cudaLaunchAttribute at[1];
-    const cudaLaunchConfig_t cfg = field_cfg<FAST, THREADS>(n_max, lw, csize, s, at);
+    cudaLaunchAttribute at[2];
+    const cudaLaunchConfig_t cfg = field_cfg<FAST, THREADS>(n_max, lw, csize, s, at, early);
     return cudaLaunchKernelEx(&cfg, k_field<FAST, THREADS>, inst, n_max, prefix, ticket, max_nodes, lw);
 }
 
 template <bool FAST>
 cudaError_t launch_field_t(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, int max_nodes, int threads,
-                           int csize, cudaStream_t s)
+                           int csize, cudaStream_t s, bool early)
 {
-    if (threads == 256) return launch_cl<FAST, 256>(inst, n_max, prefix, ticket, max_nodes, csize, s);
-    if (threads == 512) return launch_cl<FAST, 512>(inst, n_max, prefix, ticket, max_nodes, csize, s);
-    if (threads == 1024) return launch_cl<FAST, 1024>(inst, n_max, prefix, ticket, max_nodes, csize, s);
+    if (threads == 256) return launch_cl<FAST, 256>(inst, n_max, prefix, ticket, max_nodes, csize, s, early);
+    if (threads == 512) return launch_cl<FAST, 512>(inst, n_max, prefix, ticket, max_nodes, csize, s, early);
+    if (threads == 1024) return launch_cl<FAST, 1024>(inst, n_max, prefix, ticket, max_nodes, csize, s, early);
     return cudaErrorInvalidValue;
 }
 
@@ -1254,15 +1270,17 @@ cudaError_t launch_field_t(InstDev *inst, int n_max, int64_t *prefix, unsigned *
 // instance is skipped by the device guard); threads: 256, 512 or 1024 per
 // CTA; csize: CTAs per instance (1..16; raised until the node arrays fit in
 // shared memory), 0 = about one node per half warp, as many as fit in one
-// wave of clusters; -m the same with at most m.
+// wave of clusters; -m the same with at most m.  early: the launch may start
+// while the stream's preceding kernel (the step's particle kernel, which
+// signals it) finishes; the kernel waits for it before reading its results.
 cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned *ticket, bool fast, int max_nodes,
-                         int threads, cudaStream_t s, int csize)
+                         int threads, cudaStream_t s, int csize, bool early)
 {
     if (max_nodes < 3 || max_nodes > kMaxNodes || n_max > HYB_MAX_INSTANCES || n_max > threads ||
         csize > kMaxCluster || csize < -kMaxCluster)
         return cudaErrorInvalidValue;
-    return fast ? launch_field_t<true>(inst, n_max, prefix, ticket, max_nodes, threads, csize, s)
-                : launch_field_t<false>(inst, n_max, prefix, ticket, max_nodes, threads, csize, s);
+    return fast ? launch_field_t<true>(inst, n_max, prefix, ticket, max_nodes, threads, csize, s, early)
+                : launch_field_t<false>(inst, n_max, prefix, ticket, max_nodes, threads, csize, s, early);
 }
 
 }  // namespace hyb

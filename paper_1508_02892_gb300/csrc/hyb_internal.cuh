@@ -306,7 +306,7 @@ size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins, int thre
 
 // field kernel (hyb_field.cu)
 cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned int *ticket, bool fast, int max_nodes,
-                         int threads, cudaStream_t s, int csize = 0);
+                         int threads, cudaStream_t s, int csize = 0, bool early = false);
 size_t field_smem_bytes(int max_nodes, int threads);
 void configure_field_kernel();
 
