@@ -426,7 +426,16 @@ def test_full_size_sampled_step_against_oracle(cfg):
     """Full-size FP32 split discharge in the benchmark's launch configuration:
     a sample of particles is stepped one by one by the FP64 oracle from the
     GPU's pre-step state and field; states agree to FP32 rounding and the
-    collision outcomes agree except for draws within rounding of a threshold."""
+    collision outcomes agree except for draws within rounding of a threshold.
+
+    Bound on the outcome mismatches: both sides take the same uniforms (the
+    23-bit values are exact in FP32 and FP64), so a decision differs only when
+    a threshold computed in FP32 (P_max; the process sums sigma v / nu_max,
+    a few FP32 operations each; the excitation and ionization energies against
+    the FP32 energy; the wall position against the FP32 offset) lies within a
+    few FP32 ulps of the draw or the state: at most about 1e-5 per particle,
+    so 0.03 expected mismatches in 3000 and a chance below 1e-5 of more than
+    two."""
     p = getattr(W, cfg)()
     g = _gpu(p)
     g.advance(20)
@@ -457,7 +466,7 @@ def test_full_size_sampled_step_against_oracle(cfg):
         mism += not ok
         if oc == oracle.OUT_ION:
             mism += cid not in pos
-    assert mism <= 3, mism
+    assert mism <= 2, mism
 
 
 @pytest.mark.parametrize("cfg", ["config2", "config5"])
