@@ -557,7 +557,7 @@ struct hyb_batch {
     int occ_per_sm = 0;
     std::vector<Slot> slots;
     int64_t hbm_cap = 0, hbm_used = 0;
-    int max_nodes = 0, max_bins = 0;
+    int max_nodes = 0, max_bins = 0, max_xs = 0;
     LaunchCfg cfg{};
     int sort_interval = kDefaultSort;
     int since_sort = 0;
@@ -668,7 +668,7 @@ int reconfigure(hyb_batch *b)
     b->cfg.ppt = ppt;
     // the deposit pass at admission and the reaction variants run 256-thread
     // blocks with this shared memory: room for at least 256 threads' rows
-    b->cfg.smem = electron_smem_bytes(b->precision, b->max_nodes, b->max_bins, std::max(th, kElectronBlock));
+    b->cfg.smem = electron_smem_bytes(b->precision, b->max_nodes, b->max_bins, std::max(th, kElectronBlock), b->max_xs);
     int per_sm = electron_blocks_per_sm(b->precision, b->cfg.smem, th, ppt);
     if (per_sm < 1) return fail(HYB_ERR_ARG, "grid too large for the electron kernel's shared memory");
     b->occ_per_sm = per_sm;
@@ -676,11 +676,12 @@ int reconfigure(hyb_batch *b)
     return drop_graph(b);
 }
 
-int configure(hyb_batch *b, int nodes, int bins)
+int configure(hyb_batch *b, int nodes, int bins, int xs)
 {
-    if (nodes <= b->max_nodes && bins <= b->max_bins) return HYB_OK;
+    if (nodes <= b->max_nodes && bins <= b->max_bins && xs <= b->max_xs) return HYB_OK;
     b->max_nodes = std::max(b->max_nodes, nodes);
     b->max_bins = std::max(b->max_bins, bins);
+    b->max_xs = std::max(b->max_xs, xs);
     return reconfigure(b);
 }
 
@@ -1012,7 +1013,7 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     if (b->hbm_cap > 0 && b->hbm_used + (int64_t)L.total > b->hbm_cap)
         return fail(HYB_ERR_OOM, "HBM cap: %lld + %lld > %lld bytes", (long long)b->hbm_used, (long long)L.total,
                     (long long)b->hbm_cap);
-    rc = configure(b, p->n_cells + 1, bins_of(*p) + 1);
+    rc = configure(b, p->n_cells + 1, bins_of(*p) + 1, p->n_xs);
     if (rc) return rc;
 
     Slot &S = b->slots[slot];
@@ -1666,7 +1667,7 @@ int hyb_batch_create(int32_t max_instances, int32_t precision, int64_t hbm_cap_b
     CK(cudaMalloc(&b->d_prefix_ion, sizeof(int64_t) * np));
     CK(cudaMemset(b->d_prefix_ion, 0, sizeof(int64_t) * np));
     CK(cudaMalloc(&b->d_prefix1_ion, sizeof(int64_t) * 2));
-    int rc = configure(b, 3, 2);
+    int rc = configure(b, 3, 2, 2);
     if (rc) return rc;
     rc = set_lanes(b, std::min(kDefaultLanes, max_instances));
     if (rc) return rc;

@@ -282,8 +282,8 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const uint32_t sl = K->seed_lo, sh = K->seed_hi;
     const PartBuf P = K->buf[K->cur];
     const int64_t capacity = K->capacity;
-    const float *__restrict__ Ef = K->Ef;
-    const float4 *__restrict__ xs = K->xsf;
+    const float *__restrict__ gEf = K->Ef;
+    const float4 *__restrict__ gxs = K->xsf;
     const int nxs = K->n_xs;
     const float dt_dz = K->f_dt_dz, qm_dt = K->f_qm_dt, half_m_q = K->f_half_m_q, two_q_m = K->f_two_q_m;
     const float pmax = K->f_pmax, e_lo = K->f_e_lo, e_hi = K->f_e_hi, inv_e_lo = K->f_inv_e_lo;
@@ -291,18 +291,28 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const float bin_inv = K->f_bin_inv;
     const PhiloxPre pre = philox_pre(step, sh);
 
-    // shared memory: EEDF histogram, then one deposit row per warp
+    // shared memory: EEDF histogram, one deposit row per warp, then (full
+    // step) the field at the nodes and the cross-section table
     unsigned *s_eedf = reinterpret_cast<unsigned *>(smem);
     WarpRow *rows = reinterpret_cast<WarpRow *>(smem + 4 * (((nb + 2) + 3) & ~3));
+    float *s_ef = reinterpret_cast<float *>(rows + (blockDim.x >> 5));
+    float4 *s_xs = reinterpret_cast<float4 *>(s_ef + ((G + 3) & ~3));
     if (!HYB_CHECK(b <= capacity && a >= 0 && (a & (V - 1)) == 0, 10, b, capacity)) b = a;
     {
         // the histogram and one deposit row per warp must fit in the launch's
         // dynamic shared memory
         unsigned dyn;
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-        const size_t need = 4 * (size_t)(((nb + 2) + 3) & ~3) + sizeof(WarpRow) * (size_t)(blockDim.x >> 5);
+        const size_t need = 4 * (size_t)(((nb + 2) + 3) & ~3) + sizeof(WarpRow) * (size_t)(blockDim.x >> 5) +
+                            (MODE == 0 ? 4 * (size_t)((G + 3) & ~3) + 16 * (size_t)nxs : 0);
         if (!HYB_CHECK(need <= (size_t)dyn, 13, need, dyn)) return;
     }
+    if (MODE == 0) {
+        for (int j = threadIdx.x; j < G; j += blockDim.x) s_ef[j] = gEf[j];
+        for (int j = threadIdx.x; j < nxs; j += blockDim.x) s_xs[j] = gxs[j];
+    }
+    const float *Ef = s_ef;
+    const float4 *xs = s_xs;
     for (int j = threadIdx.x; j <= nb + 1; j += blockDim.x) s_eedf[j] = 0u;
     {
         unsigned *r = reinterpret_cast<unsigned *>(rows);
@@ -381,7 +391,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             if (MODE == 0) {
                 const int cg = min(max(c, 0), nc - 1);
                 const float oi = alive ? o : 0.f;
-                const float ep = (1.f - oi) * __ldg(&Ef[cg]) + oi * __ldg(&Ef[cg + 1]);
+                const float ep = (1.f - oi) * Ef[cg] + oi * Ef[cg + 1];
                 const float vzn = vz[k] - qm_dt * ep;
                 float on = oi + vzn * dt_dz;
                 const float fl = floorf(on);
@@ -437,8 +447,8 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 // above it the last node's
                 int kk = (int)(__logf(fmaxf(en, e_lo) * inv_e_lo) * inv_dlog);
                 kk = kk < 0 ? 0 : (kk > nxs - 2 ? nxs - 2 : kk);
-                const float4 lo = __ldg(&xs[kk]);
-                const float4 hi = __ldg(&xs[kk + 1]);
+                const float4 lo = xs[kk];
+                const float4 hi = xs[kk + 1];
                 const bool below = en <= e_lo, above = en >= e_hi;
                 const float f = below ? 0.f : __fdividef(en - lo.x, hi.x - lo.x);
                 const float s_el = above ? hi.y : lo.y + f * (hi.y - lo.y);
@@ -1043,10 +1053,11 @@ int electron_blocks_per_sm(int precision, size_t smem, int threads, int ppt)
     return n;
 }
 
-size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins, int threads)
+size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins, int threads, int n_xs)
 {
-    if (precision == HYB_FP32_SPLIT)  // EEDF histogram and one deposit row per warp
-        return 4 * (size_t)(((eedf_bins + 2) + 3) & ~3) + sizeof(WarpRow) * (size_t)(threads / 32) + 16;
+    if (precision == HYB_FP32_SPLIT)  // EEDF histogram, one deposit row per warp, field and table
+        return 4 * (size_t)(((eedf_bins + 2) + 3) & ~3) + sizeof(WarpRow) * (size_t)(threads / 32) +
+               4 * (size_t)((max_nodes + 3) & ~3) + 16 * (size_t)n_xs + 16;
     const size_t el = 8;
     return 3 * el * (size_t)max_nodes + 4 * (size_t)(eedf_bins + 1) + 16;
 }

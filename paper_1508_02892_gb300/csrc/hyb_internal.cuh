@@ -302,7 +302,7 @@ cudaError_t launch_sort(InstDev *inst, int n_max, int64_t *prefix, int precision
 cudaError_t launch_prefix(InstDev *inst, int n_max, int64_t *prefix, cudaStream_t s);
 cudaError_t launch_prefix_one(InstDev *inst, int64_t *prefix, cudaStream_t s);
 cudaError_t launch_set_active(InstDev *inst, int active, int64_t target_step, cudaStream_t s);
-size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins, int threads = 256);
+size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins, int threads = 256, int n_xs = 0);
 
 // field kernel (hyb_field.cu)
 cudaError_t launch_field(InstDev *inst, int n_max, int64_t *prefix, unsigned int *ticket, bool fast, int max_nodes,
