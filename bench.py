@@ -97,11 +97,20 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def source_hash(text):
+    """First 16 hex digits of the sha256 of CUDA source text with its comments
+    and blank space removed (a comment edit leaves the compiled kernel, and so
+    a profile of it, unchanged)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    text = " ".join(text.split())
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
+
+
 def kernel_hash():
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1508_02892_gb300", "csrc", "hyb_electron.cu"), "rb") as f:
-        h.update(f.read())
-    return h.hexdigest()[:16]
+    with open(os.path.join(ROOT, "paper_1508_02892_gb300", "csrc", "hyb_electron.cu")) as f:
+        return source_hash(f.read())
 
 
 def electron_profile_value(key):

@@ -2,14 +2,15 @@
 // (arXiv 1508.02892, Sec. II.A): leapfrog push in the CIC-interpolated field,
 // wall removal, CIC charge assignment with the energy moment and EEDF sample,
 // modified null-collision MCC with ionization births (Sec. II.D), plus the
-// initial load and the periodic counting sort by cell.
+// initial load (the periodic cell sort is in hyb_sort.cu).
 //
 // Work decomposition: the running instances' slot ranges are concatenated and
 // each block takes one contiguous chunk (particles are kept sorted by cell, so
-// a chunk covers a narrow range of cells).  Deposits go to block-private
-// shared-memory arrays (FP32 in split mode, FP64 in FP64 mode), aggregated per
-// warp when all lanes share a cell, and are flushed over the touched node range
-// into the FP64 global sums.
+// a chunk covers a narrow range of cells).  Deposits go to shared memory: in
+// split mode per-warp rows of 32-bit fixed-point sums over a window of cells,
+// flushed into the FP64 global sums; in FP64 mode block-private FP64 arrays,
+// summed over the warp when all lanes share a cell, flushed over the touched
+// node range.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

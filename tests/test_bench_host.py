@@ -34,3 +34,13 @@ def test_oracle_pool_deals_largest_first():
     pool.close()
     assert n == sum(p["n_particles"] for p in params) and t > 0
     assert np.isfinite(t)
+
+
+def test_source_hash_ignores_comments_but_not_code():
+    """The profile-to-source check of the bench survives comment edits only."""
+    import bench
+    a = "int f(int x) {  // one\n    return x + 1; /* two\n lines */\n}\n"
+    b = "int f(int x) {\n  return x + 1;  // other words\n}\n"
+    c = "int f(int x) {\n    return x + 2;\n}\n"
+    assert bench.source_hash(a) == bench.source_hash(b)
+    assert bench.source_hash(a) != bench.source_hash(c)
