@@ -315,8 +315,8 @@ int hyb_batch_read_finished(hyb_batch *b, int32_t slot, hyb_counters *counters, 
  * `out` (the layout of hyb_read_moments) for `slot` from the snapshot queued
  * last, waiting for that snapshot's copy only, not for the work queued after
  * it; so a loop can queue chunk n + 1 and then read chunk n's moments while
- * the GPU runs.  Errors: HYB_ERR_ARG; HYB_ERR_STATE when no snapshot was queued
- * or the slot was empty then, or has been re-admitted since with another grid;
+ * the GPU runs.  Errors: HYB_ERR_ARG; HYB_ERR_STATE when no snapshot was queued,
+ * the slot was empty then, or it has been evicted or re-admitted since;
  * HYB_ERR_CUDA. */
 int hyb_batch_snapshot_moments(hyb_batch *b);
 int hyb_batch_read_snapshot_moments(hyb_batch *b, int32_t slot, hyb_moments *out);

@@ -69,6 +69,7 @@ struct Slot {
     int64_t bytes = 0;
     int64_t target = 0;
     int64_t admit_after = 0;  // snapshots queued before the admission (they do not show it)
+    int64_t admission = 0;    // the batch's admission count when this discharge was admitted
 };
 
 double mass_gas_amu(const hyb_params &p)
@@ -588,6 +589,7 @@ struct hyb_batch {
     // two entries used in turn
     struct MomentSnap {
         int64_t *h_off = nullptr;   // pinned, max_inst + 1 offsets (doubles) into the packed data
+        std::vector<int64_t> who;   // per slot: the admission it held when the snapshot was queued
         double *h = nullptr;        // pinned, the packed data
         size_t cap = 0;             // doubles h holds
         cudaEvent_t ev = nullptr;
@@ -595,6 +597,7 @@ struct hyb_batch {
     };
     MomentSnap msnap[2];
     int msnap_cur = -1;             // the entry last queued
+    int64_t admissions = 0;         // discharges ever admitted
     int64_t *d_moff = nullptr;      // device copy of the offsets
     double *d_mpack = nullptr;      // device packed data
     size_t mpack_cap = 0;
@@ -1132,6 +1135,7 @@ int admit(hyb_batch *b, const hyb_params *p, int64_t n_steps, int *slot_out)
     S.bytes = (int64_t)L.total;
     S.target = S.h.target_step;
     S.admit_after = b->snap_issued;
+    S.admission = ++b->admissions;
     b->hbm_used += S.bytes;
     *slot_out = slot;
     if (S.h.nu_max * S.h.dt > 0.1) {
@@ -1817,10 +1821,14 @@ int hyb_batch_snapshot_moments(hyb_batch *b)
     // buffers are written again
     if (M.queued) CK(cudaEventSynchronize(M.ev));
     int64_t total = 0;
+    M.who.assign((size_t)b->max_inst, 0);
     for (int i = 0; i < b->max_inst; ++i) {
         M.h_off[i] = total;
         const Slot &S = b->slots[i];
-        if (S.used) total += 5 * (int64_t)S.h.G + S.h.eedf_bins + 2;
+        if (S.used) {
+            total += 5 * (int64_t)S.h.G + S.h.eedf_bins + 2;
+            M.who[i] = S.admission;
+        }
     }
     M.h_off[b->max_inst] = total;
     if ((size_t)total > b->mpack_cap) {
@@ -1861,6 +1869,8 @@ int hyb_batch_read_snapshot_moments(hyb_batch *b, int32_t slot, hyb_moments *out
     hyb_batch::MomentSnap &M = b->msnap[b->msnap_cur];
     const int64_t a = M.h_off[slot], n = M.h_off[slot + 1] - a;
     if (n <= 0) return fail(HYB_ERR_STATE, "slot %d was empty when the snapshot was queued", slot);
+    if (!b->slots[slot].used || b->slots[slot].admission != M.who[slot])
+        return fail(HYB_ERR_STATE, "slot %d holds another discharge than when the snapshot was queued", slot);
     CK(cudaEventSynchronize(M.ev));
     const double *d = M.h + a;
     const int64_t ns_bits = (int64_t)__builtin_bit_cast(uint64_t, d[n - 1]);

@@ -129,4 +129,9 @@ def test_moments_snapshot_reads_while_the_next_chunk_runs():
     free = [k for k in range(4) if k not in slots][0]
     rc = hybrid.lib().hyb_batch_read_snapshot_moments(b.h, free, hybrid.Moments())
     assert rc == -8, rc  # HYB_ERR_STATE
+    # the same grid re-admitted into a slot after the snapshot: refused too
+    b.evict(slots[0])
+    again = b.admit(ps[0])
+    rc = hybrid.lib().hyb_batch_read_snapshot_moments(b.h, again, hybrid.Moments())
+    assert rc == -8, rc
     b.close()
