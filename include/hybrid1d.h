@@ -403,10 +403,12 @@ int hyb_batch_set_tuning(hyb_batch *b, const hyb_tuning *t);
  * {10, 20, 50, 100}, then the electron grid at the occupancy limit or twice it,
  * then the field block size in {256, 512, 1024}, then the field cluster in
  * {automatic, 1, 2, 4, 8, 16}, then (split mode, no reaction or ion-birth
- * variant) the electron block size in {128, 256, 512}, then the lanes again.
- * Each trial advances every running discharge by one untimed chunk and then
- * by trial_steps rounded up to whole chunks (100 steps): those are real steps
- * of the runs.  Profiling must be off.  *chosen may be NULL. */
+ * variant) the electron block size in {128, 256, 512} with the particles per
+ * thread in {2, 4}, then the lanes again; finally the three fastest layouts
+ * once more over twice the trial length, the fastest of those kept.  Each
+ * trial advances every running discharge by one untimed chunk and then by
+ * trial_steps rounded up to whole chunks (100 steps): those are real steps of
+ * the runs.  Profiling must be off.  *chosen may be NULL. */
 int hyb_batch_autotune(hyb_batch *b, int32_t trial_steps, hyb_tuning *chosen);
 
 /* The batch behind a single discharge (for profiling and statistics). */
