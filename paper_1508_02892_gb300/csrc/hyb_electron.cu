@@ -293,11 +293,14 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const PhiloxPre pre = philox_pre(step, sh);
 
     // shared memory: EEDF histogram, one deposit row per warp, then (full
-    // step) the field at the nodes and the cross-section table
+    // step) the field at the nodes, the cross-section table and the slopes of
+    // its segments (formed once per block and discharge, so that a lookup is
+    // one multiply-add per process)
     unsigned *s_eedf = reinterpret_cast<unsigned *>(smem);
     WarpRow *rows = reinterpret_cast<WarpRow *>(smem + 4 * (((nb + 2) + 3) & ~3));
     float *s_ef = reinterpret_cast<float *>(rows + (blockDim.x >> 5));
     float4 *s_xs = reinterpret_cast<float4 *>(s_ef + ((G + 3) & ~3));
+    float4 *s_xsl = s_xs + nxs;
     if (!HYB_CHECK(b <= capacity && a >= 0 && (a & (V - 1)) == 0, 10, b, capacity)) b = a;
     {
         // the histogram and one deposit row per warp must fit in the launch's
@@ -305,15 +308,24 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
         unsigned dyn;
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
         const size_t need = 4 * (size_t)(((nb + 2) + 3) & ~3) + sizeof(WarpRow) * (size_t)(blockDim.x >> 5) +
-                            (MODE == 0 ? 4 * (size_t)((G + 3) & ~3) + 16 * (size_t)nxs : 0);
+                            (MODE == 0 ? 4 * (size_t)((G + 3) & ~3) + 32 * (size_t)nxs : 0);
         if (!HYB_CHECK(need <= (size_t)dyn, 13, need, dyn)) return;
     }
     if (MODE == 0) {
         for (int j = threadIdx.x; j < G; j += blockDim.x) s_ef[j] = gEf[j];
-        for (int j = threadIdx.x; j < nxs; j += blockDim.x) s_xs[j] = gxs[j];
+        for (int j = threadIdx.x; j < nxs; j += blockDim.x) {
+            const float4 a = gxs[j];
+            s_xs[j] = a;
+            if (j + 1 < nxs) {
+                const float4 b = gxs[j + 1];
+                const float inv = 1.f / (b.x - a.x);
+                s_xsl[j] = make_float4(0.f, (b.y - a.y) * inv, (b.z - a.z) * inv, (b.w - a.w) * inv);
+            }
+        }
     }
     const float *Ef = s_ef;
     const float4 *xs = s_xs;
+    const float4 *xsl = s_xsl;
     for (int j = threadIdx.x; j <= nb + 1; j += blockDim.x) s_eedf[j] = 0u;
     {
         unsigned *r = reinterpret_cast<unsigned *>(rows);
@@ -448,13 +460,17 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 // above it the last node's
                 int kk = (int)(__logf(fmaxf(en, e_lo) * inv_e_lo) * inv_dlog);
                 kk = kk < 0 ? 0 : (kk > nxs - 2 ? nxs - 2 : kk);
+                // sigma_i(E) = sigma_i(E_k) + (E - E_k) slope_i with E clamped to
+                // the table: below it the first node's values, above the last's
                 const float4 lo = xs[kk];
-                const float4 hi = xs[kk + 1];
+                const float4 slope = xsl[kk];
                 const bool below = en <= e_lo, above = en >= e_hi;
-                const float f = below ? 0.f : __fdividef(en - lo.x, hi.x - lo.x);
-                const float s_el = above ? hi.y : lo.y + f * (hi.y - lo.y);
-                const float s_ex = en < e_exc ? 0.f : (above ? hi.z : lo.z + f * (hi.z - lo.z));
-                const float s_iz = en < e_iz ? 0.f : (above ? hi.w : lo.w + f * (hi.w - lo.w));
+                const float dd = fminf(fmaxf(en, e_lo), e_hi) - lo.x;
+                const float s_el = lo.y + dd * slope.y;
+                const float s_ex = en < e_exc ? 0.f : lo.z + dd * slope.z;
+                const float s_iz = en < e_iz ? 0.f : lo.w + dd * slope.w;
+                const float4 hi = CHEM ? xs[kk + 1] : lo;
+                const float f = (below || !CHEM) ? 0.f : __fdividef(en - lo.x, hi.x - lo.x);
                 if (CHEM && cc[k] >= 0 && cc[k] < nc && u01f(rq[k].x) < K->f_rec_pmax) {
                     // electron-ion recombination (Sec. II.D), in units of nu_rec,max:
                     // R4 < (n_i / max n_i)(sigma_rec / max sigma_rec v) v
@@ -1058,7 +1074,7 @@ size_t electron_smem_bytes(int precision, int max_nodes, int eedf_bins, int thre
 {
     if (precision == HYB_FP32_SPLIT)  // EEDF histogram, one deposit row per warp, field and table
         return 4 * (size_t)(((eedf_bins + 2) + 3) & ~3) + sizeof(WarpRow) * (size_t)(threads / 32) +
-               4 * (size_t)((max_nodes + 3) & ~3) + 16 * (size_t)n_xs + 16;
+               4 * (size_t)((max_nodes + 3) & ~3) + 32 * (size_t)n_xs + 16;
     const size_t el = 8;
     return 3 * el * (size_t)max_nodes + 4 * (size_t)(eedf_bins + 1) + 16;
 }
