@@ -98,7 +98,7 @@ typedef struct hyb_params {
     const double *xs_el;        /* host, elastic cross section (m^2) at xs_ev */
     const double *xs_exc;       /* host, excitation cross section */
     const double *xs_ion;       /* host, ionization cross section */
-    int32_t n_xs;               /* >= 2 */
+    int32_t n_xs;               /* >= 2; at most 4096 in HYB_FP32_SPLIT (staged in shared memory) */
     double e_exc_ev;            /* excitation threshold / energy loss */
     double e_iz_ev;             /* ionization threshold / energy loss */
     uint64_t seed;              /* Philox counter words 1-2 */

@@ -128,6 +128,10 @@ int validate(const hyb_params *p)
     if (p->eedf_bins < 0 || p->eedf_bins > 4096) return fail(HYB_ERR_ARG, "eedf_bins must be in [0, 4096]");
     if (!p->xs_ev || !p->xs_el || !p->xs_exc || !p->xs_ion || p->n_xs < 2)
         return fail(HYB_ERR_ARG, "cross-section tables missing");
+    // the split-mode particle step keeps the table and its segment slopes in
+    // shared memory (32 bytes an entry)
+    if (p->precision == HYB_FP32_SPLIT && p->n_xs > kMaxSplitXs)
+        return fail(HYB_ERR_ARG, "n_xs must be at most %d in split mode", kMaxSplitXs);
     if (!finite_all(p->xs_ev, p->n_xs) || !finite_all(p->xs_el, p->n_xs) || !finite_all(p->xs_exc, p->n_xs) ||
         !finite_all(p->xs_ion, p->n_xs))
         return fail(HYB_ERR_NONFINITE, "non-finite cross-section table entry");

@@ -47,6 +47,10 @@ struct FieldK {
 // d mu/d(E/N), u, nu, d nu/du and two of padding (rows of 64 bytes)
 constexpr int kTabCols = 8;
 
+// Largest cross-section table of a split-mode discharge: the particle step
+// stages it with its segment slopes in shared memory (32 bytes an entry)
+constexpr int kMaxSplitXs = 4096;
+
 // Everything a kernel needs about one discharge.  Lives in device memory; the
 // host writes it at admission and the kernels update the mutable tail.
 struct InstDev {

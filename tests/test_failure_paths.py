@@ -40,6 +40,21 @@ def test_unstable_drift_diffusion_is_refused_at_create(case):
         oracle.Oracle(p)
 
 
+def test_split_mode_cross_section_table_limit():
+    """The split-mode particle step stages the cross-section table in shared
+    memory: a table of more than 4096 entries is refused at create, before any
+    GPU work; the FP64 mode takes it."""
+    from paper_1508_02892_gb300 import build, hybrid
+    build.build()
+    n = 4097
+    ev = np.logspace(-2, 3, n)
+    p = W.config1(precision=W.FP32_SPLIT, n_particles=100, xs_ev=ev, xs_el=np.full(n, 6e-20),
+                  xs_exc=np.zeros(n), xs_ion=np.zeros(n))
+    with pytest.raises(hybrid.HybError) as e:
+        hybrid.Discharge(p)
+    assert e.value.code == -1 and "4096" in str(e.value)  # HYB_ERR_ARG
+
+
 def test_stable_drift_diffusion_is_accepted_by_the_oracle():
     for case in UNSTABLE:
         p = W.config1(precision=W.FP64, n_particles=100, ion_model=UNSTABLE[case]["ion_model"])
