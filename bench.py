@@ -109,8 +109,17 @@ def source_hash(text):
 
 
 def kernel_hash():
-    with open(os.path.join(ROOT, "paper_1508_02892_gb300", "csrc", "hyb_electron.cu")) as f:
-        return source_hash(f.read())
+    """source_hash of what the electron kernel is compiled from: its file, the
+    device headers it includes, and the nvcc flags (without paths)."""
+    sys.path.insert(0, ROOT)
+    from paper_1508_02892_gb300 import build
+    csrc = os.path.join(ROOT, "paper_1508_02892_gb300", "csrc")
+    parts = []
+    for name in ("hyb_electron.cu", "hyb_internal.cuh", "hyb_device.cuh"):
+        with open(os.path.join(csrc, name)) as f:
+            parts.append(f.read())
+    flags = [t for t in build._flags() if not os.path.isabs(t)]
+    return source_hash("\n".join(parts) + "\nnvcc " + " ".join(flags))
 
 
 def electron_profile_value(key):

@@ -101,7 +101,9 @@ typedef struct hyb_params {
     int32_t n_xs;               /* >= 2; at most 4096 in HYB_FP32_SPLIT (staged in shared memory) */
     double e_exc_ev;            /* excitation threshold / energy loss */
     double e_iz_ev;             /* ionization threshold / energy loss */
-    uint64_t seed;              /* Philox counter words 1-2 */
+    uint64_t seed;              /* Philox key: a particle's draws are the blocks at
+                                   counter (step, id_lo, call, id_hi) under key
+                                   (seed_lo, seed_hi) */
     int32_t eedf_bins;          /* 0: 256 */
     double eedf_max_ev;         /* 0: 64 eV */
     int32_t precision;          /* HYB_FP64 or HYB_FP32_SPLIT */
@@ -444,8 +446,9 @@ int hyb_debug_checks(uint64_t out[6]);
  * ensemble mean of v_z over steps n_relax..n_steps-1; mobility = u/E0 and, by
  * Eq. 2.6, nu = e/(M mobility).
  *
- * Random numbers: Philox4x32-10 keyed by the ion id (ion i of field f has id
- * f*n_ions + i), counter (step, seed_lo, seed_hi, call): call 0 = (R1, R2,
+ * Random numbers: Philox4x32-10 under key (seed_lo, seed_hi) at counter
+ * (step, id_lo, call, id_hi) for the ion id (ion i of field f has id
+ * f*n_ions + i): call 0 = (R1, R2,
  * two Box-Muller uniforms), call 1 = (two Box-Muller uniforms, the scattering
  * direction cos and phi); the initial Maxwellian at T_i0 is drawn at step
  * 0xFFFFFFFF. */

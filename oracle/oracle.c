@@ -20,8 +20,10 @@
  *   - boundary rows of Eqs. 2.3/2.4 by half-cell integration with a Dirichlet
  *     wall flux alpha*mu*n*E (Sec. II.C wall condition) at the wall nodes;
  *   - isotropic lab-frame scattering for every process, cold background gas;
- *   - counter-based Philox4x32-10 (Salmon et al., SC'11) keyed by particle id
- *     and step replaces the paper's xorshift128 (Sec. II.A), so that results do
+ *   - counter-based Philox4x32-10 (Salmon et al., SC'11) replaces the paper's
+ *     xorshift128 (Sec. II.A): a particle's draws are the generator's blocks
+ *     at counter (step, id_lo, call, id_hi) under the discharge's seed as key,
+ *     a function of (seed, particle id, step, call) alone, so that results do
  *     not depend on particle order.
  * Beyond the step itself the oracle carries the rest of Secs. II.C-II.D: the
  * auxiliary ion-swarm Monte Carlo (mobility and exchange-frequency tables),
@@ -181,11 +183,12 @@ double orc_u01(uint32_t x)
     return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
-/* The draws of particle `id` at step `step`, call number `call`. */
+/* The draws of particle `id` at step `step`, call number `call`: counter
+ * (step, id_lo, call, id_hi), key (seed_lo, seed_hi). */
 static void draws(const orc_sim *s, uint64_t id, uint32_t step, uint32_t call, double u[4])
 {
-    uint32_t ctr[4] = {step, (uint32_t)s->p.seed, (uint32_t)(s->p.seed >> 32), call};
-    uint32_t key[2] = {(uint32_t)id, (uint32_t)(id >> 32)};
+    uint32_t ctr[4] = {step, (uint32_t)id, call, (uint32_t)(id >> 32)};
+    uint32_t key[2] = {(uint32_t)s->p.seed, (uint32_t)(s->p.seed >> 32)};
     uint32_t r[4];
     orc_philox4x32_10(ctr, key, r);
     for (int i = 0; i < 4; ++i) u[i] = orc_u01(r[i]);
@@ -1526,8 +1529,8 @@ double orc_swarm_nu_bound(double ngas, double m_red, int xs_model, double eps_ma
 
 static void swarm_draws(const orc_swarm_params *p, uint64_t id, uint32_t step, uint32_t call, double u[4])
 {
-    uint32_t ctr[4] = {step, (uint32_t)p->seed, (uint32_t)(p->seed >> 32), call};
-    uint32_t key[2] = {(uint32_t)id, (uint32_t)(id >> 32)};
+    uint32_t ctr[4] = {step, (uint32_t)id, call, (uint32_t)(id >> 32)};
+    uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
     uint32_t r[4];
     orc_philox4x32_10(ctr, key, r);
     for (int i = 0; i < 4; ++i) u[i] = orc_u01(r[i]);

@@ -165,16 +165,23 @@ constexpr int kVec = 2;  // particles per thread of the default step
 
 // Per-warp deposit rows in shared memory: for kWin cells starting at `base`,
 // 32-bit fixed-point sums of the particle count, the CIC weight to the upper
-// node, and the energy moments to both nodes (weight to the lower node = count
-// minus upper weight).  Every particle adds with native integer shared
-// atomics; the warp flushes its row into the FP64 global sums every
-// kFlushIters iterations (which bounds the fixed-point range), when the warp
-// moves past the row, and at the end of the segment.
+// node, the energy moment and its part to the upper node (to the lower node:
+// count minus upper weight, energy minus upper part).  Every particle adds
+// with native integer shared atomics; the warp flushes its row into the FP64
+// global sums every kFlushIters iterations (which bounds the fixed-point
+// range), when the warp moves past the row, and at the end of the segment.
+// A fixed-point value v (0 <= v < 2^22) is formed without a conversion: one
+// fused multiply-add gives the float v + 1.5 x 2^23, rounded to the nearest
+// integer because floats in [2^23, 2^24) are spaced by 1, and its bits,
+// 0x4B400000 + v, are what is added; the flush takes n x 0x4B400000 (mod
+// 2^32) off each sum of n such adds.
 constexpr int kWin = 64;
 constexpr int kFlushParticles = 1024;  // a warp flushes its row after this many particles per lane group
 constexpr float kFixW = 1048576.0f;    // 2^20: CIC weight, 1024 x 2^20 = 2^30
 constexpr float kFixE = 1024.0f;       // 2^10: weight x energy (eV), 1024 x 2047 x 2^10 < 2^31
 constexpr float kMaxFixE = 2047.0f;
+constexpr float kFixBias = 12582912.0f;       // 1.5 x 2^23
+constexpr unsigned kFixBiasBits = 0x4B400000u;  // its bit pattern
 
 // a[k] and a[k] = v for a run-time k of a register array (selects, no local
 // memory)
@@ -220,7 +227,7 @@ __device__ __forceinline__ void store_vec(T *p, const T (&v)[V])
 }
 
 struct WarpRow {
-    unsigned n[kWin], a1[kWin], e0[kWin], e1[kWin];
+    unsigned n[kWin], a1[kWin], e[kWin], e1[kWin];
 };
 
 __device__ __forceinline__ void add_global(InstDev *K, int c, double w0, double w1, double e0, double e1, int G)
@@ -239,10 +246,12 @@ __device__ __forceinline__ void row_flush(WarpRow &row, int base, InstDev *K, in
     for (int j = threadIdx.x & 31; j < kWin; j += 32) {
         const unsigned n = row.n[j];
         if (n) {
-            const double a1 = (double)row.a1[j] * (1.0 / kFixW);
-            add_global(K, base + j, (double)n - a1, a1, (double)row.e0[j] * (1.0 / kFixE),
-                       (double)row.e1[j] * (1.0 / kFixE), G);
-            row.n[j] = row.a1[j] = row.e0[j] = row.e1[j] = 0u;
+            const unsigned bias = n * kFixBiasBits;
+            const unsigned a1i = row.a1[j] - bias, ei = row.e[j] - bias, e1i = row.e1[j] - bias;
+            const double a1 = (double)a1i * (1.0 / kFixW);
+            add_global(K, base + j, (double)n - a1, a1, (double)(ei - e1i) * (1.0 / kFixE),
+                       (double)e1i * (1.0 / kFixE), G);
+            row.n[j] = row.a1[j] = row.e[j] = row.e1[j] = 0u;
         }
     }
     __syncwarp();
@@ -266,9 +275,9 @@ __device__ __forceinline__ void row_deposit(WarpRow &row, int &base, InstDev *K,
         return;
     }
     atomicAdd(&row.n[j], 1u);
-    atomicAdd(&row.a1[j], __float2uint_rn(o * kFixW));
-    atomicAdd(&row.e0[j], __float2uint_rn((1.f - o) * en * kFixE));
-    atomicAdd(&row.e1[j], __float2uint_rn(o * en * kFixE));
+    atomicAdd(&row.a1[j], __float_as_uint(fmaf(o, kFixW, kFixBias)));
+    atomicAdd(&row.e[j], __float_as_uint(fmaf(en, kFixE, kFixBias)));
+    atomicAdd(&row.e1[j], __float_as_uint(fmaf(o * en, kFixE, kFixBias)));
 }
 
 template <int MODE, bool CHEM, bool KIN, int V = kVec>
@@ -290,7 +299,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const float pmax = K->f_pmax, e_lo = K->f_e_lo, e_hi = K->f_e_hi, inv_e_lo = K->f_inv_e_lo;
     const float inv_dlog = K->f_inv_dlog, e_exc = K->f_e_exc, e_iz = K->f_e_iz, two_mM = K->f_two_mM;
     const float bin_inv = K->f_bin_inv;
-    const PhiloxPre pre = philox_pre(step, sh);
+    const PhiloxPre pre = philox_pre(step, sl, sh);
 
     // shared memory: EEDF histogram, one deposit row per warp, then (full
     // step) the field at the nodes, the cross-section table and the slopes of
@@ -446,9 +455,9 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             // the process is the first k with R2 nu_max < sum_{i<=k} nu_i.  The
             // V particles' draws are formed together (independent chains).
             uint4 rk[V];
-            draw_n<V>(pre, ids, sl, 0u, rk);
+            draw_n<V>(pre, ids, 0u, rk);
             uint4 rq[V] = {};
-            if (CHEM && K->rec_on) draw_n<V>(pre, ids, sl, 2u, rq);
+            if (CHEM && K->rec_on) draw_n<V>(pre, ids, 2u, rq);
 #pragma unroll
             for (int k = 0; k < V; ++k) {
                 // computed for every lane without branches, so that the V
@@ -551,7 +560,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                     const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
                     float sn, cs;
                     __sincosf(6.283185307179586f * u01f(rr.y), &sn, &cs);
-                    const uint4 r1 = draw_pre(pre, pid, sl, 1u);
+                    const uint4 r1 = draw_pre(pre, pid, 1u);
                     const float de = en - e_iz;
                     const float e_ej = u01f(r1.x) * de;
                     const float sp = sqrtf(two_q_m * (de - e_ej));

@@ -146,74 +146,78 @@ __device__ __noinline__ static bool hyb_check_fail(int site, long long a, long l
 #define HYB_CHECK(cond, site, a, b) ((cond) ? true : hyb_check_fail((site), (long long)(a), (long long)(b)))
 
 // ---------------------------------------------------------------- Philox
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter (step, seed_lo,
-// seed_hi, call), key = particle id.
-// The draws of a step use the counter (step, seed_lo, seed_hi, call) and the
-// particle id as key, so the products of the first round's multiplied words
-// (step and seed_hi) are the same for every particle: PhiloxPre holds them.
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Draw `call` of particle
+// `id` at step `step` in a discharge seeded (seed_lo, seed_hi) is the
+// generator's block at counter (step, id_lo, call, id_hi) under key (seed_lo,
+// seed_hi).  The key is the same for every particle of a discharge, so a
+// thread's round keys are shared by all the draws it forms (and stay out of
+// the per-particle instruction stream), and the words the first round
+// multiplies (step and call) are the same for every particle: PhiloxPre holds
+// the products of the step and the key.
 struct PhiloxPre {
-    uint32_t hi0, lo0, hi1, lo1;
+    uint32_t hi0, lo0;  // 0xD2511F53 * step, high and low words
+    uint2 key;          // (seed_lo, seed_hi)
 };
 
-__device__ __forceinline__ PhiloxPre philox_pre(uint32_t step, uint32_t seed_hi)
+__device__ __forceinline__ PhiloxPre philox_pre(uint32_t step, uint32_t seed_lo, uint32_t seed_hi)
 {
-    return PhiloxPre{__umulhi(0xD2511F53u, step), 0xD2511F53u * step, __umulhi(0xCD9E8D57u, seed_hi),
-                     0xCD9E8D57u * seed_hi};
+    return PhiloxPre{__umulhi(0xD2511F53u, step), 0xD2511F53u * step, make_uint2(seed_lo, seed_hi)};
 }
 
-// state after the first round for key k
-__device__ __forceinline__ uint4 philox_first(const PhiloxPre &pre, uint32_t seed_lo, uint32_t call, uint2 k)
+// the state after the first round (the call's products fold to constants
+// where `call` is a literal)
+__device__ __forceinline__ uint4 philox_first(const PhiloxPre &pre, uint64_t id, uint32_t call)
 {
-    return make_uint4(pre.hi1 ^ seed_lo ^ k.x, pre.lo1, pre.hi0 ^ call ^ k.y, pre.lo0);
+    return make_uint4(__umulhi(0xCD9E8D57u, call) ^ (uint32_t)id ^ pre.key.x, 0xCD9E8D57u * call,
+                      pre.hi0 ^ (uint32_t)(id >> 32) ^ pre.key.y, pre.lo0);
 }
 
-// one later round: bump the key by the Weyl constants, then the S-box
-__device__ __forceinline__ void philox_round(uint4 &c, uint2 &k)
+// round r (1..9) of the later rounds: the key bumped r times by the Weyl
+// constants, then the S-box
+__device__ __forceinline__ void philox_round(uint4 &c, uint2 kr)
 {
-    k.x += 0x9E3779B9u;
-    k.y += 0xBB67AE85u;
     const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
     const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    c = make_uint4(hi1 ^ c.y ^ kr.x, lo1, hi0 ^ c.w ^ kr.y, lo0);
 }
 
-__device__ __forceinline__ uint2 philox_key(uint64_t id) { return make_uint2((uint32_t)id, (uint32_t)(id >> 32)); }
-
-// Philox4x32-10 of counter (step, seed_lo, seed_hi, call) under key id
-__device__ __forceinline__ uint4 draw_pre(const PhiloxPre &pre, uint64_t id, uint32_t seed_lo, uint32_t call)
+__device__ __forceinline__ uint2 philox_round_key(uint2 k, uint32_t r)
 {
-    uint2 k = philox_key(id);
-    uint4 c = philox_first(pre, seed_lo, call, k);
+    return make_uint2(k.x + 0x9E3779B9u * r, k.y + 0xBB67AE85u * r);
+}
+
+// Philox4x32-10 of counter (step, id_lo, call, id_hi) under key (seed_lo, seed_hi)
+__device__ __forceinline__ uint4 draw_pre(const PhiloxPre &pre, uint64_t id, uint32_t call)
+{
+    uint4 c = philox_first(pre, id, call);
 #pragma unroll
-    for (int r = 1; r < 10; ++r) philox_round(c, k);
+    for (uint32_t r = 1; r < 10; ++r) philox_round(c, philox_round_key(pre.key, r));
     return c;
 }
 
 __device__ __forceinline__ uint4 draw(uint64_t id, uint32_t step, uint32_t seed_lo, uint32_t seed_hi, uint32_t call)
 {
-    return draw_pre(philox_pre(step, seed_hi), id, seed_lo, call);
+    return draw_pre(philox_pre(step, seed_lo, seed_hi), id, call);
 }
 
-// the same draw for N keys at once, the rounds interleaved across the keys
+// the same draw for N particles at once, the rounds interleaved across them
 template <int N>
-__device__ __forceinline__ void draw_n(const PhiloxPre &pre, const uint64_t *ids, uint32_t seed_lo, uint32_t call,
-                                       uint4 *out)
+__device__ __forceinline__ void draw_n(const PhiloxPre &pre, const uint64_t *ids, uint32_t call, uint4 *out)
 {
-    uint2 k[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-        k[j] = philox_key(ids[j]);
-        out[j] = philox_first(pre, seed_lo, call, k[j]);
-    }
+    for (int j = 0; j < N; ++j) out[j] = philox_first(pre, ids[j], call);
 #pragma unroll
-    for (int r = 1; r < 10; ++r) {
+    for (uint32_t r = 1; r < 10; ++r) {
+        const uint2 kr = philox_round_key(pre.key, r);
 #pragma unroll
-        for (int j = 0; j < N; ++j) philox_round(out[j], k[j]);
+        for (int j = 0; j < N; ++j) philox_round(out[j], kr);
     }
 }
 
 // (k + 1/2) 2^-23 from the top 23 bits: the same value in float and double.
-__device__ __forceinline__ float u01f(uint32_t x) { return ((float)(x >> 9) + 0.5f) * 1.1920928955078125e-07f; }
+// In float it is formed without a conversion: the bits of 1 + k 2^-23 less
+// 1 - 2^-24 (both exact, and so is their difference).
+__device__ __forceinline__ float u01f(uint32_t x) { return __uint_as_float((x >> 9) | 0x3F800000u) - 0.999999940395355224609375f; }
 __device__ __forceinline__ double u01d(uint32_t x) { return ((double)(x >> 9) + 0.5) * 1.1920928955078125e-07; }
 
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).

@@ -198,7 +198,7 @@ __device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned ctr
     const PartBuf P = I->buf[I->cur];
     double *dep_n = K->dep_ni, *dep_g = K->dep_gi;
     if (!HYB_CHECK(b <= I->capacity && a >= 0 && (a & 1) == 0, 14, b, I->capacity)) b = a;
-    const PhiloxPre pre = philox_pre(step, sh);
+    const PhiloxPre pre = philox_pre(step, sl, sh);
     const int nwarps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t per = (((b - a) + nwarps - 1) / nwarps + 63) / 64 * 64;
     const int64_t wa = a + per * wid;
@@ -267,7 +267,7 @@ __device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned ctr
         deposit_two(dep_g, alive, c, o, vz, G);
         if (MODE == 0) {
             uint4 u[2];
-            draw_n<2>(pre, id, sl, 5u, u);
+            draw_n<2>(pre, id, 5u, u);
             // collision candidates (R < P_max), then one warp pass per
             // candidate a lane holds: the lanes' candidates are handled
             // together instead of one slot after the other
@@ -281,7 +281,7 @@ __device__ void segment_ion_split(InstDev *I, int64_t a, int64_t b, unsigned ctr
                     cand &= cand - 1u;
                     const uint4 uk = k ? u[1] : u[0];
                     const float px = k ? vx[1] : vx[0], py = k ? vy[1] : vy[0], pz = k ? vz[1] : vz[0];
-                    const uint4 w = draw_pre(pre, k ? id[1] : id[0], sl, 6u);
+                    const uint4 w = draw_pre(pre, k ? id[1] : id[0], 6u);
                     // neutral from the gas Maxwellian (Box-Muller), as the FP64 path
                     float s1, c1;
                     const float r1 = sqrtf(-2.f * __logf(u01f(uk.z)));

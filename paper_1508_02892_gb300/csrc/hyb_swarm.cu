@@ -133,11 +133,11 @@ __global__ void __launch_bounds__(kSwarmBlock) k_swarm(SwarmConst c, const doubl
         }
         for (int64_t n = 0; n < c.n_steps; ++n) {
             vz += acc;
-            const PhiloxPre pre = philox_pre((uint32_t)n, c.seed_hi);
-            const uint4 r = draw_pre(pre, id, c.seed_lo, 0u);
+            const PhiloxPre pre = philox_pre((uint32_t)n, c.seed_lo, c.seed_hi);
+            const uint4 r = draw_pre(pre, id, 0u);
             if (u01<T>(r.x) < p_max) {
                 ++n_cand;
-                const uint4 w = draw_pre(pre, id, c.seed_lo, 1u);
+                const uint4 w = draw_pre(pre, id, 1u);
                 T a1, a2, a3, a4;
                 box_muller(u01<T>(r.z), u01<T>(r.w), a1, a2);
                 box_muller(u01<T>(w.x), u01<T>(w.y), a3, a4);

@@ -74,6 +74,10 @@ def _check(g, o, p):
 
 
 def test_fp64_kinetic_ions_match_the_oracle():
+    """Births and ion collisions are many here; ion wall losses are not (in
+    100 steps of 0.2 ps an ion moves about 20 nm, so the count over a 0.5 mm
+    gap is a Poisson count of mean below 1): the ragged case below, on a
+    20 um gap, is the one that exercises them."""
     from paper_1508_02892_gb300 import hybrid
     p = _kinetic()
     g, o = hybrid.Discharge(p), oracle.Oracle(p)
@@ -81,7 +85,7 @@ def test_fp64_kinetic_ions_match_the_oracle():
     g.advance(100)
     o.step(100)
     c, ic = o.counters(), o.ion_counters()
-    assert c["births_iz"] > 100 and ic["losses0"] + ic["losses1"] > 0 and ic["collisions"] > 0
+    assert c["births_iz"] > 100 and ic["collisions"] > 0
     _check(g, o, p)
     g.close()
     # the ion-step counter: in step 0 every loaded ion and every ion born in it moves
@@ -109,9 +113,10 @@ def test_ion_kernels_have_their_own_profile_interval():
 
 def test_fp64_kinetic_ions_ragged_and_resorted():
     """A ragged size, a sort every 7 steps, and a gap of 20 um, narrow enough
-    for ions to reach both walls within the run and release gamma electrons."""
+    for ions to reach both walls within the run and release gamma electrons
+    (about 20 ion losses a wall with 77,777 ions, and gamma 0.2 of them)."""
     from paper_1508_02892_gb300 import hybrid
-    p = _kinetic(n_particles=7777, n_cells=97, gap_m=2e-5, sort_interval=7, te0_ev=20.0, weight=4e5,
+    p = _kinetic(n_particles=77777, n_cells=97, gap_m=2e-5, sort_interval=7, te0_ev=20.0, weight=4e5,
                  v_rf_amp_v=500.0, seed=62)
     g, o = hybrid.Discharge(p), oracle.Oracle(p)
     g.advance(90)
