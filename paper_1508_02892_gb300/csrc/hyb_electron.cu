@@ -264,16 +264,16 @@ __device__ __forceinline__ void row_deposit(WarpRow &row, int &base, InstDev *K,
         add_global(K, key, 1.0 - o, o, (1.0 - o) * en, (double)o * en, G);
         key = -1;
     }
-    if (__any_sync(kFull, key >= 0 && (key < base || key >= base + kWin))) {
+    if (__any_sync(kFull, key >= 0 && (unsigned)(key - base) >= (unsigned)kWin)) {
         row_flush(row, base, K, G);
         base = __reduce_min_sync(kFull, key >= 0 ? key : INT32_MAX) - kWin / 4;
+        if (key >= 0 && (unsigned)(key - base) >= (unsigned)kWin) {  // a warp spread over more than the row
+            add_global(K, key, 1.0 - o, o, (1.0 - o) * en, (double)o * en, G);
+            return;
+        }
     }
     if (key < 0) return;
     const int j = key - base;
-    if (j < 0 || j >= kWin) {  // a warp spread over more than the row
-        add_global(K, key, 1.0 - o, o, (1.0 - o) * en, (double)o * en, G);
-        return;
-    }
     atomicAdd(&row.n[j], 1u);
     atomicAdd(&row.a1[j], __float_as_uint(fmaf(o, kFixW, kFixBias)));
     atomicAdd(&row.e[j], __float_as_uint(fmaf(en, kFixE, kFixBias)));
@@ -299,6 +299,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
     const float pmax = K->f_pmax, e_lo = K->f_e_lo, e_hi = K->f_e_hi, inv_e_lo = K->f_inv_e_lo;
     const float inv_dlog = K->f_inv_dlog, e_exc = K->f_e_exc, e_iz = K->f_e_iz, two_mM = K->f_two_mM;
     const float bin_inv = K->f_bin_inv;
+    const float inv_dlog2 = inv_dlog * 0.693147180559945309f;  // segments per octave of energy
     const PhiloxPre pre = philox_pre(step, sl, sh);
 
     // shared memory: EEDF histogram, one deposit row per warp, then (full
@@ -467,7 +468,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 const float speed = sqrtf(vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
                 // table segment: below the table the first node's values,
                 // above it the last node's
-                int kk = (int)(__logf(fmaxf(en, e_lo) * inv_e_lo) * inv_dlog);
+                int kk = (int)(__log2f(fmaxf(en, e_lo) * inv_e_lo) * inv_dlog2);
                 kk = kk < 0 ? 0 : (kk > nxs - 2 ? nxs - 2 : kk);
                 // sigma_i(E) = sigma_i(E_k) + (E - E_k) slope_i with E clamped to
                 // the table: below it the first node's values, above the last's
@@ -513,10 +514,12 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 const float dx = st * cs, dy = st * sn, dzz = ct;
                 const float rs = rsqrtf(v2);
                 const float cchi = (vx[k] * dx + vy[k] * dy + vz[k] * dzz) * rs;
-                const float sp_el = v2 * rs * sqrtf(1.f - two_mM * (1.f - cchi));
-                const float sp_ex = sqrtf(two_q_m * (en - e_exc));
+                // the squared speed after either process; one square root
+                // for the one that happened
+                const float q_el = v2 * (1.f - two_mM * (1.f - cchi));
+                const float q_ex = two_q_m * (en - e_exc);
                 const bool scat = hit && kind != 3u;
-                const float sp = kind == 1u ? sp_el : sp_ex;
+                const float sp = sqrtf(kind == 1u ? q_el : q_ex);
                 vx[k] = scat ? sp * dx : vx[k];
                 vy[k] = scat ? sp * dy : vy[k];
                 vz[k] = scat ? sp * dzz : vz[k];
