@@ -414,7 +414,8 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             if (MODE == 0) {
                 const int cg = min(max(c, 0), nc - 1);
                 const float oi = alive ? o : 0.f;
-                const float ep = (1.f - oi) * Ef[cg] + oi * Ef[cg + 1];
+                const float e0 = Ef[cg];
+                const float ep = fmaf(oi, Ef[cg + 1] - e0, e0);
                 const float vzn = vz[k] - qm_dt * ep;
                 float on = oi + vzn * dt_dz;
                 const float fl = floorf(on);
@@ -447,7 +448,7 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
             for (int k = 0; k < V; ++k) {
                 const float en = ens[k];
                 int bin = (int)(en * bin_inv);
-                bin = (bin > nb || bin < 0 || !(en >= 0.f)) ? nb : bin;
+                bin = ((unsigned)bin > (unsigned)nb || !(en >= 0.f)) ? nb : bin;
                 atomicAdd(&s_eedf[live[k] ? bin : nb + 1], 1u);
             }
         }
@@ -507,10 +508,14 @@ __device__ void segment_split(InstDev *K, int64_t a, int64_t b, unsigned char *s
                 // lane and kept where they happened; ionizations, which eject
                 // an electron, go to the warp pass below
                 const float v2 = vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k];
-                const float ct = 1.f - 2.f * u01f(rk[k].z);
+                // cos chi = 1 - 2u and phi = 2 pi u, each one fused multiply-add
+                // of the bits 1 + k 2^-23 that u01f forms (u = those less
+                // 1 - 2^-24), rounded once
+                const float ct = fmaf(u01f_bits(rk[k].z), -2.f, 3.f);
                 const float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
                 float sn, cs;
-                __sincosf(6.283185307179586f * u01f(rk[k].w), &sn, &cs);
+                __sincosf(fmaf(u01f_bits(rk[k].w), 6.283185307179586f, -6.283185307179586f * 0.999999940395355224609375f),
+                          &sn, &cs);
                 const float dx = st * cs, dy = st * sn, dzz = ct;
                 const float rs = rsqrtf(v2);
                 const float cchi = (vx[k] * dx + vy[k] * dy + vz[k] * dzz) * rs;

@@ -217,7 +217,8 @@ __device__ __forceinline__ void draw_n(const PhiloxPre &pre, const uint64_t *ids
 // (k + 1/2) 2^-23 from the top 23 bits: the same value in float and double.
 // In float it is formed without a conversion: the bits of 1 + k 2^-23 less
 // 1 - 2^-24 (both exact, and so is their difference).
-__device__ __forceinline__ float u01f(uint32_t x) { return __uint_as_float((x >> 9) | 0x3F800000u) - 0.999999940395355224609375f; }
+__device__ __forceinline__ float u01f_bits(uint32_t x) { return __uint_as_float((x >> 9) | 0x3F800000u); }
+__device__ __forceinline__ float u01f(uint32_t x) { return u01f_bits(x) - 0.999999940395355224609375f; }
 __device__ __forceinline__ double u01d(uint32_t x) { return ((double)(x >> 9) + 0.5) * 1.1920928955078125e-07; }
 
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).
