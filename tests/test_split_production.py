@@ -1,8 +1,8 @@
 """The split production path (FP32 particles, FP64 field step) against the FP64
 oracle on the kinds of discharge the benchmark runs.
 
-North star, precision pattern: the error against the FP64 oracle is stated
-for every reported moment.  Two workloads beyond config 1's drift-diffusion:
+The error against the FP64 oracle is stated for every reported moment.
+Three workloads beyond config 1's drift-diffusion:
   * a reduced config 2 (He, 1 mm / 1000 cells, 250 V, gamma 0.1, full ion
     fluid, Eq. 2.3, with the He+ tables), 3e4 electrons, 400 steps;
   * a drift-diffusion discharge with the tabulated mobility and Eq. 2.7-2.8
