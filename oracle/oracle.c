@@ -955,7 +955,7 @@ static void ion_step(orc_sim *s, uint32_t n, const double *kz, const uint64_t *k
  *  - Penning ionization of the admixture, Delta N_e = R_P n_m n_N dt dV, and
  *    metastable pooling, Delta N_e = R_pool n_m^2 dt dV, per interior node j
  *    (dV = dz S): Delta N_e / N_p/sp superparticles, the integer part plus one
- *    with the probability of the fraction (the Bernoulli draw keyed by the
+ *    with the probability of the fraction (the Bernoulli draw indexed by the
  *    process and j, call 3); each new electron is placed uniformly in the
  *    node's cell [z_j - dz/2, z_j + dz/2) with the process's energy and an
  *    isotropic direction (call 7 of its own id), and its ion enters the ion

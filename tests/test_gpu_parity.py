@@ -280,8 +280,8 @@ def test_split_mode_statistics_config1():
 @pytest.mark.parametrize("lanes,sort_interval,field_threads", [(1, 20, 1024), (2, 7, 256), (4, 20, 512)])
 def test_batch_matches_single_runs_fp64(lanes, sort_interval, field_threads):
     """Each discharge gives the same result alone and inside a batch, whatever
-    the launch layout (RNG is keyed by particle id and step, so only summation
-    order differs).  250 steps cover two captured chunks plus single steps."""
+    the launch layout (every draw is a function of the particle id and step,
+    so only summation order differs).  250 steps cover two captured chunks plus single steps."""
     from paper_1508_02892_gb300 import hybrid
     ps = [W.config1(precision=W.FP64, n_particles=5000, n_cells=80, seed=21, te0_ev=6.0),
           W.config1(precision=W.FP64, n_particles=12000, n_cells=150, seed=22, ion_model=W.ION_FULL,
