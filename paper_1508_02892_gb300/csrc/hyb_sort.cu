@@ -17,8 +17,8 @@
 // cell; a slot's destination is that plus its rank within the tile.  (The
 // store is sorted at the previous sort and drifts by a few cells between
 // sorts, so a tile holds a few cells: the global atomics on the per-cell
-// counters, which every warp of a neighbourhood used to contend for, drop by
-// about two orders of magnitude.)
+// counters, which every warp of a neighbourhood used to contend for, drop
+// from one or more per 32 slots to a few per 1024.)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
