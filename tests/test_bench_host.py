@@ -44,3 +44,17 @@ def test_source_hash_ignores_comments_but_not_code():
     c = "int f(int x) {\n    return x + 2;\n}\n"
     assert bench.source_hash(a) == bench.source_hash(b)
     assert bench.source_hash(a) != bench.source_hash(c)
+
+
+def test_kernel_hash_covers_the_nvcc_flags_but_not_paths(monkeypatch):
+    """A profile taken under other compiler flags (say without -ftz) does not
+    match the kernel; the include paths, which differ between machines, do
+    not enter the hash."""
+    import bench
+    from paper_1508_02892_gb300 import build
+    flags = build._flags()
+    base = bench.kernel_hash()
+    monkeypatch.setattr(build, "_flags", lambda: [f for f in flags if f != "-ftz=true"])
+    assert bench.kernel_hash() != base
+    monkeypatch.setattr(build, "_flags", lambda: [f if not f.startswith("/") else "/elsewhere" + f for f in flags])
+    assert bench.kernel_hash() == base
