@@ -568,3 +568,42 @@ def test_moments_time_average_and_eedf_normalisation():
     # mean energy of a 2 eV Maxwellian, early in the run: 3 eV
     ebar = m["ebar"][m["ebar"] > 0]
     assert 2.0 < np.median(ebar) < 4.0
+
+
+def test_draw_layout_of_the_mcc():
+    """The documented stream layout: draw `call` of particle `id` at step n is
+    the Philox4x32-10 block at counter (n, id_lo, call, id_hi) under key
+    (seed_lo, seed_hi); the MCC takes words 0 and 1 for R1 < P_max and
+    R2 nu_max < nu(E), words 2 and 3 for the new direction (cos chi = 1 - 2u,
+    phi = 2 pi u).  Ids with the high word set (children) pin id_hi's place;
+    a seed with both words set pins the key's."""
+    L = 1e-3
+    p = _set_xs(_quiet(gap_m=L, n_cells=10, pressure_pa=1.28e4, seed=0x0123456789ABCDEF), el=6e-20)
+    o = oracle.Oracle(p)
+    E = np.zeros(11)
+    seed = p["seed"]
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    assert 0.3 < o.p_max < 0.7
+    ev = 300.0
+    v = math.sqrt(2 * ev * QE / ME)
+    n = 5
+    seen = set()
+    for k in range(300):
+        pid = k if k % 2 == 0 else (1 << 63) | (k * 0x9E3779B97F4A7C15 & ((1 << 63) - 1))
+        st = [0.5 * L, 0.0, 0.0, v]
+        oc, out, _, _ = o.particle_step_one(E, n, st, pid)
+        r = oracle.philox4x32_10([n, pid & 0xFFFFFFFF, 0, pid >> 32], key)
+        u = [oracle.u01(x) for x in r]
+        if not u[0] < o.p_max:
+            want = oracle.OUT_NONE
+        elif u[1] * o.nu_max < o.ngas * o.xs(ev)[0] * v:
+            want = oracle.OUT_ELASTIC
+        else:
+            want = oracle.OUT_NULL
+        assert oc == want, (k, oc, want)
+        seen.add(oc)
+        if oc == oracle.OUT_ELASTIC:
+            sp = np.linalg.norm(out[1:])
+            assert out[3] / sp == pytest.approx(1.0 - 2.0 * u[2], abs=1e-12)
+            assert math.atan2(out[2], out[1]) % (2 * math.pi) == pytest.approx(2 * math.pi * u[3], abs=1e-9)
+    assert seen == {oracle.OUT_NONE, oracle.OUT_ELASTIC, oracle.OUT_NULL}
